@@ -1,0 +1,68 @@
+"""ctypes wrappers around oracle/direct.c (test infrastructure only)."""
+import ctypes
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build.build())
+        d = ctypes.POINTER(ctypes.c_double)
+        ll = ctypes.c_longlong
+        _lib.oracle_direct.argtypes = [ll, d, d, d, ll, d, d, ctypes.c_double, d, d]
+        _lib.oracle_nsli.argtypes = [ll, d, d, d, d, ll, d, d, ctypes.c_double, d, d]
+        _lib.oracle_sum3.argtypes = [ll, d, d, d, d, ll, d, d, ctypes.c_double, d, d]
+        _lib.oracle_max_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def max_threads():
+    """Number of OpenMP threads the oracle sums use."""
+    return _load().oracle_max_threads()
+
+
+def direct_sum(x, y, w, xi, eta, lz):
+    """Eq. faq, unsplit: u_k = 1/(i lz) sum_j w_j exp(i pi |xi_k - x_j|^2 / lz)."""
+    lib = _load()
+    x, y, w, xi, eta = map(_c, (x, y, w, xi, eta))
+    re = np.empty(len(xi))
+    im = np.empty(len(xi))
+    lib.oracle_direct(len(x), _p(x), _p(y), _p(w), len(xi), _p(xi), _p(eta), float(lz),
+                      _p(re), _p(im))
+    return re + 1j * im
+
+
+def nsli(X, Y, W, V, xi, eta, lz):
+    """Appendix eq. nsli: u^ap = 1/(2pi) sum_i (1 - e^{i pi r^2/lz}) / r^2 (r x ds)_i."""
+    lib = _load()
+    X, Y, W, V, xi, eta = map(_c, (X, Y, W, V, xi, eta))
+    re = np.empty(len(xi))
+    im = np.empty(len(xi))
+    lib.oracle_nsli(len(X), _p(X), _p(Y), _p(W), _p(V), len(xi), _p(xi), _p(eta), float(lz),
+                    _p(re), _p(im))
+    return re + 1j * im
+
+
+def sum3(x, y, c, xi, eta, lz):
+    """Eq. nufft3 evaluated exactly: v_k = sum_j c_j exp(-2 pi i (xi_k x_j + eta_k y_j)/lz)."""
+    lib = _load()
+    x, y, xi, eta = map(_c, (x, y, xi, eta))
+    c = np.asarray(c, dtype=np.complex128)
+    cr, ci = _c(c.real), _c(c.imag)
+    re = np.empty(len(xi))
+    im = np.empty(len(xi))
+    lib.oracle_sum3(len(x), _p(x), _p(y), _p(cr), _p(ci), len(xi), _p(xi), _p(eta), float(lz),
+                    _p(re), _p(im))
+    return re + 1j * im

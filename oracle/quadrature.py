@@ -1,0 +1,116 @@
+"""Areal quadrature, built the plain way (test infrastructure only; see oracle/__init__.py).
+
+Everything is FP64 numpy, vectorised but with no blocking or fusion beyond the
+formulas below, so each line can be checked against the paper by eye.
+
+Panel-family description (plain dict, produced by ``workloads.py``):
+
+``{"kind": "fourier", "params": [r0, a1, b1, a2, b2, ...], "n_panels": P,
+   "p": p, "m": m, "cx": cx, "cy": cy}``
+    Boundary r(t) = r0 + sum_k (a_k cos kt + b_k sin kt) about the centre
+    (cx, cy), t in [0, 2pi) counter-clockwise; P panels of p Gauss-Legendre
+    nodes on t; m radial Gauss-Legendre nodes in the dilation rule.
+
+``{"kind": "line_rule", "X", "Y", "W", "V", "m", "cx", "cy"}``
+    An explicit vector line rule (eq. vliq) plus m radial nodes.
+
+``{"kind": "nodes", "x", "y", "w"}``
+    An explicit areal rule (eq. aq).
+"""
+import numpy as np
+
+
+def gauss_legendre(n, a=-1.0, b=1.0):
+    """n-point Gauss-Legendre nodes/weights on (a, b) (the rule named in Sec. 3.1).
+
+    The library primitive ``numpy.polynomial.legendre.leggauss`` supplies the
+    rule on (-1, 1); the affine map to (a, b) scales the weights by (b-a)/2.
+    """
+    t, wt = np.polynomial.legendre.leggauss(int(n))
+    x = 0.5 * (b - a) * (t + 1.0) + a
+    return x, 0.5 * (b - a) * wt
+
+
+def fourier_radius(params, t):
+    """r(t) = r0 + sum_k (a_k cos kt + b_k sin kt) and its derivative r'(t)."""
+    params = np.asarray(params, dtype=np.float64)
+    r = np.full_like(t, params[0])
+    dr = np.zeros_like(t)
+    K = (len(params) - 1) // 2
+    for k in range(1, K + 1):
+        a, b = params[2 * k - 1], params[2 * k]
+        r += a * np.cos(k * t) + b * np.sin(k * t)
+        dr += k * (-a * np.sin(k * t) + b * np.cos(k * t))
+    return r, dr
+
+
+def fourier_line_rule(params, n_panels, p, cx=0.0, cy=0.0):
+    """Vector line rule (X_i, Y_i, W_i, V_i) of eq. vliq on a Fourier star boundary.
+
+    The boundary x(t) = (cx + r(t) cos t, cy + r(t) sin t) is traversed
+    counter-clockwise for t in [0, 2pi).  As in eq. vliq1 the vector line
+    integral is int f(x(t)) . x'(t) dt; here the t-integral is split into
+    n_panels equal panels, each with a p-point Gauss-Legendre rule (the
+    configurations' choice in place of the periodic trapezoid rule of
+    eq. ptr), so W_i = what_i X'(t_i), V_i = what_i Y'(t_i).
+    Boundary index i runs panel-major, node-minor.
+    """
+    tq, wq = gauss_legendre(p, 0.0, 2.0 * np.pi / n_panels)
+    t = (np.arange(n_panels)[:, None] * (2.0 * np.pi / n_panels) + tq[None, :]).ravel()
+    what = np.tile(wq, n_panels)
+    r, dr = fourier_radius(params, t)
+    X = cx + r * np.cos(t)
+    Y = cy + r * np.sin(t)
+    dX = dr * np.cos(t) - r * np.sin(t)
+    dY = dr * np.sin(t) + r * np.cos(t)
+    return X, Y, what * dX, what * dY
+
+
+def ptr_line_rule(curve, dcurve, n):
+    """Periodic trapezoid vector line rule, eq. ptr: t_i = 2 pi i / n, weights 2pi/n."""
+    t = 2.0 * np.pi * np.arange(1, n + 1) / n
+    X, Y = curve(t)
+    dX, dY = dcurve(t)
+    return X, Y, (2.0 * np.pi / n) * dX, (2.0 * np.pi / n) * dY
+
+
+def dilation_rule(X, Y, W, V, m, cx=0.0, cy=0.0):
+    """Areal rule by dilation about (cx, cy): eqs. aqnod and aqwei (Sec. 3.1).
+
+    With alpha_l, wtilde_l the m-point Gauss-Legendre rule on (0, 1):
+        x_{l + (i-1)m} = c + alpha_l (X_i - c)
+        w_{l + (i-1)m} = alpha_l wtilde_l ((X_i - cx) V_i - (Y_i - cy) W_i)
+    (the paper's formulas with the origin moved to c).  Nodes may fall outside
+    a non-star-shaped domain and weights may be negative; nothing is clamped.
+    Returned arrays are ordered with the radial index l fastest.
+    """
+    alpha, wt = gauss_legendre(m, 0.0, 1.0)
+    dx = np.asarray(X) - cx
+    dy = np.asarray(Y) - cy
+    cross = dx * np.asarray(V) - dy * np.asarray(W)
+    x = cx + alpha[None, :] * dx[:, None]
+    y = cy + alpha[None, :] * dy[:, None]
+    w = (alpha * wt)[None, :] * cross[:, None]
+    return x.ravel(), y.ravel(), w.ravel()
+
+
+def family_line_rule(fam):
+    """The boundary vector line rule (X, Y, W, V) and centre of one panel family."""
+    kind = fam["kind"]
+    if kind == "fourier":
+        cx, cy = fam.get("cx", 0.0), fam.get("cy", 0.0)
+        return fourier_line_rule(fam["params"], fam["n_panels"], fam["p"], cx, cy) + (cx, cy)
+    if kind == "line_rule":
+        return (np.asarray(fam["X"], float), np.asarray(fam["Y"], float),
+                np.asarray(fam["W"], float), np.asarray(fam["V"], float),
+                fam.get("cx", 0.0), fam.get("cy", 0.0))
+    raise ValueError("family kind %r has no line rule" % kind)
+
+
+def family_nodes(fam):
+    """Areal nodes and weights (x, y, w) of one panel family."""
+    if fam["kind"] == "nodes":
+        return (np.asarray(fam["x"], float), np.asarray(fam["y"], float),
+                np.asarray(fam["w"], float))
+    X, Y, W, V, cx, cy = family_line_rule(fam)
+    return dilation_rule(X, Y, W, V, fam["m"], cx, cy)

@@ -1,0 +1,276 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Every check here is CPU-only.  The planted-mistake tests at the end put a
+plausible bug into a copy of the oracle (on the CPU) and confirm that at least
+one pin catches it.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import closed_forms as CF
+from oracle import direct as D
+from oracle import quadrature as Q
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ quadrature
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 16, 33])
+def test_gauss_legendre_polynomial_exactness(n):
+    """An n-point Gauss rule integrates x^k exactly on (0,1) for k <= 2n-1."""
+    x, w = Q.gauss_legendre(n, 0.0, 1.0)
+    for k in range(2 * n):
+        assert abs(np.sum(w * x ** k) - 1.0 / (k + 1)) < 1e-14
+    if n <= 5:  # and is not exact one degree higher (so it is the n-point rule)
+        assert abs(np.sum(w * x ** (2 * n)) - 1.0 / (2 * n + 1)) > 1e-8
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_gauss_legendre_large(n):
+    x, w = Q.gauss_legendre(n, 0.0, 1.0)
+    assert np.all(np.diff(x) > 0) and x[0] > 0 and x[-1] < 1
+    assert abs(w.sum() - 1.0) < 1e-14
+    # smooth integrand: int_0^1 cos(50 x) dx = sin(50)/50
+    assert abs(np.sum(w * np.cos(50 * x)) - np.sin(50.0) / 50.0) < 1e-14
+
+
+SHAPES = {
+    "disc": [1.0],
+    "star5": W.STAR_PARAMS,
+    "random20": list(W.random_star_params()),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SHAPES))
+def test_line_rule_area_by_green(name):
+    """(1/2) sum_i (X_i V_i - Y_i W_i) = area (Green's theorem on eq. vliq)."""
+    params = SHAPES[name]
+    X, Y, Wt, V = Q.fourier_line_rule(params, 64, 16)
+    assert abs(0.5 * np.sum(X * V - Y * Wt) - CF.fourier_star_area(params)) < 1e-13
+
+
+@pytest.mark.parametrize("name", sorted(SHAPES))
+def test_areal_rule_area_and_moments(name):
+    """Dilation rule (eqs. aqnod, aqwei): exact area, zero-free moments."""
+    params = SHAPES[name]
+    fam = W.fourier_family(params, 64, 16, 24)
+    x, y, w = Q.family_nodes(fam)
+    assert len(x) == 64 * 16 * 24
+    area = CF.fourier_star_area(params)
+    assert abs(w.sum() - area) < 1e-13
+    assert abs(np.sum(w * (x * x + y * y)) - CF.fourier_star_second_moment(params)) < 1e-13
+    if name in ("disc", "star5"):  # symmetric about the x axis and (disc) both axes
+        assert abs(np.sum(w * y)) < 1e-14
+
+
+def test_areal_rule_translated_centre():
+    fam = W.fourier_family(W.STAR_PARAMS, 32, 16, 16, cx=0.7, cy=-0.4)
+    x, y, w = Q.family_nodes(fam)
+    area = CF.fourier_star_area(W.STAR_PARAMS)
+    assert abs(w.sum() - area) < 1e-13
+    assert abs(np.sum(w * x) - 0.7 * area) < 1e-13
+    assert abs(np.sum(w * y) + 0.4 * area) < 1e-13
+
+
+def test_kite_printed_radius_and_fresnel_number():
+    """Sec. 4.1 prints R ~ 1.13 for the kite and F ~ 12.8 at lambda z = 0.1."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_printed.json")))["kite"]
+    t = np.linspace(0, 2 * np.pi, 200001)
+    R = np.max(np.hypot(0.5 * np.cos(t) + 0.5 * np.cos(2 * t), np.sin(t)))
+    assert round(R, 2) == g["R_max_approx"]
+    assert round(R * R / 0.1, 1) == g["fresnel_number_lz_0p1"]
+    assert round(R * R / 0.01, 0) == g["fresnel_number_lz_0p01"]
+    # kite area (Green): pi/2
+    X, Y, Wt, V = Q.ptr_line_rule(
+        lambda s: (0.5 * np.cos(s) + 0.5 * np.cos(2 * s), np.sin(s)),
+        lambda s: (-0.5 * np.sin(s) - np.sin(2 * s), np.cos(s)), 200)
+    x, y, w = Q.dilation_rule(X, Y, Wt, V, 8)
+    assert abs(w.sum() - np.pi / 2) < 1e-13
+
+
+# ------------------------------------------------------------------ field: closed forms
+def test_disc_on_axis_dauger():
+    """Appendix eq. dauger, R(theta) = R: u^ap(0) = 1 - e^{i pi R^2 / lz}."""
+    for lz, m in ((0.1, 64), (0.25, 32), (1.0 / 30.0, 128)):
+        fam = W.fourier_family([1.0], 64, 16, m)
+        u = oracle.field([fam], lz, 1.0, [0.0], [0.0])[0]
+        assert abs(u - CF.disc_on_axis(1.0, lz)) < 1e-12
+
+
+def test_disc_off_axis_golden():
+    """Direct sum vs the stored Hankel closed form of the disc at F = 10."""
+    g = json.load(open(os.path.join(GOLDEN, "disc_F10_hankel.json")))
+    rho = np.asarray(g["rho"])
+    ref = np.asarray(g["u_re"]) + 1j * np.asarray(g["u_im"])
+    fam = W.fourier_family([g["R"]], 64, 16, 64)
+    u = oracle.field([fam], g["lambda_z"], 1.0, rho, 0.0 * rho)
+    assert np.max(np.abs(u - ref)) < 1e-10
+    # the same closed form along another direction (rotational symmetry)
+    u2 = oracle.field([fam], g["lambda_z"], 1.0, rho * np.cos(1.0), rho * np.sin(1.0))
+    assert np.max(np.abs(u2 - ref)) < 1e-10
+    # the stored Hankel values carry ~1e-11 rounding (2 pi / lz times a 6000-term sum)
+    assert abs(ref[0] - complex(*g["u_axis_dauger"])) < 5e-11
+
+
+def test_nsli_matches_areal_direct_sum():
+    """Appendix eq. nsli (a line integral) vs eq. faq (an areal sum): independent formulas."""
+    fam = W.fourier_family(W.STAR_PARAMS, 128, 16, 96)
+    X, Y, Wt, V, cx, cy = Q.family_line_rule(fam)
+    g = W.rng(99, 3)
+    xi = np.concatenate([[0.0, -1.5, 1.3, 0.0], g.uniform(-1.5, 1.5, 60)])
+    eta = np.concatenate([[0.0, -1.5, 0.0, 1.0], g.uniform(-1.5, 1.5, 60)])
+    un = D.nsli(X, Y, Wt, V, xi, eta, 0.1)
+    ud = oracle.field([fam], 0.1, 1.0, xi, eta)
+    assert np.max(np.abs(un - ud)) < 1e-11
+
+
+def test_nsli_target_on_boundary_node():
+    """NSLI with a target exactly on a boundary node (r^2 = 0 branch) stays finite and accurate."""
+    fam = W.fourier_family([1.0], 64, 16, 64)
+    X, Y, Wt, V, _, _ = Q.family_line_rule(fam)
+    xi, eta = np.array([X[5]]), np.array([Y[5]])
+    un = D.nsli(X, Y, Wt, V, xi, eta, 0.1)
+    ref = CF.disc_off_axis(1.0, 0.1, [np.hypot(X[5], Y[5])])
+    assert np.isfinite(un).all() and abs(un[0] - ref[0]) < 1e-10
+
+
+@pytest.mark.parametrize("target", [(0.3, -0.2), (1.4, 0.9)])
+def test_brute_force_adaptive_tiny(target):
+    """Eq. fres by adaptive 2D quadrature on a tiny case (F ~ 1) vs the areal sum."""
+    params = [1.0, 0.0, 0.0, 0.1, 0.05]
+    fam = W.fourier_family(params, 32, 16, 32)
+    bf = CF.brute_force_star(params, 1.0, *target)
+    u = oracle.field([fam], 1.0, 1.0, [target[0]], [target[1]])[0]
+    assert abs(bf - u) < 1e-11
+
+
+# ------------------------------------------------------------------ field: invariants
+def _star_field(params, lz, xi, eta, cx=0.0, cy=0.0, n_panels=96, m=64):
+    fam = W.fourier_family(params, n_panels, 16, m, cx, cy)
+    return oracle.field([fam], lz, 1.0, np.asarray(xi), np.asarray(eta))
+
+
+def test_translation_invariance():
+    """u_{Omega+d}(xi) = u_Omega(xi - d) (eq. fres depends on xi - x only)."""
+    g = W.rng(98, 0)
+    xi, eta = g.uniform(-1.5, 1.5, 20), g.uniform(-1.5, 1.5, 20)
+    d = (0.31, -0.17)
+    a = _star_field(W.STAR_PARAMS, 0.1, xi + d[0], eta + d[1], *d)
+    b = _star_field(W.STAR_PARAMS, 0.1, xi, eta)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_scaling_invariance():
+    """u_{s Omega}(s xi; s^2 lz) = u_Omega(xi; lz)."""
+    s = 1.7
+    params = np.asarray(W.STAR_PARAMS)
+    g = W.rng(97, 0)
+    xi, eta = g.uniform(-1.5, 1.5, 20), g.uniform(-1.5, 1.5, 20)
+    a = _star_field(s * params, s * s * 0.1, s * xi, s * eta)
+    b = _star_field(params, 0.1, xi, eta)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_reflection_symmetry():
+    """A shape symmetric under y -> -y gives u(xi, -eta) = u(xi, eta); a rotated copy does not."""
+    g = W.rng(96, 0)
+    xi, eta = g.uniform(-1.5, 1.5, 16), g.uniform(-1.5, 1.5, 16)
+    a = _star_field(W.STAR_PARAMS, 0.1, xi, eta)
+    b = _star_field(W.STAR_PARAMS, 0.1, xi, -eta)
+    assert np.max(np.abs(a - b)) < 1e-12
+    p = list(W.STAR_PARAMS)
+    p[9], p[10] = 0.3 * np.cos(0.5), 0.3 * np.sin(0.5)  # rotated star: no longer symmetric
+    c = _star_field(p, 0.1, xi, eta)
+    d = _star_field(p, 0.1, xi, -eta)
+    assert np.max(np.abs(c - d)) > 1e-3
+
+
+def test_five_fold_rotation_symmetry():
+    th = 2 * np.pi / 5
+    g = W.rng(95, 0)
+    xi, eta = g.uniform(-1.5, 1.5, 16), g.uniform(-1.5, 1.5, 16)
+    a = _star_field(W.STAR_PARAMS, 0.1, xi, eta)
+    b = _star_field(W.STAR_PARAMS, 0.1, np.cos(th) * xi - np.sin(th) * eta,
+                    np.sin(th) * xi + np.cos(th) * eta)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_babinet_output_option():
+    """Eq. bab: the occulter field is 1 - the aperture field."""
+    fam = W.fourier_family(W.STAR_PARAMS, 32, 16, 16)
+    xi, eta = np.array([0.0, 0.4, 2.0]), np.array([0.0, -0.3, 1.0])
+    ua = oracle.field([fam], 0.1, 1.0, xi, eta, output="aperture")
+    uo = oracle.field([fam], 0.1, 1.0, xi, eta, output="occulter")
+    assert np.max(np.abs(ua + uo - 1.0)) == 0.0
+
+
+def test_split_identity_pins_sum3():
+    """Eq. split: direct sum = (1/(i lz)) chirp(xi) * sum3(c), c_j = w_j chirp(x_j)."""
+    fam = W.fourier_family(W.STAR_PARAMS, 32, 16, 24)
+    x, y, w = Q.family_nodes(fam)
+    lz = 0.05
+    g = W.rng(94, 0)
+    xi, eta = g.uniform(-1.5, 1.5, 50), g.uniform(-1.5, 1.5, 50)
+    c = w * np.exp(1j * np.pi * (x * x + y * y) / lz)
+    v = D.sum3(x, y, c, xi, eta, lz)
+    u = np.exp(1j * np.pi * (xi * xi + eta * eta) / lz) * v / (1j * lz)
+    ud = D.direct_sum(x, y, w, xi, eta, lz)
+    assert np.max(np.abs(u - ud)) < 1e-11
+
+
+# ------------------------------------------------------------------ planted mistakes
+def _pins_fail(monkeypatch, patch):
+    """Apply a plausible oracle bug and report whether the closed-form pins notice it."""
+    with monkeypatch.context() as mp:
+        patch(mp)
+        failures = 0
+        fam = W.fourier_family([1.0], 64, 16, 64)
+        x, y, w = Q.family_nodes(fam)
+        failures += abs(w.sum() - np.pi) > 1e-12
+        u = oracle.field([fam], 0.1, 1.0, [0.0, 0.6], [0.0, 0.3])
+        ref = CF.disc_off_axis(1.0, 0.1, [0.0, np.hypot(0.6, 0.3)])
+        failures += np.max(np.abs(u - ref)) > 1e-10
+        fs = W.fourier_family(W.STAR_PARAMS, 64, 16, 48)
+        us = oracle.field([fs], 0.1, 1.0, [0.4], [0.25])
+        X, Y, Wt, V, _, _ = Q.family_line_rule(fs)
+        un = D.nsli(X, Y, Wt, V, np.array([0.4]), np.array([0.25]), 0.1)
+        failures += abs(us[0] - un[0]) > 1e-11
+        return failures > 0
+
+
+def test_planted_dropped_alpha_in_weights(monkeypatch):
+    orig = Q.dilation_rule
+
+    def bad(X, Y, Wt, V, m, cx=0.0, cy=0.0):
+        x, y, w = orig(X, Y, Wt, V, m, cx, cy)
+        a, _ = Q.gauss_legendre(m, 0.0, 1.0)
+        return x, y, w / np.tile(a, len(X))  # drops the alpha_l Jacobian factor
+    assert _pins_fail(monkeypatch, lambda mp: mp.setattr(Q, "dilation_rule", bad))
+
+
+def test_planted_phase_sign(monkeypatch):
+    orig = D.direct_sum
+    # conj of the integrand = wrong sign of the phase, same normalisation
+    bad = lambda x, y, w, xi, eta, lz: -np.conj(orig(x, y, w, xi, eta, lz))
+    assert _pins_fail(monkeypatch, lambda mp: mp.setattr(D, "direct_sum", bad))
+
+
+def test_planted_transposed_coordinates(monkeypatch):
+    orig = D.direct_sum
+    bad = lambda x, y, w, xi, eta, lz: orig(x, y, w, eta, xi, lz)
+    # disc is symmetric under the swap; the star target (0.4, 0.25) is not
+    assert _pins_fail(monkeypatch, lambda mp: mp.setattr(D, "direct_sum", bad))
+
+
+def test_planted_wrong_tangent(monkeypatch):
+    orig = Q.fourier_line_rule
+
+    def bad(params, n_panels, p, cx=0.0, cy=0.0):
+        X, Y, Wt, V = orig(params, n_panels, p, cx, cy)
+        return X, Y, V, Wt  # W and V swapped
+    assert _pins_fail(monkeypatch, lambda mp: mp.setattr(Q, "fourier_line_rule", bad))

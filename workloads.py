@@ -1,0 +1,115 @@
+"""Seeded synthetic workloads shaped like the paper's experiments.
+
+This module only describes inputs: boundary descriptions (panel families),
+lambda*z, and target sets, drawn from numpy's seeded generators.  It holds
+none of the method's arithmetic, and both the CUDA library and the CPU oracle
+receive exactly these arrays.
+
+Panel-family dicts (see oracle/quadrature.py and the C header
+include/fresnel.h for how each side reads them):
+
+    {"kind": "fourier", "params": [r0, a1, b1, ...], "n_panels": P, "p": p,
+     "m": m, "cx": 0.0, "cy": 0.0}
+
+Workloads (Fresnel number F = R^2 / (lambda z), Sec. 2 eq. fn):
+
+* ``disc``  -- unit disc, F = 10 (lambda z = 0.1), 64 panels x 16 GL x m radial
+               (m = 16: 16,384 nodes), 100 x 100 grid with h = 0.03 spanning
+               [-1.5, 1.5)^2 (the paper's grid convention, Sec. 3.3).
+* ``star``  -- r = 1 + 0.3 cos 5 theta, F = 100 with R = max r = 1.3
+               (lambda z = 0.0169), 128 x 16 x 256 = 524,288 nodes;
+               grid 1000 x 1000 with h = 0.003, and 1e6 scattered targets
+               uniform in the disc of radius 1.5.
+* ``random_star`` -- r = 1 + sum_{k=1}^{20} a_k cos(k theta + phi_k),
+               a_k ~ U(0, 0.02), phi_k ~ U(0, 2 pi); F = 1000 with R = max r
+               over 1e5 samples; 640 x 16 x 1024 = 10,485,760 nodes; scattered
+               targets uniform in [-1.2, 1.2]^2 (1e8 at full size).
+"""
+import numpy as np
+
+SEED0 = 20105978
+
+
+def rng(config_id, stream=0):
+    """numpy Generator seeded by the paper id, the workload id and a sub-stream."""
+    return np.random.default_rng([SEED0 + int(config_id), int(stream)])
+
+
+def fourier_family(params, n_panels, p, m, cx=0.0, cy=0.0):
+    return {"kind": "fourier", "params": np.asarray(params, dtype=np.float64),
+            "n_panels": int(n_panels), "p": int(p), "m": int(m),
+            "cx": float(cx), "cy": float(cy)}
+
+
+def grid_spec(n1, n2, h, x0=0.0, y0=0.0):
+    return {"n1": int(n1), "n2": int(n2), "h": float(h), "x0": float(x0), "y0": float(y0)}
+
+
+# ---------------------------------------------------------------- disc (F = 10)
+def disc(m=16, n_panels=64, p=16, n=100, R=1.0):
+    return {
+        "name": "disc_F10",
+        "families": [fourier_family([R], n_panels, p, m)],
+        "lam": 0.1, "z": 1.0,
+        "grid": grid_spec(n, n, 3.0 / n),
+    }
+
+
+# ---------------------------------------------------------------- star (F = 100)
+STAR_PARAMS = [1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.3, 0.0]
+
+
+def star(n_panels=128, p=16, m=256, n=1000, lz=1.3 ** 2 / 100.0):
+    return {
+        "name": "star5_F100",
+        "families": [fourier_family(STAR_PARAMS, n_panels, p, m)],
+        "lam": lz, "z": 1.0,
+        "grid": grid_spec(n, n, 3.0 / n),
+    }
+
+
+def disc_targets(M, radius, config_id, stream=1):
+    """M targets uniform in the disc |xi| <= radius: rho = radius sqrt(U), theta = 2 pi V."""
+    g = rng(config_id, stream)
+    u = g.random(M)
+    v = g.random(M)
+    rho = radius * np.sqrt(u)
+    th = 2.0 * np.pi * v
+    return rho * np.cos(th), rho * np.sin(th)
+
+
+def square_targets(M, half, config_id, stream=1):
+    """M targets uniform in [-half, half]^2."""
+    g = rng(config_id, stream)
+    return g.uniform(-half, half, M), g.uniform(-half, half, M)
+
+
+# ---------------------------------------------------------------- random star (F = 1000)
+def random_star_params(config_id=5, K=20, amax=0.02):
+    g = rng(config_id, 0)
+    a = g.uniform(0.0, amax, K)
+    ph = g.uniform(0.0, 2.0 * np.pi, K)
+    params = [1.0]
+    for k in range(K):
+        # a cos(k t + ph) = a cos(ph) cos(k t) - a sin(ph) sin(k t)
+        params += [a[k] * np.cos(ph[k]), -a[k] * np.sin(ph[k])]
+    return np.asarray(params)
+
+
+def max_radius(params, n=100000):
+    th = 2.0 * np.pi * np.arange(n) / n
+    params = np.asarray(params)
+    r = np.full(n, params[0])
+    for k in range(1, (len(params) - 1) // 2 + 1):
+        r += params[2 * k - 1] * np.cos(k * th) + params[2 * k] * np.sin(k * th)
+    return float(r.max())
+
+
+def random_star(n_panels=640, p=16, m=1024, fresnel_number=1000.0, config_id=5):
+    params = random_star_params(config_id)
+    R = max_radius(params)
+    return {
+        "name": "randstar20_F1000",
+        "families": [fourier_family(params, n_panels, p, m)],
+        "lam": R * R / fresnel_number, "z": 1.0,
+    }
