@@ -1,0 +1,328 @@
+"""Throughput benchmark: Fresnel target points per second at 1e-6 relative L2.
+
+Workload (one "step" = one pass of the whole hot path): the star aperture
+r = 1 + 0.3 cos 5 theta at Fresnel number 100 (lambda z = 0.0169, R = 1.3),
+128 panels x 16 x 256 = 524,288 quadrature nodes regenerated every step, then
+  (a) type 1: the 1000 x 1000 target grid over [-1.5, 1.5)^2 (h = 0.003), and
+  (b) type 3: 1,000,000 scattered targets uniform in the disc of radius 1.5,
+both in FP32 fast mode at tol 1e-6 (phases in FP64).  Metric value = 2e6
+targets / step time.  Synthetic, seeded inputs (workloads.py).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent copy (weak scaling, no data
+collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Fresnel target pts/sec at 1e-6 rel L2 err"
+UNIT = "targets/s"
+TOL = 1e-6
+M3 = 1_000_000
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload():
+    cfg = W.star()
+    xi, eta = W.disc_targets(M3, 1.5, 2)
+    return cfg, np.ascontiguousarray(np.stack([xi, eta], 1))
+
+
+def config_dict(cfg, n_gpus):
+    g = cfg["grid"]
+    return {"workload": "star5_F100: r=1+0.3cos5t, F=100 (lz=0.0169), 524288 nodes (128x16x256), "
+                        "t1 1000x1000 grid h=0.003 + t3 1e6 targets in disc r<=1.5",
+            "nodes": 524288, "t1_targets": g["n1"] * g["n2"], "t3_targets": M3,
+            "tol": TOL, "precision": "fp32 spread/fft/interp, fp64 phases",
+            "nodes_recomputed_each_step": True,
+            "l2": "flushed between timed steps (512 MiB write)",
+            "parallelism": "replicas x%d (independent instances, no collective)" % n_gpus}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        def run():
+            q = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap")
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                          "--query-gpu=" + q, "--format=csv,noheader,nounits"],
+                                         capture_output=True, text=True, timeout=5).stdout
+                    f = [s.strip() for s in out.strip().split(",")]
+                    if len(f) >= 7:
+                        self.samples.append(f)
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_rate(cfg, targets, budget_s):
+    """Oracle (as it stands) on a bounded sample: quadrature + direct sum, targets/s."""
+    import oracle
+    from oracle import direct
+    fam = cfg["families"]
+    g = cfg["grid"]
+    gx, gy = oracle.grid_targets(g["n1"], g["n2"], g["h"])
+    rng = W.rng(2, 11)
+    t0 = time.perf_counter()
+    oracle.field(fam, cfg["lam"], cfg["z"], gx[:8], gy[:8])
+    probe = time.perf_counter() - t0
+    per_target = max(probe / 8, 1e-6)
+    m = int(max(16, min(20000, budget_s / per_target)))
+    m -= m % 2
+    ig = rng.choice(len(gx), m // 2, replace=False)
+    it = rng.choice(len(targets), m // 2, replace=False)
+    xi = np.concatenate([gx[ig], targets[it, 0]])
+    eta = np.concatenate([gy[ig], targets[it, 1]])
+    t0 = time.perf_counter()
+    oracle.field(fam, cfg["lam"], cfg["z"], xi, eta)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": UNIT, "cores": direct.max_threads(), "kind": "oracle",
+            "sample": "%d targets (%d grid + %d scattered) of the same workload, quadrature "
+                      "rebuilt + direct O(NM) FP64 sum (eq. faq), %.1f s" % (m, m // 2, m // 2, dt)}
+
+
+def run_reference(args, rank, world):
+    cfg, targets = workload()
+    from oracle import build as obuild
+    obuild.build()
+    if rank != 0:
+        return
+    budget = 6.0
+    for _ in range(args.warmup):
+        oracle_rate(cfg, targets, 0.5)
+    vals, times = [], []
+    for _ in range(args.steps):
+        r = oracle_rate(cfg, targets, budget)
+        vals.append(r["value"])
+        times.append(budget)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 2e6 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(cfg, args.gpus),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+ALGO_BYTES = {}
+
+
+def algorithmic_bytes(info1, info3, n_nodes):
+    """Minimum bytes each stage must move (FP32 fast mode), per launch."""
+    rec = 24                       # node record: 2 x int32 cell, 2 x f32 fraction, c64 strength
+    c64 = 8
+    nf1, nf2 = info1["nf1"], info1["nf2"]
+    g3 = info3["nf1"] * info3["nf2"]
+    F3 = info3["nfft1"] * info3["nfft2"]
+    return {
+        # t1
+        "t1.spread": n_nodes * rec + nf1 * nf2 * c64,
+        "t1.fft_rows": nf1 * nf2 * c64 + 1000 * nf2 * c64,
+        "t1.fft_cols_epilogue": 1000 * nf2 * c64 + 1000 * 1000 * c64,
+        # t3
+        "t3.spread": n_nodes * rec + g3 * c64,
+        "t3.fft_rows": g3 * c64 + info3["nf2"] * info3["nfft1"] * c64,
+        "t3.fft_cols": info3["nf2"] * info3["nfft1"] * c64 + F3 * c64,
+        "t3.interp_epilogue": M3 * (16 + c64),
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2010_05978_gb300 import Plan, build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg, targets_np = workload()
+    fam, g = cfg["families"], cfg["grid"]
+    stream = torch.cuda.current_stream()
+    p1 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision="fp32", grid=g, recompute_nodes=True,
+              sync_status=False)
+    p3 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision="fp32", box=(-1.5, 1.5, -1.5, 1.5),
+              recompute_nodes=True, sync_status=False)
+    p1.set_timing(True)
+    p3.set_timing(True)
+    info1, info3 = p1.info(), p3.info()
+    targets = torch.tensor(targets_np, dtype=torch.float64, device=dev)
+    out1 = torch.empty((g["n2"], g["n1"]), dtype=torch.complex64, device=dev)
+    out3 = torch.empty((M3,), dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        p1.eval(None, out1)
+        p3.eval(targets, out3)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    p1.check()
+    p3.check()
+
+    stage_sum = {}
+    step_ms = []
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step()
+        e.record(stream)
+        e.synchronize()
+        step_ms.append(s.elapsed_time(e))
+        for k, v in p1.stage_times().items():
+            stage_sum["t1." + k] = stage_sum.get("t1." + k, 0.0) + v
+        for k, v in p3.stage_times().items():
+            stage_sum["t3." + k] = stage_sum.get("t3." + k, 0.0) + v
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    p1.check()
+    p3.check()
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = 2e6 * world / (ms_per_step * 1e-3)
+
+    # ---------------- end-to-end through the C ABI with host buffers
+    h_t3 = targets_np
+    h_out1 = np.empty((g["n2"], g["n1"]), np.complex64)
+    h_out3 = np.empty((M3,), np.complex64)
+    for _ in range(2):
+        p1.eval_host(None, h_out1)
+        p3.eval_host(h_t3, h_out3)
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p1.eval_host(None, h_out1)
+        p3.eval_host(h_t3, h_out3)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = 2e6 * world / (statistics.median(e2e_ms) * 1e-3)
+
+    if rank != 0:
+        return
+    # ---------------- roofline of the dominant kernel
+    per_launch = {k: v / args.steps for k, v in stage_sum.items()}
+    ab = algorithmic_bytes(info1, info3, info1["n_nodes"])
+    dominant = max((k for k in per_launch if k in ab), key=lambda k: per_launch[k])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = ab[dominant] / (per_launch[dominant] * 1e-3) / 1e9
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+        traffic = prof.get(dominant)
+    except Exception:
+        pass
+    cpu = oracle_rate(cfg, targets_np, 10.0)
+    launches = (info1["launches_per_eval"] + info3["launches_per_eval"]) * args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(cfg, world),
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
+                                    "fallback 6800 GB/s",
+                     "algorithmic_bytes": ab[dominant], "ms_per_launch": per_launch[dominant]},
+        "stages_ms_per_step": {k: round(v, 5) for k, v in sorted(per_launch.items())},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_t3.nbytes),
+                "d2h_bytes_per_step": int(h_out1.nbytes + h_out3.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * fresnel.h -- C ABI of libfresnel: scalar Fresnel diffraction of a planar
+ * aperture or occulter by areal quadrature + one 2D nonuniform FFT, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Barnett, "Efficient high-order accurate Fresnel diffraction via
+ * areal quadrature and the nonuniform FFT", arXiv:2010.05978.
+ *   u^ap(xi, eta) = 1/(i lz) iint_Omega exp(i pi [(xi-x)^2 + (eta-y)^2] / lz) dx dy
+ * (eq. fres, Sec. 2; lz = lambda * z; the plane-wave phase e^{2 pi i z/lambda}
+ * is dropped as in Sec. 2) is approximated by an areal quadrature (x_j, y_j,
+ * w_j) (eq. aq) and evaluated in the split form of eq. split:
+ *   c_j = w_j exp(i pi |x_j|^2 / lz)                      (Sec. 3.2, step 1)
+ *   v_k = sum_j exp(-2 pi i xi_k . x_j / lz) c_j           (eq. nufft3, step 2)
+ *   u_k = 1/(i lz) exp(i pi |xi_k|^2 / lz) v_k             (Sec. 3.2, step 3)
+ * Step 2 is a 2D type-1 NUFFT for targets on a uniform grid (Sec. 3.3) or a
+ * type-3 NUFFT for scattered targets (Sec. 3.2).  The occulter field is
+ * u^oc = 1 - u^ap (Babinet, eq. bab).
+ *
+ * Conventions for every entry point:
+ *  - Status codes are returned, never thrown; fresnel_last_error() gives a
+ *    message for the calling thread's most recent failure.
+ *  - "host" pointers are read during the call only and may be freed after it.
+ *  - "device" pointers must be CUDA device (or managed) memory on the device
+ *    that was current when the plan was made; they are owned by the caller.
+ *  - All device work is enqueued on the plan's stream (the cudaStream_t given
+ *    to fresnel_plan, or the legacy default stream for NULL).
+ */
+#ifndef FRESNEL_H
+#define FRESNEL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+    FRESNEL_OK = 0,
+    FRESNEL_ERR_ARG = -1,         /* invalid argument; nothing was launched */
+    FRESNEL_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    FRESNEL_ERR_OOM = -3,         /* device allocation failed or exceeded the cap */
+    FRESNEL_ERR_TIMEOUT = -4,     /* a bounded device wait gave up */
+    FRESNEL_ERR_UNSUPPORTED = -5, /* valid request beyond this build's limits */
+    FRESNEL_ERR_DEVICE = -6       /* a device-side check failed (e.g. target outside the plan's box) */
+} fresnel_status;
+
+/* ---------------------------------------------------------------- geometry */
+/*
+ * One family of quadrature nodes.  kind selects how params is read:
+ *
+ * FRESNEL_FAMILY_FOURIER: a smooth star-shaped boundary about (cx, cy),
+ *     X(t) = cx + r(t) cos t, Y(t) = cy + r(t) sin t, t in [0, 2 pi)
+ *     counter-clockwise, r(t) = r0 + sum_{k=1}^{K} (a_k cos kt + b_k sin kt),
+ *     params = [r0, a_1, b_1, ..., a_K, b_K] (n_params = 1 + 2K).
+ *     The vector line rule (eq. vliq) uses n_panels equal t-panels with p
+ *     Gauss-Legendre nodes each: W_i = what_i X'(t_i), V_i = what_i Y'(t_i)
+ *     (eq. vliq1 with panels in place of the trapezoid rule).  The areal rule
+ *     is the dilation rule about (cx, cy) with m Gauss-Legendre radii on (0,1)
+ *     (eqs. aqnod, aqwei, Sec. 4.1): N = n_panels * p * m nodes.
+ *
+ * FRESNEL_FAMILY_LINE_RULE: an explicit vector line rule on the boundary,
+ *     params = [X_1..X_n, Y_1..Y_n, W_1..W_n, V_1..V_n] (n_params = 4n), with
+ *     n = n_panels * p (p may be 1), dilated about (cx, cy) with m radii.
+ *
+ * FRESNEL_FAMILY_NODES: an explicit areal rule (eq. aq),
+ *     params = [x_1..x_N, y_1..y_N, w_1..w_N] (n_params = 3N); the other
+ *     fields are ignored.
+ *
+ * Negative weights and nodes outside Omega (non-star-shaped domains, Sec. 4.1)
+ * are accepted as given.  params is a HOST array copied during fresnel_plan.
+ */
+enum {
+    FRESNEL_FAMILY_FOURIER = 0,
+    FRESNEL_FAMILY_LINE_RULE = 1,
+    FRESNEL_FAMILY_NODES = 2
+};
+
+typedef struct {
+    int kind;
+    int n_panels, p, m;
+    const double* params;   /* host */
+    long long n_params;
+    double cx, cy;
+} fresnel_family;
+
+/* ---------------------------------------------------------------- options */
+enum { FRESNEL_FP64 = 0, FRESNEL_FP32_FAST = 1 };
+enum { FRESNEL_APERTURE = 0, FRESNEL_OCCULTER = 1 };
+enum { FRESNEL_GRID = 0, FRESNEL_SCATTERED = 1 };
+
+typedef struct {
+    /* FRESNEL_FP64: every stage in FP64; output complex128 (re, im doubles).
+     * FRESNEL_FP32_FAST: spreading, FFT and interpolation in FP32 with FP32
+     * accumulation; the chirp phases and the xi.x/lz scalings stay FP64 with
+     * argument reduction; output complex64 (re, im floats). */
+    int precision;
+    int output;          /* FRESNEL_APERTURE (u^ap) or FRESNEL_OCCULTER (1 - u^ap) */
+    int target_kind;     /* FRESNEL_GRID (type 1, Sec. 3.3) or FRESNEL_SCATTERED (type 3, Sec. 3.2) */
+    /* GRID targets: xi = grid_x0 + k1 h, eta = grid_y0 + k2 h,
+     * -floor(n/2) <= k < n - floor(n/2); output index k2' * grid_n1 + k1'
+     * with k' = k + floor(n/2) (k1 fastest).  A nonzero (x0, y0) is applied
+     * by pre-phasing the strengths (Sec. 3.3, last paragraph). */
+    int grid_n1, grid_n2;
+    double grid_h, grid_x0, grid_y0;
+    /* SCATTERED targets must lie in [box[0], box[1]] x [box[2], box[3]]; the
+     * plan sizes its grids from this box and eval flags targets outside it
+     * (FRESNEL_ERR_DEVICE). */
+    double box[4];
+    double sigma;        /* upsampling factor; 0 = automatic */
+    int kernel_w;        /* spreading kernel width in grid points; 0 = automatic */
+    int recompute_nodes; /* 1: node generation, chirp and binning run inside every
+                            fresnel_eval (nothing node-sized is cached); 0: done once */
+    int sync_status;     /* 1: fresnel_eval synchronises the stream and returns the
+                            device status; 0: asynchronous, see fresnel_check */
+    long long max_device_bytes; /* cap on the plan's device memory; 0 = no cap */
+} fresnel_opts;
+
+/* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,
+ * automatic sigma/width, recompute_nodes = 0, sync_status = 1. */
+void fresnel_default_opts(fresnel_opts* opts);
+
+/* ---------------------------------------------------------------- plan */
+typedef struct fresnel_plan_s* fresnel_plan_t;   /* opaque; owned by the library */
+
+/*
+ * Builds the quadrature of the n_families families, chooses the NUFFT
+ * parameters for the requested relative tolerance tol (1e-14 <= tol <= 1e-1),
+ * and allocates all device scratch.  lambda > 0, z > 0 (only lambda*z enters,
+ * eq. fres).  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * On success *out_plan receives the plan; on failure *out_plan is NULL and
+ * nothing stays allocated.  Synchronises the stream before returning.
+ */
+fresnel_status fresnel_plan(const fresnel_family* families, int n_families,
+                            double lambda, double z, double tol,
+                            const fresnel_opts* opts, void* cuda_stream,
+                            fresnel_plan_t* out_plan);
+
+/*
+ * Evaluates u at the plan's targets.
+ * GRID plans: d_targets is ignored (may be NULL) and M must equal n1 * n2.
+ * SCATTERED plans: d_targets is a DEVICE array of M (xi, eta) FP64 pairs
+ * (interleaved, 16 bytes per target); M >= 0.
+ * d_out is a DEVICE array of M complex values (complex128 for FP64 plans,
+ * complex64 for FP32_FAST plans), written in target order.
+ * Asynchronous on the plan's stream unless opts.sync_status = 1.
+ */
+fresnel_status fresnel_eval(fresnel_plan_t plan, const double* d_targets, long long M,
+                            void* d_out);
+
+/*
+ * The same evaluation with HOST buffers: h_targets (M FP64 pairs, ignored for
+ * GRID plans) is copied to the device, fresnel_eval runs, and the M complex
+ * results are copied back to h_out.  Synchronous.  Pinned host memory makes
+ * the copies faster but is not required.
+ */
+fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, long long M,
+                                 void* h_out);
+
+/* Synchronises the plan's stream and returns (then clears) the device status
+ * word: FRESNEL_OK, FRESNEL_ERR_DEVICE or FRESNEL_ERR_TIMEOUT. */
+fresnel_status fresnel_check(fresnel_plan_t plan);
+
+/* Releases everything the plan owns.  NULL-safe; synchronises the stream. */
+fresnel_status fresnel_destroy(fresnel_plan_t plan);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* fresnel_last_error(void);
+
+/* ---------------------------------------------------------------- introspection */
+typedef struct {
+    long long n_nodes;      /* N, total quadrature nodes */
+    int w;                  /* spreading kernel width (grid points) */
+    double beta;            /* exponential-of-semicircle shape parameter */
+    double sigma;           /* upsampling factor used */
+    int nf1, nf2;           /* spreading grid */
+    int nfft1, nfft2;       /* FFT grid (= spreading grid for GRID plans) */
+    int tile_x, tile_y;     /* spreading tile */
+    long long device_bytes; /* device memory the plan holds */
+    int launches_per_eval;  /* kernels launched by one fresnel_eval */
+} fresnel_info;
+
+fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info);
+
+/*
+ * Copies the plan's quadrature nodes (x, y, w; FP64, N each) into DEVICE
+ * arrays, in family order and, within a family, boundary-node-major with the
+ * radial index fastest (eqs. aqnod, aqwei).  For checking the quadrature.
+ */
+fresnel_status fresnel_get_nodes(fresnel_plan_t plan, double* d_x, double* d_y, double* d_w);
+
+/*
+ * Per-stage device time of the last fresnel_eval, in milliseconds, measured
+ * with CUDA events on the plan's stream when timing was enabled by
+ * fresnel_set_timing(plan, 1).  stage_ms receives up to max_stages values;
+ * names (optional) receives static strings.  Returns the number of stages.
+ */
+int fresnel_set_timing(fresnel_plan_t plan, int enable);
+int fresnel_stage_times(fresnel_plan_t plan, double* stage_ms, const char** names, int max_stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRESNEL_H */

@@ -30,4 +30,4 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, invariants or brute force; none is "parity unpinned".
 """
 from . import quadrature, closed_forms  # noqa: F401
-from .field import field, nodes  # noqa: F401
+from .field import field, nodes, grid_targets  # noqa: F401

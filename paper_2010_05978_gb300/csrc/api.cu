@@ -1,0 +1,775 @@
+// C ABI and plan runtime of libfresnel (declared in include/fresnel.h).
+//
+// A plan fixes the aperture (its panel families), lambda*z, the targets'
+// layout (uniform grid: type-1 NUFFT, Sec. 3.3; scattered targets in a box:
+// type-3 NUFFT, Sec. 3.2 of arXiv:2010.05978) and the tolerance, chooses the
+// spreading kernel and grids, allocates every device buffer once, and builds
+// the plan-time tables.  fresnel_eval then only launches kernels on the
+// plan's stream:
+//   nodes+chirp+count -> scan -> scatter   (skipped when nodes are cached)
+//   spread -> FFT rows -> FFT columns (+ fused type-1 epilogue)
+//   [type 3: -> interpolation + deconvolution + post-phase/chirp]
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace fres;
+
+static thread_local std::string g_last_error;
+
+fresnel_status fres_fail(fresnel_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define FRES_CK(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fres_fail(e_ == cudaErrorMemoryAllocation ? FRESNEL_ERR_OOM               \
+                                                             : FRESNEL_ERR_CUDA,             \
+                             std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+namespace {
+
+constexpr uint64_t kMagic = 0x46524553'4e454c31ull;   // "FRESNEL1"
+constexpr int kMaxEvents = 16;
+
+struct Plan {
+    uint64_t magic = kMagic;
+    int prec = FRESNEL_FP32_FAST, output = 0, tkind = 0;
+    double lz = 0, tol = 0;
+    cudaStream_t st = nullptr;
+    fresnel_opts opts{};
+    std::vector<FamilyDev> fams;
+    long long N = 0;
+    KernelShape ks{};
+    double sigma = 2.0;
+    int nf1 = 0, nf2 = 0, nfft1 = 0, nfft2 = 0;
+    int n1 = 0, n2 = 0;
+    int ntx = 0, nty = 0, ntiles = 0;
+    int chunk_cap = 0, max_chunks = 0, max_slots = 0;
+    long long n_records = 0;
+    int spread_blocks = 0;
+    ChirpParams cp{};
+    InterpParams ip{};
+    FftPlan fp1{}, fp2{};
+    std::vector<void*> allocs;
+    long long bytes = 0;
+    void* rec = nullptr;
+    void* sorted = nullptr;
+    int* counts = nullptr;
+    int* cursor = nullptr;
+    Chunk* chunks = nullptr;
+    int* n_chunks = nullptr;
+    int* tile_counters = nullptr;
+    void* partials = nullptr;
+    void* grid = nullptr;
+    void* inter = nullptr;
+    void* F = nullptr;
+    void* tw1 = nullptr;
+    void* tw2 = nullptr;
+    void* ax = nullptr;
+    void* ay = nullptr;
+    void* dec1 = nullptr;
+    void* dec2 = nullptr;
+    double* gq_t = nullptr;
+    double* gq_w = nullptr;
+    int gq_n = 0;
+    unsigned* status = nullptr;
+    bool nodes_ready = false;
+    double* stage_tgt = nullptr;
+    void* stage_out = nullptr;
+    long long stage_cap = 0;
+    int timing = 0;
+    cudaEvent_t ev[kMaxEvents] = {};
+    const char* ev_name[kMaxEvents] = {};
+    int nev = 0;
+    int launches = 0;
+
+    size_t csize() const { return prec == FRESNEL_FP64 ? 16 : 8; }
+    size_t rsize() const { return prec == FRESNEL_FP64 ? sizeof(NodeRec<double>) : sizeof(NodeRec<float>); }
+};
+
+fresnel_status dalloc(Plan* p, void** out, size_t bytes) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (p->opts.max_device_bytes > 0 && p->bytes + (long long)bytes > p->opts.max_device_bytes)
+        return fres_fail(FRESNEL_ERR_OOM, "plan would exceed max_device_bytes (" +
+                                               std::to_string(p->opts.max_device_bytes) + ")");
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fres_fail(FRESNEL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    p->allocs.push_back(*out);
+    p->bytes += (long long)bytes;
+    return FRESNEL_OK;
+}
+
+#define FRES_TRY(x)                          \
+    do {                                     \
+        fresnel_status s_ = (x);             \
+        if (s_ != FRESNEL_OK) return s_;     \
+    } while (0)
+
+void free_plan(Plan* p) {
+    if (!p) return;
+    cudaStreamSynchronize(p->st);
+    for (void* a : p->allocs) cudaFree(a);
+    for (int i = 0; i < kMaxEvents; ++i)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    p->magic = 0;
+    delete p;
+}
+
+bool is_nice(long long n) {
+    for (int f : {2, 3, 5})
+        while (n % f == 0) n /= f;
+    return n == 1;
+}
+int nice_size(double target, int mult) {
+    long long n = (long long)std::ceil(target - 1e-9);
+    if (n < mult) n = mult;
+    n = (n + mult - 1) / mult * mult;
+    while (!is_nice(n)) n += mult;
+    return (int)n;
+}
+
+// Spreading-kernel choice: exponential of semicircle, width w grid points,
+// shape beta, upsampling sigma.  The paper takes the NUFFT as a library and
+// quotes only its upsampling (5/4 for eps >= 1e-9, else 2; Sec. 4.1); the
+// width/shape rules follow the published FINUFFT method.  FP32 fast mode
+// uses sigma = 2 (at 5/4 the deconvolution amplifies FP32 rounding by >1e2 at
+// the band edge) and designs the kernel for tol/10, leaving room for FP32
+// rounding under the requested tolerance.
+void choose_kernel(Plan* p) {
+    double tk = p->tol;
+    double sigma;
+    if (p->prec == FRESNEL_FP32_FAST) {
+        sigma = p->opts.sigma > 0 ? p->opts.sigma : 2.0;
+        tk = p->tol / 10.0;
+    } else {
+        sigma = p->opts.sigma > 0 ? p->opts.sigma : (p->tol >= 1e-9 ? 1.25 : 2.0);
+    }
+    int w;
+    double beta;
+    if (std::fabs(sigma - 2.0) < 1e-12) {
+        w = (int)std::ceil(std::log10(1.0 / tk)) + 1;
+    } else {
+        w = (int)std::ceil(-std::log(tk) / (kPi * std::sqrt(1.0 - 1.0 / sigma)));
+    }
+    if (p->opts.kernel_w > 0) w = p->opts.kernel_w;
+    w = std::max(2, std::min(kMaxW, w));
+    if (std::fabs(sigma - 2.0) < 1e-12) beta = 2.30 * w;
+    else beta = 0.97 * kPi * (1.0 - 0.5 / sigma) * w;
+    p->sigma = sigma;
+    p->ks.w = w;
+    p->ks.beta = beta;
+    p->ks.betaf = (float)beta;
+}
+
+fresnel_status validate_family(const fresnel_family& f, long long* n_bdry, long long* n_nodes,
+                               int* K) {
+    if (!f.params || f.n_params <= 0) return fres_fail(FRESNEL_ERR_ARG, "family params missing");
+    for (long long i = 0; i < f.n_params; ++i)
+        if (!std::isfinite(f.params[i]))
+            return fres_fail(FRESNEL_ERR_ARG, "family params contain a non-finite value");
+    if (!std::isfinite(f.cx) || !std::isfinite(f.cy))
+        return fres_fail(FRESNEL_ERR_ARG, "family centre not finite");
+    switch (f.kind) {
+        case FRESNEL_FAMILY_FOURIER:
+            if (f.n_panels < 1 || f.p < 1 || f.m < 1 || f.p > 4096 || f.m > 65536)
+                return fres_fail(FRESNEL_ERR_ARG, "FOURIER family needs n_panels>=1, 1<=p<=4096, 1<=m<=65536");
+            if (f.n_params % 2 != 1)
+                return fres_fail(FRESNEL_ERR_ARG, "FOURIER params must be [r0, a1, b1, ...] (odd length)");
+            *K = (int)((f.n_params - 1) / 2);
+            *n_bdry = (long long)f.n_panels * f.p;
+            *n_nodes = *n_bdry * f.m;
+            return FRESNEL_OK;
+        case FRESNEL_FAMILY_LINE_RULE:
+            if (f.n_panels < 1 || f.p < 1 || f.m < 1 || f.m > 65536)
+                return fres_fail(FRESNEL_ERR_ARG, "LINE_RULE family needs n_panels>=1, p>=1, 1<=m<=65536");
+            if (f.n_params != 4LL * f.n_panels * f.p)
+                return fres_fail(FRESNEL_ERR_ARG, "LINE_RULE params must hold 4 * n_panels * p values");
+            *K = 0;
+            *n_bdry = (long long)f.n_panels * f.p;
+            *n_nodes = *n_bdry * f.m;
+            return FRESNEL_OK;
+        case FRESNEL_FAMILY_NODES:
+            if (f.n_params % 3 != 0)
+                return fres_fail(FRESNEL_ERR_ARG, "NODES params must hold 3 * N values");
+            *K = 0;
+            *n_bdry = 0;
+            *n_nodes = f.n_params / 3;
+            return FRESNEL_OK;
+        default:
+            return fres_fail(FRESNEL_ERR_ARG, "unknown family kind");
+    }
+}
+
+void ev_record(Plan* p, const char* name) {
+    if (!p->timing || p->nev >= kMaxEvents) return;
+    if (!p->ev[p->nev]) cudaEventCreate(&p->ev[p->nev]);
+    p->ev_name[p->nev] = name;
+    cudaEventRecord(p->ev[p->nev], p->st);
+    p->nev++;
+}
+
+template <typename T>
+fresnel_status run_nodes(Plan* p, double* dx, double* dy, double* dw) {
+    for (const FamilyDev& f : p->fams) {
+        if (f.kind != FRESNEL_FAMILY_NODES) {
+            launch_boundary(f, p->st);
+            p->launches++;
+        }
+        launch_nodes_count<T>(f, p->cp, (NodeRec<T>*)p->rec, p->counts, dx, dy, dw, p->status,
+                              p->st);
+        p->launches++;
+    }
+    return FRESNEL_OK;
+}
+
+template <typename T>
+fresnel_status run_sort(Plan* p) {
+    launch_scan_chunks(p->ntiles, p->counts, p->cursor, p->chunks, p->n_chunks, p->chunk_cap,
+                       p->max_chunks, p->st);
+    launch_scatter<T>(p->N, p->cp, (const NodeRec<T>*)p->rec, p->cursor, (NodeRec<T>*)p->sorted,
+                      p->n_records, p->status, p->st);
+    p->launches += 2;
+    return FRESNEL_OK;
+}
+
+template <typename T>
+fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_out) {
+    p->launches = 0;
+    p->nev = 0;
+    ev_record(p, "start");
+    if (p->opts.recompute_nodes || !p->nodes_ready) {
+        FRES_TRY(run_nodes<T>(p, nullptr, nullptr, nullptr));
+        ev_record(p, "nodes_chirp_count");
+        FRES_TRY(run_sort<T>(p));
+        ev_record(p, "scan_scatter");
+        p->nodes_ready = true;
+    }
+    launch_spread<T>((const NodeRec<T>*)p->sorted, p->chunks, p->n_chunks, p->max_chunks,
+                     (cx_t<T>*)p->grid, (cx_t<T>*)p->partials, p->tile_counters, p->nf1, p->nf2,
+                     p->ntx, p->ks, p->spread_blocks, p->st);
+    p->launches++;
+    ev_record(p, "spread");
+    if (p->tkind == FRESNEL_GRID) {
+        RowPassArgs ra{};
+        ra.in = p->grid;
+        ra.out = p->inter;
+        ra.in_stride = p->nf1;
+        ra.out_stride = p->n1;
+        ra.nrows = p->nf2;
+        ra.in_len = p->nf1;
+        ra.centered_in = 0;
+        ra.out_len = p->n1;
+        ra.twiddle = p->tw1;
+        launch_fft_rows<T>(p->fp1, ra, p->st);
+        ev_record(p, "fft_rows");
+        ColPassArgs ca{};
+        ca.in = p->inter;
+        ca.out = d_out;
+        ca.ncols = p->n1;
+        ca.in_len = p->nf2;
+        ca.centered_in = 0;
+        ca.out_len = p->n2;
+        ca.twiddle = p->tw2;
+        ca.ax = p->ax;
+        ca.ay = p->ay;
+        ca.occulter = p->output == FRESNEL_OCCULTER;
+        ca.out_is_final = 1;
+        launch_fft_cols<T>(p->fp2, ca, p->st);
+        ev_record(p, "fft_cols_epilogue");
+        p->launches += 2;
+    } else {
+        RowPassArgs ra{};
+        ra.in = p->grid;
+        ra.out = p->inter;
+        ra.in_stride = p->nf1;
+        ra.out_stride = p->nfft1;
+        ra.nrows = p->nf2;
+        ra.in_len = p->nf1;
+        ra.centered_in = 1;
+        ra.deconv_col = p->dec1;
+        ra.deconv_row = p->dec2;
+        ra.out_len = p->nfft1;
+        ra.twiddle = p->tw1;
+        launch_fft_rows<T>(p->fp1, ra, p->st);
+        ev_record(p, "fft_rows");
+        ColPassArgs ca{};
+        ca.in = p->inter;
+        ca.out = p->F;
+        ca.ncols = p->nfft1;
+        ca.in_len = p->nf2;
+        ca.centered_in = 1;
+        ca.out_len = p->nfft2;
+        ca.twiddle = p->tw2;
+        launch_fft_cols<T>(p->fp2, ca, p->st);
+        ev_record(p, "fft_cols");
+        p->launches += 2;
+        if (M > 0) {
+            launch_interp_w<T>(d_targets, M, (const cx_t<T>*)p->F, p->ip, p->ks, p->gq_t, p->gq_w,
+                               p->gq_n, d_out, p->status, p->st);
+            p->launches++;
+        }
+        ev_record(p, "interp_epilogue");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return FRESNEL_OK;
+}
+
+fresnel_status read_status(Plan* p) {
+    unsigned h = 0;
+    FRES_CK(cudaMemcpyAsync(&h, p->status, sizeof(unsigned), cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    if (h) {
+        FRES_CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->st));
+        FRES_CK(cudaStreamSynchronize(p->st));
+        std::string msg = "device check failed:";
+        if (h & kStatusTargetOutside) msg += " target outside the plan's box;";
+        if (h & kStatusNodeOutside) msg += " node support outside the type-3 grid;";
+        if (h & kStatusNonFinite) msg += " non-finite coordinate;";
+        return fres_fail(FRESNEL_ERR_DEVICE, msg);
+    }
+    return FRESNEL_OK;
+}
+
+template <typename T>
+fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_families) {
+    const bool dbl = sizeof(T) == 8;
+    // ---------------- families: device copies, Gauss-Legendre rules, boundary rules
+    long long off = 0;
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int fi = 0; fi < n_families; ++fi) {
+        const fresnel_family& hf = families[fi];
+        FamilyDev f{};
+        long long nb = 0, nn = 0;
+        int K = 0;
+        FRES_TRY(validate_family(hf, &nb, &nn, &K));
+        f.kind = hf.kind;
+        f.n_panels = hf.n_panels;
+        f.p = hf.p;
+        f.m = hf.m;
+        f.K = K;
+        f.n_bdry = nb;
+        f.n_nodes = nn;
+        f.offset = off;
+        f.cx = hf.kind == FRESNEL_FAMILY_NODES ? 0.0 : hf.cx;
+        f.cy = hf.kind == FRESNEL_FAMILY_NODES ? 0.0 : hf.cy;
+        off += nn;
+        FRES_TRY(dalloc(p, (void**)&f.params, sizeof(double) * hf.n_params));
+        FRES_CK(cudaMemcpyAsync(f.params, hf.params, sizeof(double) * hf.n_params,
+                                cudaMemcpyHostToDevice, p->st));
+        if (hf.kind == FRESNEL_FAMILY_NODES) {
+            for (long long j = 0; j < nn; ++j) {
+                xmin = std::min(xmin, hf.params[j]);
+                xmax = std::max(xmax, hf.params[j]);
+                ymin = std::min(ymin, hf.params[nn + j]);
+                ymax = std::max(ymax, hf.params[nn + j]);
+            }
+        } else {
+            if (hf.kind == FRESNEL_FAMILY_FOURIER) {
+                FRES_TRY(dalloc(p, (void**)&f.gl_p_t, sizeof(double) * f.p));
+                FRES_TRY(dalloc(p, (void**)&f.gl_p_w, sizeof(double) * f.p));
+                launch_gauss_legendre(f.p, f.gl_p_t, f.gl_p_w, p->st);
+            }
+            FRES_TRY(dalloc(p, (void**)&f.gl_m_a, sizeof(double) * f.m));
+            FRES_TRY(dalloc(p, (void**)&f.gl_m_aw, sizeof(double) * f.m));
+            launch_gauss_legendre(f.m, f.gl_m_a, f.gl_m_aw, p->st);
+            // alpha_l * wtilde_l (eq. aqwei) formed on the host from the device rule
+            std::vector<double> a(f.m), w(f.m);
+            FRES_CK(cudaMemcpyAsync(a.data(), f.gl_m_a, sizeof(double) * f.m, cudaMemcpyDeviceToHost, p->st));
+            FRES_CK(cudaMemcpyAsync(w.data(), f.gl_m_aw, sizeof(double) * f.m, cudaMemcpyDeviceToHost, p->st));
+            FRES_CK(cudaStreamSynchronize(p->st));
+            for (int l = 0; l < f.m; ++l) w[l] *= a[l];
+            FRES_CK(cudaMemcpyAsync(f.gl_m_aw, w.data(), sizeof(double) * f.m, cudaMemcpyHostToDevice, p->st));
+            FRES_TRY(dalloc(p, (void**)&f.bx, sizeof(double) * nb));
+            FRES_TRY(dalloc(p, (void**)&f.by, sizeof(double) * nb));
+            FRES_TRY(dalloc(p, (void**)&f.bc, sizeof(double) * nb));
+            launch_boundary(f, p->st);
+            // node bounding box (type 3 sizing): nodes lie on segments from the
+            // centre to the boundary nodes, so centre + boundary bounds them.
+            std::vector<double> bx(nb), by(nb);
+            FRES_CK(cudaMemcpyAsync(bx.data(), f.bx, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
+            FRES_CK(cudaMemcpyAsync(by.data(), f.by, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
+            FRES_CK(cudaStreamSynchronize(p->st));
+            xmin = std::min(xmin, f.cx);
+            xmax = std::max(xmax, f.cx);
+            ymin = std::min(ymin, f.cy);
+            ymax = std::max(ymax, f.cy);
+            for (long long i = 0; i < nb; ++i) {
+                xmin = std::min(xmin, f.cx + bx[i]);
+                xmax = std::max(xmax, f.cx + bx[i]);
+                ymin = std::min(ymin, f.cy + by[i]);
+                ymax = std::max(ymax, f.cy + by[i]);
+            }
+        }
+        p->fams.push_back(f);
+    }
+    p->N = off;
+    if (p->N < 1) return fres_fail(FRESNEL_ERR_ARG, "the quadrature has no nodes");
+    if (p->N > (1LL << 30)) return fres_fail(FRESNEL_ERR_UNSUPPORTED, "more than 2^30 nodes");
+
+    // ---------------- kernel and grids
+    choose_kernel(p);
+    const int w = p->ks.w;
+    const double lz = p->lz;
+    int cmax = 0;
+    p->cp.kq = kPi / lz;
+    p->cp.w = w;
+    if (p->tkind == FRESNEL_GRID) {
+        p->n1 = p->opts.grid_n1;
+        p->n2 = p->opts.grid_n2;
+        p->nf1 = nice_size(std::max({p->sigma * p->n1, 2.0 * w, 64.0}), kTile);
+        p->nf2 = nice_size(std::max({p->sigma * p->n2, 2.0 * w, 64.0}), kTile);
+        p->nfft1 = p->nf1;
+        p->nfft2 = p->nf2;
+        p->cp.type3 = 0;
+        p->cp.u1 = p->opts.grid_h / lz;
+        p->cp.u2 = p->opts.grid_h / lz;
+        p->cp.a1 = kTwoPi * p->opts.grid_x0 / lz;
+        p->cp.a2 = kTwoPi * p->opts.grid_y0 / lz;
+        p->cp.a0 = 0.0;
+    } else {
+        const double* b = p->opts.box;
+        double X1 = 0.5 * (xmax - xmin), X2 = 0.5 * (ymax - ymin);
+        double C1 = 0.5 * (xmax + xmin), C2 = 0.5 * (ymax + ymin);
+        X1 = std::max(X1, 1e-9 * std::max(1.0, std::fabs(C1)));
+        X2 = std::max(X2, 1e-9 * std::max(1.0, std::fabs(C2)));
+        double xic = 0.5 * (b[0] + b[1]), etac = 0.5 * (b[2] + b[3]);
+        double S1 = kTwoPi * 0.5 * (b[1] - b[0]) / lz, S2 = kTwoPi * 0.5 * (b[3] - b[2]) / lz;
+        S1 = std::max(S1, 1.0 / X1);
+        S2 = std::max(S2, 1.0 / X2);
+        const double sg = p->sigma;
+        p->nf1 = nice_size(2.0 * sg * X1 * S1 / kPi + w + 2, kTile);
+        p->nf2 = nice_size(2.0 * sg * X2 * S2 / kPi + w + 2, kTile);
+        p->nfft1 = nice_size(sg * p->nf1, 2);
+        p->nfft2 = nice_size(sg * p->nf2, 2);
+        double hs1 = kPi / (sg * S1), hs2 = kPi / (sg * S2);
+        double D1 = kTwoPi * xic / lz, D2 = kTwoPi * etac / lz;
+        p->cp.type3 = 1;
+        p->cp.C1 = C1;
+        p->cp.C2 = C2;
+        p->cp.inv_h1 = 1.0 / hs1;
+        p->cp.inv_h2 = 1.0 / hs2;
+        p->cp.a1 = D1;
+        p->cp.a2 = D2;
+        p->cp.a0 = D1 * C1 + D2 * C2;
+        InterpParams& ip = p->ip;
+        ip.xi_c = xic;
+        ip.eta_c = etac;
+        ip.K1 = hs1 * p->nfft1 / lz;
+        ip.K2 = hs2 * p->nfft2 / lz;
+        ip.sh1 = kTwoPi * hs1 / lz;
+        ip.sh2 = kTwoPi * hs2 / lz;
+        ip.kq = kPi / lz;
+        ip.p1 = -kTwoPi * C1 / lz;
+        ip.p2 = -kTwoPi * C2 / lz;
+        ip.inv_lz = 1.0 / lz;
+        for (int i = 0; i < 4; ++i) ip.box[i] = b[i];
+        ip.nfft1 = p->nfft1;
+        ip.nfft2 = p->nfft2;
+        ip.occulter = p->output == FRESNEL_OCCULTER;
+    }
+    if (!fft_supported(p->nfft1, dbl, &cmax) || !fft_supported(p->nfft2, dbl, &cmax))
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED,
+                         "FFT size " + std::to_string(p->nfft1) + " x " + std::to_string(p->nfft2) +
+                             " exceeds this build's single-pass limit (8192)");
+    p->fp1 = make_fft_plan(p->nfft1);
+    p->fp2 = make_fft_plan(p->nfft2);
+    p->cp.nf1 = p->nf1;
+    p->cp.nf2 = p->nf2;
+    p->ntx = p->nf1 / kTile;
+    p->nty = p->nf2 / kTile;
+    p->ntiles = p->ntx * p->nty;
+    p->cp.ntx = p->ntx;
+    p->cp.nty = p->nty;
+    p->chunk_cap = dbl ? 1024 : 2048;
+
+    // ---------------- node pass once: exact record / chunk / slot counts
+    FRES_TRY(dalloc(p, (void**)&p->status, sizeof(unsigned)));
+    FRES_CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->st));
+    FRES_TRY(dalloc(p, &p->rec, p->rsize() * p->N));
+    FRES_TRY(dalloc(p, (void**)&p->counts, sizeof(int) * p->ntiles));
+    FRES_TRY(dalloc(p, (void**)&p->cursor, sizeof(int) * p->ntiles));
+    FRES_TRY(dalloc(p, (void**)&p->tile_counters, sizeof(int) * p->ntiles));
+    FRES_CK(cudaMemsetAsync(p->counts, 0, sizeof(int) * p->ntiles, p->st));
+    FRES_CK(cudaMemsetAsync(p->tile_counters, 0, sizeof(int) * p->ntiles, p->st));
+    FRES_TRY(run_nodes<T>(p, nullptr, nullptr, nullptr));
+    std::vector<int> hc(p->ntiles);
+    FRES_CK(cudaMemcpyAsync(hc.data(), p->counts, sizeof(int) * p->ntiles, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    FRES_CK(cudaGetLastError());
+    long long nrec = 0, nch = 0, nsl = 0;
+    for (int c : hc) {
+        long long k = c > p->chunk_cap ? (c + p->chunk_cap - 1) / p->chunk_cap : 1;
+        nrec += c;
+        nch += k;
+        if (k > 1) nsl += k;
+    }
+    p->n_records = nrec;
+    p->max_chunks = (int)nch;
+    p->max_slots = (int)std::max(1LL, nsl);
+    FRES_TRY(dalloc(p, &p->sorted, p->rsize() * std::max(1LL, nrec)));
+    FRES_TRY(dalloc(p, (void**)&p->chunks, sizeof(Chunk) * p->max_chunks));
+    FRES_TRY(dalloc(p, (void**)&p->n_chunks, sizeof(int)));
+    FRES_TRY(dalloc(p, &p->partials, p->csize() * kTile * kTile * (size_t)p->max_slots));
+    FRES_TRY(run_sort<T>(p));
+    p->nodes_ready = true;
+    p->spread_blocks = 152 * 8;
+
+    // ---------------- grids and tables
+    const size_t cs = p->csize();
+    FRES_TRY(dalloc(p, &p->grid, cs * (size_t)p->nf1 * p->nf2));
+    // kernel-transform quadrature: Gauss-Legendre on (0,1) with 2w + 16 points
+    p->gq_n = std::min(64, 2 * w + 16);
+    FRES_TRY(dalloc(p, (void**)&p->gq_t, sizeof(double) * p->gq_n));
+    FRES_TRY(dalloc(p, (void**)&p->gq_w, sizeof(double) * p->gq_n));
+    launch_gauss_legendre(p->gq_n, p->gq_t, p->gq_w, p->st);
+    FRES_TRY(dalloc(p, &p->tw1, cs * p->nfft1));
+    launch_twiddles(p->nfft1, p->tw1, dbl, p->st);
+    if (p->nfft2 != p->nfft1) {
+        FRES_TRY(dalloc(p, &p->tw2, cs * p->nfft2));
+        launch_twiddles(p->nfft2, p->tw2, dbl, p->st);
+    } else {
+        p->tw2 = p->tw1;
+    }
+    if (p->tkind == FRESNEL_GRID) {
+        FRES_TRY(dalloc(p, &p->inter, cs * (size_t)p->nf2 * p->n1));
+        FRES_TRY(dalloc(p, &p->ax, cs * p->n1));
+        FRES_TRY(dalloc(p, &p->ay, cs * p->n2));
+        launch_t1_tables(p->n1, p->nf1, p->opts.grid_h, p->opts.grid_x0, lz, w, p->ks.beta, 1,
+                         p->ax, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
+        launch_t1_tables(p->n2, p->nf2, p->opts.grid_h, p->opts.grid_y0, lz, w, p->ks.beta, 0,
+                         p->ay, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
+    } else {
+        FRES_TRY(dalloc(p, &p->inter, cs * (size_t)p->nf2 * p->nfft1));
+        FRES_TRY(dalloc(p, &p->F, cs * (size_t)p->nfft2 * p->nfft1));
+        const size_t rs = dbl ? 8 : 4;
+        FRES_TRY(dalloc(p, &p->dec1, rs * p->nf1));
+        FRES_TRY(dalloc(p, &p->dec2, rs * p->nf2));
+        launch_t3_deconv(p->nf1, p->nfft1, w, p->ks.beta, p->dec1, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
+        launch_t3_deconv(p->nf2, p->nfft2, w, p->ks.beta, p->dec2, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
+    }
+    FRES_CK(cudaGetLastError());
+    FRES_CK(cudaStreamSynchronize(p->st));
+    return read_status(p);
+}
+
+Plan* as_plan(fresnel_plan_t h) {
+    Plan* p = reinterpret_cast<Plan*>(h);
+    if (!p || p->magic != kMagic) return nullptr;
+    return p;
+}
+
+}  // namespace
+
+struct fresnel_plan_s {};   // opaque handle type; the handle points at a Plan
+
+extern "C" {
+
+void fresnel_default_opts(fresnel_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FRESNEL_FP32_FAST;
+    o->output = FRESNEL_APERTURE;
+    o->target_kind = FRESNEL_GRID;
+    o->grid_n1 = o->grid_n2 = 100;
+    o->grid_h = 0.03;
+    o->box[0] = o->box[2] = -1.0;
+    o->box[1] = o->box[3] = 1.0;
+    o->sync_status = 1;
+}
+
+fresnel_status fresnel_plan(const fresnel_family* families, int n_families, double lambda,
+                            double z, double tol, const fresnel_opts* opts, void* cuda_stream,
+                            fresnel_plan_t* out_plan) {
+    if (!out_plan) return fres_fail(FRESNEL_ERR_ARG, "out_plan is NULL");
+    *out_plan = nullptr;
+    if (!families || n_families < 1) return fres_fail(FRESNEL_ERR_ARG, "no families");
+    if (!opts) return fres_fail(FRESNEL_ERR_ARG, "opts is NULL");
+    if (!(lambda > 0) || !(z > 0) || !std::isfinite(lambda) || !std::isfinite(z) ||
+        !std::isfinite(lambda * z) || !(lambda * z > 0))
+        return fres_fail(FRESNEL_ERR_ARG, "lambda and z must be finite and > 0");
+    if (!(tol >= 1e-14 && tol <= 1e-1)) return fres_fail(FRESNEL_ERR_ARG, "tol must lie in [1e-14, 1e-1]");
+    if (opts->precision != FRESNEL_FP64 && opts->precision != FRESNEL_FP32_FAST)
+        return fres_fail(FRESNEL_ERR_ARG, "unknown precision");
+    if (opts->precision == FRESNEL_FP32_FAST && tol < 1e-7)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "FP32 fast mode reaches tol >= 1e-7 only; use FRESNEL_FP64");
+    if (opts->output != FRESNEL_APERTURE && opts->output != FRESNEL_OCCULTER)
+        return fres_fail(FRESNEL_ERR_ARG, "unknown output");
+    if (opts->target_kind == FRESNEL_GRID) {
+        if (opts->grid_n1 < 1 || opts->grid_n2 < 1 || !(opts->grid_h > 0) ||
+            !std::isfinite(opts->grid_h) || !std::isfinite(opts->grid_x0) ||
+            !std::isfinite(opts->grid_y0))
+            return fres_fail(FRESNEL_ERR_ARG, "grid needs n1, n2 >= 1 and finite h > 0, x0, y0");
+    } else if (opts->target_kind == FRESNEL_SCATTERED) {
+        const double* b = opts->box;
+        for (int i = 0; i < 4; ++i)
+            if (!std::isfinite(b[i])) return fres_fail(FRESNEL_ERR_ARG, "box must be finite");
+        if (!(b[0] <= b[1]) || !(b[2] <= b[3])) return fres_fail(FRESNEL_ERR_ARG, "box must have min <= max");
+    } else {
+        return fres_fail(FRESNEL_ERR_ARG, "unknown target_kind");
+    }
+    if (opts->sigma != 0 && !(opts->sigma >= 1.2 && opts->sigma <= 4.0))
+        return fres_fail(FRESNEL_ERR_ARG, "sigma must be 0 (auto) or in [1.2, 4]");
+    if (opts->kernel_w < 0 || opts->kernel_w > kMaxW)
+        return fres_fail(FRESNEL_ERR_ARG, "kernel_w must be 0 (auto) or in [2, 16]");
+    int dev = 0;
+    FRES_CK(cudaGetDevice(&dev));
+    Plan* p = new Plan();
+    p->prec = opts->precision;
+    p->output = opts->output;
+    p->tkind = opts->target_kind;
+    p->lz = lambda * z;
+    p->tol = tol;
+    p->st = (cudaStream_t)cuda_stream;
+    p->opts = *opts;
+    fresnel_status s = p->prec == FRESNEL_FP64 ? build_plan<double>(p, families, n_families)
+                                               : build_plan<float>(p, families, n_families);
+    if (s != FRESNEL_OK) {
+        std::string msg = g_last_error;
+        cudaGetLastError();
+        free_plan(p);
+        g_last_error = msg;
+        return s;
+    }
+    *out_plan = reinterpret_cast<fresnel_plan_t>(p);
+    return FRESNEL_OK;
+}
+
+fresnel_status fresnel_eval(fresnel_plan_t plan, const double* d_targets, long long M, void* d_out) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (p->tkind == FRESNEL_GRID) {
+        if (M != (long long)p->n1 * p->n2)
+            return fres_fail(FRESNEL_ERR_ARG, "GRID plan: M must equal n1 * n2");
+    } else {
+        if (M < 0) return fres_fail(FRESNEL_ERR_ARG, "M must be >= 0");
+        if (M > 0 && !d_targets) return fres_fail(FRESNEL_ERR_ARG, "d_targets is NULL");
+    }
+    if (M > 0 && !d_out) return fres_fail(FRESNEL_ERR_ARG, "d_out is NULL");
+    fresnel_status s = p->prec == FRESNEL_FP64 ? eval_impl<double>(p, d_targets, M, d_out)
+                                               : eval_impl<float>(p, d_targets, M, d_out);
+    if (s != FRESNEL_OK) return s;
+    if (p->opts.sync_status) return read_status(p);
+    return FRESNEL_OK;
+}
+
+fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, long long M,
+                                 void* h_out) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (M < 0) return fres_fail(FRESNEL_ERR_ARG, "M must be >= 0");
+    if (M > 0 && !h_out) return fres_fail(FRESNEL_ERR_ARG, "h_out is NULL");
+    if (p->tkind == FRESNEL_SCATTERED && M > 0 && !h_targets)
+        return fres_fail(FRESNEL_ERR_ARG, "h_targets is NULL");
+    if (p->tkind == FRESNEL_GRID && M != (long long)p->n1 * p->n2)
+        return fres_fail(FRESNEL_ERR_ARG, "GRID plan: M must equal n1 * n2");
+    if (M > p->stage_cap) {
+        long long cap = M;
+        if (p->tkind == FRESNEL_SCATTERED) FRES_TRY(dalloc(p, (void**)&p->stage_tgt, 16 * (size_t)cap));
+        FRES_TRY(dalloc(p, &p->stage_out, p->csize() * (size_t)cap));
+        p->stage_cap = cap;
+    }
+    if (p->tkind == FRESNEL_SCATTERED && M > 0)
+        FRES_CK(cudaMemcpyAsync(p->stage_tgt, h_targets, 16 * (size_t)M, cudaMemcpyHostToDevice, p->st));
+    fresnel_status s = p->prec == FRESNEL_FP64 ? eval_impl<double>(p, p->stage_tgt, M, p->stage_out)
+                                               : eval_impl<float>(p, p->stage_tgt, M, p->stage_out);
+    if (s != FRESNEL_OK) return s;
+    if (M > 0)
+        FRES_CK(cudaMemcpyAsync(h_out, p->stage_out, p->csize() * (size_t)M, cudaMemcpyDeviceToHost, p->st));
+    return read_status(p);
+}
+
+fresnel_status fresnel_check(fresnel_plan_t plan) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    return read_status(p);
+}
+
+fresnel_status fresnel_destroy(fresnel_plan_t plan) {
+    if (!plan) return FRESNEL_OK;
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    free_plan(p);
+    return FRESNEL_OK;
+}
+
+const char* fresnel_last_error(void) { return g_last_error.c_str(); }
+
+fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
+    Plan* p = as_plan(plan);
+    if (!p || !info) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle or info");
+    info->n_nodes = p->N;
+    info->w = p->ks.w;
+    info->beta = p->ks.beta;
+    info->sigma = p->sigma;
+    info->nf1 = p->nf1;
+    info->nf2 = p->nf2;
+    info->nfft1 = p->nfft1;
+    info->nfft2 = p->nfft2;
+    info->tile_x = kTile;
+    info->tile_y = kTile;
+    info->device_bytes = p->bytes;
+    int nl = 4;   // spread, two FFT passes, (type 3) interpolation
+    if (p->tkind == FRESNEL_GRID) nl = 3;
+    if (p->opts.recompute_nodes) {
+        for (const FamilyDev& f : p->fams) nl += f.kind == FRESNEL_FAMILY_NODES ? 1 : 2;
+        nl += 2;
+    }
+    info->launches_per_eval = nl;
+    return FRESNEL_OK;
+}
+
+fresnel_status fresnel_get_nodes(fresnel_plan_t plan, double* d_x, double* d_y, double* d_w) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (!d_x || !d_y || !d_w) return fres_fail(FRESNEL_ERR_ARG, "node output arrays are NULL");
+    // Regenerates the nodes (and, harmlessly, the unsorted records and counts),
+    // then re-runs the scan so the counts are reset and the cached sort stays valid.
+    if (p->prec == FRESNEL_FP64) {
+        FRES_TRY(run_nodes<double>(p, d_x, d_y, d_w));
+        FRES_TRY(run_sort<double>(p));
+    } else {
+        FRES_TRY(run_nodes<float>(p, d_x, d_y, d_w));
+        FRES_TRY(run_sort<float>(p));
+    }
+    FRES_CK(cudaGetLastError());
+    return read_status(p);
+}
+
+int fresnel_set_timing(fresnel_plan_t plan, int enable) {
+    Plan* p = as_plan(plan);
+    if (!p) return 0;
+    p->timing = enable ? 1 : 0;
+    return p->timing;
+}
+
+int fresnel_stage_times(fresnel_plan_t plan, double* stage_ms, const char** names, int max_stages) {
+    Plan* p = as_plan(plan);
+    if (!p || !p->timing || p->nev < 2) return 0;
+    cudaEventSynchronize(p->ev[p->nev - 1]);
+    int n = 0;
+    for (int i = 1; i < p->nev && n < max_stages; ++i, ++n) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p->ev[i - 1], p->ev[i]);
+        if (stage_ms) stage_ms[n] = ms;
+        if (names) names[n] = p->ev_name[i];
+    }
+    return n;
+}
+
+}  // extern "C"

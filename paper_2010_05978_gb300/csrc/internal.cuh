@@ -1,0 +1,196 @@
+// Internal declarations shared by the libfresnel translation units.
+// Method: arXiv:2010.05978 (areal quadrature + NUFFT Fresnel diffraction).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/fresnel.h"
+
+namespace fres {
+
+constexpr int kMaxW = 16;          // widest spreading kernel supported
+constexpr int kTile = 32;          // spreading tile edge (grid points)
+constexpr int kMaxRadixStages = 32;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kPi = 3.141592653589793238462643383280;
+
+// Device status word bits (read back by fresnel_check).
+enum : unsigned {
+    kStatusTargetOutside = 1u,     // a scattered target lay outside the plan's box
+    kStatusNodeOutside = 2u,       // a node's support left the type-3 spreading grid
+    kStatusNonFinite = 4u,         // a non-finite coordinate was met
+};
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+template <typename T> using cx_t = typename Cx<T>::type;
+
+// Node record after the chirp (Sec. 3.2 step 1) and the grid-coordinate
+// split: first support cell s = floor(g - w/2) + 1 (wrapped into [0, nf) for
+// type 1), fraction f = (g - w/2) - floor(g - w/2) in [0, 1), strength c.
+template <typename T>
+struct __align__(2 * sizeof(T) > 8 ? 16 : 8) NodeRec {
+    int s1, s2;
+    T f1, f2;
+    T cre, cim;
+};
+
+// A spreading work item: nodes [begin, end) of the sorted record list that
+// touch tile `tile`.  Tiles with more than the chunk cap are split; the
+// chunks of a split tile write partial tiles to slots [first_slot, +nchunks)
+// and the last chunk to finish sums them in slot order.
+struct Chunk {
+    int tile;
+    int begin, end;
+    int slot;        // -1: tile not split, store directly
+    int first_slot;  // first partial slot of this tile (split tiles)
+    int nchunks;     // chunks of this tile
+};
+
+// Radix plan of one FFT length.
+struct FftPlan {
+    int n;
+    int nstages;
+    int radix[kMaxRadixStages];
+};
+
+// One node family resident on the device.
+struct FamilyDev {
+    int kind;
+    int n_panels, p, m;
+    int K;                 // Fourier modes (kind FOURIER)
+    long long n_bdry;      // boundary nodes
+    long long n_nodes;     // areal nodes
+    long long offset;      // first global node index
+    double cx, cy;
+    double* params;        // device copy of params
+    double* bx;            // boundary X - cx   (n_bdry)
+    double* by;            // boundary Y - cy
+    double* bc;            // (X-cx) V - (Y-cy) W
+    double* gl_p_t;        // p-point Gauss-Legendre nodes on (0,1)
+    double* gl_p_w;
+    double* gl_m_a;        // m-point Gauss-Legendre nodes alpha_l on (0,1)
+    double* gl_m_aw;       // alpha_l * wtilde_l
+};
+
+// Everything a node kernel needs to turn (x, y, w) into a record.
+struct ChirpParams {
+    double kq;             // pi / lz
+    double a1, a2, a0;     // phase = kq |x|^2 - a1 x - a2 y + a0 (pre-phase)
+    int type3;
+    // type 1: g = frac(x * u1) * nf1
+    double u1, u2;
+    // type 3: g = (x - C1) * inv_h1 + ng1 / 2
+    double C1, C2, inv_h1, inv_h2;
+    int nf1, nf2;          // spreading grid
+    int w;
+    int ntx, nty;          // tiles per dimension
+};
+
+struct KernelShape {
+    int w;
+    double beta;
+    float betaf;
+};
+
+// Fourier transform of the exponential-of-semicircle spreading kernel
+// psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)), |u| <= w/2 (grid points), at
+// t radians per grid point:
+//   psihat(t) = int psi(u) e^{-i t u} du = w int_0^1 psi(w s/2) cos(t w s/2) ds,
+// evaluated by the q-point Gauss-Legendre rule (gq_t, gq_w) on (0, 1).
+template <typename R>
+__device__ __forceinline__ R kernel_ft(R t, int w, R beta, const R* gq_t, const R* gq_w, int q) {
+    R acc = 0;
+    R hw = (R)0.5 * (R)w;
+    for (int i = 0; i < q; ++i) {
+        R s = gq_t[i];
+        acc += gq_w[i] * exp(beta * (sqrt((R)1 - s * s) - (R)1)) * cos(t * hw * s);
+    }
+    return (R)w * acc;
+}
+
+// ------------------------------------------------------------------ launchers
+// k_nodes.cu
+void launch_gauss_legendre(int n, double* t01, double* w01, cudaStream_t st);
+void launch_boundary(const FamilyDev& f, cudaStream_t st);
+template <typename T>
+void launch_nodes_count(const FamilyDev& f, const ChirpParams& cp, NodeRec<T>* rec,
+                        int* counts, double* dx, double* dy, double* dw,
+                        unsigned* status, cudaStream_t st);
+void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_chunks,
+                        int chunk_cap, int max_chunks, cudaStream_t st);
+template <typename T>
+void launch_scatter(long long n, const ChirpParams& cp, const NodeRec<T>* rec, int* cursor,
+                    NodeRec<T>* sorted, long long cap, unsigned* status, cudaStream_t st);
+void launch_twiddles(int n, void* table, int is_double, cudaStream_t st);
+// t1 output tables Ax[k1] = chirp(xi)/(i lz)/psihat(k1), Ay[k2] = chirp(eta)/psihat(k2)
+void launch_t1_tables(int n, int nf, double h, double x0, double lz, int w, double beta,
+                      int with_ilz, void* table, int is_double, const double* gq_t,
+                      const double* gq_w, int q, cudaStream_t st);
+// t3 type-2 deconvolution factors 1/psihat(2 pi l / nfft), l in [-ng/2, ng/2)
+void launch_t3_deconv(int ng, int nfft, int w, double beta, void* table, int is_double,
+                      const double* gq_t, const double* gq_w, int q, cudaStream_t st);
+
+// k_spread.cu
+template <typename T>
+void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_chunks,
+                   int max_chunks, cx_t<T>* grid, cx_t<T>* partials, int* tile_counters,
+                   int nf1, int nf2, int ntx, const KernelShape& ks, int nblocks,
+                   cudaStream_t st);
+
+// k_fft.cu
+struct RowPassArgs {
+    const void* in; void* out;
+    long long in_stride, out_stride;   // elements between rows
+    int nrows;
+    int in_len;          // input elements per row
+    int centered_in;     // 1: input index i holds mode i - in_len/2 (type 3 layout)
+    const void* deconv_col;   // per-element factor along the row (centered_in), or NULL
+    const void* deconv_row;   // per-row scalar factor (centered_in), or NULL
+    int out_len;         // kept outputs: modes k in [-out_len/2, out_len - out_len/2), stored at k + out_len/2; out_len == n: natural order
+    const void* twiddle;
+};
+struct ColPassArgs {
+    const void* in; void* out;
+    int ncols;           // columns (contiguous dimension length of in/out)
+    int in_len;          // input rows
+    int centered_in;
+    int out_len;         // kept output rows (centered as in RowPassArgs); == n: natural order
+    const void* twiddle;
+    // type-1 epilogue (final output) when ax != NULL: out[k2][k1] = F * ax[k1] * ay[k2], then Babinet
+    const void* ax; const void* ay;
+    int occulter;
+    int out_is_final;    // 1: out has ncols columns of the final type (complex64/128)
+};
+template <typename T>
+void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st);
+template <typename T>
+void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st);
+bool fft_supported(int n, int is_double, int* max_cols);
+FftPlan make_fft_plan(int n);
+
+// k_interp.cu
+struct InterpParams {
+    double xi_c, eta_c;      // target box centre
+    double K1, K2;           // tau = (xi - xi_c) * K  (grid units of the FFT grid)
+    double sh1, sh2;         // s' h = (xi - xi_c) * sh  (argument of the kernel transform)
+    double kq;               // pi / lz
+    double p1, p2;           // post-phase: -2 pi C / lz
+    double inv_lz;
+    double box[4];
+    int nfft1, nfft2;
+    int occulter;
+};
+template <typename T>
+void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
+                     const KernelShape& ks, const double* gq_t, const double* gq_w, int q,
+                     void* out, unsigned* status, cudaStream_t st);
+
+}  // namespace fres
+
+// Thread-local error message + status helpers (api.cu).
+fresnel_status fres_fail(fresnel_status s, const std::string& msg);

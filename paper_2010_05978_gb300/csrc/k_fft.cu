@@ -1,0 +1,274 @@
+// Hand-written 2D FFT for the NUFFT fine grid: batched 1D mixed-radix
+// (4, 2, 3, 5) Stockham transforms held in shared memory, one pass along rows
+// (contiguous) and one along columns (a CTA takes C adjacent columns so global
+// accesses stay coalesced).  Forward sign e^{-2 pi i k l / n}, unnormalised.
+//
+// The FFT is the middle step of the type-1 and type-3 NUFFTs used by the
+// paper's fast algorithm (arXiv:2010.05978, Secs. 3.2-3.3; "under the hood the
+// NUFFT uses FFTs", Sec. 4.1).  Both passes are pruned to what the path needs:
+// the type-1 row pass keeps only the n1 wanted modes; the type-1 column pass
+// keeps n2 modes and applies the fused output epilogue (deconvolution, target
+// chirp, 1/(i lz), Babinet); the type-3 passes read only the nonzero central
+// block of the zero-padded grid and fuse the inner type-2 deconvolution.
+//
+// Each Stockham stage with radix r and p = product of earlier radices maps
+// butterfly i (k = i mod p) from inputs x[i + q n/r] (twiddled by
+// w_n^{q k n/(p r)}) to outputs y[(i - k) r + k + t p]; stages run in place
+// with the outputs staged in registers between two barriers.
+#include "internal.cuh"
+
+namespace fres {
+
+namespace {
+
+constexpr int kFftThreads = 1024;
+
+template <typename T> struct Ops {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ C mk(T a, T b) { C c; c.x = a; c.y = b; return c; }
+    static __device__ __forceinline__ C add(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ C sub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ C mul(C a, C b) {
+        return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    }
+    static __device__ __forceinline__ C scale(C a, T s) { return mk(a.x * s, a.y * s); }
+    static __device__ __forceinline__ C mul_negi(C a) { return mk(a.y, -a.x); }   // -i a
+};
+
+// One Stockham stage of radix R over the smem array S[n][ncol] (column c of
+// element e at S[e * ncol + c]).
+template <typename T, int R, int EMAX>
+__device__ __forceinline__ void stage(cx_t<T>* S, int n, int ncol, int p, const cx_t<T>* tw) {
+    using O = Ops<T>;
+    using C = cx_t<T>;
+    constexpr int IT = (EMAX + R - 1) / R;
+    const int nb = n / R;
+    const int items = nb * ncol;
+    const int twstep = n / (p * R);
+    C y[IT][R];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = threadIdx.x + it * blockDim.x;
+        if (w < items) {
+            const int c = w % ncol, i = w / ncol, k = i % p;
+            C u[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                u[q] = S[(i + q * nb) * ncol + c];
+                if (q > 0 && k > 0) u[q] = O::mul(u[q], tw[q * k * twstep]);
+            }
+            if (R == 2) {
+                y[it][0] = O::add(u[0], u[1]);
+                y[it][1] = O::sub(u[0], u[1]);
+            } else if (R == 4) {
+                C t0 = O::add(u[0], u[2]), t1 = O::sub(u[0], u[2]);
+                C t2 = O::add(u[1], u[3]), t3 = O::mul_negi(O::sub(u[1], u[3]));
+                y[it][0] = O::add(t0, t2);
+                y[it][2] = O::sub(t0, t2);
+                y[it][1] = O::add(t1, t3);
+                y[it][3 % R] = O::sub(t1, t3);
+            } else if (R == 3) {
+                const T c3 = (T)-0.5, s3 = (T)0.86602540378443864676372317075294;
+                C s = O::add(u[1], u[2]), d = O::sub(u[1], u[2]);
+                C a = O::add(u[0], O::scale(s, c3));
+                C b = O::mul_negi(O::scale(d, s3));          // -i s3 (u1 - u2)
+                y[it][0] = O::add(u[0], s);
+                y[it][1] = O::add(a, b);
+                y[it][2 % R] = O::sub(a, b);
+            } else if (R == 5) {
+                const T c1 = (T)0.30901699437494742410229341718282;   // cos(2 pi/5)
+                const T s1 = (T)0.95105651629515357211643933337938;   // sin(2 pi/5)
+                const T c2 = (T)-0.80901699437494742410229341718282;  // cos(4 pi/5)
+                const T s2 = (T)0.58778525229247312916870595463907;   // sin(4 pi/5)
+                C a14 = O::add(u[1], u[4 % R]), d14 = O::sub(u[1], u[4 % R]);
+                C a23 = O::add(u[2 % R], u[3 % R]), d23 = O::sub(u[2 % R], u[3 % R]);
+                C r1 = O::add(u[0], O::add(O::scale(a14, c1), O::scale(a23, c2)));
+                C r2 = O::add(u[0], O::add(O::scale(a14, c2), O::scale(a23, c1)));
+                C i1 = O::mul_negi(O::add(O::scale(d14, s1), O::scale(d23, s2)));
+                C i2 = O::mul_negi(O::sub(O::scale(d14, s2), O::scale(d23, s1)));
+                y[it][0] = O::add(u[0], O::add(a14, a23));
+                y[it][1] = O::add(r1, i1);
+                y[it][4 % R] = O::sub(r1, i1);
+                y[it][2 % R] = O::add(r2, i2);
+                y[it][3 % R] = O::sub(r2, i2);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = threadIdx.x + it * blockDim.x;
+        if (w < items) {
+            const int c = w % ncol, i = w / ncol, k = i % p;
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int t = 0; t < R; ++t) S[(j + t * p) * ncol + c] = y[it][t];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int EMAX>
+__device__ void fft_smem(cx_t<T>* S, int ncol, const FftPlan& fp, const cx_t<T>* tw) {
+    int p = 1;
+    for (int s = 0; s < fp.nstages; ++s) {
+        const int r = fp.radix[s];
+        switch (r) {
+            case 4: stage<T, 4, EMAX>(S, fp.n, ncol, p, tw); break;
+            case 2: stage<T, 2, EMAX>(S, fp.n, ncol, p, tw); break;
+            case 3: stage<T, 3, EMAX>(S, fp.n, ncol, p, tw); break;
+            case 5: stage<T, 5, EMAX>(S, fp.n, ncol, p, tw); break;
+        }
+        p *= r;
+    }
+}
+
+template <typename T> __host__ __device__ constexpr int emax() { return 8; }
+
+// Position in the length-n transform of input index i when the input holds
+// modes i - len/2 (type-3 central block), else i itself.
+__device__ __forceinline__ int in_pos(int i, int len, int n, int centered) {
+    if (!centered) return i;
+    int l = i - len / 2;
+    return l < 0 ? l + n : l;
+}
+// Source index in the length-n transform of kept output kp.
+__device__ __forceinline__ int out_src(int kp, int len, int n) {
+    if (len == n) return kp;
+    int k = kp - len / 2;
+    return k < 0 ? k + n : k;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, 1)
+k_fft_rows(FftPlan fp, RowPassArgs a) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = (C*)smem_raw;
+    const int n = fp.n;
+    const C* tw = (const C*)a.twiddle;
+    for (int row = blockIdx.x; row < a.nrows; row += gridDim.x) {
+        const C* in = (const C*)a.in + (long long)row * a.in_stride;
+        if (a.centered_in || a.in_len < n)
+            for (int e = threadIdx.x; e < n; e += blockDim.x) S[e] = Ops<T>::mk(0, 0);
+        __syncthreads();
+        T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
+        const T* dcol = (const T*)a.deconv_col;
+        for (int i = threadIdx.x; i < a.in_len; i += blockDim.x) {
+            C v = in[i];
+            if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
+            S[in_pos(i, a.in_len, n, a.centered_in)] = v;
+        }
+        __syncthreads();
+        fft_smem<T, emax<T>()>(S, 1, fp, tw);
+        C* out = (C*)a.out + (long long)row * a.out_stride;
+        for (int kp = threadIdx.x; kp < a.out_len; kp += blockDim.x)
+            out[kp] = S[out_src(kp, a.out_len, n)];
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, 1)
+k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
+    using C = cx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = (C*)smem_raw;
+    const int n = fp.n;
+    const C* tw = (const C*)a.twiddle;
+    const int ngroups = (a.ncols + ncol - 1) / ncol;
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int c0 = g * ncol;
+        if (a.centered_in || a.in_len < n)
+            for (int e = threadIdx.x; e < n * ncol; e += blockDim.x) S[e] = Ops<T>::mk(0, 0);
+        __syncthreads();
+        const C* in = (const C*)a.in;
+        for (int e = threadIdx.x; e < a.in_len * ncol; e += blockDim.x) {
+            const int i = e / ncol, c = e % ncol;
+            C v = Ops<T>::mk(0, 0);
+            if (c0 + c < a.ncols) v = in[(long long)i * a.ncols + c0 + c];
+            S[in_pos(i, a.in_len, n, a.centered_in) * ncol + c] = v;
+        }
+        __syncthreads();
+        fft_smem<T, emax<T>()>(S, ncol, fp, tw);
+        for (int e = threadIdx.x; e < a.out_len * ncol; e += blockDim.x) {
+            const int kp = e / ncol, c = e % ncol;
+            if (c0 + c >= a.ncols) continue;
+            C v = S[out_src(kp, a.out_len, n) * ncol + c];
+            if (a.ax) {
+                v = Ops<T>::mul(v, ((const C*)a.ax)[c0 + c]);
+                v = Ops<T>::mul(v, ((const C*)a.ay)[kp]);
+                if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
+            }
+            ((C*)a.out)[(long long)kp * a.ncols + c0 + c] = v;
+        }
+        __syncthreads();
+    }
+}
+
+int threads_for(int elems, int em) {
+    int t = (elems + em - 1) / em;
+    t = (t + 31) / 32 * 32;
+    if (t < 64) t = 64;
+    if (t > kFftThreads) t = kFftThreads;
+    return t;
+}
+
+}  // namespace
+
+FftPlan make_fft_plan(int n) {
+    FftPlan fp{};
+    fp.n = n;
+    int m = n;
+    while (m % 4 == 0) { fp.radix[fp.nstages++] = 4; m /= 4; }
+    while (m % 2 == 0) { fp.radix[fp.nstages++] = 2; m /= 2; }
+    while (m % 3 == 0) { fp.radix[fp.nstages++] = 3; m /= 3; }
+    while (m % 5 == 0) { fp.radix[fp.nstages++] = 5; m /= 5; }
+    if (m != 1) fp.nstages = -1;
+    return fp;
+}
+
+// Largest column batch (power of two, <= 8) whose n x C block fits in the
+// per-thread register budget and in shared memory; 0 if n itself does not.
+bool fft_supported(int n, int is_double, int* max_cols) {
+    FftPlan fp = make_fft_plan(n);
+    if (fp.nstages < 0 || n < 2) return false;
+    const int em = 8;
+    const long long cap_elems = (long long)em * kFftThreads;
+    const long long smem_cap = 227 * 1024;
+    const int esz = is_double ? 16 : 8;
+    int c = 8;
+    while (c > 0 && ((long long)n * c > cap_elems || (long long)n * c * esz > smem_cap)) c >>= 1;
+    if (max_cols) *max_cols = c;
+    return c > 0;
+}
+
+template <typename T>
+void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st) {
+    const size_t smem = (size_t)fp.n * sizeof(cx_t<T>);
+    cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int threads = threads_for(fp.n, emax<T>());
+    int blocks = a.nrows < 152 * 16 ? a.nrows : 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_fft_rows<T><<<blocks, threads, smem, st>>>(fp, a);
+}
+
+template <typename T>
+void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st) {
+    int cmax = 0;
+    fft_supported(fp.n, sizeof(T) == 8, &cmax);
+    const size_t smem = (size_t)fp.n * cmax * sizeof(cx_t<T>);
+    cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int threads = threads_for(fp.n * cmax, emax<T>());
+    const int ngroups = (a.ncols + cmax - 1) / cmax;
+    int blocks = ngroups < 152 * 16 ? ngroups : 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_fft_cols<T><<<blocks, threads, smem, st>>>(fp, a, cmax);
+}
+
+template void launch_fft_rows<float>(const FftPlan&, const RowPassArgs&, cudaStream_t);
+template void launch_fft_rows<double>(const FftPlan&, const RowPassArgs&, cudaStream_t);
+template void launch_fft_cols<float>(const FftPlan&, const ColPassArgs&, cudaStream_t);
+template void launch_fft_cols<double>(const FftPlan&, const ColPassArgs&, cudaStream_t);
+
+}  // namespace fres

@@ -1,0 +1,400 @@
+// Node-side kernels: Gauss-Legendre rules, boundary line rules, the areal
+// dilation rule with the chirp (Sec. 3.2 step 1), grid coordinates and the
+// counting sort of nodes into spreading tiles; plus the small plan-time tables
+// (FFT twiddles, deconvolution and output-chirp factors).
+// Paper: arXiv:2010.05978, Secs. 3.2-3.3 and 4.1 (eqs. split, aqnod, aqwei, vliq1).
+#include "internal.cuh"
+
+namespace fres {
+
+namespace {
+
+constexpr double kTwoPiHi = 6.28318530717958623199592693709;    // fl(2 pi)
+constexpr double kTwoPiLo = 2.44929359829470635445e-16;        // 2 pi - fl(2 pi)
+constexpr double kInvTwoPi = 0.159154943091895335768883763373;
+
+// Reduce an FP64 phase into [-pi, pi]: phi - 2 pi rint(phi / 2 pi), with 2 pi
+// split into two doubles so the product n * 2 pi is carried to ~2^-106.
+__device__ __forceinline__ double reduce_phase(double ph) {
+    double n = rint(ph * kInvTwoPi);
+    ph = fma(-n, kTwoPiHi, ph);
+    return fma(-n, kTwoPiLo, ph);
+}
+
+__device__ __forceinline__ void agg_count(int key, int* counts) {
+    unsigned mask = __match_any_sync(0xffffffffu, key);
+    int lane = threadIdx.x & 31;
+    if (key >= 0 && lane == __ffs(mask) - 1) atomicAdd(&counts[key], __popc(mask));
+}
+
+__device__ __forceinline__ int agg_reserve(int key, int* cursor) {
+    unsigned mask = __match_any_sync(0xffffffffu, key);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (key >= 0 && lane == leader) base = atomicAdd(&cursor[key], __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// Up to four tiles touched by a node whose support starts at (s1, s2).
+__device__ __forceinline__ void node_tiles(int s1, int s2, const ChirpParams& cp, int key[4]) {
+    int e1 = s1 + cp.w - 1; if (e1 >= cp.nf1) e1 -= cp.nf1;
+    int e2 = s2 + cp.w - 1; if (e2 >= cp.nf2) e2 -= cp.nf2;
+    int ta = s1 / kTile, tb = e1 / kTile;
+    int sa = s2 / kTile, sb = e2 / kTile;
+    key[0] = sa * cp.ntx + ta;
+    key[1] = (tb != ta) ? sa * cp.ntx + tb : -1;
+    key[2] = (sb != sa) ? sb * cp.ntx + ta : -1;
+    key[3] = (tb != ta && sb != sa) ? sb * cp.ntx + tb : -1;
+}
+
+// ------------------------------------------------------------------ Gauss-Legendre
+// Roots of P_n by Newton's method on the three-term recurrence; the weights
+// 2 / ((1 - x^2) P_n'(x)^2); both mapped from (-1, 1) to (0, 1), ascending.
+__global__ void k_gauss_legendre(int n, double* t01, double* w01) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    int converged = 0;
+    for (int it = 0; it < 100 && converged < 2; ++it) {
+        double p0 = 1.0, p1 = x;
+        for (int j = 1; j < n; ++j) {
+            double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        double dx = p1 / dp;
+        x -= dx;
+        if (fabs(dx) < 1e-15) ++converged;
+    }
+    {
+        double p0 = 1.0, p1 = x;
+        for (int j = 1; j < n; ++j) {
+            double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+    }
+    t01[i] = 0.5 * (1.0 - x);
+    w01[i] = 1.0 / ((1.0 - x * x) * dp * dp);
+}
+
+// ------------------------------------------------------------------ boundary line rules
+// Fourier star, Sec. 4.1: X(t) = r cos t, Y(t) = r sin t about the centre,
+// r = r0 + sum (a_k cos kt + b_k sin kt); panel q of n_panels equal t-panels
+// carries p Gauss-Legendre nodes: W = what X'(t), V = what Y'(t) (eq. vliq1).
+// Stored relative to the centre: bx = X - cx, by = Y - cy, bc = bx V - by W.
+__global__ void k_boundary_fourier(FamilyDev f) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= f.n_bdry) return;
+    int q = (int)(i / f.p), s = (int)(i % f.p);
+    double hP = kTwoPi / f.n_panels;
+    double t = (q + f.gl_p_t[s]) * hP;
+    double what = f.gl_p_w[s] * hP;
+    double st, ct;
+    sincos(t, &st, &ct);
+    double r = f.params[0], dr = 0.0;
+    double ck = 1.0, sk = 0.0;
+    for (int k = 1; k <= f.K; ++k) {
+        double c2 = ck * ct - sk * st;
+        sk = sk * ct + ck * st;
+        ck = c2;
+        double a = f.params[2 * k - 1], b = f.params[2 * k];
+        r += a * ck + b * sk;
+        dr += k * (b * ck - a * sk);
+    }
+    double X = r * ct, Y = r * st;
+    double W = what * (dr * ct - r * st);
+    double V = what * (dr * st + r * ct);
+    f.bx[i] = X;
+    f.by[i] = Y;
+    f.bc[i] = X * V - Y * W;
+}
+
+// Explicit vector line rule: params = [X.., Y.., W.., V..].
+__global__ void k_boundary_line(FamilyDev f) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long n = f.n_bdry;
+    if (i >= n) return;
+    double X = f.params[i] - f.cx, Y = f.params[n + i] - f.cy;
+    double W = f.params[2 * n + i], V = f.params[3 * n + i];
+    f.bx[i] = X;
+    f.by[i] = Y;
+    f.bc[i] = X * V - Y * W;
+}
+
+// ------------------------------------------------------------------ nodes + chirp + count
+// Dilation rule (eqs. aqnod, aqwei): x = c + alpha_l (X_i - c),
+// w = alpha_l wtilde_l ((X_i-cx) V_i - (Y_i-cy) W_i), node j = i*m + l.
+// Strength (Sec. 3.2 step 1, with the optional pre-phase of Sec. 3.3):
+// c = w exp(i [pi |x|^2 / lz - a1 x - a2 y + a0]), phase in FP64 and reduced
+// mod 2 pi before the sine/cosine (FP32 sincos in the fast mode).
+// Grid coordinate: type 1 g = frac(x h / lz) nf (the folded x~ of Sec. 3.3
+// scaled to grid points); type 3 g = (x - C) / h_s + nf/2.
+template <typename T>
+__global__ void k_nodes_count(FamilyDev f, ChirpParams cp, NodeRec<T>* rec, int* counts,
+                              double* dx, double* dy, double* dw, unsigned* status) {
+    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool valid = j < f.n_nodes;
+    int key[4] = {-1, -1, -1, -1};
+    if (valid) {
+        double x, y, w;
+        if (f.kind == FRESNEL_FAMILY_NODES) {
+            x = f.params[j];
+            y = f.params[f.n_nodes + j];
+            w = f.params[2 * f.n_nodes + j];
+        } else {
+            long long i = j / f.m;
+            int l = (int)(j - i * f.m);
+            double a = f.gl_m_a[l];
+            x = f.cx + a * f.bx[i];
+            y = f.cy + a * f.by[i];
+            w = f.gl_m_aw[l] * f.bc[i];
+        }
+        long long g = f.offset + j;
+        if (dx) {
+            dx[g] = x;
+            dy[g] = y;
+            dw[g] = w;
+        }
+        double ph = reduce_phase(cp.kq * (x * x + y * y) - cp.a1 * x - cp.a2 * y + cp.a0);
+        NodeRec<T> r;
+        if (sizeof(T) == 8) {
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            r.cre = (T)(w * cs);
+            r.cim = (T)(w * sn);
+        } else {
+            float sn, cs;
+            sincosf((float)ph, &sn, &cs);
+            r.cre = (T)((float)w * cs);
+            r.cim = (T)((float)w * sn);
+        }
+        double g1, g2;
+        if (!cp.type3) {
+            double u = x * cp.u1;
+            u -= floor(u);
+            g1 = u * cp.nf1;
+            double v = y * cp.u2;
+            v -= floor(v);
+            g2 = v * cp.nf2;
+        } else {
+            g1 = (x - cp.C1) * cp.inv_h1 + 0.5 * cp.nf1;
+            g2 = (y - cp.C2) * cp.inv_h2 + 0.5 * cp.nf2;
+        }
+        if (!isfinite(g1) || !isfinite(g2)) {
+            atomicOr(status, kStatusNonFinite);
+            g1 = g2 = 0.0;
+            r.cre = r.cim = (T)0;
+        }
+        double gs1 = g1 - 0.5 * cp.w, gs2 = g2 - 0.5 * cp.w;
+        double fl1 = floor(gs1), fl2 = floor(gs2);
+        int s1 = (int)fl1 + 1, s2 = (int)fl2 + 1;
+        r.f1 = (T)(gs1 - fl1);
+        r.f2 = (T)(gs2 - fl2);
+        if (!cp.type3) {
+            if (s1 < 0) s1 += cp.nf1;
+            if (s1 >= cp.nf1) s1 -= cp.nf1;
+            if (s2 < 0) s2 += cp.nf2;
+            if (s2 >= cp.nf2) s2 -= cp.nf2;
+        } else if (s1 < 0 || s2 < 0 || s1 + cp.w > cp.nf1 || s2 + cp.w > cp.nf2) {
+            atomicOr(status, kStatusNodeOutside);
+            s1 = min(max(s1, 0), cp.nf1 - cp.w);
+            s2 = min(max(s2, 0), cp.nf2 - cp.w);
+        }
+        r.s1 = s1;
+        r.s2 = s2;
+        rec[g] = r;
+        node_tiles(s1, s2, cp, key);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) agg_count(key[k], counts);
+}
+
+// Scatter each record to every tile its support touches (positions reserved
+// with warp-aggregated atomics on per-tile cursors set by the scan).
+template <typename T>
+__global__ void k_scatter(long long n, ChirpParams cp, const NodeRec<T>* rec, int* cursor,
+                          NodeRec<T>* sorted, long long cap, unsigned* status) {
+    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int key[4] = {-1, -1, -1, -1};
+    NodeRec<T> r;
+    if (j < n) {
+        r = rec[j];
+        node_tiles(r.s1, r.s2, cp, key);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int pos = agg_reserve(key[k], cursor);
+        if (key[k] >= 0) {
+            if (pos >= 0 && pos < cap) sorted[pos] = r;
+            else atomicOr(status, kStatusNodeOutside);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scan -> chunks
+// One block: exclusive scan of per-tile record counts; every tile becomes
+// max(1, ceil(count / cap)) chunks (empty tiles still get one chunk, which
+// writes zeros, so the grid needs no separate clearing).  Resets counts.
+__global__ void k_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks,
+                              int* n_chunks, int chunk_cap, int max_chunks) {
+    __shared__ long long s_rec[1024], s_ch[1024], s_sl[1024];
+    int t = threadIdx.x, nt = blockDim.x;
+    int per = (ntiles + nt - 1) / nt;
+    int lo = min(t * per, ntiles), hi = min(lo + per, ntiles);
+    long long rsum = 0, csum = 0, ssum = 0;
+    for (int i = lo; i < hi; ++i) {
+        int c = counts[i];
+        int nch = c > chunk_cap ? (c + chunk_cap - 1) / chunk_cap : 1;
+        rsum += c;
+        csum += nch;
+        ssum += nch > 1 ? nch : 0;
+    }
+    s_rec[t] = rsum;
+    s_ch[t] = csum;
+    s_sl[t] = ssum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scan
+        long long a = 0, b = 0, c = 0;
+        if (t >= off) { a = s_rec[t - off]; b = s_ch[t - off]; c = s_sl[t - off]; }
+        __syncthreads();
+        s_rec[t] += a; s_ch[t] += b; s_sl[t] += c;
+        __syncthreads();
+    }
+    long long roff = s_rec[t] - rsum, coff = s_ch[t] - csum, soff = s_sl[t] - ssum;
+    for (int i = lo; i < hi; ++i) {
+        int c = counts[i];
+        int nch = c > chunk_cap ? (c + chunk_cap - 1) / chunk_cap : 1;
+        cursor[i] = (int)roff;
+        for (int k = 0; k < nch; ++k) {
+            long long ci = coff + k;
+            if (ci < max_chunks) {
+                Chunk ch;
+                ch.tile = i;
+                ch.begin = (int)(roff + (long long)k * chunk_cap);
+                ch.end = (int)min(roff + (long long)(k + 1) * chunk_cap, roff + c);
+                ch.slot = nch > 1 ? (int)(soff + k) : -1;
+                ch.first_slot = nch > 1 ? (int)soff : -1;
+                ch.nchunks = nch;
+                chunks[ci] = ch;
+            }
+        }
+        coff += nch;
+        if (nch > 1) soff += nch;
+        roff += c;
+        counts[i] = 0;
+    }
+    if (t == nt - 1) *n_chunks = (int)min(s_ch[t], (long long)max_chunks);
+}
+
+// ------------------------------------------------------------------ plan-time tables
+__global__ void k_twiddles(int n, void* table, int is_double) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s, c;
+    sincospi(-2.0 * j / n, &s, &c);
+    if (is_double) ((double2*)table)[j] = make_double2(c, s);
+    else ((float2*)table)[j] = make_float2((float)c, (float)s);
+}
+
+// Output factors of the type-1 path (Sec. 3.3 step 3 and the deconvolution):
+// A[k'] = exp(i pi xi^2 / lz) / psihat(2 pi k / nf) [* 1/(i lz)],
+// xi = x0 + k h, k = k' - floor(n/2).  FP64, phase reduced mod 2 pi.
+__global__ void k_t1_tables(int n, int nf, double h, double x0, double lz, int w, double beta,
+                            int with_ilz, void* table, int is_double, const double* gq_t,
+                            const double* gq_w, int q) {
+    int kp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kp >= n) return;
+    int k = kp - n / 2;
+    double xi = x0 + k * h;
+    double ph = reduce_phase(kPi * xi * xi / lz);
+    double s, c;
+    sincos(ph, &s, &c);
+    double inv = 1.0 / kernel_ft(kTwoPi * k / nf, w, beta, gq_t, gq_w, q);
+    double re = c * inv, im = s * inv;
+    if (with_ilz) {   // times 1/(i lz) = -i / lz
+        double r2 = im / lz, i2 = -re / lz;
+        re = r2;
+        im = i2;
+    }
+    if (is_double) ((double2*)table)[kp] = make_double2(re, im);
+    else ((float2*)table)[kp] = make_float2((float)re, (float)im);
+}
+
+// Type-3 inner type-2 deconvolution: 1 / psihat(2 pi l / nfft), l = i - ng/2.
+__global__ void k_t3_deconv(int ng, int nfft, int w, double beta, void* table, int is_double,
+                            const double* gq_t, const double* gq_w, int q) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    int l = i - ng / 2;
+    double v = 1.0 / kernel_ft(kTwoPi * l / nfft, w, beta, gq_t, gq_w, q);
+    if (is_double) ((double*)table)[i] = v;
+    else ((float*)table)[i] = (float)v;
+}
+
+inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_gauss_legendre(int n, double* t01, double* w01, cudaStream_t st) {
+    k_gauss_legendre<<<nblk(n, 128), 128, 0, st>>>(n, t01, w01);
+}
+
+void launch_boundary(const FamilyDev& f, cudaStream_t st) {
+    if (f.kind == FRESNEL_FAMILY_FOURIER)
+        k_boundary_fourier<<<nblk(f.n_bdry, 256), 256, 0, st>>>(f);
+    else if (f.kind == FRESNEL_FAMILY_LINE_RULE)
+        k_boundary_line<<<nblk(f.n_bdry, 256), 256, 0, st>>>(f);
+}
+
+template <typename T>
+void launch_nodes_count(const FamilyDev& f, const ChirpParams& cp, NodeRec<T>* rec, int* counts,
+                        double* dx, double* dy, double* dw, unsigned* status, cudaStream_t st) {
+    if (f.n_nodes <= 0) return;
+    k_nodes_count<T><<<nblk(f.n_nodes, 256), 256, 0, st>>>(f, cp, rec, counts, dx, dy, dw, status);
+}
+template void launch_nodes_count<float>(const FamilyDev&, const ChirpParams&, NodeRec<float>*,
+                                        int*, double*, double*, double*, unsigned*, cudaStream_t);
+template void launch_nodes_count<double>(const FamilyDev&, const ChirpParams&, NodeRec<double>*,
+                                         int*, double*, double*, double*, unsigned*, cudaStream_t);
+
+template <typename T>
+void launch_scatter(long long n, const ChirpParams& cp, const NodeRec<T>* rec, int* cursor,
+                    NodeRec<T>* sorted, long long cap, unsigned* status, cudaStream_t st) {
+    if (n <= 0) return;
+    k_scatter<T><<<nblk(n, 256), 256, 0, st>>>(n, cp, rec, cursor, sorted, cap, status);
+}
+template void launch_scatter<float>(long long, const ChirpParams&, const NodeRec<float>*, int*,
+                                    NodeRec<float>*, long long, unsigned*, cudaStream_t);
+template void launch_scatter<double>(long long, const ChirpParams&, const NodeRec<double>*, int*,
+                                     NodeRec<double>*, long long, unsigned*, cudaStream_t);
+
+void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_chunks,
+                               int chunk_cap, int max_chunks, cudaStream_t st) {
+    k_scan_chunks<<<1, 1024, 0, st>>>(ntiles, counts, cursor, chunks, n_chunks, chunk_cap,
+                                      max_chunks);
+}
+
+void launch_twiddles(int n, void* table, int is_double, cudaStream_t st) {
+    k_twiddles<<<nblk(n, 256), 256, 0, st>>>(n, table, is_double);
+}
+
+void launch_t1_tables(int n, int nf, double h, double x0, double lz, int w, double beta,
+                      int with_ilz, void* table, int is_double, const double* gq_t,
+                      const double* gq_w, int q, cudaStream_t st) {
+    k_t1_tables<<<nblk(n, 128), 128, 0, st>>>(n, nf, h, x0, lz, w, beta, with_ilz, table,
+                                              is_double, gq_t, gq_w, q);
+}
+
+void launch_t3_deconv(int ng, int nfft, int w, double beta, void* table, int is_double,
+                      const double* gq_t, const double* gq_w, int q, cudaStream_t st) {
+    k_t3_deconv<<<nblk(ng, 128), 128, 0, st>>>(ng, nfft, w, beta, table, is_double, gq_t,
+                                               gq_w, q);
+}
+
+}  // namespace fres

@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libfresnel (include/fresnel.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libfresnel.so.  PyTorch supplies device memory and the CUDA stream.
+If the library is missing this module raises; there is no CPU fallback.
+
+Names follow the C ABI: ``fresnel_plan``, ``fresnel_eval``,
+``fresnel_eval_host``, ``fresnel_check``, ``fresnel_destroy``,
+``fresnel_last_error``, ``fresnel_get_info``, ``fresnel_get_nodes``; the
+``Plan`` class wraps them for convenience.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfresnel.so")
+
+FRESNEL_OK = 0
+STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_TIMEOUT",
+                -5: "ERR_UNSUPPORTED", -6: "ERR_DEVICE"}
+FAMILY_KINDS = {"fourier": 0, "line_rule": 1, "nodes": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+OUTPUTS = {"aperture": 0, "occulter": 1}
+GRID, SCATTERED = 0, 1
+
+
+class FresnelError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Family(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_panels", ctypes.c_int), ("p", ctypes.c_int),
+                ("m", ctypes.c_int), ("params", ctypes.POINTER(ctypes.c_double)),
+                ("n_params", ctypes.c_longlong), ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("output", ctypes.c_int),
+                ("target_kind", ctypes.c_int), ("grid_n1", ctypes.c_int),
+                ("grid_n2", ctypes.c_int), ("grid_h", ctypes.c_double),
+                ("grid_x0", ctypes.c_double), ("grid_y0", ctypes.c_double),
+                ("box", ctypes.c_double * 4), ("sigma", ctypes.c_double),
+                ("kernel_w", ctypes.c_int), ("recompute_nodes", ctypes.c_int),
+                ("sync_status", ctypes.c_int), ("max_device_bytes", ctypes.c_longlong)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_longlong), ("w", ctypes.c_int), ("beta", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("nf1", ctypes.c_int), ("nf2", ctypes.c_int),
+                ("nfft1", ctypes.c_int), ("nfft2", ctypes.c_int), ("tile_x", ctypes.c_int),
+                ("tile_y", ctypes.c_int), ("device_bytes", ctypes.c_longlong),
+                ("launches_per_eval", ctypes.c_int)]
+
+
+EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_eval", "fresnel_eval_host",
+           "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
+           "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times"]
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libfresnel.so (built in-tree by paper_2010_05978_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FresnelError(-2, "libfresnel.so not found at %s; build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    vp, ll, d = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double
+    lib.fresnel_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.fresnel_default_opts.restype = None
+    lib.fresnel_plan.argtypes = [ctypes.POINTER(Family), ctypes.c_int, d, d, d,
+                                 ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.fresnel_plan.restype = ctypes.c_int
+    lib.fresnel_eval.argtypes = [vp, vp, ll, vp]
+    lib.fresnel_eval.restype = ctypes.c_int
+    lib.fresnel_eval_host.argtypes = [vp, vp, ll, vp]
+    lib.fresnel_eval_host.restype = ctypes.c_int
+    lib.fresnel_check.argtypes = [vp]
+    lib.fresnel_check.restype = ctypes.c_int
+    lib.fresnel_destroy.argtypes = [vp]
+    lib.fresnel_destroy.restype = ctypes.c_int
+    lib.fresnel_last_error.argtypes = []
+    lib.fresnel_last_error.restype = ctypes.c_char_p
+    lib.fresnel_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.fresnel_get_info.restype = ctypes.c_int
+    lib.fresnel_get_nodes.argtypes = [vp, vp, vp, vp]
+    lib.fresnel_get_nodes.restype = ctypes.c_int
+    lib.fresnel_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.fresnel_set_timing.restype = ctypes.c_int
+    lib.fresnel_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.c_int]
+    lib.fresnel_stage_times.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != FRESNEL_OK:
+        raise FresnelError(status, load_library().fresnel_last_error().decode())
+
+
+def family_params(fam):
+    """(kind, n_panels, p, m, params, cx, cy) of a panel-family dict."""
+    kind = fam["kind"]
+    if kind == "fourier":
+        params = np.ascontiguousarray(fam["params"], dtype=np.float64)
+        return 0, fam["n_panels"], fam["p"], fam["m"], params, fam.get("cx", 0.0), fam.get("cy", 0.0)
+    if kind == "line_rule":
+        params = np.ascontiguousarray(np.concatenate(
+            [np.asarray(fam[k], np.float64) for k in ("X", "Y", "W", "V")]))
+        n = len(fam["X"])
+        return 1, n, 1, fam["m"], params, fam.get("cx", 0.0), fam.get("cy", 0.0)
+    if kind == "nodes":
+        params = np.ascontiguousarray(np.concatenate(
+            [np.asarray(fam[k], np.float64) for k in ("x", "y", "w")]))
+        return 2, 0, 0, 0, params, 0.0, 0.0
+    raise ValueError("unknown family kind %r" % kind)
+
+
+class Plan:
+    """A libfresnel plan on the current CUDA device and stream.
+
+    families: list of panel-family dicts (see workloads.py); lam, z: wavelength
+    and distance (only lam*z matters, eq. fres); tol: requested relative error;
+    precision "fp32" (fast mode) or "fp64"; output "aperture" or "occulter";
+    grid=dict(n1, n2, h, x0, y0) for type-1 targets, or box=(xmin, xmax,
+    ymin, ymax) for scattered (type-3) targets.
+    """
+
+    def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
+                 box=None, sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
+                 max_device_bytes=0, stream=None):
+        import torch
+        lib = load_library()
+        self._torch = torch
+        fams = (Family * len(families))()
+        keep = []
+        for i, f in enumerate(families):
+            kind, npan, p, m, params, cx, cy = family_params(f)
+            keep.append(params)
+            fams[i] = Family(kind, int(npan), int(p), int(m),
+                             params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             len(params), float(cx), float(cy))
+        o = Opts()
+        lib.fresnel_default_opts(ctypes.byref(o))
+        o.precision = PRECISIONS[precision]
+        o.output = OUTPUTS[output]
+        if grid is not None:
+            o.target_kind = GRID
+            o.grid_n1, o.grid_n2 = int(grid["n1"]), int(grid["n2"])
+            o.grid_h = float(grid["h"])
+            o.grid_x0, o.grid_y0 = float(grid.get("x0", 0.0)), float(grid.get("y0", 0.0))
+        else:
+            o.target_kind = SCATTERED
+            for i in range(4):
+                o.box[i] = float(box[i])
+        o.sigma = float(sigma)
+        o.kernel_w = int(kernel_w)
+        o.recompute_nodes = int(bool(recompute_nodes))
+        o.sync_status = int(bool(sync_status))
+        o.max_device_bytes = int(max_device_bytes)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.fresnel_plan(fams, len(families), float(lam), float(z), float(tol),
+                                ctypes.byref(o), ctypes.c_void_p(stream.cuda_stream),
+                                ctypes.byref(h)))
+        self.handle = h
+        self.precision = precision
+        self.grid = grid
+        self.cdtype = torch.complex64 if precision == "fp32" else torch.complex128
+
+    # -------------------------------------------------------------- evaluation
+    def eval(self, targets=None, out=None):
+        """u at the plan's targets as a CUDA tensor (complex64 / complex128).
+
+        Grid plans return shape (n2, n1) (k1 fastest); scattered plans take a
+        contiguous float64 CUDA tensor of shape (M, 2) and return shape (M,).
+        """
+        torch = self._torch
+        if self.grid is not None:
+            M = self.grid["n1"] * self.grid["n2"]
+            shape = (self.grid["n2"], self.grid["n1"])
+            tptr = None
+        else:
+            assert targets.dtype == torch.float64 and targets.is_cuda and targets.is_contiguous()
+            assert targets.dim() == 2 and targets.shape[1] == 2
+            M = targets.shape[0]
+            shape = (M,)
+            tptr = targets.data_ptr() if M > 0 else None
+        if out is None:
+            out = torch.empty(shape, dtype=self.cdtype, device="cuda")
+        _check(load_library().fresnel_eval(self.handle, tptr, M, out.data_ptr() if M > 0 else None))
+        return out
+
+    def eval_host(self, targets=None, out=None):
+        """Same evaluation from HOST numpy arrays (copies inside the call)."""
+        npc = np.complex64 if self.precision == "fp32" else np.complex128
+        if self.grid is not None:
+            M = self.grid["n1"] * self.grid["n2"]
+            shape = (self.grid["n2"], self.grid["n1"])
+            tptr = None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.float64)
+            M = targets.shape[0]
+            shape = (M,)
+            tptr = targets.ctypes.data if M > 0 else None
+        if out is None:
+            out = np.empty(shape, dtype=npc)
+        _check(load_library().fresnel_eval_host(self.handle, tptr, M,
+                                                out.ctypes.data if M > 0 else None))
+        return out
+
+    def check(self):
+        _check(load_library().fresnel_check(self.handle))
+
+    def info(self):
+        inf = Info()
+        _check(load_library().fresnel_get_info(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def nodes(self):
+        """The plan's quadrature nodes (x, y, w) as float64 CUDA tensors."""
+        torch = self._torch
+        n = self.info()["n_nodes"]
+        x, y, w = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+        _check(load_library().fresnel_get_nodes(self.handle, x.data_ptr(), y.data_ptr(),
+                                                w.data_ptr()))
+        return x, y, w
+
+    def set_timing(self, enable=True):
+        load_library().fresnel_set_timing(self.handle, int(enable))
+
+    def stage_times(self):
+        ms = (ctypes.c_double * 16)()
+        names = (ctypes.c_char_p * 16)()
+        n = load_library().fresnel_stage_times(self.handle, ms, names, 16)
+        return {names[i].decode(): ms[i] for i in range(n)}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().fresnel_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# C-ABI names, for callers that want the flat interface.
+def fresnel_last_error():
+    return load_library().fresnel_last_error().decode()

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (relative L2 over the evaluated targets): <= 1e-10 in FP64 mode at
+tol 1e-12, <= tol in FP32 fast mode (the requested tolerance itself).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import quadrature as Q
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_05978_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def plan(*a, **k):
+    from paper_2010_05978_gb300 import Plan
+    return Plan(*a, **k)
+
+
+BARS = {"fp64": (1e-12, 1e-10), "fp32": (1e-6, 1e-6)}
+
+
+# ------------------------------------------------------------------ quadrature
+@pytest.mark.parametrize("fam", [
+    W.fourier_family([1.0], 64, 16, 16),
+    W.fourier_family(W.STAR_PARAMS, 32, 16, 64, cx=0.2, cy=-0.1),
+    W.fourier_family(list(W.random_star_params()), 40, 16, 24),
+])
+def test_nodes_match_oracle(fam):
+    p = plan([fam], 0.1, 1.0, 1e-6, grid=W.grid_spec(64, 64, 0.05))
+    x, y, w = (t.cpu().numpy() for t in p.nodes())
+    ox, oy, ow = Q.family_nodes(fam)
+    assert len(x) == len(ox)
+    assert np.max(np.abs(x - ox)) < 5e-15 and np.max(np.abs(y - oy)) < 5e-15
+    assert np.max(np.abs(w - ow)) < 1e-14 * np.max(np.abs(ow)) * 10
+    p.close()
+
+
+# ------------------------------------------------------------------ type 1 (grid)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_t1_disc_F10_full_grid(prec):
+    """Unit disc, F = 10, 64 x 16 x 16 nodes, 100 x 100 grid over [-1.5, 1.5)^2."""
+    cfg = W.disc()
+    fam, g = cfg["families"], cfg["grid"]
+    xi, eta = oracle.grid_targets(g["n1"], g["n2"], g["h"])
+    ref = oracle.field(fam, cfg["lam"], cfg["z"], xi, eta).reshape(g["n2"], g["n1"])
+    tol, bar = BARS[prec]
+    u = plan(fam, cfg["lam"], cfg["z"], tol, precision=prec, grid=g).eval().cpu().numpy()
+    assert u.shape == (g["n2"], g["n1"])
+    assert rel_l2(u, ref) <= bar
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_t1_ragged_offset_grid(prec):
+    """Odd, non-square grid (301 x 250) with an offset origin (pre-phase, Sec. 3.3)."""
+    fam = [W.fourier_family(W.STAR_PARAMS, 32, 16, 48, cx=0.05, cy=0.02)]
+    lz = 0.05
+    g = W.grid_spec(301, 250, 0.011, x0=0.13, y0=-0.07)
+    xi, eta = oracle.grid_targets(g["n1"], g["n2"], g["h"], g["x0"], g["y0"])
+    ref = oracle.field(fam, lz, 1.0, xi, eta).reshape(g["n2"], g["n1"])
+    tol, bar = BARS[prec]
+    u = plan(fam, lz, 1.0, tol, precision=prec, grid=g).eval().cpu().numpy()
+    assert rel_l2(u, ref) <= bar
+
+
+def test_t1_folding_coarse_grid():
+    """A grid coarser than the field (n < F): x~ must be folded mod 2 pi (Sec. 3.3)."""
+    fam = [W.fourier_family([1.0], 64, 16, 48)]
+    lz = 0.02   # F = 50
+    g = W.grid_spec(16, 16, 0.2)
+    xi, eta = oracle.grid_targets(16, 16, 0.2)
+    ref = oracle.field(fam, lz, 1.0, xi, eta).reshape(16, 16)
+    u = plan(fam, lz, 1.0, 1e-12, precision="fp64", grid=g).eval().cpu().numpy()
+    assert rel_l2(u, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_t1_occulter_babinet(prec):
+    cfg = W.disc()
+    fam, g = cfg["families"], cfg["grid"]
+    tol, _ = BARS[prec]
+    ua = plan(fam, cfg["lam"], 1.0, tol, precision=prec, grid=g).eval().cpu().numpy()
+    uo = plan(fam, cfg["lam"], 1.0, tol, precision=prec, grid=g,
+              output="occulter").eval().cpu().numpy()
+    np.testing.assert_allclose(uo, 1.0 - ua, atol=1e-12 if prec == "fp64" else 1e-6)
+
+
+def test_t1_disc_closed_form_on_axis():
+    """Disc at F = 10 with converged m = 64: the grid point (0, 0) equals 1 - e^{i 10 pi} = 0."""
+    fam = [W.fourier_family([1.0], 64, 16, 64)]
+    u = plan(fam, 0.1, 1.0, 1e-12, precision="fp64",
+             grid=W.grid_spec(100, 100, 0.03)).eval().cpu().numpy()
+    assert abs(u[50, 50] - oracle.closed_forms.disc_on_axis(1.0, 0.1)) < 1e-10
+
+
+def test_multiple_families_add():
+    f1 = W.fourier_family([0.5], 32, 16, 24, cx=-0.6)
+    f2 = W.fourier_family([0.4, 0.0, 0.0, 0.05, 0.0], 32, 16, 24, cx=0.6, cy=0.2)
+    g = W.grid_spec(96, 80, 0.03)
+    xi, eta = oracle.grid_targets(96, 80, 0.03)
+    ref = oracle.field([f1, f2], 0.05, 1.0, xi, eta).reshape(80, 96)
+    u = plan([f1, f2], 0.05, 1.0, 1e-12, precision="fp64", grid=g).eval().cpu().numpy()
+    assert rel_l2(u, ref) <= 1e-10
+
+
+def test_explicit_nodes_and_line_rule_families():
+    """NODES (negative weights allowed, Sec. 4.1) and LINE_RULE (kite via eq. ptr)."""
+    X, Y, Wt, V = Q.ptr_line_rule(
+        lambda s: (0.5 * np.cos(s) + 0.5 * np.cos(2 * s), np.sin(s)),
+        lambda s: (-0.5 * np.sin(s) - np.sin(2 * s), np.cos(s)), 160)
+    kite = {"kind": "line_rule", "X": X, "Y": Y, "W": Wt, "V": V, "m": 40}
+    g = W.rng(7, 0)
+    nodes = {"kind": "nodes", "x": g.uniform(-1, 1, 500), "y": g.uniform(-1, 1, 500),
+             "w": g.normal(0, 1e-3, 500)}
+    grid = W.grid_spec(64, 64, 0.045)
+    xi, eta = oracle.grid_targets(64, 64, 0.045)
+    for fams in ([kite], [nodes], [kite, nodes]):
+        ref = oracle.field(fams, 0.1, 1.0, xi, eta).reshape(64, 64)
+        u = plan(fams, 0.1, 1.0, 1e-12, precision="fp64", grid=grid).eval().cpu().numpy()
+        assert rel_l2(u, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_eval_host_matches_device(prec):
+    """Host-buffer entry point = device entry point (up to the order of the
+    shared-memory atomic additions, which varies between runs)."""
+    cfg = W.disc()
+    tol, _ = BARS[prec]
+    p = plan(cfg["families"], 0.1, 1.0, tol, precision=prec, grid=cfg["grid"])
+    ud = p.eval().cpu().numpy()
+    uh = p.eval_host()
+    assert rel_l2(uh, ud) <= (1e-13 if prec == "fp64" else 2e-6)
+    p3 = plan(cfg["families"], 0.1, 1.0, tol, precision=prec, box=(-1.5, 1.5, -1.5, 1.5))
+    xi, eta = W.disc_targets(777, 1.5, 1)
+    h = np.ascontiguousarray(np.stack([xi, eta], 1))
+    u3d = p3.eval(torch.tensor(h, device="cuda")).cpu().numpy()
+    u3h = p3.eval_host(h)
+    assert rel_l2(u3h, u3d) <= (1e-13 if prec == "fp64" else 2e-6)
+
+
+# ------------------------------------------------------------------ type 3 (scattered)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_t3_star_scattered(prec):
+    fam = [W.fourier_family(W.STAR_PARAMS, 32, 16, 48, cx=0.03, cy=-0.02)]
+    lz = 0.05
+    xi, eta = W.disc_targets(3001, 1.5, 2)
+    ref = oracle.field(fam, lz, 1.0, xi, eta)
+    tol, bar = BARS[prec]
+    p = plan(fam, lz, 1.0, tol, precision=prec, box=(-1.5, 1.5, -1.5, 1.5))
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    u = p.eval(t).cpu().numpy()
+    assert rel_l2(u, ref) <= bar
+
+
+def test_t3_offset_box_and_occulter():
+    fam = [W.fourier_family([1.0, 0.1, 0.0], 32, 16, 40)]
+    lz = 0.08
+    g = W.rng(8, 0)
+    xi, eta = g.uniform(0.2, 1.4, 1500), g.uniform(-1.1, -0.3, 1500)
+    ref = 1.0 - oracle.field(fam, lz, 1.0, xi, eta)
+    p = plan(fam, lz, 1.0, 1e-12, precision="fp64", output="occulter", box=(0.2, 1.4, -1.1, -0.3))
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    assert rel_l2(p.eval(t).cpu().numpy(), ref) <= 1e-10
+
+
+def test_t3_empty_and_single_target():
+    fam = [W.fourier_family([1.0], 16, 16, 16)]
+    p = plan(fam, 0.1, 1.0, 1e-12, precision="fp64", box=(-1, 1, -1, 1))
+    t0 = torch.empty((0, 2), dtype=torch.float64, device="cuda")
+    assert p.eval(t0).shape == (0,)
+    t1 = torch.tensor([[0.0, 0.0]], dtype=torch.float64, device="cuda")
+    u = p.eval(t1).cpu().numpy()
+    assert abs(u[0] - oracle.field(fam, 0.1, 1.0, [0.0], [0.0])[0]) < 1e-10
+
+
+def test_t3_target_outside_box_is_reported():
+    from paper_2010_05978_gb300 import FresnelError
+    fam = [W.fourier_family([1.0], 16, 16, 16)]
+    p = plan(fam, 0.1, 1.0, 1e-6, box=(-1, 1, -1, 1))
+    t = torch.tensor([[0.0, 0.0], [1.5, 0.0]], dtype=torch.float64, device="cuda")
+    with pytest.raises(FresnelError) as e:
+        p.eval(t)
+    assert e.value.status == -6
+    # the plan stays usable after the error
+    ok = torch.tensor([[0.5, 0.5]], dtype=torch.float64, device="cuda")
+    p.eval(ok)
+
+
+# ------------------------------------------------------------------ full-size workload
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_star_F100_t1_full_size_sampled(prec):
+    """Star r = 1 + 0.3 cos 5t at F = 100, 524,288 nodes, 1000 x 1000 grid: sampled targets."""
+    cfg = W.star()
+    fam, g = cfg["families"], cfg["grid"]
+    tol, bar = BARS[prec]
+    u = plan(fam, cfg["lam"], 1.0, tol, precision=prec, grid=g,
+             recompute_nodes=True).eval().cpu().numpy().ravel()
+    xi, eta = oracle.grid_targets(g["n1"], g["n2"], g["h"])
+    idx = W.rng(2, 7).choice(len(xi), 400, replace=False)
+    ref = oracle.field(fam, cfg["lam"], 1.0, xi[idx], eta[idx])
+    assert rel_l2(u[idx], ref) <= bar
+
+
+def test_star_F100_t3_full_size_sampled():
+    cfg = W.star()
+    fam = cfg["families"]
+    xi, eta = W.disc_targets(1000000, 1.5, 2)
+    p = plan(fam, cfg["lam"], 1.0, 1e-6, precision="fp32", box=(-1.5, 1.5, -1.5, 1.5),
+             recompute_nodes=True)
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    u = p.eval(t).cpu().numpy()
+    idx = W.rng(2, 8).choice(len(xi), 400, replace=False)
+    ref = oracle.field(fam, cfg["lam"], 1.0, xi[idx], eta[idx])
+    assert rel_l2(u[idx], ref) <= 1e-6
