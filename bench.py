@@ -103,11 +103,11 @@ def oracle_rate(cfg, targets, budget_s):
     g = cfg["grid"]
     gx, gy = oracle.grid_targets(g["n1"], g["n2"], g["h"])
     rng = W.rng(2, 11)
+    x, y, w = oracle.nodes(fam)                       # calibration only
     t0 = time.perf_counter()
-    oracle.field(fam, cfg["lam"], cfg["z"], gx[:8], gy[:8])
-    probe = time.perf_counter() - t0
-    per_target = max(probe / 8, 1e-6)
-    m = int(max(16, min(20000, budget_s / per_target)))
+    direct.direct_sum(x, y, w, gx[:64], gy[:64], cfg["lam"] * cfg["z"])
+    per_target = max((time.perf_counter() - t0) / 64, 1e-7)
+    m = int(max(16, min(200000, budget_s / per_target)))
     m -= m % 2
     ig = rng.choice(len(gx), m // 2, replace=False)
     it = rng.choice(len(targets), m // 2, replace=False)
@@ -303,8 +303,8 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
