@@ -18,7 +18,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -54,35 +53,39 @@ def config_dict(cfg, n_gpus):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi sampling (every 100 ms) of SM clocks and throttle reasons
+    while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
     def __init__(self, index):
         self.index = index
         self.samples = []
-        self._stop = threading.Event()
-        self._t = None
+        self._p = None
 
     def start(self):
-        def run():
-            q = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap")
-            while not self._stop.is_set():
-                try:
-                    out = subprocess.run(["nvidia-smi", "-i", str(self.index),
-                                          "--query-gpu=" + q, "--format=csv,noheader,nounits"],
-                                         capture_output=True, text=True, timeout=5).stdout
-                    f = [s.strip() for s in out.strip().split(",")]
-                    if len(f) >= 7:
-                        self.samples.append(f)
-                except Exception:
-                    pass
-                self._stop.wait(0.2)
-        self._t = threading.Thread(target=run, daemon=True)
-        self._t.start()
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                        "--query-gpu=" + self.QUERY,
+                                        "--format=csv,noheader,nounits", "-lms", "100"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._p = None
 
     def stop(self):
-        self._stop.set()
-        if self._t:
-            self._t.join(timeout=10)
+        if self._p is not None:
+            self._p.terminate()
+            try:
+                out, _ = self._p.communicate(timeout=10)
+            except Exception:
+                self._p.kill()
+                out, _ = self._p.communicate()
+            for line in out.splitlines():
+                f = [s.strip() for s in line.split(",")]
+                if len(f) >= 7:
+                    self.samples.append(f)
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]

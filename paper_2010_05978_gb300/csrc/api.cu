@@ -54,7 +54,7 @@ struct Plan {
     int nf1 = 0, nf2 = 0, nfft1 = 0, nfft2 = 0;
     int n1 = 0, n2 = 0;
     int ntx = 0, nty = 0, ntiles = 0;
-    int chunk_cap = 0, max_chunks = 0, max_slots = 0;
+    int chunk_cap = 0, max_chunks = 0, max_split = 0;
     long long n_records = 0;
     int spread_blocks = 0;
     ChirpParams cp{};
@@ -67,9 +67,9 @@ struct Plan {
     int* counts = nullptr;
     int* cursor = nullptr;
     Chunk* chunks = nullptr;
-    int* n_chunks = nullptr;
-    int* tile_counters = nullptr;
-    void* partials = nullptr;
+    int* n_meta = nullptr;        // [chunks, split tiles]
+    int* split_tiles = nullptr;
+    int* work = nullptr;          // dynamic chunk counter + finished blocks
     void* grid = nullptr;
     void* inter = nullptr;
     void* F = nullptr;
@@ -82,6 +82,8 @@ struct Plan {
     double* gq_t = nullptr;
     double* gq_w = nullptr;
     int gq_n = 0;
+    double* cheb = nullptr;
+    int ncheb = 0;
     unsigned* status = nullptr;
     bool nodes_ready = false;
     double* stage_tgt = nullptr;
@@ -149,6 +151,8 @@ int nice_size(double target, int mult) {
 // uses sigma = 2 (at 5/4 the deconvolution amplifies FP32 rounding by >1e2 at
 // the band edge) and designs the kernel for tol/10, leaving room for FP32
 // rounding under the requested tolerance.
+void fit_horner(int w, double beta, HornerTab* h);
+
 void choose_kernel(Plan* p) {
     double tk = p->tol;
     double sigma;
@@ -173,6 +177,65 @@ void choose_kernel(Plan* p) {
     p->ks.w = w;
     p->ks.beta = beta;
     p->ks.betaf = (float)beta;
+    p->ks.horner.deg = -1;
+    if (p->prec == FRESNEL_FP32_FAST) fit_horner(w, beta, &p->ks.horner);
+}
+
+// Fit, for each of the w unit pieces of the kernel, a polynomial in
+// t = 2 f - 1 (f the node's fractional offset): Chebyshev interpolation at
+// deg + 1 points, converted to monomials in long double.  The degree grows
+// until the maximum error (on a fine grid) stops improving or drops below
+// 1e-9; the kernel's square-root end points set a floor near e^-beta.
+void fit_horner(int w, double beta, HornerTab* h) {
+    auto psi = [&](long double z) -> long double {
+        long double a = 1.0L - z * z;
+        return a > 0 ? std::exp((long double)beta * (std::sqrt(a) - 1.0L)) : 0.0L;
+    };
+    double prev_err = 1e300;
+    HornerTab best{};
+    best.deg = -1;
+    for (int d = 4; d <= kMaxHornerDeg; ++d) {
+        const int n = d + 1;
+        HornerTab t{};
+        t.deg = d;
+        double err = 0.0;
+        for (int a = 0; a < w; ++a) {
+            auto g = [&](long double tt) {
+                long double f = 0.5L * (tt + 1.0L);
+                return psi(((long double)a + 1.0L - 0.5L * w - f) * 2.0L / w);
+            };
+            std::vector<long double> b(n), mono(n, 0.0L), T0(n, 0.0L), T1(n, 0.0L), T2(n);
+            for (int k = 0; k < n; ++k) {
+                long double acc = 0.0L;
+                for (int i = 0; i < n; ++i) {
+                    long double th = 3.14159265358979323846264338327950288L * (i + 0.5L) / n;
+                    acc += g(std::cos(th)) * std::cos(k * th);
+                }
+                b[k] = (k == 0 ? 1.0L : 2.0L) * acc / n;
+            }
+            T0[0] = 1.0L;
+            if (n > 1) T1[1] = 1.0L;
+            for (int k = 0; k < n; ++k) {
+                const std::vector<long double>& Tk = k == 0 ? T0 : T1;
+                for (int j = 0; j < n; ++j) mono[j] += b[k] * Tk[j];
+                if (k >= 1 && k + 1 < n) {   // T_{k+1} = 2 t T_k - T_{k-1}
+                    for (int j = 0; j < n; ++j) T2[j] = (j > 0 ? 2.0L * T1[j - 1] : 0.0L) - T0[j];
+                    T0 = T1;
+                    T1 = T2;
+                }
+            }
+            for (int j = 0; j < n; ++j) t.c[a][j] = (float)mono[j];
+            for (int i = 0; i <= 400; ++i) {
+                long double tt = -1.0L + i / 200.0L, acc = 0.0L;
+                for (int j = n - 1; j >= 0; --j) acc = acc * tt + mono[j];
+                err = std::max(err, (double)std::fabs(acc - g(tt)));
+            }
+        }
+        if (err < prev_err) best = t;
+        if (err < 1e-9 || err > 0.9 * prev_err) break;
+        prev_err = err;
+    }
+    *h = best;
 }
 
 fresnel_status validate_family(const fresnel_family& f, long long* n_bdry, long long* n_nodes,
@@ -238,8 +301,9 @@ fresnel_status run_nodes(Plan* p, double* dx, double* dy, double* dw) {
 
 template <typename T>
 fresnel_status run_sort(Plan* p) {
-    launch_scan_chunks(p->ntiles, p->counts, p->cursor, p->chunks, p->n_chunks, p->chunk_cap,
-                       p->max_chunks, p->st);
+    launch_scan_chunks(p->ntiles, p->counts, p->cursor, p->chunks, p->n_meta, p->split_tiles,
+                       p->chunk_cap, p->max_chunks, p->max_split, p->st);
+    ev_record(p, "scan");
     launch_scatter<T>(p->N, p->cp, (const NodeRec<T>*)p->rec, p->cursor, (NodeRec<T>*)p->sorted,
                       p->n_records, p->status, p->st);
     p->launches += 2;
@@ -255,11 +319,11 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         FRES_TRY(run_nodes<T>(p, nullptr, nullptr, nullptr));
         ev_record(p, "nodes_chirp_count");
         FRES_TRY(run_sort<T>(p));
-        ev_record(p, "scan_scatter");
+        ev_record(p, "scatter");
         p->nodes_ready = true;
     }
-    launch_spread<T>((const NodeRec<T>*)p->sorted, p->chunks, p->n_chunks, p->max_chunks,
-                     (cx_t<T>*)p->grid, (cx_t<T>*)p->partials, p->tile_counters, p->nf1, p->nf2,
+    launch_spread<T>((const NodeRec<T>*)p->sorted, p->chunks, p->n_meta, p->max_chunks,
+                     p->split_tiles, p->max_split, (cx_t<T>*)p->grid, p->work, p->nf1, p->nf2,
                      p->ntx, p->ks, p->spread_blocks, p->st);
     p->launches++;
     ev_record(p, "spread");
@@ -318,8 +382,8 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ev_record(p, "fft_cols");
         p->launches += 2;
         if (M > 0) {
-            launch_interp_w<T>(d_targets, M, (const cx_t<T>*)p->F, p->ip, p->ks, p->gq_t, p->gq_w,
-                               p->gq_n, d_out, p->status, p->st);
+            launch_interp_w<T>(d_targets, M, (const cx_t<T>*)p->F, p->ip, p->ks, p->cheb,
+                               p->ncheb, d_out, p->status, p->st);
             p->launches++;
         }
         ev_record(p, "interp_epilogue");
@@ -486,9 +550,9 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
     if (!fft_supported(p->nfft1, dbl, &cmax) || !fft_supported(p->nfft2, dbl, &cmax))
         return fres_fail(FRESNEL_ERR_UNSUPPORTED,
                          "FFT size " + std::to_string(p->nfft1) + " x " + std::to_string(p->nfft2) +
-                             " exceeds this build's single-pass limit (8192)");
-    p->fp1 = make_fft_plan(p->nfft1);
-    p->fp2 = make_fft_plan(p->nfft2);
+                             " exceeds this build's single-pass limit (8192 FP32, 4096 FP64)");
+    p->fp1 = make_fft_plan(p->nfft1, dbl ? 8 : 16);
+    p->fp2 = make_fft_plan(p->nfft2, dbl ? 8 : 16);
     p->cp.nf1 = p->nf1;
     p->cp.nf2 = p->nf2;
     p->ntx = p->nf1 / kTile;
@@ -496,7 +560,7 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
     p->ntiles = p->ntx * p->nty;
     p->cp.ntx = p->ntx;
     p->cp.nty = p->nty;
-    p->chunk_cap = dbl ? 1024 : 2048;
+    p->chunk_cap = dbl ? 256 : 512;
 
     // ---------------- node pass once: exact record / chunk / slot counts
     FRES_TRY(dalloc(p, (void**)&p->status, sizeof(unsigned)));
@@ -504,28 +568,28 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
     FRES_TRY(dalloc(p, &p->rec, p->rsize() * p->N));
     FRES_TRY(dalloc(p, (void**)&p->counts, sizeof(int) * p->ntiles));
     FRES_TRY(dalloc(p, (void**)&p->cursor, sizeof(int) * p->ntiles));
-    FRES_TRY(dalloc(p, (void**)&p->tile_counters, sizeof(int) * p->ntiles));
+    FRES_TRY(dalloc(p, (void**)&p->work, 2 * sizeof(int)));
     FRES_CK(cudaMemsetAsync(p->counts, 0, sizeof(int) * p->ntiles, p->st));
-    FRES_CK(cudaMemsetAsync(p->tile_counters, 0, sizeof(int) * p->ntiles, p->st));
+    FRES_CK(cudaMemsetAsync(p->work, 0, 2 * sizeof(int), p->st));
     FRES_TRY(run_nodes<T>(p, nullptr, nullptr, nullptr));
     std::vector<int> hc(p->ntiles);
     FRES_CK(cudaMemcpyAsync(hc.data(), p->counts, sizeof(int) * p->ntiles, cudaMemcpyDeviceToHost, p->st));
     FRES_CK(cudaStreamSynchronize(p->st));
     FRES_CK(cudaGetLastError());
-    long long nrec = 0, nch = 0, nsl = 0;
+    long long nrec = 0, nch = 0, nsplit = 0;
     for (int c : hc) {
         long long k = c > p->chunk_cap ? (c + p->chunk_cap - 1) / p->chunk_cap : 1;
         nrec += c;
         nch += k;
-        if (k > 1) nsl += k;
+        if (k > 1) ++nsplit;
     }
     p->n_records = nrec;
     p->max_chunks = (int)nch;
-    p->max_slots = (int)std::max(1LL, nsl);
+    p->max_split = (int)nsplit;
     FRES_TRY(dalloc(p, &p->sorted, p->rsize() * std::max(1LL, nrec)));
     FRES_TRY(dalloc(p, (void**)&p->chunks, sizeof(Chunk) * p->max_chunks));
-    FRES_TRY(dalloc(p, (void**)&p->n_chunks, sizeof(int)));
-    FRES_TRY(dalloc(p, &p->partials, p->csize() * kTile * kTile * (size_t)p->max_slots));
+    FRES_TRY(dalloc(p, (void**)&p->n_meta, 2 * sizeof(int)));
+    FRES_TRY(dalloc(p, (void**)&p->split_tiles, sizeof(int) * std::max(1LL, nsplit)));
     FRES_TRY(run_sort<T>(p));
     p->nodes_ready = true;
     p->spread_blocks = 152 * 8;
@@ -562,6 +626,29 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
         FRES_TRY(dalloc(p, &p->dec2, rs * p->nf2));
         launch_t3_deconv(p->nf1, p->nfft1, w, p->ks.beta, p->dec1, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
         launch_t3_deconv(p->nf2, p->nfft2, w, p->ks.beta, p->dec2, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
+        // Even Chebyshev series of psihat on [-t_max, t_max], t = (xi - xi_c) * sh.
+        const double* b = p->opts.box;
+        double tmax = std::max(0.5 * (b[1] - b[0]) * p->ip.sh1, 0.5 * (b[3] - b[2]) * p->ip.sh2);
+        tmax = std::max(tmax * (1.0 + 1e-12), 1e-3);
+        const int ns = kMaxCheb;
+        double* d_s = nullptr;
+        FRES_TRY(dalloc(p, (void**)&d_s, sizeof(double) * ns));
+        launch_cheb_samples(ns, tmax, w, p->ks.beta, p->gq_t, p->gq_w, p->gq_n, d_s, p->st);
+        std::vector<double> hs(ns), a(ns);
+        FRES_CK(cudaMemcpyAsync(hs.data(), d_s, sizeof(double) * ns, cudaMemcpyDeviceToHost, p->st));
+        FRES_CK(cudaStreamSynchronize(p->st));
+        for (int j = 0; j < ns; ++j) {        // a_j = c_{2j}
+            double acc = 0.0;
+            for (int i = 0; i < ns; ++i) acc += hs[i] * std::cos(2.0 * j * kPi * (i + 0.5) / (2.0 * ns));
+            a[j] = (j == 0 ? 1.0 : 2.0) * acc / ns;
+        }
+        int nk = ns;
+        while (nk > 1 && std::fabs(a[nk - 1]) < 1e-18 * std::fabs(a[0])) --nk;
+        FRES_CK(cudaMemcpyAsync(d_s, a.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaStreamSynchronize(p->st));
+        p->cheb = d_s;
+        p->ncheb = nk;
+        p->ip.inv_tmax = 1.0 / tmax;
     }
     FRES_CK(cudaGetLastError());
     FRES_CK(cudaStreamSynchronize(p->st));
@@ -726,6 +813,7 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
     info->device_bytes = p->bytes;
     int nl = 4;   // spread, two FFT passes, (type 3) interpolation
     if (p->tkind == FRESNEL_GRID) nl = 3;
+    if (p->max_split > 0) nl += 1;   // clearing of split tiles before the spread
     if (p->opts.recompute_nodes) {
         for (const FamilyDev& f : p->fams) nl += f.kind == FRESNEL_FAMILY_NODES ? 1 : 2;
         nl += 2;

@@ -14,6 +14,7 @@ namespace fres {
 constexpr int kMaxW = 16;          // widest spreading kernel supported
 constexpr int kTile = 32;          // spreading tile edge (grid points)
 constexpr int kMaxRadixStages = 32;
+constexpr int kMaxCheb = 64;       // Chebyshev terms kept for psihat (type 3)
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kPi = 3.141592653589793238462643383280;
 
@@ -40,15 +41,15 @@ struct __align__(2 * sizeof(T) > 8 ? 16 : 8) NodeRec {
 };
 
 // A spreading work item: nodes [begin, end) of the sorted record list that
-// touch tile `tile`.  Tiles with more than the chunk cap are split; the
-// chunks of a split tile write partial tiles to slots [first_slot, +nchunks)
-// and the last chunk to finish sums them in slot order.
+// touch tile `tile`.  Tiles with more than the chunk cap of records are split
+// into several chunks; their grid tile is cleared first and every chunk adds
+// its nonzero cells with global atomic adds.  Unsplit tiles (including empty
+// ones) are written with plain stores.  Chunks of split tiles come first in
+// the list so the heaviest work starts first.
 struct Chunk {
     int tile;
     int begin, end;
-    int slot;        // -1: tile not split, store directly
-    int first_slot;  // first partial slot of this tile (split tiles)
-    int nchunks;     // chunks of this tile
+    int split;       // 1: tile shared by several chunks
 };
 
 // Radix plan of one FFT length.
@@ -91,11 +92,34 @@ struct ChirpParams {
     int ntx, nty;          // tiles per dimension
 };
 
+// Piecewise-polynomial form of the spreading kernel for FP32: the value at
+// cell a of a node with fractional offset f is c[a][0] + c[a][1] t + ... with
+// t = 2 f - 1 (fitted once per plan on the Chebyshev points of each unit
+// piece).  deg < 0 means "evaluate exp/sqrt directly".  Passed by value, so
+// it lives in the kernel-parameter constant bank (uniform access).
+constexpr int kMaxHornerDeg = 19;
+struct HornerTab {
+    float c[kMaxW][kMaxHornerDeg + 1];
+    int deg;
+};
+
 struct KernelShape {
     int w;
     double beta;
     float betaf;
+    HornerTab horner;
 };
+
+template <int W>
+__device__ __forceinline__ void horner_eval(const HornerTab& h, float f, float* out) {
+    const float t = 2.0f * f - 1.0f;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        float acc = h.c[a][h.deg];
+        for (int k = h.deg - 1; k >= 0; --k) acc = fmaf(acc, t, h.c[a][k]);
+        out[a] = acc;
+    }
+}
 
 // Fourier transform of the exponential-of-semicircle spreading kernel
 // psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)), |u| <= w/2 (grid points), at
@@ -121,8 +145,10 @@ template <typename T>
 void launch_nodes_count(const FamilyDev& f, const ChirpParams& cp, NodeRec<T>* rec,
                         int* counts, double* dx, double* dy, double* dw,
                         unsigned* status, cudaStream_t st);
-void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_chunks,
-                        int chunk_cap, int max_chunks, cudaStream_t st);
+// n_meta[0] = chunks, n_meta[1] = split tiles (listed in split_tiles)
+void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_meta,
+                        int* split_tiles, int chunk_cap, int max_chunks, int max_split,
+                        cudaStream_t st);
 template <typename T>
 void launch_scatter(long long n, const ChirpParams& cp, const NodeRec<T>* rec, int* cursor,
                     NodeRec<T>* sorted, long long cap, unsigned* status, cudaStream_t st);
@@ -136,10 +162,11 @@ void launch_t3_deconv(int ng, int nfft, int w, double beta, void* table, int is_
                       const double* gq_t, const double* gq_w, int q, cudaStream_t st);
 
 // k_spread.cu
+// work[0]: next chunk, work[1]: finished blocks (both return to 0 at exit)
 template <typename T>
-void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_chunks,
-                   int max_chunks, cx_t<T>* grid, cx_t<T>* partials, int* tile_counters,
-                   int nf1, int nf2, int ntx, const KernelShape& ks, int nblocks,
+void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
+                   int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
+                   int* work, int nf1, int nf2, int ntx, const KernelShape& ks, int nblocks,
                    cudaStream_t st);
 
 // k_fft.cu
@@ -171,7 +198,7 @@ void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st);
 template <typename T>
 void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st);
 bool fft_supported(int n, int is_double, int* max_cols);
-FftPlan make_fft_plan(int n);
+FftPlan make_fft_plan(int n, int max_radix);
 
 // k_interp.cu
 struct InterpParams {
@@ -181,14 +208,18 @@ struct InterpParams {
     double kq;               // pi / lz
     double p1, p2;           // post-phase: -2 pi C / lz
     double inv_lz;
+    double inv_tmax;         // 1 / t_max of the Chebyshev series of psihat
     double box[4];
     int nfft1, nfft2;
     int occulter;
 };
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
-                     const KernelShape& ks, const double* gq_t, const double* gq_w, int q,
+                     const KernelShape& ks, const double* cheb, int ncheb,
                      void* out, unsigned* status, cudaStream_t st);
+// psihat at the n even-half Chebyshev points of [-t_max, t_max] (plan time)
+void launch_cheb_samples(int n, double tmax, int w, double beta, const double* gq_t,
+                         const double* gq_w, int q, double* out, cudaStream_t st);
 
 }  // namespace fres
 

@@ -21,7 +21,7 @@ namespace fres {
 
 namespace {
 
-constexpr int kFftThreads = 1024;
+constexpr int kFftThreads = 512;
 
 template <typename T> struct Ops {
     using C = cx_t<T>;
@@ -35,92 +35,173 @@ template <typename T> struct Ops {
     static __device__ __forceinline__ C mul_negi(C a) { return mk(a.y, -a.x); }   // -i a
 };
 
-// One Stockham stage of radix R over the smem array S[n][ncol] (column c of
-// element e at S[e * ncol + c]).
-template <typename T, int R, int EMAX>
-__device__ __forceinline__ void stage(cx_t<T>* S, int n, int ncol, int p, const cx_t<T>* tw) {
+// In-register DFTs y_t = sum_q u_q e^{-2 pi i q t / R}.  Radix 8 is two
+// radix-4 halves joined by w_8^k; radix 16 is 4 x 4 with w_16^{n2 k1}
+// twiddles between the two radix-4 layers (Cooley-Tukey in registers).
+template <typename T, int R> struct Dft;
+template <typename T> struct Dft<T, 2> {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ void run(const C* u, C* y) {
+        y[0] = Ops<T>::add(u[0], u[1]);
+        y[1] = Ops<T>::sub(u[0], u[1]);
+    }
+};
+template <typename T> struct Dft<T, 4> {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ void run(const C* u, C* y) {
+        using O = Ops<T>;
+        C t0 = O::add(u[0], u[2]), t1 = O::sub(u[0], u[2]);
+        C t2 = O::add(u[1], u[3]), t3 = O::mul_negi(O::sub(u[1], u[3]));
+        y[0] = O::add(t0, t2);
+        y[2] = O::sub(t0, t2);
+        y[1] = O::add(t1, t3);
+        y[3] = O::sub(t1, t3);
+    }
+};
+template <typename T> struct Dft<T, 3> {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ void run(const C* u, C* y) {
+        using O = Ops<T>;
+        const T c3 = (T)-0.5, s3 = (T)0.86602540378443864676372317075294;
+        C s = O::add(u[1], u[2]), d = O::sub(u[1], u[2]);
+        C a = O::add(u[0], O::scale(s, c3));
+        C b = O::mul_negi(O::scale(d, s3));   // -i s3 (u1 - u2)
+        y[0] = O::add(u[0], s);
+        y[1] = O::add(a, b);
+        y[2] = O::sub(a, b);
+    }
+};
+template <typename T> struct Dft<T, 5> {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ void run(const C* u, C* y) {
+        using O = Ops<T>;
+        const T c1 = (T)0.30901699437494742410229341718282;   // cos(2 pi/5)
+        const T s1 = (T)0.95105651629515357211643933337938;   // sin(2 pi/5)
+        const T c2 = (T)-0.80901699437494742410229341718282;  // cos(4 pi/5)
+        const T s2 = (T)0.58778525229247312916870595463907;   // sin(4 pi/5)
+        C a14 = O::add(u[1], u[4]), d14 = O::sub(u[1], u[4]);
+        C a23 = O::add(u[2], u[3]), d23 = O::sub(u[2], u[3]);
+        C r1 = O::add(u[0], O::add(O::scale(a14, c1), O::scale(a23, c2)));
+        C r2 = O::add(u[0], O::add(O::scale(a14, c2), O::scale(a23, c1)));
+        C i1 = O::mul_negi(O::add(O::scale(d14, s1), O::scale(d23, s2)));
+        C i2 = O::mul_negi(O::sub(O::scale(d14, s2), O::scale(d23, s1)));
+        y[0] = O::add(u[0], O::add(a14, a23));
+        y[1] = O::add(r1, i1);
+        y[4] = O::sub(r1, i1);
+        y[2] = O::add(r2, i2);
+        y[3] = O::sub(r2, i2);
+    }
+};
+template <typename T> struct Dft<T, 8> {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ void run(const C* u, C* y) {
+        using O = Ops<T>;
+        const T r = (T)0.70710678118654752440084436210485;   // 1/sqrt(2)
+        C e[4] = {u[0], u[2], u[4], u[6]}, o[4] = {u[1], u[3], u[5], u[7]}, a[4], b[4];
+        Dft<T, 4>::run(e, a);
+        Dft<T, 4>::run(o, b);
+        // w8^1 = (1 - i)/sqrt2, w8^2 = -i, w8^3 = -(1 + i)/sqrt2
+        b[1] = O::mk(r * (b[1].x + b[1].y), r * (b[1].y - b[1].x));
+        b[2] = O::mul_negi(b[2]);
+        b[3] = O::mk(r * (b[3].y - b[3].x), -r * (b[3].x + b[3].y));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            y[k] = O::add(a[k], b[k]);
+            y[k + 4] = O::sub(a[k], b[k]);
+        }
+    }
+};
+template <typename T> struct Dft<T, 16> {
+    using C = cx_t<T>;
+    static __device__ __forceinline__ void run(const C* u, C* y) {
+        using O = Ops<T>;
+        // cos / sin of 2 pi j / 16, j = 0..9
+        const T cs[10] = {(T)1, (T)0.92387953251128675612818318939679,
+                          (T)0.70710678118654752440084436210485,
+                          (T)0.38268343236508977172845998403040, (T)0,
+                          (T)-0.38268343236508977172845998403040,
+                          (T)-0.70710678118654752440084436210485,
+                          (T)-0.92387953251128675612818318939679, (T)-1,
+                          (T)-0.92387953251128675612818318939679};
+        const T sn[10] = {(T)0, (T)0.38268343236508977172845998403040,
+                          (T)0.70710678118654752440084436210485,
+                          (T)0.92387953251128675612818318939679, (T)1,
+                          (T)0.92387953251128675612818318939679,
+                          (T)0.70710678118654752440084436210485,
+                          (T)0.38268343236508977172845998403040, (T)0,
+                          (T)-0.38268343236508977172845998403040};
+        C A[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            C v[4] = {u[n2], u[4 + n2], u[8 + n2], u[12 + n2]};
+            Dft<T, 4>::run(v, A[n2]);
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) {
+                const int j = n2 * k1;
+                if (j > 0) A[n2][k1] = O::mul(A[n2][k1], O::mk(cs[j], -sn[j]));
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C v[4] = {A[0][k1], A[1][k1], A[2][k1], A[3][k1]}, d[4];
+            Dft<T, 4>::run(v, d);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = d[k2];
+        }
+    }
+};
+
+// One Stockham stage of radix R from smem array src[n][ncol] to dst[n][ncol]
+// (column c of element e at [e * ncol + c]); out of place, so each thread
+// holds one butterfly at a time and one barrier ends the stage.
+template <typename T, int R>
+__device__ __forceinline__ void stage(const cx_t<T>* __restrict__ src, cx_t<T>* __restrict__ dst,
+                                      int n, int ncol, int p, const cx_t<T>* __restrict__ tw) {
     using O = Ops<T>;
     using C = cx_t<T>;
-    constexpr int IT = (EMAX + R - 1) / R;
     const int nb = n / R;
     const int items = nb * ncol;
     const int twstep = n / (p * R);
-    C y[IT][R];
+    for (int w = threadIdx.x; w < items; w += blockDim.x) {
+        const int c = w % ncol, i = w / ncol, k = i % p;
+        C u[R], y[R];
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-        const int w = threadIdx.x + it * blockDim.x;
-        if (w < items) {
-            const int c = w % ncol, i = w / ncol, k = i % p;
-            C u[R];
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                u[q] = S[(i + q * nb) * ncol + c];
-                if (q > 0 && k > 0) u[q] = O::mul(u[q], tw[q * k * twstep]);
-            }
-            if (R == 2) {
-                y[it][0] = O::add(u[0], u[1]);
-                y[it][1] = O::sub(u[0], u[1]);
-            } else if (R == 4) {
-                C t0 = O::add(u[0], u[2]), t1 = O::sub(u[0], u[2]);
-                C t2 = O::add(u[1], u[3]), t3 = O::mul_negi(O::sub(u[1], u[3]));
-                y[it][0] = O::add(t0, t2);
-                y[it][2] = O::sub(t0, t2);
-                y[it][1] = O::add(t1, t3);
-                y[it][3 % R] = O::sub(t1, t3);
-            } else if (R == 3) {
-                const T c3 = (T)-0.5, s3 = (T)0.86602540378443864676372317075294;
-                C s = O::add(u[1], u[2]), d = O::sub(u[1], u[2]);
-                C a = O::add(u[0], O::scale(s, c3));
-                C b = O::mul_negi(O::scale(d, s3));          // -i s3 (u1 - u2)
-                y[it][0] = O::add(u[0], s);
-                y[it][1] = O::add(a, b);
-                y[it][2 % R] = O::sub(a, b);
-            } else if (R == 5) {
-                const T c1 = (T)0.30901699437494742410229341718282;   // cos(2 pi/5)
-                const T s1 = (T)0.95105651629515357211643933337938;   // sin(2 pi/5)
-                const T c2 = (T)-0.80901699437494742410229341718282;  // cos(4 pi/5)
-                const T s2 = (T)0.58778525229247312916870595463907;   // sin(4 pi/5)
-                C a14 = O::add(u[1], u[4 % R]), d14 = O::sub(u[1], u[4 % R]);
-                C a23 = O::add(u[2 % R], u[3 % R]), d23 = O::sub(u[2 % R], u[3 % R]);
-                C r1 = O::add(u[0], O::add(O::scale(a14, c1), O::scale(a23, c2)));
-                C r2 = O::add(u[0], O::add(O::scale(a14, c2), O::scale(a23, c1)));
-                C i1 = O::mul_negi(O::add(O::scale(d14, s1), O::scale(d23, s2)));
-                C i2 = O::mul_negi(O::sub(O::scale(d14, s2), O::scale(d23, s1)));
-                y[it][0] = O::add(u[0], O::add(a14, a23));
-                y[it][1] = O::add(r1, i1);
-                y[it][4 % R] = O::sub(r1, i1);
-                y[it][2 % R] = O::add(r2, i2);
-                y[it][3 % R] = O::sub(r2, i2);
-            }
+        for (int q = 0; q < R; ++q) {
+            u[q] = src[(i + q * nb) * ncol + c];
+            if (q > 0 && k > 0) u[q] = O::mul(u[q], __ldg(&tw[q * k * twstep]));
         }
-    }
-    __syncthreads();
+        Dft<T, R>::run(u, y);
+        const int j = (i - k) * R + k;
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-        const int w = threadIdx.x + it * blockDim.x;
-        if (w < items) {
-            const int c = w % ncol, i = w / ncol, k = i % p;
-            const int j = (i - k) * R + k;
-#pragma unroll
-            for (int t = 0; t < R; ++t) S[(j + t * p) * ncol + c] = y[it][t];
-        }
+        for (int t = 0; t < R; ++t) dst[(j + t * p) * ncol + c] = y[t];
     }
     __syncthreads();
 }
 
-template <typename T, int EMAX>
-__device__ void fft_smem(cx_t<T>* S, int ncol, const FftPlan& fp, const cx_t<T>* tw) {
+// Runs the plan's stages ping-ponging between A and B; returns the buffer
+// holding the result (natural order).
+template <typename T>
+__device__ cx_t<T>* fft_smem(cx_t<T>* A, cx_t<T>* B, int ncol, const FftPlan& fp,
+                             const cx_t<T>* tw) {
     int p = 1;
     for (int s = 0; s < fp.nstages; ++s) {
         const int r = fp.radix[s];
         switch (r) {
-            case 4: stage<T, 4, EMAX>(S, fp.n, ncol, p, tw); break;
-            case 2: stage<T, 2, EMAX>(S, fp.n, ncol, p, tw); break;
-            case 3: stage<T, 3, EMAX>(S, fp.n, ncol, p, tw); break;
-            case 5: stage<T, 5, EMAX>(S, fp.n, ncol, p, tw); break;
+            case 16:
+                if constexpr (sizeof(T) == 4) stage<T, 16>(A, B, fp.n, ncol, p, tw);
+                break;
+            case 8: stage<T, 8>(A, B, fp.n, ncol, p, tw); break;
+            case 4: stage<T, 4>(A, B, fp.n, ncol, p, tw); break;
+            case 2: stage<T, 2>(A, B, fp.n, ncol, p, tw); break;
+            case 3: stage<T, 3>(A, B, fp.n, ncol, p, tw); break;
+            case 5: stage<T, 5>(A, B, fp.n, ncol, p, tw); break;
         }
+        cx_t<T>* t = A;
+        A = B;
+        B = t;
         p *= r;
     }
+    return A;
 }
 
 template <typename T> __host__ __device__ constexpr int emax() { return 8; }
@@ -145,6 +226,7 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = (C*)smem_raw;
+    C* S2 = S + fp.n;
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     for (int row = blockIdx.x; row < a.nrows; row += gridDim.x) {
@@ -160,10 +242,10 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
             S[in_pos(i, a.in_len, n, a.centered_in)] = v;
         }
         __syncthreads();
-        fft_smem<T, emax<T>()>(S, 1, fp, tw);
+        const C* R = fft_smem<T>(S, S2, 1, fp, tw);
         C* out = (C*)a.out + (long long)row * a.out_stride;
         for (int kp = threadIdx.x; kp < a.out_len; kp += blockDim.x)
-            out[kp] = S[out_src(kp, a.out_len, n)];
+            out[kp] = R[out_src(kp, a.out_len, n)];
         __syncthreads();
     }
 }
@@ -174,6 +256,7 @@ k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = (C*)smem_raw;
+    C* S2 = S + fp.n * ncol;
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     const int ngroups = (a.ncols + ncol - 1) / ncol;
@@ -190,11 +273,11 @@ k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
             S[in_pos(i, a.in_len, n, a.centered_in) * ncol + c] = v;
         }
         __syncthreads();
-        fft_smem<T, emax<T>()>(S, ncol, fp, tw);
+        const C* R = fft_smem<T>(S, S2, ncol, fp, tw);
         for (int e = threadIdx.x; e < a.out_len * ncol; e += blockDim.x) {
             const int kp = e / ncol, c = e % ncol;
             if (c0 + c >= a.ncols) continue;
-            C v = S[out_src(kp, a.out_len, n) * ncol + c];
+            C v = R[out_src(kp, a.out_len, n) * ncol + c];
             if (a.ax) {
                 v = Ops<T>::mul(v, ((const C*)a.ax)[c0 + c]);
                 v = Ops<T>::mul(v, ((const C*)a.ay)[kp]);
@@ -216,10 +299,14 @@ int threads_for(int elems, int em) {
 
 }  // namespace
 
-FftPlan make_fft_plan(int n) {
+FftPlan make_fft_plan(int n, int max_radix) {
     FftPlan fp{};
     fp.n = n;
     int m = n;
+    if (max_radix >= 16)
+        while (m % 16 == 0) { fp.radix[fp.nstages++] = 16; m /= 16; }
+    if (max_radix >= 8)
+        while (m % 8 == 0) { fp.radix[fp.nstages++] = 8; m /= 8; }
     while (m % 4 == 0) { fp.radix[fp.nstages++] = 4; m /= 4; }
     while (m % 2 == 0) { fp.radix[fp.nstages++] = 2; m /= 2; }
     while (m % 3 == 0) { fp.radix[fp.nstages++] = 3; m /= 3; }
@@ -228,24 +315,22 @@ FftPlan make_fft_plan(int n) {
     return fp;
 }
 
-// Largest column batch (power of two, <= 8) whose n x C block fits in the
-// per-thread register budget and in shared memory; 0 if n itself does not.
+// Largest column batch (power of two, <= 8) whose two n x C ping-pong buffers
+// fit in shared memory; 0 if n itself does not.
 bool fft_supported(int n, int is_double, int* max_cols) {
-    FftPlan fp = make_fft_plan(n);
+    FftPlan fp = make_fft_plan(n, 4);
     if (fp.nstages < 0 || n < 2) return false;
-    const int em = 8;
-    const long long cap_elems = (long long)em * kFftThreads;
     const long long smem_cap = 227 * 1024;
     const int esz = is_double ? 16 : 8;
     int c = 8;
-    while (c > 0 && ((long long)n * c > cap_elems || (long long)n * c * esz > smem_cap)) c >>= 1;
+    while (c > 0 && 2LL * n * c * esz > smem_cap) c >>= 1;
     if (max_cols) *max_cols = c;
     return c > 0;
 }
 
 template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st) {
-    const size_t smem = (size_t)fp.n * sizeof(cx_t<T>);
+    const size_t smem = 2 * (size_t)fp.n * sizeof(cx_t<T>);
     cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int threads = threads_for(fp.n, emax<T>());
     int blocks = a.nrows < 152 * 16 ? a.nrows : 152 * 16;
@@ -257,7 +342,7 @@ template <typename T>
 void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st) {
     int cmax = 0;
     fft_supported(fp.n, sizeof(T) == 8, &cmax);
-    const size_t smem = (size_t)fp.n * cmax * sizeof(cx_t<T>);
+    const size_t smem = 2 * (size_t)fp.n * cmax * sizeof(cx_t<T>);
     cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int threads = threads_for(fp.n * cmax, emax<T>());
     const int ngroups = (a.ncols + cmax - 1) / cmax;

@@ -22,19 +22,30 @@ __device__ __forceinline__ double reduce_phase(double ph) {
     return fma(-n, kTwoPiLo, ph);
 }
 
+// psihat(t) for |t| <= t_max from its even Chebyshev series
+// sum_k a_k T_{2k}(t / t_max) = sum_k a_k T_k(2 (t/t_max)^2 - 1), by Clenshaw.
+template <typename T>
+__device__ __forceinline__ T kernel_ft_cheb(T t, const T* a, int n, T inv_tmax) {
+    const T x = t * inv_tmax;
+    const T y = (T)2 * x * x - (T)1;
+    T b1 = 0, b2 = 0;
+    for (int k = n - 1; k >= 1; --k) {
+        const T b0 = (T)2 * y * b1 - b2 + a[k];
+        b2 = b1;
+        b1 = b0;
+    }
+    return y * b1 - b2 + a[0];
+}
+
 template <typename T, int W>
 __global__ void __launch_bounds__(256)
 k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restrict__ F,
-         InterpParams ip, T beta, const double* __restrict__ gq_t,
-         const double* __restrict__ gq_w, int q, cx_t<T>* __restrict__ out,
-         unsigned* __restrict__ status) {
-    __shared__ T s_gt[64], s_gw[64];
-    for (int i = threadIdx.x; i < q && i < 64; i += blockDim.x) {
-        s_gt[i] = (T)gq_t[i];
-        s_gw[i] = (T)gq_w[i];
-    }
+         InterpParams ip, T beta, const double* __restrict__ cheb, int ncheb,
+         cx_t<T>* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz) {
+    __shared__ T s_a[kMaxCheb];
+    for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (T)cheb[i];
     __syncthreads();
-    const T half_w = (T)(0.5 * W), two_over_w = (T)(2.0 / W);
+    const T inv_tmax = (T)ip.inv_tmax;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
          k += (long long)gridDim.x * blockDim.x) {
         const double2 t = reinterpret_cast<const double2*>(targets)[k];
@@ -54,11 +65,8 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
         if (s1 < 0) s1 += ip.nfft1;
         if (s2 < 0) s2 += ip.nfft2;
         T kx[W], ky[W];
-#pragma unroll
-        for (int a = 0; a < W; ++a) {
-            kx[a] = es_kernel<T>(((T)(a + 1) - half_w - f1) * two_over_w, beta);
-            ky[a] = es_kernel<T>(((T)(a + 1) - half_w - f2) * two_over_w, beta);
-        }
+        kernel_values<T, W>(f1, beta, hz, kx);
+        kernel_values<T, W>(f2, beta, hz, ky);
         T gr = 0, gi = 0;
 #pragma unroll
         for (int b = 0; b < W; ++b) {
@@ -77,8 +85,8 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
             gr += ky[b] * rr;
             gi += ky[b] * ri;
         }
-        const T dec = kernel_ft<T>((T)(d1 * ip.sh1), W, beta, s_gt, s_gw, q) *
-                      kernel_ft<T>((T)(d2 * ip.sh2), W, beta, s_gt, s_gw, q);
+        const T dec = kernel_ft_cheb<T>((T)(d1 * ip.sh1), s_a, ncheb, inv_tmax) *
+                      kernel_ft_cheb<T>((T)(d2 * ip.sh2), s_a, ncheb, inv_tmax);
         const double ph = reduce_phase(ip.kq * (xi * xi + eta * eta) + ip.p1 * xi + ip.p2 * eta);
         T sn, cs;
         if (sizeof(T) == 8) {
@@ -107,11 +115,26 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
     }
 }
 
+// Chebyshev samples of psihat on [0, t_max]: s_i = psihat(t_max cos(pi (i + 1/2) / (2n)))
+// for i < n (the even half of a 2n-point Chebyshev grid).
+__global__ void k_cheb_samples(int n, double tmax, int w, double beta, const double* gq_t,
+                               const double* gq_w, int q, double* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = cos(kPi * (i + 0.5) / (2.0 * n));
+    out[i] = kernel_ft<double>(tmax * x, w, beta, gq_t, gq_w, q);
+}
+
 }  // namespace
+
+void launch_cheb_samples(int n, double tmax, int w, double beta, const double* gq_t,
+                         const double* gq_w, int q, double* out, cudaStream_t st) {
+    k_cheb_samples<<<(n + 63) / 64, 64, 0, st>>>(n, tmax, w, beta, gq_t, gq_w, q, out);
+}
 
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
-                     const KernelShape& ks, const double* gq_t, const double* gq_w, int q,
+                     const KernelShape& ks, const double* cheb, int ncheb,
                      void* out, unsigned* status, cudaStream_t st) {
     if (M <= 0) return;
     long long nb = (M + 255) / 256;
@@ -119,8 +142,8 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
     T beta = (T)ks.beta;
 #define FRES_INTERP_CASE(WW)                                                                   \
     case WW:                                                                                   \
-        k_interp<T, WW><<<blocks, 256, 0, st>>>(targets, M, F, ip, beta, gq_t, gq_w, q,       \
-                                                (cx_t<T>*)out, status);                        \
+        k_interp<T, WW><<<blocks, 256, 0, st>>>(targets, M, F, ip, beta, cheb, ncheb,         \
+                                                (cx_t<T>*)out, status, ks.horner);             \
         break;
     switch (ks.w) {
         FRES_INTERP_CASE(2) FRES_INTERP_CASE(3) FRES_INTERP_CASE(4) FRES_INTERP_CASE(5)
@@ -133,10 +156,10 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
 }
 
 template void launch_interp_w<float>(const double*, long long, const float2*, const InterpParams&,
-                                     const KernelShape&, const double*, const double*, int, void*,
-                                     unsigned*, cudaStream_t);
+                                     const KernelShape&, const double*, int, void*, unsigned*,
+                                     cudaStream_t);
 template void launch_interp_w<double>(const double*, long long, const double2*,
-                                      const InterpParams&, const KernelShape&, const double*,
-                                      const double*, int, void*, unsigned*, cudaStream_t);
+                                      const InterpParams&, const KernelShape&, const double*, int,
+                                      void*, unsigned*, cudaStream_t);
 
 }  // namespace fres

@@ -238,58 +238,80 @@ __global__ void k_scatter(long long n, ChirpParams cp, const NodeRec<T>* rec, in
 }
 
 // ------------------------------------------------------------------ scan -> chunks
-// One block: exclusive scan of per-tile record counts; every tile becomes
-// max(1, ceil(count / cap)) chunks (empty tiles still get one chunk, which
-// writes zeros, so the grid needs no separate clearing).  Resets counts.
-__global__ void k_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks,
-                              int* n_chunks, int chunk_cap, int max_chunks) {
-    __shared__ long long s_rec[1024], s_ch[1024], s_sl[1024];
+// One block: exclusive scan of per-tile record counts.  A tile with more than
+// chunk_cap records becomes ceil(count / cap) chunks and is listed in
+// split_tiles; every other tile (empty ones too: they write zeros, so the grid
+// needs no separate clearing) is one chunk.  Chunks of split tiles are placed
+// first, the unsplit tiles after them.  Resets counts for the next pass.
+__global__ void k_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_meta,
+                              int* split_tiles, int chunk_cap, int max_chunks, int max_split) {
+    __shared__ long long s_rec[1024], s_sc[1024], s_ns[1024], s_st[1024];
     int t = threadIdx.x, nt = blockDim.x;
     int per = (ntiles + nt - 1) / nt;
     int lo = min(t * per, ntiles), hi = min(lo + per, ntiles);
-    long long rsum = 0, csum = 0, ssum = 0;
+    long long rsum = 0, sc = 0, ns = 0, stl = 0;
     for (int i = lo; i < hi; ++i) {
         int c = counts[i];
-        int nch = c > chunk_cap ? (c + chunk_cap - 1) / chunk_cap : 1;
         rsum += c;
-        csum += nch;
-        ssum += nch > 1 ? nch : 0;
+        if (c > chunk_cap) {
+            sc += (c + chunk_cap - 1) / chunk_cap;
+            ++stl;
+        } else {
+            ++ns;
+        }
     }
     s_rec[t] = rsum;
-    s_ch[t] = csum;
-    s_sl[t] = ssum;
+    s_sc[t] = sc;
+    s_ns[t] = ns;
+    s_st[t] = stl;
     __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scan
-        long long a = 0, b = 0, c = 0;
-        if (t >= off) { a = s_rec[t - off]; b = s_ch[t - off]; c = s_sl[t - off]; }
+    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scans
+        long long a = 0, b = 0, c = 0, d = 0;
+        if (t >= off) { a = s_rec[t - off]; b = s_sc[t - off]; c = s_ns[t - off]; d = s_st[t - off]; }
         __syncthreads();
-        s_rec[t] += a; s_ch[t] += b; s_sl[t] += c;
+        s_rec[t] += a; s_sc[t] += b; s_ns[t] += c; s_st[t] += d;
         __syncthreads();
     }
-    long long roff = s_rec[t] - rsum, coff = s_ch[t] - csum, soff = s_sl[t] - ssum;
+    const long long total_split_chunks = s_sc[nt - 1];
+    long long roff = s_rec[t] - rsum, scoff = s_sc[t] - sc, nsoff = s_ns[t] - ns, stoff = s_st[t] - stl;
     for (int i = lo; i < hi; ++i) {
         int c = counts[i];
-        int nch = c > chunk_cap ? (c + chunk_cap - 1) / chunk_cap : 1;
         cursor[i] = (int)roff;
-        for (int k = 0; k < nch; ++k) {
-            long long ci = coff + k;
+        if (c > chunk_cap) {
+            int nch = (c + chunk_cap - 1) / chunk_cap;
+            for (int k = 0; k < nch; ++k) {
+                long long ci = scoff + k;
+                if (ci < max_chunks) {
+                    Chunk ch;
+                    ch.tile = i;
+                    ch.begin = (int)(roff + (long long)k * chunk_cap);
+                    ch.end = (int)min(roff + (long long)(k + 1) * chunk_cap, roff + c);
+                    ch.split = 1;
+                    chunks[ci] = ch;
+                }
+            }
+            scoff += nch;
+            if (stoff < max_split) split_tiles[stoff] = i;
+            ++stoff;
+        } else {
+            long long ci = total_split_chunks + nsoff;
             if (ci < max_chunks) {
                 Chunk ch;
                 ch.tile = i;
-                ch.begin = (int)(roff + (long long)k * chunk_cap);
-                ch.end = (int)min(roff + (long long)(k + 1) * chunk_cap, roff + c);
-                ch.slot = nch > 1 ? (int)(soff + k) : -1;
-                ch.first_slot = nch > 1 ? (int)soff : -1;
-                ch.nchunks = nch;
+                ch.begin = (int)roff;
+                ch.end = (int)(roff + c);
+                ch.split = 0;
                 chunks[ci] = ch;
             }
+            ++nsoff;
         }
-        coff += nch;
-        if (nch > 1) soff += nch;
         roff += c;
         counts[i] = 0;
     }
-    if (t == nt - 1) *n_chunks = (int)min(s_ch[t], (long long)max_chunks);
+    if (t == nt - 1) {
+        n_meta[0] = (int)min(total_split_chunks + s_ns[t], (long long)max_chunks);
+        n_meta[1] = (int)min(s_st[t], (long long)max_split);
+    }
 }
 
 // ------------------------------------------------------------------ plan-time tables
@@ -374,10 +396,11 @@ template void launch_scatter<float>(long long, const ChirpParams&, const NodeRec
 template void launch_scatter<double>(long long, const ChirpParams&, const NodeRec<double>*, int*,
                                      NodeRec<double>*, long long, unsigned*, cudaStream_t);
 
-void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_chunks,
-                               int chunk_cap, int max_chunks, cudaStream_t st) {
-    k_scan_chunks<<<1, 1024, 0, st>>>(ntiles, counts, cursor, chunks, n_chunks, chunk_cap,
-                                      max_chunks);
+void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_meta,
+                        int* split_tiles, int chunk_cap, int max_chunks, int max_split,
+                        cudaStream_t st) {
+    k_scan_chunks<<<1, 1024, 0, st>>>(ntiles, counts, cursor, chunks, n_meta, split_tiles,
+                                      chunk_cap, max_chunks, max_split);
 }
 
 void launch_twiddles(int n, void* table, int is_double, cudaStream_t st) {

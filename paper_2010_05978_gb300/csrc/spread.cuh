@@ -5,13 +5,26 @@
 // NUFFTs of arXiv:2010.05978 (the paper uses them as a library, FINUFFT).
 //
 // Owner-computes tiles: every 32 x 32 tile of the grid is produced by one
-// work item (or, for tiles holding more than the chunk cap of node records,
-// several chunks whose partial tiles are summed in a fixed order by the last
-// chunk to finish).  Nodes whose support straddles tiles were duplicated into
-// each touched tile by the binning, so each chunk adds only inside its own
-// tile: accumulation is in shared memory, write-back is one coalesced store
-// per grid point, and no global atomics or grid clearing are needed.
+// work item.  Nodes whose support straddles tiles were duplicated into each
+// touched tile by the binning, so each work item adds only inside its own
+// tile and writes it back with one coalesced store per grid point: no grid
+// clearing pass.  Tiles holding more than the chunk cap of records (the
+// dilation rule's spokes all meet at the centre, so a few tiles can hold
+// tens of thousands) are split into chunks that run in parallel; such a tile
+// is cleared first and its chunks add their nonzero cells with global atomic
+// adds.  Work items are handed out dynamically, split chunks first.
+//
+// Inside a chunk there are no atomics either: each warp owns a private copy
+// of the tile in shared memory.  A warp stages 32 records at a time (one per
+// lane: support offsets, the w kernel values along x, and c times the w
+// kernel values along y), then walks them one by one with its lanes mapped
+// onto the w x w support cells, so every lane updates a distinct cell
+// (read-modify-write, no conflicts between lanes).  The warps' tiles are
+// summed once per chunk.  Dense clusters of nodes (the dilation rule's
+// spokes meet at the centre) therefore cost the same as sparse ones.
 #pragma once
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace fres {
@@ -26,104 +39,192 @@ template <> __device__ __forceinline__ double es_kernel<double>(double z, double
     return a > 0.0 ? exp(beta * (sqrt(a) - 1.0)) : 0.0;
 }
 
+// The w kernel values of a node with fractional offset f: cell s + a sits at
+// offset (a + 1 - w/2 - f) from the node.  FP32 uses the plan's Horner
+// polynomials when present; FP64 evaluates exp/sqrt.
 template <typename T, int W>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void kernel_values(T f, T beta, const HornerTab& hz, T* out) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (hz.deg >= 0) {
+            horner_eval<W>(hz, f, out);
+            return;
+        }
+    }
+    const T half_w = (T)(0.5 * W), two_over_w = (T)(2.0 / W);
+#pragma unroll
+    for (int a = 0; a < W; ++a) out[a] = es_kernel<T>(((T)(a + 1) - half_w - f) * two_over_w, beta);
+}
+
+constexpr int kSpreadWarps = 4;
+constexpr int kTileStride = 40;   // float2 row stride: rows land on disjoint bank halves
+
+template <typename T, int W>
+struct SpreadSmem {
+    cx_t<T> tile[kSpreadWarps][kTile * kTileStride];
+    T kx[kSpreadWarps][32][W + 1];
+    cx_t<T> cky[kSpreadWarps][32][W];
+    int dxy[kSpreadWarps][32][2];
+    int s_ci;
+};
+
+// Clears the grid tiles that several chunks will add into.
+template <typename T>
+__global__ void k_zero_split_tiles(const int* __restrict__ split_tiles,
+                                   const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid,
+                                   int nf1, int ntx) {
+    const int ns = n_meta[1];
+    for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+        const int tile = split_tiles[i];
+        const int tx0 = (tile % ntx) * kTile, ty0 = (tile / ntx) * kTile;
+        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+            cx_t<T> z;
+            z.x = (T)0;
+            z.y = (T)0;
+            grid[(long long)(ty0 + e / kTile) * nf1 + tx0 + e % kTile] = z;
+        }
+    }
+}
+
+// Chunks are taken dynamically from work[0]; the last block to finish puts
+// both counters back to zero for the next launch.
+template <typename T, int W>
+__global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks,
-         const int* __restrict__ n_chunks_p, cx_t<T>* __restrict__ grid,
-         cx_t<T>* __restrict__ partials, int* __restrict__ tile_counters, int nf1, int nf2,
-         int ntx, T beta) {
+         const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid, int* __restrict__ work,
+         int nf1, int nf2, int ntx, T beta, const HornerTab hz) {
     constexpr int TT = kTile * kTile;
-    __shared__ cx_t<T> tile[TT];
-    __shared__ int s_last;
-    const int n_chunks = *n_chunks_p;
-    const T half_w = (T)(0.5 * W);
-    const T two_over_w = (T)(2.0 / W);
-    for (int ci = blockIdx.x; ci < n_chunks; ci += gridDim.x) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SpreadSmem<T, W>& sm = *reinterpret_cast<SpreadSmem<T, W>*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    cx_t<T>* my = sm.tile[warp];
+    const int n_chunks = n_meta[0];
+    for (;;) {
+        if (threadIdx.x == 0) sm.s_ci = atomicAdd(&work[0], 1);
+        __syncthreads();
+        const int ci = sm.s_ci;
+        if (ci >= n_chunks) break;
         const Chunk ch = chunks[ci];
         const int tx0 = (ch.tile % ntx) * kTile;
         const int ty0 = (ch.tile / ntx) * kTile;
-        for (int e = threadIdx.x; e < TT; e += blockDim.x) {
-            tile[e].x = (T)0;
-            tile[e].y = (T)0;
+        for (int e = lane; e < TT; e += 32) {
+            cx_t<T> z;
+            z.x = (T)0;
+            z.y = (T)0;
+            my[(e / kTile) * kTileStride + (e % kTile)] = z;
         }
-        __syncthreads();
-        for (int k = ch.begin + threadIdx.x; k < ch.end; k += blockDim.x) {
-            const NodeRec<T> r = sorted[k];
-            int dx = r.s1 - tx0;
-            if (dx >= kTile) dx -= nf1;
-            int dy = r.s2 - ty0;
-            if (dy >= kTile) dy -= nf2;
-            T kx[W], ky[W];
+        __syncwarp();
+        for (int base = ch.begin + warp * 32; base < ch.end; base += kSpreadWarps * 32) {
+            const int k = base + lane;
+            const int cnt = min(32, ch.end - base);
+            if (lane < cnt) {
+                const NodeRec<T> r = sorted[k];
+                int dx = r.s1 - tx0;
+                if (dx >= kTile) dx -= nf1;
+                int dy = r.s2 - ty0;
+                if (dy >= kTile) dy -= nf2;
+                sm.dxy[warp][lane][0] = dx;
+                sm.dxy[warp][lane][1] = dy;
+                T kxv[W], kyv[W];
+                kernel_values<T, W>(r.f1, beta, hz, kxv);
+                kernel_values<T, W>(r.f2, beta, hz, kyv);
 #pragma unroll
-            for (int a = 0; a < W; ++a) {
-                // cell s + a sits at offset (a + 1 - w/2 - f) from the node
-                kx[a] = es_kernel<T>(((T)(a + 1) - half_w - r.f1) * two_over_w, beta);
-                ky[a] = es_kernel<T>(((T)(a + 1) - half_w - r.f2) * two_over_w, beta);
+                for (int a = 0; a < W; ++a) {
+                    sm.kx[warp][lane][a] = kxv[a];
+                    cx_t<T> v;
+                    v.x = r.cre * kyv[a];
+                    v.y = r.cim * kyv[a];
+                    sm.cky[warp][lane][a] = v;
+                }
             }
+            __syncwarp();
+            // lane -> support column a = lane % W and rows b0, b0 + RPW, ...
+            constexpr int RPW = 32 / W;             // rows covered per pass
+            constexpr int NPASS = (W + RPW - 1) / RPW;
+            const int a = lane % W, b0 = lane / W;
+            const bool lane_on = lane < RPW * W;
+            for (int j = 0; j < cnt; ++j) {
+                const int dx = sm.dxy[warp][j][0], dy = sm.dxy[warp][j][1];
+                const int x = dx + a;
+                if (lane_on && (unsigned)x < (unsigned)kTile) {
+                    const T kxv = sm.kx[warp][j][a];
 #pragma unroll
-            for (int b = 0; b < W; ++b) {
-                const int yy = dy + b;
-                if (yy >= 0 && yy < kTile) {
-                    const T vr = r.cre * ky[b], vi = r.cim * ky[b];
-#pragma unroll
-                    for (int a = 0; a < W; ++a) {
-                        const int xx = dx + a;
-                        if (xx >= 0 && xx < kTile) {
-                            atomicAdd(&tile[yy * kTile + xx].x, vr * kx[a]);
-                            atomicAdd(&tile[yy * kTile + xx].y, vi * kx[a]);
+                    for (int k = 0; k < NPASS; ++k) {
+                        const int b = b0 + k * RPW;
+                        const int y = dy + b;
+                        if (b < W && (unsigned)y < (unsigned)kTile) {
+                            const cx_t<T> c = sm.cky[warp][j][b];
+                            cx_t<T>& cell = my[y * kTileStride + x];
+                            cx_t<T> o = cell;
+                            o.x += c.x * kxv;
+                            o.y += c.y * kxv;
+                            cell = o;
                         }
                     }
                 }
+                __syncwarp();
             }
         }
         __syncthreads();
-        if (ch.slot < 0) {
-            for (int e = threadIdx.x; e < TT; e += blockDim.x) {
-                const int rr = e / kTile, cc = e % kTile;
-                grid[(long long)(ty0 + rr) * nf1 + tx0 + cc] = tile[e];
+        // sum the warps' tiles (fixed order); store, or add into a shared tile
+        cx_t<T>* dst = grid + (long long)ty0 * nf1 + tx0;
+        for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+            const int rr = e / kTile, cc = e % kTile;
+            cx_t<T> s = sm.tile[0][rr * kTileStride + cc];
+#pragma unroll
+            for (int v = 1; v < kSpreadWarps; ++v) {
+                const cx_t<T> t = sm.tile[v][rr * kTileStride + cc];
+                s.x += t.x;
+                s.y += t.y;
             }
-        } else {
-            cx_t<T>* mine = partials + (long long)ch.slot * TT;
-            for (int e = threadIdx.x; e < TT; e += blockDim.x) mine[e] = tile[e];
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0)
-                s_last = (atomicAdd(&tile_counters[ch.tile], 1) == ch.nchunks - 1);
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                for (int e = threadIdx.x; e < TT; e += blockDim.x) {
-                    T sr = (T)0, si = (T)0;
-                    for (int s = 0; s < ch.nchunks; ++s) {
-                        const cx_t<T> v = __ldcg(&partials[(long long)(ch.first_slot + s) * TT + e]);
-                        sr += v.x;
-                        si += v.y;
-                    }
-                    const int rr = e / kTile, cc = e % kTile;
-                    cx_t<T> o;
-                    o.x = sr;
-                    o.y = si;
-                    grid[(long long)(ty0 + rr) * nf1 + tx0 + cc] = o;
-                }
-                if (threadIdx.x == 0) tile_counters[ch.tile] = 0;
+            cx_t<T>* g = dst + (long long)rr * nf1 + cc;
+            if (!ch.split) {
+                *g = s;
+            } else if (s.x != (T)0 || s.y != (T)0) {
+                atomicAdd(&g->x, s.x);
+                atomicAdd(&g->y, s.y);
             }
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&work[1], 1) == (int)gridDim.x - 1) {
+            work[0] = 0;
+            work[1] = 0;
+        }
+    }
+}
+
+template <typename T, int W>
+void launch_spread_w(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
+                     int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
+                     int* work, int nf1, int nf2, int ntx, T beta, const HornerTab& hz,
+                     int nblocks, cudaStream_t st) {
+    if (max_split > 0)
+        k_zero_split_tiles<T><<<max_split, 256, 0, st>>>(split_tiles, n_meta, grid, nf1, ntx);
+    const size_t smem = sizeof(SpreadSmem<T, W>);
+    cudaFuncSetAttribute(k_spread<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread<T, W>, kSpreadWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int g = 152 * per_sm;
+    if (nblocks > 0 && nblocks < g) g = nblocks;
+    if (g > max_chunks) g = max_chunks;
+    if (g < 1) g = 1;
+    k_spread<T, W><<<g, kSpreadWarps * 32, smem, st>>>(sorted, chunks, n_meta, grid, work, nf1,
+                                                       nf2, ntx, beta, hz);
 }
 
 template <typename T>
-void launch_spread_impl(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_chunks,
-                        int max_chunks, cx_t<T>* grid, cx_t<T>* partials, int* tile_counters,
-                        int nf1, int nf2, int ntx, const KernelShape& ks, int nblocks,
+void launch_spread_impl(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
+                        int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
+                        int* work, int nf1, int nf2, int ntx, const KernelShape& ks, int nblocks,
                         cudaStream_t st) {
-    int g = nblocks < max_chunks ? nblocks : max_chunks;
-    if (g < 1) g = 1;
     T beta = (T)ks.beta;
 #define FRES_SPREAD_CASE(WW)                                                                  \
     case WW:                                                                                  \
-        k_spread<T, WW><<<g, 256, 0, st>>>(sorted, chunks, n_chunks, grid, partials,          \
-                                           tile_counters, nf1, nf2, ntx, beta);               \
+        launch_spread_w<T, WW>(sorted, chunks, n_meta, max_chunks, split_tiles, max_split,   \
+                               grid, work, nf1, nf2, ntx, beta, ks.horner, nblocks, st);     \
         break;
     switch (ks.w) {
         FRES_SPREAD_CASE(2) FRES_SPREAD_CASE(3) FRES_SPREAD_CASE(4) FRES_SPREAD_CASE(5)
