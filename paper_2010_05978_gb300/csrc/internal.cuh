@@ -209,6 +209,7 @@ struct InterpParams {
     double p1, p2;           // post-phase: -2 pi C / lz
     double inv_lz;
     double inv_tmax;         // 1 / t_max of the Chebyshev series of psihat
+    int nbin1, nbin2;        // 16 x 16 target bins per dimension of the FFT grid
     double box[4];
     int nfft1, nfft2;
     int occulter;
@@ -216,7 +217,12 @@ struct InterpParams {
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
                      const KernelShape& ks, const double* cheb, int ncheb,
-                     void* out, unsigned* status, cudaStream_t st);
+                     void* out, unsigned* status, const int* perm, cudaStream_t st);
+// Counting sort of the targets by 16 x 16 bins of the FFT grid -> perm
+// (three launches: count, scan, scatter).  counts must be zero on entry and
+// is left zero.
+void launch_target_sort(const double* targets, long long M, const InterpParams& ip, int* counts,
+                        int* cursor, int* perm, cudaStream_t st);
 // psihat at the n even-half Chebyshev points of [-t_max, t_max] (plan time)
 void launch_cheb_samples(int n, double tmax, int w, double beta, const double* gq_t,
                          const double* gq_w, int q, double* out, cudaStream_t st);

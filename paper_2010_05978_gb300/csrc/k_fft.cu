@@ -21,7 +21,9 @@ namespace fres {
 
 namespace {
 
-constexpr int kFftThreads = 512;
+constexpr int kFftThreads = 256;
+constexpr int kFftBlocksPerSm = 3;
+constexpr long long kFftSmemTarget = 76 * 1024;   // three blocks per SM
 
 template <typename T> struct Ops {
     using C = cx_t<T>;
@@ -151,6 +153,11 @@ template <typename T> struct Dft<T, 16> {
     }
 };
 
+// Shared-memory element index with one padding slot per 16 elements, so the
+// stride-R writes of the early Stockham stages spread over all banks.
+__host__ __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4) + 1; }
+
 // One Stockham stage of radix R from smem array src[n][ncol] to dst[n][ncol]
 // (column c of element e at [e * ncol + c]); out of place, so each thread
 // holds one butterfly at a time and one barrier ends the stage.
@@ -167,13 +174,13 @@ __device__ __forceinline__ void stage(const cx_t<T>* __restrict__ src, cx_t<T>* 
         C u[R], y[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            u[q] = src[(i + q * nb) * ncol + c];
+            u[q] = src[pad(i + q * nb) * ncol + c];
             if (q > 0 && k > 0) u[q] = O::mul(u[q], __ldg(&tw[q * k * twstep]));
         }
         Dft<T, R>::run(u, y);
         const int j = (i - k) * R + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) dst[(j + t * p) * ncol + c] = y[t];
+        for (int t = 0; t < R; ++t) dst[pad(j + t * p) * ncol + c] = y[t];
     }
     __syncthreads();
 }
@@ -221,63 +228,64 @@ __device__ __forceinline__ int out_src(int kp, int len, int n) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 1)
+__global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm)
 k_fft_rows(FftPlan fp, RowPassArgs a) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = (C*)smem_raw;
-    C* S2 = S + fp.n;
+    C* S2 = S + padded_len(fp.n);
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     for (int row = blockIdx.x; row < a.nrows; row += gridDim.x) {
         const C* in = (const C*)a.in + (long long)row * a.in_stride;
         if (a.centered_in || a.in_len < n)
-            for (int e = threadIdx.x; e < n; e += blockDim.x) S[e] = Ops<T>::mk(0, 0);
+            for (int e = threadIdx.x; e < padded_len(n); e += blockDim.x) S[e] = Ops<T>::mk(0, 0);
         __syncthreads();
         T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
         const T* dcol = (const T*)a.deconv_col;
         for (int i = threadIdx.x; i < a.in_len; i += blockDim.x) {
             C v = in[i];
             if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
-            S[in_pos(i, a.in_len, n, a.centered_in)] = v;
+            S[pad(in_pos(i, a.in_len, n, a.centered_in))] = v;
         }
         __syncthreads();
         const C* R = fft_smem<T>(S, S2, 1, fp, tw);
         C* out = (C*)a.out + (long long)row * a.out_stride;
         for (int kp = threadIdx.x; kp < a.out_len; kp += blockDim.x)
-            out[kp] = R[out_src(kp, a.out_len, n)];
+            out[kp] = R[pad(out_src(kp, a.out_len, n))];
         __syncthreads();
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 1)
+__global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm)
 k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = (C*)smem_raw;
-    C* S2 = S + fp.n * ncol;
+    C* S2 = S + padded_len(fp.n) * ncol;
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     const int ngroups = (a.ncols + ncol - 1) / ncol;
     for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int c0 = g * ncol;
         if (a.centered_in || a.in_len < n)
-            for (int e = threadIdx.x; e < n * ncol; e += blockDim.x) S[e] = Ops<T>::mk(0, 0);
+            for (int e = threadIdx.x; e < padded_len(n) * ncol; e += blockDim.x)
+                S[e] = Ops<T>::mk(0, 0);
         __syncthreads();
         const C* in = (const C*)a.in;
         for (int e = threadIdx.x; e < a.in_len * ncol; e += blockDim.x) {
             const int i = e / ncol, c = e % ncol;
             C v = Ops<T>::mk(0, 0);
             if (c0 + c < a.ncols) v = in[(long long)i * a.ncols + c0 + c];
-            S[in_pos(i, a.in_len, n, a.centered_in) * ncol + c] = v;
+            S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = v;
         }
         __syncthreads();
         const C* R = fft_smem<T>(S, S2, ncol, fp, tw);
         for (int e = threadIdx.x; e < a.out_len * ncol; e += blockDim.x) {
             const int kp = e / ncol, c = e % ncol;
             if (c0 + c >= a.ncols) continue;
-            C v = R[out_src(kp, a.out_len, n) * ncol + c];
+            C v = R[pad(out_src(kp, a.out_len, n)) * ncol + c];
             if (a.ax) {
                 v = Ops<T>::mul(v, ((const C*)a.ax)[c0 + c]);
                 v = Ops<T>::mul(v, ((const C*)a.ay)[kp]);
@@ -323,14 +331,14 @@ bool fft_supported(int n, int is_double, int* max_cols) {
     const long long smem_cap = 227 * 1024;
     const int esz = is_double ? 16 : 8;
     int c = 8;
-    while (c > 0 && 2LL * n * c * esz > smem_cap) c >>= 1;
+    while (c > 0 && 2LL * padded_len(n) * c * esz > smem_cap) c >>= 1;
     if (max_cols) *max_cols = c;
     return c > 0;
 }
 
 template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st) {
-    const size_t smem = 2 * (size_t)fp.n * sizeof(cx_t<T>);
+    const size_t smem = 2 * (size_t)padded_len(fp.n) * sizeof(cx_t<T>);
     cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int threads = threads_for(fp.n, emax<T>());
     int blocks = a.nrows < 152 * 16 ? a.nrows : 152 * 16;
@@ -342,7 +350,10 @@ template <typename T>
 void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st) {
     int cmax = 0;
     fft_supported(fp.n, sizeof(T) == 8, &cmax);
-    const size_t smem = 2 * (size_t)fp.n * cmax * sizeof(cx_t<T>);
+    // fewer columns per block when that keeps three blocks per SM
+    while (cmax > 1 && 2LL * padded_len(fp.n) * cmax * (long long)sizeof(cx_t<T>) > kFftSmemTarget)
+        cmax >>= 1;
+    const size_t smem = 2 * (size_t)padded_len(fp.n) * cmax * sizeof(cx_t<T>);
     cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int threads = threads_for(fp.n * cmax, emax<T>());
     const int ngroups = (a.ncols + cmax - 1) / cmax;

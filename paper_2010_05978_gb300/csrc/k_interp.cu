@@ -37,17 +37,77 @@ __device__ __forceinline__ T kernel_ft_cheb(T t, const T* a, int n, T inv_tmax) 
     return y * b1 - b2 + a[0];
 }
 
+// Bin of a target: the 16 x 16 block of the FFT grid holding its frequency.
+__device__ __forceinline__ int target_bin(double xi, double eta, const InterpParams& ip) {
+    double tau1 = (xi - ip.xi_c) * ip.K1, tau2 = (eta - ip.eta_c) * ip.K2;
+    if (!(fabs(tau1) <= ip.nfft1) || !(fabs(tau2) <= ip.nfft2)) return 0;
+    int c1 = (int)floor(tau1), c2 = (int)floor(tau2);
+    if (c1 < 0) c1 += ip.nfft1;
+    if (c2 < 0) c2 += ip.nfft2;
+    c1 = min(c1, ip.nfft1 - 1);
+    c2 = min(c2, ip.nfft2 - 1);
+    return (c2 >> 4) * ip.nbin1 + (c1 >> 4);
+}
+
+__global__ void k_target_count(const double* __restrict__ targets, long long M, InterpParams ip,
+                               int* __restrict__ counts) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double2 t = reinterpret_cast<const double2*>(targets)[k];
+        atomicAdd(&counts[target_bin(t.x, t.y, ip)], 1);
+    }
+}
+
+// One block: exclusive scan of the bin counts into cursors; resets counts.
+__global__ void k_target_scan(int nbins, int* counts, int* cursor) {
+    __shared__ long long s[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int per = (nbins + nt - 1) / nt;
+    const int lo = min(t * per, nbins), hi = min(lo + per, nbins);
+    long long sum = 0;
+    for (int i = lo; i < hi; ++i) sum += counts[i];
+    s[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        long long a = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += a;
+        __syncthreads();
+    }
+    long long run = s[t] - sum;
+    for (int i = lo; i < hi; ++i) {
+        const int c = counts[i];
+        cursor[i] = (int)run;
+        run += c;
+        counts[i] = 0;
+    }
+}
+
+__global__ void k_target_scatter(const double* __restrict__ targets, long long M, InterpParams ip,
+                                 int* __restrict__ cursor, int* __restrict__ perm) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double2 t = reinterpret_cast<const double2*>(targets)[k];
+        const int pos = atomicAdd(&cursor[target_bin(t.x, t.y, ip)], 1);
+        if (pos >= 0 && pos < M) perm[pos] = (int)k;
+    }
+}
+
+// Targets are visited in bin order (perm) when a permutation is given, so a
+// warp's targets share grid cells in L1; results go to the caller's order.
 template <typename T, int W>
 __global__ void __launch_bounds__(256)
 k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restrict__ F,
          InterpParams ip, T beta, const double* __restrict__ cheb, int ncheb,
-         cx_t<T>* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz) {
+         cx_t<T>* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz,
+         const int* __restrict__ perm) {
     __shared__ T s_a[kMaxCheb];
     for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (T)cheb[i];
     __syncthreads();
     const T inv_tmax = (T)ip.inv_tmax;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
-         k += (long long)gridDim.x * blockDim.x) {
+    for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < M;
+         kk += (long long)gridDim.x * blockDim.x) {
+        const long long k = perm ? (long long)perm[kk] : kk;
         const double2 t = reinterpret_cast<const double2*>(targets)[k];
         const double xi = t.x, eta = t.y;
         if (!(xi >= ip.box[0] && xi <= ip.box[1] && eta >= ip.box[2] && eta <= ip.box[3]))
@@ -132,10 +192,20 @@ void launch_cheb_samples(int n, double tmax, int w, double beta, const double* g
     k_cheb_samples<<<(n + 63) / 64, 64, 0, st>>>(n, tmax, w, beta, gq_t, gq_w, q, out);
 }
 
+void launch_target_sort(const double* targets, long long M, const InterpParams& ip, int* counts,
+                        int* cursor, int* perm, cudaStream_t st) {
+    if (M <= 0) return;
+    long long nb = (M + 255) / 256;
+    int blocks = (int)(nb < 152LL * 16 ? nb : 152LL * 16);
+    k_target_count<<<blocks, 256, 0, st>>>(targets, M, ip, counts);
+    k_target_scan<<<1, 1024, 0, st>>>(ip.nbin1 * ip.nbin2, counts, cursor);
+    k_target_scatter<<<blocks, 256, 0, st>>>(targets, M, ip, cursor, perm);
+}
+
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
                      const KernelShape& ks, const double* cheb, int ncheb,
-                     void* out, unsigned* status, cudaStream_t st) {
+                     void* out, unsigned* status, const int* perm, cudaStream_t st) {
     if (M <= 0) return;
     long long nb = (M + 255) / 256;
     int blocks = (int)(nb < 152LL * 32 ? nb : 152LL * 32);
@@ -143,7 +213,7 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
 #define FRES_INTERP_CASE(WW)                                                                   \
     case WW:                                                                                   \
         k_interp<T, WW><<<blocks, 256, 0, st>>>(targets, M, F, ip, beta, cheb, ncheb,         \
-                                                (cx_t<T>*)out, status, ks.horner);             \
+                                                (cx_t<T>*)out, status, ks.horner, perm);       \
         break;
     switch (ks.w) {
         FRES_INTERP_CASE(2) FRES_INTERP_CASE(3) FRES_INTERP_CASE(4) FRES_INTERP_CASE(5)
@@ -157,9 +227,9 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
 
 template void launch_interp_w<float>(const double*, long long, const float2*, const InterpParams&,
                                      const KernelShape&, const double*, int, void*, unsigned*,
-                                     cudaStream_t);
+                                     const int*, cudaStream_t);
 template void launch_interp_w<double>(const double*, long long, const double2*,
                                       const InterpParams&, const KernelShape&, const double*, int,
-                                      void*, unsigned*, cudaStream_t);
+                                      void*, unsigned*, const int*, cudaStream_t);
 
 }  // namespace fres
