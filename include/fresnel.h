@@ -187,6 +187,27 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info);
  */
 fresnel_status fresnel_get_nodes(fresnel_plan_t plan, double* d_x, double* d_y, double* d_w);
 
+/* ---------------------------------------------------------------- spreading primitive */
+/*
+ * The spreading stage of the NUFFT on its own (the first step of the type-1
+ * and type-3 transforms behind Secs. 3.2-3.3): for N points with periodic
+ * grid coordinates (g1_j, g2_j) (FP64, grid units, any real value; taken
+ * modulo nf1, nf2) and FP32 complex strengths c_j,
+ *   grid[l2 * nf1 + l1] = sum_j c_j psi(l1 - g1_j) psi(l2 - g2_j),
+ *   psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)) for |u| < w/2, else 0,
+ * with l - g taken periodically.  All pointers are DEVICE memory:
+ * d_g1, d_g2 (N doubles each), d_c (N complex64 = interleaved float pairs),
+ * d_grid (nf1 * nf2 complex64, overwritten).  2 <= w <= 16, beta > 0,
+ * nf1 and nf2 multiples of 32 and >= 64.  The kernel values are evaluated
+ * with exp/sqrt (not the plan's polynomial form).  Scratch is allocated
+ * stream-ordered (cudaMallocAsync) on cuda_stream and released before the
+ * call returns; the call synchronises the stream.  Returns FRESNEL_ERR_DEVICE
+ * if a coordinate is not finite (that point is dropped).
+ */
+fresnel_status fresnel_spread(const double* d_g1, const double* d_g2, const void* d_c,
+                              long long N, int nf1, int nf2, int w, double beta,
+                              void* d_grid, void* cuda_stream);
+
 /*
  * Per-stage device time of the last fresnel_eval, in milliseconds, measured
  * with CUDA events on the plan's stream when timing was enabled by

@@ -15,7 +15,8 @@ OUT = os.path.join(HERE, "libfresnel.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]
-SOURCES = ["api.cu", "k_nodes.cu", "k_spread_f32.cu", "k_spread_f64.cu", "k_fft.cu", "k_interp.cu"]
+SOURCES = ["api.cu", "k_nodes.cu", "k_spread_f32.cu", "k_spread_f64.cu", "k_fft.cu", "k_interp.cu",
+           "spread_api.cu"]
 
 
 def _nvcc():

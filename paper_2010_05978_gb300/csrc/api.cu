@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 using namespace fres;
@@ -299,11 +300,14 @@ template <typename T>
 fresnel_status run_nodes(Plan* p, double* dx, double* dy, double* dw) {
     for (const FamilyDev& f : p->fams) {
         if (f.kind != FRESNEL_FAMILY_NODES) {
-            launch_boundary(f, p->st);
+            launch_boundary(f, p->cp, p->st);
             p->launches++;
         }
-        launch_nodes_count<T>(f, p->cp, (NodeRec<T>*)p->rec, p->counts, dx, dy, dw, p->status,
-                              p->st);
+        if (f.spoke && !dx)   // FP32 fast mode: double-float spoke form, no FP64 per node
+            launch_nodes_count_df(f, p->cp, (NodeRec<float>*)p->rec, p->counts, p->status, p->st);
+        else
+            launch_nodes_count<T>(f, p->cp, (NodeRec<T>*)p->rec, p->counts, dx, dy, dw,
+                                  p->status, p->st);
         p->launches++;
     }
     return FRESNEL_OK;
@@ -487,7 +491,23 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
             FRES_TRY(dalloc(p, (void**)&f.bx, sizeof(double) * nb));
             FRES_TRY(dalloc(p, (void**)&f.by, sizeof(double) * nb));
             FRES_TRY(dalloc(p, (void**)&f.bc, sizeof(double) * nb));
-            launch_boundary(f, p->st);
+            if (!dbl) {   // double-float radial rule for the FP32 spoke form
+                std::vector<float> adf(2 * f.m), awf(f.m);
+                for (int l = 0; l < f.m; ++l) {
+                    dflt s = df_host(a[l]);
+                    adf[2 * l] = s.hi;
+                    adf[2 * l + 1] = s.lo;
+                    awf[l] = (float)w[l];
+                }
+                FRES_TRY(dalloc(p, (void**)&f.adf, sizeof(float) * 2 * f.m));
+                FRES_TRY(dalloc(p, (void**)&f.awf, sizeof(float) * f.m));
+                FRES_CK(cudaMemcpyAsync(f.adf, adf.data(), sizeof(float) * 2 * f.m,
+                                        cudaMemcpyHostToDevice, p->st));
+                FRES_CK(cudaMemcpyAsync(f.awf, awf.data(), sizeof(float) * f.m,
+                                        cudaMemcpyHostToDevice, p->st));
+                FRES_CK(cudaStreamSynchronize(p->st));
+            }
+            launch_boundary(f, p->cp, p->st);
             // node bounding box (type 3 sizing): nodes lie on segments from the
             // centre to the boundary nodes, so centre + boundary bounds them.
             std::vector<double> bx(nb), by(nb);
@@ -572,6 +592,21 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
         ip.nfft2 = p->nfft2;
         ip.nbin1 = (p->nfft1 + 15) / 16;
         ip.nbin2 = (p->nfft2 + 15) / 16;
+        auto put = [](float* d, double v) {
+            dflt s = df_host(v);
+            d[0] = s.hi;
+            d[1] = s.lo;
+        };
+        put(ip.dK1, ip.K1);
+        put(ip.dK2, ip.K2);
+        put(ip.dG1, -xic * ip.K1 - 0.5 * w);
+        put(ip.dG2, -etac * ip.K2 - 0.5 * w);
+        put(ip.dkq, ip.kq);
+        put(ip.dp1, ip.p1);
+        put(ip.dp2, ip.p2);
+        for (int i = 0; i < 4; ++i) ip.boxf[i] = (float)b[i];
+        ip.shK1 = (float)(ip.sh1 / ip.K1);
+        ip.shK2 = (float)(ip.sh2 / ip.K2);
         ip.occulter = p->output == FRESNEL_OCCULTER;
     }
     if (!fft_supported(p->nfft1, dbl, &cmax) || !fft_supported(p->nfft2, dbl, &cmax))
@@ -588,6 +623,32 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
     p->cp.ntx = p->ntx;
     p->cp.nty = p->nty;
     p->chunk_cap = dbl ? 256 : 512;
+
+    // ---------------- FP32 fast mode: spoke coefficients and family constants
+    if (!dbl) {
+        const ChirpParams& cp = p->cp;
+        for (FamilyDev& f : p->fams) {
+            if (f.kind == FRESNEL_FAMILY_NODES) continue;
+            FRES_TRY(dalloc(p, (void**)&f.spoke, sizeof(float) * 8 * f.n_bdry));
+            FRES_TRY(dalloc(p, (void**)&f.bcf, sizeof(float) * f.n_bdry));
+            const double A0 = cp.kq * (f.cx * f.cx + f.cy * f.cy) - cp.a1 * f.cx - cp.a2 * f.cy + cp.a0;
+            double G0x, G0y;
+            if (!cp.type3) {
+                G0x = (double)cp.nf1 * cp.u1 * f.cx - 0.5 * w;
+                G0y = (double)cp.nf2 * cp.u2 * f.cy - 0.5 * w;
+            } else {
+                G0x = (f.cx - cp.C1) * cp.inv_h1 + 0.5 * cp.nf1 - 0.5 * w;
+                G0y = (f.cy - cp.C2) * cp.inv_h2 + 0.5 * cp.nf2 - 0.5 * w;
+            }
+            const dflt a0 = df_host(A0), gx = df_host(G0x), gy = df_host(G0y);
+            f.A0[0] = a0.hi;
+            f.A0[1] = a0.lo;
+            f.G0x[0] = gx.hi;
+            f.G0x[1] = gx.lo;
+            f.G0y[0] = gy.hi;
+            f.G0y[1] = gy.lo;
+        }
+    }
 
     // ---------------- node pass once: exact record / chunk / slot counts
     FRES_TRY(dalloc(p, (void**)&p->status, sizeof(unsigned)));

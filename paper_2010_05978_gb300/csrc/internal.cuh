@@ -76,6 +76,14 @@ struct FamilyDev {
     double* gl_p_w;
     double* gl_m_a;        // m-point Gauss-Legendre nodes alpha_l on (0,1)
     double* gl_m_aw;       // alpha_l * wtilde_l
+    // FP32 fast mode (double-float "spoke" form of the dilation rule): with
+    // x = c + alpha b_i the chirp phase is A0 + alpha (A1_i + alpha A2_i) and
+    // the grid coordinate (minus w/2) is G0 + alpha G1_i per dimension.
+    float* spoke;          // per boundary node: A1, A2, G1x, G1y as (hi, lo) pairs
+    float* bcf;            // bc as FP32 (weights need only FP32)
+    float* adf;            // alpha_l as (hi, lo)
+    float* awf;            // alpha_l wtilde_l as FP32
+    float A0[2], G0x[2], G0y[2];
 };
 
 // Everything a node kernel needs to turn (x, y, w) into a record.
@@ -140,11 +148,18 @@ __device__ __forceinline__ R kernel_ft(R t, int w, R beta, const R* gq_t, const 
 // ------------------------------------------------------------------ launchers
 // k_nodes.cu
 void launch_gauss_legendre(int n, double* t01, double* w01, cudaStream_t st);
-void launch_boundary(const FamilyDev& f, cudaStream_t st);
+void launch_boundary(const FamilyDev& f, const ChirpParams& cp, cudaStream_t st);
+// FP32 fast mode, dilation families: double-float spoke form (no FP64 per node)
+void launch_nodes_count_df(const FamilyDev& f, const ChirpParams& cp, NodeRec<float>* rec,
+                           int* counts, unsigned* status, cudaStream_t st);
 template <typename T>
 void launch_nodes_count(const FamilyDev& f, const ChirpParams& cp, NodeRec<T>* rec,
                         int* counts, double* dx, double* dy, double* dw,
                         unsigned* status, cudaStream_t st);
+// records + tile counts for points given by periodic grid coordinates (fresnel_spread)
+void launch_records_from_coords(long long n, const double* g1, const double* g2, const float2* c,
+                                const ChirpParams& cp, NodeRec<float>* rec, int* counts,
+                                unsigned* status, cudaStream_t st);
 // n_meta[0] = chunks, n_meta[1] = split tiles (listed in split_tiles)
 void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_meta,
                         int* split_tiles, int chunk_cap, int max_chunks, int max_split,
@@ -209,6 +224,11 @@ struct InterpParams {
     double p1, p2;           // post-phase: -2 pi C / lz
     double inv_lz;
     double inv_tmax;         // 1 / t_max of the Chebyshev series of psihat
+    // FP32 fast mode, double-float (hi, lo) constants:
+    //   g = xi K + G  (grid coordinate minus w/2), phase = xi (kq xi + p1) + eta (kq eta + p2)
+    float dK1[2], dK2[2], dG1[2], dG2[2], dkq[2], dp1[2], dp2[2];
+    float boxf[4];
+    float shK1, shK2;        // (g + w/2) * shK = argument of psihat
     int nbin1, nbin2;        // 16 x 16 target bins per dimension of the FFT grid
     double box[4];
     int nfft1, nfft2;

@@ -6,6 +6,7 @@
 // centring together with the target chirp and 1/(i lz):
 //   u_k = 1/(i lz) exp(i pi |xi_k|^2 / lz - 2 pi i xi_k.C / lz) v'_k,
 // optionally u^oc = 1 - u^ap (eq. bab).  Phases in FP64 with reduction.
+#include "dfloat.cuh"
 #include "spread.cuh"
 
 namespace fres {
@@ -109,21 +110,54 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
          kk += (long long)gridDim.x * blockDim.x) {
         const long long k = perm ? (long long)perm[kk] : kk;
         const double2 t = reinterpret_cast<const double2*>(targets)[k];
-        const double xi = t.x, eta = t.y;
-        if (!(xi >= ip.box[0] && xi <= ip.box[1] && eta >= ip.box[2] && eta <= ip.box[3]))
-            atomicOr(status, kStatusTargetOutside);
-        const double d1 = xi - ip.xi_c, d2 = eta - ip.eta_c;
-        double tau1 = d1 * ip.K1, tau2 = d2 * ip.K2;
-        if (!isfinite(tau1) || !isfinite(tau2) || fabs(tau1) > ip.nfft1 || fabs(tau2) > ip.nfft2) {
-            atomicOr(status, kStatusNonFinite);
-            tau1 = tau2 = 0.0;
+        int s1, s2;
+        T f1, f2, targ1, targ2, phr;
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32 fast mode: double-float coordinates and phase (no FP64 arithmetic)
+            const dflt xi = df_from_double(t.x), eta = df_from_double(t.y);
+            if (!(xi.hi >= ip.boxf[0] && xi.hi <= ip.boxf[1] && eta.hi >= ip.boxf[2] &&
+                  eta.hi <= ip.boxf[3]))
+                atomicOr(status, kStatusTargetOutside);
+            dflt g1 = df_add(df_mul(xi, dflt{ip.dK1[0], ip.dK1[1]}), dflt{ip.dG1[0], ip.dG1[1]});
+            dflt g2 = df_add(df_mul(eta, dflt{ip.dK2[0], ip.dK2[1]}), dflt{ip.dG2[0], ip.dG2[1]});
+            if (!(fabsf(g1.hi) <= (float)ip.nfft1) || !(fabsf(g2.hi) <= (float)ip.nfft2)) {
+                atomicOr(status, kStatusNonFinite);
+                g1 = g2 = dflt{0.0f, 0.0f};
+            }
+            int c1, c2;
+            df_floor_split(g1, &c1, &f1);
+            df_floor_split(g2, &c2, &f2);
+            s1 = c1 + 1;
+            s2 = c2 + 1;
+            targ1 = (g1.hi + 0.5f * W) * ip.shK1;
+            targ2 = (g2.hi + 0.5f * W) * ip.shK2;
+            const dflt kq = {ip.dkq[0], ip.dkq[1]};
+            const dflt q1 = df_mul(xi, df_add(df_mul(kq, xi), dflt{ip.dp1[0], ip.dp1[1]}));
+            const dflt q2 = df_mul(eta, df_add(df_mul(kq, eta), dflt{ip.dp2[0], ip.dp2[1]}));
+            phr = df_reduce_2pi(df_add(q1, q2));
+        } else {
+            const double xi = t.x, eta = t.y;
+            if (!(xi >= ip.box[0] && xi <= ip.box[1] && eta >= ip.box[2] && eta <= ip.box[3]))
+                atomicOr(status, kStatusTargetOutside);
+            const double d1 = xi - ip.xi_c, d2 = eta - ip.eta_c;
+            double tau1 = d1 * ip.K1, tau2 = d2 * ip.K2;
+            if (!isfinite(tau1) || !isfinite(tau2) || fabs(tau1) > ip.nfft1 ||
+                fabs(tau2) > ip.nfft2) {
+                atomicOr(status, kStatusNonFinite);
+                tau1 = tau2 = 0.0;
+            }
+            const double gs1 = tau1 - 0.5 * W, gs2 = tau2 - 0.5 * W;
+            const double fl1 = floor(gs1), fl2 = floor(gs2);
+            f1 = (T)(gs1 - fl1);
+            f2 = (T)(gs2 - fl2);
+            s1 = (int)fl1 + 1;
+            s2 = (int)fl2 + 1;
+            targ1 = (T)(d1 * ip.sh1);
+            targ2 = (T)(d2 * ip.sh2);
+            phr = (T)reduce_phase(ip.kq * (xi * xi + eta * eta) + ip.p1 * xi + ip.p2 * eta);
         }
-        const double gs1 = tau1 - 0.5 * W, gs2 = tau2 - 0.5 * W;
-        const double fl1 = floor(gs1), fl2 = floor(gs2);
-        const T f1 = (T)(gs1 - fl1), f2 = (T)(gs2 - fl2);
-        int s1 = (int)fl1 + 1, s2 = (int)fl2 + 1;
-        if (s1 < 0) s1 += ip.nfft1;
-        if (s2 < 0) s2 += ip.nfft2;
+        s1 = ((s1 % ip.nfft1) + ip.nfft1) % ip.nfft1;
+        s2 = ((s2 % ip.nfft2) + ip.nfft2) % ip.nfft2;
         T kx[W], ky[W];
         kernel_values<T, W>(f1, beta, hz, kx);
         kernel_values<T, W>(f2, beta, hz, ky);
@@ -145,20 +179,13 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
             gr += ky[b] * rr;
             gi += ky[b] * ri;
         }
-        const T dec = kernel_ft_cheb<T>((T)(d1 * ip.sh1), s_a, ncheb, inv_tmax) *
-                      kernel_ft_cheb<T>((T)(d2 * ip.sh2), s_a, ncheb, inv_tmax);
-        const double ph = reduce_phase(ip.kq * (xi * xi + eta * eta) + ip.p1 * xi + ip.p2 * eta);
+        const T dec = kernel_ft_cheb<T>(targ1, s_a, ncheb, inv_tmax) *
+                      kernel_ft_cheb<T>(targ2, s_a, ncheb, inv_tmax);
         T sn, cs;
-        if (sizeof(T) == 8) {
-            double s_, c_;
-            sincos(ph, &s_, &c_);
-            sn = (T)s_;
-            cs = (T)c_;
+        if constexpr (std::is_same<T, float>::value) {
+            sincosf(phr, &sn, &cs);
         } else {
-            float s_, c_;
-            sincosf((float)ph, &s_, &c_);
-            sn = (T)s_;
-            cs = (T)c_;
+            sincos(phr, &sn, &cs);
         }
         // (cs + i sn) (gr + i gi) / dec * (-i / lz)
         const T sc = (T)ip.inv_lz / dec;

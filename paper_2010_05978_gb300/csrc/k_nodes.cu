@@ -3,6 +3,7 @@
 // counting sort of nodes into spreading tiles; plus the small plan-time tables
 // (FFT twiddles, deconvolution and output-chirp factors).
 // Paper: arXiv:2010.05978, Secs. 3.2-3.3 and 4.1 (eqs. split, aqnod, aqwei, vliq1).
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace fres {
@@ -88,7 +89,32 @@ __global__ void k_gauss_legendre(int n, double* t01, double* w01) {
 // r = r0 + sum (a_k cos kt + b_k sin kt); panel q of n_panels equal t-panels
 // carries p Gauss-Legendre nodes: W = what X'(t), V = what Y'(t) (eq. vliq1).
 // Stored relative to the centre: bx = X - cx, by = Y - cy, bc = bx V - by W.
-__global__ void k_boundary_fourier(FamilyDev f) {
+__device__ __forceinline__ void split_store(float* dst, double v) {
+    const float hi = (float)v;
+    dst[0] = hi;
+    dst[1] = (float)(v - (double)hi);
+}
+
+// Spoke coefficients of boundary node i for the FP32 fast mode (see
+// k_nodes_count_df): A1 = 2 kq c.b - a.b, A2 = kq |b|^2, and the per-unit-alpha
+// grid-coordinate slopes G1.  Computed once per boundary node in FP64.
+__device__ __forceinline__ void store_spoke(const FamilyDev& f, const ChirpParams& cp, long long i,
+                                            double bx, double by, double bc) {
+    if (!f.spoke) return;
+    float* s = f.spoke + 8 * i;
+    split_store(s + 0, 2.0 * cp.kq * (f.cx * bx + f.cy * by) - cp.a1 * bx - cp.a2 * by);
+    split_store(s + 2, cp.kq * (bx * bx + by * by));
+    if (!cp.type3) {
+        split_store(s + 4, (double)cp.nf1 * cp.u1 * bx);
+        split_store(s + 6, (double)cp.nf2 * cp.u2 * by);
+    } else {
+        split_store(s + 4, bx * cp.inv_h1);
+        split_store(s + 6, by * cp.inv_h2);
+    }
+    f.bcf[i] = (float)bc;
+}
+
+__global__ void k_boundary_fourier(FamilyDev f, ChirpParams cp) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= f.n_bdry) return;
     int q = (int)(i / f.p), s = (int)(i % f.p);
@@ -113,10 +139,11 @@ __global__ void k_boundary_fourier(FamilyDev f) {
     f.bx[i] = X;
     f.by[i] = Y;
     f.bc[i] = X * V - Y * W;
+    store_spoke(f, cp, i, X, Y, X * V - Y * W);
 }
 
 // Explicit vector line rule: params = [X.., Y.., W.., V..].
-__global__ void k_boundary_line(FamilyDev f) {
+__global__ void k_boundary_line(FamilyDev f, ChirpParams cp) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long n = f.n_bdry;
     if (i >= n) return;
@@ -125,6 +152,68 @@ __global__ void k_boundary_line(FamilyDev f) {
     f.bx[i] = X;
     f.by[i] = Y;
     f.bc[i] = X * V - Y * W;
+    store_spoke(f, cp, i, X, Y, X * V - Y * W);
+}
+
+// ------------------------------------------------------------------ FP32 fast mode nodes
+// Double-float form of the dilation rule for one spoke (boundary node i):
+// with x = c + alpha b, the chirp phase kq |x|^2 - a.x + a0 equals
+// A0 + alpha (A1 + alpha A2) and the grid coordinate (minus w/2) equals
+// G0 + alpha G1, so a node costs a few double-float operations and no FP64.
+template <typename T>
+__global__ void k_nodes_count_df(FamilyDev f, ChirpParams cp, NodeRec<float>* rec, int* counts,
+                                 unsigned* status) {
+    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int key[4] = {-1, -1, -1, -1};
+    if (j < f.n_nodes) {
+        const long long i = j / f.m;
+        const int l = (int)(j - i * f.m);
+        const float4 sA = reinterpret_cast<const float4*>(f.spoke)[2 * i];
+        const float4 sG = reinterpret_cast<const float4*>(f.spoke)[2 * i + 1];
+        const float2 a2 = reinterpret_cast<const float2*>(f.adf)[l];
+        const dflt al = {a2.x, a2.y};
+        dflt ph = df_mul(al, dflt{sA.z, sA.w});
+        ph = df_add(ph, dflt{sA.x, sA.y});
+        ph = df_mul(al, ph);
+        ph = df_add(ph, dflt{f.A0[0], f.A0[1]});
+        const float phr = df_reduce_2pi(ph);
+        const float w = f.awf[l] * f.bcf[i];
+        float sn, cs;
+        sincosf(phr, &sn, &cs);
+        NodeRec<float> r;
+        r.cre = w * cs;
+        r.cim = w * sn;
+        dflt v1 = df_add(df_mul(al, dflt{sG.x, sG.y}), dflt{f.G0x[0], f.G0x[1]});
+        dflt v2 = df_add(df_mul(al, dflt{sG.z, sG.w}), dflt{f.G0y[0], f.G0y[1]});
+        if (!cp.type3) {   // fold into [0, nf): the type-1 grid is periodic (Sec. 3.3)
+            const float q1 = floorf(v1.hi / (float)cp.nf1), q2 = floorf(v2.hi / (float)cp.nf2);
+            v1 = df_add(v1, dflt{-q1 * (float)cp.nf1, 0.0f});
+            v2 = df_add(v2, dflt{-q2 * (float)cp.nf2, 0.0f});
+        }
+        int c1, c2;
+        df_floor_split(v1, &c1, &r.f1);
+        df_floor_split(v2, &c2, &r.f2);
+        int s1 = c1 + 1, s2 = c2 + 1;
+        if (!(v1.hi == v1.hi) || !(v2.hi == v2.hi)) {
+            atomicOr(status, kStatusNonFinite);
+            s1 = s2 = 0;
+            r.cre = r.cim = 0.0f;
+        }
+        if (!cp.type3) {
+            s1 = ((s1 % cp.nf1) + cp.nf1) % cp.nf1;
+            s2 = ((s2 % cp.nf2) + cp.nf2) % cp.nf2;
+        } else if (s1 < 0 || s2 < 0 || s1 + cp.w > cp.nf1 || s2 + cp.w > cp.nf2) {
+            atomicOr(status, kStatusNodeOutside);
+            s1 = min(max(s1, 0), cp.nf1 - cp.w);
+            s2 = min(max(s2, 0), cp.nf2 - cp.w);
+        }
+        r.s1 = s1;
+        r.s2 = s2;
+        rec[f.offset + j] = r;
+        node_tiles(s1, s2, cp, key);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) agg_count(key[k], counts);
 }
 
 // ------------------------------------------------------------------ nodes + chirp + count
@@ -215,6 +304,40 @@ __global__ void k_nodes_count(FamilyDev f, ChirpParams cp, NodeRec<T>* rec, int*
     for (int k = 0; k < 4; ++k) agg_count(key[k], counts);
 }
 
+// Records for the standalone spreader (fresnel_spread): points given directly
+// by periodic grid coordinates (g1, g2) and FP32 strengths.
+__global__ void k_records_from_coords(long long n, const double* __restrict__ g1,
+                                      const double* __restrict__ g2,
+                                      const float2* __restrict__ c, ChirpParams cp,
+                                      NodeRec<float>* __restrict__ rec, int* __restrict__ counts,
+                                      unsigned* __restrict__ status) {
+    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int key[4] = {-1, -1, -1, -1};
+    if (j < n) {
+        double a = g1[j] - 0.5 * cp.w, b = g2[j] - 0.5 * cp.w;
+        NodeRec<float> r;
+        float2 cj = c[j];
+        if (!isfinite(a) || !isfinite(b)) {
+            atomicOr(status, kStatusNonFinite);
+            a = b = 0.0;
+            cj = make_float2(0.0f, 0.0f);
+        }
+        a -= cp.nf1 * floor(a / cp.nf1);
+        b -= cp.nf2 * floor(b / cp.nf2);
+        const double fa = floor(a), fb = floor(b);
+        r.f1 = (float)(a - fa);
+        r.f2 = (float)(b - fb);
+        r.s1 = (((int)fa + 1) % cp.nf1 + cp.nf1) % cp.nf1;
+        r.s2 = (((int)fb + 1) % cp.nf2 + cp.nf2) % cp.nf2;
+        r.cre = cj.x;
+        r.cim = cj.y;
+        rec[j] = r;
+        node_tiles(r.s1, r.s2, cp, key);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) agg_count(key[k], counts);
+}
+
 // Scatter each record to every tile its support touches (positions reserved
 // with warp-aggregated atomics on per-tile cursors set by the scan).
 template <typename T>
@@ -243,15 +366,30 @@ __global__ void k_scatter(long long n, ChirpParams cp, const NodeRec<T>* rec, in
 // split_tiles; every other tile (empty ones too: they write zeros, so the grid
 // needs no separate clearing) is one chunk.  Chunks of split tiles are placed
 // first, the unsplit tiles after them.  Resets counts for the next pass.
-__global__ void k_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_meta,
-                              int* split_tiles, int chunk_cap, int max_chunks, int max_split) {
+// When the counts fit in shared memory (staged = 1) they are first copied in
+// one coalesced burst and the global copy is cleared at once, so the block
+// pays one memory round trip instead of one per tile it owns.
+__global__ void k_scan_chunks(int ntiles, int* __restrict__ counts, int* __restrict__ cursor,
+                              Chunk* __restrict__ chunks, int* __restrict__ n_meta,
+                              int* __restrict__ split_tiles, int chunk_cap, int max_chunks,
+                              int max_split, int staged) {
     __shared__ long long s_rec[1024], s_sc[1024], s_ns[1024], s_st[1024];
+    extern __shared__ int s_counts[];
     int t = threadIdx.x, nt = blockDim.x;
+    const int* cnt = counts;
+    if (staged) {
+        for (int i = t; i < ntiles; i += nt) {
+            s_counts[i] = counts[i];
+            counts[i] = 0;
+        }
+        __syncthreads();
+        cnt = s_counts;
+    }
     int per = (ntiles + nt - 1) / nt;
     int lo = min(t * per, ntiles), hi = min(lo + per, ntiles);
     long long rsum = 0, sc = 0, ns = 0, stl = 0;
     for (int i = lo; i < hi; ++i) {
-        int c = counts[i];
+        int c = cnt[i];
         rsum += c;
         if (c > chunk_cap) {
             sc += (c + chunk_cap - 1) / chunk_cap;
@@ -275,7 +413,7 @@ __global__ void k_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunk
     const long long total_split_chunks = s_sc[nt - 1];
     long long roff = s_rec[t] - rsum, scoff = s_sc[t] - sc, nsoff = s_ns[t] - ns, stoff = s_st[t] - stl;
     for (int i = lo; i < hi; ++i) {
-        int c = counts[i];
+        int c = cnt[i];
         cursor[i] = (int)roff;
         if (c > chunk_cap) {
             int nch = (c + chunk_cap - 1) / chunk_cap;
@@ -306,7 +444,7 @@ __global__ void k_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunk
             ++nsoff;
         }
         roff += c;
-        counts[i] = 0;
+        if (!staged) counts[i] = 0;
     }
     if (t == nt - 1) {
         n_meta[0] = (int)min(total_split_chunks + s_ns[t], (long long)max_chunks);
@@ -367,11 +505,17 @@ void launch_gauss_legendre(int n, double* t01, double* w01, cudaStream_t st) {
     k_gauss_legendre<<<nblk(n, 128), 128, 0, st>>>(n, t01, w01);
 }
 
-void launch_boundary(const FamilyDev& f, cudaStream_t st) {
+void launch_boundary(const FamilyDev& f, const ChirpParams& cp, cudaStream_t st) {
     if (f.kind == FRESNEL_FAMILY_FOURIER)
-        k_boundary_fourier<<<nblk(f.n_bdry, 256), 256, 0, st>>>(f);
+        k_boundary_fourier<<<nblk(f.n_bdry, 128), 128, 0, st>>>(f, cp);
     else if (f.kind == FRESNEL_FAMILY_LINE_RULE)
-        k_boundary_line<<<nblk(f.n_bdry, 256), 256, 0, st>>>(f);
+        k_boundary_line<<<nblk(f.n_bdry, 128), 128, 0, st>>>(f, cp);
+}
+
+void launch_nodes_count_df(const FamilyDev& f, const ChirpParams& cp, NodeRec<float>* rec,
+                           int* counts, unsigned* status, cudaStream_t st) {
+    if (f.n_nodes <= 0) return;
+    k_nodes_count_df<float><<<nblk(f.n_nodes, 256), 256, 0, st>>>(f, cp, rec, counts, status);
 }
 
 template <typename T>
@@ -396,11 +540,25 @@ template void launch_scatter<float>(long long, const ChirpParams&, const NodeRec
 template void launch_scatter<double>(long long, const ChirpParams&, const NodeRec<double>*, int*,
                                      NodeRec<double>*, long long, unsigned*, cudaStream_t);
 
+void launch_records_from_coords(long long n, const double* g1, const double* g2, const float2* c,
+                                const ChirpParams& cp, NodeRec<float>* rec, int* counts,
+                                unsigned* status, cudaStream_t st) {
+    if (n <= 0) return;
+    k_records_from_coords<<<nblk(n, 256), 256, 0, st>>>(n, g1, g2, c, cp, rec, counts, status);
+}
+
 void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int* n_meta,
                         int* split_tiles, int chunk_cap, int max_chunks, int max_split,
                         cudaStream_t st) {
-    k_scan_chunks<<<1, 1024, 0, st>>>(ntiles, counts, cursor, chunks, n_meta, split_tiles,
-                                      chunk_cap, max_chunks, max_split);
+    // counts staged in shared memory when they fit next to the static arrays
+    const size_t dyn = sizeof(int) * (size_t)ntiles;
+    const int staged = dyn <= 160 * 1024 ? 1 : 0;
+    if (staged)
+        cudaFuncSetAttribute(k_scan_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn);
+    k_scan_chunks<<<1, 1024, staged ? dyn : 0, st>>>(ntiles, counts, cursor, chunks, n_meta,
+                                                     split_tiles, chunk_cap, max_chunks,
+                                                     max_split, staged);
 }
 
 void launch_twiddles(int n, void* table, int is_double, cudaStream_t st) {

@@ -135,6 +135,7 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
                     v.y = r.cim * kyv[a];
                     sm.cky[warp][lane][a] = v;
                 }
+                sm.kx[warp][lane][W] = (T)0;   // pad: odd widths end on half a pair
             }
             __syncwarp();
             // lane -> support column a = lane % W and rows b0, b0 + RPW, ...

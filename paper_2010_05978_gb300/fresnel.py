@@ -58,7 +58,7 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_eval", "fresnel_eval_host",
            "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
-           "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times"]
+           "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread"]
 
 _lib = None
 
@@ -97,6 +97,9 @@ def load_library(path=LIB_PATH):
     lib.fresnel_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.c_int]
     lib.fresnel_stage_times.restype = ctypes.c_int
+    lib.fresnel_spread.argtypes = [vp, vp, vp, ll, ctypes.c_int, ctypes.c_int, ctypes.c_int, d,
+                                   vp, vp]
+    lib.fresnel_spread.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -260,3 +263,29 @@ class Plan:
 # C-ABI names, for callers that want the flat interface.
 def fresnel_last_error():
     return load_library().fresnel_last_error().decode()
+
+
+def _spread_args(g1, g2, c, nf1, nf2, out):
+    import torch
+    for t in (g1, g2):
+        assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    assert c.dtype == torch.complex64 and c.is_cuda and c.is_contiguous()
+    n = g1.numel()
+    assert g2.numel() == n and c.numel() == n
+    if out is None:
+        out = torch.empty((nf2, nf1), dtype=torch.complex64, device=g1.device)
+    ptr = lambda t: t.data_ptr() if t.numel() > 0 else None
+    return n, ptr(g1), ptr(g2), ptr(c), out
+
+
+def fresnel_spread(g1, g2, c, nf1, nf2, w, beta, out=None, stream=None):
+    """Spread N points (periodic grid coordinates g1, g2: float64 CUDA tensors;
+    strengths c: complex64) onto an nf2 x nf1 complex64 grid with the
+    exponential-of-semicircle kernel of width w and shape beta."""
+    import torch
+    n, p1, p2, pc, out = _spread_args(g1, g2, c, nf1, nf2, out)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load_library().fresnel_spread(p1, p2, pc, n, int(nf1), int(nf2), int(w), float(beta),
+                                         out.data_ptr(), ctypes.c_void_p(stream.cuda_stream)))
+    return out
