@@ -209,6 +209,30 @@ fresnel_status fresnel_spread(const double* d_g1, const double* d_g2, const void
                               void* d_grid, void* cuda_stream);
 
 /*
+ * fresnel_spread for callers that cannot allocate device memory: code that
+ * may not call cudaMalloc (or any allocating routine) because another
+ * framework owns the device memory pool or is capturing a CUDA graph, and
+ * embedded or real-time callers that forbid allocation after start-up.  The
+ * paper has no counterpart: this is a property of the library, not of the
+ * method.  Same arguments, result and errors as fresnel_spread, with limits:
+ * N <= FRESNEL_SPREAD_NOALLOC_MAX_POINTS and nf1 * nf2 <=
+ * FRESNEL_SPREAD_NOALLOC_MAX_GRID (else FRESNEL_ERR_UNSUPPORTED, nothing
+ * launched).  The scratch is a static device array of
+ * FRESNEL_SPREAD_NOALLOC_SCRATCH_BYTES that every device which loads the
+ * library holds until the process exits; the call allocates nothing.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls on a device share
+ * the array, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them.  Synchronises cuda_stream.
+ */
+#define FRESNEL_SPREAD_NOALLOC_MAX_POINTS 65536
+#define FRESNEL_SPREAD_NOALLOC_MAX_GRID (2048 * 2048)
+#define FRESNEL_SPREAD_NOALLOC_SCRATCH_BYTES (8 * 1024 * 1024)
+fresnel_status fresnel_spread_noalloc(const double* d_g1, const double* d_g2, const void* d_c,
+                                      long long N, int nf1, int nf2, int w, double beta,
+                                      void* d_grid, void* cuda_stream);
+
+/*
  * Per-stage device time of the last fresnel_eval, in milliseconds, measured
  * with CUDA events on the plan's stream when timing was enabled by
  * fresnel_set_timing(plan, 1).  stage_ms receives up to max_stages values;

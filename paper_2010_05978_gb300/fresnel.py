@@ -58,7 +58,8 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_eval", "fresnel_eval_host",
            "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
-           "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread"]
+           "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread",
+           "fresnel_spread_noalloc"]
 
 _lib = None
 
@@ -100,6 +101,8 @@ def load_library(path=LIB_PATH):
     lib.fresnel_spread.argtypes = [vp, vp, vp, ll, ctypes.c_int, ctypes.c_int, ctypes.c_int, d,
                                    vp, vp]
     lib.fresnel_spread.restype = ctypes.c_int
+    lib.fresnel_spread_noalloc.argtypes = lib.fresnel_spread.argtypes
+    lib.fresnel_spread_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -288,4 +291,18 @@ def fresnel_spread(g1, g2, c, nf1, nf2, w, beta, out=None, stream=None):
         stream = torch.cuda.current_stream()
     _check(load_library().fresnel_spread(p1, p2, pc, n, int(nf1), int(nf2), int(w), float(beta),
                                          out.data_ptr(), ctypes.c_void_p(stream.cuda_stream)))
+    return out
+
+
+def fresnel_spread_noalloc(g1, g2, c, nf1, nf2, w, beta, out, stream=None):
+    """fresnel_spread without any device allocation (for callers that cannot
+    allocate): scratch is the library's static device array, so the caller
+    must pass the output grid and keep calls on one device from overlapping."""
+    import torch
+    n, p1, p2, pc, out = _spread_args(g1, g2, c, nf1, nf2, out)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load_library().fresnel_spread_noalloc(p1, p2, pc, n, int(nf1), int(nf2), int(w),
+                                                 float(beta), out.data_ptr(),
+                                                 ctypes.c_void_p(stream.cuda_stream)))
     return out
