@@ -599,8 +599,9 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
         };
         put(ip.dK1, ip.K1);
         put(ip.dK2, ip.K2);
-        put(ip.dG1, -xic * ip.K1 - 0.5 * w);
-        put(ip.dG2, -etac * ip.K2 - 0.5 * w);
+        // grid coordinate in the fftshifted FFT grid, minus w/2
+        put(ip.dG1, -xic * ip.K1 + 0.5 * p->nfft1 - 0.5 * w);
+        put(ip.dG2, -etac * ip.K2 + 0.5 * p->nfft2 - 0.5 * w);
         put(ip.dkq, ip.kq);
         put(ip.dp1, ip.p1);
         put(ip.dp2, ip.p2);

@@ -193,7 +193,7 @@ struct RowPassArgs {
     int centered_in;     // 1: input index i holds mode i - in_len/2 (type 3 layout)
     const void* deconv_col;   // per-element factor along the row (centered_in), or NULL
     const void* deconv_row;   // per-row scalar factor (centered_in), or NULL
-    int out_len;         // kept outputs: modes k in [-out_len/2, out_len - out_len/2), stored at k + out_len/2; out_len == n: natural order
+    int out_len;         // kept outputs: modes k in [-out_len/2, out_len - out_len/2), stored at k + out_len/2 (out_len == n: fftshifted)
     const void* twiddle;
 };
 struct ColPassArgs {
@@ -201,7 +201,7 @@ struct ColPassArgs {
     int ncols;           // columns (contiguous dimension length of in/out)
     int in_len;          // input rows
     int centered_in;
-    int out_len;         // kept output rows (centered as in RowPassArgs); == n: natural order
+    int out_len;         // kept output rows (centred as in RowPassArgs)
     const void* twiddle;
     // type-1 epilogue (final output) when ax != NULL: out[k2][k1] = F * ax[k1] * ay[k2], then Babinet
     const void* ax; const void* ay;

@@ -220,9 +220,10 @@ __device__ __forceinline__ int in_pos(int i, int len, int n, int centered) {
     int l = i - len / 2;
     return l < 0 ? l + n : l;
 }
-// Source index in the length-n transform of kept output kp.
+// Source index in the length-n transform of kept output kp: outputs are in
+// centred order, kp <-> mode kp - len/2 (for len == n this is the fftshifted
+// full transform).
 __device__ __forceinline__ int out_src(int kp, int len, int n) {
-    if (len == n) return kp;
     int k = kp - len / 2;
     return k < 0 ? k + n : k;
 }

@@ -129,8 +129,9 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
             df_floor_split(g2, &c2, &f2);
             s1 = c1 + 1;
             s2 = c2 + 1;
-            targ1 = (g1.hi + 0.5f * W) * ip.shK1;
-            targ2 = (g2.hi + 0.5f * W) * ip.shK2;
+            // tau = g - (nfft/2 - w/2), exactly in double-float, then scaled
+            targ1 = df_add(g1, dflt{-(0.5f * ip.nfft1 - 0.5f * W), 0.0f}).hi * ip.shK1;
+            targ2 = df_add(g2, dflt{-(0.5f * ip.nfft2 - 0.5f * W), 0.0f}).hi * ip.shK2;
             const dflt kq = {ip.dkq[0], ip.dkq[1]};
             const dflt q1 = df_mul(xi, df_add(df_mul(kq, xi), dflt{ip.dp1[0], ip.dp1[1]}));
             const dflt q2 = df_mul(eta, df_add(df_mul(kq, eta), dflt{ip.dp2[0], ip.dp2[1]}));
@@ -146,7 +147,8 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
                 atomicOr(status, kStatusNonFinite);
                 tau1 = tau2 = 0.0;
             }
-            const double gs1 = tau1 - 0.5 * W, gs2 = tau2 - 0.5 * W;
+            const double gs1 = tau1 + 0.5 * ip.nfft1 - 0.5 * W;
+            const double gs2 = tau2 + 0.5 * ip.nfft2 - 0.5 * W;
             const double fl1 = floor(gs1), fl2 = floor(gs2);
             f1 = (T)(gs1 - fl1);
             f2 = (T)(gs2 - fl2);
@@ -156,28 +158,59 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
             targ2 = (T)(d2 * ip.sh2);
             phr = (T)reduce_phase(ip.kq * (xi * xi + eta * eta) + ip.p1 * xi + ip.p2 * eta);
         }
-        s1 = ((s1 % ip.nfft1) + ip.nfft1) % ip.nfft1;
-        s2 = ((s2 % ip.nfft2) + ip.nfft2) % ip.nfft2;
+        // F is stored fftshifted, so a target's support never wraps; targets
+        // of the plan's box sit in the middle half of the grid.
+        const int lim1 = ip.nfft1 - W - 2, lim2 = ip.nfft2 - W;
+        if (s1 < 0 || s1 > lim1 || s2 < 0 || s2 > lim2) {
+            atomicOr(status, kStatusTargetOutside);
+            s1 = min(max(s1, 0), lim1);
+            s2 = min(max(s2, 0), lim2);
+        }
         T kx[W], ky[W];
         kernel_values<T, W>(f1, beta, hz, kx);
         kernel_values<T, W>(f2, beta, hz, ky);
         T gr = 0, gi = 0;
+        if constexpr (std::is_same<T, float>::value && (W % 2 == 0)) {
+            // W + 2 cells from the even cell at or below s1, as W/2 + 1
+            // aligned 16-byte loads; the weights are shifted by s1's parity.
+            const int odd = s1 & 1;
+            float kk[W + 2];
 #pragma unroll
-        for (int b = 0; b < W; ++b) {
-            int yy = s2 + b;
-            if (yy >= ip.nfft2) yy -= ip.nfft2;
-            const cx_t<T>* row = F + (long long)yy * ip.nfft1;
-            T rr = 0, ri = 0;
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                int xx = s1 + a;
-                if (xx >= ip.nfft1) xx -= ip.nfft1;
-                const cx_t<T> v = __ldg(&row[xx]);
-                rr += kx[a] * v.x;
-                ri += kx[a] * v.y;
+            for (int i = 0; i < W + 2; ++i) {
+                const float lo = (i < W) ? kx[i] : 0.0f;
+                const float hi = (i >= 1 && i <= W) ? kx[i - 1] : 0.0f;
+                kk[i] = odd ? hi : lo;
             }
-            gr += ky[b] * rr;
-            gi += ky[b] * ri;
+            const float4* base =
+                reinterpret_cast<const float4*>(F + (long long)s2 * ip.nfft1 + (s1 - odd));
+            const int row4 = ip.nfft1 / 2;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const float4* row = base + (long long)b * row4;
+                float rr = 0.0f, ri = 0.0f;
+#pragma unroll
+                for (int q = 0; q < W / 2 + 1; ++q) {
+                    const float4 v = __ldg(row + q);
+                    rr = fmaf(kk[2 * q], v.x, fmaf(kk[2 * q + 1], v.z, rr));
+                    ri = fmaf(kk[2 * q], v.y, fmaf(kk[2 * q + 1], v.w, ri));
+                }
+                gr = fmaf(ky[b], rr, gr);
+                gi = fmaf(ky[b], ri, gi);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const cx_t<T>* row = F + (long long)(s2 + b) * ip.nfft1 + s1;
+                T rr = 0, ri = 0;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const cx_t<T> v = __ldg(&row[a]);
+                    rr += kx[a] * v.x;
+                    ri += kx[a] * v.y;
+                }
+                gr += ky[b] * rr;
+                gi += ky[b] * ri;
+            }
         }
         const T dec = kernel_ft_cheb<T>(targ1, s_a, ncheb, inv_tmax) *
                       kernel_ft_cheb<T>(targ2, s_a, ncheb, inv_tmax);

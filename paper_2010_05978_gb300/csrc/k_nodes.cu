@@ -411,21 +411,31 @@ __global__ void k_scan_chunks(int ntiles, int* __restrict__ counts, int* __restr
         __syncthreads();
     }
     const long long total_split_chunks = s_sc[nt - 1];
+    // staged: per split tile (in order) its first chunk, record offset and count
+    int* s_cstart = s_counts + ntiles;
+    int* s_sroff = s_cstart + ntiles + 1;
+    int* s_scnt = s_sroff + ntiles;
     long long roff = s_rec[t] - rsum, scoff = s_sc[t] - sc, nsoff = s_ns[t] - ns, stoff = s_st[t] - stl;
     for (int i = lo; i < hi; ++i) {
         int c = cnt[i];
         cursor[i] = (int)roff;
         if (c > chunk_cap) {
             int nch = (c + chunk_cap - 1) / chunk_cap;
-            for (int k = 0; k < nch; ++k) {
-                long long ci = scoff + k;
-                if (ci < max_chunks) {
-                    Chunk ch;
-                    ch.tile = i;
-                    ch.begin = (int)(roff + (long long)k * chunk_cap);
-                    ch.end = (int)min(roff + (long long)(k + 1) * chunk_cap, roff + c);
-                    ch.split = 1;
-                    chunks[ci] = ch;
+            if (staged) {   // chunks written below, in parallel over the block
+                s_cstart[stoff] = (int)scoff;
+                s_sroff[stoff] = (int)roff;
+                s_scnt[stoff] = c;
+            } else {
+                for (int k = 0; k < nch; ++k) {
+                    long long ci = scoff + k;
+                    if (ci < max_chunks) {
+                        Chunk ch;
+                        ch.tile = i;
+                        ch.begin = (int)(roff + (long long)k * chunk_cap);
+                        ch.end = (int)min(roff + (long long)(k + 1) * chunk_cap, roff + c);
+                        ch.split = 1;
+                        chunks[ci] = ch;
+                    }
                 }
             }
             scoff += nch;
@@ -445,6 +455,28 @@ __global__ void k_scan_chunks(int ntiles, int* __restrict__ counts, int* __restr
         }
         roff += c;
         if (!staged) counts[i] = 0;
+    }
+    if (staged) {
+        const int nsplit = (int)s_st[nt - 1];
+        if (t == 0) s_cstart[nsplit] = (int)total_split_chunks;
+        __syncthreads();
+        // chunk ci of the split tiles: find its tile by binary search
+        for (long long ci = t; ci < total_split_chunks && ci < max_chunks; ci += nt) {
+            int a = 0, b = nsplit - 1;
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (s_cstart[mid] <= ci) a = mid;
+                else b = mid - 1;
+            }
+            const int k = (int)(ci - s_cstart[a]);
+            const long long r0 = s_sroff[a], c = s_scnt[a];
+            Chunk ch;
+            ch.tile = split_tiles[a];
+            ch.begin = (int)(r0 + (long long)k * chunk_cap);
+            ch.end = (int)min(r0 + (long long)(k + 1) * chunk_cap, r0 + c);
+            ch.split = 1;
+            chunks[ci] = ch;
+        }
     }
     if (t == nt - 1) {
         n_meta[0] = (int)min(total_split_chunks + s_ns[t], (long long)max_chunks);
@@ -551,7 +583,7 @@ void launch_scan_chunks(int ntiles, int* counts, int* cursor, Chunk* chunks, int
                         int* split_tiles, int chunk_cap, int max_chunks, int max_split,
                         cudaStream_t st) {
     // counts staged in shared memory when they fit next to the static arrays
-    const size_t dyn = sizeof(int) * (size_t)ntiles;
+    const size_t dyn = sizeof(int) * (4 * (size_t)ntiles + 1);   // counts + split-tile tables
     const int staged = dyn <= 160 * 1024 ? 1 : 0;
     if (staged)
         cudaFuncSetAttribute(k_scan_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
