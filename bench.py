@@ -151,7 +151,19 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
-ALGO_BYTES = {}
+def aggregate_ranks(total_ms, steps, units_per_step, world, device="cpu"):
+    """Weak scaling over independent replicas: every rank processed
+    units_per_step per step; the job's time is the slowest rank's (max over
+    ranks, the only collective).  Returns (ms per step, job units per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / steps
+    return ms_per_step, units_per_step * world / (ms_per_step * 1e-3)
 
 
 def algorithmic_bytes(info1, info3, n_nodes):
@@ -235,15 +247,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop() if clocks else None
     p1.check()
     p3.check()
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = 2e6 * world / (ms_per_step * 1e-3)
+    ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, 2e6, world, dev)
 
     # ---------------- end-to-end through the C ABI with host buffers
     h_t3 = targets_np

@@ -112,6 +112,11 @@ typedef struct {
     int sync_status;     /* 1: fresnel_eval synchronises the stream and returns the
                             device status; 0: asynchronous, see fresnel_check */
     long long max_device_bytes; /* cap on the plan's device memory; 0 = no cap */
+    /* SCATTERED + FP32_FAST: bucket the targets by 16 x 16 blocks of the FFT
+     * grid and interpolate from shared-memory patches (1), gather each target
+     * straight from global memory (-1), or choose (0: bucket when the FFT grid
+     * exceeds 64 MB, i.e. would not stay in L2, and M >= 32768). */
+    int t3_binning;
 } fresnel_opts;
 
 /* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,

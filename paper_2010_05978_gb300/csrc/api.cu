@@ -41,10 +41,13 @@ namespace {
 
 constexpr uint64_t kMagic = 0x46524553'4e454c31ull;   // "FRESNEL1"
 constexpr int kMaxEvents = 16;
-// Type-3 target sorting by FFT-grid bin: measured on the 1e6-target star
-// workload it cost more (count + scan + scatter 0.10 ms) than it saved in the
-// interpolation (0.03 ms), so it is off unless M reaches this size.
-constexpr long long kSortTargetsFrom = 1LL << 40;
+// FP32 type-3 target binning (16 x 16 blocks of the FFT grid, interpolation
+// from shared-memory patches) is chosen automatically only when the FFT grid
+// would not stay in L2 and the target set is large.  Measured on the
+// F = 100 star workload (29 MB grid, 1e6 targets): binned 0.18 ms against
+// 0.126 ms for direct gathers from L2, so small grids gather directly.
+constexpr long long kSortTargetsFrom = 32768;
+constexpr long long kBinFromGridBytes = 64LL << 20;
 
 struct Plan {
     uint64_t magic = kMagic;
@@ -88,7 +91,9 @@ struct Plan {
     double* gq_w = nullptr;
     int gq_n = 0;
     int* tcounts = nullptr;       // type-3 target bins (zero between evaluations)
+    int* tstart = nullptr;
     int* tcursor = nullptr;
+    int* twork = nullptr;         // binned interpolation's dynamic bin counter
     int* perm = nullptr;          // type-3 target permutation, grown on demand
     long long perm_cap = 0;
     double* cheb = nullptr;
@@ -396,8 +401,13 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ev_record(p, "fft_cols");
         p->launches += 2;
         if (M > 0) {
-            const int* perm = nullptr;
-            if (M >= kSortTargetsFrom) {
+            T3Sort sort{};
+            const T3Sort* sp = nullptr;
+            const long long fbytes = (long long)p->nfft1 * p->nfft2 * (long long)sizeof(cx_t<T>);
+            const bool want = p->opts.t3_binning > 0 ||
+                              (p->opts.t3_binning == 0 && M >= kSortTargetsFrom &&
+                               fbytes > kBinFromGridBytes);
+            if (sizeof(T) == 4 && want && M < (1LL << 31) && interp_binned_width(p->ks.w)) {
                 if (M > p->perm_cap) {   // grown once; later evaluations reuse it
                     if (p->perm) cudaFree(p->perm);
                     p->perm = nullptr;
@@ -405,13 +415,12 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
                     FRES_CK(cudaMalloc((void**)&p->perm, sizeof(int) * (size_t)M));
                     p->perm_cap = M;
                 }
-                launch_target_sort(d_targets, M, p->ip, p->tcounts, p->tcursor, p->perm, p->st);
+                sort = T3Sort{p->tcounts, p->tstart, p->tcursor, p->perm, p->twork};
+                sp = &sort;
                 p->launches += 3;
-                perm = p->perm;
-                ev_record(p, "target_sort");
             }
             launch_interp_w<T>(d_targets, M, (const cx_t<T>*)p->F, p->ip, p->ks, p->cheb,
-                               p->ncheb, d_out, p->status, perm, p->st);
+                               p->ncheb, d_out, p->status, sp, p->st);
             p->launches++;
         }
         ev_record(p, "interp_epilogue");
@@ -738,9 +747,14 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
         p->cheb = d_s;
         p->ncheb = nk;
         const int nbins = p->ip.nbin1 * p->ip.nbin2;
+        if ((size_t)nbins * sizeof(int) > 160 * 1024)   // bin scan is staged in shared memory
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "type-3 FFT grid too large for the bin scan");
         FRES_TRY(dalloc(p, (void**)&p->tcounts, sizeof(int) * nbins));
+        FRES_TRY(dalloc(p, (void**)&p->tstart, sizeof(int) * nbins));
         FRES_TRY(dalloc(p, (void**)&p->tcursor, sizeof(int) * nbins));
+        FRES_TRY(dalloc(p, (void**)&p->twork, 2 * sizeof(int)));
         FRES_CK(cudaMemsetAsync(p->tcounts, 0, sizeof(int) * nbins, p->st));
+        FRES_CK(cudaMemsetAsync(p->twork, 0, 2 * sizeof(int), p->st));
         p->ip.inv_tmax = 1.0 / tmax;
     }
     FRES_CK(cudaGetLastError());
@@ -807,6 +821,8 @@ fresnel_status fresnel_plan(const fresnel_family* families, int n_families, doub
         return fres_fail(FRESNEL_ERR_ARG, "sigma must be 0 (auto) or in [1.2, 4]");
     if (opts->kernel_w < 0 || opts->kernel_w > kMaxW)
         return fres_fail(FRESNEL_ERR_ARG, "kernel_w must be 0 (auto) or in [2, 16]");
+    if (opts->t3_binning < -1 || opts->t3_binning > 1)
+        return fres_fail(FRESNEL_ERR_ARG, "t3_binning must be -1, 0 or 1");
     int dev = 0;
     FRES_CK(cudaGetDevice(&dev));
     Plan* p = new Plan();

@@ -234,15 +234,24 @@ struct InterpParams {
     int nfft1, nfft2;
     int occulter;
 };
+// Buffers of the binned FP32 type-3 interpolation: per-bin counts (zero on
+// entry, left zero), bin starts, scatter cursors, the target permutation
+// (>= M entries) and the dynamic bin counter (2 ints, zero, left zero).
+struct T3Sort {
+    int* counts;
+    int* start;
+    int* cursor;
+    int* perm;
+    int* work;
+};
+// sort == NULL (or FP64, or a width without a binned kernel): one thread per
+// target straight from global memory.  Otherwise four launches: bin count,
+// scan, scatter, binned interpolation.
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
                      const KernelShape& ks, const double* cheb, int ncheb,
-                     void* out, unsigned* status, const int* perm, cudaStream_t st);
-// Counting sort of the targets by 16 x 16 bins of the FFT grid -> perm
-// (three launches: count, scan, scatter).  counts must be zero on entry and
-// is left zero.
-void launch_target_sort(const double* targets, long long M, const InterpParams& ip, int* counts,
-                        int* cursor, int* perm, cudaStream_t st);
+                     void* out, unsigned* status, const T3Sort* sort, cudaStream_t st);
+bool interp_binned_width(int w);
 // psihat at the n even-half Chebyshev points of [-t_max, t_max] (plan time)
 void launch_cheb_samples(int n, double tmax, int w, double beta, const double* gq_t,
                          const double* gq_w, int q, double* out, cudaStream_t st);

@@ -24,6 +24,7 @@ namespace {
 constexpr int kFftThreads = 256;
 constexpr int kFftBlocksPerSm = 3;
 constexpr long long kFftSmemTarget = 76 * 1024;   // three blocks per SM
+constexpr int kPrefetch = 8;                       // next-row inputs held per thread
 
 template <typename T> struct Ops {
     using C = cx_t<T>;
@@ -237,6 +238,19 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
     C* S2 = S + padded_len(fp.n);
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
+    // The first kPrefetch * blockDim.x inputs of the block's next row are
+    // loaded into registers while the current row is transformed.
+    C buf[kPrefetch];
+    const int npf = min(a.in_len, kPrefetch * (int)blockDim.x);
+    auto prefetch = [&](int row) {
+        const C* in = (const C*)a.in + (long long)row * a.in_stride;
+#pragma unroll
+        for (int k = 0; k < kPrefetch; ++k) {
+            const int i = threadIdx.x + k * blockDim.x;
+            if (i < npf) buf[k] = in[i];
+        }
+    };
+    if (blockIdx.x < a.nrows) prefetch(blockIdx.x);
     for (int row = blockIdx.x; row < a.nrows; row += gridDim.x) {
         const C* in = (const C*)a.in + (long long)row * a.in_stride;
         if (a.centered_in || a.in_len < n)
@@ -244,12 +258,22 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
         __syncthreads();
         T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
         const T* dcol = (const T*)a.deconv_col;
-        for (int i = threadIdx.x; i < a.in_len; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < kPrefetch; ++k) {
+            const int i = threadIdx.x + k * blockDim.x;
+            if (i < npf) {
+                C v = buf[k];
+                if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
+                S[pad(in_pos(i, a.in_len, n, a.centered_in))] = v;
+            }
+        }
+        for (int i = npf + threadIdx.x; i < a.in_len; i += blockDim.x) {
             C v = in[i];
             if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
             S[pad(in_pos(i, a.in_len, n, a.centered_in))] = v;
         }
         __syncthreads();
+        if (row + (int)gridDim.x < a.nrows) prefetch(row + gridDim.x);
         const C* R = fft_smem<T>(S, S2, 1, fp, tw);
         C* out = (C*)a.out + (long long)row * a.out_stride;
         for (int kp = threadIdx.x; kp < a.out_len; kp += blockDim.x)
@@ -268,20 +292,46 @@ k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     const int ngroups = (a.ncols + ncol - 1) / ncol;
+    const C* in = (const C*)a.in;
+    // Inputs of the block's next column group are prefetched into registers
+    // (first kPrefetch * blockDim.x of them) while the current group runs.
+    C buf[kPrefetch];
+    const int nin = a.in_len * ncol;
+    const int npf = min(nin, kPrefetch * (int)blockDim.x);
+    auto prefetch = [&](int g) {
+        const int c0 = g * ncol;
+#pragma unroll
+        for (int k = 0; k < kPrefetch; ++k) {
+            const int e = threadIdx.x + k * blockDim.x;
+            if (e < npf) {
+                const int i = e / ncol, c = e % ncol;
+                buf[k] = c0 + c < a.ncols ? in[(long long)i * a.ncols + c0 + c] : Ops<T>::mk(0, 0);
+            }
+        }
+    };
+    if (blockIdx.x < ngroups) prefetch(blockIdx.x);
     for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int c0 = g * ncol;
         if (a.centered_in || a.in_len < n)
             for (int e = threadIdx.x; e < padded_len(n) * ncol; e += blockDim.x)
                 S[e] = Ops<T>::mk(0, 0);
         __syncthreads();
-        const C* in = (const C*)a.in;
-        for (int e = threadIdx.x; e < a.in_len * ncol; e += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < kPrefetch; ++k) {
+            const int e = threadIdx.x + k * blockDim.x;
+            if (e < npf) {
+                const int i = e / ncol, c = e % ncol;
+                S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = buf[k];
+            }
+        }
+        for (int e = npf + threadIdx.x; e < nin; e += blockDim.x) {
             const int i = e / ncol, c = e % ncol;
             C v = Ops<T>::mk(0, 0);
             if (c0 + c < a.ncols) v = in[(long long)i * a.ncols + c0 + c];
             S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = v;
         }
         __syncthreads();
+        if (g + (int)gridDim.x < ngroups) prefetch(g + gridDim.x);
         const C* R = fft_smem<T>(S, S2, ncol, fp, tw);
         for (int e = threadIdx.x; e < a.out_len * ncol; e += blockDim.x) {
             const int kp = e / ncol, c = e % ncol;

@@ -5,7 +5,16 @@
 // type-3 deconvolution), and apply the post-phase exp(-i s.C) of the node
 // centring together with the target chirp and 1/(i lz):
 //   u_k = 1/(i lz) exp(i pi |xi_k|^2 / lz - 2 pi i xi_k.C / lz) v'_k,
-// optionally u^oc = 1 - u^ap (eq. bab).  Phases in FP64 with reduction.
+// optionally u^oc = 1 - u^ap (eq. bab).
+//
+// The FFT grid F is stored fftshifted, so a target's w x w support never
+// wraps.  FP32 fast mode: target coordinates, the box check and the phase are
+// double-float (no FP64 arithmetic); for large target sets the targets are
+// first bucketed by the 16 x 16 block of F holding their support, and each
+// block's (16 + w)^2 patch of F is interpolated from shared memory.  FP64
+// mode: FP64 coordinates and phase, gathers straight from global memory.
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "spread.cuh"
 
@@ -16,6 +25,7 @@ namespace {
 constexpr double kTwoPiHi = 6.28318530717958623199592693709;
 constexpr double kTwoPiLo = 2.44929359829470635445e-16;
 constexpr double kInvTwoPi = 0.159154943091895335768883763373;
+constexpr int kBin = 16;            // target bins: 16 x 16 cells of F
 
 __device__ __forceinline__ double reduce_phase(double ph) {
     double n = rint(ph * kInvTwoPi);
@@ -38,113 +48,94 @@ __device__ __forceinline__ T kernel_ft_cheb(T t, const T* a, int n, T inv_tmax) 
     return y * b1 - b2 + a[0];
 }
 
-// Bin of a target: the 16 x 16 block of the FFT grid holding its frequency.
-__device__ __forceinline__ int target_bin(double xi, double eta, const InterpParams& ip) {
-    double tau1 = (xi - ip.xi_c) * ip.K1, tau2 = (eta - ip.eta_c) * ip.K2;
-    if (!(fabs(tau1) <= ip.nfft1) || !(fabs(tau2) <= ip.nfft2)) return 0;
-    int c1 = (int)floor(tau1), c2 = (int)floor(tau2);
-    if (c1 < 0) c1 += ip.nfft1;
-    if (c2 < 0) c2 += ip.nfft2;
-    c1 = min(c1, ip.nfft1 - 1);
-    c2 = min(c2, ip.nfft2 - 1);
-    return (c2 >> 4) * ip.nbin1 + (c1 >> 4);
+// Support start (s1, s2) and fractional offsets of a target in the
+// fftshifted FFT grid, FP32 fast mode (double-float), plus the argument of
+// the kernel transform per dimension.  Out-of-box targets are flagged and
+// clamped so every access stays inside F.
+template <int W>
+__device__ __forceinline__ void geom_f32(const double2 t, const InterpParams& ip, unsigned* status,
+                                         dflt& xi, dflt& eta, int& s1, int& s2, float& f1,
+                                         float& f2, float& targ1, float& targ2) {
+    xi = df_from_double(t.x);
+    eta = df_from_double(t.y);
+    bool bad = !(xi.hi >= ip.boxf[0] && xi.hi <= ip.boxf[1] && eta.hi >= ip.boxf[2] &&
+                 eta.hi <= ip.boxf[3]);
+    dflt g1 = df_add(df_mul(xi, dflt{ip.dK1[0], ip.dK1[1]}), dflt{ip.dG1[0], ip.dG1[1]});
+    dflt g2 = df_add(df_mul(eta, dflt{ip.dK2[0], ip.dK2[1]}), dflt{ip.dG2[0], ip.dG2[1]});
+    if (!(fabsf(g1.hi) <= (float)ip.nfft1) || !(fabsf(g2.hi) <= (float)ip.nfft2)) {
+        bad = true;
+        g1 = g2 = dflt{0.0f, 0.0f};
+    }
+    int c1, c2;
+    df_floor_split(g1, &c1, &f1);
+    df_floor_split(g2, &c2, &f2);
+    s1 = c1 + 1;
+    s2 = c2 + 1;
+    const int lim1 = ip.nfft1 - W - 2, lim2 = ip.nfft2 - W;
+    if (s1 < 0 || s1 > lim1 || s2 < 0 || s2 > lim2) {
+        bad = true;
+        s1 = min(max(s1, 0), lim1);
+        s2 = min(max(s2, 0), lim2);
+    }
+    if (bad && status) atomicOr(status, kStatusTargetOutside);
+    // tau = g - (nfft/2 - w/2), exactly in double-float, then scaled
+    targ1 = df_add(g1, dflt{-(0.5f * ip.nfft1 - 0.5f * W), 0.0f}).hi * ip.shK1;
+    targ2 = df_add(g2, dflt{-(0.5f * ip.nfft2 - 0.5f * W), 0.0f}).hi * ip.shK2;
 }
 
-__global__ void k_target_count(const double* __restrict__ targets, long long M, InterpParams ip,
-                               int* __restrict__ counts) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
-         k += (long long)gridDim.x * blockDim.x) {
-        const double2 t = reinterpret_cast<const double2*>(targets)[k];
-        atomicAdd(&counts[target_bin(t.x, t.y, ip)], 1);
-    }
+// Chirp and post-phase xi (kq xi + p1) + eta (kq eta + p2), reduced mod 2 pi.
+__device__ __forceinline__ float phase_f32(dflt xi, dflt eta, const InterpParams& ip) {
+    const dflt kq = {ip.dkq[0], ip.dkq[1]};
+    const dflt q1 = df_mul(xi, df_add(df_mul(kq, xi), dflt{ip.dp1[0], ip.dp1[1]}));
+    const dflt q2 = df_mul(eta, df_add(df_mul(kq, eta), dflt{ip.dp2[0], ip.dp2[1]}));
+    return df_reduce_2pi(df_add(q1, q2));
 }
 
-// One block: exclusive scan of the bin counts into cursors; resets counts.
-__global__ void k_target_scan(int nbins, int* counts, int* cursor) {
-    __shared__ long long s[1024];
-    const int t = threadIdx.x, nt = blockDim.x;
-    const int per = (nbins + nt - 1) / nt;
-    const int lo = min(t * per, nbins), hi = min(lo + per, nbins);
-    long long sum = 0;
-    for (int i = lo; i < hi; ++i) sum += counts[i];
-    s[t] = sum;
-    __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {
-        long long a = t >= off ? s[t - off] : 0;
-        __syncthreads();
-        s[t] += a;
-        __syncthreads();
+// u = (cs + i sn) g / dec * (-i / lz), then Babinet if requested.
+template <typename T>
+__device__ __forceinline__ cx_t<T> epilogue(T gr, T gi, T dec, T sn, T cs, const InterpParams& ip) {
+    const T sc = (T)ip.inv_lz / dec;
+    const T pr = cs * gr - sn * gi, pi = cs * gi + sn * gr;
+    T ur = pi * sc, ui = -pr * sc;
+    if (ip.occulter) {
+        ur = (T)1 - ur;
+        ui = -ui;
     }
-    long long run = s[t] - sum;
-    for (int i = lo; i < hi; ++i) {
-        const int c = counts[i];
-        cursor[i] = (int)run;
-        run += c;
-        counts[i] = 0;
-    }
+    cx_t<T> o;
+    o.x = ur;
+    o.y = ui;
+    return o;
 }
 
-__global__ void k_target_scatter(const double* __restrict__ targets, long long M, InterpParams ip,
-                                 int* __restrict__ cursor, int* __restrict__ perm) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
-         k += (long long)gridDim.x * blockDim.x) {
-        const double2 t = reinterpret_cast<const double2*>(targets)[k];
-        const int pos = atomicAdd(&cursor[target_bin(t.x, t.y, ip)], 1);
-        if (pos >= 0 && pos < M) perm[pos] = (int)k;
-    }
-}
-
-// Targets are visited in bin order (perm) when a permutation is given, so a
-// warp's targets share grid cells in L1; results go to the caller's order.
+// ------------------------------------------------------------------ generic kernel
+// One thread per target, gathers from global memory (FP64 mode, and FP32
+// mode for small target sets).
 template <typename T, int W>
 __global__ void __launch_bounds__(256)
 k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restrict__ F,
          InterpParams ip, T beta, const double* __restrict__ cheb, int ncheb,
-         cx_t<T>* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz,
-         const int* __restrict__ perm) {
+         cx_t<T>* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz) {
     __shared__ T s_a[kMaxCheb];
     for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (T)cheb[i];
     __syncthreads();
     const T inv_tmax = (T)ip.inv_tmax;
-    for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < M;
-         kk += (long long)gridDim.x * blockDim.x) {
-        const long long k = perm ? (long long)perm[kk] : kk;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
+         k += (long long)gridDim.x * blockDim.x) {
         const double2 t = reinterpret_cast<const double2*>(targets)[k];
         int s1, s2;
         T f1, f2, targ1, targ2, phr;
         if constexpr (std::is_same<T, float>::value) {
-            // FP32 fast mode: double-float coordinates and phase (no FP64 arithmetic)
-            const dflt xi = df_from_double(t.x), eta = df_from_double(t.y);
-            if (!(xi.hi >= ip.boxf[0] && xi.hi <= ip.boxf[1] && eta.hi >= ip.boxf[2] &&
-                  eta.hi <= ip.boxf[3]))
-                atomicOr(status, kStatusTargetOutside);
-            dflt g1 = df_add(df_mul(xi, dflt{ip.dK1[0], ip.dK1[1]}), dflt{ip.dG1[0], ip.dG1[1]});
-            dflt g2 = df_add(df_mul(eta, dflt{ip.dK2[0], ip.dK2[1]}), dflt{ip.dG2[0], ip.dG2[1]});
-            if (!(fabsf(g1.hi) <= (float)ip.nfft1) || !(fabsf(g2.hi) <= (float)ip.nfft2)) {
-                atomicOr(status, kStatusNonFinite);
-                g1 = g2 = dflt{0.0f, 0.0f};
-            }
-            int c1, c2;
-            df_floor_split(g1, &c1, &f1);
-            df_floor_split(g2, &c2, &f2);
-            s1 = c1 + 1;
-            s2 = c2 + 1;
-            // tau = g - (nfft/2 - w/2), exactly in double-float, then scaled
-            targ1 = df_add(g1, dflt{-(0.5f * ip.nfft1 - 0.5f * W), 0.0f}).hi * ip.shK1;
-            targ2 = df_add(g2, dflt{-(0.5f * ip.nfft2 - 0.5f * W), 0.0f}).hi * ip.shK2;
-            const dflt kq = {ip.dkq[0], ip.dkq[1]};
-            const dflt q1 = df_mul(xi, df_add(df_mul(kq, xi), dflt{ip.dp1[0], ip.dp1[1]}));
-            const dflt q2 = df_mul(eta, df_add(df_mul(kq, eta), dflt{ip.dp2[0], ip.dp2[1]}));
-            phr = df_reduce_2pi(df_add(q1, q2));
+            dflt xi, eta;
+            geom_f32<W>(t, ip, status, xi, eta, s1, s2, f1, f2, targ1, targ2);
+            phr = phase_f32(xi, eta, ip);
         } else {
             const double xi = t.x, eta = t.y;
-            if (!(xi >= ip.box[0] && xi <= ip.box[1] && eta >= ip.box[2] && eta <= ip.box[3]))
-                atomicOr(status, kStatusTargetOutside);
+            bool bad = !(xi >= ip.box[0] && xi <= ip.box[1] && eta >= ip.box[2] && eta <= ip.box[3]);
             const double d1 = xi - ip.xi_c, d2 = eta - ip.eta_c;
             double tau1 = d1 * ip.K1, tau2 = d2 * ip.K2;
             if (!isfinite(tau1) || !isfinite(tau2) || fabs(tau1) > ip.nfft1 ||
                 fabs(tau2) > ip.nfft2) {
-                atomicOr(status, kStatusNonFinite);
+                bad = true;
                 tau1 = tau2 = 0.0;
             }
             const double gs1 = tau1 + 0.5 * ip.nfft1 - 0.5 * W;
@@ -154,84 +145,188 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
             f2 = (T)(gs2 - fl2);
             s1 = (int)fl1 + 1;
             s2 = (int)fl2 + 1;
+            const int lim1 = ip.nfft1 - W - 2, lim2 = ip.nfft2 - W;
+            if (s1 < 0 || s1 > lim1 || s2 < 0 || s2 > lim2) {
+                bad = true;
+                s1 = min(max(s1, 0), lim1);
+                s2 = min(max(s2, 0), lim2);
+            }
+            if (bad) atomicOr(status, kStatusTargetOutside);
             targ1 = (T)(d1 * ip.sh1);
             targ2 = (T)(d2 * ip.sh2);
             phr = (T)reduce_phase(ip.kq * (xi * xi + eta * eta) + ip.p1 * xi + ip.p2 * eta);
-        }
-        // F is stored fftshifted, so a target's support never wraps; targets
-        // of the plan's box sit in the middle half of the grid.
-        const int lim1 = ip.nfft1 - W - 2, lim2 = ip.nfft2 - W;
-        if (s1 < 0 || s1 > lim1 || s2 < 0 || s2 > lim2) {
-            atomicOr(status, kStatusTargetOutside);
-            s1 = min(max(s1, 0), lim1);
-            s2 = min(max(s2, 0), lim2);
         }
         T kx[W], ky[W];
         kernel_values<T, W>(f1, beta, hz, kx);
         kernel_values<T, W>(f2, beta, hz, ky);
         T gr = 0, gi = 0;
-        if constexpr (std::is_same<T, float>::value && (W % 2 == 0)) {
-            // W + 2 cells from the even cell at or below s1, as W/2 + 1
-            // aligned 16-byte loads; the weights are shifted by s1's parity.
-            const int odd = s1 & 1;
-            float kk[W + 2];
 #pragma unroll
-            for (int i = 0; i < W + 2; ++i) {
-                const float lo = (i < W) ? kx[i] : 0.0f;
-                const float hi = (i >= 1 && i <= W) ? kx[i - 1] : 0.0f;
-                kk[i] = odd ? hi : lo;
+        for (int b = 0; b < W; ++b) {
+            const cx_t<T>* row = F + (long long)(s2 + b) * ip.nfft1 + s1;
+            T rr = 0, ri = 0;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                const cx_t<T> v = __ldg(&row[a]);
+                rr += kx[a] * v.x;
+                ri += kx[a] * v.y;
             }
-            const float4* base =
-                reinterpret_cast<const float4*>(F + (long long)s2 * ip.nfft1 + (s1 - odd));
-            const int row4 = ip.nfft1 / 2;
-#pragma unroll
-            for (int b = 0; b < W; ++b) {
-                const float4* row = base + (long long)b * row4;
-                float rr = 0.0f, ri = 0.0f;
-#pragma unroll
-                for (int q = 0; q < W / 2 + 1; ++q) {
-                    const float4 v = __ldg(row + q);
-                    rr = fmaf(kk[2 * q], v.x, fmaf(kk[2 * q + 1], v.z, rr));
-                    ri = fmaf(kk[2 * q], v.y, fmaf(kk[2 * q + 1], v.w, ri));
-                }
-                gr = fmaf(ky[b], rr, gr);
-                gi = fmaf(ky[b], ri, gi);
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < W; ++b) {
-                const cx_t<T>* row = F + (long long)(s2 + b) * ip.nfft1 + s1;
-                T rr = 0, ri = 0;
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const cx_t<T> v = __ldg(&row[a]);
-                    rr += kx[a] * v.x;
-                    ri += kx[a] * v.y;
-                }
-                gr += ky[b] * rr;
-                gi += ky[b] * ri;
-            }
+            gr += ky[b] * rr;
+            gi += ky[b] * ri;
         }
         const T dec = kernel_ft_cheb<T>(targ1, s_a, ncheb, inv_tmax) *
                       kernel_ft_cheb<T>(targ2, s_a, ncheb, inv_tmax);
         T sn, cs;
-        if constexpr (std::is_same<T, float>::value) {
-            sincosf(phr, &sn, &cs);
-        } else {
-            sincos(phr, &sn, &cs);
+        if constexpr (std::is_same<T, float>::value) sincosf(phr, &sn, &cs);
+        else sincos(phr, &sn, &cs);
+        out[k] = epilogue<T>(gr, gi, dec, sn, cs, ip);
+    }
+}
+
+// ------------------------------------------------------------------ binned FP32 path
+template <int W>
+__device__ __forceinline__ int target_bin(const double2 t, const InterpParams& ip) {
+    dflt xi, eta;
+    int s1, s2;
+    float f1, f2, a1, a2;
+    geom_f32<W>(t, ip, nullptr, xi, eta, s1, s2, f1, f2, a1, a2);
+    return (s2 / kBin) * ip.nbin1 + (s1 / kBin);
+}
+
+template <int W>
+__global__ void k_target_count(const double* __restrict__ targets, long long M, InterpParams ip,
+                               int* __restrict__ counts) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double2 t = reinterpret_cast<const double2*>(targets)[k];
+        atomicAdd(&counts[target_bin<W>(t, ip)], 1);
+    }
+}
+
+// One block: exclusive scan of the bin counts (staged in shared memory) into
+// bin starts and scatter cursors; clears the counts.
+__global__ void k_target_scan(int nbins, int* __restrict__ counts, int* __restrict__ start,
+                              int* __restrict__ cursor) {
+    __shared__ long long s[1024];
+    extern __shared__ int s_cnt[];
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < nbins; i += nt) {
+        s_cnt[i] = counts[i];
+        counts[i] = 0;
+    }
+    __syncthreads();
+    const int per = (nbins + nt - 1) / nt;
+    const int lo = min(t * per, nbins), hi = min(lo + per, nbins);
+    long long sum = 0;
+    for (int i = lo; i < hi; ++i) sum += s_cnt[i];
+    s[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        const long long a = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += a;
+        __syncthreads();
+    }
+    long long run = s[t] - sum;
+    for (int i = lo; i < hi; ++i) {
+        const int c = s_cnt[i];
+        s_cnt[i] = (int)run;
+        run += c;
+    }
+    __syncthreads();
+    for (int i = t; i < nbins; i += nt) {
+        start[i] = s_cnt[i];
+        cursor[i] = s_cnt[i];
+    }
+}
+
+template <int W>
+__global__ void k_target_scatter(const double* __restrict__ targets, long long M, InterpParams ip,
+                                 int* __restrict__ cursor, int* __restrict__ perm) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double2 t = reinterpret_cast<const double2*>(targets)[k];
+        const int pos = atomicAdd(&cursor[target_bin<W>(t, ip)], 1);
+        if (pos >= 0 && pos < M) perm[pos] = (int)k;
+    }
+}
+
+// Binned interpolation: a block takes bins dynamically (work[0]); it copies
+// the bin's (16 + w) x (16 + w) patch of F to shared memory and interpolates
+// the bin's targets from it, writing each result to the target's own index.
+template <int W>
+__global__ void __launch_bounds__(128)
+k_interp_binned(const double* __restrict__ targets, long long M, const float2* __restrict__ F,
+                InterpParams ip, const double* __restrict__ cheb, int ncheb,
+                float2* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz,
+                const int* __restrict__ perm, const int* __restrict__ bin_start, int nbins,
+                int* __restrict__ work, float beta) {
+    constexpr int P = kBin + W;          // patch edge
+    constexpr int PS = P + 1;            // patch row stride (float2)
+    __shared__ float2 patch[P * PS];
+    __shared__ float s_a[kMaxCheb];
+    __shared__ int s_b;
+    for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (float)cheb[i];
+    const float inv_tmax = (float)ip.inv_tmax;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_b = atomicAdd(&work[0], 1);
+        __syncthreads();
+        const int b = s_b;
+        if (b >= nbins) break;
+        const int beg = bin_start[b];
+        const int end = b + 1 < nbins ? bin_start[b + 1] : (int)M;
+        if (beg >= end) continue;
+        const int ox = (b % ip.nbin1) * kBin, oy = (b / ip.nbin1) * kBin;
+        for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+            const int r = e / P, c = e % P;
+            const int gy = oy + r, gx = ox + c;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (gy < ip.nfft2 && gx < ip.nfft1) v = __ldg(&F[(long long)gy * ip.nfft1 + gx]);
+            patch[r * PS + c] = v;
         }
-        // (cs + i sn) (gr + i gi) / dec * (-i / lz)
-        const T sc = (T)ip.inv_lz / dec;
-        const T pr = cs * gr - sn * gi, pi = cs * gi + sn * gr;
-        T ur = pi * sc, ui = -pr * sc;
-        if (ip.occulter) {
-            ur = (T)1 - ur;
-            ui = -ui;
+        __syncthreads();
+        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+            const int k = perm[i];
+            const double2 t = reinterpret_cast<const double2*>(targets)[k];
+            dflt xi, eta;
+            int s1, s2;
+            float f1, f2, targ1, targ2;
+            geom_f32<W>(t, ip, status, xi, eta, s1, s2, f1, f2, targ1, targ2);
+            const int x = s1 - ox, y = s2 - oy;   // in [0, 16) by construction of the bins
+            float kx[W], ky[W];
+            kernel_values<float, W>(f1, beta, hz, kx);
+            kernel_values<float, W>(f2, beta, hz, ky);
+            float gr = 0.0f, gi = 0.0f;
+            if ((unsigned)x < (unsigned)kBin && (unsigned)y < (unsigned)kBin) {
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    const float2* row = patch + (y + bb) * PS + x;
+                    float rr = 0.0f, ri = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        const float2 v = row[a];
+                        rr = fmaf(kx[a], v.x, rr);
+                        ri = fmaf(kx[a], v.y, ri);
+                    }
+                    gr = fmaf(ky[bb], rr, gr);
+                    gi = fmaf(ky[bb], ri, gi);
+                }
+            } else if (status) {
+                atomicOr(status, kStatusNonFinite);   // bin / geometry mismatch: cannot happen
+            }
+            const float dec = kernel_ft_cheb<float>(targ1, s_a, ncheb, inv_tmax) *
+                              kernel_ft_cheb<float>(targ2, s_a, ncheb, inv_tmax);
+            float sn, cs;
+            sincosf(phase_f32(xi, eta, ip), &sn, &cs);
+            out[k] = epilogue<float>(gr, gi, dec, sn, cs, ip);
         }
-        cx_t<T> o;
-        o.x = ur;
-        o.y = ui;
-        out[k] = o;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&work[1], 1) == (int)gridDim.x - 1) {
+            work[0] = 0;
+            work[1] = 0;
+        }
     }
 }
 
@@ -245,6 +340,11 @@ __global__ void k_cheb_samples(int n, double tmax, int w, double beta, const dou
     out[i] = kernel_ft<double>(tmax * x, w, beta, gq_t, gq_w, q);
 }
 
+inline int nblk(long long n, int b, int cap) {
+    long long g = (n + b - 1) / b;
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
 }  // namespace
 
 void launch_cheb_samples(int n, double tmax, int w, double beta, const double* gq_t,
@@ -252,28 +352,42 @@ void launch_cheb_samples(int n, double tmax, int w, double beta, const double* g
     k_cheb_samples<<<(n + 63) / 64, 64, 0, st>>>(n, tmax, w, beta, gq_t, gq_w, q, out);
 }
 
-void launch_target_sort(const double* targets, long long M, const InterpParams& ip, int* counts,
-                        int* cursor, int* perm, cudaStream_t st) {
-    if (M <= 0) return;
-    long long nb = (M + 255) / 256;
-    int blocks = (int)(nb < 152LL * 16 ? nb : 152LL * 16);
-    k_target_count<<<blocks, 256, 0, st>>>(targets, M, ip, counts);
-    k_target_scan<<<1, 1024, 0, st>>>(ip.nbin1 * ip.nbin2, counts, cursor);
-    k_target_scatter<<<blocks, 256, 0, st>>>(targets, M, ip, cursor, perm);
-}
-
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
-                     const KernelShape& ks, const double* cheb, int ncheb,
-                     void* out, unsigned* status, const int* perm, cudaStream_t st) {
+                     const KernelShape& ks, const double* cheb, int ncheb, void* out,
+                     unsigned* status, const T3Sort* sort, cudaStream_t st) {
     if (M <= 0) return;
-    long long nb = (M + 255) / 256;
-    int blocks = (int)(nb < 152LL * 32 ? nb : 152LL * 32);
     T beta = (T)ks.beta;
+    if constexpr (std::is_same<T, float>::value) {
+        if (sort) {   // binned path: count, scan, scatter, interpolate from patches
+            const int nbins = ip.nbin1 * ip.nbin2;
+            const int gb = nblk(M, 256, 152 * 16);
+            const size_t dyn = sizeof(int) * (size_t)nbins;
+            cudaFuncSetAttribute(k_target_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dyn);
+#define FRES_BINNED_CASE(WW)                                                                   \
+    case WW:                                                                                   \
+        k_target_count<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->counts);                  \
+        k_target_scan<<<1, 1024, dyn, st>>>(nbins, sort->counts, sort->start, sort->cursor);   \
+        k_target_scatter<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->cursor, sort->perm);    \
+        k_interp_binned<WW><<<152 * 8, 128, 0, st>>>(targets, M, F, ip, cheb, ncheb,           \
+                                                      (float2*)out, status, ks.horner,         \
+                                                      sort->perm, sort->start, nbins,          \
+                                                      sort->work, beta);                       \
+        return;
+            switch (ks.w) {
+                FRES_BINNED_CASE(4) FRES_BINNED_CASE(5) FRES_BINNED_CASE(6) FRES_BINNED_CASE(7)
+                FRES_BINNED_CASE(8) FRES_BINNED_CASE(9) FRES_BINNED_CASE(10)
+                default: break;   // other widths: generic kernel below
+            }
+#undef FRES_BINNED_CASE
+        }
+    }
+    const int blocks = nblk(M, 256, 152 * 32);
 #define FRES_INTERP_CASE(WW)                                                                   \
     case WW:                                                                                   \
         k_interp<T, WW><<<blocks, 256, 0, st>>>(targets, M, F, ip, beta, cheb, ncheb,         \
-                                                (cx_t<T>*)out, status, ks.horner, perm);       \
+                                                (cx_t<T>*)out, status, ks.horner);             \
         break;
     switch (ks.w) {
         FRES_INTERP_CASE(2) FRES_INTERP_CASE(3) FRES_INTERP_CASE(4) FRES_INTERP_CASE(5)
@@ -285,11 +399,14 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
 #undef FRES_INTERP_CASE
 }
 
+bool interp_binned_width(int w) { return w >= 4 && w <= 10; }
+
 template void launch_interp_w<float>(const double*, long long, const float2*, const InterpParams&,
                                      const KernelShape&, const double*, int, void*, unsigned*,
-                                     const int*, cudaStream_t);
+                                     const T3Sort*, cudaStream_t);
 template void launch_interp_w<double>(const double*, long long, const double2*,
                                       const InterpParams&, const KernelShape&, const double*, int,
-                                      void*, unsigned*, const int*, cudaStream_t);
+                                      void*, unsigned*, const T3Sort*, cudaStream_t);
 
 }  // namespace fres
+

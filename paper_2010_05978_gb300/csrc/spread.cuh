@@ -143,51 +143,25 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
             constexpr int NPASS = (W + RPW - 1) / RPW;
             const int a = lane % W, b0 = lane / W;
             const bool lane_on = lane < RPW * W;
-            // Records are applied in order; two consecutive records whose
-            // supports are disjoint are applied together (independent cells,
-            // so their shared-memory read-modify-writes overlap in time).
-            for (int j = 0; j < cnt;) {
+            for (int j = 0; j < cnt; ++j) {
                 const int dx = sm.dxy[warp][j][0], dy = sm.dxy[warp][j][1];
-                int dx2 = 0, dy2 = 0;
-                bool pair = false;
-                if (j + 1 < cnt) {
-                    dx2 = sm.dxy[warp][j + 1][0];
-                    dy2 = sm.dxy[warp][j + 1][1];
-                    pair = abs(dx2 - dx) >= W || abs(dy2 - dy) >= W;
-                }
-                const int x = dx + a, x2 = dx2 + a;
-                const bool on1 = lane_on && (unsigned)x < (unsigned)kTile;
-                const bool on2 = pair && lane_on && (unsigned)x2 < (unsigned)kTile;
-                const T kxv = on1 ? sm.kx[warp][j][a] : (T)0;
-                const T kxv2 = on2 ? sm.kx[warp][j + 1][a] : (T)0;
+                const int x = dx + a;
+                if (lane_on && (unsigned)x < (unsigned)kTile) {
+                    const T kxv = sm.kx[warp][j][a];
 #pragma unroll
-                for (int k = 0; k < NPASS; ++k) {
-                    const int b = b0 + k * RPW;
-                    const int y = dy + b, y2 = dy2 + b;
-                    const bool c1 = on1 && b < W && (unsigned)y < (unsigned)kTile;
-                    const bool c2 = on2 && b < W && (unsigned)y2 < (unsigned)kTile;
-                    cx_t<T> o, o2;
-                    cx_t<T> cc, cc2;
-                    if (c1) {
-                        cc = sm.cky[warp][j][b];
-                        o = my[y * kTileStride + x];
-                    }
-                    if (c2) {
-                        cc2 = sm.cky[warp][j + 1][b];
-                        o2 = my[y2 * kTileStride + x2];
-                    }
-                    if (c1) {
-                        o.x += cc.x * kxv;
-                        o.y += cc.y * kxv;
-                        my[y * kTileStride + x] = o;
-                    }
-                    if (c2) {
-                        o2.x += cc2.x * kxv2;
-                        o2.y += cc2.y * kxv2;
-                        my[y2 * kTileStride + x2] = o2;
+                    for (int k = 0; k < NPASS; ++k) {
+                        const int b = b0 + k * RPW;
+                        const int y = dy + b;
+                        if (b < W && (unsigned)y < (unsigned)kTile) {
+                            const cx_t<T> c = sm.cky[warp][j][b];
+                            cx_t<T>& cell = my[y * kTileStride + x];
+                            cx_t<T> o = cell;
+                            o.x += c.x * kxv;
+                            o.y += c.y * kxv;
+                            cell = o;
+                        }
                     }
                 }
-                j += pair ? 2 : 1;
                 __syncwarp();
             }
         }

@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
                 ("grid_x0", ctypes.c_double), ("grid_y0", ctypes.c_double),
                 ("box", ctypes.c_double * 4), ("sigma", ctypes.c_double),
                 ("kernel_w", ctypes.c_int), ("recompute_nodes", ctypes.c_int),
-                ("sync_status", ctypes.c_int), ("max_device_bytes", ctypes.c_longlong)]
+                ("sync_status", ctypes.c_int), ("max_device_bytes", ctypes.c_longlong),
+                ("t3_binning", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -142,7 +143,7 @@ class Plan:
 
     def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
                  box=None, sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
-                 max_device_bytes=0, stream=None):
+                 max_device_bytes=0, t3_binning=0, stream=None):
         import torch
         lib = load_library()
         self._torch = torch
@@ -172,6 +173,7 @@ class Plan:
         o.recompute_nodes = int(bool(recompute_nodes))
         o.sync_status = int(bool(sync_status))
         o.max_device_bytes = int(max_device_bytes)
+        o.t3_binning = int(t3_binning)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

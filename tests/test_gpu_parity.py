@@ -179,6 +179,39 @@ def test_t3_offset_box_and_occulter():
     assert rel_l2(p.eval(t).cpu().numpy(), ref) <= 1e-10
 
 
+@pytest.mark.parametrize("M", [40000, 777])
+def test_t3_binned_path_matches_oracle_and_direct_path(M):
+    """FP32 type-3 with target binning forced on (interpolation from
+    shared-memory patches) and off (direct gathers): both must match the
+    oracle and each other."""
+    fam = [W.fourier_family(W.STAR_PARAMS, 48, 16, 64, cx=0.02)]
+    lz = 0.03
+    xi, eta = W.disc_targets(M, 1.5, 9)
+    xi[:5], eta[:5] = 0.0, 0.0               # duplicates at the box centre
+    xi[5], eta[5] = 1.5, 0.0                 # on the box edge
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    box = (-1.5, 1.5, -1.5, 1.5)
+    u_binned = plan(fam, lz, 1.0, 1e-6, box=box, t3_binning=1).eval(t).cpu().numpy()
+    u_direct = plan(fam, lz, 1.0, 1e-6, box=box, t3_binning=-1).eval(t).cpu().numpy()
+    assert rel_l2(u_binned, u_direct) <= 1e-6
+    idx = W.rng(9, 3).choice(len(xi), min(600, M), replace=False)
+    idx[:6] = np.arange(6)
+    ref = oracle.field(fam, lz, 1.0, xi[idx], eta[idx])
+    assert rel_l2(u_binned[idx], ref) <= 1e-6
+
+
+def test_t3_binned_path_flags_outside_targets():
+    from paper_2010_05978_gb300 import FresnelError
+    fam = [W.fourier_family([1.0], 16, 16, 16)]
+    p = plan(fam, 0.1, 1.0, 1e-6, box=(-1, 1, -1, 1), t3_binning=1)
+    xi, eta = W.square_targets(40000, 0.9, 5)
+    xi[123] = 1.7
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    with pytest.raises(FresnelError) as e:
+        p.eval(t)
+    assert e.value.status == -6
+
+
 def test_t3_empty_and_single_target():
     fam = [W.fourier_family([1.0], 16, 16, 16)]
     p = plan(fam, 0.1, 1.0, 1e-12, precision="fp64", box=(-1, 1, -1, 1))
