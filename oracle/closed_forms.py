@@ -88,3 +88,59 @@ def brute_force_star(params, lz, xi, eta, cx=0.0, cy=0.0, tol=1e-12):
     im, _ = integrate.dblquad(lambda r, th: np.sin(phase(r, th)) * r, 0.0, 2.0 * np.pi,
                               lambda th: 0.0, rmax, epsabs=tol, epsrel=tol)
     return (re + 1j * im) / (1j * lz)
+
+
+def flower_area_moments(a, R, A):
+    """Area and second moment of the starshade of eq. Omega (Sec. 4.2).
+
+    At radius r the petals cover an angle N_p * 2 pi A(r) / N_p = 2 pi A(r),
+    the disc the full 2 pi, so
+        area = pi a^2 + 2 pi int_a^R A(r) r dr,
+        int |x|^2 dA = pi a^4 / 2 + 2 pi int_a^R A(r) r^3 dr,
+    the 1D integrals by adaptive Gauss-Kronrod (scipy quad).
+    """
+    opt = dict(epsabs=1e-14, epsrel=1e-14, limit=400)
+    area = np.pi * a * a + 2.0 * np.pi * integrate.quad(lambda r: A(r) * r, a, R, **opt)[0]
+    mom = 0.5 * np.pi * a ** 4 + 2.0 * np.pi * integrate.quad(lambda r: A(r) * r ** 3, a, R, **opt)[0]
+    return area, mom
+
+
+def flower_on_axis(a, R, A, lz):
+    """u^ap at the centre of the starshade (eq. fres at xi = 0, polar coordinates).
+
+    The angular integral at radius r gives 2 pi (disc) or 2 pi A(r) (petals), so
+        u = 1 - e^{i pi a^2/lz} + (2 pi/(i lz)) int_a^R A(r) e^{i pi r^2/lz} r dr,
+    the last integral by adaptive Gauss-Kronrod on its real and imaginary parts.
+    """
+    opt = dict(epsabs=1e-14, epsrel=1e-13, limit=2000)
+    re = integrate.quad(lambda r: A(r) * np.cos(np.pi * r * r / lz) * r, a, R, **opt)[0]
+    im = integrate.quad(lambda r: A(r) * np.sin(np.pi * r * r / lz) * r, a, R, **opt)[0]
+    return 1.0 - np.exp(1j * np.pi * a * a / lz) + (2.0 * np.pi / (1j * lz)) * (re + 1j * im)
+
+
+def brute_force_flower(n_petals, a, R, A, lz, xi, eta, tol=1e-11):
+    """Eq. fres by adaptive 2D integration over the starshade of eq. Omega.
+
+    Omega = {0 <= r <= R : P(N_p theta) in (-pi A(r), pi A(r))}, A = 1 on r < a:
+    the disc r < a plus, for each k, the petal a < r < R,
+    |theta - 2 pi k/N_p| < pi A(r)/N_p.  Each piece is integrated in polar
+    coordinates (area element r dr dtheta) with scipy.integrate.dblquad.
+    """
+    def phase(r, th):
+        dx = xi - r * np.cos(th)
+        dy = eta - r * np.sin(th)
+        return np.pi * (dx * dx + dy * dy) / lz
+
+    def piece(r0, r1, lo, hi):
+        re, _ = integrate.dblquad(lambda th, r: np.cos(phase(r, th)) * r, r0, r1, lo, hi,
+                                  epsabs=tol, epsrel=tol)
+        im, _ = integrate.dblquad(lambda th, r: np.sin(phase(r, th)) * r, r0, r1, lo, hi,
+                                  epsabs=tol, epsrel=tol)
+        return re + 1j * im
+
+    total = piece(0.0, a, lambda r: 0.0, lambda r: 2.0 * np.pi)
+    for k in range(n_petals):
+        c = 2.0 * np.pi * k / n_petals
+        total += piece(a, R, lambda r, c=c: c - np.pi * A(r) / n_petals,
+                       lambda r, c=c: c + np.pi * A(r) / n_petals)
+    return total / (1j * lz)

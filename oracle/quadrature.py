@@ -16,6 +16,18 @@ Panel-family description (plain dict, produced by ``workloads.py``):
 
 ``{"kind": "nodes", "x", "y", "w"}``
     An explicit areal rule (eq. aq).
+
+``{"kind": "petals", "n_petals": Np, "a": a, "R": R, "m": m, "n_p": n_p,
+   "n_d": n_d, "m_d": m_d, "profile": {...}, "cx": cx, "cy": cy}``
+    The starshade rule of Sec. 4.2: the disc r < a (n_d-node periodic
+    trapezoid boundary rule, m_d radii) plus Np petals whose angular width at
+    radius r is 2 pi A(r) / Np (eq. Omega), each covered by m Gauss-Legendre
+    radii on (a, R) times n_p Gauss-Legendre angles.  The profile A is
+    ``{"kind": "hg", "b": b, "q": q}`` (offset hyper-Gaussian
+    A = exp(-((r - a)/b)^q)), ``{"kind": "bspline", "coefs": [...]}`` (clamped
+    uniform cubic B-spline on [a, R]) or ``{"kind": "table", "A": [...]}``
+    (values at the m ascending Gauss-Legendre radii).  The whole shape is
+    translated by (cx, cy).
 """
 import numpy as np
 
@@ -94,6 +106,64 @@ def dilation_rule(X, Y, W, V, m, cx=0.0, cy=0.0):
     return x.ravel(), y.ravel(), w.ravel()
 
 
+def bspline_knots(a, R, n):
+    """Clamped uniform cubic knot vector on [a, R] for n >= 4 coefficients."""
+    inner = np.linspace(a, R, n - 2)[1:-1]
+    return np.concatenate([[a] * 4, inner, [R] * 4])
+
+
+def petal_profile(profile, a, R, r):
+    """Apodisation A(r) of Sec. 4.2 on [a, R] (the profile dict of a petal family)."""
+    kind = profile["kind"]
+    if kind == "hg":
+        return np.exp(-((r - a) / profile["b"]) ** profile["q"])
+    if kind == "bspline":
+        from scipy.interpolate import BSpline
+        c = np.asarray(profile["coefs"], float)
+        return BSpline(bspline_knots(a, R, len(c)), c, 3)(r)
+    if kind == "table":
+        return np.asarray(profile["A"], float)
+    raise ValueError("unknown profile kind %r" % kind)
+
+
+def starshade_rule(fam):
+    """Areal rule for the starshade ("flower") of eq. Omega, Sec. 4.2.
+
+    Disc part: the periodic trapezoid rule (eq. ptr) on the circle
+    (a cos t, a sin t) with n_d nodes, dilated with m_d radii (eqs. aqnod,
+    aqwei).  Petal part: (r_l, what_l) the m-point Gauss-Legendre rule on
+    (a, R), (t_i, omegahat_i) the n_p-point Gauss-Legendre rule on
+    [-pi/Np, pi/Np]; in petal k (centred on angle 2 pi k / Np, where
+    P(Np theta) = 0) the node at (l, i) is
+        r_l (cos(A(r_l) t_i + 2 pi k/Np), sin(A(r_l) t_i + 2 pi k/Np)),
+    weight r_l what_l A(r_l) omegahat_i (area element r dr dtheta with
+    theta = A(r) t; the printed A(r_i) is read as A(r_l)).
+    Order: disc nodes (boundary-major, radius fastest), then petal k, angle
+    i, radius l fastest.  N = n_d m_d + Np n_p m.
+    """
+    Np, a, R = int(fam["n_petals"]), float(fam["a"]), float(fam["R"])
+    m, n_p = int(fam["m"]), int(fam["n_p"])
+    n_d, m_d = int(fam.get("n_d", 0)), int(fam.get("m_d", 0))
+    cx, cy = fam.get("cx", 0.0), fam.get("cy", 0.0)
+    xs, ys, ws = [], [], []
+    if n_d > 0:
+        X, Y, W, V = ptr_line_rule(lambda t: (a * np.cos(t), a * np.sin(t)),
+                                   lambda t: (-a * np.sin(t), a * np.cos(t)), n_d)
+        x, y, w = dilation_rule(X, Y, W, V, m_d)
+        xs.append(x)
+        ys.append(y)
+        ws.append(w)
+    r, wr = gauss_legendre(m, a, R)
+    t, wt = gauss_legendre(n_p, -np.pi / Np, np.pi / Np)
+    A = petal_profile(fam["profile"], a, R, r)
+    for k in range(Np):
+        theta = A[None, :] * t[:, None] + 2.0 * np.pi * k / Np     # [i, l]
+        xs.append((r[None, :] * np.cos(theta)).ravel())
+        ys.append((r[None, :] * np.sin(theta)).ravel())
+        ws.append((wt[:, None] * (r * wr * A)[None, :]).ravel())
+    return cx + np.concatenate(xs), cy + np.concatenate(ys), np.concatenate(ws)
+
+
 def family_line_rule(fam):
     """The boundary vector line rule (X, Y, W, V) and centre of one panel family."""
     kind = fam["kind"]
@@ -112,5 +182,7 @@ def family_nodes(fam):
     if fam["kind"] == "nodes":
         return (np.asarray(fam["x"], float), np.asarray(fam["y"], float),
                 np.asarray(fam["w"], float))
+    if fam["kind"] == "petals":
+        return starshade_rule(fam)
     X, Y, W, V, cx, cy = family_line_rule(fam)
     return dilation_rule(X, Y, W, V, fam["m"], cx, cy)

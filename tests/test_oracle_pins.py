@@ -223,6 +223,134 @@ def test_split_identity_pins_sum3():
     assert np.max(np.abs(u - ud)) < 1e-11
 
 
+# ------------------------------------------------------------------ starshade rule (Sec. 4.2)
+HG = lambda a, b, q: (lambda r: np.exp(-((r - a) / b) ** q))
+SMALL_FLOWER = dict(n_petals=5, a=0.4, R=1.0, profile={"kind": "hg", "b": 0.35, "q": 4})
+
+
+def _small_flower(m=40, n_p=30, n_d=60, m_d=40, **kw):
+    d = dict(SMALL_FLOWER)
+    d.update(kw)
+    return W.petal_family(d["n_petals"], d["a"], d["R"], d["profile"], m, n_p, n_d, m_d,
+                          d.get("cx", 0.0), d.get("cy", 0.0))
+
+
+def test_starshade_printed_node_count():
+    """Table t:star: HG with 16 petals, m = 60, n_p = 30 has N = 37440 nodes."""
+    with open(os.path.join(GOLDEN, "paper_printed.json")) as fh:
+        g = json.load(fh)["starshade_node_counts"]["HG"]
+    n_d = int(round(0.3 * g["N_p"] * g["n_p"]))
+    fam = W.petal_family(g["N_p"], 12.5, 31.0, {"kind": "hg", "b": 12.5, "q": 6}, g["m"],
+                         g["n_p"], n_d, g["m"])
+    x, y, w = Q.family_nodes(fam)
+    assert len(x) == len(y) == len(w) == g["N"]
+
+
+@pytest.mark.parametrize("shape", ["paper_hg", "hg24", "small"])
+def test_starshade_area_and_moments(shape):
+    """Sum w = pi a^2 + 2 pi int A r dr; sum w |x|^2 likewise; first moments 0."""
+    if shape == "paper_hg":
+        a, R, b, q, Np, m, n_p = 12.5, 31.0, 12.5, 6, 16, 60, 30
+    elif shape == "hg24":
+        a, R, b, q, Np, m, n_p = 6.0, 14.0, 3.9, 6, 24, 40, 20
+    else:
+        a, R, b, q, Np, m, n_p = 0.4, 1.0, 0.35, 4, 5, 40, 30
+    fam = W.petal_family(Np, a, R, {"kind": "hg", "b": b, "q": q}, m, n_p,
+                         int(np.ceil(0.3 * Np * n_p)), m)
+    x, y, w = Q.family_nodes(fam)
+    area, mom = CF.flower_area_moments(a, R, HG(a, b, q))
+    assert abs(w.sum() - area) < 1e-13 * area
+    assert abs(np.sum(w * (x * x + y * y)) - mom) < 1e-13 * mom
+    assert abs(np.sum(w * x)) < 1e-13 * area * R and abs(np.sum(w * y)) < 1e-13 * area * R
+
+
+def test_bspline_profile_partition_of_unity_and_linear_precision():
+    """Clamped cubic B-splines sum to 1 and reproduce r from its Greville abscissae."""
+    a, R, n = 6.0, 14.0, 20
+    r = np.linspace(a, R, 301)
+    one = Q.petal_profile({"kind": "bspline", "coefs": np.ones(n)}, a, R, r)
+    assert np.max(np.abs(one - 1.0)) < 1e-14
+    t = Q.bspline_knots(a, R, n)
+    greville = (t[1:n + 1] + t[2:n + 2] + t[3:n + 3]) / 3.0
+    lin = Q.petal_profile({"kind": "bspline", "coefs": greville}, a, R, r)
+    assert np.max(np.abs(lin - r)) < 1e-13 * R
+    assert t[0] == t[3] == a and t[-1] == t[-4] == R and len(t) == n + 4
+    assert np.allclose(np.diff(t[3:n + 1]), (R - a) / (n - 3))
+
+
+def test_starshade_full_width_petals_make_a_disc():
+    """A = 1 on [a, R]: the petals tile the annulus and the flower is the disc of radius R."""
+    lz = 0.1
+    fam = _small_flower(m=48, n_p=60, n_d=80, m_d=48,
+                        profile={"kind": "bspline", "coefs": np.ones(12)})
+    rho = np.array([0.0, 0.37, 0.8, 1.3])
+    th = np.array([0.3, 1.1, 2.0, -0.7])
+    u = oracle.field([fam], lz, 1.0, rho * np.cos(th), rho * np.sin(th))
+    ref = CF.disc_off_axis(1.0, lz, rho)
+    assert np.max(np.abs(u - ref)) < 1e-11
+
+
+def test_starshade_on_axis_closed_form():
+    lz = 0.05
+    fam = _small_flower(m=64, n_p=20, n_d=80, m_d=64)
+    u = oracle.field([fam], lz, 1.0, [0.0], [0.0])[0]
+    ref = CF.flower_on_axis(0.4, 1.0, HG(0.4, 0.35, 4), lz)
+    assert abs(u - ref) < 1e-11
+
+
+@pytest.mark.parametrize("target", [(0.3, 0.1), (0.9, -0.4), (1.3, 0.6)])
+def test_starshade_brute_force_off_axis(target):
+    """Areal rule vs adaptive 2D integration over the region of eq. Omega."""
+    lz = 0.5
+    u = oracle.field([_small_flower()], lz, 1.0, [target[0]], [target[1]])[0]
+    ref = CF.brute_force_flower(5, 0.4, 1.0, HG(0.4, 0.35, 4), lz, *target)
+    assert abs(u - ref) < 1e-10
+
+
+def test_starshade_rotation_and_translation():
+    lz = 0.07
+    fam = _small_flower()
+    xi, eta = np.array([0.21, 0.83, -0.5]), np.array([0.05, -0.32, 0.61])
+    rot = 2.0 * np.pi / 5
+    u = oracle.field([fam], lz, 1.0, xi, eta)
+    ur = oracle.field([fam], lz, 1.0, np.cos(rot) * xi - np.sin(rot) * eta,
+                      np.sin(rot) * xi + np.cos(rot) * eta)
+    assert np.max(np.abs(u - ur)) < 1e-12
+    ut = oracle.field([_small_flower(cx=0.3, cy=-0.2)], lz, 1.0, xi + 0.3, eta - 0.2)
+    assert np.max(np.abs(u - ut)) < 1e-12
+
+
+def test_planted_starshade_printed_weight_index(monkeypatch):
+    """The literal printed weight r_l what_l A(r_i) omegahat_i (A at the wrong
+    radius) is caught by the area pin."""
+    orig = Q.petal_profile
+
+    def bad(profile, a, R, r):
+        A = orig(profile, a, R, r)
+        return A[np.arange(len(A)) % 7]          # A taken at another radius index
+    fam = _small_flower()
+    area, _ = CF.flower_area_moments(0.4, 1.0, HG(0.4, 0.35, 4))
+    with monkeypatch.context() as mp:
+        mp.setattr(Q, "petal_profile", bad)
+        _, _, w = Q.family_nodes(fam)
+    assert abs(w.sum() - area) > 1e-6
+
+
+def test_planted_petals_off_centre(monkeypatch):
+    """Petals centred half a period off (on pi (2k+1)/Np) fail the brute-force pin."""
+    fam = _small_flower()
+    x, y, w = Q.family_nodes(fam)
+    n_disc = 60 * 40
+    th = np.pi / 5
+    xb, yb = x.copy(), y.copy()
+    xb[n_disc:] = np.cos(th) * x[n_disc:] - np.sin(th) * y[n_disc:]
+    yb[n_disc:] = np.sin(th) * x[n_disc:] + np.cos(th) * y[n_disc:]
+    lz, target = 0.5, (0.9, -0.4)
+    u = D.direct_sum(xb, yb, w, np.array([target[0]]), np.array([target[1]]), lz)[0]
+    ref = CF.brute_force_flower(5, 0.4, 1.0, HG(0.4, 0.35, 4), lz, *target)
+    assert abs(u - ref) > 1e-4
+
+
 # ------------------------------------------------------------------ planted mistakes
 def _pins_fail(monkeypatch, patch):
     """Apply a plausible oracle bug and report whether the closed-form pins notice it."""

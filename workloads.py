@@ -20,6 +20,14 @@ Workloads (Fresnel number F = R^2 / (lambda z), Sec. 2 eq. fn):
                (lambda z = 0.0169), 128 x 16 x 256 = 524,288 nodes;
                grid 1000 x 1000 with h = 0.003, and 1e6 scattered targets
                uniform in the disc of radius 1.5.
+* ``starshade_sweep`` -- 24-petal offset hyper-Gaussian starshade
+               (A(r) = exp(-((r - 6)/3.9)^6) on [6, 14] m, Sec. 4.2), z = 3.7e7 m,
+               64 wavelengths evenly spaced in [400, 1000] nm (F = 13.2 .. 5.3);
+               per wavelength m = max(30, ceil(3F)) radii and n_p = max(15,
+               ceil(1.5F)) angles per petal, n_d = ceil(0.3 * 24 n_p) disc
+               boundary nodes with m_d = m radii (14,040 .. 24,960 nodes);
+               512 x 512 grid with h = 2.4/512 over the 2.4 m pupil, of which
+               the 205,859 points with rho <= 1.2 are kept.
 * ``random_star`` -- r = 1 + sum_{k=1}^{20} a_k cos(k theta + phi_k),
                a_k ~ U(0, 0.02), phi_k ~ U(0, 2 pi); F = 1000 with R = max r
                over 1e5 samples; 640 x 16 x 1024 = 10,485,760 nodes; scattered
@@ -103,6 +111,48 @@ def max_radius(params, n=100000):
     for k in range(1, (len(params) - 1) // 2 + 1):
         r += params[2 * k - 1] * np.cos(k * th) + params[2 * k] * np.sin(k * th)
     return float(r.max())
+
+
+def petal_family(n_petals, a, R, profile, m, n_p, n_d=0, m_d=0, cx=0.0, cy=0.0):
+    """A starshade (disc r < a plus n_petals petals on [a, R]) as a panel family.
+
+    profile: {"kind": "hg", "b": b, "q": q}, {"kind": "bspline", "coefs": [...]}
+    or {"kind": "table", "A": [...]} (A at the m Gauss-Legendre radii).
+    """
+    prof = dict(profile)
+    for key in ("coefs", "A"):
+        if key in prof:
+            prof[key] = np.asarray(prof[key], dtype=np.float64)
+    return {"kind": "petals", "n_petals": int(n_petals), "a": float(a), "R": float(R),
+            "m": int(m), "n_p": int(n_p), "n_d": int(n_d), "m_d": int(m_d),
+            "profile": prof, "cx": float(cx), "cy": float(cy)}
+
+
+HG24 = {"n_petals": 24, "a": 6.0, "R": 14.0, "b": 3.9, "q": 6.0, "z": 3.7e7}
+
+
+def starshade_resolution(fresnel_number, n_petals):
+    """(m, n_p, n_d, m_d) for a starshade at Fresnel number F (workload recipe)."""
+    F = float(fresnel_number)
+    m = max(30, int(np.ceil(3.0 * F)))
+    n_p = max(15, int(np.ceil(1.5 * F)))
+    n_d = int(np.ceil(0.3 * n_petals * n_p))
+    return m, n_p, n_d, m
+
+
+def starshade_sweep(n_lambda=64, lam_lo=400e-9, lam_hi=1000e-9, n=512, pupil=2.4):
+    s = HG24
+    lams = np.linspace(lam_lo, lam_hi, n_lambda)
+    problems = []
+    for lam in lams:
+        F = s["R"] ** 2 / (lam * s["z"])
+        m, n_p, n_d, m_d = starshade_resolution(F, s["n_petals"])
+        fam = petal_family(s["n_petals"], s["a"], s["R"], {"kind": "hg", "b": s["b"], "q": s["q"]},
+                           m, n_p, n_d, m_d)
+        problems.append({"families": [fam], "lam": float(lam), "z": s["z"]})
+    h = pupil / n
+    return {"name": "hg24_sweep%d" % n_lambda, "problems": problems,
+            "grid": grid_spec(n, n, h), "pupil_radius": 0.5 * pupil}
 
 
 def random_star(n_panels=640, p=16, m=1024, fresnel_number=1000.0, config_id=5):
