@@ -65,14 +65,40 @@ typedef enum {
  *     params = [x_1..x_N, y_1..y_N, w_1..w_N] (n_params = 3N); the other
  *     fields are ignored.
  *
+ * FRESNEL_FAMILY_PETALS: a starshade (Sec. 4.2, eq. Omega): the disc r < a
+ *     plus n_panels identical petals; petal k is centred on the angle
+ *     2 pi k / n_panels and its angular width at radius r in (a, R) is
+ *     2 pi A(r) / n_panels.  params = [a, R, n_d, m_d, profile, data...]:
+ *       n_d >= 0  disc boundary nodes (periodic trapezoid rule of eq. ptr,
+ *                 t_i = 2 pi i / n_d), dilated with m_d >= 1 radii (eqs.
+ *                 aqnod, aqwei); n_d = 0 leaves the disc out;
+ *       profile   FRESNEL_PETAL_HG: data = [b, q], A = exp(-((r - a)/b)^q)
+ *                 (the offset hyper-Gaussian, n_params = 7);
+ *                 FRESNEL_PETAL_BSPLINE: data = n >= 4 coefficients of a
+ *                 clamped uniform cubic B-spline on [a, R] (knots a x4, the
+ *                 n - 4 interior points of an (n - 3)-interval uniform mesh,
+ *                 R x4; n_params = 5 + n);
+ *                 FRESNEL_PETAL_TABLE: data = A at the m ascending
+ *                 Gauss-Legendre radii on (a, R) (n_params = 5 + m).
+ *     Each petal has m Gauss-Legendre radii r_l on (a, R) times p
+ *     Gauss-Legendre angles t_i on [-pi/n_panels, pi/n_panels]: node
+ *     r_l (cos th, sin th) with th = A(r_l) t_i + 2 pi k / n_panels, weight
+ *     r_l what_l A(r_l) omegahat_i.  Nodes are ordered disc first
+ *     (boundary-major, radius fastest), then petal, angle, radius fastest:
+ *     N = n_d m_d + n_panels p m.  (cx, cy) translates the whole shape.
+ *     n_d, m_d and profile are whole numbers stored as doubles.  A may be
+ *     negative or exceed 1 (non-ideal profiles); nothing is clamped.
+ *
  * Negative weights and nodes outside Omega (non-star-shaped domains, Sec. 4.1)
  * are accepted as given.  params is a HOST array copied during fresnel_plan.
  */
 enum {
     FRESNEL_FAMILY_FOURIER = 0,
     FRESNEL_FAMILY_LINE_RULE = 1,
-    FRESNEL_FAMILY_NODES = 2
+    FRESNEL_FAMILY_NODES = 2,
+    FRESNEL_FAMILY_PETALS = 3
 };
+enum { FRESNEL_PETAL_HG = 0, FRESNEL_PETAL_BSPLINE = 1, FRESNEL_PETAL_TABLE = 2 };
 
 typedef struct {
     int kind;
@@ -140,7 +166,33 @@ fresnel_status fresnel_plan(const fresnel_family* families, int n_families,
                             fresnel_plan_t* out_plan);
 
 /*
- * Evaluates u at the plan's targets.
+ * A batch of independent problems sharing one target grid, e.g. one
+ * starshade at many wavelengths (the wavelength sweeps of Sec. 4.2): each
+ * problem has its own families (host array) and lambda, z.  Only GRID plans
+ * (opts->target_kind = FRESNEL_GRID) are batched in this build; tol, opts
+ * and the grid are common.  All problems share one spreading kernel and one
+ * FFT size, so one launch per stage serves the whole batch.  Otherwise as
+ * fresnel_plan (which is the one-problem case).
+ */
+typedef struct {
+    const fresnel_family* families;
+    int n_families;
+    double lambda, z;
+} fresnel_problem;
+
+fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems, double tol,
+                                 const fresnel_opts* opts, void* cuda_stream,
+                                 fresnel_plan_t* out_plan);
+
+/*
+ * Evaluates every problem of a plan on its grid: d_out is a DEVICE array of
+ * n_problems * grid_n2 * grid_n1 complex values (problem-major, each problem
+ * as fresnel_eval writes it).  Asynchronous unless opts.sync_status = 1.
+ */
+fresnel_status fresnel_eval_many(fresnel_plan_t plan, void* d_out);
+
+/*
+ * Evaluates u at the plan's targets (plans with one problem).
  * GRID plans: d_targets is ignored (may be NULL) and M must equal n1 * n2.
  * SCATTERED plans: d_targets is a DEVICE array of M (xi, eta) FP64 pairs
  * (interleaved, 16 bytes per target); M >= 0.
@@ -172,7 +224,7 @@ const char* fresnel_last_error(void);
 
 /* ---------------------------------------------------------------- introspection */
 typedef struct {
-    long long n_nodes;      /* N, total quadrature nodes */
+    long long n_nodes;      /* N, total quadrature nodes (over all problems) */
     int w;                  /* spreading kernel width (grid points) */
     double beta;            /* exponential-of-semicircle shape parameter */
     double sigma;           /* upsampling factor used */

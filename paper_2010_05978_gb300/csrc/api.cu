@@ -52,11 +52,17 @@ constexpr long long kBinFromGridBytes = 64LL << 20;
 struct Plan {
     uint64_t magic = kMagic;
     int prec = FRESNEL_FP32_FAST, output = 0, tkind = 0;
-    double lz = 0, tol = 0;
+    double lz = 0, tol = 0;       // lz: the first problem's lambda * z
     cudaStream_t st = nullptr;
     fresnel_opts opts{};
+    int B = 1;                    // independent problems (fresnel_plan_many)
+    std::vector<double> lzs;      // lambda * z per problem
+    std::vector<ChirpParams> cps; // chirp / grid parameters per problem
     std::vector<FamilyDev> fams;
     long long N = 0;
+    FamTable ft{};                // device copies of fams, cps and the block starts
+    int node_blocks = 0;
+    ScanLayout layout{};          // per-problem sort regions (device)
     KernelShape ks{};
     double sigma = 2.0;
     int nf1 = 0, nf2 = 0, nfft1 = 0, nfft2 = 0;
@@ -288,6 +294,38 @@ fresnel_status validate_family(const fresnel_family& f, long long* n_bdry, long 
             *n_bdry = 0;
             *n_nodes = f.n_params / 3;
             return FRESNEL_OK;
+        case FRESNEL_FAMILY_PETALS: {
+            if (f.n_panels < 1 || f.p < 1 || f.m < 1 || f.n_panels > 65536 || f.p > 4096 ||
+                f.m > 65536)
+                return fres_fail(FRESNEL_ERR_ARG,
+                                 "PETALS family needs 1<=n_panels<=65536, 1<=p<=4096, 1<=m<=65536");
+            if (f.n_params < 5)
+                return fres_fail(FRESNEL_ERR_ARG, "PETALS params must be [a, R, n_d, m_d, profile, ...]");
+            const double a = f.params[0], R = f.params[1];
+            const double n_d = f.params[2], m_d = f.params[3], prof = f.params[4];
+            if (!(a >= 0.0) || !(R > a))
+                return fres_fail(FRESNEL_ERR_ARG, "PETALS needs 0 <= a < R");
+            if (n_d != std::floor(n_d) || n_d < 0 || n_d > 1e7 || m_d != std::floor(m_d) ||
+                (n_d > 0 && (m_d < 1 || m_d > 65536)))
+                return fres_fail(FRESNEL_ERR_ARG, "PETALS needs whole n_d in [0, 1e7] and m_d in [1, 65536]");
+            const long long nprof = f.n_params - 5;
+            if (prof == FRESNEL_PETAL_HG) {
+                if (nprof != 2 || !(f.params[5] > 0.0) || !(f.params[6] > 0.0))
+                    return fres_fail(FRESNEL_ERR_ARG, "PETAL_HG profile needs [b > 0, q > 0]");
+            } else if (prof == FRESNEL_PETAL_BSPLINE) {
+                if (nprof < 4 || nprof > (1 << 20))
+                    return fres_fail(FRESNEL_ERR_ARG, "PETAL_BSPLINE profile needs 4 to 2^20 coefficients");
+            } else if (prof == FRESNEL_PETAL_TABLE) {
+                if (nprof != f.m)
+                    return fres_fail(FRESNEL_ERR_ARG, "PETAL_TABLE profile needs m values");
+            } else {
+                return fres_fail(FRESNEL_ERR_ARG, "unknown petal profile");
+            }
+            *K = 0;
+            *n_bdry = (long long)f.p * f.m;
+            *n_nodes = (long long)f.n_panels * f.p * f.m;
+            return FRESNEL_OK;
+        }
         default:
             return fres_fail(FRESNEL_ERR_ARG, "unknown family kind");
     }
@@ -303,28 +341,19 @@ void ev_record(Plan* p, const char* name) {
 
 template <typename T>
 fresnel_status run_nodes(Plan* p, double* dx, double* dy, double* dw) {
-    for (const FamilyDev& f : p->fams) {
-        if (f.kind != FRESNEL_FAMILY_NODES) {
-            launch_boundary(f, p->cp, p->st);
-            p->launches++;
-        }
-        if (f.spoke && !dx)   // FP32 fast mode: double-float spoke form, no FP64 per node
-            launch_nodes_count_df(f, p->cp, (NodeRec<float>*)p->rec, p->counts, p->status, p->st);
-        else
-            launch_nodes_count<T>(f, p->cp, (NodeRec<T>*)p->rec, p->counts, dx, dy, dw,
-                                  p->status, p->st);
-        p->launches++;
-    }
+    launch_nodes<T>(p->ft, p->node_blocks, (NodeRec<T>*)p->rec, p->counts, dx, dy, dw, p->status,
+                    p->st);
+    p->launches++;
     return FRESNEL_OK;
 }
 
 template <typename T>
 fresnel_status run_sort(Plan* p) {
-    launch_scan_chunks(p->ntiles, p->counts, p->cursor, p->chunks, p->n_meta, p->split_tiles,
-                       p->chunk_cap, p->max_chunks, p->max_split, p->st);
+    launch_scan_problems(p->B, p->ntiles, p->counts, p->cursor, p->chunks, p->split_tiles,
+                         p->layout, p->chunk_cap, p->status, p->st);
     ev_record(p, "scan");
-    launch_scatter<T>(p->N, p->cp, (const NodeRec<T>*)p->rec, p->cursor, (NodeRec<T>*)p->sorted,
-                      p->n_records, p->status, p->st);
+    launch_scatter_fams<T>(p->ft, p->node_blocks, (const NodeRec<T>*)p->rec, p->cursor,
+                           (NodeRec<T>*)p->sorted, p->n_records, p->status, p->st);
     p->launches += 2;
     return FRESNEL_OK;
 }
@@ -343,7 +372,7 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
     }
     launch_spread<T>((const NodeRec<T>*)p->sorted, p->chunks, p->n_meta, p->max_chunks,
                      p->split_tiles, p->max_split, (cx_t<T>*)p->grid, p->work, p->nf1, p->nf2,
-                     p->ntx, p->ks, p->spread_blocks, p->st);
+                     p->ntx, p->ntiles, p->ks, p->spread_blocks, p->st);
     p->launches += p->max_split > 0 ? 2 : 1;
     ev_record(p, "spread");
     if (p->tkind == FRESNEL_GRID) {
@@ -352,11 +381,14 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ra.out = p->inter;
         ra.in_stride = p->nf1;
         ra.out_stride = p->n1;
-        ra.nrows = p->nf2;
+        ra.nrows = p->nf2 * p->B;
         ra.in_len = p->nf1;
         ra.centered_in = 0;
         ra.out_len = p->n1;
         ra.twiddle = p->tw1;
+        ra.live = p->layout.live;
+        ra.batch_rows = p->nf2;
+        ra.nty = p->nty;
         launch_fft_rows<T>(p->fp1, ra, p->st);
         ev_record(p, "fft_rows");
         ColPassArgs ca{};
@@ -371,6 +403,11 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ca.ay = p->ay;
         ca.occulter = p->output == FRESNEL_OCCULTER;
         ca.out_is_final = 1;
+        ca.batch = p->B;
+        ca.in_bstride = (long long)p->nf2 * p->n1;
+        ca.out_bstride = (long long)p->n2 * p->n1;
+        ca.live = p->layout.live;
+        ca.nty = p->nty;
         launch_fft_cols<T>(p->fp2, ca, p->st);
         ev_record(p, "fft_cols_epilogue");
         p->launches += 2;
@@ -443,20 +480,137 @@ fresnel_status read_status(Plan* p) {
         if (h & kStatusTargetOutside) msg += " target outside the plan's box;";
         if (h & kStatusNodeOutside) msg += " node support outside the type-3 grid;";
         if (h & kStatusNonFinite) msg += " non-finite coordinate;";
+        if (h & kStatusOverflow) msg += " sort region overflow;";
         return fres_fail(FRESNEL_ERR_DEVICE, msg);
     }
     return FRESNEL_OK;
 }
 
+struct Bounds {
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    void add(double x, double y) {
+        xmin = std::min(xmin, x);
+        xmax = std::max(xmax, x);
+        ymin = std::min(ymin, y);
+        ymax = std::max(ymax, y);
+    }
+};
+
+fresnel_status copy_params(Plan* p, FamilyDev& f, const double* hparams, long long n) {
+    FRES_TRY(dalloc(p, (void**)&f.params, sizeof(double) * n));
+    FRES_CK(cudaMemcpyAsync(f.params, hparams, sizeof(double) * n, cudaMemcpyHostToDevice, p->st));
+    return FRESNEL_OK;
+}
+
 template <typename T>
-fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_families) {
+fresnel_status setup_nodes_family(Plan* p, FamilyDev& f, const double* hparams, long long n,
+                                  Bounds& bb) {
+    FRES_TRY(copy_params(p, f, hparams, n));
+    for (long long j = 0; j < f.n_nodes; ++j) bb.add(hparams[j], hparams[f.n_nodes + j]);
+    return FRESNEL_OK;
+}
+
+// Device params, Gauss-Legendre rules and boundary line rule of a family
+// used through the dilation rule (FOURIER, LINE_RULE, a starshade's disc),
+// and the bounds of its nodes.
+template <typename T>
+fresnel_status setup_dilation_family(Plan* p, FamilyDev& f, const double* hparams, long long n,
+                                     Bounds& bb) {
+    const bool dbl = sizeof(T) == 8;
+    const long long nb = f.n_bdry;
+    FRES_TRY(copy_params(p, f, hparams, n));
+    if (f.kind == FRESNEL_FAMILY_FOURIER && !f.ptr) {
+        FRES_TRY(dalloc(p, (void**)&f.gl_p_t, sizeof(double) * f.p));
+        FRES_TRY(dalloc(p, (void**)&f.gl_p_w, sizeof(double) * f.p));
+        launch_gauss_legendre(f.p, f.gl_p_t, f.gl_p_w, p->st);
+    }
+    FRES_TRY(dalloc(p, (void**)&f.gl_m_a, sizeof(double) * f.m));
+    FRES_TRY(dalloc(p, (void**)&f.gl_m_aw, sizeof(double) * f.m));
+    launch_gauss_legendre(f.m, f.gl_m_a, f.gl_m_aw, p->st);
+    // alpha_l * wtilde_l (eq. aqwei) formed on the host from the device rule
+    std::vector<double> a(f.m), w(f.m);
+    FRES_CK(cudaMemcpyAsync(a.data(), f.gl_m_a, sizeof(double) * f.m, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaMemcpyAsync(w.data(), f.gl_m_aw, sizeof(double) * f.m, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    for (int l = 0; l < f.m; ++l) w[l] *= a[l];
+    FRES_CK(cudaMemcpyAsync(f.gl_m_aw, w.data(), sizeof(double) * f.m, cudaMemcpyHostToDevice, p->st));
+    FRES_TRY(dalloc(p, (void**)&f.bx, sizeof(double) * nb));
+    FRES_TRY(dalloc(p, (void**)&f.by, sizeof(double) * nb));
+    FRES_TRY(dalloc(p, (void**)&f.bc, sizeof(double) * nb));
+    if (!dbl) {   // double-float radial rule for the FP32 spoke form
+        std::vector<float> adf(2 * f.m), awf(f.m);
+        for (int l = 0; l < f.m; ++l) {
+            dflt s = df_host(a[l]);
+            adf[2 * l] = s.hi;
+            adf[2 * l + 1] = s.lo;
+            awf[l] = (float)w[l];
+        }
+        FRES_TRY(dalloc(p, (void**)&f.adf, sizeof(float) * 2 * f.m));
+        FRES_TRY(dalloc(p, (void**)&f.awf, sizeof(float) * f.m));
+        FRES_CK(cudaMemcpyAsync(f.adf, adf.data(), sizeof(float) * 2 * f.m, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaMemcpyAsync(f.awf, awf.data(), sizeof(float) * f.m, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaStreamSynchronize(p->st));
+    }
+    launch_boundary(f, p->cp, p->st);
+    // node bounds (type 3 sizing): nodes lie on segments from the centre to
+    // the boundary nodes, so centre + boundary bounds them.
+    std::vector<double> bx(nb), by(nb);
+    FRES_CK(cudaMemcpyAsync(bx.data(), f.bx, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaMemcpyAsync(by.data(), f.by, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    bb.add(f.cx, f.cy);
+    for (long long i = 0; i < nb; ++i) bb.add(f.cx + bx[i], f.cy + by[i]);
+    return FRESNEL_OK;
+}
+
+// Petal tables of a starshade family (Sec. 4.2) and the bounds of its nodes.
+fresnel_status setup_petal_family(Plan* p, FamilyDev& f, const fresnel_family& hf, Bounds& bb) {
+    const long long nb = f.n_bdry;
+    FRES_TRY(copy_params(p, f, hf.params, hf.n_params));
+    f.pa = hf.params[0];
+    f.pR = hf.params[1];
+    f.profile = (int)hf.params[4];
+    f.n_prof = hf.n_params - 5;
+    FRES_TRY(dalloc(p, (void**)&f.gl_p_t, sizeof(double) * f.p));
+    FRES_TRY(dalloc(p, (void**)&f.gl_p_w, sizeof(double) * f.p));
+    launch_gauss_legendre(f.p, f.gl_p_t, f.gl_p_w, p->st);
+    FRES_TRY(dalloc(p, (void**)&f.gl_m_a, sizeof(double) * f.m));
+    FRES_TRY(dalloc(p, (void**)&f.gl_m_aw, sizeof(double) * f.m));
+    launch_gauss_legendre(f.m, f.gl_m_a, f.gl_m_aw, p->st);
+    FRES_TRY(dalloc(p, (void**)&f.bx, sizeof(double) * nb));
+    FRES_TRY(dalloc(p, (void**)&f.by, sizeof(double) * nb));
+    FRES_TRY(dalloc(p, (void**)&f.bc, sizeof(double) * nb));
+    FRES_TRY(dalloc(p, (void**)&f.rot, sizeof(double) * 2 * f.n_panels));
+    launch_boundary(f, p->cp, p->st);
+    std::vector<double> u(nb), v(nb), rot(2 * f.n_panels);
+    FRES_CK(cudaMemcpyAsync(u.data(), f.bx, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaMemcpyAsync(v.data(), f.by, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaMemcpyAsync(rot.data(), f.rot, sizeof(double) * 2 * f.n_panels,
+                            cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    FRES_CK(cudaGetLastError());
+    for (long long q = 0; q < nb; ++q) {
+        if (!std::isfinite(u[q]) || !std::isfinite(v[q]))
+            return fres_fail(FRESNEL_ERR_ARG, "petal profile gives a non-finite node");
+        for (int k = 0; k < f.n_panels; ++k) {
+            const double c = rot[2 * k], s = rot[2 * k + 1];
+            bb.add(f.cx + u[q] * c - v[q] * s, f.cy + u[q] * s + v[q] * c);
+        }
+    }
+    return FRESNEL_OK;
+}
+
+template <typename T>
+fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     const bool dbl = sizeof(T) == 8;
     // ---------------- families: device copies, Gauss-Legendre rules, boundary rules
     long long off = 0;
-    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-    for (int fi = 0; fi < n_families; ++fi) {
-        const fresnel_family& hf = families[fi];
+    Bounds bb;
+    for (int pb = 0; pb < p->B; ++pb)
+    for (int fi = 0; fi < problems[pb].n_families; ++fi) {
+        const fresnel_family& hf = problems[pb].families[fi];
         FamilyDev f{};
+        f.prob = pb;
         long long nb = 0, nn = 0;
         int K = 0;
         FRES_TRY(validate_family(hf, &nb, &nn, &K));
@@ -467,75 +621,43 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
         f.K = K;
         f.n_bdry = nb;
         f.n_nodes = nn;
-        f.offset = off;
         f.cx = hf.kind == FRESNEL_FAMILY_NODES ? 0.0 : hf.cx;
         f.cy = hf.kind == FRESNEL_FAMILY_NODES ? 0.0 : hf.cy;
-        off += nn;
-        FRES_TRY(dalloc(p, (void**)&f.params, sizeof(double) * hf.n_params));
-        FRES_CK(cudaMemcpyAsync(f.params, hf.params, sizeof(double) * hf.n_params,
-                                cudaMemcpyHostToDevice, p->st));
         if (hf.kind == FRESNEL_FAMILY_NODES) {
-            for (long long j = 0; j < nn; ++j) {
-                xmin = std::min(xmin, hf.params[j]);
-                xmax = std::max(xmax, hf.params[j]);
-                ymin = std::min(ymin, hf.params[nn + j]);
-                ymax = std::max(ymax, hf.params[nn + j]);
+            f.offset = off;
+            off += nn;
+            FRES_TRY(setup_nodes_family<T>(p, f, hf.params, hf.n_params, bb));
+        } else if (hf.kind == FRESNEL_FAMILY_PETALS) {
+            // the disc r < a: a FOURIER circle on the periodic trapezoid rule
+            const int n_d = (int)hf.params[2], m_d = (int)hf.params[3];
+            if (n_d > 0) {
+                FamilyDev d{};
+                d.prob = pb;
+                d.kind = FRESNEL_FAMILY_FOURIER;
+                d.ptr = 1;
+                d.n_panels = n_d;
+                d.p = 1;
+                d.m = m_d;
+                d.n_bdry = n_d;
+                d.n_nodes = (long long)n_d * m_d;
+                d.cx = hf.cx;
+                d.cy = hf.cy;
+                d.offset = off;
+                off += d.n_nodes;
+                FRES_TRY(setup_dilation_family<T>(p, d, hf.params, 1, bb));
+                p->fams.push_back(d);
             }
+            f.offset = off;
+            off += nn;
+            FRES_TRY(setup_petal_family(p, f, hf, bb));
         } else {
-            if (hf.kind == FRESNEL_FAMILY_FOURIER) {
-                FRES_TRY(dalloc(p, (void**)&f.gl_p_t, sizeof(double) * f.p));
-                FRES_TRY(dalloc(p, (void**)&f.gl_p_w, sizeof(double) * f.p));
-                launch_gauss_legendre(f.p, f.gl_p_t, f.gl_p_w, p->st);
-            }
-            FRES_TRY(dalloc(p, (void**)&f.gl_m_a, sizeof(double) * f.m));
-            FRES_TRY(dalloc(p, (void**)&f.gl_m_aw, sizeof(double) * f.m));
-            launch_gauss_legendre(f.m, f.gl_m_a, f.gl_m_aw, p->st);
-            // alpha_l * wtilde_l (eq. aqwei) formed on the host from the device rule
-            std::vector<double> a(f.m), w(f.m);
-            FRES_CK(cudaMemcpyAsync(a.data(), f.gl_m_a, sizeof(double) * f.m, cudaMemcpyDeviceToHost, p->st));
-            FRES_CK(cudaMemcpyAsync(w.data(), f.gl_m_aw, sizeof(double) * f.m, cudaMemcpyDeviceToHost, p->st));
-            FRES_CK(cudaStreamSynchronize(p->st));
-            for (int l = 0; l < f.m; ++l) w[l] *= a[l];
-            FRES_CK(cudaMemcpyAsync(f.gl_m_aw, w.data(), sizeof(double) * f.m, cudaMemcpyHostToDevice, p->st));
-            FRES_TRY(dalloc(p, (void**)&f.bx, sizeof(double) * nb));
-            FRES_TRY(dalloc(p, (void**)&f.by, sizeof(double) * nb));
-            FRES_TRY(dalloc(p, (void**)&f.bc, sizeof(double) * nb));
-            if (!dbl) {   // double-float radial rule for the FP32 spoke form
-                std::vector<float> adf(2 * f.m), awf(f.m);
-                for (int l = 0; l < f.m; ++l) {
-                    dflt s = df_host(a[l]);
-                    adf[2 * l] = s.hi;
-                    adf[2 * l + 1] = s.lo;
-                    awf[l] = (float)w[l];
-                }
-                FRES_TRY(dalloc(p, (void**)&f.adf, sizeof(float) * 2 * f.m));
-                FRES_TRY(dalloc(p, (void**)&f.awf, sizeof(float) * f.m));
-                FRES_CK(cudaMemcpyAsync(f.adf, adf.data(), sizeof(float) * 2 * f.m,
-                                        cudaMemcpyHostToDevice, p->st));
-                FRES_CK(cudaMemcpyAsync(f.awf, awf.data(), sizeof(float) * f.m,
-                                        cudaMemcpyHostToDevice, p->st));
-                FRES_CK(cudaStreamSynchronize(p->st));
-            }
-            launch_boundary(f, p->cp, p->st);
-            // node bounding box (type 3 sizing): nodes lie on segments from the
-            // centre to the boundary nodes, so centre + boundary bounds them.
-            std::vector<double> bx(nb), by(nb);
-            FRES_CK(cudaMemcpyAsync(bx.data(), f.bx, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
-            FRES_CK(cudaMemcpyAsync(by.data(), f.by, sizeof(double) * nb, cudaMemcpyDeviceToHost, p->st));
-            FRES_CK(cudaStreamSynchronize(p->st));
-            xmin = std::min(xmin, f.cx);
-            xmax = std::max(xmax, f.cx);
-            ymin = std::min(ymin, f.cy);
-            ymax = std::max(ymax, f.cy);
-            for (long long i = 0; i < nb; ++i) {
-                xmin = std::min(xmin, f.cx + bx[i]);
-                xmax = std::max(xmax, f.cx + bx[i]);
-                ymin = std::min(ymin, f.cy + by[i]);
-                ymax = std::max(ymax, f.cy + by[i]);
-            }
+            f.offset = off;
+            off += nn;
+            FRES_TRY(setup_dilation_family<T>(p, f, hf.params, hf.n_params, bb));
         }
         p->fams.push_back(f);
     }
+    const double xmin = bb.xmin, xmax = bb.xmax, ymin = bb.ymin, ymax = bb.ymax;
     p->N = off;
     if (p->N < 1) return fres_fail(FRESNEL_ERR_ARG, "the quadrature has no nodes");
     if (p->N > (1LL << 30)) return fres_fail(FRESNEL_ERR_UNSUPPORTED, "more than 2^30 nodes");
@@ -632,15 +754,60 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
     p->ntiles = p->ntx * p->nty;
     p->cp.ntx = p->ntx;
     p->cp.nty = p->nty;
+    p->cp.tile_base = 0;
     p->chunk_cap = dbl ? 256 : 512;
+    if ((long long)p->B * p->ntiles >= (1LL << 31) ||
+        (long long)p->B * p->nf1 * p->nf2 >= (1LL << 40))
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "batch too large");
+    // per-problem chirp parameters: the grid is common, lambda z is not
+    p->cps.assign(p->B, p->cp);
+    for (int b = 0; b < p->B; ++b) {
+        ChirpParams& c = p->cps[b];
+        const double lzb = p->lzs[b];
+        c.tile_base = b * p->ntiles;
+        if (p->tkind == FRESNEL_GRID) {
+            c.kq = kPi / lzb;
+            c.u1 = p->opts.grid_h / lzb;
+            c.u2 = p->opts.grid_h / lzb;
+            c.a1 = kTwoPi * p->opts.grid_x0 / lzb;
+            c.a2 = kTwoPi * p->opts.grid_y0 / lzb;
+        }
+    }
 
     // ---------------- FP32 fast mode: spoke coefficients and family constants
     if (!dbl) {
-        const ChirpParams& cp = p->cp;
         for (FamilyDev& f : p->fams) {
+            const ChirpParams& cp = p->cps[f.prob];
             if (f.kind == FRESNEL_FAMILY_NODES) continue;
-            FRES_TRY(dalloc(p, (void**)&f.spoke, sizeof(float) * 8 * f.n_bdry));
-            FRES_TRY(dalloc(p, (void**)&f.bcf, sizeof(float) * f.n_bdry));
+            if (f.kind == FRESNEL_FAMILY_PETALS) {
+                FRES_TRY(dalloc(p, (void**)&f.ptab, sizeof(float) * 8 * f.n_bdry));
+                FRES_TRY(dalloc(p, (void**)&f.pk, sizeof(float) * 12 * f.n_panels));
+                // per-petal slopes: phase E.d with E = 2 kq c - a, grid U d
+                std::vector<double> rot(2 * f.n_panels);
+                FRES_CK(cudaMemcpyAsync(rot.data(), f.rot, sizeof(double) * 2 * f.n_panels,
+                                        cudaMemcpyDeviceToHost, p->st));
+                FRES_CK(cudaStreamSynchronize(p->st));
+                const double E1 = 2.0 * cp.kq * f.cx - cp.a1, E2 = 2.0 * cp.kq * f.cy - cp.a2;
+                const double U1 = cp.type3 ? cp.inv_h1 : (double)cp.nf1 * cp.u1;
+                const double U2 = cp.type3 ? cp.inv_h2 : (double)cp.nf2 * cp.u2;
+                std::vector<float> pk(12 * f.n_panels);
+                for (int k = 0; k < f.n_panels; ++k) {
+                    const double c = rot[2 * k], sn = rot[2 * k + 1];
+                    const double vals[6] = {c * E1 + sn * E2, c * E2 - sn * E1, c * U1,
+                                            -sn * U1, sn * U2, c * U2};
+                    for (int v = 0; v < 6; ++v) {
+                        const dflt d = df_host(vals[v]);
+                        pk[12 * k + 2 * v] = d.hi;
+                        pk[12 * k + 2 * v + 1] = d.lo;
+                    }
+                }
+                FRES_CK(cudaMemcpyAsync(f.pk, pk.data(), sizeof(float) * 12 * f.n_panels,
+                                        cudaMemcpyHostToDevice, p->st));
+                FRES_CK(cudaStreamSynchronize(p->st));
+            } else {
+                FRES_TRY(dalloc(p, (void**)&f.spoke, sizeof(float) * 8 * f.n_bdry));
+                FRES_TRY(dalloc(p, (void**)&f.bcf, sizeof(float) * f.n_bdry));
+            }
             const double A0 = cp.kq * (f.cx * f.cx + f.cy * f.cy) - cp.a1 * f.cx - cp.a2 * f.cy + cp.a0;
             double G0x, G0y;
             if (!cp.type3) {
@@ -657,44 +824,124 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
             f.G0x[1] = gx.lo;
             f.G0y[0] = gy.hi;
             f.G0y[1] = gy.lo;
+            launch_boundary(f, cp, p->st);   // spoke coefficients, once per plan
         }
+    }
+
+    // ---------------- family table for the node and scatter launches
+    {
+        const int nfam = (int)p->fams.size();
+        std::vector<int> blk0(nfam + 1, 0);
+        for (int i = 0; i < nfam; ++i) {
+            const long long nb = (p->fams[i].n_nodes + kNodeThreads - 1) / kNodeThreads;
+            if ((long long)blk0[i] + nb >= (1LL << 31))
+                return fres_fail(FRESNEL_ERR_UNSUPPORTED, "too many nodes for one launch");
+            blk0[i + 1] = blk0[i] + (int)nb;
+        }
+        FamilyDev* d_f = nullptr;
+        ChirpParams* d_c = nullptr;
+        int* d_b = nullptr;
+        FRES_TRY(dalloc(p, (void**)&d_f, sizeof(FamilyDev) * nfam));
+        FRES_TRY(dalloc(p, (void**)&d_c, sizeof(ChirpParams) * p->B));
+        FRES_TRY(dalloc(p, (void**)&d_b, sizeof(int) * (nfam + 1)));
+        FRES_CK(cudaMemcpyAsync(d_f, p->fams.data(), sizeof(FamilyDev) * nfam, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaMemcpyAsync(d_c, p->cps.data(), sizeof(ChirpParams) * p->B, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaMemcpyAsync(d_b, blk0.data(), sizeof(int) * (nfam + 1), cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaStreamSynchronize(p->st));
+        p->ft.fams = d_f;
+        p->ft.cps = d_c;
+        p->ft.blk0 = d_b;
+        p->ft.nfam = nfam;
+        p->node_blocks = blk0[nfam];
     }
 
     // ---------------- node pass once: exact record / chunk / slot counts
     FRES_TRY(dalloc(p, (void**)&p->status, sizeof(unsigned)));
     FRES_CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->st));
     FRES_TRY(dalloc(p, &p->rec, p->rsize() * p->N));
-    FRES_TRY(dalloc(p, (void**)&p->counts, sizeof(int) * p->ntiles));
-    FRES_TRY(dalloc(p, (void**)&p->cursor, sizeof(int) * p->ntiles));
+    const long long tt = (long long)p->B * p->ntiles;
+    FRES_TRY(dalloc(p, (void**)&p->counts, sizeof(int) * tt));
+    FRES_TRY(dalloc(p, (void**)&p->cursor, sizeof(int) * tt));
     FRES_TRY(dalloc(p, (void**)&p->work, 2 * sizeof(int)));
-    FRES_CK(cudaMemsetAsync(p->counts, 0, sizeof(int) * p->ntiles, p->st));
+    FRES_CK(cudaMemsetAsync(p->counts, 0, sizeof(int) * tt, p->st));
     FRES_CK(cudaMemsetAsync(p->work, 0, 2 * sizeof(int), p->st));
     FRES_TRY(run_nodes<T>(p, nullptr, nullptr, nullptr));
-    std::vector<int> hc(p->ntiles);
-    FRES_CK(cudaMemcpyAsync(hc.data(), p->counts, sizeof(int) * p->ntiles, cudaMemcpyDeviceToHost, p->st));
+    std::vector<int> hc(tt);
+    FRES_CK(cudaMemcpyAsync(hc.data(), p->counts, sizeof(int) * tt, cudaMemcpyDeviceToHost, p->st));
     FRES_CK(cudaStreamSynchronize(p->st));
     FRES_CK(cudaGetLastError());
-    long long nrec = 0, nch = 0, nsplit = 0;
-    for (int c : hc) {
-        long long k = c > p->chunk_cap ? (c + p->chunk_cap - 1) / p->chunk_cap : 1;
-        nrec += c;
-        nch += k;
-        if (k > 1) ++nsplit;
+    // per-problem regions: every problem's split chunks, then its plain tiles
+    std::vector<int> sc_off(p->B + 1, 0), pl_off(p->B + 1, 0), st_off(p->B + 1, 0);
+    std::vector<long long> rec_off(p->B + 1, 0);
+    // type 1: tile rows without records are neither spread nor transformed
+    const bool prune = p->tkind == FRESNEL_GRID;
+    if (p->nty > kMaxTileRows) return fres_fail(FRESNEL_ERR_UNSUPPORTED, "spreading grid too tall");
+    for (int b = 0; b < p->B; ++b) {
+        long long nrec = 0, nsc = 0, nsplit = 0, nlive = 0;
+        std::vector<char> live(p->nty, prune ? 0 : 1);
+        for (int i = 0; i < p->ntiles; ++i)
+            if (hc[(size_t)b * p->ntiles + i] > 0) live[i / p->ntx] = 1;
+        for (int r = 0; r < p->nty; ++r) nlive += live[r] ? p->ntx : 0;
+        for (int i = 0; i < p->ntiles; ++i) {
+            const int c = hc[(size_t)b * p->ntiles + i];
+            nrec += c;
+            if (c > p->chunk_cap) {
+                nsc += (c + p->chunk_cap - 1) / p->chunk_cap;
+                ++nsplit;
+            }
+        }
+        if (sc_off[b] + nsc + (long long)p->B * p->ntiles >= (1LL << 31) ||
+            rec_off[b] + nrec >= (1LL << 31))
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "more than 2^31 records or chunks");
+        sc_off[b + 1] = sc_off[b] + (int)nsc;
+        st_off[b + 1] = st_off[b] + (int)nsplit;
+        pl_off[b + 1] = pl_off[b] + (int)(nlive - nsplit);
+        rec_off[b + 1] = rec_off[b] + nrec;
     }
-    p->n_records = nrec;
-    p->max_chunks = (int)nch;
-    p->max_split = (int)nsplit;
-    FRES_TRY(dalloc(p, &p->sorted, p->rsize() * std::max(1LL, nrec)));
+    for (int b = 0; b <= p->B; ++b) pl_off[b] += sc_off[p->B];
+    p->n_records = rec_off[p->B];
+    p->max_chunks = pl_off[p->B];
+    p->max_split = st_off[p->B];
+    FRES_TRY(dalloc(p, &p->sorted, p->rsize() * std::max(1LL, p->n_records)));
     FRES_TRY(dalloc(p, (void**)&p->chunks, sizeof(Chunk) * p->max_chunks));
     FRES_TRY(dalloc(p, (void**)&p->n_meta, 2 * sizeof(int)));
-    FRES_TRY(dalloc(p, (void**)&p->split_tiles, sizeof(int) * std::max(1LL, nsplit)));
+    FRES_TRY(dalloc(p, (void**)&p->split_tiles, sizeof(int) * std::max(1, p->max_split)));
+    {
+        int* d_sc = nullptr;
+        int* d_pl = nullptr;
+        int* d_st = nullptr;
+        long long* d_ro = nullptr;
+        const size_t nb1 = (size_t)p->B + 1;
+        FRES_TRY(dalloc(p, (void**)&d_sc, sizeof(int) * nb1));
+        FRES_TRY(dalloc(p, (void**)&d_pl, sizeof(int) * nb1));
+        FRES_TRY(dalloc(p, (void**)&d_st, sizeof(int) * nb1));
+        FRES_TRY(dalloc(p, (void**)&d_ro, sizeof(long long) * nb1));
+        FRES_CK(cudaMemcpyAsync(d_sc, sc_off.data(), sizeof(int) * nb1, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaMemcpyAsync(d_pl, pl_off.data(), sizeof(int) * nb1, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaMemcpyAsync(d_st, st_off.data(), sizeof(int) * nb1, cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaMemcpyAsync(d_ro, rec_off.data(), sizeof(long long) * nb1, cudaMemcpyHostToDevice, p->st));
+        const int meta[2] = {p->max_chunks, p->max_split};
+        FRES_CK(cudaMemcpyAsync(p->n_meta, meta, sizeof(meta), cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaStreamSynchronize(p->st));
+        p->layout.sc_off = d_sc;
+        p->layout.pl_off = d_pl;
+        p->layout.st_off = d_st;
+        p->layout.rec_off = d_ro;
+        p->layout.ntx = p->ntx;
+        p->layout.nty = p->nty;
+        p->layout.live = nullptr;
+        if (prune) {
+            FRES_TRY(dalloc(p, (void**)&p->layout.live, sizeof(int) * p->nty * (size_t)p->B));
+            FRES_CK(cudaMemsetAsync(p->layout.live, 0, sizeof(int) * p->nty * (size_t)p->B, p->st));
+        }
+    }
     FRES_TRY(run_sort<T>(p));
     p->nodes_ready = true;
     p->spread_blocks = 152 * 8;
 
     // ---------------- grids and tables
     const size_t cs = p->csize();
-    FRES_TRY(dalloc(p, &p->grid, cs * (size_t)p->nf1 * p->nf2));
+    FRES_TRY(dalloc(p, &p->grid, cs * (size_t)p->nf1 * p->nf2 * p->B));
     // kernel-transform quadrature: Gauss-Legendre on (0,1) with 2w + 16 points
     p->gq_n = std::min(64, 2 * w + 16);
     FRES_TRY(dalloc(p, (void**)&p->gq_t, sizeof(double) * p->gq_n));
@@ -709,13 +956,17 @@ fresnel_status build_plan(Plan* p, const fresnel_family* families, int n_familie
         p->tw2 = p->tw1;
     }
     if (p->tkind == FRESNEL_GRID) {
-        FRES_TRY(dalloc(p, &p->inter, cs * (size_t)p->nf2 * p->n1));
-        FRES_TRY(dalloc(p, &p->ax, cs * p->n1));
-        FRES_TRY(dalloc(p, &p->ay, cs * p->n2));
-        launch_t1_tables(p->n1, p->nf1, p->opts.grid_h, p->opts.grid_x0, lz, w, p->ks.beta, 1,
-                         p->ax, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
-        launch_t1_tables(p->n2, p->nf2, p->opts.grid_h, p->opts.grid_y0, lz, w, p->ks.beta, 0,
-                         p->ay, dbl, p->gq_t, p->gq_w, p->gq_n, p->st);
+        FRES_TRY(dalloc(p, &p->inter, cs * (size_t)p->nf2 * p->n1 * p->B));
+        FRES_TRY(dalloc(p, &p->ax, cs * p->n1 * p->B));
+        FRES_TRY(dalloc(p, &p->ay, cs * p->n2 * p->B));
+        for (int b = 0; b < p->B; ++b) {   // per problem: the chirp depends on lambda z
+            launch_t1_tables(p->n1, p->nf1, p->opts.grid_h, p->opts.grid_x0, p->lzs[b], w,
+                             p->ks.beta, 1, (char*)p->ax + cs * p->n1 * b, dbl, p->gq_t, p->gq_w,
+                             p->gq_n, p->st);
+            launch_t1_tables(p->n2, p->nf2, p->opts.grid_h, p->opts.grid_y0, p->lzs[b], w,
+                             p->ks.beta, 0, (char*)p->ay + cs * p->n2 * b, dbl, p->gq_t, p->gq_w,
+                             p->gq_n, p->st);
+        }
     } else {
         FRES_TRY(dalloc(p, &p->inter, cs * (size_t)p->nf2 * p->nfft1));
         FRES_TRY(dalloc(p, &p->F, cs * (size_t)p->nfft2 * p->nfft1));
@@ -787,16 +1038,22 @@ void fresnel_default_opts(fresnel_opts* o) {
     o->sync_status = 1;
 }
 
-fresnel_status fresnel_plan(const fresnel_family* families, int n_families, double lambda,
-                            double z, double tol, const fresnel_opts* opts, void* cuda_stream,
-                            fresnel_plan_t* out_plan) {
+fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems, double tol,
+                                 const fresnel_opts* opts, void* cuda_stream,
+                                 fresnel_plan_t* out_plan) {
     if (!out_plan) return fres_fail(FRESNEL_ERR_ARG, "out_plan is NULL");
     *out_plan = nullptr;
-    if (!families || n_families < 1) return fres_fail(FRESNEL_ERR_ARG, "no families");
+    if (!problems || n_problems < 1) return fres_fail(FRESNEL_ERR_ARG, "no problems");
+    if (n_problems > (1 << 20)) return fres_fail(FRESNEL_ERR_UNSUPPORTED, "more than 2^20 problems");
+    for (int b = 0; b < n_problems; ++b) {
+        const fresnel_problem& q = problems[b];
+        if (!q.families || q.n_families < 1) return fres_fail(FRESNEL_ERR_ARG, "no families");
+        const double lambda = q.lambda, z = q.z;
+        if (!(lambda > 0) || !(z > 0) || !std::isfinite(lambda) || !std::isfinite(z) ||
+            !std::isfinite(lambda * z) || !(lambda * z > 0))
+            return fres_fail(FRESNEL_ERR_ARG, "lambda and z must be finite and > 0");
+    }
     if (!opts) return fres_fail(FRESNEL_ERR_ARG, "opts is NULL");
-    if (!(lambda > 0) || !(z > 0) || !std::isfinite(lambda) || !std::isfinite(z) ||
-        !std::isfinite(lambda * z) || !(lambda * z > 0))
-        return fres_fail(FRESNEL_ERR_ARG, "lambda and z must be finite and > 0");
     if (!(tol >= 1e-14 && tol <= 1e-1)) return fres_fail(FRESNEL_ERR_ARG, "tol must lie in [1e-14, 1e-1]");
     if (opts->precision != FRESNEL_FP64 && opts->precision != FRESNEL_FP32_FAST)
         return fres_fail(FRESNEL_ERR_ARG, "unknown precision");
@@ -814,6 +1071,8 @@ fresnel_status fresnel_plan(const fresnel_family* families, int n_families, doub
         for (int i = 0; i < 4; ++i)
             if (!std::isfinite(b[i])) return fres_fail(FRESNEL_ERR_ARG, "box must be finite");
         if (!(b[0] <= b[1]) || !(b[2] <= b[3])) return fres_fail(FRESNEL_ERR_ARG, "box must have min <= max");
+        if (n_problems > 1)
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "batched plans take GRID targets only");
     } else {
         return fres_fail(FRESNEL_ERR_ARG, "unknown target_kind");
     }
@@ -829,12 +1088,14 @@ fresnel_status fresnel_plan(const fresnel_family* families, int n_families, doub
     p->prec = opts->precision;
     p->output = opts->output;
     p->tkind = opts->target_kind;
-    p->lz = lambda * z;
+    p->B = n_problems;
+    for (int b = 0; b < n_problems; ++b) p->lzs.push_back(problems[b].lambda * problems[b].z);
+    p->lz = p->lzs[0];
     p->tol = tol;
     p->st = (cudaStream_t)cuda_stream;
     p->opts = *opts;
-    fresnel_status s = p->prec == FRESNEL_FP64 ? build_plan<double>(p, families, n_families)
-                                               : build_plan<float>(p, families, n_families);
+    fresnel_status s = p->prec == FRESNEL_FP64 ? build_plan<double>(p, problems)
+                                               : build_plan<float>(p, problems);
     if (s != FRESNEL_OK) {
         std::string msg = g_last_error;
         cudaGetLastError();
@@ -846,9 +1107,30 @@ fresnel_status fresnel_plan(const fresnel_family* families, int n_families, doub
     return FRESNEL_OK;
 }
 
+fresnel_status fresnel_plan(const fresnel_family* families, int n_families, double lambda,
+                            double z, double tol, const fresnel_opts* opts, void* cuda_stream,
+                            fresnel_plan_t* out_plan) {
+    fresnel_problem one{families, n_families, lambda, z};
+    return fresnel_plan_many(&one, 1, tol, opts, cuda_stream, out_plan);
+}
+
+fresnel_status fresnel_eval_many(fresnel_plan_t plan, void* d_out) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (p->tkind != FRESNEL_GRID) return fres_fail(FRESNEL_ERR_ARG, "fresnel_eval_many needs a GRID plan");
+    if (!d_out) return fres_fail(FRESNEL_ERR_ARG, "d_out is NULL");
+    const long long M = (long long)p->n1 * p->n2;
+    fresnel_status s = p->prec == FRESNEL_FP64 ? eval_impl<double>(p, nullptr, M, d_out)
+                                               : eval_impl<float>(p, nullptr, M, d_out);
+    if (s != FRESNEL_OK) return s;
+    if (p->opts.sync_status) return read_status(p);
+    return FRESNEL_OK;
+}
+
 fresnel_status fresnel_eval(fresnel_plan_t plan, const double* d_targets, long long M, void* d_out) {
     Plan* p = as_plan(plan);
     if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (p->B != 1) return fres_fail(FRESNEL_ERR_ARG, "plan has several problems: use fresnel_eval_many");
     if (p->tkind == FRESNEL_GRID) {
         if (M != (long long)p->n1 * p->n2)
             return fres_fail(FRESNEL_ERR_ARG, "GRID plan: M must equal n1 * n2");
@@ -868,6 +1150,7 @@ fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, l
                                  void* h_out) {
     Plan* p = as_plan(plan);
     if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (p->B != 1) return fres_fail(FRESNEL_ERR_ARG, "plan has several problems: use fresnel_eval_many");
     if (M < 0) return fres_fail(FRESNEL_ERR_ARG, "M must be >= 0");
     if (M > 0 && !h_out) return fres_fail(FRESNEL_ERR_ARG, "h_out is NULL");
     if (p->tkind == FRESNEL_SCATTERED && M > 0 && !h_targets)
@@ -923,10 +1206,7 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
     int nl = 4;   // spread, two FFT passes, (type 3) interpolation
     if (p->tkind == FRESNEL_GRID) nl = 3;
     if (p->max_split > 0) nl += 1;   // clearing of split tiles before the spread
-    if (p->opts.recompute_nodes) {
-        for (const FamilyDev& f : p->fams) nl += f.kind == FRESNEL_FAMILY_NODES ? 1 : 2;
-        nl += 2;
-    }
+    if (p->opts.recompute_nodes) nl += 3;   // nodes, scan, scatter
     info->launches_per_eval = p->last_launches > 0 ? p->last_launches : nl;
     return FRESNEL_OK;
 }

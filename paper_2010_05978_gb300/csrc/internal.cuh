@@ -23,6 +23,7 @@ enum : unsigned {
     kStatusTargetOutside = 1u,     // a scattered target lay outside the plan's box
     kStatusNodeOutside = 2u,       // a node's support left the type-3 spreading grid
     kStatusNonFinite = 4u,         // a non-finite coordinate was met
+    kStatusOverflow = 8u,          // a sort region was smaller than its records (batched plans)
 };
 
 template <typename T> struct Cx;
@@ -64,7 +65,16 @@ struct FamilyDev {
     int kind;
     int n_panels, p, m;
     int K;                 // Fourier modes (kind FOURIER)
-    long long n_bdry;      // boundary nodes
+    int ptr;               // FOURIER on the periodic trapezoid rule (p = 1), t_q = 2 pi (q+1)/n_panels
+    // PETALS (Sec. 4.2): bx, by, bc hold the first petal's u = r_l cos(A_l t_i),
+    // v = r_l sin(A_l t_i), w = r_l what_l A_l omegahat_i at index i*m + l;
+    // petal k is that petal rotated by rot[2k], rot[2k+1] = cos, sin(2 pi k/n_panels).
+    int profile;
+    long long n_prof;      // profile data values (at params + 5)
+    double pa, pR;         // petal radii a < r < R
+    double* rot;
+    int prob;              // problem of a batched plan this family belongs to
+    long long n_bdry;      // boundary nodes (PETALS: table entries p*m)
     long long n_nodes;     // areal nodes
     long long offset;      // first global node index
     double cx, cy;
@@ -83,6 +93,13 @@ struct FamilyDev {
     float* bcf;            // bc as FP32 (weights need only FP32)
     float* adf;            // alpha_l as (hi, lo)
     float* awf;            // alpha_l wtilde_l as FP32
+    // FP32 fast mode, PETALS: per table entry (i, l) 8 floats: u, v, the
+    // phase kq r_l^2 mod 2 pi (each hi, lo), the weight, a pad; per petal k
+    // 12 floats: phase slopes P, Q and grid-coordinate slopes G1u, G1v, G2u,
+    // G2v (each hi, lo), so that phase = A0 + R + u P + v Q and grid
+    // coordinate (minus w/2) = G0 + u Gu + v Gv.
+    float* ptab;
+    float* pk;
     float A0[2], G0x[2], G0y[2];
 };
 
@@ -98,6 +115,7 @@ struct ChirpParams {
     int nf1, nf2;          // spreading grid
     int w;
     int ntx, nty;          // tiles per dimension
+    int tile_base;         // first tile of this problem in a batched plan (problem * ntx * nty)
 };
 
 // Piecewise-polynomial form of the spreading kernel for FP32: the value at
@@ -145,17 +163,50 @@ __device__ __forceinline__ R kernel_ft(R t, int w, R beta, const R* gq_t, const 
     return (R)w * acc;
 }
 
+// The families of a plan for one node launch: family f owns blocks
+// [blk0[f], blk0[f+1]); its problem's chirp parameters are cps[fams[f].prob].
+struct FamTable {
+    const FamilyDev* fams;
+    const ChirpParams* cps;
+    const int* blk0;
+    int nfam;
+};
+constexpr int kNodeThreads = 256;
+
+// Per-problem regions of a batched plan's chunk list, split-tile list and
+// sorted records (B + 1 entries each, absolute starts; sized at plan time).
+// Chunk index space: every problem's split chunks first, then every
+// problem's one-per-tile plain chunks.
+// live (type 1 only, else NULL): per problem and tile row, 1 if any tile of
+// the row holds records.  Tiles of dead rows get no chunk: the grid there is
+// never written, and the FFT passes skip those rows (they are zero).
+struct ScanLayout {
+    const int* sc_off;
+    const int* pl_off;
+    const int* st_off;
+    const long long* rec_off;
+    int* live;
+    int ntx, nty;
+};
+constexpr int kMaxTileRows = 256;   // nf2 <= 8192
+
 // ------------------------------------------------------------------ launchers
 // k_nodes.cu
 void launch_gauss_legendre(int n, double* t01, double* w01, cudaStream_t st);
 void launch_boundary(const FamilyDev& f, const ChirpParams& cp, cudaStream_t st);
-// FP32 fast mode, dilation families: double-float spoke form (no FP64 per node)
-void launch_nodes_count_df(const FamilyDev& f, const ChirpParams& cp, NodeRec<float>* rec,
-                           int* counts, unsigned* status, cudaStream_t st);
+// All families of a plan in one launch: records, tile counts (keys offset by
+// each problem's tile_base) and, when dx != NULL, the FP64 nodes.
 template <typename T>
-void launch_nodes_count(const FamilyDev& f, const ChirpParams& cp, NodeRec<T>* rec,
-                        int* counts, double* dx, double* dy, double* dw,
-                        unsigned* status, cudaStream_t st);
+void launch_nodes(const FamTable& ft, int nblocks, NodeRec<T>* rec, int* counts, double* dx,
+                  double* dy, double* dw, unsigned* status, cudaStream_t st);
+template <typename T>
+void launch_scatter_fams(const FamTable& ft, int nblocks, const NodeRec<T>* rec, int* cursor,
+                         NodeRec<T>* sorted, long long cap, unsigned* status, cudaStream_t st);
+// One block per problem (B blocks): cursors, chunks and split tiles into the
+// problem's regions of L; clears the counts.
+void launch_scan_problems(int B, int ntiles, int* counts, int* cursor, Chunk* chunks,
+                          int* split_tiles, const ScanLayout& L, int chunk_cap, unsigned* status,
+                          cudaStream_t st);
 // records + tile counts for points given by periodic grid coordinates (fresnel_spread)
 void launch_records_from_coords(long long n, const double* g1, const double* g2, const float2* c,
                                 const ChirpParams& cp, NodeRec<float>* rec, int* counts,
@@ -178,11 +229,14 @@ void launch_t3_deconv(int ng, int nfft, int w, double beta, void* table, int is_
 
 // k_spread.cu
 // work[0]: next chunk, work[1]: finished blocks (both return to 0 at exit)
+// Chunk tiles are global tile ids: problem = tile / ntiles (its grid is
+// nf1 * nf2 cells after the previous problem's); split_tiles entries < 0 are
+// padding.
 template <typename T>
 void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
                    int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
-                   int* work, int nf1, int nf2, int ntx, const KernelShape& ks, int nblocks,
-                   cudaStream_t st);
+                   int* work, int nf1, int nf2, int ntx, int ntiles, const KernelShape& ks,
+                   int nblocks, cudaStream_t st);
 
 // k_fft.cu
 struct RowPassArgs {
@@ -195,6 +249,10 @@ struct RowPassArgs {
     const void* deconv_row;   // per-row scalar factor (centered_in), or NULL
     int out_len;         // kept outputs: modes k in [-out_len/2, out_len - out_len/2), stored at k + out_len/2 (out_len == n: fftshifted)
     const void* twiddle;
+    // rows of dead tile rows (live[(row / batch_rows) * nty + (row % batch_rows) / 32] == 0)
+    // are skipped: neither read nor written.  NULL: every row is live.
+    const int* live;
+    int batch_rows, nty;
 };
 struct ColPassArgs {
     const void* in; void* out;
@@ -207,6 +265,13 @@ struct ColPassArgs {
     const void* ax; const void* ay;
     int occulter;
     int out_is_final;    // 1: out has ncols columns of the final type (complex64/128)
+    // batch of independent transforms: in/out of batch b start b * in_bstride /
+    // out_bstride elements in; the epilogue tables of b at b * ncols / b * out_len
+    int batch;
+    long long in_bstride, out_bstride;
+    // input row i of transform b is zero (not read) when live[b * nty + i / 32] == 0
+    const int* live;
+    int nty;
 };
 template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st);

@@ -250,8 +250,16 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
             if (i < npf) buf[k] = in[i];
         }
     };
-    if (blockIdx.x < a.nrows) prefetch(blockIdx.x);
-    for (int row = blockIdx.x; row < a.nrows; row += gridDim.x) {
+    // rows of dead tile rows are zero in and out of the transform: skipped
+    auto next_live = [&](int r) {
+        if (a.live)
+            while (r < a.nrows && !a.live[(r / a.batch_rows) * a.nty + (r % a.batch_rows) / kTile])
+                r += gridDim.x;
+        return r;
+    };
+    int row = next_live(blockIdx.x);
+    if (row < a.nrows) prefetch(row);
+    while (row < a.nrows) {
         const C* in = (const C*)a.in + (long long)row * a.in_stride;
         if (a.centered_in || a.in_len < n)
             for (int e = threadIdx.x; e < padded_len(n); e += blockDim.x) S[e] = Ops<T>::mk(0, 0);
@@ -273,12 +281,14 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
             S[pad(in_pos(i, a.in_len, n, a.centered_in))] = v;
         }
         __syncthreads();
-        if (row + (int)gridDim.x < a.nrows) prefetch(row + gridDim.x);
+        const int nxt = next_live(row + gridDim.x);
+        if (nxt < a.nrows) prefetch(nxt);
         const C* R = fft_smem<T>(S, S2, 1, fp, tw);
         C* out = (C*)a.out + (long long)row * a.out_stride;
         for (int kp = threadIdx.x; kp < a.out_len; kp += blockDim.x)
             out[kp] = R[pad(out_src(kp, a.out_len, n))];
         __syncthreads();
+        row = nxt;
     }
 }
 
@@ -292,26 +302,31 @@ k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     const int ngroups = (a.ncols + ncol - 1) / ncol;
-    const C* in = (const C*)a.in;
-    // Inputs of the block's next column group are prefetched into registers
-    // (first kPrefetch * blockDim.x of them) while the current group runs.
+    const int total = ngroups * max(a.batch, 1);   // (transform, column group) work items
+    // Inputs of the block's next work item are prefetched into registers
+    // (first kPrefetch * blockDim.x of them) while the current one runs.
     C buf[kPrefetch];
     const int nin = a.in_len * ncol;
     const int npf = min(nin, kPrefetch * (int)blockDim.x);
-    auto prefetch = [&](int g) {
-        const int c0 = g * ncol;
+    // input row i of transform bi: zero without a load when its tile row is dead
+    auto load = [&](const C* in, const int* lv, int i, int col) {
+        if (col >= a.ncols || (lv && !lv[i / kTile])) return Ops<T>::mk(0, 0);
+        return in[(long long)i * a.ncols + col];
+    };
+    auto prefetch = [&](int gg) {
+        const int bi = gg / ngroups, c0 = (gg - bi * ngroups) * ncol;
+        const C* in = (const C*)a.in + (long long)bi * a.in_bstride;
+        const int* lv = a.live ? a.live + (long long)bi * a.nty : nullptr;
 #pragma unroll
         for (int k = 0; k < kPrefetch; ++k) {
             const int e = threadIdx.x + k * blockDim.x;
-            if (e < npf) {
-                const int i = e / ncol, c = e % ncol;
-                buf[k] = c0 + c < a.ncols ? in[(long long)i * a.ncols + c0 + c] : Ops<T>::mk(0, 0);
-            }
+            if (e < npf) buf[k] = load(in, lv, e / ncol, c0 + e % ncol);
         }
     };
-    if (blockIdx.x < ngroups) prefetch(blockIdx.x);
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int c0 = g * ncol;
+    if (blockIdx.x < total) prefetch(blockIdx.x);
+    for (int gg = blockIdx.x; gg < total; gg += gridDim.x) {
+        const int bi = gg / ngroups, c0 = (gg - bi * ngroups) * ncol;
+        const C* in = (const C*)a.in + (long long)bi * a.in_bstride;
         if (a.centered_in || a.in_len < n)
             for (int e = threadIdx.x; e < padded_len(n) * ncol; e += blockDim.x)
                 S[e] = Ops<T>::mk(0, 0);
@@ -324,25 +339,27 @@ k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
                 S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = buf[k];
             }
         }
+        const int* lv = a.live ? a.live + (long long)bi * a.nty : nullptr;
         for (int e = npf + threadIdx.x; e < nin; e += blockDim.x) {
             const int i = e / ncol, c = e % ncol;
-            C v = Ops<T>::mk(0, 0);
-            if (c0 + c < a.ncols) v = in[(long long)i * a.ncols + c0 + c];
-            S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = v;
+            S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = load(in, lv, i, c0 + c);
         }
         __syncthreads();
-        if (g + (int)gridDim.x < ngroups) prefetch(g + gridDim.x);
+        if (gg + (int)gridDim.x < total) prefetch(gg + gridDim.x);
         const C* R = fft_smem<T>(S, S2, ncol, fp, tw);
+        C* out = (C*)a.out + (long long)bi * a.out_bstride;
+        const C* ax = a.ax ? (const C*)a.ax + (long long)bi * a.ncols : nullptr;
+        const C* ay = a.ax ? (const C*)a.ay + (long long)bi * a.out_len : nullptr;
         for (int e = threadIdx.x; e < a.out_len * ncol; e += blockDim.x) {
             const int kp = e / ncol, c = e % ncol;
             if (c0 + c >= a.ncols) continue;
             C v = R[pad(out_src(kp, a.out_len, n)) * ncol + c];
-            if (a.ax) {
-                v = Ops<T>::mul(v, ((const C*)a.ax)[c0 + c]);
-                v = Ops<T>::mul(v, ((const C*)a.ay)[kp]);
+            if (ax) {
+                v = Ops<T>::mul(v, ax[c0 + c]);
+                v = Ops<T>::mul(v, ay[kp]);
                 if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
             }
-            ((C*)a.out)[(long long)kp * a.ncols + c0 + c] = v;
+            out[(long long)kp * a.ncols + c0 + c] = v;
         }
         __syncthreads();
     }
@@ -407,8 +424,8 @@ void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st) {
     const size_t smem = 2 * (size_t)padded_len(fp.n) * cmax * sizeof(cx_t<T>);
     cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int threads = threads_for(fp.n * cmax, emax<T>());
-    const int ngroups = (a.ncols + cmax - 1) / cmax;
-    int blocks = ngroups < 152 * 16 ? ngroups : 152 * 16;
+    const long long ngroups = (long long)((a.ncols + cmax - 1) / cmax) * (a.batch > 1 ? a.batch : 1);
+    int blocks = ngroups < 152 * 16 ? (int)ngroups : 152 * 16;
     if (blocks < 1) blocks = 1;
     k_fft_cols<T><<<blocks, threads, smem, st>>>(fp, a, cmax);
 }

@@ -160,18 +160,48 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
         kernel_values<T, W>(f1, beta, hz, kx);
         kernel_values<T, W>(f2, beta, hz, ky);
         T gr = 0, gi = 0;
+        if constexpr (std::is_same<T, float>::value && (W % 2 == 0)) {
+            // W + 2 cells from the even cell at or below s1, as W/2 + 1
+            // aligned 16-byte loads (nfft1 is even; s1 <= nfft1 - W - 2 keeps
+            // the last load inside the row); weights shifted by s1's parity.
+            const int odd = s1 & 1;
+            float kk[W + 2];
 #pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const cx_t<T>* row = F + (long long)(s2 + b) * ip.nfft1 + s1;
-            T rr = 0, ri = 0;
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                const cx_t<T> v = __ldg(&row[a]);
-                rr += kx[a] * v.x;
-                ri += kx[a] * v.y;
+            for (int i = 0; i < W + 2; ++i) {
+                const float lo = (i < W) ? kx[i] : 0.0f;
+                const float hi = (i >= 1 && i <= W) ? kx[i - 1] : 0.0f;
+                kk[i] = odd ? hi : lo;
             }
-            gr += ky[b] * rr;
-            gi += ky[b] * ri;
+            const float4* base =
+                reinterpret_cast<const float4*>(F + (long long)s2 * ip.nfft1 + (s1 - odd));
+            const int row4 = ip.nfft1 / 2;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const float4* row = base + (long long)b * row4;
+                float rr = 0.0f, ri = 0.0f;
+#pragma unroll
+                for (int q = 0; q < W / 2 + 1; ++q) {
+                    const float4 v = __ldg(row + q);
+                    rr = fmaf(kk[2 * q], v.x, fmaf(kk[2 * q + 1], v.z, rr));
+                    ri = fmaf(kk[2 * q], v.y, fmaf(kk[2 * q + 1], v.w, ri));
+                }
+                gr = fmaf(ky[b], rr, gr);
+                gi = fmaf(ky[b], ri, gi);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const cx_t<T>* row = F + (long long)(s2 + b) * ip.nfft1 + s1;
+                T rr = 0, ri = 0;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const cx_t<T> v = __ldg(&row[a]);
+                    rr += kx[a] * v.x;
+                    ri += kx[a] * v.y;
+                }
+                gr += ky[b] * rr;
+                gi += ky[b] * ri;
+            }
         }
         const T dec = kernel_ft_cheb<T>(targ1, s_a, ncheb, inv_tmax) *
                       kernel_ft_cheb<T>(targ2, s_a, ncheb, inv_tmax);

@@ -44,10 +44,11 @@ __device__ __forceinline__ void node_tiles(int s1, int s2, const ChirpParams& cp
     int e2 = s2 + cp.w - 1; if (e2 >= cp.nf2) e2 -= cp.nf2;
     int ta = s1 / kTile, tb = e1 / kTile;
     int sa = s2 / kTile, sb = e2 / kTile;
-    key[0] = sa * cp.ntx + ta;
-    key[1] = (tb != ta) ? sa * cp.ntx + tb : -1;
-    key[2] = (sb != sa) ? sb * cp.ntx + ta : -1;
-    key[3] = (tb != ta && sb != sa) ? sb * cp.ntx + tb : -1;
+    const int b = cp.tile_base;
+    key[0] = b + sa * cp.ntx + ta;
+    key[1] = (tb != ta) ? b + sa * cp.ntx + tb : -1;
+    key[2] = (sb != sa) ? b + sb * cp.ntx + ta : -1;
+    key[3] = (tb != ta && sb != sa) ? b + sb * cp.ntx + tb : -1;
 }
 
 // ------------------------------------------------------------------ Gauss-Legendre
@@ -119,8 +120,9 @@ __global__ void k_boundary_fourier(FamilyDev f, ChirpParams cp) {
     if (i >= f.n_bdry) return;
     int q = (int)(i / f.p), s = (int)(i % f.p);
     double hP = kTwoPi / f.n_panels;
-    double t = (q + f.gl_p_t[s]) * hP;
-    double what = f.gl_p_w[s] * hP;
+    // GL panels, or the periodic trapezoid rule t_q = 2 pi (q+1)/n (eq. ptr)
+    double t = f.ptr ? (q + 1) * hP : (q + f.gl_p_t[s]) * hP;
+    double what = f.ptr ? hP : f.gl_p_w[s] * hP;
     double st, ct;
     sincos(t, &st, &ct);
     double r = f.params[0], dr = 0.0;
@@ -155,153 +157,328 @@ __global__ void k_boundary_line(FamilyDev f, ChirpParams cp) {
     store_spoke(f, cp, i, X, Y, X * V - Y * W);
 }
 
+// ------------------------------------------------------------------ starshade petals
+// Apodisation A(r) of a petal family at r in (a, R) (Sec. 4.2).
+__device__ double petal_profile(const FamilyDev& f, int l, double r) {
+    const double* d = f.params + 5;
+    if (f.profile == FRESNEL_PETAL_HG) return exp(-pow((r - f.pa) / d[0], d[1]));
+    if (f.profile == FRESNEL_PETAL_TABLE) return d[l];
+    // clamped uniform cubic B-spline, de Boor's recursion on the span of r
+    const int n = (int)f.n_prof;
+    const double step = (f.pR - f.pa) / (n - 3);
+    auto knot = [&](int i) {
+        return i <= 3 ? f.pa : (i >= n ? f.pR : f.pa + (i - 3) * step);
+    };
+    int mu = 3 + (int)floor((r - f.pa) / step);
+    mu = min(max(mu, 3), n - 1);
+    double c[4];
+    for (int j = 0; j < 4; ++j) c[j] = d[mu - 3 + j];
+    for (int k = 1; k <= 3; ++k)
+        for (int j = 3; j >= k; --j) {
+            const double lo = knot(mu - 3 + j), hi = knot(mu + 1 + j - k);
+            const double al = (r - lo) / (hi - lo);
+            c[j] = (1.0 - al) * c[j - 1] + al * c[j];
+        }
+    return c[3];
+}
+
+// Tables of the first petal (centred on angle 0) for index i*m + l:
+// r_l = a + (R-a) rho_l and what_l = (R-a) rhow_l from the m-point rule on
+// (0,1); t_i = -pi/Np + (2 pi/Np) tau_i, omegahat_i = (2 pi/Np) tauw_i from
+// the p-point rule; u, v = r_l (cos, sin)(A(r_l) t_i), w = r_l what_l A omegahat_i.
+// Also the petal rotations cos, sin(2 pi k / Np).
+__global__ void k_petal_tables(FamilyDev f) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < f.n_panels) {
+        double s, c;
+        sincospi(2.0 * (double)q / f.n_panels, &s, &c);
+        f.rot[2 * q] = c;
+        f.rot[2 * q + 1] = s;
+    }
+    if (q >= f.n_bdry) return;
+    const int i = (int)(q / f.m), l = (int)(q - (long long)i * f.m);
+    const double span = f.pR - f.pa, wedge = kTwoPi / f.n_panels;
+    const double r = f.pa + span * f.gl_m_a[l];
+    const double A = petal_profile(f, l, r);
+    const double t = -0.5 * wedge + wedge * f.gl_p_t[i];
+    double s, c;
+    sincos(A * t, &s, &c);
+    f.bx[q] = r * c;
+    f.by[q] = r * s;
+    f.bc[q] = r * (span * f.gl_m_aw[l]) * A * (wedge * f.gl_p_w[i]);
+}
+
 // ------------------------------------------------------------------ FP32 fast mode nodes
 // Double-float form of the dilation rule for one spoke (boundary node i):
 // with x = c + alpha b, the chirp phase kq |x|^2 - a.x + a0 equals
 // A0 + alpha (A1 + alpha A2) and the grid coordinate (minus w/2) equals
 // G0 + alpha G1, so a node costs a few double-float operations and no FP64.
+// Common tail of the double-float node paths: fold (type 1), split into
+// support start and fraction, bounds, record and tile keys.
+__device__ __forceinline__ void finish_df(dflt v1, dflt v2, float cre, float cim,
+                                          const ChirpParams& cp, NodeRec<float>* out,
+                                          unsigned* status, int key[4]) {
+    NodeRec<float> r;
+    r.cre = cre;
+    r.cim = cim;
+    if (!cp.type3) {   // fold into [0, nf): the type-1 grid is periodic (Sec. 3.3)
+        const float q1 = floorf(v1.hi / (float)cp.nf1), q2 = floorf(v2.hi / (float)cp.nf2);
+        v1 = df_add(v1, dflt{-q1 * (float)cp.nf1, 0.0f});
+        v2 = df_add(v2, dflt{-q2 * (float)cp.nf2, 0.0f});
+    }
+    int c1, c2;
+    df_floor_split(v1, &c1, &r.f1);
+    df_floor_split(v2, &c2, &r.f2);
+    int s1 = c1 + 1, s2 = c2 + 1;
+    if (!(v1.hi == v1.hi) || !(v2.hi == v2.hi)) {
+        atomicOr(status, kStatusNonFinite);
+        s1 = s2 = 0;
+        r.cre = r.cim = 0.0f;
+    }
+    if (!cp.type3) {
+        s1 = ((s1 % cp.nf1) + cp.nf1) % cp.nf1;
+        s2 = ((s2 % cp.nf2) + cp.nf2) % cp.nf2;
+    } else if (s1 < 0 || s2 < 0 || s1 + cp.w > cp.nf1 || s2 + cp.w > cp.nf2) {
+        atomicOr(status, kStatusNodeOutside);
+        s1 = min(max(s1, 0), cp.nf1 - cp.w);
+        s2 = min(max(s2, 0), cp.nf2 - cp.w);
+    }
+    r.s1 = s1;
+    r.s2 = s2;
+    *out = r;
+    node_tiles(s1, s2, cp, key);
+}
+
+__device__ __forceinline__ void node_df(const FamilyDev& f, const ChirpParams& cp, long long j,
+                                        NodeRec<float>* rec, unsigned* status, int key[4]) {
+    const long long i = j / f.m;
+    const int l = (int)(j - i * f.m);
+    const float4 sA = reinterpret_cast<const float4*>(f.spoke)[2 * i];
+    const float4 sG = reinterpret_cast<const float4*>(f.spoke)[2 * i + 1];
+    const float2 a2 = reinterpret_cast<const float2*>(f.adf)[l];
+    const dflt al = {a2.x, a2.y};
+    dflt ph = df_mul(al, dflt{sA.z, sA.w});
+    ph = df_add(ph, dflt{sA.x, sA.y});
+    ph = df_mul(al, ph);
+    ph = df_add(ph, dflt{f.A0[0], f.A0[1]});
+    const float phr = df_reduce_2pi(ph);
+    const float w = f.awf[l] * f.bcf[i];
+    float sn, cs;
+    sincosf(phr, &sn, &cs);
+    dflt v1 = df_add(df_mul(al, dflt{sG.x, sG.y}), dflt{f.G0x[0], f.G0x[1]});
+    dflt v2 = df_add(df_mul(al, dflt{sG.z, sG.w}), dflt{f.G0y[0], f.G0y[1]});
+    finish_df(v1, v2, w * cs, w * sn, cp, rec + f.offset + j, status, key);
+}
+
+// Starshade petals in the double-float form: node (k, i, l) is table entry
+// (i, l) of petal 0 rotated to petal k, whose rotation is folded into the
+// per-petal slopes (Sec. 4.2 nodes; no FP64 per node).
+__device__ __forceinline__ void node_petal_df(const FamilyDev& f, const ChirpParams& cp,
+                                              long long j, NodeRec<float>* rec, unsigned* status,
+                                              int key[4]) {
+    const long long k = j / f.n_bdry, q = j - k * f.n_bdry;
+    const float4 t0 = reinterpret_cast<const float4*>(f.ptab)[2 * q];
+    const float4 t1 = reinterpret_cast<const float4*>(f.ptab)[2 * q + 1];
+    const dflt u = {t0.x, t0.y}, v = {t0.z, t0.w};
+    const float* K = f.pk + 12 * k;
+    dflt ph = df_add(df_mul(u, dflt{K[0], K[1]}), df_mul(v, dflt{K[2], K[3]}));
+    ph = df_add(ph, df_add(dflt{t1.x, t1.y}, dflt{f.A0[0], f.A0[1]}));
+    const float phr = df_reduce_2pi(ph);
+    float sn, cs;
+    sincosf(phr, &sn, &cs);
+    dflt v1 = df_add(df_add(df_mul(u, dflt{K[4], K[5]}), df_mul(v, dflt{K[6], K[7]})),
+                     dflt{f.G0x[0], f.G0x[1]});
+    dflt v2 = df_add(df_add(df_mul(u, dflt{K[8], K[9]}), df_mul(v, dflt{K[10], K[11]})),
+                     dflt{f.G0y[0], f.G0y[1]});
+    finish_df(v1, v2, t1.z * cs, t1.z * sn, cp, rec + f.offset + j, status, key);
+}
+
+// Double-float table of a petal family (FP32 fast mode), from its FP64 table.
+__global__ void k_petal_df_tables(FamilyDev f, ChirpParams cp) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= f.n_bdry) return;
+    const double u = f.bx[q], v = f.by[q];
+    const double R = reduce_phase(cp.kq * (u * u + v * v));
+    float* t = f.ptab + 8 * q;
+    split_store(t + 0, u);
+    split_store(t + 2, v);
+    split_store(t + 4, R);
+    t[6] = (float)f.bc[q];
+    t[7] = 0.0f;
+}
+
 template <typename T>
-__global__ void k_nodes_count_df(FamilyDev f, ChirpParams cp, NodeRec<float>* rec, int* counts,
-                                 unsigned* status) {
-    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpParams& cp, long long j,
+                                             NodeRec<T>* rec, double* dx, double* dy, double* dw,
+                                             unsigned* status, int key[4]) {
+    double x, y, w;
+    if (f.kind == FRESNEL_FAMILY_NODES) {
+        x = f.params[j];
+        y = f.params[f.n_nodes + j];
+        w = f.params[2 * f.n_nodes + j];
+    } else if (f.kind == FRESNEL_FAMILY_PETALS) {
+        // node (k, i, l) = petal 0's node (i, l) rotated by 2 pi k / Np
+        const long long k = j / f.n_bdry, q = j - k * f.n_bdry;
+        const double u = f.bx[q], v = f.by[q];
+        const double c = f.rot[2 * k], s = f.rot[2 * k + 1];
+        x = f.cx + (u * c - v * s);
+        y = f.cy + (u * s + v * c);
+        w = f.bc[q];
+    } else {
+        long long i = j / f.m;
+        int l = (int)(j - i * f.m);
+        double a = f.gl_m_a[l];
+        x = f.cx + a * f.bx[i];
+        y = f.cy + a * f.by[i];
+        w = f.gl_m_aw[l] * f.bc[i];
+    }
+    long long g = f.offset + j;
+    if (dx) {
+        dx[g] = x;
+        dy[g] = y;
+        dw[g] = w;
+    }
+    double ph = reduce_phase(cp.kq * (x * x + y * y) - cp.a1 * x - cp.a2 * y + cp.a0);
+    NodeRec<T> r;
+    if (sizeof(T) == 8) {
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        r.cre = (T)(w * cs);
+        r.cim = (T)(w * sn);
+    } else {
+        float sn, cs;
+        sincosf((float)ph, &sn, &cs);
+        r.cre = (T)((float)w * cs);
+        r.cim = (T)((float)w * sn);
+    }
+    double g1, g2;
+    if (!cp.type3) {
+        double u = x * cp.u1;
+        u -= floor(u);
+        g1 = u * cp.nf1;
+        double v = y * cp.u2;
+        v -= floor(v);
+        g2 = v * cp.nf2;
+    } else {
+        g1 = (x - cp.C1) * cp.inv_h1 + 0.5 * cp.nf1;
+        g2 = (y - cp.C2) * cp.inv_h2 + 0.5 * cp.nf2;
+    }
+    if (!isfinite(g1) || !isfinite(g2)) {
+        atomicOr(status, kStatusNonFinite);
+        g1 = g2 = 0.0;
+        r.cre = r.cim = (T)0;
+    }
+    double gs1 = g1 - 0.5 * cp.w, gs2 = g2 - 0.5 * cp.w;
+    double fl1 = floor(gs1), fl2 = floor(gs2);
+    int s1 = (int)fl1 + 1, s2 = (int)fl2 + 1;
+    r.f1 = (T)(gs1 - fl1);
+    r.f2 = (T)(gs2 - fl2);
+    if (!cp.type3) {
+        if (s1 < 0) s1 += cp.nf1;
+        if (s1 >= cp.nf1) s1 -= cp.nf1;
+        if (s2 < 0) s2 += cp.nf2;
+        if (s2 >= cp.nf2) s2 -= cp.nf2;
+    } else if (s1 < 0 || s2 < 0 || s1 + cp.w > cp.nf1 || s2 + cp.w > cp.nf2) {
+        atomicOr(status, kStatusNodeOutside);
+        s1 = min(max(s1, 0), cp.nf1 - cp.w);
+        s2 = min(max(s2, 0), cp.nf2 - cp.w);
+    }
+    r.s1 = s1;
+    r.s2 = s2;
+    rec[g] = r;
+    node_tiles(s1, s2, cp, key);
+}
+
+// Block -> family (binary search over the block starts), then the family
+// and its problem's chirp parameters are copied into shared memory.
+struct FamSmem {
+    FamilyDev f;
+    ChirpParams cp;
+    int fi;
+};
+
+__device__ __forceinline__ void load_family(const FamTable& ft, FamSmem& sm) {
+    if (threadIdx.x == 0) {
+        int a = 0, b = ft.nfam - 1;
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (ft.blk0[mid] <= (int)blockIdx.x) a = mid;
+            else b = mid - 1;
+        }
+        sm.fi = a;
+    }
+    __syncthreads();
+    static_assert(sizeof(FamilyDev) % 4 == 0 && sizeof(ChirpParams) % 4 == 0, "word copy");
+    const int* src = reinterpret_cast<const int*>(ft.fams + sm.fi);
+    int* dst = reinterpret_cast<int*>(&sm.f);
+    for (int i = threadIdx.x; i < (int)(sizeof(FamilyDev) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    const int* src2 = reinterpret_cast<const int*>(ft.cps + sm.f.prob);
+    int* dst2 = reinterpret_cast<int*>(&sm.cp);
+    for (int i = threadIdx.x; i < (int)(sizeof(ChirpParams) / 4); i += blockDim.x) dst2[i] = src2[i];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ nodes + chirp + count
+// Dilation rule (eqs. aqnod, aqwei): x = c + alpha_l (X_i - c),
+// w = alpha_l wtilde_l ((X_i-cx) V_i - (Y_i-cy) W_i), node j = i*m + l; the
+// starshade petals (Sec. 4.2) from their tables; explicit nodes as given.
+// Strength (Sec. 3.2 step 1, with the optional pre-phase of Sec. 3.3):
+// c = w exp(i [pi |x|^2 / lz - a1 x - a2 y + a0]), phase reduced mod 2 pi
+// before the sine/cosine.  Grid coordinate: type 1 g = frac(x h / lz) nf (the
+// folded x~ of Sec. 3.3 scaled to grid points); type 3 g = (x - C)/h_s + nf/2.
+// FP32 fast mode runs the dilation families in the double-float spoke form
+// (no FP64 per node); FP64 per node otherwise.  One launch covers every
+// family of every problem of the plan.
+template <typename T>
+__global__ void __launch_bounds__(kNodeThreads)
+k_nodes(FamTable ft, NodeRec<T>* rec, int* counts, double* dx, double* dy, double* dw,
+        unsigned* status) {
+    __shared__ __align__(16) FamSmem sm;
+    load_family(ft, sm);
+    const FamilyDev& f = sm.f;
+    const long long j = (long long)(blockIdx.x - ft.blk0[sm.fi]) * blockDim.x + threadIdx.x;
     int key[4] = {-1, -1, -1, -1};
     if (j < f.n_nodes) {
-        const long long i = j / f.m;
-        const int l = (int)(j - i * f.m);
-        const float4 sA = reinterpret_cast<const float4*>(f.spoke)[2 * i];
-        const float4 sG = reinterpret_cast<const float4*>(f.spoke)[2 * i + 1];
-        const float2 a2 = reinterpret_cast<const float2*>(f.adf)[l];
-        const dflt al = {a2.x, a2.y};
-        dflt ph = df_mul(al, dflt{sA.z, sA.w});
-        ph = df_add(ph, dflt{sA.x, sA.y});
-        ph = df_mul(al, ph);
-        ph = df_add(ph, dflt{f.A0[0], f.A0[1]});
-        const float phr = df_reduce_2pi(ph);
-        const float w = f.awf[l] * f.bcf[i];
-        float sn, cs;
-        sincosf(phr, &sn, &cs);
-        NodeRec<float> r;
-        r.cre = w * cs;
-        r.cim = w * sn;
-        dflt v1 = df_add(df_mul(al, dflt{sG.x, sG.y}), dflt{f.G0x[0], f.G0x[1]});
-        dflt v2 = df_add(df_mul(al, dflt{sG.z, sG.w}), dflt{f.G0y[0], f.G0y[1]});
-        if (!cp.type3) {   // fold into [0, nf): the type-1 grid is periodic (Sec. 3.3)
-            const float q1 = floorf(v1.hi / (float)cp.nf1), q2 = floorf(v2.hi / (float)cp.nf2);
-            v1 = df_add(v1, dflt{-q1 * (float)cp.nf1, 0.0f});
-            v2 = df_add(v2, dflt{-q2 * (float)cp.nf2, 0.0f});
+        if constexpr (sizeof(T) == 4) {
+            if (f.spoke && !dx)
+                node_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key);
+            else if (f.ptab && !dx)
+                node_petal_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key);
+            else
+                node_generic<T>(f, sm.cp, j, rec, dx, dy, dw, status, key);
+        } else {
+            node_generic<T>(f, sm.cp, j, rec, dx, dy, dw, status, key);
         }
-        int c1, c2;
-        df_floor_split(v1, &c1, &r.f1);
-        df_floor_split(v2, &c2, &r.f2);
-        int s1 = c1 + 1, s2 = c2 + 1;
-        if (!(v1.hi == v1.hi) || !(v2.hi == v2.hi)) {
-            atomicOr(status, kStatusNonFinite);
-            s1 = s2 = 0;
-            r.cre = r.cim = 0.0f;
-        }
-        if (!cp.type3) {
-            s1 = ((s1 % cp.nf1) + cp.nf1) % cp.nf1;
-            s2 = ((s2 % cp.nf2) + cp.nf2) % cp.nf2;
-        } else if (s1 < 0 || s2 < 0 || s1 + cp.w > cp.nf1 || s2 + cp.w > cp.nf2) {
-            atomicOr(status, kStatusNodeOutside);
-            s1 = min(max(s1, 0), cp.nf1 - cp.w);
-            s2 = min(max(s2, 0), cp.nf2 - cp.w);
-        }
-        r.s1 = s1;
-        r.s2 = s2;
-        rec[f.offset + j] = r;
-        node_tiles(s1, s2, cp, key);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) agg_count(key[k], counts);
 }
 
-// ------------------------------------------------------------------ nodes + chirp + count
-// Dilation rule (eqs. aqnod, aqwei): x = c + alpha_l (X_i - c),
-// w = alpha_l wtilde_l ((X_i-cx) V_i - (Y_i-cy) W_i), node j = i*m + l.
-// Strength (Sec. 3.2 step 1, with the optional pre-phase of Sec. 3.3):
-// c = w exp(i [pi |x|^2 / lz - a1 x - a2 y + a0]), phase in FP64 and reduced
-// mod 2 pi before the sine/cosine (FP32 sincos in the fast mode).
-// Grid coordinate: type 1 g = frac(x h / lz) nf (the folded x~ of Sec. 3.3
-// scaled to grid points); type 3 g = (x - C) / h_s + nf/2.
+// Scatter of a plan's records (families as in k_nodes) to every tile their
+// support touches.
 template <typename T>
-__global__ void k_nodes_count(FamilyDev f, ChirpParams cp, NodeRec<T>* rec, int* counts,
-                              double* dx, double* dy, double* dw, unsigned* status) {
-    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    bool valid = j < f.n_nodes;
+__global__ void __launch_bounds__(kNodeThreads)
+k_scatter_fams(FamTable ft, const NodeRec<T>* rec, int* cursor, NodeRec<T>* sorted,
+               long long cap, unsigned* status) {
+    __shared__ __align__(16) FamSmem sm;
+    load_family(ft, sm);
+    const FamilyDev& f = sm.f;
+    const long long j = (long long)(blockIdx.x - ft.blk0[sm.fi]) * blockDim.x + threadIdx.x;
     int key[4] = {-1, -1, -1, -1};
-    if (valid) {
-        double x, y, w;
-        if (f.kind == FRESNEL_FAMILY_NODES) {
-            x = f.params[j];
-            y = f.params[f.n_nodes + j];
-            w = f.params[2 * f.n_nodes + j];
-        } else {
-            long long i = j / f.m;
-            int l = (int)(j - i * f.m);
-            double a = f.gl_m_a[l];
-            x = f.cx + a * f.bx[i];
-            y = f.cy + a * f.by[i];
-            w = f.gl_m_aw[l] * f.bc[i];
-        }
-        long long g = f.offset + j;
-        if (dx) {
-            dx[g] = x;
-            dy[g] = y;
-            dw[g] = w;
-        }
-        double ph = reduce_phase(cp.kq * (x * x + y * y) - cp.a1 * x - cp.a2 * y + cp.a0);
-        NodeRec<T> r;
-        if (sizeof(T) == 8) {
-            double sn, cs;
-            sincos(ph, &sn, &cs);
-            r.cre = (T)(w * cs);
-            r.cim = (T)(w * sn);
-        } else {
-            float sn, cs;
-            sincosf((float)ph, &sn, &cs);
-            r.cre = (T)((float)w * cs);
-            r.cim = (T)((float)w * sn);
-        }
-        double g1, g2;
-        if (!cp.type3) {
-            double u = x * cp.u1;
-            u -= floor(u);
-            g1 = u * cp.nf1;
-            double v = y * cp.u2;
-            v -= floor(v);
-            g2 = v * cp.nf2;
-        } else {
-            g1 = (x - cp.C1) * cp.inv_h1 + 0.5 * cp.nf1;
-            g2 = (y - cp.C2) * cp.inv_h2 + 0.5 * cp.nf2;
-        }
-        if (!isfinite(g1) || !isfinite(g2)) {
-            atomicOr(status, kStatusNonFinite);
-            g1 = g2 = 0.0;
-            r.cre = r.cim = (T)0;
-        }
-        double gs1 = g1 - 0.5 * cp.w, gs2 = g2 - 0.5 * cp.w;
-        double fl1 = floor(gs1), fl2 = floor(gs2);
-        int s1 = (int)fl1 + 1, s2 = (int)fl2 + 1;
-        r.f1 = (T)(gs1 - fl1);
-        r.f2 = (T)(gs2 - fl2);
-        if (!cp.type3) {
-            if (s1 < 0) s1 += cp.nf1;
-            if (s1 >= cp.nf1) s1 -= cp.nf1;
-            if (s2 < 0) s2 += cp.nf2;
-            if (s2 >= cp.nf2) s2 -= cp.nf2;
-        } else if (s1 < 0 || s2 < 0 || s1 + cp.w > cp.nf1 || s2 + cp.w > cp.nf2) {
-            atomicOr(status, kStatusNodeOutside);
-            s1 = min(max(s1, 0), cp.nf1 - cp.w);
-            s2 = min(max(s2, 0), cp.nf2 - cp.w);
-        }
-        r.s1 = s1;
-        r.s2 = s2;
-        rec[g] = r;
-        node_tiles(s1, s2, cp, key);
+    NodeRec<T> r;
+    if (j < f.n_nodes) {
+        r = rec[f.offset + j];
+        node_tiles(r.s1, r.s2, sm.cp, key);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) agg_count(key[k], counts);
+    for (int k = 0; k < 4; ++k) {
+        int pos = agg_reserve(key[k], cursor);
+        if (key[k] >= 0) {
+            if (pos >= 0 && pos < cap) sorted[pos] = r;
+            else atomicOr(status, kStatusOverflow);
+        }
+    }
 }
 
 // Records for the standalone spreader (fresnel_spread): points given directly
@@ -484,6 +661,147 @@ __global__ void k_scan_chunks(int ntiles, int* __restrict__ counts, int* __restr
     }
 }
 
+// Batched plans: block b scans problem b's tiles [b ntiles, (b+1) ntiles).
+// Cursors are absolute positions from rec_off[b]; split tiles (count > cap)
+// give ceil(count / cap) chunks in the problem's split-chunk region, every
+// other tile one chunk in its plain region, split tiles are listed in its
+// split-tile region.  The regions were sized at plan time from the same
+// deterministic counts; unused entries are padded (empty split-flagged
+// chunks add nothing, split-tile entries -1 are skipped) and a count beyond
+// a region sets kStatusOverflow (the entries beyond it are dropped).
+// Clears the counts.
+__global__ void __launch_bounds__(1024)
+k_scan_problems(int ntiles, int* __restrict__ counts, int* __restrict__ cursor,
+                Chunk* __restrict__ chunks, int* __restrict__ split_tiles, ScanLayout L,
+                int chunk_cap, int staged, unsigned* __restrict__ status) {
+    __shared__ long long s_rec[1024], s_sc[1024], s_ns[1024], s_st[1024];
+    extern __shared__ int s_counts[];
+    const int t = threadIdx.x, nt = blockDim.x, b = blockIdx.x;
+    const int base = b * ntiles;
+    int* cnt_g = counts + base;
+    int* cur = cursor + base;
+    const int sc0 = L.sc_off[b], sc1 = L.sc_off[b + 1];
+    const int pl0 = L.pl_off[b], pl1 = L.pl_off[b + 1];
+    const int st0 = L.st_off[b], st1 = L.st_off[b + 1];
+    const long long r0 = L.rec_off[b], r1 = L.rec_off[b + 1];
+    const int* cnt = cnt_g;
+    __shared__ int s_live[kMaxTileRows];
+    if (staged) {
+        for (int i = t; i < ntiles; i += nt) {
+            s_counts[i] = cnt_g[i];
+            cnt_g[i] = 0;
+        }
+        cnt = s_counts;
+    }
+    // tile rows holding records (all rows live when no live map is kept)
+    for (int r = t; r < L.nty && r < kMaxTileRows; r += nt) s_live[r] = L.live ? 0 : 1;
+    __syncthreads();
+    if (L.live) {
+        for (int i = t; i < ntiles; i += nt)
+            if (cnt[i] > 0) s_live[i / L.ntx] = 1;
+        __syncthreads();
+        for (int r = t; r < L.nty; r += nt) L.live[b * L.nty + r] = s_live[r];
+    }
+    const int per = (ntiles + nt - 1) / nt;
+    const int lo = min(t * per, ntiles), hi = min(lo + per, ntiles);
+    long long rsum = 0, sc = 0, ns = 0, stl = 0;
+    for (int i = lo; i < hi; ++i) {
+        const int c = cnt[i];
+        rsum += c;
+        if (c > chunk_cap) {
+            sc += (c + chunk_cap - 1) / chunk_cap;
+            ++stl;
+        } else if (s_live[i / L.ntx]) {
+            ++ns;
+        }
+    }
+    s_rec[t] = rsum;
+    s_sc[t] = sc;
+    s_ns[t] = ns;
+    s_st[t] = stl;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scans
+        long long a = 0, bb = 0, c = 0, d = 0;
+        if (t >= off) { a = s_rec[t - off]; bb = s_sc[t - off]; c = s_ns[t - off]; d = s_st[t - off]; }
+        __syncthreads();
+        s_rec[t] += a; s_sc[t] += bb; s_ns[t] += c; s_st[t] += d;
+        __syncthreads();
+    }
+    const long long TS = s_sc[nt - 1], NS = s_ns[nt - 1], TST = s_st[nt - 1], RT = s_rec[nt - 1];
+    if (t == 0 && (TS > sc1 - sc0 || NS > pl1 - pl0 || TST > st1 - st0 || RT > r1 - r0))
+        atomicOr(status, kStatusOverflow);
+    int* s_cstart = s_counts + ntiles;
+    int* s_sroff = s_cstart + ntiles + 1;
+    int* s_scnt = s_sroff + ntiles;
+    long long roff = s_rec[t] - rsum, scoff = s_sc[t] - sc, nsoff = s_ns[t] - ns, stoff = s_st[t] - stl;
+    for (int i = lo; i < hi; ++i) {
+        const int c = cnt[i];
+        cur[i] = (int)(r0 + roff);
+        if (c > chunk_cap) {
+            const int nch = (c + chunk_cap - 1) / chunk_cap;
+            if (staged) {   // chunks written below, in parallel over the block
+                s_cstart[stoff] = (int)scoff;
+                s_sroff[stoff] = (int)roff;
+                s_scnt[stoff] = c;
+            } else {
+                for (int k = 0; k < nch; ++k) {
+                    const long long ci = sc0 + scoff + k;
+                    if (ci < sc1) {
+                        Chunk ch;
+                        ch.tile = base + i;
+                        ch.begin = (int)(r0 + roff + (long long)k * chunk_cap);
+                        ch.end = (int)(r0 + min(roff + (long long)(k + 1) * chunk_cap, roff + c));
+                        ch.split = 1;
+                        chunks[ci] = ch;
+                    }
+                }
+            }
+            scoff += nch;
+            if (st0 + stoff < st1) split_tiles[st0 + stoff] = base + i;
+            ++stoff;
+        } else if (s_live[i / L.ntx]) {
+            const long long ci = pl0 + nsoff;
+            if (ci < pl1) {
+                Chunk ch;
+                ch.tile = base + i;
+                ch.begin = (int)(r0 + roff);
+                ch.end = (int)(r0 + roff + c);
+                ch.split = 0;
+                chunks[ci] = ch;
+            }
+            ++nsoff;
+        }
+        roff += c;
+        if (!staged) cnt_g[i] = 0;
+    }
+    if (staged) {
+        const int nsplit = (int)TST;
+        if (t == 0) s_cstart[nsplit] = (int)TS;
+        __syncthreads();
+        for (long long ci = t; ci < TS && sc0 + ci < sc1; ci += nt) {
+            int a = 0, bb = nsplit - 1;
+            while (a < bb) {
+                const int mid = (a + bb + 1) >> 1;
+                if (s_cstart[mid] <= ci) a = mid;
+                else bb = mid - 1;
+            }
+            if (st0 + a >= st1) continue;   // region overflow (already flagged)
+            const int k = (int)(ci - s_cstart[a]);
+            const long long ro = s_sroff[a], c = s_scnt[a];
+            Chunk ch;
+            ch.tile = split_tiles[st0 + a];
+            ch.begin = (int)(r0 + ro + (long long)k * chunk_cap);
+            ch.end = (int)(r0 + min(ro + (long long)(k + 1) * chunk_cap, ro + c));
+            ch.split = 1;
+            chunks[sc0 + ci] = ch;
+        }
+    }
+    // padding of unused region entries
+    for (long long ci = sc0 + TS + t; ci < sc1; ci += nt) chunks[ci] = Chunk{base, 0, 0, 1};
+    for (long long ci = pl0 + NS + t; ci < pl1; ci += nt) chunks[ci] = Chunk{base, 0, 0, 1};
+    for (long long i = st0 + TST + t; i < st1; i += nt) split_tiles[i] = -1;
+}
+
 // ------------------------------------------------------------------ plan-time tables
 __global__ void k_twiddles(int n, void* table, int is_double) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -542,24 +860,45 @@ void launch_boundary(const FamilyDev& f, const ChirpParams& cp, cudaStream_t st)
         k_boundary_fourier<<<nblk(f.n_bdry, 128), 128, 0, st>>>(f, cp);
     else if (f.kind == FRESNEL_FAMILY_LINE_RULE)
         k_boundary_line<<<nblk(f.n_bdry, 128), 128, 0, st>>>(f, cp);
-}
-
-void launch_nodes_count_df(const FamilyDev& f, const ChirpParams& cp, NodeRec<float>* rec,
-                           int* counts, unsigned* status, cudaStream_t st) {
-    if (f.n_nodes <= 0) return;
-    k_nodes_count_df<float><<<nblk(f.n_nodes, 256), 256, 0, st>>>(f, cp, rec, counts, status);
+    else if (f.kind == FRESNEL_FAMILY_PETALS && !f.ptab)
+        k_petal_tables<<<nblk(std::max<long long>(f.n_bdry, f.n_panels), 128), 128, 0, st>>>(f);
+    else if (f.kind == FRESNEL_FAMILY_PETALS)
+        k_petal_df_tables<<<nblk(f.n_bdry, 128), 128, 0, st>>>(f, cp);
 }
 
 template <typename T>
-void launch_nodes_count(const FamilyDev& f, const ChirpParams& cp, NodeRec<T>* rec, int* counts,
-                        double* dx, double* dy, double* dw, unsigned* status, cudaStream_t st) {
-    if (f.n_nodes <= 0) return;
-    k_nodes_count<T><<<nblk(f.n_nodes, 256), 256, 0, st>>>(f, cp, rec, counts, dx, dy, dw, status);
+void launch_nodes(const FamTable& ft, int nblocks, NodeRec<T>* rec, int* counts, double* dx,
+                  double* dy, double* dw, unsigned* status, cudaStream_t st) {
+    if (nblocks <= 0) return;
+    k_nodes<T><<<nblocks, kNodeThreads, 0, st>>>(ft, rec, counts, dx, dy, dw, status);
 }
-template void launch_nodes_count<float>(const FamilyDev&, const ChirpParams&, NodeRec<float>*,
-                                        int*, double*, double*, double*, unsigned*, cudaStream_t);
-template void launch_nodes_count<double>(const FamilyDev&, const ChirpParams&, NodeRec<double>*,
-                                         int*, double*, double*, double*, unsigned*, cudaStream_t);
+template void launch_nodes<float>(const FamTable&, int, NodeRec<float>*, int*, double*, double*,
+                                  double*, unsigned*, cudaStream_t);
+template void launch_nodes<double>(const FamTable&, int, NodeRec<double>*, int*, double*,
+                                   double*, double*, unsigned*, cudaStream_t);
+
+template <typename T>
+void launch_scatter_fams(const FamTable& ft, int nblocks, const NodeRec<T>* rec, int* cursor,
+                         NodeRec<T>* sorted, long long cap, unsigned* status, cudaStream_t st) {
+    if (nblocks <= 0) return;
+    k_scatter_fams<T><<<nblocks, kNodeThreads, 0, st>>>(ft, rec, cursor, sorted, cap, status);
+}
+template void launch_scatter_fams<float>(const FamTable&, int, const NodeRec<float>*, int*,
+                                         NodeRec<float>*, long long, unsigned*, cudaStream_t);
+template void launch_scatter_fams<double>(const FamTable&, int, const NodeRec<double>*, int*,
+                                          NodeRec<double>*, long long, unsigned*, cudaStream_t);
+
+void launch_scan_problems(int B, int ntiles, int* counts, int* cursor, Chunk* chunks,
+                          int* split_tiles, const ScanLayout& L, int chunk_cap, unsigned* status,
+                          cudaStream_t st) {
+    const size_t dyn = sizeof(int) * (4 * (size_t)ntiles + 1);
+    const int staged = dyn <= 160 * 1024 ? 1 : 0;
+    if (staged)
+        cudaFuncSetAttribute(k_scan_problems, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn);
+    k_scan_problems<<<B, 1024, staged ? dyn : 0, st>>>(ntiles, counts, cursor, chunks,
+                                                       split_tiles, L, chunk_cap, staged, status);
+}
 
 template <typename T>
 void launch_scatter(long long n, const ChirpParams& cp, const NodeRec<T>* rec, int* cursor,

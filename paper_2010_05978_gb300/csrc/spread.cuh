@@ -68,19 +68,30 @@ struct SpreadSmem {
 };
 
 // Clears the grid tiles that several chunks will add into.
+// Tile ids are global over the problems of a batched plan: problem
+// tile / ntiles, whose grid starts nf1 * nf2 cells after the previous one's.
+template <typename T>
+__device__ __forceinline__ cx_t<T>* tile_origin(cx_t<T>* grid, int tile, int nf1, int nf2,
+                                                int ntx, int ntiles) {
+    const int prob = tile / ntiles, lt = tile - prob * ntiles;
+    return grid + (long long)prob * nf1 * nf2 + (long long)((lt / ntx) * kTile) * nf1 +
+           (lt % ntx) * kTile;
+}
+
 template <typename T>
 __global__ void k_zero_split_tiles(const int* __restrict__ split_tiles,
                                    const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid,
-                                   int nf1, int ntx) {
+                                   int nf1, int nf2, int ntx, int ntiles) {
     const int ns = n_meta[1];
     for (int i = blockIdx.x; i < ns; i += gridDim.x) {
         const int tile = split_tiles[i];
-        const int tx0 = (tile % ntx) * kTile, ty0 = (tile / ntx) * kTile;
+        if (tile < 0) continue;
+        cx_t<T>* dst = tile_origin<T>(grid, tile, nf1, nf2, ntx, ntiles);
         for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
             cx_t<T> z;
             z.x = (T)0;
             z.y = (T)0;
-            grid[(long long)(ty0 + e / kTile) * nf1 + tx0 + e % kTile] = z;
+            dst[(long long)(e / kTile) * nf1 + e % kTile] = z;
         }
     }
 }
@@ -91,7 +102,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks,
          const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid, int* __restrict__ work,
-         int nf1, int nf2, int ntx, T beta, const HornerTab hz) {
+         int nf1, int nf2, int ntx, int ntiles, T beta, const HornerTab hz) {
     constexpr int TT = kTile * kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, W>& sm = *reinterpret_cast<SpreadSmem<T, W>*>(smem_raw);
@@ -104,8 +115,9 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
         const int ci = sm.s_ci;
         if (ci >= n_chunks) break;
         const Chunk ch = chunks[ci];
-        const int tx0 = (ch.tile % ntx) * kTile;
-        const int ty0 = (ch.tile / ntx) * kTile;
+        const int lt = ch.tile % ntiles;
+        const int tx0 = (lt % ntx) * kTile;
+        const int ty0 = (lt / ntx) * kTile;
         for (int e = lane; e < TT; e += 32) {
             cx_t<T> z;
             z.x = (T)0;
@@ -167,7 +179,7 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
         }
         __syncthreads();
         // sum the warps' tiles (fixed order); store, or add into a shared tile
-        cx_t<T>* dst = grid + (long long)ty0 * nf1 + tx0;
+        cx_t<T>* dst = tile_origin<T>(grid, ch.tile, nf1, nf2, ntx, ntiles);
         for (int e = threadIdx.x; e < TT; e += blockDim.x) {
             const int rr = e / kTile, cc = e % kTile;
             cx_t<T> s = sm.tile[0][rr * kTileStride + cc];
@@ -199,10 +211,11 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
 template <typename T, int W>
 void launch_spread_w(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
                      int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
-                     int* work, int nf1, int nf2, int ntx, T beta, const HornerTab& hz,
-                     int nblocks, cudaStream_t st) {
+                     int* work, int nf1, int nf2, int ntx, int ntiles, T beta,
+                     const HornerTab& hz, int nblocks, cudaStream_t st) {
     if (max_split > 0)
-        k_zero_split_tiles<T><<<max_split, 256, 0, st>>>(split_tiles, n_meta, grid, nf1, ntx);
+        k_zero_split_tiles<T><<<max_split, 256, 0, st>>>(split_tiles, n_meta, grid, nf1, nf2,
+                                                         ntx, ntiles);
     const size_t smem = sizeof(SpreadSmem<T, W>);
     cudaFuncSetAttribute(k_spread<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -213,19 +226,20 @@ void launch_spread_w(const NodeRec<T>* sorted, const Chunk* chunks, const int* n
     if (g > max_chunks) g = max_chunks;
     if (g < 1) g = 1;
     k_spread<T, W><<<g, kSpreadWarps * 32, smem, st>>>(sorted, chunks, n_meta, grid, work, nf1,
-                                                       nf2, ntx, beta, hz);
+                                                       nf2, ntx, ntiles, beta, hz);
 }
 
 template <typename T>
 void launch_spread_impl(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
                         int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
-                        int* work, int nf1, int nf2, int ntx, const KernelShape& ks, int nblocks,
-                        cudaStream_t st) {
+                        int* work, int nf1, int nf2, int ntx, int ntiles, const KernelShape& ks,
+                        int nblocks, cudaStream_t st) {
     T beta = (T)ks.beta;
 #define FRES_SPREAD_CASE(WW)                                                                  \
     case WW:                                                                                  \
         launch_spread_w<T, WW>(sorted, chunks, n_meta, max_chunks, split_tiles, max_split,   \
-                               grid, work, nf1, nf2, ntx, beta, ks.horner, nblocks, st);     \
+                               grid, work, nf1, nf2, ntx, ntiles, beta, ks.horner, nblocks,  \
+                               st);                                                          \
         break;
     switch (ks.w) {
         FRES_SPREAD_CASE(2) FRES_SPREAD_CASE(3) FRES_SPREAD_CASE(4) FRES_SPREAD_CASE(5)

@@ -107,7 +107,7 @@ fresnel_status fres_spread_run(const double* g1, const double* g2, const void* c
                        kStandaloneChunkCap, mch, ntiles, st);
     launch_scatter<float>(n, cp, s.rec, s.cursor, s.sorted, max_records(n), s.status, st);
     launch_spread<float>(s.sorted, s.chunks, s.n_meta, mch, s.split_tiles, ntiles, (float2*)grid,
-                         s.work, nf1, nf2, ntx, ks, 0, st);
+                         s.work, nf1, nf2, ntx, ntiles, ks, 0, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fres_fail(FRESNEL_ERR_CUDA, std::string("spread launch: ") + cudaGetErrorString(e));

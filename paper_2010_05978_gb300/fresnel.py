@@ -4,10 +4,11 @@ Argument marshalling only: every step of the computation runs in the CUDA
 kernels of libfresnel.so.  PyTorch supplies device memory and the CUDA stream.
 If the library is missing this module raises; there is no CPU fallback.
 
-Names follow the C ABI: ``fresnel_plan``, ``fresnel_eval``,
-``fresnel_eval_host``, ``fresnel_check``, ``fresnel_destroy``,
-``fresnel_last_error``, ``fresnel_get_info``, ``fresnel_get_nodes``; the
-``Plan`` class wraps them for convenience.
+Names follow the C ABI: ``fresnel_plan``, ``fresnel_plan_many``,
+``fresnel_eval``, ``fresnel_eval_many``, ``fresnel_eval_host``,
+``fresnel_check``, ``fresnel_destroy``, ``fresnel_last_error``,
+``fresnel_get_info``, ``fresnel_get_nodes``; the ``Plan`` and ``BatchPlan``
+classes wrap them for convenience.
 """
 import ctypes
 import os
@@ -20,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libfresnel.so")
 FRESNEL_OK = 0
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_TIMEOUT",
                 -5: "ERR_UNSUPPORTED", -6: "ERR_DEVICE"}
-FAMILY_KINDS = {"fourier": 0, "line_rule": 1, "nodes": 2}
+FAMILY_KINDS = {"fourier": 0, "line_rule": 1, "nodes": 2, "petals": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 OUTPUTS = {"aperture": 0, "occulter": 1}
 GRID, SCATTERED = 0, 1
@@ -36,6 +37,11 @@ class Family(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n_panels", ctypes.c_int), ("p", ctypes.c_int),
                 ("m", ctypes.c_int), ("params", ctypes.POINTER(ctypes.c_double)),
                 ("n_params", ctypes.c_longlong), ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("families", ctypes.POINTER(Family)), ("n_families", ctypes.c_int),
+                ("lam", ctypes.c_double), ("z", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -57,7 +63,8 @@ class Info(ctypes.Structure):
                 ("launches_per_eval", ctypes.c_int)]
 
 
-EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_eval", "fresnel_eval_host",
+EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_plan_many", "fresnel_eval",
+           "fresnel_eval_many", "fresnel_eval_host",
            "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
            "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread",
            "fresnel_spread_noalloc"]
@@ -80,8 +87,13 @@ def load_library(path=LIB_PATH):
     lib.fresnel_plan.argtypes = [ctypes.POINTER(Family), ctypes.c_int, d, d, d,
                                  ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     lib.fresnel_plan.restype = ctypes.c_int
+    lib.fresnel_plan_many.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, d,
+                                      ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.fresnel_plan_many.restype = ctypes.c_int
     lib.fresnel_eval.argtypes = [vp, vp, ll, vp]
     lib.fresnel_eval.restype = ctypes.c_int
+    lib.fresnel_eval_many.argtypes = [vp, vp]
+    lib.fresnel_eval_many.restype = ctypes.c_int
     lib.fresnel_eval_host.argtypes = [vp, vp, ll, vp]
     lib.fresnel_eval_host.restype = ctypes.c_int
     lib.fresnel_check.argtypes = [vp]
@@ -128,10 +140,146 @@ def family_params(fam):
         params = np.ascontiguousarray(np.concatenate(
             [np.asarray(fam[k], np.float64) for k in ("x", "y", "w")]))
         return 2, 0, 0, 0, params, 0.0, 0.0
+    if kind == "petals":
+        prof = fam["profile"]
+        if prof["kind"] == "hg":
+            code, data = 0, [prof["b"], prof["q"]]
+        elif prof["kind"] == "bspline":
+            code, data = 1, prof["coefs"]
+        elif prof["kind"] == "table":
+            code, data = 2, prof["A"]
+        else:
+            raise ValueError("unknown petal profile %r" % prof["kind"])
+        head = [fam["a"], fam["R"], fam.get("n_d", 0), fam.get("m_d", 0), code]
+        params = np.ascontiguousarray(np.concatenate(
+            [np.asarray(head, np.float64), np.asarray(data, np.float64)]))
+        return 3, fam["n_petals"], fam["n_p"], fam["m"], params, fam.get("cx", 0.0), fam.get("cy", 0.0)
     raise ValueError("unknown family kind %r" % kind)
 
 
-class Plan:
+def _family_array(families):
+    """ctypes array of Family structs and the numpy params it points into."""
+    fams = (Family * len(families))()
+    keep = []
+    for i, f in enumerate(families):
+        kind, npan, p, m, params, cx, cy = family_params(f)
+        keep.append(params)
+        fams[i] = Family(kind, int(npan), int(p), int(m),
+                         params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         len(params), float(cx), float(cy))
+    return fams, keep
+
+
+def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes, sync_status,
+               max_device_bytes, t3_binning):
+    o = Opts()
+    lib.fresnel_default_opts(ctypes.byref(o))
+    o.precision = PRECISIONS[precision]
+    o.output = OUTPUTS[output]
+    if grid is not None:
+        o.target_kind = GRID
+        o.grid_n1, o.grid_n2 = int(grid["n1"]), int(grid["n2"])
+        o.grid_h = float(grid["h"])
+        o.grid_x0, o.grid_y0 = float(grid.get("x0", 0.0)), float(grid.get("y0", 0.0))
+    else:
+        o.target_kind = SCATTERED
+        for i in range(4):
+            o.box[i] = float(box[i])
+    o.sigma = float(sigma)
+    o.kernel_w = int(kernel_w)
+    o.recompute_nodes = int(bool(recompute_nodes))
+    o.sync_status = int(bool(sync_status))
+    o.max_device_bytes = int(max_device_bytes)
+    o.t3_binning = int(t3_binning)
+    return o
+
+
+class _PlanHandle:
+    """Methods shared by single and batched plans."""
+
+    def check(self):
+        _check(load_library().fresnel_check(self.handle))
+
+    def info(self):
+        inf = Info()
+        _check(load_library().fresnel_get_info(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def nodes(self):
+        """The plan's quadrature nodes (x, y, w) as float64 CUDA tensors."""
+        torch = self._torch
+        n = self.info()["n_nodes"]
+        x, y, w = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+        _check(load_library().fresnel_get_nodes(self.handle, x.data_ptr(), y.data_ptr(),
+                                                w.data_ptr()))
+        return x, y, w
+
+    def set_timing(self, enable=True):
+        load_library().fresnel_set_timing(self.handle, int(enable))
+
+    def stage_times(self):
+        ms = (ctypes.c_double * 16)()
+        names = (ctypes.c_char_p * 16)()
+        n = load_library().fresnel_stage_times(self.handle, ms, names, 16)
+        return {names[i].decode(): ms[i] for i in range(n)}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().fresnel_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPlan(_PlanHandle):
+    """Several independent problems on one target grid (``fresnel_plan_many``).
+
+    problems: list of dicts {"families": [...], "lam": lambda, "z": z}; the
+    other arguments as for ``Plan`` (grid targets only).  ``eval()`` returns a
+    CUDA tensor of shape (n_problems, n2, n1).
+    """
+
+    def __init__(self, problems, tol, precision="fp32", output="aperture", grid=None, sigma=0.0,
+                 kernel_w=0, recompute_nodes=False, sync_status=True, max_device_bytes=0,
+                 stream=None):
+        import torch
+        lib = load_library()
+        self._torch = torch
+        probs = (Problem * len(problems))()
+        self._keep = []
+        for b, q in enumerate(problems):
+            fams, keep = _family_array(q["families"])
+            self._keep.append((fams, keep))
+            probs[b] = Problem(fams, len(q["families"]), float(q["lam"]), float(q["z"]))
+        o = _make_opts(lib, precision, output, grid, None, sigma, kernel_w, recompute_nodes,
+                       sync_status, max_device_bytes, 0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.fresnel_plan_many(probs, len(problems), float(tol), ctypes.byref(o),
+                                     ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+        self.handle = h
+        self.precision = precision
+        self.grid = grid
+        self.n_problems = len(problems)
+        self.cdtype = torch.complex64 if precision == "fp32" else torch.complex128
+
+    def eval(self, out=None):
+        torch = self._torch
+        shape = (self.n_problems, self.grid["n2"], self.grid["n1"])
+        if out is None:
+            out = torch.empty(shape, dtype=self.cdtype, device="cuda")
+        assert out.is_cuda and out.is_contiguous() and tuple(out.shape) == shape
+        _check(load_library().fresnel_eval_many(self.handle, out.data_ptr()))
+        return out
+
+
+class Plan(_PlanHandle):
     """A libfresnel plan on the current CUDA device and stream.
 
     families: list of panel-family dicts (see workloads.py); lam, z: wavelength
@@ -147,33 +295,9 @@ class Plan:
         import torch
         lib = load_library()
         self._torch = torch
-        fams = (Family * len(families))()
-        keep = []
-        for i, f in enumerate(families):
-            kind, npan, p, m, params, cx, cy = family_params(f)
-            keep.append(params)
-            fams[i] = Family(kind, int(npan), int(p), int(m),
-                             params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                             len(params), float(cx), float(cy))
-        o = Opts()
-        lib.fresnel_default_opts(ctypes.byref(o))
-        o.precision = PRECISIONS[precision]
-        o.output = OUTPUTS[output]
-        if grid is not None:
-            o.target_kind = GRID
-            o.grid_n1, o.grid_n2 = int(grid["n1"]), int(grid["n2"])
-            o.grid_h = float(grid["h"])
-            o.grid_x0, o.grid_y0 = float(grid.get("x0", 0.0)), float(grid.get("y0", 0.0))
-        else:
-            o.target_kind = SCATTERED
-            for i in range(4):
-                o.box[i] = float(box[i])
-        o.sigma = float(sigma)
-        o.kernel_w = int(kernel_w)
-        o.recompute_nodes = int(bool(recompute_nodes))
-        o.sync_status = int(bool(sync_status))
-        o.max_device_bytes = int(max_device_bytes)
-        o.t3_binning = int(t3_binning)
+        fams, keep = _family_array(families)
+        o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
+                       sync_status, max_device_bytes, t3_binning)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -226,43 +350,6 @@ class Plan:
         _check(load_library().fresnel_eval_host(self.handle, tptr, M,
                                                 out.ctypes.data if M > 0 else None))
         return out
-
-    def check(self):
-        _check(load_library().fresnel_check(self.handle))
-
-    def info(self):
-        inf = Info()
-        _check(load_library().fresnel_get_info(self.handle, ctypes.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in Info._fields_}
-
-    def nodes(self):
-        """The plan's quadrature nodes (x, y, w) as float64 CUDA tensors."""
-        torch = self._torch
-        n = self.info()["n_nodes"]
-        x, y, w = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
-        _check(load_library().fresnel_get_nodes(self.handle, x.data_ptr(), y.data_ptr(),
-                                                w.data_ptr()))
-        return x, y, w
-
-    def set_timing(self, enable=True):
-        load_library().fresnel_set_timing(self.handle, int(enable))
-
-    def stage_times(self):
-        ms = (ctypes.c_double * 16)()
-        names = (ctypes.c_char_p * 16)()
-        n = load_library().fresnel_stage_times(self.handle, ms, names, 16)
-        return {names[i].decode(): ms[i] for i in range(n)}
-
-    def close(self):
-        if getattr(self, "handle", None) is not None and self.handle.value:
-            load_library().fresnel_destroy(self.handle)
-            self.handle = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
 
 
 # C-ABI names, for callers that want the flat interface.

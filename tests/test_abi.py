@@ -47,9 +47,10 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_2010_05978_gb300 import fresnel
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "%s"\n'
-                   'int main(void){printf("%%zu %%zu %%zu %%zu %%zu\\n", sizeof(fresnel_opts),'
+                   'int main(void){printf("%%zu %%zu %%zu %%zu %%zu %%zu %%zu\\n", sizeof(fresnel_opts),'
                    ' sizeof(fresnel_family), sizeof(fresnel_info),'
-                   ' offsetof(fresnel_opts, box), offsetof(fresnel_opts, max_device_bytes));'
+                   ' offsetof(fresnel_opts, box), offsetof(fresnel_opts, max_device_bytes),'
+                   ' sizeof(fresnel_problem), offsetof(fresnel_problem, lambda));'
                    'return 0;}\n' % HEADER)
     exe = tmp_path / "sz"
     subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
@@ -57,7 +58,28 @@ def test_struct_layouts_match_header(tmp_path):
                                        check=True).stdout.split()))
     assert got == [ctypes.sizeof(fresnel.Opts), ctypes.sizeof(fresnel.Family),
                    ctypes.sizeof(fresnel.Info), fresnel.Opts.box.offset,
-                   fresnel.Opts.max_device_bytes.offset]
+                   fresnel.Opts.max_device_bytes.offset, ctypes.sizeof(fresnel.Problem),
+                   fresnel.Problem.lam.offset]
+
+
+def test_plan_many_argument_errors(lib):
+    from paper_2010_05978_gb300 import fresnel
+    fams, keep = _disc_family()
+    probs = (fresnel.Problem * 2)()
+    probs[0] = fresnel.Problem(fams, 1, 0.1, 1.0)
+    probs[1] = fresnel.Problem(fams, 1, -0.1, 1.0)
+    o = fresnel.Opts()
+    lib.fresnel_default_opts(ctypes.byref(o))
+    h = ctypes.c_void_p(5)
+    assert lib.fresnel_plan_many(probs, 0, 1e-6, ctypes.byref(o), None, ctypes.byref(h)) == -1
+    assert h.value is None
+    assert lib.fresnel_plan_many(probs, 2, 1e-6, ctypes.byref(o), None, ctypes.byref(h)) == -1
+    assert "lambda" in lib.fresnel_last_error().decode()
+    probs[1] = fresnel.Problem(fams, 1, 0.2, 1.0)
+    o.target_kind = 1
+    assert lib.fresnel_plan_many(probs, 2, 1e-6, ctypes.byref(o), None, ctypes.byref(h)) == -5
+    assert "GRID" in lib.fresnel_last_error().decode()
+    assert lib.fresnel_eval_many(None, None) == -1
 
 
 def test_default_opts(lib):
@@ -91,7 +113,8 @@ def _disc_family():
 
 @pytest.mark.parametrize("case", ["no_families", "bad_lambda", "bad_z", "tol_low", "tol_high",
                                   "fp32_tol", "bad_grid", "bad_box", "bad_kind", "even_params",
-                                  "nan_param", "bad_sigma", "bad_width"])
+                                  "nan_param", "bad_sigma", "bad_width", "petal_radii",
+                                  "petal_profile", "petal_table", "petal_disc"])
 def test_plan_argument_errors(lib, case):
     fams, keep = _disc_family()
     kw = {}
@@ -121,6 +144,15 @@ def test_plan_argument_errors(lib, case):
         fams[0].n_params = 2
     elif case == "nan_param":
         keep[0] = np.nan
+    elif case.startswith("petal"):
+        head = {"petal_radii": [2.0, 1.0, 8, 4, 0, 0.5, 4],
+                "petal_profile": [1.0, 2.0, 8, 4, 5, 0.5, 4],
+                "petal_table": [1.0, 2.0, 8, 4, 2, 0.5, 0.4],
+                "petal_disc": [1.0, 2.0, 8.5, 4, 0, 0.5, 4]}[case]
+        keep = np.array(head, dtype=np.float64)
+        fams[0].kind = 3
+        fams[0].params = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        fams[0].n_params = len(keep)
     elif case == "bad_sigma":
         kw["opts"] = {"sigma": 1.0}
     elif case == "bad_width":
@@ -129,7 +161,7 @@ def test_plan_argument_errors(lib, case):
     # on a machine without a GPU the family checks may surface as a CUDA
     # error instead (they run after the device query); both leave no plan
     expect = {-5} if case == "fp32_tol" else {-1}
-    if case in ("bad_kind", "even_params", "nan_param"):
+    if case in ("bad_kind", "even_params", "nan_param") or case.startswith("petal"):
         expect = expect | {-2}
     assert s in expect, (s, msg)
     assert h is None and msg
@@ -155,3 +187,10 @@ def test_binding_family_marshalling():
     assert (k, npan, p, m) == (1, 3, 1, 5) and len(params) == 12 and params[3] == 1.0
     k, _, _, _, params, _, _ = fresnel.family_params({"kind": "nodes", "x": X, "y": X, "w": X})
     assert k == 2 and len(params) == 9
+    k, npan, p, m, params, cx, _ = fresnel.family_params(
+        W.petal_family(24, 6.0, 14.0, {"kind": "hg", "b": 3.9, "q": 6}, 40, 20, 144, 40, cx=0.5))
+    assert (k, npan, p, m, cx) == (3, 24, 20, 40, 0.5)
+    assert list(params) == [6.0, 14.0, 144, 40, 0, 3.9, 6]
+    _, _, _, _, params, _, _ = fresnel.family_params(
+        W.petal_family(8, 1.0, 2.0, {"kind": "bspline", "coefs": [1, 2, 3, 4, 5]}, 6, 5))
+    assert list(params) == [1.0, 2.0, 0, 0, 1, 1, 2, 3, 4, 5]
