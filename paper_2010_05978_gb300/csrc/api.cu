@@ -766,6 +766,8 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         const double lzb = p->lzs[b];
         c.tile_base = b * p->ntiles;
         if (p->tkind == FRESNEL_GRID) {
+            c.sh1 = p->nf1 / 2 + kTile / 2;   // x~ = 0 -> the middle of a tile
+            c.sh2 = p->nf2 / 2 + kTile / 2;
             c.kq = kPi / lzb;
             c.u1 = p->opts.grid_h / lzb;
             c.u2 = p->opts.grid_h / lzb;
@@ -811,8 +813,8 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
             const double A0 = cp.kq * (f.cx * f.cx + f.cy * f.cy) - cp.a1 * f.cx - cp.a2 * f.cy + cp.a0;
             double G0x, G0y;
             if (!cp.type3) {
-                G0x = (double)cp.nf1 * cp.u1 * f.cx - 0.5 * w;
-                G0y = (double)cp.nf2 * cp.u2 * f.cy - 0.5 * w;
+                G0x = (double)cp.nf1 * cp.u1 * f.cx - 0.5 * w + cp.sh1;
+                G0y = (double)cp.nf2 * cp.u2 * f.cy - 0.5 * w + cp.sh2;
             } else {
                 G0x = (f.cx - cp.C1) * cp.inv_h1 + 0.5 * cp.nf1 - 0.5 * w;
                 G0y = (f.cy - cp.C2) * cp.inv_h2 + 0.5 * cp.nf2 - 0.5 * w;
@@ -961,11 +963,11 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         FRES_TRY(dalloc(p, &p->ay, cs * p->n2 * p->B));
         for (int b = 0; b < p->B; ++b) {   // per problem: the chirp depends on lambda z
             launch_t1_tables(p->n1, p->nf1, p->opts.grid_h, p->opts.grid_x0, p->lzs[b], w,
-                             p->ks.beta, 1, (char*)p->ax + cs * p->n1 * b, dbl, p->gq_t, p->gq_w,
-                             p->gq_n, p->st);
+                             p->ks.beta, 1, p->cps[b].sh1, (char*)p->ax + cs * p->n1 * b, dbl,
+                             p->gq_t, p->gq_w, p->gq_n, p->st);
             launch_t1_tables(p->n2, p->nf2, p->opts.grid_h, p->opts.grid_y0, p->lzs[b], w,
-                             p->ks.beta, 0, (char*)p->ay + cs * p->n2 * b, dbl, p->gq_t, p->gq_w,
-                             p->gq_n, p->st);
+                             p->ks.beta, 0, p->cps[b].sh2, (char*)p->ay + cs * p->n2 * b, dbl,
+                             p->gq_t, p->gq_w, p->gq_n, p->st);
         }
     } else {
         FRES_TRY(dalloc(p, &p->inter, cs * (size_t)p->nf2 * p->nfft1));

@@ -116,6 +116,10 @@ struct ChirpParams {
     int w;
     int ntx, nty;          // tiles per dimension
     int tile_base;         // first tile of this problem in a batched plan (problem * ntx * nty)
+    // type 1: the periodic grid is spread shifted by (sh1, sh2) cells (a node at
+    // x~ = 0 lands mid-tile, so a cluster round the origin does not straddle
+    // the wrap); the output tables undo it with exp(+2 pi i k sh / nf).
+    int sh1, sh2;
 };
 
 // Piecewise-polynomial form of the spreading kernel for FP32: the value at
@@ -219,9 +223,10 @@ template <typename T>
 void launch_scatter(long long n, const ChirpParams& cp, const NodeRec<T>* rec, int* cursor,
                     NodeRec<T>* sorted, long long cap, unsigned* status, cudaStream_t st);
 void launch_twiddles(int n, void* table, int is_double, cudaStream_t st);
-// t1 output tables Ax[k1] = chirp(xi)/(i lz)/psihat(k1), Ay[k2] = chirp(eta)/psihat(k2)
+// t1 output tables Ax[k1] = chirp(xi)/(i lz)/psihat(k1), Ay[k2] = chirp(eta)/psihat(k2),
+// each times exp(2 pi i k shift / nf) for a grid spread shifted by shift cells
 void launch_t1_tables(int n, int nf, double h, double x0, double lz, int w, double beta,
-                      int with_ilz, void* table, int is_double, const double* gq_t,
+                      int with_ilz, int shift, void* table, int is_double, const double* gq_t,
                       const double* gq_w, int q, cudaStream_t st);
 // t3 type-2 deconvolution factors 1/psihat(2 pi l / nfft), l in [-ng/2, ng/2)
 void launch_t3_deconv(int ng, int nfft, int w, double beta, void* table, int is_double,

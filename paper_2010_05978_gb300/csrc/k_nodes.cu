@@ -355,10 +355,12 @@ __device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpPara
     if (!cp.type3) {
         double u = x * cp.u1;
         u -= floor(u);
-        g1 = u * cp.nf1;
+        g1 = u * cp.nf1 + cp.sh1;
+        if (g1 >= cp.nf1) g1 -= cp.nf1;
         double v = y * cp.u2;
         v -= floor(v);
-        g2 = v * cp.nf2;
+        g2 = v * cp.nf2 + cp.sh2;
+        if (g2 >= cp.nf2) g2 -= cp.nf2;
     } else {
         g1 = (x - cp.C1) * cp.inv_h1 + 0.5 * cp.nf1;
         g2 = (y - cp.C2) * cp.inv_h2 + 0.5 * cp.nf2;
@@ -816,8 +818,8 @@ __global__ void k_twiddles(int n, void* table, int is_double) {
 // A[k'] = exp(i pi xi^2 / lz) / psihat(2 pi k / nf) [* 1/(i lz)],
 // xi = x0 + k h, k = k' - floor(n/2).  FP64, phase reduced mod 2 pi.
 __global__ void k_t1_tables(int n, int nf, double h, double x0, double lz, int w, double beta,
-                            int with_ilz, void* table, int is_double, const double* gq_t,
-                            const double* gq_w, int q) {
+                            int with_ilz, int shift, void* table, int is_double,
+                            const double* gq_t, const double* gq_w, int q) {
     int kp = blockIdx.x * blockDim.x + threadIdx.x;
     if (kp >= n) return;
     int k = kp - n / 2;
@@ -825,6 +827,14 @@ __global__ void k_t1_tables(int n, int nf, double h, double x0, double lz, int w
     double ph = reduce_phase(kPi * xi * xi / lz);
     double s, c;
     sincos(ph, &s, &c);
+    // undo the spreading shift: exp(2 pi i k shift / nf), argument exact mod nf
+    long long m = ((long long)k * shift) % nf;
+    if (m < 0) m += nf;
+    double ss, cs;
+    sincospi(2.0 * (double)m / nf, &ss, &cs);
+    const double c2 = c * cs - s * ss, s2 = s * cs + c * ss;
+    c = c2;
+    s = s2;
     double inv = 1.0 / kernel_ft(kTwoPi * k / nf, w, beta, gq_t, gq_w, q);
     double re = c * inv, im = s * inv;
     if (with_ilz) {   // times 1/(i lz) = -i / lz
@@ -937,9 +947,9 @@ void launch_twiddles(int n, void* table, int is_double, cudaStream_t st) {
 }
 
 void launch_t1_tables(int n, int nf, double h, double x0, double lz, int w, double beta,
-                      int with_ilz, void* table, int is_double, const double* gq_t,
+                      int with_ilz, int shift, void* table, int is_double, const double* gq_t,
                       const double* gq_w, int q, cudaStream_t st) {
-    k_t1_tables<<<nblk(n, 128), 128, 0, st>>>(n, nf, h, x0, lz, w, beta, with_ilz, table,
+    k_t1_tables<<<nblk(n, 128), 128, 0, st>>>(n, nf, h, x0, lz, w, beta, with_ilz, shift, table,
                                               is_double, gq_t, gq_w, q);
 }
 
