@@ -50,11 +50,12 @@ def workload():
 
 
 SWEEP_METRIC = "starshade wavelength sweeps/sec (64 lambda, 512^2 pupil grid, 1e-6 rel L2)"
+SWEEP_METRIC_N = "starshade wavelength sweeps/sec (%d lambda, 512^2 pupil grid, 1e-6 rel L2)"
 SWEEP_UNIT = "sweeps/s"
 
 
-def sweep_workload():
-    cfg = W.starshade_sweep(64)
+def sweep_workload(n_lambda=64):
+    cfg = W.starshade_sweep(n_lambda)
     g = cfg["grid"]
     gx, gy = np.meshgrid(g["h"] * np.arange(-256, 256), g["h"] * np.arange(-256, 256))
     in_pupil = int(np.count_nonzero(gx * gx + gy * gy <= cfg["pupil_radius"] ** 2))
@@ -62,9 +63,10 @@ def sweep_workload():
 
 
 def sweep_config(cfg, in_pupil, n_gpus):
-    return {"workload": "hg24_sweep64: 24-petal HG starshade A=exp(-((r-6)/3.9)^6) on [6,14] m, "
-                        "z=3.7e7 m, 64 lambda in [400,1000] nm (F=13.2..5.3), u^oc on 512x512 grid "
-                        "h=2.4/512 m over the pupil",
+    nl = len(cfg["problems"])
+    return {"workload": "hg24_sweep%d: 24-petal HG starshade A=exp(-((r-6)/3.9)^6) on [6,14] m, "
+                        "z=3.7e7 m, %d lambda in [400,1000] nm (F=13.2..5.3), u^oc on 512x512 grid "
+                        "h=2.4/512 m over the pupil" % (nl, nl),
             "n_lambda": len(cfg["problems"]), "grid": "512x512", "in_pupil_targets": in_pupil,
             "tol": TOL, "precision": "fp32 spread/fft, double-float/fp64 phases",
             "nodes_recomputed_each_step": True,
@@ -361,16 +363,16 @@ def sweep_oracle_rate(cfg, budget_s):
         t_total += time.perf_counter() - t0
         n_total += m
     per_target = t_total / n_total
-    sweep_s = per_target * len(gx) * len(cfg["problems"])
+    sweep_s = per_target * len(gx) * len(cfg["problems"])   # the whole sweep
     return {"value": 1.0 / sweep_s, "unit": SWEEP_UNIT, "cores": direct.max_threads(),
             "kind": "oracle",
             "sample": "%d grid targets at each of 3 wavelengths (400, ~700, 1000 nm), quadrature "
-                      "rebuilt + direct O(NM) FP64 sum (eq. faq), %.1f s; scaled to 64 x 512^2"
-                      % (m, t_total)}
+                      "rebuilt + direct O(NM) FP64 sum (eq. faq), %.1f s; scaled to %d x 512^2"
+                      % (m, t_total, len(cfg["problems"]))}
 
 
 def run_sweep_reference(args, rank, world):
-    cfg, in_pupil = sweep_workload()
+    cfg, in_pupil = sweep_workload(args.lambdas)
     from oracle import build as obuild
     obuild.build()
     if rank != 0:
@@ -380,7 +382,8 @@ def run_sweep_reference(args, rank, world):
     vals = [sweep_oracle_rate(cfg, 6.0)["value"] for _ in range(args.steps)]
     r = sweep_oracle_rate(cfg, 1.0)
     v = statistics.median(vals)
-    line = {"impl": "reference", "metric": SWEEP_METRIC, "value": v, "unit": SWEEP_UNIT,
+    line = {"impl": "reference", "metric": SWEEP_METRIC_N % args.lambdas, "value": v,
+            "unit": SWEEP_UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -403,7 +406,7 @@ def run_sweep(args, rank, world, local_rank):
         build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    cfg, in_pupil = sweep_workload()
+    cfg, in_pupil = sweep_workload(args.lambdas)
     g = cfg["grid"]
     B = len(cfg["problems"])
     stream = torch.cuda.current_stream()
@@ -471,7 +474,7 @@ def run_sweep(args, rank, world, local_rank):
     achieved = ab[dominant] / (per_launch[dominant] * 1e-3) / 1e9
     cpu = sweep_oracle_rate(cfg, 10.0)
     line = {
-        "metric": SWEEP_METRIC, "value": value, "unit": SWEEP_UNIT, "n_gpus": world,
+        "metric": SWEEP_METRIC_N % B, "value": value, "unit": SWEEP_UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": sweep_config(cfg, in_pupil, world),
@@ -498,6 +501,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="star5_F100", choices=["star5_F100", "starshade_sweep"])
+    ap.add_argument("--lambdas", type=int, default=64,
+                    help="starshade_sweep only: wavelengths per sweep (64 is the benchmark; "
+                         "fewer for small profiling captures)")
     args = ap.parse_args()
     sweep = args.workload == "starshade_sweep"
     rank = int(os.environ.get("RANK", "0"))

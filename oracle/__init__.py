@@ -25,6 +25,10 @@ arXiv:2010.05978, that it follows):
                       integration of eq. fres on tiny cases.
 * ``field``        -- the whole field u^ap / u^oc = 1 - u^ap (eq. bab) for a
                       list of panel families, built only from the above.
+* ``gradient``     -- a starshade loss (mean |u^oc|^2 over kept targets and
+                      problems) and its gradient with respect to the
+                      B-spline petal profile, by differentiating the direct
+                      sum of eq. faq by hand (adjoint sums in direct.c).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, invariants or brute force; none is "parity unpinned".

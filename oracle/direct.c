@@ -115,6 +115,51 @@ void oracle_sum3(long long n_nodes, const double* x, const double* y, const doub
     }
 }
 
+/*
+ * Adjoint sums for the gradient of a real loss of the field (derivative of
+ * eq. faq with respect to the nodes and weights): for node j and complex
+ * target coefficients g_k,
+ *   P_j  = sum_k g_k exp(i phi_jk),
+ *   Qx_j = sum_k g_k exp(i phi_jk) (x_j - xi_k),  Qy_j likewise with y, eta,
+ * phi_jk = pi [(xi_k - x_j)^2 + (eta_k - y_j)^2] / lz.  One thread per node,
+ * fixed-order blocked sums over targets.
+ */
+void oracle_adjoint(long long n_nodes, const double* x, const double* y, long long n_targets,
+                    const double* xi, const double* eta, double lz, const double* g_re,
+                    const double* g_im, double* P, double* Qx, double* Qy)
+{
+    const double k = M_PI / lz;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long j = 0; j < n_nodes; ++j) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};   /* P re/im, Qx re/im, Qy re/im */
+        for (long long t0 = 0; t0 < n_targets; t0 += ORACLE_BLOCK) {
+            long long t1 = t0 + ORACLE_BLOCK < n_targets ? t0 + ORACLE_BLOCK : n_targets;
+            double b[6] = {0, 0, 0, 0, 0, 0};
+            for (long long t = t0; t < t1; ++t) {
+                double dx = x[j] - xi[t];
+                double dy = y[j] - eta[t];
+                double phi = k * (dx * dx + dy * dy);
+                double c = cos(phi), s = sin(phi);
+                double er = g_re[t] * c - g_im[t] * s;   /* g exp(i phi) */
+                double ei = g_re[t] * s + g_im[t] * c;
+                b[0] += er;
+                b[1] += ei;
+                b[2] += er * dx;
+                b[3] += ei * dx;
+                b[4] += er * dy;
+                b[5] += ei * dy;
+            }
+            for (int q = 0; q < 6; ++q) acc[q] += b[q];
+        }
+        P[2 * j] = acc[0];
+        P[2 * j + 1] = acc[1];
+        Qx[2 * j] = acc[2];
+        Qx[2 * j + 1] = acc[3];
+        Qy[2 * j] = acc[4];
+        Qy[2 * j + 1] = acc[5];
+    }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

@@ -16,6 +16,7 @@ def _load():
         _lib.oracle_direct.argtypes = [ll, d, d, d, ll, d, d, ctypes.c_double, d, d]
         _lib.oracle_nsli.argtypes = [ll, d, d, d, d, ll, d, d, ctypes.c_double, d, d]
         _lib.oracle_sum3.argtypes = [ll, d, d, d, d, ll, d, d, ctypes.c_double, d, d]
+        _lib.oracle_adjoint.argtypes = [ll, d, d, ll, d, d, ctypes.c_double, d, d, d, d, d]
         _lib.oracle_max_threads.restype = ctypes.c_int
     return _lib
 
@@ -66,3 +67,18 @@ def sum3(x, y, c, xi, eta, lz):
     lib.oracle_sum3(len(x), _p(x), _p(y), _p(cr), _p(ci), len(xi), _p(xi), _p(eta), float(lz),
                     _p(re), _p(im))
     return re + 1j * im
+
+
+def adjoint_sums(x, y, xi, eta, lz, g):
+    """P_j = sum_k g_k e^{i phi_jk} and Q_j = sum_k g_k e^{i phi_jk} (x_j - xi_k) (2-vector)."""
+    lib = _load()
+    x, y, xi, eta = map(_c, (x, y, xi, eta))
+    g = np.asarray(g, dtype=np.complex128)
+    gr, gi = _c(g.real), _c(g.imag)
+    P = np.empty(2 * len(x))
+    Qx = np.empty(2 * len(x))
+    Qy = np.empty(2 * len(x))
+    lib.oracle_adjoint(len(x), _p(x), _p(y), len(xi), _p(xi), _p(eta), float(lz), _p(gr), _p(gi),
+                       _p(P), _p(Qx), _p(Qy))
+    v = lambda a: a[0::2] + 1j * a[1::2]
+    return v(P), v(Qx), v(Qy)

@@ -351,6 +351,68 @@ def test_planted_petals_off_centre(monkeypatch):
     assert abs(u - ref) > 1e-4
 
 
+# ------------------------------------------------------------------ spline-profile gradient
+def _spline_case(kind="hg24", n=20):
+    """Spline-profile starshades: "hg24" is the 24-petal occulter at two
+    wavelengths on a pupil grid (the tangential node motion cancels there over
+    the petals: only angular harmonics of order 24 survive, and their Bessel
+    factors J_24(2 pi r rho / lz) are ~1e-11); "small" is a 5-petal shape seen
+    far off axis, where both weight and node-motion terms matter."""
+    if kind == "hg24":
+        a, R, Np, b, lams, z, ng, half = 6.0, 14.0, 24, 3.9, (500e-9, 900e-9), 3.7e7, 24, 1.2
+        res = (40, 20, 144, 40)
+    else:
+        a, R, Np, b, lams, z, ng, half = 0.4, 1.0, 5, 0.35, (0.03, 0.05), 1.0, 16, 1.5
+        res = (30, 24, 40, 30)
+    t = Q.bspline_knots(a, R, n)
+    grev = (t[1:n + 1] + t[2:n + 2] + t[3:n + 3]) / 3.0
+    theta = np.exp(-((grev - a) / b) ** 6) + 1e-3 * W.rng(4, 1).standard_normal(n)
+    probs = [{"family": W.petal_family(Np, a, R, {"kind": "bspline", "coefs": theta}, *res),
+              "lam": lam, "z": z} for lam in lams]
+    grid = W.grid_spec(ng, ng, 2 * half / ng, x0=0.013)
+    xi, eta = oracle.grid_targets(ng, ng, 2 * half / ng, 0.013)
+    return theta, probs, grid, xi * xi + eta * eta <= half ** 2
+
+
+def test_spline_loss_gradient_matches_central_differences():
+    """Adjoint gradient of the mean pupil intensity w.r.t. the B-spline
+    coefficients against central differences (h = 1e-6) of the loss itself."""
+    from oracle import gradient as G
+    for kind in ("hg24", "small"):
+        theta, probs, grid, keep = _spline_case(kind)
+        _check_gradient(G, theta, probs, grid, keep)
+
+
+def _check_gradient(G, theta, probs, grid, keep):
+    L, g = G.loss_and_grad(theta, probs, grid, keep)
+    assert abs(L - G.loss(theta, probs, grid, keep)) < 1e-14
+    h = 1e-6
+    for m in (0, 3, 10, 17, 19):
+        e = np.zeros_like(theta)
+        e[m] = h
+        fd = (G.loss(theta + e, probs, grid, keep) - G.loss(theta - e, probs, grid, keep)) / (2 * h)
+        assert abs(g[m] - fd) <= 1e-7 * max(abs(fd), 1e-3), (m, g[m], fd)
+
+
+def test_planted_gradient_without_node_motion(monkeypatch):
+    """Dropping the node-position term of the adjoint (weights only) fails the
+    central-difference pin."""
+    from oracle import gradient as G
+    theta, probs, grid, keep = _spline_case("small")
+    orig = G.direct.adjoint_sums
+
+    def bad(x, y, xi, eta, lz, g):
+        P, Qx, Qy = orig(x, y, xi, eta, lz, g)
+        return P, 0 * Qx, 0 * Qy
+    with monkeypatch.context() as mp:
+        mp.setattr(G.direct, "adjoint_sums", bad)
+        _, g = G.loss_and_grad(theta, probs, grid, keep)
+    e = np.zeros_like(theta)
+    e[10] = 1e-6
+    fd = (G.loss(theta + e, probs, grid, keep) - G.loss(theta - e, probs, grid, keep)) / 2e-6
+    assert abs(g[10] - fd) > 1e-3 * abs(fd)
+
+
 # ------------------------------------------------------------------ planted mistakes
 def _pins_fail(monkeypatch, patch):
     """Apply a plausible oracle bug and report whether the closed-form pins notice it."""
