@@ -192,6 +192,27 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
 fresnel_status fresnel_eval_many(fresnel_plan_t plan, void* d_out);
 
 /*
+ * Gradient of a real loss of a GRID plan's output with respect to the
+ * profile parameters of its FRESNEL_FAMILY_PETALS families (Sec. 4.2: the
+ * apodisation A(r) sets the petal widths), for optimising starshade designs.
+ * d_gamma (DEVICE, the same layout and type as the output of
+ * fresnel_eval_many / fresnel_eval: n_problems * grid_n2 * grid_n1 complex)
+ * holds the loss's sensitivity: dL = Re sum_k conj(gamma_k) du_k for
+ * perturbations du of the plan's output field (u^ap or u^oc as configured);
+ * for L = sum |u_k|^2, gamma = 2 u.  d_grad (DEVICE, FP64) receives, for every
+ * PETALS family in plan order (problem-major, then family order), dL/dparam
+ * for its profile data params[5...]: [b, q] for FRESNEL_PETAL_HG, the n
+ * spline coefficients for FRESNEL_PETAL_BSPLINE, the m values of A for
+ * FRESNEL_PETAL_TABLE.  It is the exact derivative of the computed
+ * (discretised) field: the adjoint of the spreading / FFT / output chain is a
+ * type-2 transform interpolated at the nodes with the kernel and its
+ * derivative.  The quadrature nodes are taken as last evaluated (call after
+ * an evaluation with the same profile).  Reuses the plan's spreading grid.
+ * Asynchronous unless opts.sync_status = 1.
+ */
+fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, double* d_grad);
+
+/*
  * Evaluates u at the plan's targets (plans with one problem).
  * GRID plans: d_targets is ignored (may be NULL) and M must equal n1 * n2.
  * SCATTERED plans: d_targets is a DEVICE array of M (xi, eta) FP64 pairs

@@ -115,6 +115,14 @@ struct Plan {
     int nev = 0;
     int launches = 0;
     int last_launches = 0;     // kernels launched by the most recent evaluation
+    // profile-gradient scratch (allocated on first use)
+    void* adj_in = nullptr;       // B x n2 x n1: sgn conj(gamma) ax ay
+    void* adj_rows = nullptr;     // B x n2 x nf1 after the row pass
+    double* contrib = nullptr;    // per node dL/dA contribution
+    int* pf = nullptr;            // PETALS families (indices into fams)
+    long long* gofs = nullptr;    // their offsets in the gradient output
+    int npf = 0;
+    long long n_grad = 0;
 
     size_t csize() const { return prec == FRESNEL_FP64 ? 16 : 8; }
     size_t rsize() const { return prec == FRESNEL_FP64 ? sizeof(NodeRec<double>) : sizeof(NodeRec<float>); }
@@ -1025,6 +1033,73 @@ Plan* as_plan(fresnel_plan_t h) {
 
 struct fresnel_plan_s {};   // opaque handle type; the handle points at a Plan
 
+namespace {
+template <typename T>
+fresnel_status grad_profile_impl(Plan* p, const void* d_gamma, double* d_grad) {
+    const bool dbl = sizeof(T) == 8;
+    const size_t cs = p->csize();
+    if (!p->adj_in) {
+        std::vector<int> pf;
+        std::vector<long long> gofs;
+        long long off = 0;
+        for (int i = 0; i < (int)p->fams.size(); ++i)
+            if (p->fams[i].kind == FRESNEL_FAMILY_PETALS) {
+                pf.push_back(i);
+                gofs.push_back(off);
+                off += p->fams[i].n_prof;
+            }
+        FRES_TRY(dalloc(p, &p->adj_in, cs * (size_t)p->n1 * p->n2 * p->B));
+        FRES_TRY(dalloc(p, &p->adj_rows, cs * (size_t)p->n2 * p->nf1 * p->B));
+        FRES_TRY(dalloc(p, (void**)&p->contrib, sizeof(double) * p->N));
+        FRES_TRY(dalloc(p, (void**)&p->pf, sizeof(int) * std::max<size_t>(1, pf.size())));
+        FRES_TRY(dalloc(p, (void**)&p->gofs, sizeof(long long) * std::max<size_t>(1, gofs.size())));
+        if (!pf.empty()) {
+            FRES_CK(cudaMemcpyAsync(p->pf, pf.data(), sizeof(int) * pf.size(), cudaMemcpyHostToDevice, p->st));
+            FRES_CK(cudaMemcpyAsync(p->gofs, gofs.data(), sizeof(long long) * gofs.size(),
+                                    cudaMemcpyHostToDevice, p->st));
+        }
+        FRES_CK(cudaStreamSynchronize(p->st));
+        p->npf = (int)pf.size();
+        p->n_grad = off;
+    }
+    if (p->n_grad > 0) FRES_CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * p->n_grad, p->st));
+    launch_adj_prologue<T>(d_gamma, p->ax, p->ay, p->adj_in, p->n1, p->n2, p->B,
+                           p->output == FRESNEL_OCCULTER, p->st);
+    RowPassArgs ra{};
+    ra.in = p->adj_in;
+    ra.out = p->adj_rows;
+    ra.in_stride = p->n1;
+    ra.out_stride = p->nf1;
+    ra.nrows = p->n2 * p->B;
+    ra.in_len = p->n1;
+    ra.centered_in = 1;
+    ra.out_len = p->nf1;
+    ra.twiddle = p->tw1;
+    launch_fft_rows<T>(p->fp1, ra, p->st);
+    ColPassArgs ca{};
+    ca.in = p->adj_rows;
+    ca.out = p->grid;
+    ca.ncols = p->nf1;
+    ca.in_len = p->n2;
+    ca.centered_in = 1;
+    ca.out_len = p->nf2;
+    ca.twiddle = p->tw2;
+    ca.out_is_final = 0;
+    ca.batch = p->B;
+    ca.in_bstride = (long long)p->n2 * p->nf1;
+    ca.out_bstride = (long long)p->nf2 * p->nf1;
+    launch_fft_cols<T>(p->fp2, ca, p->st);
+    launch_adj_nodes<T>(p->ft, p->node_blocks, p->grid, p->nf1, p->nf2, p->ks, p->contrib, p->st);
+    launch_adj_reduce(p->ft.fams, p->pf, p->gofs, p->npf, p->contrib, d_grad, p->st);
+    (void)dbl;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return FRESNEL_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void fresnel_default_opts(fresnel_opts* o) {
@@ -1173,6 +1248,22 @@ fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, l
     if (M > 0)
         FRES_CK(cudaMemcpyAsync(h_out, p->stage_out, p->csize() * (size_t)M, cudaMemcpyDeviceToHost, p->st));
     return read_status(p);
+}
+
+fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, double* d_grad) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (p->tkind != FRESNEL_GRID)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients need a GRID plan");
+    bool any = false;
+    for (const FamilyDev& f : p->fams) any = any || f.kind == FRESNEL_FAMILY_PETALS;
+    if (!any) return fres_fail(FRESNEL_ERR_ARG, "the plan has no PETALS family");
+    if (!d_gamma || !d_grad) return fres_fail(FRESNEL_ERR_ARG, "d_gamma or d_grad is NULL");
+    fresnel_status s = p->prec == FRESNEL_FP64 ? grad_profile_impl<double>(p, d_gamma, d_grad)
+                                               : grad_profile_impl<float>(p, d_gamma, d_grad);
+    if (s != FRESNEL_OK) return s;
+    if (p->opts.sync_status) return read_status(p);
+    return FRESNEL_OK;
 }
 
 fresnel_status fresnel_check(fresnel_plan_t plan) {

@@ -58,6 +58,10 @@ struct FftPlan {
     int n;
     int nstages;
     int radix[kMaxRadixStages];
+    // stage s: p = product of the earlier radices and ceil(2^32 / p), so that
+    // i / p = umulhi(i, pmagic) exactly for i * p < 2^32 (p = 1: magic 0)
+    int p[kMaxRadixStages];
+    unsigned pmagic[kMaxRadixStages];
 };
 
 // One node family resident on the device.
@@ -242,6 +246,16 @@ void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_m
                    int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
                    int* work, int nf1, int nf2, int ntx, int ntiles, const KernelShape& ks,
                    int nblocks, cudaStream_t st);
+
+// k_adjoint.cu (derivatives of type-1 plans with respect to petal profiles)
+template <typename T>
+void launch_adj_prologue(const void* gamma, const void* ax, const void* ay, void* out, int n1,
+                         int n2, int B, int occulter, cudaStream_t st);
+template <typename T>
+void launch_adj_nodes(const FamTable& ft, int nblocks, const void* bt, int nf1, int nf2,
+                      const KernelShape& ks, double* contrib, cudaStream_t st);
+void launch_adj_reduce(const FamilyDev* fams, const int* pf, const long long* gofs, int npf,
+                       const double* contrib, double* grad, cudaStream_t st);
 
 // k_fft.cu
 struct RowPassArgs {

@@ -159,55 +159,57 @@ template <typename T> struct Dft<T, 16> {
 __host__ __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 __host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4) + 1; }
 
-// One Stockham stage of radix R from smem array src[n][ncol] to dst[n][ncol]
-// (column c of element e at [e * ncol + c]); out of place, so each thread
-// holds one butterfly at a time and one barrier ends the stage.
-template <typename T, int R>
+// One Stockham stage of radix R from smem array src[n][NCOL] to dst[n][NCOL]
+// (column c of element e at [pad(e) * NCOL + c]); out of place, so each
+// thread holds one butterfly at a time and one barrier ends the stage.
+// NCOL is a power of two; k = i mod p comes from the plan's magic multiplier.
+template <typename T, int R, int NCOL>
 __device__ __forceinline__ void stage(const cx_t<T>* __restrict__ src, cx_t<T>* __restrict__ dst,
-                                      int n, int ncol, int p, const cx_t<T>* __restrict__ tw) {
+                                      int n, int p, unsigned pmagic,
+                                      const cx_t<T>* __restrict__ tw) {
     using O = Ops<T>;
     using C = cx_t<T>;
     const int nb = n / R;
-    const int items = nb * ncol;
+    const int items = nb * NCOL;
     const int twstep = n / (p * R);
     for (int w = threadIdx.x; w < items; w += blockDim.x) {
-        const int c = w % ncol, i = w / ncol, k = i % p;
+        const int c = w & (NCOL - 1), i = w / NCOL;
+        const int k = p == 1 ? 0 : i - (int)__umulhi((unsigned)i, pmagic) * p;
+        const int kt = k * twstep;
         C u[R], y[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            u[q] = src[pad(i + q * nb) * ncol + c];
-            if (q > 0 && k > 0) u[q] = O::mul(u[q], __ldg(&tw[q * k * twstep]));
+            u[q] = src[pad(i + q * nb) * NCOL + c];
+            if (q > 0 && k > 0) u[q] = O::mul(u[q], __ldg(&tw[q * kt]));
         }
         Dft<T, R>::run(u, y);
         const int j = (i - k) * R + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) dst[pad(j + t * p) * ncol + c] = y[t];
+        for (int t = 0; t < R; ++t) dst[pad(j + t * p) * NCOL + c] = y[t];
     }
     __syncthreads();
 }
 
 // Runs the plan's stages ping-ponging between A and B; returns the buffer
 // holding the result (natural order).
-template <typename T>
-__device__ cx_t<T>* fft_smem(cx_t<T>* A, cx_t<T>* B, int ncol, const FftPlan& fp,
-                             const cx_t<T>* tw) {
-    int p = 1;
+template <typename T, int NCOL>
+__device__ cx_t<T>* fft_smem(cx_t<T>* A, cx_t<T>* B, const FftPlan& fp, const cx_t<T>* tw) {
     for (int s = 0; s < fp.nstages; ++s) {
-        const int r = fp.radix[s];
+        const int r = fp.radix[s], p = fp.p[s];
+        const unsigned mg = fp.pmagic[s];
         switch (r) {
             case 16:
-                if constexpr (sizeof(T) == 4) stage<T, 16>(A, B, fp.n, ncol, p, tw);
+                if constexpr (sizeof(T) == 4) stage<T, 16, NCOL>(A, B, fp.n, p, mg, tw);
                 break;
-            case 8: stage<T, 8>(A, B, fp.n, ncol, p, tw); break;
-            case 4: stage<T, 4>(A, B, fp.n, ncol, p, tw); break;
-            case 2: stage<T, 2>(A, B, fp.n, ncol, p, tw); break;
-            case 3: stage<T, 3>(A, B, fp.n, ncol, p, tw); break;
-            case 5: stage<T, 5>(A, B, fp.n, ncol, p, tw); break;
+            case 8: stage<T, 8, NCOL>(A, B, fp.n, p, mg, tw); break;
+            case 4: stage<T, 4, NCOL>(A, B, fp.n, p, mg, tw); break;
+            case 2: stage<T, 2, NCOL>(A, B, fp.n, p, mg, tw); break;
+            case 3: stage<T, 3, NCOL>(A, B, fp.n, p, mg, tw); break;
+            case 5: stage<T, 5, NCOL>(A, B, fp.n, p, mg, tw); break;
         }
         cx_t<T>* t = A;
         A = B;
         B = t;
-        p *= r;
     }
     return A;
 }
@@ -283,7 +285,7 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
         __syncthreads();
         const int nxt = next_live(row + gridDim.x);
         if (nxt < a.nrows) prefetch(nxt);
-        const C* R = fft_smem<T>(S, S2, 1, fp, tw);
+        const C* R = fft_smem<T, 1>(S, S2, fp, tw);
         C* out = (C*)a.out + (long long)row * a.out_stride;
         for (int kp = threadIdx.x; kp < a.out_len; kp += blockDim.x)
             out[kp] = R[pad(out_src(kp, a.out_len, n))];
@@ -292,74 +294,84 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
     }
 }
 
-template <typename T>
+template <typename T, int NCOL>
 __global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm)
-k_fft_cols(FftPlan fp, ColPassArgs a, int ncol) {
+k_fft_cols(FftPlan fp, ColPassArgs a) {
     using C = cx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned s_live[kMaxTileRows / 32];
     C* S = (C*)smem_raw;
-    C* S2 = S + padded_len(fp.n) * ncol;
+    C* S2 = S + padded_len(fp.n) * NCOL;
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
-    const int ngroups = (a.ncols + ncol - 1) / ncol;
+    const int ngroups = (a.ncols + NCOL - 1) / NCOL;
     const int total = ngroups * max(a.batch, 1);   // (transform, column group) work items
+    const int c = threadIdx.x & (NCOL - 1);        // this thread's column in every group
+    const int r0 = threadIdx.x / NCOL, rstep = blockDim.x / NCOL;
     // Inputs of the block's next work item are prefetched into registers
     // (first kPrefetch * blockDim.x of them) while the current one runs.
     C buf[kPrefetch];
-    const int nin = a.in_len * ncol;
-    const int npf = min(nin, kPrefetch * (int)blockDim.x);
-    // input row i of transform bi: zero without a load when its tile row is dead
-    auto load = [&](const C* in, const int* lv, int i, int col) {
-        if (col >= a.ncols || (lv && !lv[i / kTile])) return Ops<T>::mk(0, 0);
-        return in[(long long)i * a.ncols + col];
+    const int npf_rows = min(a.in_len, kPrefetch * rstep);
+    // live-row bit of input row i of transform bi (all live without a map)
+    auto live_bit = [&](int bi, int i) {
+        return !a.live || a.live[(long long)bi * a.nty + i / kTile] != 0;
     };
     auto prefetch = [&](int gg) {
-        const int bi = gg / ngroups, c0 = (gg - bi * ngroups) * ncol;
-        const C* in = (const C*)a.in + (long long)bi * a.in_bstride;
-        const int* lv = a.live ? a.live + (long long)bi * a.nty : nullptr;
+        const int bi = gg / ngroups, col = (gg - bi * ngroups) * NCOL + c;
+        const C* in = (const C*)a.in + (long long)bi * a.in_bstride + col;
 #pragma unroll
         for (int k = 0; k < kPrefetch; ++k) {
-            const int e = threadIdx.x + k * blockDim.x;
-            if (e < npf) buf[k] = load(in, lv, e / ncol, c0 + e % ncol);
+            const int i = r0 + k * rstep;
+            buf[k] = (i < npf_rows && col < a.ncols && live_bit(bi, i))
+                         ? in[(long long)i * a.ncols] : Ops<T>::mk(0, 0);
         }
     };
     if (blockIdx.x < total) prefetch(blockIdx.x);
     for (int gg = blockIdx.x; gg < total; gg += gridDim.x) {
-        const int bi = gg / ngroups, c0 = (gg - bi * ngroups) * ncol;
-        const C* in = (const C*)a.in + (long long)bi * a.in_bstride;
+        const int bi = gg / ngroups, c0 = (gg - bi * ngroups) * NCOL;
+        const int col = c0 + c;
+        const C* in = (const C*)a.in + (long long)bi * a.in_bstride + col;
+        if (a.live) {
+            for (int t = threadIdx.x; t < kMaxTileRows / 32; t += blockDim.x) s_live[t] = 0u;
+            __syncthreads();
+            for (int t = threadIdx.x; t < a.nty; t += blockDim.x)
+                if (a.live[(long long)bi * a.nty + t]) atomicOr(&s_live[t >> 5], 1u << (t & 31));
+        }
         if (a.centered_in || a.in_len < n)
-            for (int e = threadIdx.x; e < padded_len(n) * ncol; e += blockDim.x)
+            for (int e = threadIdx.x; e < padded_len(n) * NCOL; e += blockDim.x)
                 S[e] = Ops<T>::mk(0, 0);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kPrefetch; ++k) {
-            const int e = threadIdx.x + k * blockDim.x;
-            if (e < npf) {
-                const int i = e / ncol, c = e % ncol;
-                S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = buf[k];
-            }
+            const int i = r0 + k * rstep;
+            if (i < npf_rows) S[pad(in_pos(i, a.in_len, n, a.centered_in)) * NCOL + c] = buf[k];
         }
-        const int* lv = a.live ? a.live + (long long)bi * a.nty : nullptr;
-        for (int e = npf + threadIdx.x; e < nin; e += blockDim.x) {
-            const int i = e / ncol, c = e % ncol;
-            S[pad(in_pos(i, a.in_len, n, a.centered_in)) * ncol + c] = load(in, lv, i, c0 + c);
+        for (int i = npf_rows + r0; i < a.in_len; i += rstep) {
+            C v = Ops<T>::mk(0, 0);
+            const int tr = i / kTile;
+            if (col < a.ncols && (!a.live || ((s_live[tr >> 5] >> (tr & 31)) & 1u)))
+                v = in[(long long)i * a.ncols];
+            S[pad(in_pos(i, a.in_len, n, a.centered_in)) * NCOL + c] = v;
         }
         __syncthreads();
         if (gg + (int)gridDim.x < total) prefetch(gg + gridDim.x);
-        const C* R = fft_smem<T>(S, S2, ncol, fp, tw);
+        const C* R = fft_smem<T, NCOL>(S, S2, fp, tw);
         C* out = (C*)a.out + (long long)bi * a.out_bstride;
-        const C* ax = a.ax ? (const C*)a.ax + (long long)bi * a.ncols : nullptr;
-        const C* ay = a.ax ? (const C*)a.ay + (long long)bi * a.out_len : nullptr;
-        for (int e = threadIdx.x; e < a.out_len * ncol; e += blockDim.x) {
-            const int kp = e / ncol, c = e % ncol;
-            if (c0 + c >= a.ncols) continue;
-            C v = R[pad(out_src(kp, a.out_len, n)) * ncol + c];
-            if (ax) {
-                v = Ops<T>::mul(v, ax[c0 + c]);
-                v = Ops<T>::mul(v, ay[kp]);
-                if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
+        if (col < a.ncols) {
+            C axc = Ops<T>::mk(1, 0);
+            const C* ay = nullptr;
+            if (a.ax) {
+                axc = ((const C*)a.ax)[(long long)bi * a.ncols + col];
+                ay = (const C*)a.ay + (long long)bi * a.out_len;
             }
-            out[(long long)kp * a.ncols + c0 + c] = v;
+            for (int kp = r0; kp < a.out_len; kp += rstep) {
+                C v = R[pad(out_src(kp, a.out_len, n)) * NCOL + c];
+                if (ay) {
+                    v = Ops<T>::mul(Ops<T>::mul(v, axc), __ldg(&ay[kp]));
+                    if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
+                }
+                out[(long long)kp * a.ncols + col] = v;
+            }
         }
         __syncthreads();
     }
@@ -388,6 +400,12 @@ FftPlan make_fft_plan(int n, int max_radix) {
     while (m % 3 == 0) { fp.radix[fp.nstages++] = 3; m /= 3; }
     while (m % 5 == 0) { fp.radix[fp.nstages++] = 5; m /= 5; }
     if (m != 1) fp.nstages = -1;
+    long long p = 1;
+    for (int s = 0; s < fp.nstages; ++s) {
+        fp.p[s] = (int)p;
+        fp.pmagic[s] = p == 1 ? 0u : (unsigned)(((1ULL << 32) + (unsigned long long)p - 1) / p);
+        p *= fp.radix[s];
+    }
     return fp;
 }
 
@@ -422,12 +440,21 @@ void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st) {
     while (cmax > 1 && 2LL * padded_len(fp.n) * cmax * (long long)sizeof(cx_t<T>) > kFftSmemTarget)
         cmax >>= 1;
     const size_t smem = 2 * (size_t)padded_len(fp.n) * cmax * sizeof(cx_t<T>);
-    cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int threads = threads_for(fp.n * cmax, emax<T>());
     const long long ngroups = (long long)((a.ncols + cmax - 1) / cmax) * (a.batch > 1 ? a.batch : 1);
     int blocks = ngroups < 152 * 16 ? (int)ngroups : 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_fft_cols<T><<<blocks, threads, smem, st>>>(fp, a, cmax);
+#define FRES_COLS(NC)                                                                         \
+    case NC:                                                                                  \
+        cudaFuncSetAttribute(k_fft_cols<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             (int)smem);                                                      \
+        k_fft_cols<T, NC><<<blocks, threads, smem, st>>>(fp, a);                              \
+        break;
+    switch (cmax) {
+        FRES_COLS(1) FRES_COLS(2) FRES_COLS(4) FRES_COLS(8)
+        default: break;
+    }
+#undef FRES_COLS
 }
 
 template void launch_fft_rows<float>(const FftPlan&, const RowPassArgs&, cudaStream_t);

@@ -5,6 +5,7 @@
 // Paper: arXiv:2010.05978, Secs. 3.2-3.3 and 4.1 (eqs. split, aqnod, aqwei, vliq1).
 #include "dfloat.cuh"
 #include "internal.cuh"
+#include "petal.cuh"
 
 namespace fres {
 
@@ -158,30 +159,6 @@ __global__ void k_boundary_line(FamilyDev f, ChirpParams cp) {
 }
 
 // ------------------------------------------------------------------ starshade petals
-// Apodisation A(r) of a petal family at r in (a, R) (Sec. 4.2).
-__device__ double petal_profile(const FamilyDev& f, int l, double r) {
-    const double* d = f.params + 5;
-    if (f.profile == FRESNEL_PETAL_HG) return exp(-pow((r - f.pa) / d[0], d[1]));
-    if (f.profile == FRESNEL_PETAL_TABLE) return d[l];
-    // clamped uniform cubic B-spline, de Boor's recursion on the span of r
-    const int n = (int)f.n_prof;
-    const double step = (f.pR - f.pa) / (n - 3);
-    auto knot = [&](int i) {
-        return i <= 3 ? f.pa : (i >= n ? f.pR : f.pa + (i - 3) * step);
-    };
-    int mu = 3 + (int)floor((r - f.pa) / step);
-    mu = min(max(mu, 3), n - 1);
-    double c[4];
-    for (int j = 0; j < 4; ++j) c[j] = d[mu - 3 + j];
-    for (int k = 1; k <= 3; ++k)
-        for (int j = 3; j >= k; --j) {
-            const double lo = knot(mu - 3 + j), hi = knot(mu + 1 + j - k);
-            const double al = (r - lo) / (hi - lo);
-            c[j] = (1.0 - al) * c[j - 1] + al * c[j];
-        }
-    return c[3];
-}
-
 // Tables of the first petal (centred on angle 0) for index i*m + l:
 // r_l = a + (R-a) rho_l and what_l = (R-a) rhow_l from the m-point rule on
 // (0,1); t_i = -pi/Np + (2 pi/Np) tau_i, omegahat_i = (2 pi/Np) tauw_i from

@@ -64,7 +64,7 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_plan_many", "fresnel_eval",
-           "fresnel_eval_many", "fresnel_eval_host",
+           "fresnel_eval_many", "fresnel_eval_host", "fresnel_grad_profile",
            "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
            "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread",
            "fresnel_spread_noalloc"]
@@ -94,6 +94,8 @@ def load_library(path=LIB_PATH):
     lib.fresnel_eval.restype = ctypes.c_int
     lib.fresnel_eval_many.argtypes = [vp, vp]
     lib.fresnel_eval_many.restype = ctypes.c_int
+    lib.fresnel_grad_profile.argtypes = [vp, vp, vp]
+    lib.fresnel_grad_profile.restype = ctypes.c_int
     lib.fresnel_eval_host.argtypes = [vp, vp, ll, vp]
     lib.fresnel_eval_host.restype = ctypes.c_int
     lib.fresnel_check.argtypes = [vp]
@@ -194,8 +196,23 @@ def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nod
     return o
 
 
+def _profile_sizes(families):
+    """Profile data length of each PETALS family (the gradient layout)."""
+    return [len(family_params(f)[4]) - 5 for f in families if f["kind"] == "petals"]
+
+
 class _PlanHandle:
     """Methods shared by single and batched plans."""
+
+    def grad_profile(self, gamma):
+        """dL/d(profile data) of every PETALS family (FP64 CUDA tensor, families
+        concatenated in plan order) for dL = Re sum conj(gamma) du, gamma shaped
+        like the output (torch's gradient convention for complex tensors)."""
+        torch = self._torch
+        gamma = gamma.to(self.cdtype).contiguous()
+        out = torch.empty(max(1, sum(self.profile_sizes)), dtype=torch.float64, device="cuda")
+        _check(load_library().fresnel_grad_profile(self.handle, gamma.data_ptr(), out.data_ptr()))
+        return out[:sum(self.profile_sizes)]
 
     def check(self):
         _check(load_library().fresnel_check(self.handle))
@@ -250,6 +267,7 @@ class BatchPlan(_PlanHandle):
         lib = load_library()
         self._torch = torch
         probs = (Problem * len(problems))()
+        self.profile_sizes = [n for q in problems for n in _profile_sizes(q["families"])]
         self._keep = []
         for b, q in enumerate(problems):
             fams, keep = _family_array(q["families"])
@@ -296,6 +314,7 @@ class Plan(_PlanHandle):
         lib = load_library()
         self._torch = torch
         fams, keep = _family_array(families)
+        self.profile_sizes = _profile_sizes(families)
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning)
         if stream is None:
@@ -350,6 +369,36 @@ class Plan(_PlanHandle):
         _check(load_library().fresnel_eval_host(self.handle, tptr, M,
                                                 out.ctypes.data if M > 0 else None))
         return out
+
+
+def profile_field(theta, make_plan):
+    """The field of a starshade design as a differentiable function of its
+    petal profile data theta (a float64 torch tensor).
+
+    make_plan(theta_numpy) returns a Plan or BatchPlan (grid targets) whose
+    PETALS families all take their profile data (e.g. B-spline coefficients)
+    from theta.  Returns the output tensor; backward gives dL/dtheta through
+    fresnel_grad_profile (summed over the families sharing theta)."""
+    import torch
+
+    class _ProfileField(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            plan = make_plan(th.detach().cpu().numpy().astype(np.float64))
+            u = plan.eval()
+            ctx.plan = plan
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            plan = ctx.plan
+            g = plan.grad_profile(grad_u)
+            n = theta.numel()
+            assert all(k == n for k in plan.profile_sizes)
+            gt = g.view(len(plan.profile_sizes), n).sum(0)
+            return gt.to(theta.device, theta.dtype).view_as(theta)
+
+    return _ProfileField.apply(theta)
 
 
 # C-ABI names, for callers that want the flat interface.

@@ -352,26 +352,8 @@ def test_planted_petals_off_centre(monkeypatch):
 
 
 # ------------------------------------------------------------------ spline-profile gradient
-def _spline_case(kind="hg24", n=20):
-    """Spline-profile starshades: "hg24" is the 24-petal occulter at two
-    wavelengths on a pupil grid (the tangential node motion cancels there over
-    the petals: only angular harmonics of order 24 survive, and their Bessel
-    factors J_24(2 pi r rho / lz) are ~1e-11); "small" is a 5-petal shape seen
-    far off axis, where both weight and node-motion terms matter."""
-    if kind == "hg24":
-        a, R, Np, b, lams, z, ng, half = 6.0, 14.0, 24, 3.9, (500e-9, 900e-9), 3.7e7, 24, 1.2
-        res = (40, 20, 144, 40)
-    else:
-        a, R, Np, b, lams, z, ng, half = 0.4, 1.0, 5, 0.35, (0.03, 0.05), 1.0, 16, 1.5
-        res = (30, 24, 40, 30)
-    t = Q.bspline_knots(a, R, n)
-    grev = (t[1:n + 1] + t[2:n + 2] + t[3:n + 3]) / 3.0
-    theta = np.exp(-((grev - a) / b) ** 6) + 1e-3 * W.rng(4, 1).standard_normal(n)
-    probs = [{"family": W.petal_family(Np, a, R, {"kind": "bspline", "coefs": theta}, *res),
-              "lam": lam, "z": z} for lam in lams]
-    grid = W.grid_spec(ng, ng, 2 * half / ng, x0=0.013)
-    xi, eta = oracle.grid_targets(ng, ng, 2 * half / ng, 0.013)
-    return theta, probs, grid, xi * xi + eta * eta <= half ** 2
+def _spline_case(kind):
+    return W.spline_starshade("hg24_small" if kind == "hg24" else kind)
 
 
 def test_spline_loss_gradient_matches_central_differences():

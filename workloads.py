@@ -155,6 +155,53 @@ def starshade_sweep(n_lambda=64, lam_lo=400e-9, lam_hi=1000e-9, n=512, pupil=2.4
             "grid": grid_spec(n, n, h), "pupil_radius": 0.5 * pupil}
 
 
+def spline_starshade(kind="c4", n_coef=None, lams=None, ngrid=None):
+    """A starshade whose petal profile is a clamped uniform cubic B-spline.
+
+    Coefficients: the design profile sampled at the spline's Greville
+    abscissae (knot averages) plus seeded N(0, 1e-3^2) perturbations.
+    kind "c4": the 24-petal HG occulter of ``starshade_sweep`` with 200
+    coefficients, 8 wavelengths in [400, 1000] nm, the 256 x 256 pupil grid
+    (h = 2.4/256), targets kept for rho <= 1.2 (51,431 points), per-wavelength
+    resolution as in ``starshade_sweep``.  kind "hg24_small": the same
+    occulter with 20 coefficients at 2 wavelengths on a 24 x 24 grid.  kind
+    "small": a 5-petal shape seen far off axis (both the weight and the
+    node-motion parts of the gradient matter there).
+    Returns (theta, problems, grid, keep): problems = [{"family", "lam", "z"}]
+    (family profile data = theta), keep = boolean mask over the grid targets
+    (k1 fastest).
+    """
+    if kind == "small":
+        a, R, Np, b, z, half = 0.4, 1.0, 5, 0.35, 1.0, 1.5
+        n_coef, lams, ngrid = n_coef or 20, lams or (0.03, 0.05), ngrid or 16
+        res = lambda lam: (30, 24, 40, 30)
+        x0 = 0.013
+    else:
+        s = HG24
+        a, R, Np, b, z, half = s["a"], s["R"], s["n_petals"], s["b"], s["z"], 1.2
+        if kind == "c4":
+            n_coef, ngrid = n_coef or 200, ngrid or 256
+            lams = lams or tuple(np.linspace(400e-9, 1000e-9, 8))
+            res = lambda lam: starshade_resolution(R * R / (lam * z), Np)
+            x0 = 0.0
+        else:
+            n_coef, lams, ngrid = n_coef or 20, lams or (500e-9, 900e-9), ngrid or 24
+            res = lambda lam: (40, 20, 144, 40)
+            x0 = 0.013
+    n = n_coef
+    inner = np.linspace(a, R, n - 2)[1:-1]
+    t = np.concatenate([[a] * 4, inner, [R] * 4])
+    grev = (t[1:n + 1] + t[2:n + 2] + t[3:n + 3]) / 3.0
+    theta = np.exp(-((grev - a) / b) ** 6) + 1e-3 * rng(4, 1).standard_normal(n)
+    problems = [{"family": petal_family(Np, a, R, {"kind": "bspline", "coefs": theta}, *res(lam)),
+                 "lam": float(lam), "z": z} for lam in lams]
+    h = 2 * half / ngrid
+    k = np.arange(-(ngrid // 2), ngrid - ngrid // 2)
+    XI, ETA = np.meshgrid(x0 + h * k, h * k, indexing="xy")
+    keep = (XI * XI + ETA * ETA <= half * half).ravel()
+    return theta, problems, grid_spec(ngrid, ngrid, h, x0=x0), keep
+
+
 def random_star(n_panels=640, p=16, m=1024, fresnel_number=1000.0, config_id=5):
     params = random_star_params(config_id)
     R = max_radius(params)
