@@ -13,8 +13,11 @@
 //
 // Each Stockham stage with radix r and p = product of earlier radices maps
 // butterfly i (k = i mod p) from inputs x[i + q n/r] (twiddled by
-// w_n^{q k n/(p r)}) to outputs y[(i - k) r + k + t p]; stages run in place
-// with the outputs staged in registers between two barriers.
+// w_n^{q k n/(p r)}) to outputs y[(i - k) r + k + t p]; stages ping-pong
+// between two shared-memory buffers with one barrier each.  The first stage
+// reads its inputs straight from global memory and the last writes its
+// outputs straight to global memory (through the pruning and the epilogue),
+// so a transform makes no separate staging passes.
 #include "internal.cuh"
 
 namespace fres {
@@ -24,7 +27,6 @@ namespace {
 constexpr int kFftThreads = 256;
 constexpr int kFftBlocksPerSm = 3;
 constexpr long long kFftSmemTarget = 76 * 1024;   // three blocks per SM
-constexpr int kPrefetch = 8;                       // next-row inputs held per thread
 
 template <typename T> struct Ops {
     using C = cx_t<T>;
@@ -159,14 +161,17 @@ template <typename T> struct Dft<T, 16> {
 __host__ __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 __host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4) + 1; }
 
-// One Stockham stage of radix R from smem array src[n][NCOL] to dst[n][NCOL]
-// (column c of element e at [pad(e) * NCOL + c]); out of place, so each
-// thread holds one butterfly at a time and one barrier ends the stage.
-// NCOL is a power of two; k = i mod p comes from the plan's magic multiplier.
-template <typename T, int R, int NCOL>
-__device__ __forceinline__ void stage(const cx_t<T>* __restrict__ src, cx_t<T>* __restrict__ dst,
-                                      int n, int p, unsigned pmagic,
-                                      const cx_t<T>* __restrict__ tw) {
+template <typename T> __host__ __device__ constexpr int emax() { return 8; }
+
+// A stage whose inputs come from global memory (FIRST: load(e) for natural
+// input index e, always p = 1) and/or whose outputs go straight to global
+// memory (LAST: store(k, value) for natural output index k); otherwise as
+// stage().  Fusing the first and last stages with the loads and stores saves
+// two shared-memory round trips and two barriers per transform.
+template <typename T, int R, int NCOL, bool FIRST, bool LAST, class Load, class Store>
+__device__ __forceinline__ void stage_io(const cx_t<T>* __restrict__ src, cx_t<T>* __restrict__ dst,
+                                         int n, int p, unsigned pmagic,
+                                         const cx_t<T>* __restrict__ tw, Load& load, Store& store) {
     using O = Ops<T>;
     using C = cx_t<T>;
     const int nb = n / R;
@@ -174,62 +179,86 @@ __device__ __forceinline__ void stage(const cx_t<T>* __restrict__ src, cx_t<T>* 
     const int twstep = n / (p * R);
     for (int w = threadIdx.x; w < items; w += blockDim.x) {
         const int c = w & (NCOL - 1), i = w / NCOL;
-        const int k = p == 1 ? 0 : i - (int)__umulhi((unsigned)i, pmagic) * p;
+        const int k = (FIRST || p == 1) ? 0 : i - (int)__umulhi((unsigned)i, pmagic) * p;
         const int kt = k * twstep;
         C u[R], y[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            u[q] = src[pad(i + q * nb) * NCOL + c];
-            if (q > 0 && k > 0) u[q] = O::mul(u[q], __ldg(&tw[q * kt]));
+            if constexpr (FIRST) {
+                u[q] = load(i + q * nb);
+            } else {
+                u[q] = src[pad(i + q * nb) * NCOL + c];
+                if (q > 0 && k > 0) u[q] = O::mul(u[q], __ldg(&tw[q * kt]));
+            }
         }
         Dft<T, R>::run(u, y);
         const int j = (i - k) * R + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) dst[pad(j + t * p) * NCOL + c] = y[t];
+        for (int t = 0; t < R; ++t) {
+            if constexpr (LAST) store(j + t * p, y[t]);
+            else dst[pad(j + t * p) * NCOL + c] = y[t];
+        }
     }
     __syncthreads();
 }
 
-// Runs the plan's stages ping-ponging between A and B; returns the buffer
-// holding the result (natural order).
-template <typename T, int NCOL>
-__device__ cx_t<T>* fft_smem(cx_t<T>* A, cx_t<T>* B, const FftPlan& fp, const cx_t<T>* tw) {
-    for (int s = 0; s < fp.nstages; ++s) {
-        const int r = fp.radix[s], p = fp.p[s];
-        const unsigned mg = fp.pmagic[s];
-        switch (r) {
-            case 16:
-                if constexpr (sizeof(T) == 4) stage<T, 16, NCOL>(A, B, fp.n, p, mg, tw);
-                break;
-            case 8: stage<T, 8, NCOL>(A, B, fp.n, p, mg, tw); break;
-            case 4: stage<T, 4, NCOL>(A, B, fp.n, p, mg, tw); break;
-            case 2: stage<T, 2, NCOL>(A, B, fp.n, p, mg, tw); break;
-            case 3: stage<T, 3, NCOL>(A, B, fp.n, p, mg, tw); break;
-            case 5: stage<T, 5, NCOL>(A, B, fp.n, p, mg, tw); break;
-        }
+template <typename T, int NCOL, bool FIRST, bool LAST, class Load, class Store>
+__device__ __forceinline__ void stage_dispatch(int r, const cx_t<T>* src, cx_t<T>* dst, int n, int p,
+                                               unsigned mg, const cx_t<T>* tw, Load& load,
+                                               Store& store) {
+    switch (r) {
+        case 16:
+            if constexpr (sizeof(T) == 4)
+                stage_io<T, 16, NCOL, FIRST, LAST>(src, dst, n, p, mg, tw, load, store);
+            break;
+        case 8: stage_io<T, 8, NCOL, FIRST, LAST>(src, dst, n, p, mg, tw, load, store); break;
+        case 4: stage_io<T, 4, NCOL, FIRST, LAST>(src, dst, n, p, mg, tw, load, store); break;
+        case 2: stage_io<T, 2, NCOL, FIRST, LAST>(src, dst, n, p, mg, tw, load, store); break;
+        case 3: stage_io<T, 3, NCOL, FIRST, LAST>(src, dst, n, p, mg, tw, load, store); break;
+        case 5: stage_io<T, 5, NCOL, FIRST, LAST>(src, dst, n, p, mg, tw, load, store); break;
+    }
+}
+
+// The whole transform with the first stage reading load(e) and the last
+// writing store(k, v) (natural indices); A and B are the shared ping-pong
+// buffers.  Every thread of the block must call it (it holds barriers).
+template <typename T, int NCOL, class Load, class Store>
+__device__ void fft_fused(cx_t<T>* A, cx_t<T>* B, const FftPlan& fp, const cx_t<T>* tw, Load& load,
+                          Store& store) {
+    const int S = fp.nstages;
+    if (S == 1) {
+        stage_dispatch<T, NCOL, true, true>(fp.radix[0], A, B, fp.n, 1, 0u, tw, load, store);
+        return;
+    }
+    stage_dispatch<T, NCOL, true, false>(fp.radix[0], A, A, fp.n, 1, 0u, tw, load, store);
+    for (int s = 1; s < S - 1; ++s) {
+        stage_dispatch<T, NCOL, false, false>(fp.radix[s], A, B, fp.n, fp.p[s], fp.pmagic[s], tw,
+                                              load, store);
         cx_t<T>* t = A;
         A = B;
         B = t;
     }
-    return A;
+    stage_dispatch<T, NCOL, false, true>(fp.radix[S - 1], A, B, fp.n, fp.p[S - 1],
+                                         fp.pmagic[S - 1], tw, load, store);
 }
 
-template <typename T> __host__ __device__ constexpr int emax() { return 8; }
+// Natural input index e of a length-n transform whose len inputs hold modes
+// i - len/2 (centred) or index i itself: the input index, or -1 (zero).
+__device__ __forceinline__ int in_src(int e, int len, int n, int centered) {
+    if (!centered) return e < len ? e : -1;
+    const int hi = len - len / 2;
+    if (e < hi) return e + len / 2;
+    if (e >= n - len / 2) return e - n + len / 2;
+    return -1;
+}
+// Kept output slot of natural output index k (centred order over len), or -1.
+__device__ __forceinline__ int out_slot(int k, int len, int n) {
+    if (k < len - len / 2) return k + len / 2;
+    if (k >= n - len / 2) return k - n + len / 2;
+    return -1;
+}
 
-// Position in the length-n transform of input index i when the input holds
-// modes i - len/2 (type-3 central block), else i itself.
-__device__ __forceinline__ int in_pos(int i, int len, int n, int centered) {
-    if (!centered) return i;
-    int l = i - len / 2;
-    return l < 0 ? l + n : l;
-}
-// Source index in the length-n transform of kept output kp: outputs are in
-// centred order, kp <-> mode kp - len/2 (for len == n this is the fftshifted
-// full transform).
-__device__ __forceinline__ int out_src(int kp, int len, int n) {
-    int k = kp - len / 2;
-    return k < 0 ? k + n : k;
-}
+
 
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm)
@@ -240,18 +269,7 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
     C* S2 = S + padded_len(fp.n);
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
-    // The first kPrefetch * blockDim.x inputs of the block's next row are
-    // loaded into registers while the current row is transformed.
-    C buf[kPrefetch];
-    const int npf = min(a.in_len, kPrefetch * (int)blockDim.x);
-    auto prefetch = [&](int row) {
-        const C* in = (const C*)a.in + (long long)row * a.in_stride;
-#pragma unroll
-        for (int k = 0; k < kPrefetch; ++k) {
-            const int i = threadIdx.x + k * blockDim.x;
-            if (i < npf) buf[k] = in[i];
-        }
-    };
+    const T* dcol = (const T*)a.deconv_col;
     // rows of dead tile rows are zero in and out of the transform: skipped
     auto next_live = [&](int r) {
         if (a.live)
@@ -259,38 +277,22 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
                 r += gridDim.x;
         return r;
     };
-    int row = next_live(blockIdx.x);
-    if (row < a.nrows) prefetch(row);
-    while (row < a.nrows) {
+    for (int row = next_live(blockIdx.x); row < a.nrows; row = next_live(row + gridDim.x)) {
         const C* in = (const C*)a.in + (long long)row * a.in_stride;
-        if (a.centered_in || a.in_len < n)
-            for (int e = threadIdx.x; e < padded_len(n); e += blockDim.x) S[e] = Ops<T>::mk(0, 0);
-        __syncthreads();
-        T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
-        const T* dcol = (const T*)a.deconv_col;
-#pragma unroll
-        for (int k = 0; k < kPrefetch; ++k) {
-            const int i = threadIdx.x + k * blockDim.x;
-            if (i < npf) {
-                C v = buf[k];
-                if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
-                S[pad(in_pos(i, a.in_len, n, a.centered_in))] = v;
-            }
-        }
-        for (int i = npf + threadIdx.x; i < a.in_len; i += blockDim.x) {
+        C* out = (C*)a.out + (long long)row * a.out_stride;
+        const T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
+        auto load = [&](int e) {
+            const int i = in_src(e, a.in_len, n, a.centered_in);
+            if (i < 0) return Ops<T>::mk(0, 0);
             C v = in[i];
             if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
-            S[pad(in_pos(i, a.in_len, n, a.centered_in))] = v;
-        }
-        __syncthreads();
-        const int nxt = next_live(row + gridDim.x);
-        if (nxt < a.nrows) prefetch(nxt);
-        const C* R = fft_smem<T, 1>(S, S2, fp, tw);
-        C* out = (C*)a.out + (long long)row * a.out_stride;
-        for (int kp = threadIdx.x; kp < a.out_len; kp += blockDim.x)
-            out[kp] = R[pad(out_src(kp, a.out_len, n))];
-        __syncthreads();
-        row = nxt;
+            return v;
+        };
+        auto store = [&](int k, C v) {
+            const int kp = out_slot(k, a.out_len, n);
+            if (kp >= 0) out[kp] = v;
+        };
+        fft_fused<T, 1>(S, S2, fp, tw, load, store);
     }
 }
 
@@ -307,73 +309,43 @@ k_fft_cols(FftPlan fp, ColPassArgs a) {
     const int ngroups = (a.ncols + NCOL - 1) / NCOL;
     const int total = ngroups * max(a.batch, 1);   // (transform, column group) work items
     const int c = threadIdx.x & (NCOL - 1);        // this thread's column in every group
-    const int r0 = threadIdx.x / NCOL, rstep = blockDim.x / NCOL;
-    // Inputs of the block's next work item are prefetched into registers
-    // (first kPrefetch * blockDim.x of them) while the current one runs.
-    C buf[kPrefetch];
-    const int npf_rows = min(a.in_len, kPrefetch * rstep);
-    // live-row bit of input row i of transform bi (all live without a map)
-    auto live_bit = [&](int bi, int i) {
-        return !a.live || a.live[(long long)bi * a.nty + i / kTile] != 0;
-    };
-    auto prefetch = [&](int gg) {
-        const int bi = gg / ngroups, col = (gg - bi * ngroups) * NCOL + c;
-        const C* in = (const C*)a.in + (long long)bi * a.in_bstride + col;
-#pragma unroll
-        for (int k = 0; k < kPrefetch; ++k) {
-            const int i = r0 + k * rstep;
-            buf[k] = (i < npf_rows && col < a.ncols && live_bit(bi, i))
-                         ? in[(long long)i * a.ncols] : Ops<T>::mk(0, 0);
-        }
-    };
-    if (blockIdx.x < total) prefetch(blockIdx.x);
     for (int gg = blockIdx.x; gg < total; gg += gridDim.x) {
-        const int bi = gg / ngroups, c0 = (gg - bi * ngroups) * NCOL;
-        const int col = c0 + c;
+        const int bi = gg / ngroups, col = (gg - bi * ngroups) * NCOL + c;
+        const bool on = col < a.ncols;
         const C* in = (const C*)a.in + (long long)bi * a.in_bstride + col;
-        if (a.live) {
+        C* out = (C*)a.out + (long long)bi * a.out_bstride + col;
+        if (a.live) {   // live tile rows of this transform as a bit mask
             for (int t = threadIdx.x; t < kMaxTileRows / 32; t += blockDim.x) s_live[t] = 0u;
             __syncthreads();
             for (int t = threadIdx.x; t < a.nty; t += blockDim.x)
                 if (a.live[(long long)bi * a.nty + t]) atomicOr(&s_live[t >> 5], 1u << (t & 31));
+            __syncthreads();
         }
-        if (a.centered_in || a.in_len < n)
-            for (int e = threadIdx.x; e < padded_len(n) * NCOL; e += blockDim.x)
-                S[e] = Ops<T>::mk(0, 0);
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kPrefetch; ++k) {
-            const int i = r0 + k * rstep;
-            if (i < npf_rows) S[pad(in_pos(i, a.in_len, n, a.centered_in)) * NCOL + c] = buf[k];
+        C axc = Ops<T>::mk(1, 0);
+        const C* ay = nullptr;
+        if (a.ax && on) {
+            axc = ((const C*)a.ax)[(long long)bi * a.ncols + col];
+            ay = (const C*)a.ay + (long long)bi * a.out_len;
         }
-        for (int i = npf_rows + r0; i < a.in_len; i += rstep) {
-            C v = Ops<T>::mk(0, 0);
-            const int tr = i / kTile;
-            if (col < a.ncols && (!a.live || ((s_live[tr >> 5] >> (tr & 31)) & 1u)))
-                v = in[(long long)i * a.ncols];
-            S[pad(in_pos(i, a.in_len, n, a.centered_in)) * NCOL + c] = v;
-        }
-        __syncthreads();
-        if (gg + (int)gridDim.x < total) prefetch(gg + gridDim.x);
-        const C* R = fft_smem<T, NCOL>(S, S2, fp, tw);
-        C* out = (C*)a.out + (long long)bi * a.out_bstride;
-        if (col < a.ncols) {
-            C axc = Ops<T>::mk(1, 0);
-            const C* ay = nullptr;
-            if (a.ax) {
-                axc = ((const C*)a.ax)[(long long)bi * a.ncols + col];
-                ay = (const C*)a.ay + (long long)bi * a.out_len;
+        auto load = [&](int e) {
+            const int i = in_src(e, a.in_len, n, a.centered_in);
+            if (i < 0 || !on) return Ops<T>::mk(0, 0);
+            if (a.live) {
+                const int tr = i / kTile;
+                if (!((s_live[tr >> 5] >> (tr & 31)) & 1u)) return Ops<T>::mk(0, 0);
             }
-            for (int kp = r0; kp < a.out_len; kp += rstep) {
-                C v = R[pad(out_src(kp, a.out_len, n)) * NCOL + c];
-                if (ay) {
-                    v = Ops<T>::mul(Ops<T>::mul(v, axc), __ldg(&ay[kp]));
-                    if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
-                }
-                out[(long long)kp * a.ncols + col] = v;
+            return in[(long long)i * a.ncols];
+        };
+        auto store = [&](int k, C v) {
+            const int kp = out_slot(k, a.out_len, n);
+            if (kp < 0 || !on) return;
+            if (ay) {
+                v = Ops<T>::mul(Ops<T>::mul(v, axc), __ldg(&ay[kp]));
+                if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
             }
-        }
-        __syncthreads();
+            out[(long long)kp * a.ncols] = v;
+        };
+        fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
     }
 }
 
