@@ -143,6 +143,12 @@ typedef struct {
      * straight from global memory (-1), or choose (0: bucket when the FFT grid
      * exceeds 64 MB, i.e. would not stay in L2, and M >= 32768). */
     int t3_binning;
+    /* FFT lengths above this run as four-step transforms fa x fb (two launches
+     * per pass through an intermediate buffer) instead of one shared-memory
+     * pass; 0 = only when one pass does not fit in shared memory (lengths
+     * above ~13,600 in FP32, ~6,800 in FP64).  Batched plans and profile
+     * gradients need single-pass lengths. */
+    int fft_split_above;
 } fresnel_opts;
 
 /* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,

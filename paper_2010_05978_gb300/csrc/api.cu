@@ -49,6 +49,18 @@ constexpr int kMaxEvents = 16;
 constexpr long long kSortTargetsFrom = 32768;
 constexpr long long kBinFromGridBytes = 64LL << 20;
 
+// FFT along one dimension: one shared-memory pass, or four steps fa x fb
+// (A-point transforms, twiddle, B-point transforms) for longer lengths.
+struct FftDim {
+    int n = 0;
+    bool big = false;
+    int fa = 0, fb = 0;
+    FftPlan fp{}, fpa{}, fpb{};
+    void* tw = nullptr;            // w_n table (for a four-step length, the w_N twiddles)
+    void* twa = nullptr;
+    void* twb = nullptr;
+};
+
 struct Plan {
     uint64_t magic = kMagic;
     int prec = FRESNEL_FP32_FAST, output = 0, tkind = 0;
@@ -74,6 +86,8 @@ struct Plan {
     ChirpParams cp{};
     InterpParams ip{};
     FftPlan fp1{}, fp2{};
+    FftDim d1{}, d2{};            // FFT along x (rows) and y (columns)
+    void* fscratch = nullptr;     // four-step intermediate
     std::vector<void*> allocs;
     long long bytes = 0;
     void* rec = nullptr;
@@ -100,6 +114,7 @@ struct Plan {
     int* tstart = nullptr;
     int* tcursor = nullptr;
     int* twork = nullptr;         // binned interpolation's dynamic bin counter
+    int* tpartial = nullptr;      // chunk sums of the multi-block bin scan
     int* perm = nullptr;          // type-3 target permutation, grown on demand
     long long perm_cap = 0;
     double* cheb = nullptr;
@@ -366,6 +381,94 @@ fresnel_status run_sort(Plan* p) {
     return FRESNEL_OK;
 }
 
+// Row pass (transforms along x) through one pass or the four-step path.
+template <typename T>
+void run_rows(Plan* p, RowPassArgs ra) {
+    const FftDim& d = p->d1;
+    if (!d.big) {
+        ra.twiddle = d.tw;
+        launch_fft_rows<T>(d.fp, ra, p->st);
+        p->launches++;
+        return;
+    }
+    ColPassArgs c1{};
+    c1.mode = kFftRowStep1;
+    c1.in = ra.in;
+    c1.in_stride = ra.in_stride;
+    c1.in_len = ra.in_len;
+    c1.centered_in = ra.centered_in;
+    c1.deconv_col = ra.deconv_col;
+    c1.deconv_row = ra.deconv_row;
+    c1.out = p->fscratch;
+    c1.ncols = d.fb;
+    c1.nouter = ra.nrows;
+    c1.fa = d.fa;
+    c1.fb = d.fb;
+    c1.fN = d.n;
+    c1.out_len = d.fa;
+    c1.twiddle = d.twa;
+    launch_fft_cols<T>(d.fpa, c1, p->st);
+    RowPassArgs r2{};
+    r2.mode = kFftStep2;
+    r2.in = p->fscratch;
+    r2.in_stride = d.fb;
+    r2.nrows = ra.nrows * d.fa;
+    r2.in_len = d.fb;
+    r2.out = ra.out;
+    r2.out_stride = ra.out_stride;
+    r2.out_len = ra.out_len;
+    r2.fa = d.fa;
+    r2.fb = d.fb;
+    r2.fN = d.n;
+    r2.twN = d.tw;
+    r2.twiddle = d.twb;
+    launch_fft_rows<T>(d.fpb, r2, p->st);
+    p->launches += 2;
+}
+
+// Column pass (transforms along y), likewise.
+template <typename T>
+void run_cols(Plan* p, ColPassArgs ca) {
+    const FftDim& d = p->d2;
+    if (!d.big) {
+        ca.twiddle = d.tw;
+        launch_fft_cols<T>(d.fp, ca, p->st);
+        p->launches++;
+        return;
+    }
+    ColPassArgs c1{};
+    c1.mode = kFftColStep1;
+    c1.in = ca.in;
+    c1.ncols = ca.ncols;
+    c1.in_len = ca.in_len;
+    c1.centered_in = ca.centered_in;
+    c1.out = p->fscratch;
+    c1.nouter = d.fb;
+    c1.fa = d.fa;
+    c1.fb = d.fb;
+    c1.fN = d.n;
+    c1.out_len = d.fa;
+    c1.twiddle = d.twa;
+    launch_fft_cols<T>(d.fpa, c1, p->st);
+    ColPassArgs c2{};
+    c2.mode = kFftColStep2;
+    c2.in = p->fscratch;
+    c2.ncols = ca.ncols;
+    c2.out = ca.out;
+    c2.nouter = d.fa;
+    c2.fa = d.fa;
+    c2.fb = d.fb;
+    c2.fN = d.n;
+    c2.out_len = ca.out_len;
+    c2.twN = d.tw;
+    c2.twiddle = d.twb;
+    c2.ax = ca.ax;
+    c2.ay = ca.ay;
+    c2.occulter = ca.occulter;
+    launch_fft_cols<T>(d.fpb, c2, p->st);
+    p->launches += 2;
+}
+
 template <typename T>
 fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_out) {
     p->launches = 0;
@@ -393,11 +496,10 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ra.in_len = p->nf1;
         ra.centered_in = 0;
         ra.out_len = p->n1;
-        ra.twiddle = p->tw1;
         ra.live = p->layout.live;
         ra.batch_rows = p->nf2;
         ra.nty = p->nty;
-        launch_fft_rows<T>(p->fp1, ra, p->st);
+        run_rows<T>(p, ra);
         ev_record(p, "fft_rows");
         ColPassArgs ca{};
         ca.in = p->inter;
@@ -416,9 +518,8 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ca.out_bstride = (long long)p->n2 * p->n1;
         ca.live = p->layout.live;
         ca.nty = p->nty;
-        launch_fft_cols<T>(p->fp2, ca, p->st);
+        run_cols<T>(p, ca);
         ev_record(p, "fft_cols_epilogue");
-        p->launches += 2;
     } else {
         RowPassArgs ra{};
         ra.in = p->grid;
@@ -431,8 +532,7 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ra.deconv_col = p->dec1;
         ra.deconv_row = p->dec2;
         ra.out_len = p->nfft1;
-        ra.twiddle = p->tw1;
-        launch_fft_rows<T>(p->fp1, ra, p->st);
+        run_rows<T>(p, ra);
         ev_record(p, "fft_rows");
         ColPassArgs ca{};
         ca.in = p->inter;
@@ -441,10 +541,8 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ca.in_len = p->nf2;
         ca.centered_in = 1;
         ca.out_len = p->nfft2;
-        ca.twiddle = p->tw2;
-        launch_fft_cols<T>(p->fp2, ca, p->st);
+        run_cols<T>(p, ca);
         ev_record(p, "fft_cols");
-        p->launches += 2;
         if (M > 0) {
             T3Sort sort{};
             const T3Sort* sp = nullptr;
@@ -460,9 +558,9 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
                     FRES_CK(cudaMalloc((void**)&p->perm, sizeof(int) * (size_t)M));
                     p->perm_cap = M;
                 }
-                sort = T3Sort{p->tcounts, p->tstart, p->tcursor, p->perm, p->twork};
+                sort = T3Sort{p->tcounts, p->tstart, p->tcursor, p->perm, p->twork, p->tpartial};
                 sp = &sort;
-                p->launches += 3;
+                p->launches += p->ip.nbin1 * p->ip.nbin2 <= kBinScanStaged ? 3 : 5;
             }
             launch_interp_w<T>(d_targets, M, (const cx_t<T>*)p->F, p->ip, p->ks, p->cheb,
                                p->ncheb, d_out, p->status, sp, p->st);
@@ -749,12 +847,25 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         ip.shK2 = (float)(ip.sh2 / ip.K2);
         ip.occulter = p->output == FRESNEL_OCCULTER;
     }
-    if (!fft_supported(p->nfft1, dbl, &cmax) || !fft_supported(p->nfft2, dbl, &cmax))
-        return fres_fail(FRESNEL_ERR_UNSUPPORTED,
-                         "FFT size " + std::to_string(p->nfft1) + " x " + std::to_string(p->nfft2) +
-                             " exceeds this build's single-pass limit (8192 FP32, 4096 FP64)");
-    p->fp1 = make_fft_plan(p->nfft1, dbl ? 8 : 16);
-    p->fp2 = make_fft_plan(p->nfft2, dbl ? 8 : 16);
+    // FFT lengths: one shared-memory pass, or the four-step split
+    for (FftDim* d : {&p->d1, &p->d2}) {
+        d->n = d == &p->d1 ? p->nfft1 : p->nfft2;
+        const bool forced = p->opts.fft_split_above > 0 && d->n > p->opts.fft_split_above;
+        if (fft_supported(d->n, dbl, &cmax) && !forced) {
+            d->fp = make_fft_plan(d->n, dbl ? 8 : 16);
+        } else if (fft_split(d->n, dbl, &d->fa, &d->fb)) {
+            d->big = true;
+            d->fpa = make_fft_plan(d->fa, dbl ? 8 : 16);
+            d->fpb = make_fft_plan(d->fb, dbl ? 8 : 16);
+        } else {
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "FFT length " + std::to_string(d->n) +
+                                                          " has no supported split");
+        }
+    }
+    if ((p->d1.big || p->d2.big) && p->B > 1)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "batched plans need single-pass FFT lengths");
+    p->fp1 = p->d1.fp;
+    p->fp2 = p->d2.fp;
     p->cp.nf1 = p->nf1;
     p->cp.nf2 = p->nf2;
     p->ntx = p->nf1 / kTile;
@@ -884,8 +995,10 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     std::vector<int> sc_off(p->B + 1, 0), pl_off(p->B + 1, 0), st_off(p->B + 1, 0);
     std::vector<long long> rec_off(p->B + 1, 0);
     // type 1: tile rows without records are neither spread nor transformed
-    const bool prune = p->tkind == FRESNEL_GRID;
-    if (p->nty > kMaxTileRows) return fres_fail(FRESNEL_ERR_UNSUPPORTED, "spreading grid too tall");
+    // (the four-step FFT path reads every row, so it keeps them all)
+    const bool prune = p->tkind == FRESNEL_GRID && !p->d1.big && !p->d2.big;
+    if (prune && p->nty > kMaxTileRows)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "spreading grid too tall");
     for (int b = 0; b < p->B; ++b) {
         long long nrec = 0, nsc = 0, nsplit = 0, nlive = 0;
         std::vector<char> live(p->nty, prune ? 0 : 1);
@@ -957,13 +1070,23 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     FRES_TRY(dalloc(p, (void**)&p->gq_t, sizeof(double) * p->gq_n));
     FRES_TRY(dalloc(p, (void**)&p->gq_w, sizeof(double) * p->gq_n));
     launch_gauss_legendre(p->gq_n, p->gq_t, p->gq_w, p->st);
-    FRES_TRY(dalloc(p, &p->tw1, cs * p->nfft1));
-    launch_twiddles(p->nfft1, p->tw1, dbl, p->st);
-    if (p->nfft2 != p->nfft1) {
-        FRES_TRY(dalloc(p, &p->tw2, cs * p->nfft2));
-        launch_twiddles(p->nfft2, p->tw2, dbl, p->st);
-    } else {
-        p->tw2 = p->tw1;
+    for (FftDim* d : {&p->d1, &p->d2}) {
+        FRES_TRY(dalloc(p, &d->tw, cs * d->n));
+        launch_twiddles(d->n, d->tw, dbl, p->st);
+        if (d->big) {
+            FRES_TRY(dalloc(p, &d->twa, cs * d->fa));
+            launch_twiddles(d->fa, d->twa, dbl, p->st);
+            FRES_TRY(dalloc(p, &d->twb, cs * d->fb));
+            launch_twiddles(d->fb, d->twb, dbl, p->st);
+        }
+    }
+    p->tw1 = p->d1.tw;
+    p->tw2 = p->d2.tw;
+    if (p->d1.big || p->d2.big) {   // four-step intermediate, shared by both passes
+        const size_t rows = p->d1.big ? (size_t)p->nf2 * p->d1.n : 0;
+        const size_t ncol = p->tkind == FRESNEL_GRID ? (size_t)p->n1 : (size_t)p->nfft1;
+        const size_t cols = p->d2.big ? (size_t)p->d2.n * ncol : 0;
+        FRES_TRY(dalloc(p, &p->fscratch, cs * std::max(rows, cols)));
     }
     if (p->tkind == FRESNEL_GRID) {
         FRES_TRY(dalloc(p, &p->inter, cs * (size_t)p->nf2 * p->n1 * p->B));
@@ -1008,8 +1131,8 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         p->cheb = d_s;
         p->ncheb = nk;
         const int nbins = p->ip.nbin1 * p->ip.nbin2;
-        if ((size_t)nbins * sizeof(int) > 160 * 1024)   // bin scan is staged in shared memory
-            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "type-3 FFT grid too large for the bin scan");
+        FRES_TRY(dalloc(p, (void**)&p->tpartial,
+                        sizeof(int) * (size_t)((nbins + kBinChunk - 1) / kBinChunk)));
         FRES_TRY(dalloc(p, (void**)&p->tcounts, sizeof(int) * nbins));
         FRES_TRY(dalloc(p, (void**)&p->tstart, sizeof(int) * nbins));
         FRES_TRY(dalloc(p, (void**)&p->tcursor, sizeof(int) * nbins));
@@ -1159,6 +1282,8 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
         return fres_fail(FRESNEL_ERR_ARG, "kernel_w must be 0 (auto) or in [2, 16]");
     if (opts->t3_binning < -1 || opts->t3_binning > 1)
         return fres_fail(FRESNEL_ERR_ARG, "t3_binning must be -1, 0 or 1");
+    if (opts->fft_split_above < 0)
+        return fres_fail(FRESNEL_ERR_ARG, "fft_split_above must be >= 0");
     int dev = 0;
     FRES_CK(cudaGetDevice(&dev));
     Plan* p = new Plan();
@@ -1258,6 +1383,8 @@ fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, do
     bool any = false;
     for (const FamilyDev& f : p->fams) any = any || f.kind == FRESNEL_FAMILY_PETALS;
     if (!any) return fres_fail(FRESNEL_ERR_ARG, "the plan has no PETALS family");
+    if (p->d1.big || p->d2.big)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients need single-pass FFT lengths");
     if (!d_gamma || !d_grad) return fres_fail(FRESNEL_ERR_ARG, "d_gamma or d_grad is NULL");
     fresnel_status s = p->prec == FRESNEL_FP64 ? grad_profile_impl<double>(p, d_gamma, d_grad)
                                                : grad_profile_impl<float>(p, d_gamma, d_grad);

@@ -272,6 +272,11 @@ struct RowPassArgs {
     // are skipped: neither read nor written.  NULL: every row is live.
     const int* live;
     int batch_rows, nty;
+    // four-step second half (mode kFftStep2, see ColPassArgs): row r = (l, k1),
+    // l = r / fa, of a scratch holding B-point inputs; twN = w_N table
+    int mode;
+    int fa, fb, fN;
+    const void* twN;
 };
 struct ColPassArgs {
     const void* in; void* out;
@@ -291,12 +296,30 @@ struct ColPassArgs {
     // input row i of transform b is zero (not read) when live[b * nty + i / 32] == 0
     const int* live;
     int nty;
+    // Four-step transforms of length fN = fa * fb beyond one shared-memory pass
+    // (natural input index e = fb * a + b, output k = k1 + fa * k2):
+    //  kFftRowStep1: A-point DFTs over a of every grid row o (nouter rows,
+    //    in_stride apart; centred input with deconv as RowPassArgs), columns
+    //    b < fb; output scratch[o * fN + k1 * fb + b];
+    //  kFftColStep1: A-point DFTs over a down the grid columns (ncols), one
+    //    outer index per b; output scratch[(k1 * fb + b) * ncols + c];
+    //  kFftColStep2: B-point DFTs over b of scratch (outer index k1) with the
+    //    twiddle w_N^(b k1); output row out_slot(k1 + fa * k2) (+ epilogue).
+    int mode;
+    int fa, fb, fN, nouter;
+    long long in_stride;
+    const void* twN;
+    const void* deconv_col;
+    const void* deconv_row;
 };
+enum { kFftPlain = 0, kFftRowStep1 = 1, kFftColStep1 = 2, kFftColStep2 = 3, kFftStep2 = 4 };
 template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st);
 template <typename T>
 void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st);
 bool fft_supported(int n, int is_double, int* max_cols);
+// Split of a length beyond one pass into fa * fb (both single-pass), or false.
+bool fft_split(int n, int is_double, int* fa, int* fb);
 FftPlan make_fft_plan(int n, int max_radix);
 
 // k_interp.cu
@@ -327,7 +350,10 @@ struct T3Sort {
     int* cursor;
     int* perm;
     int* work;
+    int* partial;   // per 4096-bin chunk sums (bin counts too many to scan in one block)
 };
+constexpr int kBinScanStaged = 40000;   // bins scanned by one block in shared memory
+constexpr int kBinChunk = 4096;         // bins per block of the multi-block scan
 // sort == NULL (or FP64, or a width without a binned kernel): one thread per
 // target straight from global memory.  Otherwise four launches: bin count,
 // scan, scatter, binned interpolation.

@@ -260,7 +260,7 @@ __device__ __forceinline__ int out_slot(int k, int len, int n) {
 
 
 
-template <typename T>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm)
 k_fft_rows(FftPlan fp, RowPassArgs a) {
     using C = cx_t<T>;
@@ -272,31 +272,45 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
     const T* dcol = (const T*)a.deconv_col;
     // rows of dead tile rows are zero in and out of the transform: skipped
     auto next_live = [&](int r) {
-        if (a.live)
+        if (MODE == kFftPlain && a.live)
             while (r < a.nrows && !a.live[(r / a.batch_rows) * a.nty + (r % a.batch_rows) / kTile])
                 r += gridDim.x;
         return r;
     };
     for (int row = next_live(blockIdx.x); row < a.nrows; row = next_live(row + gridDim.x)) {
         const C* in = (const C*)a.in + (long long)row * a.in_stride;
-        C* out = (C*)a.out + (long long)row * a.out_stride;
-        const T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
-        auto load = [&](int e) {
-            const int i = in_src(e, a.in_len, n, a.centered_in);
-            if (i < 0) return Ops<T>::mk(0, 0);
-            C v = in[i];
-            if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
-            return v;
-        };
-        auto store = [&](int k, C v) {
-            const int kp = out_slot(k, a.out_len, n);
-            if (kp >= 0) out[kp] = v;
-        };
-        fft_fused<T, 1>(S, S2, fp, tw, load, store);
+        if constexpr (MODE == kFftStep2) {
+            // row = (l, k1): B-point DFT of scratch row with twiddle w_N^(b k1),
+            // output k = k1 + fa k2 into grid row l
+            const int l = row / a.fa, k1 = row - l * a.fa;
+            const C* twN = (const C*)a.twN;
+            C* out = (C*)a.out + (long long)l * a.out_stride;
+            auto load = [&](int b) { return Ops<T>::mul(in[b], __ldg(&twN[b * k1])); };
+            auto store = [&](int k2, C v) {
+                const int kp = out_slot(k1 + a.fa * k2, a.out_len, a.fN);
+                if (kp >= 0) out[kp] = v;
+            };
+            fft_fused<T, 1>(S, S2, fp, tw, load, store);
+        } else {
+            C* out = (C*)a.out + (long long)row * a.out_stride;
+            const T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
+            auto load = [&](int e) {
+                const int i = in_src(e, a.in_len, n, a.centered_in);
+                if (i < 0) return Ops<T>::mk(0, 0);
+                C v = in[i];
+                if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
+                return v;
+            };
+            auto store = [&](int k, C v) {
+                const int kp = out_slot(k, a.out_len, n);
+                if (kp >= 0) out[kp] = v;
+            };
+            fft_fused<T, 1>(S, S2, fp, tw, load, store);
+        }
     }
 }
 
-template <typename T, int NCOL>
+template <typename T, int NCOL, int MODE>
 __global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm)
 k_fft_cols(FftPlan fp, ColPassArgs a) {
     using C = cx_t<T>;
@@ -307,45 +321,101 @@ k_fft_cols(FftPlan fp, ColPassArgs a) {
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     const int ngroups = (a.ncols + NCOL - 1) / NCOL;
-    const int total = ngroups * max(a.batch, 1);   // (transform, column group) work items
+    const int nouter = MODE == kFftPlain ? max(a.batch, 1) : a.nouter;
+    const int total = ngroups * nouter;            // (outer index, column group) work items
     const int c = threadIdx.x & (NCOL - 1);        // this thread's column in every group
     for (int gg = blockIdx.x; gg < total; gg += gridDim.x) {
-        const int bi = gg / ngroups, col = (gg - bi * ngroups) * NCOL + c;
+        const int o = gg / ngroups, col = (gg - o * ngroups) * NCOL + c;
         const bool on = col < a.ncols;
-        const C* in = (const C*)a.in + (long long)bi * a.in_bstride + col;
-        C* out = (C*)a.out + (long long)bi * a.out_bstride + col;
-        if (a.live) {   // live tile rows of this transform as a bit mask
-            for (int t = threadIdx.x; t < kMaxTileRows / 32; t += blockDim.x) s_live[t] = 0u;
-            __syncthreads();
-            for (int t = threadIdx.x; t < a.nty; t += blockDim.x)
-                if (a.live[(long long)bi * a.nty + t]) atomicOr(&s_live[t >> 5], 1u << (t & 31));
-            __syncthreads();
-        }
-        C axc = Ops<T>::mk(1, 0);
-        const C* ay = nullptr;
-        if (a.ax && on) {
-            axc = ((const C*)a.ax)[(long long)bi * a.ncols + col];
-            ay = (const C*)a.ay + (long long)bi * a.out_len;
-        }
-        auto load = [&](int e) {
-            const int i = in_src(e, a.in_len, n, a.centered_in);
-            if (i < 0 || !on) return Ops<T>::mk(0, 0);
-            if (a.live) {
-                const int tr = i / kTile;
-                if (!((s_live[tr >> 5] >> (tr & 31)) & 1u)) return Ops<T>::mk(0, 0);
+        if constexpr (MODE == kFftPlain) {
+            const int bi = o;
+            const C* in = (const C*)a.in + (long long)bi * a.in_bstride + col;
+            C* out = (C*)a.out + (long long)bi * a.out_bstride + col;
+            if (a.live) {   // live tile rows of this transform as a bit mask
+                for (int t = threadIdx.x; t < kMaxTileRows / 32; t += blockDim.x) s_live[t] = 0u;
+                __syncthreads();
+                for (int t = threadIdx.x; t < a.nty; t += blockDim.x)
+                    if (a.live[(long long)bi * a.nty + t]) atomicOr(&s_live[t >> 5], 1u << (t & 31));
+                __syncthreads();
             }
-            return in[(long long)i * a.ncols];
-        };
-        auto store = [&](int k, C v) {
-            const int kp = out_slot(k, a.out_len, n);
-            if (kp < 0 || !on) return;
-            if (ay) {
-                v = Ops<T>::mul(Ops<T>::mul(v, axc), __ldg(&ay[kp]));
-                if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
+            C axc = Ops<T>::mk(1, 0);
+            const C* ay = nullptr;
+            if (a.ax && on) {
+                axc = ((const C*)a.ax)[(long long)bi * a.ncols + col];
+                ay = (const C*)a.ay + (long long)bi * a.out_len;
             }
-            out[(long long)kp * a.ncols] = v;
-        };
-        fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
+            auto load = [&](int e) {
+                const int i = in_src(e, a.in_len, n, a.centered_in);
+                if (i < 0 || !on) return Ops<T>::mk(0, 0);
+                if (a.live) {
+                    const int tr = i / kTile;
+                    if (!((s_live[tr >> 5] >> (tr & 31)) & 1u)) return Ops<T>::mk(0, 0);
+                }
+                return in[(long long)i * a.ncols];
+            };
+            auto store = [&](int k, C v) {
+                const int kp = out_slot(k, a.out_len, n);
+                if (kp < 0 || !on) return;
+                if (ay) {
+                    v = Ops<T>::mul(Ops<T>::mul(v, axc), __ldg(&ay[kp]));
+                    if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
+                }
+                out[(long long)kp * a.ncols] = v;
+            };
+            fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
+        } else if constexpr (MODE == kFftRowStep1) {
+            // grid row o viewed as fa x fb (element e = fb a + b at column b = col)
+            const C* in = (const C*)a.in + (long long)o * a.in_stride;
+            C* out = (C*)a.out + (long long)o * a.fN + col;
+            const T rowf = a.deconv_row ? ((const T*)a.deconv_row)[o] : (T)1;
+            const T* dcol = (const T*)a.deconv_col;
+            auto load = [&](int ea) {
+                if (!on) return Ops<T>::mk(0, 0);
+                const int i = in_src(a.fb * ea + col, a.in_len, a.fN, a.centered_in);
+                if (i < 0) return Ops<T>::mk(0, 0);
+                C v = in[i];
+                if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
+                return v;
+            };
+            auto store = [&](int k1, C v) {
+                if (on) out[(long long)k1 * a.fb] = v;
+            };
+            fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
+        } else if constexpr (MODE == kFftColStep1) {
+            // outer index o = b: rows e = fb a + b of the grid columns
+            const C* in = (const C*)a.in + col;
+            C* out = (C*)a.out + (long long)o * a.ncols + col;
+            auto load = [&](int ea) {
+                if (!on) return Ops<T>::mk(0, 0);
+                const int i = in_src(a.fb * ea + o, a.in_len, a.fN, a.centered_in);
+                if (i < 0) return Ops<T>::mk(0, 0);
+                return in[(long long)i * a.ncols];
+            };
+            auto store = [&](int k1, C v) {
+                if (on) out[(long long)k1 * a.fb * a.ncols] = v;
+            };
+            fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
+        } else {   // kFftColStep2: outer index o = k1
+            const C* in = (const C*)a.in + (long long)o * a.fb * a.ncols + col;
+            C* out = (C*)a.out + col;
+            const C* twN = (const C*)a.twN;
+            C axc = Ops<T>::mk(1, 0);
+            if (a.ax && on) axc = ((const C*)a.ax)[col];
+            auto load = [&](int b) {
+                if (!on) return Ops<T>::mk(0, 0);
+                return Ops<T>::mul(in[(long long)b * a.ncols], __ldg(&twN[b * o]));
+            };
+            auto store = [&](int k2, C v) {
+                const int kp = out_slot(o + a.fa * k2, a.out_len, a.fN);
+                if (kp < 0 || !on) return;
+                if (a.ax) {
+                    v = Ops<T>::mul(Ops<T>::mul(v, axc), __ldg(&((const C*)a.ay)[kp]));
+                    if (a.occulter) v = Ops<T>::mk((T)1 - v.x, -v.y);
+                }
+                out[(long long)kp * a.ncols] = v;
+            };
+            fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
+        }
     }
 }
 
@@ -397,11 +467,39 @@ bool fft_supported(int n, int is_double, int* max_cols) {
 template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st) {
     const size_t smem = 2 * (size_t)padded_len(fp.n) * sizeof(cx_t<T>);
-    cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int threads = threads_for(fp.n, emax<T>());
     int blocks = a.nrows < 152 * 16 ? a.nrows : 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_fft_rows<T><<<blocks, threads, smem, st>>>(fp, a);
+    if (a.mode == kFftStep2) {
+        cudaFuncSetAttribute(k_fft_rows<T, kFftStep2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_fft_rows<T, kFftStep2><<<blocks, threads, smem, st>>>(fp, a);
+    } else {
+        cudaFuncSetAttribute(k_fft_rows<T, kFftPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_fft_rows<T, kFftPlain><<<blocks, threads, smem, st>>>(fp, a);
+    }
+}
+
+template <typename T, int MODE>
+void launch_cols_mode(const FftPlan& fp, const ColPassArgs& a, int cmax, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)padded_len(fp.n) * cmax * sizeof(cx_t<T>);
+    const int threads = threads_for(fp.n * cmax, emax<T>());
+    const int nouter = MODE == kFftPlain ? (a.batch > 1 ? a.batch : 1) : a.nouter;
+    const long long work = (long long)((a.ncols + cmax - 1) / cmax) * nouter;
+    int blocks = work < 152 * 16 ? (int)work : 152 * 16;
+    if (blocks < 1) blocks = 1;
+#define FRES_COLS(NC)                                                                          \
+    case NC:                                                                                   \
+        cudaFuncSetAttribute(k_fft_cols<T, NC, MODE>,                                          \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+        k_fft_cols<T, NC, MODE><<<blocks, threads, smem, st>>>(fp, a);                         \
+        break;
+    switch (cmax) {
+        FRES_COLS(1) FRES_COLS(2) FRES_COLS(4) FRES_COLS(8)
+        default: break;
+    }
+#undef FRES_COLS
 }
 
 template <typename T>
@@ -411,22 +509,27 @@ void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st) {
     // fewer columns per block when that keeps three blocks per SM
     while (cmax > 1 && 2LL * padded_len(fp.n) * cmax * (long long)sizeof(cx_t<T>) > kFftSmemTarget)
         cmax >>= 1;
-    const size_t smem = 2 * (size_t)padded_len(fp.n) * cmax * sizeof(cx_t<T>);
-    const int threads = threads_for(fp.n * cmax, emax<T>());
-    const long long ngroups = (long long)((a.ncols + cmax - 1) / cmax) * (a.batch > 1 ? a.batch : 1);
-    int blocks = ngroups < 152 * 16 ? (int)ngroups : 152 * 16;
-    if (blocks < 1) blocks = 1;
-#define FRES_COLS(NC)                                                                         \
-    case NC:                                                                                  \
-        cudaFuncSetAttribute(k_fft_cols<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                             (int)smem);                                                      \
-        k_fft_cols<T, NC><<<blocks, threads, smem, st>>>(fp, a);                              \
-        break;
-    switch (cmax) {
-        FRES_COLS(1) FRES_COLS(2) FRES_COLS(4) FRES_COLS(8)
-        default: break;
+    switch (a.mode) {
+        case kFftRowStep1: launch_cols_mode<T, kFftRowStep1>(fp, a, cmax, st); break;
+        case kFftColStep1: launch_cols_mode<T, kFftColStep1>(fp, a, cmax, st); break;
+        case kFftColStep2: launch_cols_mode<T, kFftColStep2>(fp, a, cmax, st); break;
+        default: launch_cols_mode<T, kFftPlain>(fp, a, cmax, st); break;
     }
-#undef FRES_COLS
+}
+
+// n = fa * fb with both factors single-pass lengths, fa the divisor closest
+// to sqrt(n) from below that works.
+bool fft_split(int n, int is_double, int* fa, int* fb) {
+    int best = 0;
+    for (int d = 2; (long long)d * d <= n; ++d) {
+        if (n % d) continue;
+        if (make_fft_plan(d, 4).nstages < 0 || make_fft_plan(n / d, 4).nstages < 0) continue;
+        if (fft_supported(d, is_double, nullptr) && fft_supported(n / d, is_double, nullptr)) best = d;
+    }
+    if (!best) return false;
+    *fa = best;
+    *fb = n / best;
+    return true;
 }
 
 template void launch_fft_rows<float>(const FftPlan&, const RowPassArgs&, cudaStream_t);

@@ -269,6 +269,80 @@ __global__ void k_target_scan(int nbins, int* __restrict__ counts, int* __restri
     }
 }
 
+// Multi-block exclusive scan of the bin counts for large FFT grids: chunk
+// sums, one block scanning the chunk sums, then each chunk's own scan from
+// its offset (into bin starts and scatter cursors; counts cleared).
+__global__ void k_bin_chunk_sums(int nbins, const int* __restrict__ counts, int* __restrict__ partial) {
+    __shared__ int s[32];
+    const int b0 = blockIdx.x * kBinChunk;
+    int sum = 0;
+    for (int i = b0 + threadIdx.x; i < min(b0 + kBinChunk, nbins); i += blockDim.x) sum += counts[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < (int)(blockDim.x >> 5) ? s[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_bin_chunk_scan(int nchunks, int* __restrict__ partial) {
+    if (threadIdx.x != 0) return;
+    int run = 0;
+    for (int i = 0; i < nchunks; ++i) {
+        const int c = partial[i];
+        partial[i] = run;
+        run += c;
+    }
+}
+
+__global__ void k_bin_chunk_write(int nbins, int* __restrict__ counts, const int* __restrict__ partial,
+                                  int* __restrict__ start, int* __restrict__ cursor) {
+    __shared__ int s[kBinChunk];
+    __shared__ int w[32];
+    const int b0 = blockIdx.x * kBinChunk, n = min(kBinChunk, nbins - b0);
+    const int per = kBinChunk / blockDim.x;          // contiguous bins per thread
+    const int lo = threadIdx.x * per;
+    int sum = 0;
+    for (int i = 0; i < per; ++i) {
+        const int v = lo + i < n ? counts[b0 + lo + i] : 0;
+        s[lo + i] = v;
+        sum += v;
+    }
+    // exclusive scan of the per-thread sums (warp shuffles, then warp totals)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) w[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < (int)(blockDim.x >> 5) ? w[lane] : 0;
+        int vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += y;
+        }
+        w[lane] = vi - v;
+    }
+    __syncthreads();
+    int run = partial[blockIdx.x] + w[wid] + inc - sum;
+    for (int i = 0; i < per && lo + i < n; ++i) {
+        const int b = b0 + lo + i;
+        start[b] = run;
+        cursor[b] = run;
+        counts[b] = 0;
+        run += s[lo + i];
+    }
+}
+
 template <int W>
 __global__ void k_target_scatter(const double* __restrict__ targets, long long M, InterpParams ip,
                                  int* __restrict__ cursor, int* __restrict__ perm) {
@@ -392,13 +466,27 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
         if (sort) {   // binned path: count, scan, scatter, interpolate from patches
             const int nbins = ip.nbin1 * ip.nbin2;
             const int gb = nblk(M, 256, 152 * 16);
+            const bool staged = nbins <= kBinScanStaged;
             const size_t dyn = sizeof(int) * (size_t)nbins;
-            cudaFuncSetAttribute(k_target_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dyn);
+            const int nchunks = (nbins + kBinChunk - 1) / kBinChunk;
+            if (staged)
+                cudaFuncSetAttribute(k_target_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dyn);
+            auto scan = [&]() {
+                if (staged) {
+                    k_target_scan<<<1, 1024, dyn, st>>>(nbins, sort->counts, sort->start,
+                                                        sort->cursor);
+                } else {
+                    k_bin_chunk_sums<<<nchunks, 256, 0, st>>>(nbins, sort->counts, sort->partial);
+                    k_bin_chunk_scan<<<1, 32, 0, st>>>(nchunks, sort->partial);
+                    k_bin_chunk_write<<<nchunks, 256, 0, st>>>(nbins, sort->counts, sort->partial,
+                                                               sort->start, sort->cursor);
+                }
+            };
 #define FRES_BINNED_CASE(WW)                                                                   \
     case WW:                                                                                   \
         k_target_count<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->counts);                  \
-        k_target_scan<<<1, 1024, dyn, st>>>(nbins, sort->counts, sort->start, sort->cursor);   \
+        scan();                                                                                \
         k_target_scatter<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->cursor, sort->perm);    \
         k_interp_binned<WW><<<152 * 8, 128, 0, st>>>(targets, M, F, ip, cheb, ncheb,           \
                                                       (float2*)out, status, ks.horner,         \

@@ -690,7 +690,7 @@ k_scan_problems(int ntiles, int* __restrict__ counts, int* __restrict__ cursor,
         if (c > chunk_cap) {
             sc += (c + chunk_cap - 1) / chunk_cap;
             ++stl;
-        } else if (s_live[i / L.ntx]) {
+        } else if (!L.live || s_live[i / L.ntx]) {
             ++ns;
         }
     }
@@ -738,7 +738,7 @@ k_scan_problems(int ntiles, int* __restrict__ counts, int* __restrict__ cursor,
             scoff += nch;
             if (st0 + stoff < st1) split_tiles[st0 + stoff] = base + i;
             ++stoff;
-        } else if (s_live[i / L.ntx]) {
+        } else if (!L.live || s_live[i / L.ntx]) {
             const long long ci = pl0 + nsoff;
             if (ci < pl1) {
                 Chunk ch;

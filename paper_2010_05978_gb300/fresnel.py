@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
                 ("box", ctypes.c_double * 4), ("sigma", ctypes.c_double),
                 ("kernel_w", ctypes.c_int), ("recompute_nodes", ctypes.c_int),
                 ("sync_status", ctypes.c_int), ("max_device_bytes", ctypes.c_longlong),
-                ("t3_binning", ctypes.c_int)]
+                ("t3_binning", ctypes.c_int), ("fft_split_above", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -173,7 +173,7 @@ def _family_array(families):
 
 
 def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes, sync_status,
-               max_device_bytes, t3_binning):
+               max_device_bytes, t3_binning, fft_split_above=0):
     o = Opts()
     lib.fresnel_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -193,6 +193,7 @@ def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nod
     o.sync_status = int(bool(sync_status))
     o.max_device_bytes = int(max_device_bytes)
     o.t3_binning = int(t3_binning)
+    o.fft_split_above = int(fft_split_above)
     return o
 
 
@@ -309,14 +310,14 @@ class Plan(_PlanHandle):
 
     def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
                  box=None, sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
-                 max_device_bytes=0, t3_binning=0, stream=None):
+                 max_device_bytes=0, t3_binning=0, fft_split_above=0, stream=None):
         import torch
         lib = load_library()
         self._torch = torch
         fams, keep = _family_array(families)
         self.profile_sizes = _profile_sizes(families)
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
-                       sync_status, max_device_bytes, t3_binning)
+                       sync_status, max_device_bytes, t3_binning, fft_split_above)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
