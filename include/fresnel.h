@@ -174,10 +174,11 @@ fresnel_status fresnel_plan(const fresnel_family* families, int n_families,
 /*
  * A batch of independent problems sharing one target grid, e.g. one
  * starshade at many wavelengths (the wavelength sweeps of Sec. 4.2): each
- * problem has its own families (host array) and lambda, z.  Only GRID plans
- * (opts->target_kind = FRESNEL_GRID) are batched in this build; tol, opts
- * and the grid are common.  All problems share one spreading kernel and one
- * FFT size, so one launch per stage serves the whole batch.  Otherwise as
+ * problem has its own families (host array) and lambda, z; tol and opts are
+ * common.  GRID targets: all problems share the grid, one spreading kernel
+ * and one FFT size, so one launch per stage serves the whole batch
+ * (fresnel_eval_many).  SCATTERED targets: one sub-plan per problem, sized
+ * for it, evaluated together by fresnel_eval_many_scattered.  Otherwise as
  * fresnel_plan (which is the one-problem case).
  */
 typedef struct {
@@ -189,6 +190,21 @@ typedef struct {
 fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems, double tol,
                                  const fresnel_opts* opts, void* cuda_stream,
                                  fresnel_plan_t* out_plan);
+
+/*
+ * Scattered-target batches (fresnel_plan_many with opts->target_kind =
+ * FRESNEL_SCATTERED): every problem gets its own NUFFT sizes (its aperture
+ * and lambda z set them), all with the opts box; problem b has M_each[b]
+ * targets (HOST array of n_problems counts, each >= 0).  d_targets (DEVICE)
+ * holds all problems' (xi, eta) FP64 pairs concatenated in problem order and
+ * d_out (DEVICE) receives the concatenated fields (complex64 / complex128).
+ * The whole batch is one CUDA graph (captured on the first call and again
+ * whenever the counts or pointers change) spread over four internal streams
+ * and joined back into the plan's stream.  Asynchronous unless
+ * opts.sync_status = 1.  Also accepts a one-problem SCATTERED plan.
+ */
+fresnel_status fresnel_eval_many_scattered(fresnel_plan_t plan, const double* d_targets,
+                                           const long long* M_each, void* d_out);
 
 /*
  * Evaluates every problem of a plan on its grid: d_out is a DEVICE array of

@@ -130,6 +130,15 @@ struct Plan {
     int nev = 0;
     int launches = 0;
     int last_launches = 0;     // kernels launched by the most recent evaluation
+    // scattered-target batches: one sub-plan per problem, evaluated as one
+    // CUDA graph over kLanes internal streams
+    std::vector<Plan*> subs;
+    cudaStream_t lanes[4] = {};
+    cudaEvent_t ev_fork = nullptr, ev_in = nullptr, ev_out = nullptr, ev_join[4] = {};
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<long long> g_M;   // key of the captured graph: counts and pointers
+    const void* g_t = nullptr;
+    void* g_out = nullptr;
     // profile-gradient scratch (allocated on first use)
     void* adj_in = nullptr;       // B x n2 x n1: sgn conj(gamma) ax ay
     void* adj_rows = nullptr;     // B x n2 x nf1 after the row pass
@@ -168,6 +177,13 @@ fresnel_status dalloc(Plan* p, void** out, size_t bytes) {
 void free_plan(Plan* p) {
     if (!p) return;
     cudaStreamSynchronize(p->st);
+    for (Plan* q : p->subs) free_plan(q);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (cudaStream_t& l : p->lanes)
+        if (l) cudaStreamDestroy(l);
+    for (cudaEvent_t e : {p->ev_fork, p->ev_in, p->ev_out, p->ev_join[0], p->ev_join[1],
+                          p->ev_join[2], p->ev_join[3]})
+        if (e) cudaEventDestroy(e);
     for (void* a : p->allocs) cudaFree(a);
     if (p->perm) cudaFree(p->perm);
     for (int i = 0; i < kMaxEvents; ++i)
@@ -1223,6 +1239,16 @@ fresnel_status grad_profile_impl(Plan* p, const void* d_gamma, double* d_grad) {
 
 }  // namespace
 
+namespace {
+// A scattered-target batch: one sub-plan per problem (each sized for its own
+// aperture and lambda z; all with the opts box), internal streams and events
+// for the graph that evaluates them together.
+fresnel_status plan_scattered_batch(const fresnel_problem* problems, int n, double tol,
+                                    const fresnel_opts* opts, void* stream,
+                                    fresnel_plan_t* out_plan);
+fresnel_status read_batch_status(Plan* p);
+}  // namespace
+
 extern "C" {
 
 void fresnel_default_opts(fresnel_opts* o) {
@@ -1271,8 +1297,6 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
         for (int i = 0; i < 4; ++i)
             if (!std::isfinite(b[i])) return fres_fail(FRESNEL_ERR_ARG, "box must be finite");
         if (!(b[0] <= b[1]) || !(b[2] <= b[3])) return fres_fail(FRESNEL_ERR_ARG, "box must have min <= max");
-        if (n_problems > 1)
-            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "batched plans take GRID targets only");
     } else {
         return fres_fail(FRESNEL_ERR_ARG, "unknown target_kind");
     }
@@ -1286,6 +1310,8 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
         return fres_fail(FRESNEL_ERR_ARG, "fft_split_above must be >= 0");
     int dev = 0;
     FRES_CK(cudaGetDevice(&dev));
+    if (opts->target_kind == FRESNEL_SCATTERED && n_problems > 1)
+        return plan_scattered_batch(problems, n_problems, tol, opts, cuda_stream, out_plan);
     Plan* p = new Plan();
     p->prec = opts->precision;
     p->output = opts->output;
@@ -1396,6 +1422,7 @@ fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, do
 fresnel_status fresnel_check(fresnel_plan_t plan) {
     Plan* p = as_plan(plan);
     if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (!p->subs.empty()) return read_batch_status(p);
     return read_status(p);
 }
 
@@ -1412,6 +1439,19 @@ const char* fresnel_last_error(void) { return g_last_error.c_str(); }
 fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
     Plan* p = as_plan(plan);
     if (!p || !info) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle or info");
+    if (!p->subs.empty()) {   // batch: the first problem's shapes, totals over all
+        FRES_TRY(fresnel_get_info(reinterpret_cast<fresnel_plan_t>(p->subs[0]), info));
+        info->n_nodes = p->N;
+        long long bytes = 0;
+        int launches = 0;
+        for (Plan* q : p->subs) {
+            bytes += q->bytes;
+            launches += q->last_launches;
+        }
+        info->device_bytes = bytes;
+        info->launches_per_eval = launches;
+        return FRESNEL_OK;
+    }
     info->n_nodes = p->N;
     info->w = p->ks.w;
     info->beta = p->ks.beta;
@@ -1435,6 +1475,8 @@ fresnel_status fresnel_get_nodes(fresnel_plan_t plan, double* d_x, double* d_y, 
     Plan* p = as_plan(plan);
     if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
     if (!d_x || !d_y || !d_w) return fres_fail(FRESNEL_ERR_ARG, "node output arrays are NULL");
+    if (!p->subs.empty())
+        return fres_fail(FRESNEL_ERR_ARG, "scattered-target batch: nodes are per sub-plan");
     // Regenerates the nodes (and, harmlessly, the unsorted records and counts),
     // then re-runs the scan so the counts are reset and the cached sort stays valid.
     if (p->prec == FRESNEL_FP64) {
@@ -1467,6 +1509,168 @@ int fresnel_stage_times(fresnel_plan_t plan, double* stage_ms, const char** name
         if (names) names[n] = p->ev_name[i];
     }
     return n;
+}
+
+}  // extern "C"
+
+namespace {
+
+fresnel_status plan_scattered_batch(const fresnel_problem* problems, int n, double tol,
+                                    const fresnel_opts* opts, void* stream,
+                                    fresnel_plan_t* out_plan) {
+    Plan* p = new Plan();
+    p->prec = opts->precision;
+    p->output = opts->output;
+    p->tkind = FRESNEL_SCATTERED;
+    p->B = n;
+    p->tol = tol;
+    p->st = (cudaStream_t)stream;
+    p->opts = *opts;
+    fresnel_opts so = *opts;
+    so.sync_status = 0;   // the batch reads every sub-plan's status itself
+    auto fail = [&](fresnel_status st) {
+        std::string msg = g_last_error;
+        cudaGetLastError();
+        free_plan(p);
+        g_last_error = msg;
+        return st;
+    };
+    for (int b = 0; b < n; ++b) {
+        fresnel_plan_t h = nullptr;
+        fresnel_status st = fresnel_plan_many(&problems[b], 1, tol, &so, stream, &h);
+        if (st != FRESNEL_OK) {
+            g_last_error = "problem " + std::to_string(b) + ": " + g_last_error;
+            return fail(st);
+        }
+        p->subs.push_back(reinterpret_cast<Plan*>(h));
+        p->N += p->subs.back()->N;
+        p->lzs.push_back(p->subs.back()->lz);
+        p->bytes += p->subs.back()->bytes;
+    }
+    p->lz = p->lzs[0];
+    for (cudaStream_t& l : p->lanes)
+        if (cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(fres_fail(FRESNEL_ERR_CUDA, "cudaStreamCreate failed"));
+    for (cudaEvent_t* e : {&p->ev_fork, &p->ev_in, &p->ev_out, &p->ev_join[0], &p->ev_join[1],
+                           &p->ev_join[2], &p->ev_join[3]})
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(fres_fail(FRESNEL_ERR_CUDA, "cudaEventCreate failed"));
+    for (int b = 0; b < n; ++b) p->subs[b]->st = p->lanes[b % 4];
+    *out_plan = reinterpret_cast<fresnel_plan_t>(p);
+    return FRESNEL_OK;
+}
+
+// Grows a type-3 plan's target permutation ahead of graph capture (no
+// allocation may happen while the evaluation is being captured).
+fresnel_status ensure_perm(Plan* q, long long M) {
+    if (q->prec != FRESNEL_FP32_FAST || M < kSortTargetsFrom || M <= q->perm_cap) return FRESNEL_OK;
+    FRES_CK(cudaStreamSynchronize(q->st));
+    if (q->perm) cudaFree(q->perm);
+    q->perm = nullptr;
+    q->perm_cap = 0;
+    FRES_CK(cudaMalloc((void**)&q->perm, sizeof(int) * (size_t)M));
+    q->perm_cap = M;
+    return FRESNEL_OK;
+}
+
+// Captures the batch's evaluation on the internal lanes (fork from lane 0,
+// problem b on lane b mod 4, join back) into p->gexec.
+template <typename T>
+fresnel_status capture_batch(Plan* p, const double* d_targets, const long long* M, void* d_out) {
+    for (int b = 0; b < p->B; ++b) FRES_TRY(ensure_perm(p->subs[b], M[b]));
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    FRES_CK(cudaStreamBeginCapture(p->lanes[0], cudaStreamCaptureModeRelaxed));
+    fresnel_status st = FRESNEL_OK;
+    cudaEventRecord(p->ev_fork, p->lanes[0]);
+    for (int k = 1; k < 4; ++k) cudaStreamWaitEvent(p->lanes[k], p->ev_fork, 0);
+    const size_t cs = p->csize();
+    long long off = 0;
+    for (int b = 0; b < p->B && st == FRESNEL_OK; ++b) {
+        st = eval_impl<T>(p->subs[b], M[b] > 0 ? d_targets + 2 * off : nullptr, M[b],
+                          M[b] > 0 ? (char*)d_out + cs * off : nullptr);
+        off += M[b];
+    }
+    for (int k = 1; k < 4; ++k) {
+        cudaEventRecord(p->ev_join[k], p->lanes[k]);
+        cudaStreamWaitEvent(p->lanes[0], p->ev_join[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->lanes[0], &g);
+    if (st != FRESNEL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess)
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    p->g_M.assign(M, M + p->B);
+    p->g_t = d_targets;
+    p->g_out = d_out;
+    return FRESNEL_OK;
+}
+
+// Reads (and clears) every sub-plan's device status after the batch joined
+// back into the caller's stream.
+fresnel_status read_batch_status(Plan* p) {
+    std::vector<unsigned> h(p->subs.size(), 0u);
+    for (size_t b = 0; b < p->subs.size(); ++b)
+        FRES_CK(cudaMemcpyAsync(&h[b], p->subs[b]->status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    for (size_t b = 0; b < p->subs.size(); ++b)
+        if (h[b]) {
+            FRES_CK(cudaMemsetAsync(p->subs[b]->status, 0, sizeof(unsigned), p->st));
+            FRES_CK(cudaStreamSynchronize(p->st));
+            std::string msg = "problem " + std::to_string(b) + ": device check failed:";
+            if (h[b] & kStatusTargetOutside) msg += " target outside the plan's box;";
+            if (h[b] & kStatusNodeOutside) msg += " node support outside the type-3 grid;";
+            if (h[b] & kStatusNonFinite) msg += " non-finite coordinate;";
+            if (h[b] & kStatusOverflow) msg += " sort region overflow;";
+            return fres_fail(FRESNEL_ERR_DEVICE, msg);
+        }
+    return FRESNEL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fresnel_status fresnel_eval_many_scattered(fresnel_plan_t plan, const double* d_targets,
+                                           const long long* M_each, void* d_out) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (p->tkind != FRESNEL_SCATTERED)
+        return fres_fail(FRESNEL_ERR_ARG, "fresnel_eval_many_scattered needs a SCATTERED plan");
+    if (!M_each) return fres_fail(FRESNEL_ERR_ARG, "M_each is NULL");
+    long long total = 0;
+    for (int b = 0; b < p->B; ++b) {
+        if (M_each[b] < 0) return fres_fail(FRESNEL_ERR_ARG, "M_each entries must be >= 0");
+        total += M_each[b];
+    }
+    if (total > 0 && (!d_targets || !d_out))
+        return fres_fail(FRESNEL_ERR_ARG, "d_targets or d_out is NULL");
+    if (p->subs.empty()) return fresnel_eval(plan, d_targets, M_each[0], d_out);
+    const bool same = p->gexec && p->g_t == d_targets && p->g_out == d_out &&
+                      std::equal(p->g_M.begin(), p->g_M.end(), M_each);
+    if (!same) {
+        // the previous graph may still run on the lanes: capture after it
+        FRES_CK(cudaStreamSynchronize(p->lanes[0]));
+        FRES_TRY(p->prec == FRESNEL_FP64 ? capture_batch<double>(p, d_targets, M_each, d_out)
+                                         : capture_batch<float>(p, d_targets, M_each, d_out));
+    }
+    FRES_CK(cudaEventRecord(p->ev_in, p->st));
+    FRES_CK(cudaStreamWaitEvent(p->lanes[0], p->ev_in, 0));
+    FRES_CK(cudaGraphLaunch(p->gexec, p->lanes[0]));
+    FRES_CK(cudaEventRecord(p->ev_out, p->lanes[0]));
+    FRES_CK(cudaStreamWaitEvent(p->st, p->ev_out, 0));
+    if (p->opts.sync_status) return read_batch_status(p);
+    return FRESNEL_OK;
 }
 
 }  // extern "C"

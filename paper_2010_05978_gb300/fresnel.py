@@ -64,7 +64,8 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_plan_many", "fresnel_eval",
-           "fresnel_eval_many", "fresnel_eval_host", "fresnel_grad_profile",
+           "fresnel_eval_many", "fresnel_eval_many_scattered", "fresnel_eval_host",
+           "fresnel_grad_profile",
            "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
            "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread",
            "fresnel_spread_noalloc"]
@@ -94,6 +95,8 @@ def load_library(path=LIB_PATH):
     lib.fresnel_eval.restype = ctypes.c_int
     lib.fresnel_eval_many.argtypes = [vp, vp]
     lib.fresnel_eval_many.restype = ctypes.c_int
+    lib.fresnel_eval_many_scattered.argtypes = [vp, vp, ctypes.POINTER(ll), vp]
+    lib.fresnel_eval_many_scattered.restype = ctypes.c_int
     lib.fresnel_grad_profile.argtypes = [vp, vp, vp]
     lib.fresnel_grad_profile.restype = ctypes.c_int
     lib.fresnel_eval_host.argtypes = [vp, vp, ll, vp]
@@ -254,16 +257,18 @@ class _PlanHandle:
 
 
 class BatchPlan(_PlanHandle):
-    """Several independent problems on one target grid (``fresnel_plan_many``).
+    """Several independent problems in one plan (``fresnel_plan_many``).
 
     problems: list of dicts {"families": [...], "lam": lambda, "z": z}; the
-    other arguments as for ``Plan`` (grid targets only).  ``eval()`` returns a
-    CUDA tensor of shape (n_problems, n2, n1).
+    other arguments as for ``Plan``.  With grid=...: ``eval()`` returns a
+    CUDA tensor of shape (n_problems, n2, n1).  With box=...: ``eval(targets,
+    counts)`` takes every problem's targets concatenated (float64 CUDA tensor
+    (sum(counts), 2)) and returns the concatenated fields.
     """
 
-    def __init__(self, problems, tol, precision="fp32", output="aperture", grid=None, sigma=0.0,
-                 kernel_w=0, recompute_nodes=False, sync_status=True, max_device_bytes=0,
-                 stream=None):
+    def __init__(self, problems, tol, precision="fp32", output="aperture", grid=None, box=None,
+                 sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
+                 max_device_bytes=0, t3_binning=0, fft_split_above=0, stream=None):
         import torch
         lib = load_library()
         self._torch = torch
@@ -274,8 +279,8 @@ class BatchPlan(_PlanHandle):
             fams, keep = _family_array(q["families"])
             self._keep.append((fams, keep))
             probs[b] = Problem(fams, len(q["families"]), float(q["lam"]), float(q["z"]))
-        o = _make_opts(lib, precision, output, grid, None, sigma, kernel_w, recompute_nodes,
-                       sync_status, max_device_bytes, 0)
+        o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
+                       sync_status, max_device_bytes, t3_binning, fft_split_above)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -288,13 +293,26 @@ class BatchPlan(_PlanHandle):
         self.n_problems = len(problems)
         self.cdtype = torch.complex64 if precision == "fp32" else torch.complex128
 
-    def eval(self, out=None):
+    def eval(self, targets=None, counts=None, out=None):
         torch = self._torch
-        shape = (self.n_problems, self.grid["n2"], self.grid["n1"])
+        if self.grid is not None:
+            shape = (self.n_problems, self.grid["n2"], self.grid["n1"])
+            if out is None:
+                out = torch.empty(shape, dtype=self.cdtype, device="cuda")
+            assert out.is_cuda and out.is_contiguous() and tuple(out.shape) == shape
+            _check(load_library().fresnel_eval_many(self.handle, out.data_ptr()))
+            return out
+        counts = [int(m) for m in counts]
+        assert len(counts) == self.n_problems
+        total = sum(counts)
+        assert targets.dtype == torch.float64 and targets.is_cuda and targets.is_contiguous()
+        assert tuple(targets.shape) == (total, 2)
         if out is None:
-            out = torch.empty(shape, dtype=self.cdtype, device="cuda")
-        assert out.is_cuda and out.is_contiguous() and tuple(out.shape) == shape
-        _check(load_library().fresnel_eval_many(self.handle, out.data_ptr()))
+            out = torch.empty((total,), dtype=self.cdtype, device="cuda")
+        M = (ctypes.c_longlong * self.n_problems)(*counts)
+        _check(load_library().fresnel_eval_many_scattered(
+            self.handle, targets.data_ptr() if total else None, M,
+            out.data_ptr() if total else None))
         return out
 
 

@@ -75,11 +75,9 @@ def test_plan_many_argument_errors(lib):
     assert h.value is None
     assert lib.fresnel_plan_many(probs, 2, 1e-6, ctypes.byref(o), None, ctypes.byref(h)) == -1
     assert "lambda" in lib.fresnel_last_error().decode()
-    probs[1] = fresnel.Problem(fams, 1, 0.2, 1.0)
-    o.target_kind = 1
-    assert lib.fresnel_plan_many(probs, 2, 1e-6, ctypes.byref(o), None, ctypes.byref(h)) == -5
-    assert "GRID" in lib.fresnel_last_error().decode()
     assert lib.fresnel_eval_many(None, None) == -1
+    M = (ctypes.c_longlong * 2)(1, 2)
+    assert lib.fresnel_eval_many_scattered(None, None, M, None) == -1
 
 
 def test_default_opts(lib):

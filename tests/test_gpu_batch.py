@@ -99,3 +99,96 @@ def test_single_eval_rejects_batched_plan():
     with pytest.raises(FresnelError):
         from paper_2010_05978_gb300.fresnel import _check
         _check(load_library().fresnel_eval(p.handle, None, 256, out.data_ptr()))
+
+
+# ------------------------------------------------------------------ scattered-target batches
+def _scattered_problems():
+    return [
+        {"families": [W.fourier_family(W.STAR_PARAMS, 32, 16, 32, cx=0.1)], "lam": 0.03, "z": 1.0},
+        {"families": [W.fourier_family([1.0], 24, 16, 24)], "lam": 0.1, "z": 1.0},
+        {"families": [W.petal_family(5, 0.4, 1.0, {"kind": "hg", "b": 0.35, "q": 4},
+                                     30, 20, 40, 30)], "lam": 0.05, "z": 1.0},
+    ]
+
+
+def _targets(counts, half=1.5):
+    xs, ys = [], []
+    for i, m in enumerate(counts):
+        x, y = W.square_targets(m, half, 11, 300 + i)
+        xs.append(x)
+        ys.append(y)
+    xi, eta = np.concatenate(xs), np.concatenate(ys)
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    return xi, eta, t
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_scattered_batch_matches_oracle_and_single_plans(prec):
+    from paper_2010_05978_gb300 import BatchPlan, Plan
+    probs = _scattered_problems()
+    counts = [700, 0, 40000]     # an empty problem and one large enough to bin (FP32)
+    xi, eta, t = _targets(counts)
+    tol, bar = BARS[prec]
+    box = (-1.5, 1.5, -1.5, 1.5)
+    p = BatchPlan(probs, tol, precision=prec, box=box, output="occulter")
+    u = p.eval(t, counts).cpu().numpy()
+    off = 0
+    for b, q in enumerate(probs):
+        m = counts[b]
+        if m:
+            sl = slice(off, off + m)
+            idx = np.arange(off, off + m)[:: max(1, m // 300)]
+            ref = oracle.field(q["families"], q["lam"], q["z"], xi[idx], eta[idx], output="occulter")
+            assert rel_l2(1.0 - u[idx], 1.0 - ref) <= bar, b
+            single = Plan(q["families"], q["lam"], q["z"], tol, precision=prec, box=box,
+                          output="occulter").eval(t[sl].contiguous()).cpu().numpy()
+            assert np.max(np.abs(single - u[sl])) <= (1e-13 if prec == "fp64" else 2e-6)
+        off += m
+    p.check()
+
+
+def test_scattered_batch_graph_replay_and_recapture():
+    from paper_2010_05978_gb300 import BatchPlan
+    probs = _scattered_problems()
+    p = BatchPlan(probs, 1e-12, precision="fp64", box=(-1.5, 1.5, -1.5, 1.5))
+    counts = [300, 200, 100]
+    xi, eta, t = _targets(counts)
+    out = torch.empty(sum(counts), dtype=torch.complex128, device="cuda")
+    a = p.eval(t, counts, out).cpu().numpy()
+    for _ in range(3):                       # replays of the captured graph
+        b = p.eval(t, counts, out).cpu().numpy()
+        # equal up to the order of the atomic adds into shared spreading tiles
+        assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
+    counts2 = [100, 300, 200]                # new counts: captured again
+    xi2, eta2, t2 = _targets(counts2)
+    c = p.eval(t2, counts2).cpu().numpy()
+    ref = oracle.field(probs[1]["families"], probs[1]["lam"], 1.0, xi2[100:400], eta2[100:400])
+    assert rel_l2(c[100:400], ref) <= 1e-10
+    info = p.info()
+    assert info["n_nodes"] == sum(len(oracle.nodes(q["families"])[0]) for q in probs)
+
+
+def test_random_star_batch32_full_size_sampled():
+    """32 uneven instances (1e5-2e6 nodes, F = 100..450, 1e5-1e7 targets each,
+    5.5e7 in all) in one batched evaluation, FP32 fast mode; 20 sampled
+    targets per instance against the oracle."""
+    from paper_2010_05978_gb300 import BatchPlan
+    probs, counts = W.random_star_batch()
+    total = sum(counts)
+    t = torch.empty((total, 2), dtype=torch.float64, device="cuda")
+    samples = []
+    off = 0
+    for i, m in enumerate(counts):
+        x, y = W.square_targets(m, 1.2, 5, 100 + i)
+        t[off:off + m, 0].copy_(torch.from_numpy(x))
+        t[off:off + m, 1].copy_(torch.from_numpy(y))
+        idx = W.rng(5, 500 + i).choice(m, 20, replace=False)
+        samples.append((off + idx, x[idx], y[idx]))
+        off += m
+    p = BatchPlan(probs, 1e-6, precision="fp32", box=(-1.2, 1.2, -1.2, 1.2))
+    u = p.eval(t, counts)
+    for (gidx, x, y), q in zip(samples, probs):
+        got = u[torch.tensor(gidx, device="cuda")].cpu().numpy()
+        ref = oracle.field(q["families"], q["lam"], q["z"], x, y)
+        assert rel_l2(got, ref) <= 1e-6
+    p.check()

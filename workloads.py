@@ -93,8 +93,8 @@ def square_targets(M, half, config_id, stream=1):
 
 
 # ---------------------------------------------------------------- random star (F = 1000)
-def random_star_params(config_id=5, K=20, amax=0.02):
-    g = rng(config_id, 0)
+def random_star_params(config_id=5, K=20, amax=0.02, stream=0):
+    g = rng(config_id, stream)
     a = g.uniform(0.0, amax, K)
     ph = g.uniform(0.0, 2.0 * np.pi, K)
     params = [1.0]
@@ -210,3 +210,25 @@ def random_star(n_panels=640, p=16, m=1024, fresnel_number=1000.0, config_id=5):
         "families": [fourier_family(params, n_panels, p, m)],
         "lam": R * R / fresnel_number, "z": 1.0,
     }
+
+
+def random_star_batch(n=32, config_id=5):
+    """32 uneven instances of the random smooth aperture: N_i log-uniform in
+    [1e5, 2e6] nodes, F_i = 1000 sqrt(N_i / 1e7), a fresh shape each, M_i
+    log-uniform in [1e5, 1e7] targets uniform in [-1.2, 1.2]^2.  Node layout
+    as in ``random_star`` (boundary nodes : radii = 10 : 1, 16 per panel).
+    Returns (problems, counts); targets of instance i from
+    ``square_targets(counts[i], 1.2, config_id, 100 + i)``."""
+    g = rng(config_id, 40)
+    N = np.exp(g.uniform(np.log(1e5), np.log(2e6), n))
+    M = np.exp(g.uniform(np.log(1e5), np.log(1e7), n)).astype(np.int64)
+    problems = []
+    for i in range(n):
+        params = random_star_params(config_id, stream=100 + i)
+        m = int(np.ceil(np.sqrt(N[i] / 10.0)))
+        n_panels = int(np.ceil(N[i] / (16.0 * m)))
+        F = 1000.0 * np.sqrt(N[i] / 1e7)
+        R = max_radius(params)
+        problems.append({"families": [fourier_family(params, n_panels, 16, m)],
+                         "lam": R * R / F, "z": 1.0})
+    return problems, [int(x) for x in M]
