@@ -494,13 +494,209 @@ def run_sweep(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ F = 1000 random aperture
+R1000_METRIC = "Fresnel target pts/sec at 1e-6 rel L2 err (F=1000, 1e7 nodes, 1e8 scattered targets)"
+BATCH_METRIC = "Fresnel target pts/sec at 1e-6 rel L2 err (32-instance batch, 1e5-2e6 nodes, 5.5e7 targets)"
+
+
+def _host_targets(counts, config_id, streams):
+    xs, ys = [], []
+    for m, st in zip(counts, streams):
+        x, y = W.square_targets(m, 1.2, config_id, st)
+        xs.append(x)
+        ys.append(y)
+    return np.ascontiguousarray(np.stack([np.concatenate(xs), np.concatenate(ys)], 1))
+
+
+def _oracle_rate_t3(problems, targets_per, budget_s):
+    """Oracle targets/s on a bounded sample: a few targets of each problem,
+    quadrature rebuilt + direct FP64 sum, scaled by each problem's share."""
+    import oracle
+    from oracle import direct
+    t_total, n_total = 0.0, 0
+    for q, (x, y) in zip(problems, targets_per):
+        t0 = time.perf_counter()
+        oracle.field(q["families"], q["lam"], q["z"], x, y)
+        t_total += time.perf_counter() - t0
+        n_total += len(x)
+        if t_total > budget_s:
+            break
+    return n_total / t_total, direct.max_threads(), n_total, t_total
+
+
+def run_randstar(args, rank, world, local_rank, batch):
+    import torch
+    from paper_2010_05978_gb300 import BatchPlan, Plan, build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    box = (-1.2, 1.2, -1.2, 1.2)
+    if batch:
+        problems, counts = W.random_star_batch()
+        h_t = _host_targets(counts, 5, [100 + i for i in range(len(counts))])
+        p = BatchPlan(problems, TOL, precision="fp32", box=box, recompute_nodes=True,
+                      sync_status=False)
+        step = lambda t, o: p.eval(t, counts, o)
+        metric, name = BATCH_METRIC, "randstar_batch32"
+    else:
+        cfg = W.random_star()
+        problems = [{"families": cfg["families"], "lam": cfg["lam"], "z": cfg["z"]}]
+        counts = [100_000_000]
+        h_t = _host_targets(counts, 5, [1])
+        p = Plan(cfg["families"], cfg["lam"], cfg["z"], TOL, precision="fp32", box=box,
+                 recompute_nodes=True, sync_status=False)
+        p.set_timing(True)
+        step = lambda t, o: p.eval(t, o)
+        metric, name = R1000_METRIC, "randstar20_F1000"
+    total = sum(counts)
+    info = p.info()
+    t = torch.from_numpy(h_t).to(dev)
+    out = torch.empty(total, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        step(t, out)
+    torch.cuda.synchronize()
+    p.check()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    step_ms, stage_sum = [], {}
+    for _ in range(args.steps):       # inputs (1.6 GB / 0.9 GB) are larger than L2
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step(t, out)
+        e.record(stream)
+        e.synchronize()
+        step_ms.append(s.elapsed_time(e))
+        if not batch:
+            for k, v in p.stage_times().items():
+                stage_sum[k] = stage_sum.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    p.check()
+    ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, float(total), world, dev)
+    # end to end: host targets in, host fields out, inside the timed region
+    h_out = torch.empty(total, dtype=torch.complex64, pin_memory=True)
+    h_in = torch.from_numpy(h_t).pin_memory()
+    e2e_ms = []
+    for i in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t.copy_(h_in, non_blocking=True)
+        step(t, out)
+        h_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        if i:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = total * world / (statistics.median(e2e_ms) * 1e-3)
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    c64 = 8
+    if batch:   # stage times are not kept inside the captured graph: whole step
+        ab = total * (16 + c64) + info["n_nodes"] * 24
+        roof = {"bound": "hbm", "kernel": "whole batch step (one graph)", "achieved":
+                ab / (ms_per_step * 1e-3) / 1e9, "algorithmic_bytes": ab,
+                "ms_per_launch": ms_per_step}
+    else:
+        per = {k: v / args.steps for k, v in stage_sum.items()}
+        g = info["nf1"] * info["nf2"]
+        F = info["nfft1"] * info["nfft2"]
+        ab = {"spread": info["n_nodes"] * 24 + g * c64,
+              "fft_rows": (g + info["nf2"] * info["nfft1"]) * c64,
+              "fft_cols": (info["nf2"] * info["nfft1"] + F) * c64,
+              "interp_epilogue": total * (16 + c64)}
+        dom = max((k for k in per if k in ab), key=lambda k: per[k])
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ab[dom] / (per[dom] * 1e-3) / 1e9,
+                "algorithmic_bytes": ab[dom], "ms_per_launch": per[dom]}
+    roof.update({"peak": peak, "unit": "GB/s", "frac": roof["achieved"] / peak, "traffic": None,
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
+                                "fallback 6800 GB/s"})
+    sample = []
+    off = 0
+    for i, m in enumerate(counts):
+        idx = W.rng(5, 900 + i).choice(m, 8 if batch else 200, replace=False)
+        sample.append((h_t[off + idx, 0], h_t[off + idx, 1]))
+        off += m
+    rate, cores, n_s, t_s = _oracle_rate_t3(problems, sample, 10.0)
+    line = {
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": name, "targets": total, "nodes": info["n_nodes"],
+                   "instances": len(problems), "tol": TOL,
+                   "precision": "fp32 spread/fft/interp, double-float phases",
+                   "nodes_recomputed_each_step": True,
+                   "l2": "inputs larger than L2 (targets %.1f GB)" % (16 * total / 1e9),
+                   "parallelism": "replicas x%d (independent instances, no collective)" % world},
+        "roofline": roof,
+        "stages_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(stage_sum.items())},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d targets of the same instances, quadrature rebuilt + "
+                                   "direct O(NM) FP64 sum (eq. faq), %.1f s" % (n_s, t_s)},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(16 * total),
+                "d2h_bytes_per_step": int(8 * total)},
+        "gpu_launches": p.info()["launches_per_eval"] * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_randstar_reference(args, rank, world, batch):
+    from oracle import build as obuild
+    obuild.build()
+    if rank != 0:
+        return
+    if batch:
+        problems, counts = W.random_star_batch()
+        metric, name, streams = BATCH_METRIC, "randstar_batch32", [100 + i for i in range(32)]
+    else:
+        cfg = W.random_star()
+        problems = [{"families": cfg["families"], "lam": cfg["lam"], "z": cfg["z"]}]
+        counts, metric, name, streams = [100_000_000], R1000_METRIC, "randstar20_F1000", [1]
+    sample = []
+    for i, (m, st) in enumerate(zip(counts, streams)):
+        x, y = W.square_targets(min(m, 4096), 1.2, 5, st)
+        sample.append((x[: 4 if batch else 100], y[: 4 if batch else 100]))
+    vals = []
+    for _ in range(max(1, args.steps)):
+        rate, cores, n_s, t_s = _oracle_rate_t3(problems, sample, 8.0)
+        vals.append(rate)
+    v = statistics.median(vals)
+    total = sum(counts)
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name, "targets": total},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d targets, quadrature rebuilt + direct O(NM) FP64 sum, "
+                                       "%.1f s per step" % (n_s, t_s)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="star5_F100", choices=["star5_F100", "starshade_sweep"])
+    ap.add_argument("--workload", default="star5_F100",
+                    choices=["star5_F100", "starshade_sweep", "randstar_F1000", "randstar_batch32"])
     ap.add_argument("--lambdas", type=int, default=64,
                     help="starshade_sweep only: wavelengths per sweep (64 is the benchmark; "
                          "fewer for small profiling captures)")
@@ -510,14 +706,20 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        (run_sweep_reference if sweep else run_reference)(args, rank, world)
+        if args.workload in ("randstar_F1000", "randstar_batch32"):
+            run_randstar_reference(args, rank, world, args.workload == "randstar_batch32")
+        else:
+            (run_sweep_reference if sweep else run_reference)(args, rank, world)
         return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    (run_sweep if sweep else run_ours)(args, rank, world, local_rank)
+    if args.workload in ("randstar_F1000", "randstar_batch32"):
+        run_randstar(args, rank, world, local_rank, args.workload == "randstar_batch32")
+    else:
+        (run_sweep if sweep else run_ours)(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

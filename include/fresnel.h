@@ -149,6 +149,14 @@ typedef struct {
      * above ~13,600 in FP32, ~6,800 in FP64).  Batched plans and profile
      * gradients need single-pass lengths. */
     int fft_split_above;
+    /* 1: measure before committing to a configuration.  FP64 with automatic
+     * sigma / width: plans with sigma = 5/4 and 2 are built and timed on the
+     * device (type 1: an evaluation of the grid; type 3: 2^20 targets spread
+     * over the box) and the faster is kept.  FP32 type 3 with t3_binning = 0:
+     * binned and direct interpolation are timed the same way and the faster
+     * is fixed for the plan.  Plan time grows accordingly; results stay
+     * within tol either way.  Not applied to scattered-target batches. */
+    int autotune;
 } fresnel_opts;
 
 /* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,

@@ -1247,6 +1247,8 @@ fresnel_status plan_scattered_batch(const fresnel_problem* problems, int n, doub
                                     const fresnel_opts* opts, void* stream,
                                     fresnel_plan_t* out_plan);
 fresnel_status read_batch_status(Plan* p);
+fresnel_status plan_autotuned(const fresnel_problem* problems, int n, double tol,
+                              const fresnel_opts* opts, void* stream, fresnel_plan_t* out_plan);
 }  // namespace
 
 extern "C" {
@@ -1312,6 +1314,8 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
     FRES_CK(cudaGetDevice(&dev));
     if (opts->target_kind == FRESNEL_SCATTERED && n_problems > 1)
         return plan_scattered_batch(problems, n_problems, tol, opts, cuda_stream, out_plan);
+    if (opts->autotune)
+        return plan_autotuned(problems, n_problems, tol, opts, cuda_stream, out_plan);
     Plan* p = new Plan();
     p->prec = opts->precision;
     p->output = opts->output;
@@ -1674,3 +1678,138 @@ fresnel_status fresnel_eval_many_scattered(fresnel_plan_t plan, const double* d_
 }
 
 }  // extern "C"
+
+namespace {
+
+// Device time (ms) of one evaluation of p, averaged over three after one
+// warm-up; type 3 on `targets` (M pairs), type 1 on the plan's grid.
+fresnel_status time_eval(Plan* p, const double* targets, long long M, void* out, float* ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    FRES_CK(cudaEventCreate(&a));
+    FRES_CK(cudaEventCreate(&b));
+    fresnel_status st = FRESNEL_OK;
+    auto one = [&]() {
+        return p->prec == FRESNEL_FP64 ? eval_impl<double>(p, targets, M, out)
+                                       : eval_impl<float>(p, targets, M, out);
+    };
+    st = one();
+    if (st == FRESNEL_OK) {
+        cudaEventRecord(a, p->st);
+        for (int i = 0; i < 3 && st == FRESNEL_OK; ++i) st = one();
+        cudaEventRecord(b, p->st);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(ms, a, b);
+        *ms /= 3.0f;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+fresnel_status plan_autotuned(const fresnel_problem* problems, int n, double tol,
+                              const fresnel_opts* opts, void* stream, fresnel_plan_t* out_plan) {
+    fresnel_opts o = *opts;
+    o.autotune = 0;
+    std::vector<double> sigmas{opts->sigma};
+    if (opts->precision == FRESNEL_FP64 && opts->sigma == 0 && opts->kernel_w == 0)
+        sigmas = {1.25, 2.0};
+    const bool scattered = opts->target_kind == FRESNEL_SCATTERED;
+    const bool tune_bins = scattered && opts->precision == FRESNEL_FP32_FAST && opts->t3_binning == 0;
+    // synthetic targets for type 3: 2^20 points spread evenly over the box
+    const long long MT = scattered ? (1LL << 20) : 0;
+    double* d_t = nullptr;
+    void* d_out = nullptr;
+    long long out_elems = 0;
+    Plan* best = nullptr;
+    float best_ms = 0.0f;
+    int best_bins = opts->t3_binning;
+    fresnel_status last = FRESNEL_OK;
+    std::string last_msg;
+    for (double sg : sigmas) {
+        o.sigma = sg;
+        fresnel_plan_t h = nullptr;
+        fresnel_status st = fresnel_plan_many(problems, n, tol, &o, stream, &h);
+        if (st != FRESNEL_OK) {
+            last = st;
+            last_msg = g_last_error;
+            continue;
+        }
+        Plan* q = reinterpret_cast<Plan*>(h);
+        const long long need = scattered ? MT : (long long)q->n1 * q->n2 * q->B;
+        if (need > out_elems) {
+            if (d_out) cudaFree(d_out);
+            d_out = nullptr;
+            if (cudaMalloc(&d_out, 16 * (size_t)need) != cudaSuccess) {
+                cudaGetLastError();
+                free_plan(q);
+                last = fres_fail(FRESNEL_ERR_OOM, "autotune scratch");
+                last_msg = g_last_error;
+                break;
+            }
+            out_elems = need;
+        }
+        if (scattered && !d_t) {
+            std::vector<double> ht(2 * MT);
+            const double* bx = opts->box;
+            const int side = 1024;   // 1024 x 1024 lattice, offset by a golden-ratio shift
+            for (long long k = 0; k < MT; ++k) {
+                const double u = ((k % side) + 0.618033988749895) / side;
+                const double v = ((k / side) + 0.381966011250105) / side;
+                ht[2 * k] = bx[0] + (bx[1] - bx[0]) * u;
+                ht[2 * k + 1] = bx[2] + (bx[3] - bx[2]) * v;
+            }
+            if (cudaMalloc((void**)&d_t, sizeof(double) * 2 * MT) != cudaSuccess) {
+                cudaGetLastError();
+                free_plan(q);
+                last = fres_fail(FRESNEL_ERR_OOM, "autotune targets");
+                last_msg = g_last_error;
+                break;
+            }
+            cudaMemcpy(d_t, ht.data(), sizeof(double) * 2 * MT, cudaMemcpyHostToDevice);
+        }
+        int bins = opts->t3_binning;
+        float ms = 0.0f;
+        if (tune_bins) {
+            float m1 = 0.0f, m2 = 0.0f;
+            q->opts.t3_binning = -1;
+            st = time_eval(q, d_t, MT, d_out, &m1);
+            if (st == FRESNEL_OK) {
+                q->opts.t3_binning = 1;
+                st = time_eval(q, d_t, MT, d_out, &m2);
+            }
+            bins = m2 < m1 ? 1 : -1;
+            ms = std::min(m1, m2);
+            q->opts.t3_binning = bins;
+        } else {
+            st = time_eval(q, d_t, MT, d_out, &ms);
+        }
+        cudaMemsetAsync(q->status, 0, sizeof(unsigned), q->st);   // synthetic run: no report
+        if (st != FRESNEL_OK) {
+            last = st;
+            last_msg = g_last_error;
+            free_plan(q);
+            continue;
+        }
+        if (!best || ms < best_ms) {
+            if (best) free_plan(best);
+            best = q;
+            best_ms = ms;
+            best_bins = bins;
+        } else {
+            free_plan(q);
+        }
+    }
+    if (d_t) cudaFree(d_t);
+    if (d_out) cudaFree(d_out);
+    if (!best) {
+        g_last_error = last_msg;
+        return last != FRESNEL_OK ? last : fres_fail(FRESNEL_ERR_ARG, "autotune found no plan");
+    }
+    best->opts.autotune = 1;
+    best->opts.t3_binning = best_bins;
+    cudaStreamSynchronize(best->st);
+    *out_plan = reinterpret_cast<fresnel_plan_t>(best);
+    return FRESNEL_OK;
+}
+
+}  // namespace

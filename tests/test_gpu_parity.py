@@ -261,3 +261,26 @@ def test_star_F100_t3_full_size_sampled():
     idx = W.rng(2, 8).choice(len(xi), 400, replace=False)
     ref = oracle.field(fam, cfg["lam"], 1.0, xi[idx], eta[idx])
     assert rel_l2(u[idx], ref) <= 1e-6
+
+
+# ------------------------------------------------------------------ autotuned plans
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotuned_plans_match_oracle(prec):
+    """autotune = 1 times candidate configurations on the device (sigma 5/4 or
+    2 in FP64; binned or direct interpolation for FP32 type 3) and keeps the
+    faster; the result must meet the same bar."""
+    tol, bar = BARS[prec]
+    cfg = W.disc()
+    fam, g = cfg["families"], cfg["grid"]
+    xi, eta = oracle.grid_targets(g["n1"], g["n2"], g["h"])
+    p = plan(fam, cfg["lam"], cfg["z"], tol, precision=prec, grid=g, autotune=True)
+    assert p.info()["sigma"] in (1.25, 2.0)
+    ref = oracle.field(fam, cfg["lam"], cfg["z"], xi, eta).reshape(g["n2"], g["n1"])
+    assert rel_l2(p.eval().cpu().numpy(), ref) <= bar
+    fam3 = [W.fourier_family(W.STAR_PARAMS, 32, 16, 48)]
+    x3, y3 = W.disc_targets(40000, 1.5, 12)
+    t = torch.tensor(np.stack([x3, y3], 1), dtype=torch.float64, device="cuda")
+    p3 = plan(fam3, 0.03, 1.0, tol, precision=prec, box=(-1.5, 1.5, -1.5, 1.5), autotune=True)
+    u3 = p3.eval(t).cpu().numpy()
+    idx = np.arange(0, 40000, 97)
+    assert rel_l2(u3[idx], oracle.field(fam3, 0.03, 1.0, x3[idx], y3[idx])) <= bar
