@@ -141,6 +141,10 @@ __global__ void k_boundary_fourier(FamilyDev f, ChirpParams cp) {
     double V = what * (dr * st + r * ct);
     f.bx[i] = X;
     f.by[i] = Y;
+    if (f.bw) {
+        f.bw[i] = W;
+        f.bv[i] = V;
+    }
     f.bc[i] = X * V - Y * W;
     store_spoke(f, cp, i, X, Y, X * V - Y * W);
 }
@@ -154,6 +158,10 @@ __global__ void k_boundary_line(FamilyDev f, ChirpParams cp) {
     double W = f.params[2 * n + i], V = f.params[3 * n + i];
     f.bx[i] = X;
     f.by[i] = Y;
+    if (f.bw) {
+        f.bw[i] = W;
+        f.bv[i] = V;
+    }
     f.bc[i] = X * V - Y * W;
     store_spoke(f, cp, i, X, Y, X * V - Y * W);
 }
@@ -694,16 +702,31 @@ k_scan_problems(int ntiles, int* __restrict__ counts, int* __restrict__ cursor,
             ++ns;
         }
     }
-    s_rec[t] = rsum;
-    s_sc[t] = sc;
-    s_ns[t] = ns;
-    s_st[t] = stl;
-    __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scans
-        long long a = 0, bb = 0, c = 0, d = 0;
-        if (t >= off) { a = s_rec[t - off]; bb = s_sc[t - off]; c = s_ns[t - off]; d = s_st[t - off]; }
+    {   // inclusive block scans of the four sums: warp shuffles, then warp totals
+        __shared__ long long w_tot[4][32];
+        const int lane = t & 31, wid = t >> 5, nwarp = (nt + 31) >> 5;
+        auto wscan = [&](long long v) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            return v;
+        };
+        long long inc[4] = {wscan(rsum), wscan(sc), wscan(ns), wscan(stl)};
+        if (lane == 31)
+            for (int q = 0; q < 4; ++q) w_tot[q][wid] = inc[q];
         __syncthreads();
-        s_rec[t] += a; s_sc[t] += bb; s_ns[t] += c; s_st[t] += d;
+        if (wid == 0)
+            for (int q = 0; q < 4; ++q) {
+                const long long v = lane < nwarp ? w_tot[q][lane] : 0;
+                w_tot[q][lane] = wscan(v) - v;
+            }
+        __syncthreads();
+        s_rec[t] = inc[0] + w_tot[0][wid];
+        s_sc[t] = inc[1] + w_tot[1][wid];
+        s_ns[t] = inc[2] + w_tot[2][wid];
+        s_st[t] = inc[3] + w_tot[3][wid];
         __syncthreads();
     }
     const long long TS = s_sc[nt - 1], NS = s_ns[nt - 1], TST = s_st[nt - 1], RT = s_rec[nt - 1];
