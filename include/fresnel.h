@@ -263,7 +263,19 @@ fresnel_status fresnel_eval(fresnel_plan_t plan, const double* d_targets, long l
 fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, long long M,
                                  void* h_out);
 
-/* Synchronises the plan's stream and returns (then clears) the device status
+/*
+ * Non-singular line integral (Appendix, eq. nsli) on the device: u at M
+ * scattered targets (DEVICE (xi, eta) FP64 pairs) from the boundary line
+ * rules of the plan's families alone, O(n M) in FP64, written to d_out
+ * (DEVICE, M complex128, aperture or occulter as the plan's output) whatever
+ * the plan's precision.  An independent reference for the areal path, valid
+ * up to and on the boundary (the summand is 0 where r = 0).  One-problem
+ * plans whose families are all FRESNEL_FAMILY_FOURIER or LINE_RULE.
+ */
+fresnel_status fresnel_nsli(fresnel_plan_t plan, const double* d_targets, long long M,
+                            void* d_out);
+
+/* Synchronises the plan's stream and returns (then clears) the device status/* Synchronises the plan's stream and returns (then clears) the device status
  * word: FRESNEL_OK, FRESNEL_ERR_DEVICE or FRESNEL_ERR_TIMEOUT. */
 fresnel_status fresnel_check(fresnel_plan_t plan);
 

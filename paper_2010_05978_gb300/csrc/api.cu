@@ -659,6 +659,8 @@ fresnel_status setup_dilation_family(Plan* p, FamilyDev& f, const double* hparam
     FRES_TRY(dalloc(p, (void**)&f.bx, sizeof(double) * nb));
     FRES_TRY(dalloc(p, (void**)&f.by, sizeof(double) * nb));
     FRES_TRY(dalloc(p, (void**)&f.bc, sizeof(double) * nb));
+    FRES_TRY(dalloc(p, (void**)&f.bw, sizeof(double) * nb));
+    FRES_TRY(dalloc(p, (void**)&f.bv, sizeof(double) * nb));
     if (!dbl) {   // double-float radial rule for the FP32 spoke form
         std::vector<float> adf(2 * f.m), awf(f.m);
         for (int l = 0; l < f.m; ++l) {
@@ -1420,6 +1422,27 @@ fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, do
                                                : grad_profile_impl<float>(p, d_gamma, d_grad);
     if (s != FRESNEL_OK) return s;
     if (p->opts.sync_status) return read_status(p);
+    return FRESNEL_OK;
+}
+
+fresnel_status fresnel_nsli(fresnel_plan_t plan, const double* d_targets, long long M,
+                            void* d_out) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (!p->subs.empty() || p->B != 1)
+        return fres_fail(FRESNEL_ERR_ARG, "fresnel_nsli takes a one-problem plan");
+    for (const FamilyDev& f : p->fams)
+        if (f.kind != FRESNEL_FAMILY_FOURIER && f.kind != FRESNEL_FAMILY_LINE_RULE)
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED,
+                             "the line integral needs FOURIER or LINE_RULE families only");
+    if (M < 0) return fres_fail(FRESNEL_ERR_ARG, "M must be >= 0");
+    if (M > 0 && (!d_targets || !d_out)) return fres_fail(FRESNEL_ERR_ARG, "d_targets or d_out is NULL");
+    launch_nsli(p->fams.data(), (int)p->fams.size(), p->lz, d_targets, M,
+                p->output == FRESNEL_OCCULTER, (double2*)d_out, p->st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("line integral: ") + cudaGetErrorString(e));
+    if (p->opts.sync_status) FRES_CK(cudaStreamSynchronize(p->st));
     return FRESNEL_OK;
 }
 

@@ -86,6 +86,8 @@ struct FamilyDev {
     double* bx;            // boundary X - cx   (n_bdry)
     double* by;            // boundary Y - cy
     double* bc;            // (X-cx) V - (Y-cy) W
+    double* bw;            // the line rule's W, V (kept for the line integral, eq. nsli)
+    double* bv;
     double* gl_p_t;        // p-point Gauss-Legendre nodes on (0,1)
     double* gl_p_w;
     double* gl_m_a;        // m-point Gauss-Legendre nodes alpha_l on (0,1)
@@ -246,6 +248,11 @@ void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_m
                    int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
                    int* work, int nf1, int nf2, int ntx, int ntiles, const KernelShape& ks,
                    int nblocks, cudaStream_t st);
+
+// k_nsli.cu: non-singular line integral (Appendix, eq. nsli) over the
+// boundary rules of the given families, FP64, one thread per target
+void launch_nsli(const FamilyDev* fams_host, int nfam, double lz, const double* targets,
+                 long long M, int occulter, double2* out, cudaStream_t st);
 
 // k_adjoint.cu (derivatives of type-1 plans with respect to petal profiles)
 template <typename T>

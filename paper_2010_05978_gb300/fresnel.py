@@ -66,7 +66,7 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_plan_many", "fresnel_eval",
            "fresnel_eval_many", "fresnel_eval_many_scattered", "fresnel_eval_host",
-           "fresnel_grad_profile",
+           "fresnel_grad_profile", "fresnel_nsli",
            "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
            "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread",
            "fresnel_spread_noalloc"]
@@ -100,6 +100,8 @@ def load_library(path=LIB_PATH):
     lib.fresnel_eval_many_scattered.restype = ctypes.c_int
     lib.fresnel_grad_profile.argtypes = [vp, vp, vp]
     lib.fresnel_grad_profile.restype = ctypes.c_int
+    lib.fresnel_nsli.argtypes = [vp, vp, ll, vp]
+    lib.fresnel_nsli.restype = ctypes.c_int
     lib.fresnel_eval_host.argtypes = [vp, vp, ll, vp]
     lib.fresnel_eval_host.restype = ctypes.c_int
     lib.fresnel_check.argtypes = [vp]
@@ -373,6 +375,17 @@ class Plan(_PlanHandle):
         if out is None:
             out = torch.empty(shape, dtype=self.cdtype, device="cuda")
         _check(load_library().fresnel_eval(self.handle, tptr, M, out.data_ptr() if M > 0 else None))
+        return out
+
+    def nsli(self, targets):
+        """u at scattered targets by the line integral of eq. nsli (FP64,
+        complex128 CUDA tensor), from the plan's boundary rules."""
+        torch = self._torch
+        assert targets.dtype == torch.float64 and targets.is_cuda and targets.is_contiguous()
+        M = targets.shape[0]
+        out = torch.empty((M,), dtype=torch.complex128, device="cuda")
+        _check(load_library().fresnel_nsli(self.handle, targets.data_ptr() if M else None, M,
+                                           out.data_ptr() if M else None))
         return out
 
     def eval_host(self, targets=None, out=None):

@@ -284,3 +284,36 @@ def test_autotuned_plans_match_oracle(prec):
     u3 = p3.eval(t).cpu().numpy()
     idx = np.arange(0, 40000, 97)
     assert rel_l2(u3[idx], oracle.field(fam3, 0.03, 1.0, x3[idx], y3[idx])) <= bar
+
+
+# ------------------------------------------------------------------ line integral on the device
+def test_nsli_matches_oracle_line_integral():
+    """GPU eq. nsli against the oracle's, on the same boundary rule, including a
+    target exactly on a boundary node (r = 0) and targets near the boundary."""
+    fam = W.fourier_family(W.STAR_PARAMS, 32, 16, 8, cx=0.1, cy=-0.05)
+    X, Y, Wt, V, _, _ = Q.family_line_rule(fam)
+    xi, eta = W.disc_targets(2000, 1.6, 13)
+    xi[0], eta[0] = X[17], Y[17]
+    xi[1], eta[1] = 1.0001 * X[40], 1.0001 * Y[40]
+    lz = 0.04
+    from oracle import direct
+    ref = direct.nsli(X, Y, Wt, V, xi, eta, lz)
+    p = plan([fam], lz, 1.0, 1e-12, precision="fp64", box=(-1.6, 1.6, -1.6, 1.6))
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    u = p.nsli(t).cpu().numpy()
+    assert np.max(np.abs(u - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_nsli_agrees_with_areal_path():
+    """Converged disc (F = 10, m = 64): the areal NUFFT path and the device line
+    integral agree, and both match the Hankel closed form."""
+    fam = [W.fourier_family([1.0], 64, 16, 64)]
+    rho = np.linspace(0.0, 1.45, 40)
+    xi, eta = rho * np.cos(0.7), rho * np.sin(0.7)
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    p = plan(fam, 0.1, 1.0, 1e-12, precision="fp64", box=(-1.5, 1.5, -1.5, 1.5))
+    ua = p.eval(t).cpu().numpy()
+    un = p.nsli(t).cpu().numpy()
+    ref = oracle.closed_forms.disc_off_axis(1.0, 0.1, rho)
+    assert np.max(np.abs(ua - un)) < 1e-9
+    assert np.max(np.abs(un - ref)) < 1e-9
