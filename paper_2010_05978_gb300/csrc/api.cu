@@ -255,7 +255,7 @@ void fit_horner(int w, double beta, HornerTab* h) {
     double prev_err = 1e300;
     HornerTab best{};
     best.deg = -1;
-    for (int d = 4; d <= kMaxHornerDeg; ++d) {
+    for (int d = 4; d <= kHornerDeg; ++d) {
         const int n = d + 1;
         HornerTab t{};
         t.deg = d;
@@ -424,21 +424,22 @@ void run_rows(Plan* p, RowPassArgs ra) {
     c1.out_len = d.fa;
     c1.twiddle = d.twa;
     launch_fft_cols<T>(d.fpa, c1, p->st);
-    RowPassArgs r2{};
-    r2.mode = kFftStep2;
-    r2.in = p->fscratch;
-    r2.in_stride = d.fb;
-    r2.nrows = ra.nrows * d.fa;
-    r2.in_len = d.fb;
-    r2.out = ra.out;
-    r2.out_stride = ra.out_stride;
-    r2.out_len = ra.out_len;
-    r2.fa = d.fa;
-    r2.fb = d.fb;
-    r2.fN = d.n;
-    r2.twN = d.tw;
-    r2.twiddle = d.twb;
-    launch_fft_rows<T>(d.fpb, r2, p->st);
+    // B-point transforms: groups of adjacent scratch rows (consecutive k1)
+    // per block, so short transforms still fill the GPU
+    ColPassArgs c2{};
+    c2.mode = kFftRowStep2;
+    c2.in = p->fscratch;
+    c2.ncols = d.fa;
+    c2.nouter = ra.nrows;
+    c2.out = ra.out;
+    c2.out_stride = ra.out_stride;
+    c2.out_len = ra.out_len;
+    c2.fa = d.fa;
+    c2.fb = d.fb;
+    c2.fN = d.n;
+    c2.twN = d.tw;
+    c2.twiddle = d.twb;
+    launch_fft_cols<T>(d.fpb, c2, p->st);
     p->launches += 2;
 }
 
@@ -1143,7 +1144,9 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
             a[j] = (j == 0 ? 1.0 : 2.0) * acc / ns;
         }
         int nk = ns;
-        while (nk > 1 && std::fabs(a[nk - 1]) < 1e-18 * std::fabs(a[0])) --nk;
+        // terms below the arithmetic's resolution are dropped (FP32: 1e-10)
+        const double cut = dbl ? 1e-18 : 1e-10;
+        while (nk > 1 && std::fabs(a[nk - 1]) < cut * std::fabs(a[0])) --nk;
         FRES_CK(cudaMemcpyAsync(d_s, a.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, p->st));
         FRES_CK(cudaStreamSynchronize(p->st));
         p->cheb = d_s;

@@ -131,11 +131,14 @@ struct ChirpParams {
 // Piecewise-polynomial form of the spreading kernel for FP32: the value at
 // cell a of a node with fractional offset f is c[a][0] + c[a][1] t + ... with
 // t = 2 f - 1 (fitted once per plan on the Chebyshev points of each unit
-// piece).  deg < 0 means "evaluate exp/sqrt directly".  Passed by value, so
-// it lives in the kernel-parameter constant bank (uniform access).
-constexpr int kMaxHornerDeg = 19;
+// piece).  Every piece is evaluated to the fixed degree kHornerDeg (the fit's
+// own degree, at most kHornerDeg, zero-padded), so the fully unrolled Horner
+// chain takes its coefficients as constant operands.  deg < 0 means
+// "evaluate exp/sqrt directly".  Passed by value, so it lives in the
+// kernel-parameter constant bank (uniform access).
+constexpr int kHornerDeg = 10;
 struct HornerTab {
-    float c[kMaxW][kMaxHornerDeg + 1];
+    float c[kMaxW][kHornerDeg + 1];
     int deg;
 };
 
@@ -151,8 +154,9 @@ __device__ __forceinline__ void horner_eval(const HornerTab& h, float f, float* 
     const float t = 2.0f * f - 1.0f;
 #pragma unroll
     for (int a = 0; a < W; ++a) {
-        float acc = h.c[a][h.deg];
-        for (int k = h.deg - 1; k >= 0; --k) acc = fmaf(acc, t, h.c[a][k]);
+        float acc = h.c[a][kHornerDeg];
+#pragma unroll
+        for (int k = kHornerDeg - 1; k >= 0; --k) acc = fmaf(acc, t, h.c[a][k]);
         out[a] = acc;
     }
 }
@@ -279,11 +283,6 @@ struct RowPassArgs {
     // are skipped: neither read nor written.  NULL: every row is live.
     const int* live;
     int batch_rows, nty;
-    // four-step second half (mode kFftStep2, see ColPassArgs): row r = (l, k1),
-    // l = r / fa, of a scratch holding B-point inputs; twN = w_N table
-    int mode;
-    int fa, fb, fN;
-    const void* twN;
 };
 struct ColPassArgs {
     const void* in; void* out;
@@ -312,14 +311,17 @@ struct ColPassArgs {
     //    outer index per b; output scratch[(k1 * fb + b) * ncols + c];
     //  kFftColStep2: B-point DFTs over b of scratch (outer index k1) with the
     //    twiddle w_N^(b k1); output row out_slot(k1 + fa * k2) (+ epilogue).
+    //  kFftRowStep2: B-point DFTs of scratch rows (l, k1) (outer index l,
+    //    "columns" k1 < fa, elements b at stride 1) with the twiddle
+    //    w_N^(b k1); output grid row l at out_stride, slot out_slot(k1 + fa k2).
     int mode;
     int fa, fb, fN, nouter;
-    long long in_stride;
+    long long in_stride, out_stride;
     const void* twN;
     const void* deconv_col;
     const void* deconv_row;
 };
-enum { kFftPlain = 0, kFftRowStep1 = 1, kFftColStep1 = 2, kFftColStep2 = 3, kFftStep2 = 4 };
+enum { kFftPlain = 0, kFftRowStep1 = 1, kFftColStep1 = 2, kFftColStep2 = 3, kFftRowStep2 = 4 };
 template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st);
 template <typename T>

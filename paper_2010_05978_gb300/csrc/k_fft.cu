@@ -260,7 +260,7 @@ __device__ __forceinline__ int out_slot(int k, int len, int n) {
 
 
 
-template <typename T, int MODE>
+template <typename T>
 __global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm)
 k_fft_rows(FftPlan fp, RowPassArgs a) {
     using C = cx_t<T>;
@@ -272,41 +272,27 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
     const T* dcol = (const T*)a.deconv_col;
     // rows of dead tile rows are zero in and out of the transform: skipped
     auto next_live = [&](int r) {
-        if (MODE == kFftPlain && a.live)
+        if (a.live)
             while (r < a.nrows && !a.live[(r / a.batch_rows) * a.nty + (r % a.batch_rows) / kTile])
                 r += gridDim.x;
         return r;
     };
     for (int row = next_live(blockIdx.x); row < a.nrows; row = next_live(row + gridDim.x)) {
         const C* in = (const C*)a.in + (long long)row * a.in_stride;
-        if constexpr (MODE == kFftStep2) {
-            // row = (l, k1): B-point DFT of scratch row with twiddle w_N^(b k1),
-            // output k = k1 + fa k2 into grid row l
-            const int l = row / a.fa, k1 = row - l * a.fa;
-            const C* twN = (const C*)a.twN;
-            C* out = (C*)a.out + (long long)l * a.out_stride;
-            auto load = [&](int b) { return Ops<T>::mul(in[b], __ldg(&twN[b * k1])); };
-            auto store = [&](int k2, C v) {
-                const int kp = out_slot(k1 + a.fa * k2, a.out_len, a.fN);
-                if (kp >= 0) out[kp] = v;
-            };
-            fft_fused<T, 1>(S, S2, fp, tw, load, store);
-        } else {
-            C* out = (C*)a.out + (long long)row * a.out_stride;
-            const T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
-            auto load = [&](int e) {
-                const int i = in_src(e, a.in_len, n, a.centered_in);
-                if (i < 0) return Ops<T>::mk(0, 0);
-                C v = in[i];
-                if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
-                return v;
-            };
-            auto store = [&](int k, C v) {
-                const int kp = out_slot(k, a.out_len, n);
-                if (kp >= 0) out[kp] = v;
-            };
-            fft_fused<T, 1>(S, S2, fp, tw, load, store);
-        }
+        C* out = (C*)a.out + (long long)row * a.out_stride;
+        const T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
+        auto load = [&](int e) {
+            const int i = in_src(e, a.in_len, n, a.centered_in);
+            if (i < 0) return Ops<T>::mk(0, 0);
+            C v = in[i];
+            if (a.centered_in) v = Ops<T>::scale(v, rowf * (dcol ? dcol[i] : (T)1));
+            return v;
+        };
+        auto store = [&](int k, C v) {
+            const int kp = out_slot(k, a.out_len, n);
+            if (kp >= 0) out[kp] = v;
+        };
+        fft_fused<T, 1>(S, S2, fp, tw, load, store);
     }
 }
 
@@ -395,6 +381,20 @@ k_fft_cols(FftPlan fp, ColPassArgs a) {
                 if (on) out[(long long)k1 * a.fb * a.ncols] = v;
             };
             fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
+        } else if constexpr (MODE == kFftRowStep2) {
+            // transform (l = o, k1 = col): scratch row (o fa + k1), b contiguous
+            const C* in = (const C*)a.in + ((long long)o * a.fa + col) * a.fb;
+            C* out = (C*)a.out + (long long)o * a.out_stride;
+            const C* twN = (const C*)a.twN;
+            auto load = [&](int b) {
+                if (!on) return Ops<T>::mk(0, 0);
+                return Ops<T>::mul(in[b], __ldg(&twN[b * col]));
+            };
+            auto store = [&](int k2, C v) {
+                const int kp = out_slot(col + a.fa * k2, a.out_len, a.fN);
+                if (kp >= 0 && on) out[kp] = v;
+            };
+            fft_fused<T, NCOL>(S, S2, fp, tw, load, store);
         } else {   // kFftColStep2: outer index o = k1
             const C* in = (const C*)a.in + (long long)o * a.fb * a.ncols + col;
             C* out = (C*)a.out + col;
@@ -470,15 +470,8 @@ void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st) {
     const int threads = threads_for(fp.n, emax<T>());
     int blocks = a.nrows < 152 * 16 ? a.nrows : 152 * 16;
     if (blocks < 1) blocks = 1;
-    if (a.mode == kFftStep2) {
-        cudaFuncSetAttribute(k_fft_rows<T, kFftStep2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        k_fft_rows<T, kFftStep2><<<blocks, threads, smem, st>>>(fp, a);
-    } else {
-        cudaFuncSetAttribute(k_fft_rows<T, kFftPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        k_fft_rows<T, kFftPlain><<<blocks, threads, smem, st>>>(fp, a);
-    }
+    cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fft_rows<T><<<blocks, threads, smem, st>>>(fp, a);
 }
 
 template <typename T, int MODE>
@@ -513,6 +506,7 @@ void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st) {
         case kFftRowStep1: launch_cols_mode<T, kFftRowStep1>(fp, a, cmax, st); break;
         case kFftColStep1: launch_cols_mode<T, kFftColStep1>(fp, a, cmax, st); break;
         case kFftColStep2: launch_cols_mode<T, kFftColStep2>(fp, a, cmax, st); break;
+        case kFftRowStep2: launch_cols_mode<T, kFftRowStep2>(fp, a, cmax, st); break;
         default: launch_cols_mode<T, kFftPlain>(fp, a, cmax, st); break;
     }
 }

@@ -371,15 +371,22 @@ k_interp_binned(const double* __restrict__ targets, long long M, const float2* _
     __shared__ int s_b;
     for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (float)cheb[i];
     const float inv_tmax = (float)ip.inv_tmax;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_b = atomicAdd(&work[0], 1);
-        __syncthreads();
-        const int b = s_b;
-        if (b >= nbins) break;
+    // bins are claimed kClaim at a time (one atomic per claim; most bins of a
+    // large grid hold no targets and cost only a bounds check)
+    constexpr int kClaim = 16;
+    for (int b = nbins, b_end = nbins;; ++b) {
+        if (b >= b_end) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_b = atomicAdd(&work[0], kClaim);
+            __syncthreads();
+            b = s_b;
+            if (b >= nbins) break;
+            b_end = min(b + kClaim, nbins);
+        }
         const int beg = bin_start[b];
         const int end = b + 1 < nbins ? bin_start[b + 1] : (int)M;
         if (beg >= end) continue;
+        __syncthreads();   // the previous bin's targets are done with the patch
         const int ox = (b % ip.nbin1) * kBin, oy = (b / ip.nbin1) * kBin;
         for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
             const int r = e / P, c = e % P;
