@@ -1143,10 +1143,12 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
             for (int i = 0; i < ns; ++i) acc += hs[i] * std::cos(2.0 * j * kPi * (i + 0.5) / (2.0 * ns));
             a[j] = (j == 0 ? 1.0 : 2.0) * acc / ns;
         }
-        int nk = ns;
-        // terms below the arithmetic's resolution are dropped (FP32: 1e-10)
-        const double cut = dbl ? 1e-18 : 1e-10;
-        while (nk > 1 && std::fabs(a[nk - 1]) < cut * std::fabs(a[0])) --nk;
+        // The coefficients fall geometrically to a roundoff plateau (~1e-16 of
+        // a_0); the series ends at the first term below the arithmetic's
+        // resolution (FP32 1e-10, FP64 1e-15): 9 and 11 terms for w = 8.
+        const double cut = dbl ? 1e-15 : 1e-10;
+        int nk = 1;
+        while (nk < ns && std::fabs(a[nk]) >= cut * std::fabs(a[0])) ++nk;
         FRES_CK(cudaMemcpyAsync(d_s, a.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, p->st));
         FRES_CK(cudaStreamSynchronize(p->st));
         p->cheb = d_s;
