@@ -212,6 +212,96 @@ k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restr
     }
 }
 
+// ------------------------------------------------------------------ cooperative FP32 kernel
+// FP32 direct gathers, cooperatively: a warp takes 32 targets; each lane
+// first does its own target's geometry, phase and kernel values (into shared
+// memory), then LP lanes at a time gather one target's w x w support a row
+// per instruction (LP consecutive cells: one or two cache lines, instead of
+// one line per lane), reduce across the LP lanes and hand the sum to the
+// target's lane for the deconvolution and epilogue.  Random targets make the
+// per-lane pattern L1-bound (one wavefront per lane per load); this one needs
+// a fraction of the wavefronts.
+template <int W>
+__global__ void __launch_bounds__(256)
+k_interp_coop(const double* __restrict__ targets, long long M, const float2* __restrict__ F,
+              InterpParams ip, const double* __restrict__ cheb, int ncheb,
+              float2* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz,
+              float beta) {
+    constexpr int LP = W <= 8 ? 8 : 16;   // lanes per target in the gather
+    constexpr int TG = 32 / LP;           // targets per gather step
+    __shared__ float s_a[kMaxCheb];
+    __shared__ float s_kx[8][32][LP];
+    __shared__ float s_ky[8][32][LP];
+    __shared__ int2 s_s[8][32];
+    for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (float)cheb[i];
+    __syncthreads();
+    const float inv_tmax = (float)ip.inv_tmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int a = lane % LP, sub = lane / LP;
+    for (long long base = ((long long)blockIdx.x * 8 + warp) * 32; base < M;
+         base += (long long)gridDim.x * 8 * 32) {
+        const long long k = base + lane;
+        const bool on = k < M;
+        int s1 = 0, s2 = 0;
+        float f1 = 0.0f, f2 = 0.0f, targ1 = 0.0f, targ2 = 0.0f, phr = 0.0f;
+        if (on) {
+            const double2 t = reinterpret_cast<const double2*>(targets)[k];
+            dflt xi, eta;
+            geom_f32<W>(t, ip, status, xi, eta, s1, s2, f1, f2, targ1, targ2);
+            phr = phase_f32(xi, eta, ip);
+        }
+        float kx[W], ky[W];
+        kernel_values<float, W>(f1, beta, hz, kx);
+        kernel_values<float, W>(f2, beta, hz, ky);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            s_kx[warp][lane][q] = kx[q];
+            s_ky[warp][lane][q] = ky[q];
+        }
+        s_s[warp][lane] = make_int2(s1, s2);
+        __syncwarp();
+        float gr = 0.0f, gi = 0.0f;
+#pragma unroll 1
+        for (int g = 0; g < 32 / TG; ++g) {
+            const int j = g * TG + sub;
+            const int2 sj = s_s[warp][j];
+            float rr = 0.0f, ri = 0.0f;
+            if (a < W) {
+                const float kxa = s_kx[warp][j][a];
+                const float2* col = F + (long long)sj.y * ip.nfft1 + sj.x + a;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const float2 v = __ldg(col + (long long)b * ip.nfft1);
+                    const float wgt = s_ky[warp][j][b] * kxa;
+                    rr = fmaf(wgt, v.x, rr);
+                    ri = fmaf(wgt, v.y, ri);
+                }
+            }
+#pragma unroll
+            for (int o = LP / 2; o > 0; o >>= 1) {
+                rr += __shfl_xor_sync(0xffffffffu, rr, o);
+                ri += __shfl_xor_sync(0xffffffffu, ri, o);
+            }
+            // lanes g TG .. g TG + TG - 1 own this step's targets: sum from lane (l - g TG) LP
+            const int src = ((lane - g * TG) * LP) & 31;
+            const float vr = __shfl_sync(0xffffffffu, rr, src);
+            const float vi = __shfl_sync(0xffffffffu, ri, src);
+            if (lane >= g * TG && lane < (g + 1) * TG) {
+                gr = vr;
+                gi = vi;
+            }
+        }
+        __syncwarp();   // the next 32 targets overwrite the shared tables
+        if (on) {
+            const float dec = kernel_ft_cheb<float>(targ1, s_a, ncheb, inv_tmax) *
+                              kernel_ft_cheb<float>(targ2, s_a, ncheb, inv_tmax);
+            float sn, cs;
+            sincosf(phr, &sn, &cs);
+            out[k] = epilogue<float>(gr, gi, dec, sn, cs, ip);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ binned FP32 path
 template <int W>
 __device__ __forceinline__ int target_bin(const double2 t, const InterpParams& ip) {
@@ -506,6 +596,23 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
                 default: break;   // other widths: generic kernel below
             }
 #undef FRES_BINNED_CASE
+        }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (ks.w <= 12 && ks.horner.deg >= 0) {   // FP32: cooperative gathers
+            const int cb = nblk(M, 256, 152 * 16);
+#define FRES_COOP_CASE(WW)                                                                     \
+    case WW:                                                                                   \
+        k_interp_coop<WW><<<cb, 256, 0, st>>>(targets, M, F, ip, cheb, ncheb, (float2*)out,     \
+                                              status, ks.horner, beta);                        \
+        return;
+            switch (ks.w) {
+                FRES_COOP_CASE(2) FRES_COOP_CASE(3) FRES_COOP_CASE(4) FRES_COOP_CASE(5)
+                FRES_COOP_CASE(6) FRES_COOP_CASE(7) FRES_COOP_CASE(8) FRES_COOP_CASE(9)
+                FRES_COOP_CASE(10) FRES_COOP_CASE(11) FRES_COOP_CASE(12)
+                default: break;
+            }
+#undef FRES_COOP_CASE
         }
     }
     const int blocks = nblk(M, 256, 152 * 32);

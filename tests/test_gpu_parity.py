@@ -317,3 +317,17 @@ def test_nsli_agrees_with_areal_path():
     ref = oracle.closed_forms.disc_off_axis(1.0, 0.1, rho)
     assert np.max(np.abs(ua - un)) < 1e-9
     assert np.max(np.abs(un - ref)) < 1e-9
+
+
+@pytest.mark.parametrize("tol,w", [(1e-7, 9), (1e-3, 5)])
+def test_t3_fp32_kernel_widths(tol, w):
+    """FP32 type 3 at the widths the tolerance picks (w = 9 gathers with 16
+    lanes per target, w = 5 leaves lanes idle) against the oracle."""
+    fam = [W.fourier_family(W.STAR_PARAMS, 32, 16, 48)]
+    xi, eta = W.disc_targets(5000, 1.5, 14)
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    p = plan(fam, 0.04, 1.0, tol, precision="fp32", box=(-1.5, 1.5, -1.5, 1.5))
+    assert p.info()["w"] == w
+    u = p.eval(t).cpu().numpy()
+    ref = oracle.field(fam, 0.04, 1.0, xi, eta)
+    assert rel_l2(u, ref) <= max(tol, 1e-6)
