@@ -58,11 +58,26 @@ __device__ __forceinline__ void kernel_values(T f, T beta, const HornerTab& hz, 
 constexpr int kSpreadWarps = 4;
 constexpr int kTileStride = 40;   // float2 row stride: rows land on disjoint bank halves
 
+// Lane -> support cell map of a staged record: column a = lane % W and rows
+// b0 + p RPW (p < NPASS), b0 = lane / W.  A record's c ky values are staged
+// in the order slot = (b % RPW) NPASS + b / RPW, so each lane's NPASS values
+// are adjacent, in rows of CS slots.  FP32 with NPASS even reads them as
+// 16-byte pairs: CS = 2 mod 4 keeps the pairs aligned and the staging stores
+// at two-way bank conflicts.  Otherwise CS is odd (conflict-free stores).
+template <typename T, int W>
+struct LaneMap {
+    static constexpr int RPW = 32 / W < W ? 32 / W : W;   // rows covered per pass
+    static constexpr int NPASS = (W + RPW - 1) / RPW;
+    static constexpr bool kPairs = std::is_same<T, float>::value && NPASS % 2 == 0;
+    static constexpr int CS = kPairs ? (RPW * NPASS % 4 == 0 ? RPW * NPASS + 2 : RPW * NPASS)
+                                     : (RPW * NPASS) | 1;
+};
+
 template <typename T, int W>
 struct SpreadSmem {
     cx_t<T> tile[kSpreadWarps][kTile * kTileStride];
+    cx_t<T> cky[kSpreadWarps][32][LaneMap<T, W>::CS];
     T kx[kSpreadWarps][32][W + 1];
-    cx_t<T> cky[kSpreadWarps][32][W];
     int dxy[kSpreadWarps][32][2];
     int s_ci;
 };
@@ -96,6 +111,23 @@ __global__ void k_zero_split_tiles(const int* __restrict__ split_tiles,
     }
 }
 
+// A lane's NPASS staged values (adjacent slots): 16-byte loads where the
+// pairs are aligned (FP32, NPASS even: CS and the slot offset b0 NPASS even).
+template <typename T, int NPASS>
+__device__ __forceinline__ void load_pass_values(const cx_t<T>* src, cx_t<T>* v) {
+    if constexpr (std::is_same<T, float>::value && NPASS % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < NPASS; k += 2) {
+            const float4 q = *reinterpret_cast<const float4*>(src + k);
+            v[k] = make_float2(q.x, q.y);
+            v[k + 1] = make_float2(q.z, q.w);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NPASS; ++k) v[k] = src[k];
+    }
+}
+
 // Chunks are taken dynamically from work[0]; the last block to finish puts
 // both counters back to zero for the next launch.
 template <typename T, int W>
@@ -106,6 +138,7 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
     constexpr int TT = kTile * kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, W>& sm = *reinterpret_cast<SpreadSmem<T, W>*>(smem_raw);
+    constexpr int RPW = LaneMap<T, W>::RPW, NPASS = LaneMap<T, W>::NPASS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     cx_t<T>* my = sm.tile[warp];
     const int n_chunks = n_meta[0];
@@ -145,14 +178,11 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
                     cx_t<T> v;
                     v.x = r.cre * kyv[a];
                     v.y = r.cim * kyv[a];
-                    sm.cky[warp][lane][a] = v;
+                    sm.cky[warp][lane][(a % RPW) * NPASS + a / RPW] = v;
                 }
-                sm.kx[warp][lane][W] = (T)0;   // pad: odd widths end on half a pair
+                sm.kx[warp][lane][W] = (T)0;
             }
             __syncwarp();
-            // lane -> support column a = lane % W and rows b0, b0 + RPW, ...
-            constexpr int RPW = 32 / W;             // rows covered per pass
-            constexpr int NPASS = (W + RPW - 1) / RPW;
             const int a = lane % W, b0 = lane / W;
             const bool lane_on = lane < RPW * W;
             for (int j = 0; j < cnt; ++j) {
@@ -160,12 +190,14 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
                 const int x = dx + a;
                 if (lane_on && (unsigned)x < (unsigned)kTile) {
                     const T kxv = sm.kx[warp][j][a];
+                    cx_t<T> cv[NPASS];
+                    load_pass_values<T, NPASS>(&sm.cky[warp][j][b0 * NPASS], cv);
 #pragma unroll
                     for (int k = 0; k < NPASS; ++k) {
                         const int b = b0 + k * RPW;
                         const int y = dy + b;
                         if (b < W && (unsigned)y < (unsigned)kTile) {
-                            const cx_t<T> c = sm.cky[warp][j][b];
+                            const cx_t<T> c = cv[k];
                             cx_t<T>& cell = my[y * kTileStride + x];
                             cx_t<T> o = cell;
                             o.x += c.x * kxv;
