@@ -467,7 +467,10 @@ bool fft_supported(int n, int is_double, int* max_cols) {
 template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st) {
     const size_t smem = 2 * (size_t)padded_len(fp.n) * sizeof(cx_t<T>);
-    const int threads = threads_for(fp.n, emax<T>());
+    // one thread per butterfly of the leading (largest) radix: a radix-16
+    // plan gets n/16 threads, all busy in its radix-16 stages, and more rows
+    // resident per SM
+    const int threads = threads_for(fp.n, fp.radix[0] > emax<T>() ? fp.radix[0] : emax<T>());
     int blocks = a.nrows < 152 * 16 ? a.nrows : 152 * 16;
     if (blocks < 1) blocks = 1;
     cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
