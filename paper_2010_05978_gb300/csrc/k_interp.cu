@@ -230,8 +230,8 @@ k_interp_coop(const double* __restrict__ targets, long long M, const float2* __r
     constexpr int LP = W <= 8 ? 8 : 16;   // lanes per target in the gather
     constexpr int TG = 32 / LP;           // targets per gather step
     __shared__ float s_a[kMaxCheb];
-    __shared__ float s_kx[8][32][LP];
-    __shared__ float s_ky[8][32][LP];
+    __shared__ __align__(16) float s_kx[8][32][LP];
+    __shared__ __align__(16) float s_ky[8][32][LP];
     __shared__ int2 s_s[8][32];
     for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (float)cheb[i];
     __syncthreads();
@@ -253,10 +253,21 @@ k_interp_coop(const double* __restrict__ targets, long long M, const float2* __r
         float kx[W], ky[W];
         kernel_values<float, W>(f1, beta, hz, kx);
         kernel_values<float, W>(f2, beta, hz, ky);
+        // a lane's row of LP slots as 16-byte stores (scalar stores of rows LP
+        // floats apart would be LP/4-way bank conflicted)
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-            s_kx[warp][lane][q] = kx[q];
-            s_ky[warp][lane][q] = ky[q];
+        for (int q = 0; q < LP; q += 4) {
+            float4 vx, vy;
+            vx.x = q < W ? kx[q] : 0.0f;
+            vx.y = q + 1 < W ? kx[q + 1] : 0.0f;
+            vx.z = q + 2 < W ? kx[q + 2] : 0.0f;
+            vx.w = q + 3 < W ? kx[q + 3] : 0.0f;
+            vy.x = q < W ? ky[q] : 0.0f;
+            vy.y = q + 1 < W ? ky[q + 1] : 0.0f;
+            vy.z = q + 2 < W ? ky[q + 2] : 0.0f;
+            vy.w = q + 3 < W ? ky[q + 3] : 0.0f;
+            *reinterpret_cast<float4*>(&s_kx[warp][lane][q]) = vx;
+            *reinterpret_cast<float4*>(&s_ky[warp][lane][q]) = vy;
         }
         s_s[warp][lane] = make_int2(s1, s2);
         __syncwarp();
@@ -458,23 +469,28 @@ k_interp_binned(const double* __restrict__ targets, long long M, const float2* _
     constexpr int PS = P + 1;            // patch row stride (float2)
     __shared__ float2 patch[P * PS];
     __shared__ float s_a[kMaxCheb];
+    // bins are claimed kClaim at a time (one atomic per claim; most bins of a
+    // large grid hold no targets and cost only a bounds check), their starts
+    // loaded together
+    constexpr int kClaim = 16;
     __shared__ int s_b;
+    __shared__ int s_start[kClaim + 1];
     for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (float)cheb[i];
     const float inv_tmax = (float)ip.inv_tmax;
-    // bins are claimed kClaim at a time (one atomic per claim; most bins of a
-    // large grid hold no targets and cost only a bounds check)
-    constexpr int kClaim = 16;
-    for (int b = nbins, b_end = nbins;; ++b) {
+    for (int b = nbins, b0 = nbins, b_end = nbins;; ++b) {
         if (b >= b_end) {
             __syncthreads();
             if (threadIdx.x == 0) s_b = atomicAdd(&work[0], kClaim);
             __syncthreads();
-            b = s_b;
+            b = b0 = s_b;
             if (b >= nbins) break;
             b_end = min(b + kClaim, nbins);
+            if (threadIdx.x <= b_end - b0)
+                s_start[threadIdx.x] = b0 + (int)threadIdx.x < nbins ? bin_start[b0 + threadIdx.x] : (int)M;
+            __syncthreads();
         }
-        const int beg = bin_start[b];
-        const int end = b + 1 < nbins ? bin_start[b + 1] : (int)M;
+        const int beg = s_start[b - b0];
+        const int end = s_start[b - b0 + 1];
         if (beg >= end) continue;
         __syncthreads();   // the previous bin's targets are done with the patch
         const int ox = (b % ip.nbin1) * kBin, oy = (b / ip.nbin1) * kBin;
