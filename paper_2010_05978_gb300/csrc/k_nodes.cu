@@ -236,8 +236,9 @@ __device__ __forceinline__ void finish_df(dflt v1, dflt v2, float cre, float cim
 
 __device__ __forceinline__ void node_df(const FamilyDev& f, const ChirpParams& cp, long long j,
                                         NodeRec<float>* rec, unsigned* status, int key[4]) {
-    const long long i = j / f.m;
-    const int l = (int)(j - i * f.m);
+    // j < 2^30 (plan limit): 32-bit division
+    const unsigned i = (unsigned)j / (unsigned)f.m;
+    const int l = (int)((unsigned)j - i * (unsigned)f.m);
     const float4 sA = reinterpret_cast<const float4*>(f.spoke)[2 * i];
     const float4 sG = reinterpret_cast<const float4*>(f.spoke)[2 * i + 1];
     const float2 a2 = reinterpret_cast<const float2*>(f.adf)[l];
@@ -261,7 +262,8 @@ __device__ __forceinline__ void node_df(const FamilyDev& f, const ChirpParams& c
 __device__ __forceinline__ void node_petal_df(const FamilyDev& f, const ChirpParams& cp,
                                               long long j, NodeRec<float>* rec, unsigned* status,
                                               int key[4]) {
-    const long long k = j / f.n_bdry, q = j - k * f.n_bdry;
+    const unsigned k = (unsigned)j / (unsigned)f.n_bdry;   // j < 2^30
+    const unsigned q = (unsigned)j - k * (unsigned)f.n_bdry;
     const float4 t0 = reinterpret_cast<const float4*>(f.ptab)[2 * q];
     const float4 t1 = reinterpret_cast<const float4*>(f.ptab)[2 * q + 1];
     const dflt u = {t0.x, t0.y}, v = {t0.z, t0.w};
@@ -303,15 +305,16 @@ __device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpPara
         w = f.params[2 * f.n_nodes + j];
     } else if (f.kind == FRESNEL_FAMILY_PETALS) {
         // node (k, i, l) = petal 0's node (i, l) rotated by 2 pi k / Np
-        const long long k = j / f.n_bdry, q = j - k * f.n_bdry;
+        const unsigned k = (unsigned)j / (unsigned)f.n_bdry;   // j < 2^30
+        const unsigned q = (unsigned)j - k * (unsigned)f.n_bdry;
         const double u = f.bx[q], v = f.by[q];
         const double c = f.rot[2 * k], s = f.rot[2 * k + 1];
         x = f.cx + (u * c - v * s);
         y = f.cy + (u * s + v * c);
         w = f.bc[q];
     } else {
-        long long i = j / f.m;
-        int l = (int)(j - i * f.m);
+        const unsigned i = (unsigned)j / (unsigned)f.m;   // j < 2^30
+        const int l = (int)((unsigned)j - i * (unsigned)f.m);
         double a = f.gl_m_a[l];
         x = f.cx + a * f.bx[i];
         y = f.cy + a * f.by[i];
@@ -381,7 +384,7 @@ __device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpPara
 struct FamSmem {
     FamilyDev f;
     ChirpParams cp;
-    int fi;
+    int fi, b0, prob;   // family, its first block, its problem
 };
 
 __device__ __forceinline__ void load_family(const FamTable& ft, FamSmem& sm) {
@@ -393,16 +396,21 @@ __device__ __forceinline__ void load_family(const FamTable& ft, FamSmem& sm) {
             else b = mid - 1;
         }
         sm.fi = a;
+        sm.b0 = ft.blk0[a];
+        sm.prob = ft.fams[a].prob;
     }
     __syncthreads();
+    // both records in one pass (the family's words, then its problem's)
     static_assert(sizeof(FamilyDev) % 4 == 0 && sizeof(ChirpParams) % 4 == 0, "word copy");
+    constexpr int nf = (int)(sizeof(FamilyDev) / 4), nc = (int)(sizeof(ChirpParams) / 4);
     const int* src = reinterpret_cast<const int*>(ft.fams + sm.fi);
+    const int* src2 = reinterpret_cast<const int*>(ft.cps + sm.prob);
     int* dst = reinterpret_cast<int*>(&sm.f);
-    for (int i = threadIdx.x; i < (int)(sizeof(FamilyDev) / 4); i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-    const int* src2 = reinterpret_cast<const int*>(ft.cps + sm.f.prob);
     int* dst2 = reinterpret_cast<int*>(&sm.cp);
-    for (int i = threadIdx.x; i < (int)(sizeof(ChirpParams) / 4); i += blockDim.x) dst2[i] = src2[i];
+    for (int i = threadIdx.x; i < nf + nc; i += blockDim.x) {
+        if (i < nf) dst[i] = src[i];
+        else dst2[i - nf] = src2[i - nf];
+    }
     __syncthreads();
 }
 
@@ -424,7 +432,7 @@ k_nodes(FamTable ft, NodeRec<T>* rec, int* counts, double* dx, double* dy, doubl
     __shared__ __align__(16) FamSmem sm;
     load_family(ft, sm);
     const FamilyDev& f = sm.f;
-    const long long j = (long long)(blockIdx.x - ft.blk0[sm.fi]) * blockDim.x + threadIdx.x;
+    const long long j = (long long)(blockIdx.x - sm.b0) * blockDim.x + threadIdx.x;
     int key[4] = {-1, -1, -1, -1};
     if (j < f.n_nodes) {
         if constexpr (sizeof(T) == 4) {
@@ -451,7 +459,7 @@ k_scatter_fams(FamTable ft, const NodeRec<T>* rec, int* cursor, NodeRec<T>* sort
     __shared__ __align__(16) FamSmem sm;
     load_family(ft, sm);
     const FamilyDev& f = sm.f;
-    const long long j = (long long)(blockIdx.x - ft.blk0[sm.fi]) * blockDim.x + threadIdx.x;
+    const long long j = (long long)(blockIdx.x - sm.b0) * blockDim.x + threadIdx.x;
     int key[4] = {-1, -1, -1, -1};
     NodeRec<T> r;
     if (j < f.n_nodes) {
