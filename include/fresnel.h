@@ -257,8 +257,15 @@ fresnel_status fresnel_eval(fresnel_plan_t plan, const double* d_targets, long l
 /*
  * The same evaluation with HOST buffers: h_targets (M FP64 pairs, ignored for
  * GRID plans) is copied to the device, fresnel_eval runs, and the M complex
- * results are copied back to h_out.  Synchronous.  Pinned host memory makes
- * the copies faster but is not required.
+ * results are copied back to h_out.  The targets' copy runs on a second
+ * stream of the plan, overlapping the stages that do not need the targets
+ * (nodes, sort, spreading, FFT).  With opts.sync_status = 1 the call returns
+ * after the results are in h_out (and reports the device status); with
+ * opts.sync_status = 0 it returns once the work is queued, like fresnel_eval:
+ * h_out is complete, and h_targets may be reused, after the plan's stream
+ * has been synchronised (fresnel_check, or a stream / device
+ * synchronisation).  Pinned host memory makes the copies asynchronous and
+ * fast; pageable memory works, with copies that block the caller.
  */
 fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, long long M,
                                  void* h_out);

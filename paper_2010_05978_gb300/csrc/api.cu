@@ -124,6 +124,13 @@ struct Plan {
     double* stage_tgt = nullptr;
     void* stage_out = nullptr;
     long long stage_cap = 0;
+    // host-buffer evaluations: the targets' copy runs on cst while the node,
+    // sort, spreading and FFT stages run on st; st waits for ev_h2d (wait_tgt)
+    // only before the target-side kernels; cst waits for ev_free (the previous
+    // evaluation done with stage_tgt) before overwriting it
+    cudaStream_t cst = nullptr;
+    cudaEvent_t ev_h2d = nullptr, ev_free = nullptr;
+    cudaEvent_t wait_tgt = nullptr;
     int timing = 0;
     cudaEvent_t ev[kMaxEvents] = {};
     const char* ev_name[kMaxEvents] = {};
@@ -182,8 +189,12 @@ void free_plan(Plan* p) {
     for (cudaStream_t& l : p->lanes)
         if (l) cudaStreamDestroy(l);
     for (cudaEvent_t e : {p->ev_fork, p->ev_in, p->ev_out, p->ev_join[0], p->ev_join[1],
-                          p->ev_join[2], p->ev_join[3]})
+                          p->ev_join[2], p->ev_join[3], p->ev_h2d, p->ev_free})
         if (e) cudaEventDestroy(e);
+    if (p->cst) {
+        cudaStreamSynchronize(p->cst);
+        cudaStreamDestroy(p->cst);
+    }
     for (void* a : p->allocs) cudaFree(a);
     if (p->perm) cudaFree(p->perm);
     for (int i = 0; i < kMaxEvents; ++i)
@@ -561,6 +572,10 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         run_cols<T>(p, ca);
         ev_record(p, "fft_cols");
         if (M > 0) {
+            if (p->wait_tgt) {   // the host targets' copy (fresnel_eval_host)
+                FRES_CK(cudaStreamWaitEvent(p->st, p->wait_tgt, 0));
+                p->wait_tgt = nullptr;
+            }
             T3Sort sort{};
             const T3Sort* sp = nullptr;
             const long long fbytes = (long long)p->nfft1 * p->nfft2 * (long long)sizeof(cx_t<T>);
@@ -1402,14 +1417,27 @@ fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, l
         FRES_TRY(dalloc(p, &p->stage_out, p->csize() * (size_t)cap));
         p->stage_cap = cap;
     }
-    if (p->tkind == FRESNEL_SCATTERED && M > 0)
-        FRES_CK(cudaMemcpyAsync(p->stage_tgt, h_targets, 16 * (size_t)M, cudaMemcpyHostToDevice, p->st));
+    if (p->tkind == FRESNEL_SCATTERED && M > 0) {
+        // the copy overlaps the target-independent stages (nodes to FFT)
+        if (!p->cst) {
+            FRES_CK(cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking));
+            FRES_CK(cudaEventCreateWithFlags(&p->ev_h2d, cudaEventDisableTiming));
+            FRES_CK(cudaEventCreateWithFlags(&p->ev_free, cudaEventDisableTiming));
+        }
+        FRES_CK(cudaStreamWaitEvent(p->cst, p->ev_free, 0));
+        FRES_CK(cudaMemcpyAsync(p->stage_tgt, h_targets, 16 * (size_t)M, cudaMemcpyHostToDevice, p->cst));
+        FRES_CK(cudaEventRecord(p->ev_h2d, p->cst));
+        p->wait_tgt = p->ev_h2d;
+    }
     fresnel_status s = p->prec == FRESNEL_FP64 ? eval_impl<double>(p, p->stage_tgt, M, p->stage_out)
                                                : eval_impl<float>(p, p->stage_tgt, M, p->stage_out);
+    p->wait_tgt = nullptr;
     if (s != FRESNEL_OK) return s;
+    if (p->ev_free) FRES_CK(cudaEventRecord(p->ev_free, p->st));
     if (M > 0)
         FRES_CK(cudaMemcpyAsync(h_out, p->stage_out, p->csize() * (size_t)M, cudaMemcpyDeviceToHost, p->st));
-    return read_status(p);
+    if (p->opts.sync_status) return read_status(p);
+    return FRESNEL_OK;
 }
 
 fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, double* d_grad) {

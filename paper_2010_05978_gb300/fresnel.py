@@ -389,7 +389,10 @@ class Plan(_PlanHandle):
         return out
 
     def eval_host(self, targets=None, out=None):
-        """Same evaluation from HOST numpy arrays (copies inside the call)."""
+        """Same evaluation from HOST numpy arrays (copies inside the call).
+        With sync_status=False the call returns once the work is queued: out
+        is complete after the plan's stream is synchronised (pinned arrays,
+        e.g. numpy views of pin_memory tensors, give asynchronous copies)."""
         npc = np.complex64 if self.precision == "fp32" else np.complex128
         if self.grid is not None:
             M = self.grid["n1"] * self.grid["n2"]

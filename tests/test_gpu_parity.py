@@ -331,3 +331,28 @@ def test_t3_fp32_kernel_widths(tol, w):
     u = p.eval(t).cpu().numpy()
     ref = oracle.field(fam, 0.04, 1.0, xi, eta)
     assert rel_l2(u, ref) <= max(tol, 1e-6)
+
+
+def test_eval_host_async_pinned_back_to_back():
+    """Host-buffer evaluations with sync_status off return once queued: two
+    calls with different pinned target sets, then one check (stream
+    synchronisation).  The second call's target copy must not overwrite the
+    staged targets while the first evaluation still reads them."""
+    fam = [W.fourier_family(W.STAR_PARAMS, 32, 16, 48)]
+    p = plan(fam, 0.05, 1.0, 1e-6, precision="fp32", box=(-1.5, 1.5, -1.5, 1.5),
+             sync_status=False)
+    xa, ya = W.disc_targets(60000, 1.5, 21)
+    xb, yb = W.disc_targets(60000, 1.5, 22)
+    ha = torch.tensor(np.stack([xa, ya], 1), dtype=torch.float64).pin_memory()
+    hb = torch.tensor(np.stack([xb, yb], 1), dtype=torch.float64).pin_memory()
+    oa = torch.empty(60000, dtype=torch.complex64).pin_memory()
+    ob = torch.empty(60000, dtype=torch.complex64).pin_memory()
+    p.eval_host(ha.numpy(), oa.numpy())
+    p.eval_host(hb.numpy(), ob.numpy())
+    p.check()
+    ua = p.eval(ha.cuda()).cpu().numpy()
+    ub = p.eval(hb.cuda()).cpu().numpy()
+    assert rel_l2(oa.numpy(), ua) <= 2e-6 and rel_l2(ob.numpy(), ub) <= 2e-6
+    sel = np.arange(0, 60000, 997)
+    ref = oracle.field(fam, 0.05, 1.0, xb[sel], yb[sel])
+    assert rel_l2(ob.numpy()[sel], ref) <= 1e-6
