@@ -157,10 +157,16 @@ typedef struct {
      * is fixed for the plan.  Plan time grows accordingly; results stay
      * within tol either way.  Not applied to scattered-target batches. */
     int autotune;
+    /* fresnel_nsli only (Appendix, remark r:shadfix): targets whose nearest
+     * boundary node is at least nsli_far away use the classical line
+     * integral eq. li with the winding number of eq. geom rounded to an
+     * integer (exact u_geom, so a shadow's u^oc is not 1 minus a quadrature
+     * of 1); nearer targets use eq. nsli.  0 = eq. nsli everywhere. */
+    double nsli_far;
 } fresnel_opts;
 
 /* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,
- * automatic sigma/width, recompute_nodes = 0, sync_status = 1. */
+ * automatic sigma/width, recompute_nodes = 0, sync_status = 1, nsli_far = 0. */
 void fresnel_default_opts(fresnel_opts* opts);
 
 /* ---------------------------------------------------------------- plan */

@@ -56,6 +56,36 @@ def nsli(X, Y, W, V, xi, eta, lz):
     return re + 1j * im
 
 
+def line_integral_far(X, Y, W, V, xi, eta, lz, far):
+    """Appendix remark r:shadfix: targets whose nearest boundary node is at
+    least `far` away use the classical line integral eq. li,
+        u^ap = -1/(2 pi) sum_i e^{i pi r^2/lz} (r x ds)_i / r^2 + u_geom,
+    with u_geom the winding number of eq. geom, (1/(2 pi)) sum_i (r x ds)_i / r^2,
+    rounded to an integer; the others use eq. nsli.  Returns (u^ap, u^oc),
+    u^oc = (1 - u_geom) + 1/(2 pi) sum_i e^{i pi r^2/lz} (r x ds)_i / r^2 for
+    far targets (no cancellation against 1 in a shadow) and 1 - u^ap
+    otherwise.  Plain numpy, in chunks of targets.
+    """
+    X, Y, W, V = (np.asarray(a, float) for a in (X, Y, W, V))
+    xi, eta = np.atleast_1d(np.asarray(xi, float)), np.atleast_1d(np.asarray(eta, float))
+    uap = nsli(X, Y, W, V, xi, eta, lz)
+    uoc = 1.0 - uap
+    for s in range(0, len(xi), 256):
+        rx = X[None, :] - xi[s:s + 256, None]
+        ry = Y[None, :] - eta[s:s + 256, None]
+        r2 = rx * rx + ry * ry
+        cr = rx * V[None, :] - ry * W[None, :]
+        far_k = r2.min(axis=1) >= far * far
+        if far > 0 and np.any(far_k):
+            k = np.nonzero(far_k)[0]
+            inv = cr[k] / r2[k]
+            ug = np.rint(inv.sum(axis=1) / (2.0 * np.pi))
+            B = (np.exp(1j * np.pi * r2[k] / lz) * inv).sum(axis=1) / (2.0 * np.pi)
+            uap[s + k] = ug - B
+            uoc[s + k] = (1.0 - ug) + B
+    return uap, uoc
+
+
 def sum3(x, y, c, xi, eta, lz):
     """Eq. nufft3 evaluated exactly: v_k = sum_j c_j exp(-2 pi i (xi_k x_j + eta_k y_j)/lz)."""
     lib = _load()

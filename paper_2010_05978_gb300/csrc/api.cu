@@ -1332,6 +1332,8 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
         return fres_fail(FRESNEL_ERR_ARG, "t3_binning must be -1, 0 or 1");
     if (opts->fft_split_above < 0)
         return fres_fail(FRESNEL_ERR_ARG, "fft_split_above must be >= 0");
+    if (!(opts->nsli_far >= 0.0) || !std::isfinite(opts->nsli_far))
+        return fres_fail(FRESNEL_ERR_ARG, "nsli_far must be finite and >= 0");
     int dev = 0;
     FRES_CK(cudaGetDevice(&dev));
     if (opts->target_kind == FRESNEL_SCATTERED && n_problems > 1)
@@ -1471,7 +1473,7 @@ fresnel_status fresnel_nsli(fresnel_plan_t plan, const double* d_targets, long l
     if (M < 0) return fres_fail(FRESNEL_ERR_ARG, "M must be >= 0");
     if (M > 0 && (!d_targets || !d_out)) return fres_fail(FRESNEL_ERR_ARG, "d_targets or d_out is NULL");
     launch_nsli(p->fams.data(), (int)p->fams.size(), p->lz, d_targets, M,
-                p->output == FRESNEL_OCCULTER, (double2*)d_out, p->st);
+                p->output == FRESNEL_OCCULTER, p->opts.nsli_far, (double2*)d_out, p->st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fres_fail(FRESNEL_ERR_CUDA, std::string("line integral: ") + cudaGetErrorString(e));

@@ -256,7 +256,7 @@ void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_m
 // k_nsli.cu: non-singular line integral (Appendix, eq. nsli) over the
 // boundary rules of the given families, FP64, one thread per target
 void launch_nsli(const FamilyDev* fams_host, int nfam, double lz, const double* targets,
-                 long long M, int occulter, double2* out, cudaStream_t st);
+                 long long M, int occulter, double far, double2* out, cudaStream_t st);
 
 // k_adjoint.cu (derivatives of type-1 plans with respect to petal profiles)
 template <typename T>

@@ -6,6 +6,14 @@
 // with the summand 0 where r = 0 (the cross product vanishes there).  An
 // independent O(n M) FP64 evaluation used to check the areal path on the
 // device; accurate up to the boundary itself.
+//
+// Option far > 0 (the Appendix's remark on shadows): a target whose nearest
+// boundary node is at least far away takes the classical line integral
+// eq. li instead,
+//   u^ap = -1/(2 pi) sum_i e^{i pi r^2/lz} (r x ds)_i / r^2 + u_geom,
+// with u_geom the winding number of eq. geom, 1/(2 pi) sum_i (r x ds)_i / r^2,
+// rounded to an integer, and u^oc = (1 - u_geom) + 1/(2 pi) sum_i ... formed
+// without subtracting from 1.
 #include "internal.cuh"
 
 namespace fres {
@@ -27,7 +35,7 @@ __device__ __forceinline__ double reduce_phase(double ph) {
 // tiles of one node per thread.  bnd = (X, Y, W, V) absolute coordinates.
 __global__ void __launch_bounds__(kNsliThreads)
 k_nsli(const double4_32a* __restrict__ bnd, long long n, double lz, const double* __restrict__ targets,
-       long long M, int occulter, double2* __restrict__ out) {
+       long long M, int occulter, double far2, double2* __restrict__ out) {
     __shared__ double4_32a tile[kNsliThreads];
     const double kq = kPi / lz;
     for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < M;
@@ -35,7 +43,9 @@ k_nsli(const double4_32a* __restrict__ bnd, long long n, double lz, const double
         const long long t = t0 + threadIdx.x;
         const bool on = t < M;
         const double xi = on ? targets[2 * t] : 0.0, eta = on ? targets[2 * t + 1] : 0.0;
-        double sr = 0.0, si = 0.0;
+        double sr = 0.0, si = 0.0;            // eq. nsli sum
+        double wsum = 0.0, br = 0.0, bi = 0.0;  // eq. geom and eq. li sums (far > 0)
+        double r2min = INFINITY;
         for (long long i0 = 0; i0 < n; i0 += kNsliThreads) {
             __syncthreads();
             if (i0 + threadIdx.x < n) tile[threadIdx.x] = bnd[i0 + threadIdx.x];
@@ -52,14 +62,28 @@ k_nsli(const double4_32a* __restrict__ bnd, long long n, double lz, const double
                     const double inv = cr / r2;
                     sr += (1.0 - c) * inv;
                     si -= s * inv;
+                    if (far2 > 0.0) {
+                        wsum += inv;
+                        br += c * inv;
+                        bi += s * inv;
+                    }
                 }
+                r2min = fmin(r2min, r2);
             }
         }
         if (on) {
-            double ur = sr / kTwoPi, ui = si / kTwoPi;
-            if (occulter) {
-                ur = 1.0 - ur;
-                ui = -ui;
+            double ur, ui;
+            if (far2 > 0.0 && r2min >= far2) {   // eq. li with the exact winding number
+                const double ug = rint(wsum / kTwoPi);
+                ur = occulter ? (1.0 - ug) + br / kTwoPi : ug - br / kTwoPi;
+                ui = occulter ? bi / kTwoPi : -bi / kTwoPi;
+            } else {
+                ur = sr / kTwoPi;
+                ui = si / kTwoPi;
+                if (occulter) {
+                    ur = 1.0 - ur;
+                    ui = -ui;
+                }
             }
             out[t] = make_double2(ur, ui);
         }
@@ -76,7 +100,7 @@ __global__ void k_nsli_pack(FamilyDev f, double4_32a* __restrict__ dst) {
 }  // namespace
 
 void launch_nsli(const FamilyDev* fams_host, int nfam, double lz, const double* targets,
-                 long long M, int occulter, double2* out, cudaStream_t st) {
+                 long long M, int occulter, double far, double2* out, cudaStream_t st) {
     long long n = 0;
     for (int i = 0; i < nfam; ++i) n += fams_host[i].n_bdry;
     double4_32a* bnd = nullptr;
@@ -91,7 +115,8 @@ void launch_nsli(const FamilyDev* fams_host, int nfam, double lz, const double* 
     }
     if (M > 0) {
         const long long blocks = std::min<long long>((M + kNsliThreads - 1) / kNsliThreads, 152 * 8);
-        k_nsli<<<(int)blocks, kNsliThreads, 0, st>>>(bnd, n, lz, targets, M, occulter, out);
+        k_nsli<<<(int)blocks, kNsliThreads, 0, st>>>(bnd, n, lz, targets, M, occulter, far * far,
+                                                     out);
     }
     cudaFreeAsync(bnd, st);
 }

@@ -53,7 +53,7 @@ class Opts(ctypes.Structure):
                 ("kernel_w", ctypes.c_int), ("recompute_nodes", ctypes.c_int),
                 ("sync_status", ctypes.c_int), ("max_device_bytes", ctypes.c_longlong),
                 ("t3_binning", ctypes.c_int), ("fft_split_above", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("nsli_far", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -179,7 +179,7 @@ def _family_array(families):
 
 
 def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes, sync_status,
-               max_device_bytes, t3_binning, fft_split_above=0, autotune=False):
+               max_device_bytes, t3_binning, fft_split_above=0, autotune=False, nsli_far=0.0):
     o = Opts()
     lib.fresnel_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -201,6 +201,7 @@ def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nod
     o.t3_binning = int(t3_binning)
     o.fft_split_above = int(fft_split_above)
     o.autotune = int(bool(autotune))
+    o.nsli_far = float(nsli_far)
     return o
 
 
@@ -273,7 +274,7 @@ class BatchPlan(_PlanHandle):
     def __init__(self, problems, tol, precision="fp32", output="aperture", grid=None, box=None,
                  sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None):
+                 stream=None, nsli_far=0.0):
         import torch
         lib = load_library()
         self._torch = torch
@@ -285,7 +286,8 @@ class BatchPlan(_PlanHandle):
             self._keep.append((fams, keep))
             probs[b] = Problem(fams, len(q["families"]), float(q["lam"]), float(q["z"]))
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
-                       sync_status, max_device_bytes, t3_binning, fft_split_above, autotune)
+                       sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
+                       nsli_far)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -334,14 +336,15 @@ class Plan(_PlanHandle):
     def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
                  box=None, sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None):
+                 stream=None, nsli_far=0.0):
         import torch
         lib = load_library()
         self._torch = torch
         fams, keep = _family_array(families)
         self.profile_sizes = _profile_sizes(families)
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
-                       sync_status, max_device_bytes, t3_binning, fft_split_above, autotune)
+                       sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
+                       nsli_far)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -304,6 +304,33 @@ def test_nsli_matches_oracle_line_integral():
     assert np.max(np.abs(u - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("output", ["aperture", "occulter"])
+def test_nsli_far_matches_oracle(output):
+    """The far-target option (eq. li with the rounded winding number, the
+    Appendix's remark on shadows) against the oracle's line_integral_far on
+    a coarse rule (inexact winding numbers), near and far targets, inside
+    and outside."""
+    fam = W.fourier_family(W.STAR_PARAMS, 12, 4, 8, cx=0.1, cy=-0.05)
+    X, Y, Wt, V, _, _ = Q.family_line_rule(fam)
+    xi, eta = W.disc_targets(3000, 1.6, 15)
+    lz, far = 0.04, 0.15
+    from oracle import direct
+    uap, uoc = direct.line_integral_far(X, Y, Wt, V, xi, eta, lz, far)
+    ref = uoc if output == "occulter" else uap
+    p = plan([fam], lz, 1.0, 1e-12, precision="fp64", box=(-1.6, 1.6, -1.6, 1.6),
+             output=output, nsli_far=far)
+    t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
+    u = p.nsli(t).cpu().numpy()
+    assert np.max(np.abs(u - ref)) <= 1e-12
+    # both kinds of target are present (the oracle copies eq. nsli's value
+    # for near ones), and the option changed the far ones
+    un = direct.nsli(X, Y, Wt, V, xi, eta, lz)
+    un = 1.0 - un if output == "occulter" else un
+    near = ref == un
+    assert np.count_nonzero(near) > 10 and np.count_nonzero(~near) > 100
+    assert np.min(np.abs(u - un)[~near]) > 1e-9 or np.median(np.abs(u - un)[~near]) > 1e-6
+
+
 def test_nsli_agrees_with_areal_path():
     """Converged disc (F = 10, m = 64): the areal NUFFT path and the device line
     integral agree, and both match the Hankel closed form."""

@@ -446,3 +446,47 @@ def test_planted_wrong_tangent(monkeypatch):
         X, Y, Wt, V = orig(params, n_panels, p, cx, cy)
         return X, Y, V, Wt  # W and V swapped
     assert _pins_fail(monkeypatch, lambda mp: mp.setattr(Q, "fourier_line_rule", bad))
+
+
+# ------------------------------------------------------------------ eq. li far from the boundary
+def _disc_ptr(n, R=1.0):
+    return Q.ptr_line_rule(lambda s: (R * np.cos(s), R * np.sin(s)),
+                           lambda s: (-R * np.sin(s), R * np.cos(s)), n)
+
+
+def test_line_integral_far_matches_nsli_on_a_converged_rule():
+    """Eq. li with the rounded winding number (Appendix remark r:shadfix) and
+    eq. nsli are the same integral: on a converged rule they agree at far
+    targets inside (u_geom = 1) and outside (u_geom = 0) the disc, for u^ap
+    and u^oc; near targets take eq. nsli unchanged."""
+    from oracle import direct
+    X, Y, Wt, V = _disc_ptr(240)
+    xi = np.array([0.0, 0.35, -0.2, 1.7, -2.5, 0.995])
+    eta = np.array([0.0, -0.3, 0.45, 0.4, 1.0, 0.0])
+    uap, uoc = direct.line_integral_far(X, Y, Wt, V, xi, eta, 0.05, 0.25)
+    un = direct.nsli(X, Y, Wt, V, xi, eta, 0.05)
+    assert np.max(np.abs(uap - un)) < 1e-13
+    assert np.max(np.abs(uoc - (1.0 - un))) < 1e-13
+    assert uoc[-1] == 1.0 - un[-1]   # nearest node 0.005 away: eq. nsli
+    # on axis the disc's closed form
+    assert abs(uap[0] - CF.disc_on_axis(1.0, 0.05)) < 1e-13
+
+
+def test_line_integral_far_uses_the_exact_winding_number():
+    """With a coarse rule the quadrature's winding number (eq. geom) is not
+    an integer; eq. li replaces it by the integer, so the two forms differ
+    by exactly (round(w) - w), w = 1/(2 pi) sum (r x ds)/r^2 (eq. nsli =
+    w - 1/(2 pi) sum e^{i pi r^2/lz} (r x ds)/r^2)."""
+    from oracle import direct
+    X, Y, Wt, V = _disc_ptr(9, R=1.0)
+    xi, eta = np.array([0.3, 3.0]), np.array([0.1, -0.5])
+    uap, uoc = direct.line_integral_far(X, Y, Wt, V, xi, eta, 0.1, 0.3)
+    un = direct.nsli(X, Y, Wt, V, xi, eta, 0.1)
+    for k in range(2):
+        rx, ry = X - xi[k], Y - eta[k]
+        w = np.sum((rx * V - ry * Wt) / (rx * rx + ry * ry)) / (2 * np.pi)
+        assert abs(w - np.rint(w)) > 1e-9          # the coarse rule's winding is inexact
+        assert abs((uap[k] - un[k]) - (np.rint(w) - w)) < 1e-13
+        assert abs(uoc[k] - (1.0 - uap[k])) < 1e-13
+    assert np.rint(np.sum(((X - 0.3) * V - (Y - 0.1) * Wt) / ((X - 0.3) ** 2 + (Y - 0.1) ** 2))
+                   / (2 * np.pi)) == 1.0
