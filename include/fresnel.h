@@ -163,6 +163,25 @@ typedef struct {
      * integer (exact u_geom, so a shadow's u^oc is not 1 minus a quadrature
      * of 1); nearer targets use eq. nsli.  0 = eq. nsli everywhere. */
     double nsli_far;
+    /* Source-plane screen (Sec. 5: the strengths' w_j times the source term
+     * at each areal node): s(x, y) = A(x, y) exp(2 pi i OPD(x, y) / lambda),
+     * lambda each problem's own.  screen_amp (amplitude A) and screen_opd
+     * (optical path difference, same length unit as lambda) are HOST arrays
+     * of screen_n2 rows of screen_n1 samples (row-major; either may be NULL:
+     * A = 1 / OPD = 0) at x = box[0] + i (box[1] - box[0]) / (n1 - 1),
+     * y = box[2] + k (box[3] - box[2]) / (n2 - 1), copied at plan time, and
+     * interpolated by Catmull-Rom (cubic convolution, exact for polynomials of
+     * degree <= 2).  The interpolation stencil stays inside the samples: the
+     * box must reach one spacing beyond the aperture (nodes nearer the edge
+     * take the nearest interior value).  screen_n1 = screen_n2 = 0: no screen.
+     * FP32_FAST plans evaluate the screen in FP32: its phase 2 pi OPD / lambda
+     * carries an error of ~1e-7 of its range, so at tol 1e-6 keep that range
+     * within ~10 rad or use FP64.  Not with profile gradients or the line
+     * integral. */
+    const double* screen_amp;
+    const double* screen_opd;
+    int screen_n1, screen_n2;
+    double screen_box[4];
 } fresnel_opts;
 
 /* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,

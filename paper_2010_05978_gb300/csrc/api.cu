@@ -983,6 +983,30 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         }
     }
 
+    // ---------------- source screen: samples in the plan's precision, k per problem
+    if (p->opts.screen_n1 > 0) {
+        const fresnel_opts& o = p->opts;
+        const size_t ns = (size_t)o.screen_n1 * o.screen_n2;
+        ScreenDev& sc = p->ft.scr;
+        for (int k = 0; k < 2; ++k) {
+            const double* src = k == 0 ? o.screen_amp : o.screen_opd;
+            if (!src) continue;
+            std::vector<T> h(src, src + ns);
+            void* d = nullptr;
+            FRES_TRY(dalloc(p, &d, sizeof(T) * ns));
+            FRES_CK(cudaMemcpyAsync(d, h.data(), sizeof(T) * ns, cudaMemcpyHostToDevice, p->st));
+            FRES_CK(cudaStreamSynchronize(p->st));
+            (k == 0 ? sc.amp : sc.opd) = d;
+        }
+        sc.n1 = o.screen_n1;
+        sc.n2 = o.screen_n2;
+        sc.x0 = o.screen_box[0];
+        sc.y0 = o.screen_box[2];
+        sc.ihx = (o.screen_n1 - 1) / (o.screen_box[1] - o.screen_box[0]);
+        sc.ihy = (o.screen_n2 - 1) / (o.screen_box[3] - o.screen_box[2]);
+        for (int b = 0; b < p->B; ++b) p->cps[b].screen_k = kTwoPi / problems[b].lambda;
+    }
+
     // ---------------- family table for the node and scatter launches
     {
         const int nfam = (int)p->fams.size();
@@ -1334,6 +1358,19 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
         return fres_fail(FRESNEL_ERR_ARG, "fft_split_above must be >= 0");
     if (!(opts->nsli_far >= 0.0) || !std::isfinite(opts->nsli_far))
         return fres_fail(FRESNEL_ERR_ARG, "nsli_far must be finite and >= 0");
+    if (opts->screen_n1 || opts->screen_n2 || opts->screen_amp || opts->screen_opd) {
+        const double* bx = opts->screen_box;
+        if (opts->screen_n1 < 4 || opts->screen_n2 < 4)
+            return fres_fail(FRESNEL_ERR_ARG, "a screen needs at least 4 x 4 samples");
+        if (!opts->screen_amp && !opts->screen_opd)
+            return fres_fail(FRESNEL_ERR_ARG, "a screen needs screen_amp and/or screen_opd");
+        if ((long long)opts->screen_n1 * opts->screen_n2 > (1LL << 28))
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "screen larger than 2^28 samples");
+        for (int i = 0; i < 4; ++i)
+            if (!std::isfinite(bx[i])) return fres_fail(FRESNEL_ERR_ARG, "screen_box not finite");
+        if (!(bx[1] > bx[0]) || !(bx[3] > bx[2]))
+            return fres_fail(FRESNEL_ERR_ARG, "screen_box must have box[1] > box[0], box[3] > box[2]");
+    }
     int dev = 0;
     FRES_CK(cudaGetDevice(&dev));
     if (opts->target_kind == FRESNEL_SCATTERED && n_problems > 1)
@@ -1453,6 +1490,8 @@ fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, do
     if (p->d1.big || p->d2.big)
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients need single-pass FFT lengths");
     if (!d_gamma || !d_grad) return fres_fail(FRESNEL_ERR_ARG, "d_gamma or d_grad is NULL");
+    if (p->ft.scr.n1 > 0)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients do not take a source screen");
     fresnel_status s = p->prec == FRESNEL_FP64 ? grad_profile_impl<double>(p, d_gamma, d_grad)
                                                : grad_profile_impl<float>(p, d_gamma, d_grad);
     if (s != FRESNEL_OK) return s;
@@ -1470,6 +1509,8 @@ fresnel_status fresnel_nsli(fresnel_plan_t plan, const double* d_targets, long l
         if (f.kind != FRESNEL_FAMILY_FOURIER && f.kind != FRESNEL_FAMILY_LINE_RULE)
             return fres_fail(FRESNEL_ERR_UNSUPPORTED,
                              "the line integral needs FOURIER or LINE_RULE families only");
+    if (p->ft.scr.n1 > 0)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "the line integral cannot include a source screen");
     if (M < 0) return fres_fail(FRESNEL_ERR_ARG, "M must be >= 0");
     if (M > 0 && (!d_targets || !d_out)) return fres_fail(FRESNEL_ERR_ARG, "d_targets or d_out is NULL");
     launch_nsli(p->fams.data(), (int)p->fams.size(), p->lz, d_targets, M,

@@ -126,6 +126,7 @@ struct ChirpParams {
     // x~ = 0 lands mid-tile, so a cluster round the origin does not straddle
     // the wrap); the output tables undo it with exp(+2 pi i k sh / nf).
     int sh1, sh2;
+    double screen_k;       // 2 pi / lambda of the problem (source screens)
 };
 
 // Piecewise-polynomial form of the spreading kernel for FP32: the value at
@@ -179,11 +180,22 @@ __device__ __forceinline__ R kernel_ft(R t, int w, R beta, const R* gq_t, const 
 
 // The families of a plan for one node launch: family f owns blocks
 // [blk0[f], blk0[f+1]); its problem's chirp parameters are cps[fams[f].prob].
+// Source-plane screen (fresnel_opts.screen_*) on the device: n2 rows of n1
+// samples in the plan's precision from (x0, y0) with spacings 1/ihx, 1/ihy;
+// amp / opd NULL mean A = 1 / OPD = 0; n1 = 0: no screen.
+struct ScreenDev {
+    const void* amp = nullptr;
+    const void* opd = nullptr;
+    int n1 = 0, n2 = 0;
+    double x0 = 0, y0 = 0, ihx = 0, ihy = 0;
+};
+
 struct FamTable {
     const FamilyDev* fams;
     const ChirpParams* cps;
     const int* blk0;
     int nfam;
+    ScreenDev scr;
 };
 constexpr int kNodeThreads = 256;
 

@@ -39,6 +39,61 @@ __device__ __forceinline__ int agg_reserve(int key, int* cursor) {
     return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// ------------------------------------------------------------------ source screens
+// s(x, y) = A(x, y) exp(i k OPD(x, y)) (Sec. 5: the strength of each areal
+// node times the source term), A and OPD by Catmull-Rom interpolation of
+// their samples: cubic convolution with the weights, for the fraction t of
+// the cell, -t(1-t)^2/2, (2 - 5t^2 + 3t^3)/2, t(1 + 4t - 3t^2)/2, -t^2(1-t)/2
+// on samples -1, 0, 1, 2.  The stencil stays inside the samples (cells 1 ..
+// n - 3; nodes beyond take the nearest interior value).
+template <typename T>
+__device__ __forceinline__ void cr_weights(T t, T w[4]) {
+    const T t2 = t * t, t3 = t2 * t;
+    w[0] = (T)0.5 * (-t3 + (T)2 * t2 - t);
+    w[1] = (T)0.5 * ((T)3 * t3 - (T)5 * t2 + (T)2);
+    w[2] = (T)0.5 * ((T)-3 * t3 + (T)4 * t2 + t);
+    w[3] = (T)0.5 * (t3 - t2);
+}
+
+template <typename T>
+__device__ __forceinline__ T cr_interp(const T* __restrict__ a, int n1, int i1, int i2,
+                                       const T wx[4], const T wy[4]) {
+    T s = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const T* row = a + (long long)(i2 - 1 + b) * n1 + (i1 - 1);
+        const T r = wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2] + wx[3] * row[3];
+        s += wy[b] * r;
+    }
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ void apply_screen(const ScreenDev& sc, double k, T x, T y, T& cre,
+                                             T& cim) {
+    T u = (x - (T)sc.x0) * (T)sc.ihx, v = (y - (T)sc.y0) * (T)sc.ihy;
+    u = u < (T)1 ? (T)1 : (u > (T)(sc.n1 - 2) ? (T)(sc.n1 - 2) : u);
+    v = v < (T)1 ? (T)1 : (v > (T)(sc.n2 - 2) ? (T)(sc.n2 - 2) : v);
+    if (!(u == u) || !(v == v)) u = v = (T)1;   // non-finite node: flagged elsewhere
+    const int i1 = min((int)u, sc.n1 - 3), i2 = min((int)v, sc.n2 - 3);
+    T wx[4], wy[4];
+    cr_weights<T>(u - (T)i1, wx);
+    cr_weights<T>(v - (T)i2, wy);
+    const T A = sc.amp ? cr_interp<T>((const T*)sc.amp, sc.n1, i1, i2, wx, wy) : (T)1;
+    T sr = A, si = (T)0;
+    if (sc.opd) {
+        const T ph = (T)k * cr_interp<T>((const T*)sc.opd, sc.n1, i1, i2, wx, wy);
+        T sn, cs;
+        if constexpr (sizeof(T) == 4) sincosf(ph, &sn, &cs);
+        else sincos(ph, &sn, &cs);
+        sr = A * cs;
+        si = A * sn;
+    }
+    const T r = cre * sr - cim * si, im = cre * si + cim * sr;
+    cre = r;
+    cim = im;
+}
+
 // Up to four tiles touched by a node whose support starts at (s1, s2).
 __device__ __forceinline__ void node_tiles(int s1, int s2, const ChirpParams& cp, int key[4]) {
     int e1 = s1 + cp.w - 1; if (e1 >= cp.nf1) e1 -= cp.nf1;
@@ -235,7 +290,8 @@ __device__ __forceinline__ void finish_df(dflt v1, dflt v2, float cre, float cim
 }
 
 __device__ __forceinline__ void node_df(const FamilyDev& f, const ChirpParams& cp, long long j,
-                                        NodeRec<float>* rec, unsigned* status, int key[4]) {
+                                        NodeRec<float>* rec, unsigned* status, int key[4],
+                                        const ScreenDev& scr) {
     // j < 2^30 (plan limit): 32-bit division
     const unsigned i = (unsigned)j / (unsigned)f.m;
     const int l = (int)((unsigned)j - i * (unsigned)f.m);
@@ -253,7 +309,13 @@ __device__ __forceinline__ void node_df(const FamilyDev& f, const ChirpParams& c
     sincosf(phr, &sn, &cs);
     dflt v1 = df_add(df_mul(al, dflt{sG.x, sG.y}), dflt{f.G0x[0], f.G0x[1]});
     dflt v2 = df_add(df_mul(al, dflt{sG.z, sG.w}), dflt{f.G0y[0], f.G0y[1]});
-    finish_df(v1, v2, w * cs, w * sn, cp, rec + f.offset + j, status, key);
+    float cre = w * cs, cim = w * sn;
+    if (scr.n1) {   // the node itself, c + alpha (X_i - c), in FP32
+        const float x = (float)f.cx + al.hi * (float)f.bx[i];
+        const float y = (float)f.cy + al.hi * (float)f.by[i];
+        apply_screen<float>(scr, cp.screen_k, x, y, cre, cim);
+    }
+    finish_df(v1, v2, cre, cim, cp, rec + f.offset + j, status, key);
 }
 
 // Starshade petals in the double-float form: node (k, i, l) is table entry
@@ -261,7 +323,7 @@ __device__ __forceinline__ void node_df(const FamilyDev& f, const ChirpParams& c
 // per-petal slopes (Sec. 4.2 nodes; no FP64 per node).
 __device__ __forceinline__ void node_petal_df(const FamilyDev& f, const ChirpParams& cp,
                                               long long j, NodeRec<float>* rec, unsigned* status,
-                                              int key[4]) {
+                                              int key[4], const ScreenDev& scr) {
     const unsigned k = (unsigned)j / (unsigned)f.n_bdry;   // j < 2^30
     const unsigned q = (unsigned)j - k * (unsigned)f.n_bdry;
     const float4 t0 = reinterpret_cast<const float4*>(f.ptab)[2 * q];
@@ -277,7 +339,14 @@ __device__ __forceinline__ void node_petal_df(const FamilyDev& f, const ChirpPar
                      dflt{f.G0x[0], f.G0x[1]});
     dflt v2 = df_add(df_add(df_mul(u, dflt{K[8], K[9]}), df_mul(v, dflt{K[10], K[11]})),
                      dflt{f.G0y[0], f.G0y[1]});
-    finish_df(v1, v2, t1.z * cs, t1.z * sn, cp, rec + f.offset + j, status, key);
+    float cre = t1.z * cs, cim = t1.z * sn;
+    if (scr.n1) {   // the node itself: petal 0's (u, v) rotated to petal k, in FP32
+        const float c = (float)f.rot[2 * k], sr = (float)f.rot[2 * k + 1];
+        const float x = (float)f.cx + (u.hi * c - v.hi * sr);
+        const float y = (float)f.cy + (u.hi * sr + v.hi * c);
+        apply_screen<float>(scr, cp.screen_k, x, y, cre, cim);
+    }
+    finish_df(v1, v2, cre, cim, cp, rec + f.offset + j, status, key);
 }
 
 // Double-float table of a petal family (FP32 fast mode), from its FP64 table.
@@ -297,7 +366,7 @@ __global__ void k_petal_df_tables(FamilyDev f, ChirpParams cp) {
 template <typename T>
 __device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpParams& cp, long long j,
                                              NodeRec<T>* rec, double* dx, double* dy, double* dw,
-                                             unsigned* status, int key[4]) {
+                                             unsigned* status, int key[4], const ScreenDev& scr) {
     double x, y, w;
     if (f.kind == FRESNEL_FAMILY_NODES) {
         x = f.params[j];
@@ -339,6 +408,7 @@ __device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpPara
         r.cre = (T)((float)w * cs);
         r.cim = (T)((float)w * sn);
     }
+    if (scr.n1) apply_screen<T>(scr, cp.screen_k, (T)x, (T)y, r.cre, r.cim);
     double g1, g2;
     if (!cp.type3) {
         double u = x * cp.u1;
@@ -437,13 +507,14 @@ k_nodes(FamTable ft, NodeRec<T>* rec, int* counts, double* dx, double* dy, doubl
     if (j < f.n_nodes) {
         if constexpr (sizeof(T) == 4) {
             if (f.spoke && !dx)
-                node_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key);
+                node_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key, ft.scr);
             else if (f.ptab && !dx)
-                node_petal_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key);
+                node_petal_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key,
+                              ft.scr);
             else
-                node_generic<T>(f, sm.cp, j, rec, dx, dy, dw, status, key);
+                node_generic<T>(f, sm.cp, j, rec, dx, dy, dw, status, key, ft.scr);
         } else {
-            node_generic<T>(f, sm.cp, j, rec, dx, dy, dw, status, key);
+            node_generic<T>(f, sm.cp, j, rec, dx, dy, dw, status, key, ft.scr);
         }
     }
 #pragma unroll

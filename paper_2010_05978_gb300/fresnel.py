@@ -53,7 +53,10 @@ class Opts(ctypes.Structure):
                 ("kernel_w", ctypes.c_int), ("recompute_nodes", ctypes.c_int),
                 ("sync_status", ctypes.c_int), ("max_device_bytes", ctypes.c_longlong),
                 ("t3_binning", ctypes.c_int), ("fft_split_above", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("nsli_far", ctypes.c_double)]
+                ("autotune", ctypes.c_int), ("nsli_far", ctypes.c_double),
+                ("screen_amp", ctypes.c_void_p), ("screen_opd", ctypes.c_void_p),
+                ("screen_n1", ctypes.c_int), ("screen_n2", ctypes.c_int),
+                ("screen_box", ctypes.c_double * 4)]
 
 
 class Info(ctypes.Structure):
@@ -179,7 +182,8 @@ def _family_array(families):
 
 
 def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes, sync_status,
-               max_device_bytes, t3_binning, fft_split_above=0, autotune=False, nsli_far=0.0):
+               max_device_bytes, t3_binning, fft_split_above=0, autotune=False, nsli_far=0.0,
+               screen=None):
     o = Opts()
     lib.fresnel_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -202,6 +206,22 @@ def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nod
     o.fft_split_above = int(fft_split_above)
     o.autotune = int(bool(autotune))
     o.nsli_far = float(nsli_far)
+    o._keep = []
+    if screen is not None:
+        # dict(amp=, opd=, box=(x0, x1, y0, y1)): 2D arrays (n2 rows of n1)
+        arrs = {k: np.ascontiguousarray(screen[k], dtype=np.float64)
+                for k in ("amp", "opd") if screen.get(k) is not None}
+        if not arrs:
+            raise ValueError("screen needs amp and/or opd")
+        shp = next(iter(arrs.values())).shape
+        if len(shp) != 2 or any(a.shape != shp for a in arrs.values()):
+            raise ValueError("screen arrays must be 2D and of one shape")
+        o.screen_n2, o.screen_n1 = int(shp[0]), int(shp[1])
+        o.screen_amp = arrs["amp"].ctypes.data if "amp" in arrs else None
+        o.screen_opd = arrs["opd"].ctypes.data if "opd" in arrs else None
+        for i in range(4):
+            o.screen_box[i] = float(screen["box"][i])
+        o._keep = list(arrs.values())
     return o
 
 
@@ -274,7 +294,7 @@ class BatchPlan(_PlanHandle):
     def __init__(self, problems, tol, precision="fp32", output="aperture", grid=None, box=None,
                  sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None, nsli_far=0.0):
+                 stream=None, nsli_far=0.0, screen=None):
         import torch
         lib = load_library()
         self._torch = torch
@@ -287,7 +307,7 @@ class BatchPlan(_PlanHandle):
             probs[b] = Problem(fams, len(q["families"]), float(q["lam"]), float(q["z"]))
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
-                       nsli_far)
+                       nsli_far, screen)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -336,7 +356,7 @@ class Plan(_PlanHandle):
     def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
                  box=None, sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None, nsli_far=0.0):
+                 stream=None, nsli_far=0.0, screen=None):
         import torch
         lib = load_library()
         self._torch = torch
@@ -344,7 +364,7 @@ class Plan(_PlanHandle):
         self.profile_sizes = _profile_sizes(families)
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
-                       nsli_far)
+                       nsli_far, screen)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -490,3 +490,84 @@ def test_line_integral_far_uses_the_exact_winding_number():
         assert abs(uoc[k] - (1.0 - uap[k])) < 1e-13
     assert np.rint(np.sum(((X - 0.3) * V - (Y - 0.1) * Wt) / ((X - 0.3) ** 2 + (Y - 0.1) ** 2))
                    / (2 * np.pi)) == 1.0
+
+
+# ------------------------------------------------------------------ source screens (Sec. 5)
+def _field_module():
+    import importlib
+    return importlib.import_module("oracle.field")
+
+
+def _screen_grid(f, box, n1, n2):
+    xs = np.linspace(box[0], box[1], n1)
+    ys = np.linspace(box[2], box[3], n2)
+    X, Y = np.meshgrid(xs, ys)
+    return f(X, Y)
+
+
+def test_screen_interpolation_reproduces_quadratics():
+    """Cubic convolution with a = -1/2 is exact for polynomials of degree <= 2
+    inside the samples' interior (and not for cubics)."""
+    FL = _field_module()
+    box = (-1.2, 1.3, -1.1, 1.0)
+    f = lambda x, y: 0.3 + 0.7 * x - 0.2 * y + 0.5 * x * x - 0.4 * x * y + 0.9 * y * y
+    g = W.rng(41, 0)
+    x, y = g.uniform(-0.95, 1.05, 2000), g.uniform(-0.85, 0.75, 2000)
+    s = FL.screen_value({"amp": _screen_grid(f, box, 13, 11), "box": box}, 1.0, x, y)
+    assert np.max(np.abs(s - f(x, y))) < 1e-13
+    f3 = lambda x, y: x ** 3
+    s3 = FL.screen_value({"amp": _screen_grid(f3, box, 13, 11), "box": box}, 1.0, x, y)
+    assert np.max(np.abs(s3 - f3(x, y))) > 1e-5
+
+
+def test_screen_amplitude_disc_on_axis_closed_form():
+    """Disc of radius R under the amplitude screen A = 1 - r^2/R^2: on axis,
+    u = (pi/(i lz)) int_0^{R^2} (1 - t/R^2) e^{i a t} dt (a = pi/lz), i.e.
+    (pi/(i lz)) [E/(i a) - (R^2 e^{i a R^2}/(i a) - E/(i a)^2)/R^2], E = e^{i a R^2} - 1."""
+    FL = _field_module()
+    R, lz = 1.0, 0.1
+    box = (-1.3, 1.3, -1.3, 1.3)
+    amp = _screen_grid(lambda x, y: 1.0 - (x * x + y * y) / (R * R), box, 27, 27)
+    u = FL.field([W.fourier_family([R], 64, 16, 64)], lz, 1.0, np.array([0.0]), np.array([0.0]),
+                 screen={"amp": amp, "box": box})[0]
+    a = np.pi / lz
+    T = R * R
+    E = np.exp(1j * a * T) - 1.0
+    ref = (np.pi / (1j * lz)) * (E / (1j * a) - (T * np.exp(1j * a * T) / (1j * a) - E / (1j * a) ** 2) / T)
+    assert abs(u - ref) < 1e-11
+
+
+def test_screen_tilt_is_a_target_shift():
+    """Linear OPD = tx x + ty y (a tilted incident wave) shifts the pattern by
+    d = (tx z, ty z): u_s(xi) = e^{i pi (|xi|^2 - |xi - d|^2)/lz} u(xi - d),
+    term by term in the discrete sum (linear OPD is interpolated exactly)."""
+    FL = _field_module()
+    fam = [W.fourier_family(W.STAR_PARAMS, 32, 16, 24)]
+    lam, z, tx, ty = 0.02, 2.0, 0.03, -0.05
+    box = (-1.6, 1.6, -1.6, 1.6)
+    opd = _screen_grid(lambda x, y: tx * x + ty * y, box, 17, 17)
+    xi, eta = W.disc_targets(60, 1.2, 42)
+    us = FL.field(fam, lam, z, xi, eta, screen={"opd": opd, "box": box})
+    d1, d2 = tx * z, ty * z
+    u0 = FL.field(fam, lam, z, xi - d1, eta - d2)
+    ph = np.exp(1j * np.pi * (xi ** 2 + eta ** 2 - (xi - d1) ** 2 - (eta - d2) ** 2) / (lam * z))
+    assert np.max(np.abs(us - ph * u0)) < 1e-12
+
+
+def test_screen_defocus_is_a_new_distance():
+    """Quadratic OPD = -(x^2 + y^2)/(2D) (a converging wave, focus D) gives the
+    field at the effective distance 1/z' = 1/z - 1/D on targets scaled by z'/z:
+    u_s(xi; z) = (z'/z) e^{i pi (|xi|^2/z - |xi'|^2/z')/lam} u(xi'; z'), xi' = xi z'/z,
+    term by term (the spherical incidence of Sec. 2 with the sign of D reversed)."""
+    FL = _field_module()
+    fam = [W.fourier_family([1.0, 0.1, 0.0, 0.05, 0.0], 32, 16, 24)]
+    lam, z, D = 0.01, 3.0, 7.0
+    box = (-1.5, 1.5, -1.5, 1.5)
+    opd = _screen_grid(lambda x, y: -(x * x + y * y) / (2.0 * D), box, 21, 21)
+    xi, eta = W.disc_targets(60, 1.0, 43)
+    us = FL.field(fam, lam, z, xi, eta, screen={"opd": opd, "box": box})
+    zp = 1.0 / (1.0 / z - 1.0 / D)
+    xp, ep = xi * zp / z, eta * zp / z
+    u0 = FL.field(fam, lam, zp, xp, ep)
+    ref = (zp / z) * np.exp(1j * np.pi * ((xi ** 2 + eta ** 2) / z - (xp ** 2 + ep ** 2) / zp) / lam) * u0
+    assert np.max(np.abs(us - ref)) < 1e-11
