@@ -89,6 +89,18 @@ typedef enum {
  *     n_d, m_d and profile are whole numbers stored as doubles.  A may be
  *     negative or exceed 1 (non-ideal profiles); nothing is clamped.
  *
+ * FRESNEL_FAMILY_TRIANGLES: a union of triangles (Sec. 4.3, the Koch
+ *     snowflake construction), params = [v0x, v0y, v1x, v1y, v2x, v2y] per
+ *     triangle (n_params = 6 n_panels, n_panels triangles), translated by
+ *     (cx, cy).  Each triangle is a p x p product rule: v0 moved to the
+ *     origin, p Gauss-Legendre nodes s_i on the edge v1 -> v2 form the line
+ *     rule X_i = v1 + s_i (v2 - v1), (W_i, V_i) = what_i (v2 - v1), and the
+ *     dilation rule (eqs. aqnod, aqwei) with the same p radii alpha_l gives
+ *     x = v0 + alpha_l (X_i - v0), w = alpha_l what_l what_i
+ *     (v1 - v0) x (v2 - v1); the weights sum to the signed area (positive for
+ *     counter-clockwise v0, v1, v2).  m is ignored (p radii).  Nodes are
+ *     ordered triangle-major, then edge node, radius fastest: N = n_panels p^2.
+ *
  * Negative weights and nodes outside Omega (non-star-shaped domains, Sec. 4.1)
  * are accepted as given.  params is a HOST array copied during fresnel_plan.
  */
@@ -96,7 +108,8 @@ enum {
     FRESNEL_FAMILY_FOURIER = 0,
     FRESNEL_FAMILY_LINE_RULE = 1,
     FRESNEL_FAMILY_NODES = 2,
-    FRESNEL_FAMILY_PETALS = 3
+    FRESNEL_FAMILY_PETALS = 3,
+    FRESNEL_FAMILY_TRIANGLES = 4
 };
 enum { FRESNEL_PETAL_HG = 0, FRESNEL_PETAL_BSPLINE = 1, FRESNEL_PETAL_TABLE = 2 };
 

@@ -177,8 +177,29 @@ def family_line_rule(fam):
     raise ValueError("family kind %r has no line rule" % kind)
 
 
+def triangle_rule(tri, p, cx=0.0, cy=0.0):
+    """p x p areal rule of each triangle (Sec. 4.3): move vertex v0 to the
+    origin, discretise the line integral along the opposite edge v1 -> v2
+    with p Gauss-Legendre nodes (X_i = v1 + s_i (v2 - v1), tangent weights
+    what_i (v2 - v1)) and apply the dilation rule (eqs. aqnod, aqwei) with p
+    radii.  tri: (n, 6) rows (v0x, v0y, v1x, v1y, v2x, v2y).  Ordered
+    triangle-major, edge node, radius fastest."""
+    tri = np.asarray(tri, float).reshape(-1, 6)
+    s, ws = gauss_legendre(p, 0.0, 1.0)
+    xs, ys, wts = [], [], []
+    for v0x, v0y, v1x, v1y, v2x, v2y in tri:
+        ex, ey = v2x - v1x, v2y - v1y
+        X, Y = v1x + s * ex, v1y + s * ey
+        # the dilation rule about v0 with the edge's line rule
+        x, y, w = dilation_rule(X, Y, ws * ex, ws * ey, p, v0x, v0y)
+        xs.append(x), ys.append(y), wts.append(w)
+    return (cx + np.concatenate(xs), cy + np.concatenate(ys), np.concatenate(wts))
+
+
 def family_nodes(fam):
     """Areal nodes and weights (x, y, w) of one panel family."""
+    if fam["kind"] == "triangles":
+        return triangle_rule(fam["tri"], fam["p"], fam.get("cx", 0.0), fam.get("cy", 0.0))
     if fam["kind"] == "nodes":
         return (np.asarray(fam["x"], float), np.asarray(fam["y"], float),
                 np.asarray(fam["w"], float))

@@ -344,6 +344,15 @@ fresnel_status validate_family(const fresnel_family& f, long long* n_bdry, long 
             *n_bdry = 0;
             *n_nodes = f.n_params / 3;
             return FRESNEL_OK;
+        case FRESNEL_FAMILY_TRIANGLES:
+            if (f.n_panels < 1 || f.p < 1 || f.p > 4096)
+                return fres_fail(FRESNEL_ERR_ARG, "TRIANGLES family needs n_panels>=1, 1<=p<=4096");
+            if (f.n_params != 6LL * f.n_panels)
+                return fres_fail(FRESNEL_ERR_ARG, "TRIANGLES params must hold 6 * n_panels values");
+            *K = 0;
+            *n_bdry = 0;
+            *n_nodes = (long long)f.n_panels * f.p * f.p;
+            return FRESNEL_OK;
         case FRESNEL_FAMILY_PETALS: {
             if (f.n_panels < 1 || f.p < 1 || f.m < 1 || f.n_panels > 65536 || f.p > 4096 ||
                 f.m > 65536)
@@ -648,6 +657,31 @@ fresnel_status setup_nodes_family(Plan* p, FamilyDev& f, const double* hparams, 
     return FRESNEL_OK;
 }
 
+// A union of triangles: device vertices and the p-point Gauss-Legendre rule
+// on (0, 1) as alpha (gl_m_a, also the edge parameters), alpha * what
+// (gl_m_aw) and what (gl_p_w); nodes lie inside each triangle, so the
+// translated vertices bound them.
+fresnel_status setup_triangle_family(Plan* p, FamilyDev& f, const double* hparams, long long n,
+                                     Bounds& bb) {
+    FRES_TRY(copy_params(p, f, hparams, n));
+    f.m = f.p;
+    FRES_TRY(dalloc(p, (void**)&f.gl_m_a, sizeof(double) * f.p));
+    FRES_TRY(dalloc(p, (void**)&f.gl_m_aw, sizeof(double) * f.p));
+    FRES_TRY(dalloc(p, (void**)&f.gl_p_w, sizeof(double) * f.p));
+    launch_gauss_legendre(f.p, f.gl_m_a, f.gl_p_w, p->st);
+    std::vector<double> a(f.p), w(f.p);
+    FRES_CK(cudaMemcpyAsync(a.data(), f.gl_m_a, sizeof(double) * f.p, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaMemcpyAsync(w.data(), f.gl_p_w, sizeof(double) * f.p, cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    for (int l = 0; l < f.p; ++l) w[l] *= a[l];
+    FRES_CK(cudaMemcpyAsync(f.gl_m_aw, w.data(), sizeof(double) * f.p, cudaMemcpyHostToDevice, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    for (long long t = 0; t < f.n_panels; ++t)
+        for (int v = 0; v < 3; ++v)
+            bb.add(f.cx + hparams[6 * t + 2 * v], f.cy + hparams[6 * t + 2 * v + 1]);
+    return FRESNEL_OK;
+}
+
 // Device params, Gauss-Legendre rules and boundary line rule of a family
 // used through the dilation rule (FOURIER, LINE_RULE, a starshade's disc),
 // and the bounds of its nodes.
@@ -767,6 +801,10 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
             f.offset = off;
             off += nn;
             FRES_TRY(setup_nodes_family<T>(p, f, hf.params, hf.n_params, bb));
+        } else if (hf.kind == FRESNEL_FAMILY_TRIANGLES) {
+            f.offset = off;
+            off += nn;
+            FRES_TRY(setup_triangle_family(p, f, hf.params, hf.n_params, bb));
         } else if (hf.kind == FRESNEL_FAMILY_PETALS) {
             // the disc r < a: a FOURIER circle on the periodic trapezoid rule
             const int n_d = (int)hf.params[2], m_d = (int)hf.params[3];
@@ -933,7 +971,7 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     if (!dbl) {
         for (FamilyDev& f : p->fams) {
             const ChirpParams& cp = p->cps[f.prob];
-            if (f.kind == FRESNEL_FAMILY_NODES) continue;
+            if (f.kind == FRESNEL_FAMILY_NODES || f.kind == FRESNEL_FAMILY_TRIANGLES) continue;
             if (f.kind == FRESNEL_FAMILY_PETALS) {
                 FRES_TRY(dalloc(p, (void**)&f.ptab, sizeof(float) * 8 * f.n_bdry));
                 FRES_TRY(dalloc(p, (void**)&f.pk, sizeof(float) * 12 * f.n_panels));

@@ -372,6 +372,19 @@ __device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpPara
         x = f.params[j];
         y = f.params[f.n_nodes + j];
         w = f.params[2 * f.n_nodes + j];
+    } else if (f.kind == FRESNEL_FAMILY_TRIANGLES) {
+        // triangle t, edge node i on v1 -> v2, radius l about v0 (Sec. 4.3):
+        // x = v0 + alpha_l (X_i - v0), w = alpha_l what_l what_i (v1 - v0) x (v2 - v1)
+        const unsigned pp = (unsigned)(f.p * f.p);                 // j < 2^30
+        const unsigned t = (unsigned)j / pp, q = (unsigned)j - t * pp;
+        const unsigned i = q / (unsigned)f.p, l = q - i * (unsigned)f.p;
+        const double* v = f.params + 6 * (size_t)t;
+        const double d1x = v[2] - v[0], d1y = v[3] - v[1];         // v1 - v0
+        const double ex = v[4] - v[2], ey = v[5] - v[3];           // v2 - v1
+        const double s = f.gl_m_a[i], a = f.gl_m_a[l];
+        x = f.cx + v[0] + a * (d1x + s * ex);
+        y = f.cy + v[1] + a * (d1y + s * ey);
+        w = f.gl_m_aw[l] * f.gl_p_w[i] * (d1x * ey - d1y * ex);
     } else if (f.kind == FRESNEL_FAMILY_PETALS) {
         // node (k, i, l) = petal 0's node (i, l) rotated by 2 pi k / Np
         const unsigned k = (unsigned)j / (unsigned)f.n_bdry;   // j < 2^30

@@ -151,6 +151,9 @@ def family_params(fam):
         params = np.ascontiguousarray(np.concatenate(
             [np.asarray(fam[k], np.float64) for k in ("x", "y", "w")]))
         return 2, 0, 0, 0, params, 0.0, 0.0
+    if kind == "triangles":
+        tri = np.ascontiguousarray(np.asarray(fam["tri"], np.float64).reshape(-1, 6).ravel())
+        return 4, len(tri) // 6, fam["p"], 0, tri, fam.get("cx", 0.0), fam.get("cy", 0.0)
     if kind == "petals":
         prof = fam["profile"]
         if prof["kind"] == "hg":

@@ -571,3 +571,75 @@ def test_screen_defocus_is_a_new_distance():
     u0 = FL.field(fam, lam, zp, xp, ep)
     ref = (zp / z) * np.exp(1j * np.pi * ((xi ** 2 + eta ** 2) / z - (xp ** 2 + ep ** 2) / zp) / lam) * u0
     assert np.max(np.abs(us - ref)) < 1e-11
+
+
+# ------------------------------------------------------------------ triangle unions (Sec. 4.3)
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 5])
+def test_koch_area_closed_form(level):
+    """Weights of the snowflake's triangle rules sum to the level-L area
+    A_L = A_0 (1 + sum_{k=1}^L 3 4^(k-1) / 9^k), A_0 = 3 sqrt(3)/4 (side sqrt(3)),
+    and the triangle counts are 1 + 3 sum_{k<L} 4^k (Sec. 4.3)."""
+    fams = W.koch_families(level, 0.2)
+    total = sum(Q.family_nodes(f)[2].sum() for f in fams)
+    A0 = 3.0 * np.sqrt(3.0) / 4.0
+    AL = A0 * (1.0 + sum(3.0 * 4.0 ** (k - 1) / 9.0 ** k for k in range(1, level + 1)))
+    assert abs(total - AL) < 1e-13
+    assert sum(len(f["tri"]) for f in fams) == 1 + 3 * sum(4 ** k for k in range(level))
+
+
+def test_triangle_rule_polynomial_exactness():
+    """The p x p triangle rule integrates x^a y^b (a + b <= 2p - 2) exactly:
+    against Green's theorem, iint x^a y^b = oint x^(a+1)/(a+1) y^b dy over the
+    counter-clockwise edges, each edge by a 12-point Gauss rule in t."""
+    g = W.rng(44, 0)
+    v = g.uniform(-1, 1, 6)
+    if (v[2] - v[0]) * (v[5] - v[1]) - (v[3] - v[1]) * (v[4] - v[0]) < 0:
+        v = v[[0, 1, 4, 5, 2, 3]]
+    x, y, w = Q.triangle_rule(v[None, :], 4)
+    t, wt = Q.gauss_legendre(12, 0.0, 1.0)
+    P = v.reshape(3, 2)
+    for a in range(7):
+        for b in range(7 - a):
+            exact = 0.0
+            for k in range(3):
+                p0, p1 = P[k], P[(k + 1) % 3]
+                xs, ys = p0[0] + t * (p1[0] - p0[0]), p0[1] + t * (p1[1] - p0[1])
+                exact += np.sum(wt * xs ** (a + 1) / (a + 1) * ys ** b) * (p1[1] - p0[1])
+            assert abs(np.sum(w * x ** a * y ** b) - exact) < 1e-13 * max(1.0, abs(exact))
+
+
+def test_square_from_two_triangles_fresnel_integrals():
+    """A rectangle as two triangles: u^ap = F_x F_y / (2i), F = (C(u2) - C(u1))
+    + i (S(u2) - S(u1)), u = sqrt(2/lz) (edge - target) (eq. fres separates)."""
+    from scipy.special import fresnel
+    x1, x2, y1, y2, lz = -0.4, 0.6, -0.5, 0.3, 0.05
+    tri = np.array([[x1, y1, x2, y1, x2, y2], [x1, y1, x2, y2, x1, y2]])
+    fam = [{"kind": "triangles", "tri": tri, "p": 120}]
+    xi = np.array([0.0, 0.3, -0.7, 0.9, 0.1])
+    eta = np.array([0.0, -0.2, 0.4, 0.6, -0.9])
+    u = oracle.field(fam, lz, 1.0, xi, eta)
+
+    def F(a, b, c):
+        s2, c2 = fresnel(np.sqrt(2.0 / lz) * (b - c))
+        s1, c1 = fresnel(np.sqrt(2.0 / lz) * (a - c))
+        return (c2 - c1) + 1j * (s2 - s1)
+    ref = F(x1, x2, xi) * F(y1, y2, eta) / 2j
+    assert np.max(np.abs(u - ref)) < 1e-12
+
+
+def test_triangle_rule_matches_polygon_line_rule():
+    """The snowflake's base triangle two ways: the p x p triangle rule, and
+    its three edges as a vector line rule (Gauss panels) dilated about the
+    centroid (eqs. vliq, aqnod, aqwei): the fields agree once both converge."""
+    tri = W.koch_triangles(0)[0]
+    P = tri.reshape(3, 2)
+    t, wt = Q.gauss_legendre(60, 0.0, 1.0)
+    X = np.concatenate([P[k, 0] + t * (P[(k + 1) % 3, 0] - P[k, 0]) for k in range(3)])
+    Y = np.concatenate([P[k, 1] + t * (P[(k + 1) % 3, 1] - P[k, 1]) for k in range(3)])
+    Wt = np.concatenate([wt * (P[(k + 1) % 3, 0] - P[k, 0]) for k in range(3)])
+    V = np.concatenate([wt * (P[(k + 1) % 3, 1] - P[k, 1]) for k in range(3)])
+    line = {"kind": "line_rule", "X": X, "Y": Y, "W": Wt, "V": V, "m": 60}
+    xi, eta = W.disc_targets(40, 1.0, 45)
+    u1 = oracle.field([{"kind": "triangles", "tri": tri, "p": 60}], 0.25, 1.0, xi, eta)
+    u2 = oracle.field([line], 0.25, 1.0, xi, eta)
+    assert np.max(np.abs(u1 - u2)) < 1e-11

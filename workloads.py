@@ -212,6 +212,42 @@ def random_star(n_panels=640, p=16, m=1024, fresnel_number=1000.0, config_id=5):
     }
 
 
+def koch_triangles(level):
+    """Triangles of the level-L Koch snowflake of maximum radius 1 (Sec. 4.3):
+    the equilateral triangle of side sqrt(3) (vertices at angles 90, 210, 330
+    degrees on the unit circle), then at each level k = 1..L one triangle of
+    side sqrt(3)/3^k on the middle third of every boundary edge of the
+    previous level, pointing outward.  Returns one (n_k, 6) array per level
+    (rows v0, v1, v2 counter-clockwise), n_0 = 1, n_k = 3 * 4^(k-1)."""
+    ang = np.pi / 2 + 2 * np.pi / 3 * np.arange(3)
+    P = np.stack([np.cos(ang), np.sin(ang)], 1)
+    out = [np.concatenate([P[0], P[1], P[2]])[None, :]]
+    A, B = P, np.roll(P, -1, axis=0)            # counter-clockwise boundary edges
+    c60, s60 = 0.5, np.sqrt(3.0) / 2.0
+    for _ in range(level):
+        c = A + (B - A) / 3.0
+        d = A + 2.0 * (B - A) / 3.0
+        u = d - c                               # outward apex: u turned 60 degrees clockwise
+        e = c + np.stack([c60 * u[:, 0] + s60 * u[:, 1], -s60 * u[:, 0] + c60 * u[:, 1]], 1)
+        out.append(np.concatenate([c, e, d], 1))
+        A, B = (np.stack([A, c, e, d], 1).reshape(-1, 2), np.stack([c, e, d, B], 1).reshape(-1, 2))
+    return out
+
+
+def koch_families(level, lz, p_max=None):
+    """The level-L snowflake as one TRIANGLES family per construction level,
+    level k with p_k = max(1, ceil(s_k / (0.8 lz))) Gauss-Legendre points per
+    direction, s_k = sqrt(3)/3^k its side (node spacing ~ lz; at lz = 0.01
+    the largest triangle gets p = 217, the value Sec. 4.3 quotes)."""
+    fams = []
+    for k, tri in enumerate(koch_triangles(level)):
+        pk = max(1, int(np.ceil(np.sqrt(3.0) / 3.0 ** k / (0.8 * lz))))
+        if p_max is not None:
+            pk = min(pk, p_max)
+        fams.append({"kind": "triangles", "tri": tri, "p": pk})
+    return fams
+
+
 def random_star_batch(n=32, config_id=5):
     """32 uneven instances of the random smooth aperture: N_i log-uniform in
     [1e5, 2e6] nodes, F_i = 1000 sqrt(N_i / 1e7), a fresh shape each, M_i
