@@ -17,7 +17,8 @@ one batched evaluation of all 64 wavelengths (nodes regenerated).  Metric:
 wavelength sweeps per second.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload star5_F100|starshade_sweep]
+                       [--workload star5_F100|starshade_sweep|randstar_F1000|
+                                   randstar_batch32|koch_L13]
 Under torchrun each rank runs an independent copy (weak scaling, no data
 collective); rank 0 prints one JSON line.
 """
@@ -710,6 +711,159 @@ def run_randstar_reference(args, rank, world, batch):
     print(json.dumps(line), flush=True)
 
 
+KOCH_METRIC = "Fresnel target pts/sec at 1e-6 rel L2 err (Koch snowflake L=13, 1000^2 grid)"
+KOCH_LEVEL, KOCH_LZ = 13, 0.01
+
+
+def _koch_oracle_rate(fams, budget_s):
+    """The oracle as it stands (snowflake rule rebuilt + direct FP64 sum) on a
+    bounded sample of the 1000^2 grid's targets; targets/s."""
+    import oracle
+    from oracle import direct
+    xi, eta = oracle.grid_targets(1000, 1000, 0.003)
+    rng = W.rng(13, 900)
+    t0 = time.perf_counter()
+    oracle.field(fams, KOCH_LZ, 1.0, xi[:16], eta[:16], output="occulter")   # calibration
+    per = max((time.perf_counter() - t0) / 16, 1e-6)
+    m = int(max(16, min(4096, budget_s / per)))
+    idx = rng.choice(len(xi), m, replace=False)
+    t0 = time.perf_counter()
+    oracle.field(fams, KOCH_LZ, 1.0, xi[idx], eta[idx], output="occulter")
+    dt = time.perf_counter() - t0
+    return m / dt, direct.max_threads(), m, dt
+
+
+def run_koch(args, rank, world, local_rank):
+    """Sec. 4.3's snowflake: level 13 (67,108,864 triangles, p = 217 down to 1
+    by level: 67.2M nodes regenerated every step), type 1 to the 1000^2 grid
+    over [-1.5, 1.5)^2 at lz = 0.01, occulter field, FP32 fast mode."""
+    import torch
+    from paper_2010_05978_gb300 import Plan, build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    fams = W.koch_families(KOCH_LEVEL, KOCH_LZ)
+    n_tri = sum(len(f["tri"]) for f in fams)
+    g = W.grid_spec(1000, 1000, 0.003)
+    p = Plan(fams, KOCH_LZ, 1.0, TOL, precision="fp32", grid=g, output="occulter",
+             recompute_nodes=True, sync_status=False)
+    p.set_timing(True)
+    info = p.info()
+    out = torch.empty((1000, 1000), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        p.eval(None, out)
+    torch.cuda.synchronize()
+    p.check()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    step_ms, stage_sum = [], {}
+    for _ in range(args.steps):       # the triangle list (3.2 GB) is larger than L2
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        p.eval(None, out)
+        e.record(stream)
+        e.synchronize()
+        step_ms.append(s.elapsed_time(e))
+        for k, v in p.stage_times().items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    p.check()
+    ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, 1e6, world, dev)
+    h_out = torch.empty((1000, 1000), dtype=torch.complex64, pin_memory=True).numpy()
+    e2e_ms = []
+    for i in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p.eval_host(None, h_out)
+        torch.cuda.synchronize()
+        if i:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    p.check()
+    e2e = 1e6 * world / (statistics.median(e2e_ms) * 1e-3)
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    per = {k: v / args.steps for k, v in stage_sum.items()}
+    N, c64 = info["n_nodes"], 8
+    nf = info["nf1"] * info["nf2"]
+    ab = {"nodes_chirp_count": 48 * n_tri + 24 * N,   # triangle vertices in, records out
+          "spread": 24 * N + nf * c64,
+          "fft_rows": (nf + 1000 * info["nf2"]) * c64,
+          "fft_cols_epilogue": (1000 * info["nf2"] + 1000 * 1000) * c64}
+    dom = max((k for k in per if k in ab), key=lambda k: per[k])
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ab[dom] / (per[dom] * 1e-3) / 1e9,
+            "algorithmic_bytes": ab[dom], "ms_per_launch": per[dom], "peak": peak,
+            "unit": "GB/s", "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
+                           "fallback 6800 GB/s"}
+    roof["frac"] = roof["achieved"] / peak
+    rate, cores, n_s, t_s = _koch_oracle_rate(fams, 10.0)
+    line = {
+        "metric": KOCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "koch_L13: Koch snowflake R=1 level 13 (%d triangles, p=%d..1 by "
+                               "level), lz=0.01, u^oc on 1000x1000 grid h=0.003" % (
+                                   n_tri, fams[0]["p"]),
+                   "nodes": N, "triangles": n_tri, "targets": 1_000_000, "tol": TOL,
+                   "precision": "fp32 spread/fft, double-float node coordinates and phases",
+                   "nodes_recomputed_each_step": True,
+                   "l2": "inputs larger than L2 (triangle list %.1f GB)" % (48 * n_tri / 1e9),
+                   "parallelism": "replicas x%d (independent instances, no collective)" % world},
+        "roofline": roof,
+        "stages_ms_per_step": {k: round(v, 4) for k, v in sorted(per.items())},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d grid targets, snowflake rule rebuilt + direct O(NM) "
+                                   "FP64 sum (eq. faq), %.1f s" % (n_s, t_s)},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(h_out.nbytes)},
+        "gpu_launches": info["launches_per_eval"] * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_koch_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    obuild.build()
+    fams = W.koch_families(KOCH_LEVEL, KOCH_LZ)
+    _koch_oracle_rate(fams, 1.0)
+    vals, last = [], None
+    for _ in range(max(1, args.steps)):
+        last = _koch_oracle_rate(fams, 8.0)
+        vals.append(last[0])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": KOCH_METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e6 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "koch_L13", "targets": 1_000_000},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last[1], "kind": "oracle",
+                             "sample": "%d grid targets per step, snowflake rule rebuilt + direct "
+                                       "O(NM) FP64 sum, %.1f s" % (last[2], last[3])},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,7 +871,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="star5_F100",
-                    choices=["star5_F100", "starshade_sweep", "randstar_F1000", "randstar_batch32"])
+                    choices=["star5_F100", "starshade_sweep", "randstar_F1000", "randstar_batch32",
+                             "koch_L13"])
     ap.add_argument("--lambdas", type=int, default=64,
                     help="starshade_sweep only: wavelengths per sweep (64 is the benchmark; "
                          "fewer for small profiling captures)")
@@ -727,7 +882,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if args.workload in ("randstar_F1000", "randstar_batch32"):
+        if args.workload == "koch_L13":
+            run_koch_reference(args, rank, world)
+        elif args.workload in ("randstar_F1000", "randstar_batch32"):
             run_randstar_reference(args, rank, world, args.workload == "randstar_batch32")
         else:
             (run_sweep_reference if sweep else run_reference)(args, rank, world)
@@ -737,7 +894,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload in ("randstar_F1000", "randstar_batch32"):
+    if args.workload == "koch_L13":
+        run_koch(args, rank, world, local_rank)
+    elif args.workload in ("randstar_F1000", "randstar_batch32"):
         run_randstar(args, rank, world, local_rank, args.workload == "randstar_batch32")
     else:
         (run_sweep if sweep else run_ours)(args, rank, world, local_rank)

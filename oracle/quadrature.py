@@ -181,19 +181,20 @@ def triangle_rule(tri, p, cx=0.0, cy=0.0):
     """p x p areal rule of each triangle (Sec. 4.3): move vertex v0 to the
     origin, discretise the line integral along the opposite edge v1 -> v2
     with p Gauss-Legendre nodes (X_i = v1 + s_i (v2 - v1), tangent weights
-    what_i (v2 - v1)) and apply the dilation rule (eqs. aqnod, aqwei) with p
-    radii.  tri: (n, 6) rows (v0x, v0y, v1x, v1y, v2x, v2y).  Ordered
-    triangle-major, edge node, radius fastest."""
+    what_i (v2 - v1)) and apply the dilation rule (eqs. aqnod, aqwei) with the
+    same p-point rule as radii: x = v0 + alpha_l (X_i - v0),
+    w = alpha_l what_l ((X_i - v0) x tangent_i) = alpha_l what_l what_i (v1 - v0) x (v2 - v1).
+    tri: (n, 6) rows (v0x, v0y, v1x, v1y, v2x, v2y).  Ordered triangle-major,
+    edge node, radius fastest; all triangles at once (numpy broadcasting)."""
     tri = np.asarray(tri, float).reshape(-1, 6)
     s, ws = gauss_legendre(p, 0.0, 1.0)
-    xs, ys, wts = [], [], []
-    for v0x, v0y, v1x, v1y, v2x, v2y in tri:
-        ex, ey = v2x - v1x, v2y - v1y
-        X, Y = v1x + s * ex, v1y + s * ey
-        # the dilation rule about v0 with the edge's line rule
-        x, y, w = dilation_rule(X, Y, ws * ex, ws * ey, p, v0x, v0y)
-        xs.append(x), ys.append(y), wts.append(w)
-    return (cx + np.concatenate(xs), cy + np.concatenate(ys), np.concatenate(wts))
+    v0, v1, v2 = tri[:, 0:2], tri[:, 2:4], tri[:, 4:6]
+    d1, e = v1 - v0, v2 - v1
+    rel = d1[:, None, :] + s[None, :, None] * e[:, None, :]            # X_i - v0: (n, i, 2)
+    cross = (d1[:, 0] * e[:, 1] - d1[:, 1] * e[:, 0])[:, None] * ws[None, :]   # (n, i)
+    pts = v0[:, None, None, :] + s[None, None, :, None] * rel[:, :, None, :]   # (n, i, l, 2)
+    w = cross[:, :, None] * (s * ws)[None, None, :]
+    return cx + pts[..., 0].ravel(), cy + pts[..., 1].ravel(), w.ravel()
 
 
 def family_nodes(fam):

@@ -971,7 +971,52 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     if (!dbl) {
         for (FamilyDev& f : p->fams) {
             const ChirpParams& cp = p->cps[f.prob];
-            if (f.kind == FRESNEL_FAMILY_NODES || f.kind == FRESNEL_FAMILY_TRIANGLES) continue;
+            if (f.kind == FRESNEL_FAMILY_NODES) continue;
+            if (f.kind == FRESNEL_FAMILY_TRIANGLES) {   // double-float triangle tables
+                const int np = f.p;
+                std::vector<double> a(np), aw(np), wp(np);
+                FRES_CK(cudaMemcpyAsync(a.data(), f.gl_m_a, sizeof(double) * np, cudaMemcpyDeviceToHost, p->st));
+                FRES_CK(cudaMemcpyAsync(aw.data(), f.gl_m_aw, sizeof(double) * np, cudaMemcpyDeviceToHost, p->st));
+                FRES_CK(cudaMemcpyAsync(wp.data(), f.gl_p_w, sizeof(double) * np, cudaMemcpyDeviceToHost, p->st));
+                FRES_CK(cudaStreamSynchronize(p->st));
+                std::vector<float> adf(2 * np), awf(np), wpf(np);
+                for (int l = 0; l < np; ++l) {
+                    const dflt d = df_host(a[l]);
+                    adf[2 * l] = d.hi;
+                    adf[2 * l + 1] = d.lo;
+                    awf[l] = (float)aw[l];
+                    wpf[l] = (float)wp[l];
+                }
+                FRES_TRY(dalloc(p, (void**)&f.adf, sizeof(float) * 2 * np));
+                FRES_TRY(dalloc(p, (void**)&f.awf, sizeof(float) * np));
+                FRES_TRY(dalloc(p, (void**)&f.wpf, sizeof(float) * np));
+                FRES_TRY(dalloc(p, (void**)&f.tdf, sizeof(float) * 16 * (size_t)f.n_panels));
+                FRES_CK(cudaMemcpyAsync(f.adf, adf.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice, p->st));
+                FRES_CK(cudaMemcpyAsync(f.awf, awf.data(), sizeof(float) * np, cudaMemcpyHostToDevice, p->st));
+                FRES_CK(cudaMemcpyAsync(f.wpf, wpf.data(), sizeof(float) * np, cudaMemcpyHostToDevice, p->st));
+                const double U1 = cp.type3 ? cp.inv_h1 : (double)cp.nf1 * cp.u1;
+                const double U2 = cp.type3 ? cp.inv_h2 : (double)cp.nf2 * cp.u2;
+                const double G0x = cp.type3 ? -cp.C1 * cp.inv_h1 + 0.5 * cp.nf1 - 0.5 * w
+                                            : cp.sh1 - 0.5 * w;
+                const double G0y = cp.type3 ? -cp.C2 * cp.inv_h2 + 0.5 * cp.nf2 - 0.5 * w
+                                            : cp.sh2 - 0.5 * w;
+                const double tk[5] = {cp.kq, -cp.a1, -cp.a2, U1, U2};
+                for (int k = 0; k < 5; ++k) {
+                    const dflt d = df_host(tk[k]);
+                    f.tk[2 * k] = d.hi;
+                    f.tk[2 * k + 1] = d.lo;
+                }
+                const dflt a0 = df_host(cp.a0), gx = df_host(G0x), gy = df_host(G0y);
+                f.A0[0] = a0.hi;
+                f.A0[1] = a0.lo;
+                f.G0x[0] = gx.hi;
+                f.G0x[1] = gx.lo;
+                f.G0y[0] = gy.hi;
+                f.G0y[1] = gy.lo;
+                launch_boundary(f, cp, p->st);   // the per-triangle tables, once per plan
+                FRES_CK(cudaStreamSynchronize(p->st));
+                continue;
+            }
             if (f.kind == FRESNEL_FAMILY_PETALS) {
                 FRES_TRY(dalloc(p, (void**)&f.ptab, sizeof(float) * 8 * f.n_bdry));
                 FRES_TRY(dalloc(p, (void**)&f.pk, sizeof(float) * 12 * f.n_panels));

@@ -107,6 +107,14 @@ struct FamilyDev {
     float* ptab;
     float* pk;
     float A0[2], G0x[2], G0y[2];
+    // FP32 fast mode, TRIANGLES: per triangle 16 floats: v0 + c, v1 - v0 and
+    // v2 - v1 (x, y of each as hi, lo) and (v1 - v0) x (v2 - v1) in FP32; per
+    // family kq, -a1, -a2 (chirp) and U1, U2 (grid scale) as (hi, lo), with A0
+    // = a0 and G0x, G0y the grid offsets minus w/2, so phase = kq |x|^2 -
+    // a1 x - a2 y + a0 and grid coordinate (minus w/2) = U x + G0.
+    float* tdf;
+    float* wpf;            // the plain Gauss-Legendre weights what_i as FP32
+    float tk[10];
 };
 
 // Everything a node kernel needs to turn (x, y, w) into a record.

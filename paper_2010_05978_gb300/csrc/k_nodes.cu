@@ -349,6 +349,25 @@ __device__ __forceinline__ void node_petal_df(const FamilyDev& f, const ChirpPar
     finish_df(v1, v2, cre, cim, cp, rec + f.offset + j, status, key);
 }
 
+// Double-float table of a triangle family (FP32 fast mode), from its FP64
+// vertices: v0 + c, v1 - v0, v2 - v1 as (hi, lo) pairs and the FP32 cross
+// product (v1 - v0) x (v2 - v1).
+__global__ void k_tri_df_tables(FamilyDev f) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= f.n_panels) return;
+    const double* v = f.params + 6 * t;
+    const double d1x = v[2] - v[0], d1y = v[3] - v[1], ex = v[4] - v[2], ey = v[5] - v[3];
+    float* o = f.tdf + 16 * t;
+    split_store(o + 0, f.cx + v[0]);
+    split_store(o + 2, f.cy + v[1]);
+    split_store(o + 4, d1x);
+    split_store(o + 6, d1y);
+    split_store(o + 8, ex);
+    split_store(o + 10, ey);
+    o[12] = (float)(d1x * ey - d1y * ex);
+    o[13] = o[14] = o[15] = 0.0f;
+}
+
 // Double-float table of a petal family (FP32 fast mode), from its FP64 table.
 __global__ void k_petal_df_tables(FamilyDev f, ChirpParams cp) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -361,6 +380,41 @@ __global__ void k_petal_df_tables(FamilyDev f, ChirpParams cp) {
     split_store(t + 4, R);
     t[6] = (float)f.bc[q];
     t[7] = 0.0f;
+}
+
+// Triangle-union nodes in the double-float form (FP32 fast mode, no FP64
+// per node): x = v0 + alpha_l ((v1 - v0) + s_i (v2 - v1)) with s = alpha the
+// family's Gauss rule on (0, 1), w = alpha_l what_l what_i (v1 - v0) x (v2 - v1)
+// (Sec. 4.3 with eqs. aqnod, aqwei), then the chirp phase and the grid
+// coordinate from the family's double-float constants.
+__device__ __forceinline__ void node_tri_df(const FamilyDev& f, const ChirpParams& cp, long long j,
+                                            NodeRec<float>* rec, unsigned* status, int key[4],
+                                            const ScreenDev& scr) {
+    const unsigned pp = (unsigned)(f.p * f.p);                     // j < 2^30
+    const unsigned t = (unsigned)j / pp, q = (unsigned)j - t * pp;
+    const unsigned i = q / (unsigned)f.p, l = q - i * (unsigned)f.p;
+    const float4* T = reinterpret_cast<const float4*>(f.tdf) + 4 * (size_t)t;
+    const float4 A = T[0], B = T[1], C = T[2];
+    const float cross = T[3].x;
+    const float2 s2 = reinterpret_cast<const float2*>(f.adf)[i];
+    const float2 a2 = reinterpret_cast<const float2*>(f.adf)[l];
+    const dflt s = {s2.x, s2.y}, a = {a2.x, a2.y};
+    const dflt rx = df_add(dflt{B.x, B.y}, df_mul(s, dflt{C.x, C.y}));
+    const dflt ry = df_add(dflt{B.z, B.w}, df_mul(s, dflt{C.z, C.w}));
+    const dflt x = df_add(dflt{A.x, A.y}, df_mul(a, rx));
+    const dflt y = df_add(dflt{A.z, A.w}, df_mul(a, ry));
+    const float w = f.awf[l] * f.wpf[i] * cross;
+    dflt ph = df_mul(dflt{f.tk[0], f.tk[1]}, df_add(df_mul(x, x), df_mul(y, y)));
+    ph = df_add(ph, df_mul(dflt{f.tk[2], f.tk[3]}, x));
+    ph = df_add(ph, df_mul(dflt{f.tk[4], f.tk[5]}, y));
+    ph = df_add(ph, dflt{f.A0[0], f.A0[1]});
+    float sn, cs;
+    sincosf(df_reduce_2pi(ph), &sn, &cs);
+    float cre = w * cs, cim = w * sn;
+    if (scr.n1) apply_screen<float>(scr, cp.screen_k, x.hi, y.hi, cre, cim);
+    const dflt v1 = df_add(df_mul(x, dflt{f.tk[6], f.tk[7]}), dflt{f.G0x[0], f.G0x[1]});
+    const dflt v2 = df_add(df_mul(y, dflt{f.tk[8], f.tk[9]}), dflt{f.G0y[0], f.G0y[1]});
+    finish_df(v1, v2, cre, cim, cp, rec + f.offset + j, status, key);
 }
 
 template <typename T>
@@ -524,6 +578,9 @@ k_nodes(FamTable ft, NodeRec<T>* rec, int* counts, double* dx, double* dy, doubl
             else if (f.ptab && !dx)
                 node_petal_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key,
                               ft.scr);
+            else if (f.tdf && !dx)
+                node_tri_df(f, sm.cp, j, reinterpret_cast<NodeRec<float>*>(rec), status, key,
+                            ft.scr);
             else
                 node_generic<T>(f, sm.cp, j, rec, dx, dy, dw, status, key, ft.scr);
         } else {
@@ -966,6 +1023,8 @@ void launch_boundary(const FamilyDev& f, const ChirpParams& cp, cudaStream_t st)
         k_petal_tables<<<nblk(std::max<long long>(f.n_bdry, f.n_panels), 128), 128, 0, st>>>(f);
     else if (f.kind == FRESNEL_FAMILY_PETALS)
         k_petal_df_tables<<<nblk(f.n_bdry, 128), 128, 0, st>>>(f, cp);
+    else if (f.kind == FRESNEL_FAMILY_TRIANGLES && f.tdf)
+        k_tri_df_tables<<<nblk(f.n_panels, 128), 128, 0, st>>>(f);
 }
 
 template <typename T>
