@@ -72,3 +72,17 @@ def test_triangles_t3_scattered(prec):
     p = plan(fam, 0.05, 1.0, tol, precision=prec, box=(-1.3, 1.3, -1.3, 1.3))
     u = p.eval(torch.tensor(np.stack([xi, eta], 1), device="cuda")).cpu().numpy()
     assert rel_l2(u, ref) <= bar
+
+
+def test_koch_L13_full_size_sampled():
+    """The bench's workload at full size (level 13: 67.1M triangles, 67.2M
+    nodes, FP32 fast mode, 1000^2 grid at lz = 0.01): sampled grid targets
+    against the oracle's direct sum over its own snowflake rule."""
+    fams = W.koch_families(13, 0.01)
+    g = W.grid_spec(1000, 1000, 0.003)
+    u = plan(fams, 0.01, 1.0, 1e-6, precision="fp32", grid=g, output="occulter",
+             recompute_nodes=True).eval().cpu().numpy().ravel()
+    xi, eta = oracle.grid_targets(1000, 1000, 0.003)
+    sel = W.rng(48, 0).choice(1_000_000, 12, replace=False)
+    ref = oracle.field(fams, 0.01, 1.0, xi[sel], eta[sel], output="occulter")
+    assert rel_l2(u[sel], ref) <= 1e-6
