@@ -1132,6 +1132,19 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     FRES_CK(cudaMemcpyAsync(hc.data(), p->counts, sizeof(int) * tt, cudaMemcpyDeviceToHost, p->st));
     FRES_CK(cudaStreamSynchronize(p->st));
     FRES_CK(cudaGetLastError());
+    // chunk cap: tiles with more records are split into chunks that run in
+    // parallel and add into the tile with global atomics.  A cap of about the
+    // records per eight chunks per resident spreading block keeps the load
+    // balanced; when every tile is heavily loaded (N >> nf1 nf2: the Koch
+    // snowflake's 67M nodes on a 2048^2 grid) a larger cap saves most of the
+    // atomic tile additions.  Small plans keep the base cap.
+    {
+        long long total = 0;
+        for (int c : hc) total += c;
+        const long long slots = 152LL * 4 * 8;
+        const long long base = p->chunk_cap;
+        p->chunk_cap = (int)std::max(base, std::min(total / slots, 1LL << 20));
+    }
     // per-problem regions: every problem's split chunks, then its plain tiles
     std::vector<int> sc_off(p->B + 1, 0), pl_off(p->B + 1, 0), st_off(p->B + 1, 0);
     std::vector<long long> rec_off(p->B + 1, 0);
