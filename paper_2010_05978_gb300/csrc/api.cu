@@ -81,6 +81,7 @@ struct Plan {
     int n1 = 0, n2 = 0;
     int ntx = 0, nty = 0, ntiles = 0;
     int chunk_cap = 0, max_chunks = 0, max_split = 0;
+    bool col_dft = false;         // type-1 column pass as a direct DFT over the live rows
     long long n_records = 0;
     int spread_blocks = 0;
     ChirpParams cp{};
@@ -555,7 +556,13 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ca.out_bstride = (long long)p->n2 * p->n1;
         ca.live = p->layout.live;
         ca.nty = p->nty;
-        run_cols<T>(p, ca);
+        if (p->col_dft) {
+            ca.twiddle = p->d2.tw;
+            launch_col_dft<T>(ca, p->nf2, p->status, p->st);
+            p->launches++;
+        } else {
+            run_cols<T>(p, ca);
+        }
         ev_record(p, "fft_cols_epilogue");
     } else {
         RowPassArgs ra{};
@@ -1153,12 +1160,16 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     const bool prune = p->tkind == FRESNEL_GRID && !p->d1.big && !p->d2.big;
     if (prune && p->nty > kMaxTileRows)
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "spreading grid too tall");
+    int max_live_rows = 0;   // live tile rows of the fullest problem
     for (int b = 0; b < p->B; ++b) {
         long long nrec = 0, nsc = 0, nsplit = 0, nlive = 0;
         std::vector<char> live(p->nty, prune ? 0 : 1);
         for (int i = 0; i < p->ntiles; ++i)
             if (hc[(size_t)b * p->ntiles + i] > 0) live[i / p->ntx] = 1;
         for (int r = 0; r < p->nty; ++r) nlive += live[r] ? p->ntx : 0;
+        int lr = 0;
+        for (int r = 0; r < p->nty; ++r) lr += live[r] ? 1 : 0;
+        max_live_rows = std::max(max_live_rows, lr);
         for (int i = 0; i < p->ntiles; ++i) {
             const int c = hc[(size_t)b * p->ntiles + i];
             nrec += c;
@@ -1176,6 +1187,14 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         rec_off[b + 1] = rec_off[b] + nrec;
     }
     for (int b = 0; b <= p->B; ++b) pl_off[b] += sc_off[p->B];
+    // narrow live band: the direct column DFT costs R complex multiply-adds
+    // (4 FMA) per kept output, R n2 per column, against ~150 instructions per
+    // point of the nf2-point transform (measured over three radix stages):
+    // direct when R n2 <= 24 nf2 (e.g. one live tile row, 512 of 1024 modes)
+    {
+        const long long R = (long long)kTile * max_live_rows;
+        p->col_dft = prune && R > 0 && R <= kDftMaxRows && R * p->n2 <= 24LL * p->nf2;
+    }
     p->n_records = rec_off[p->B];
     p->max_chunks = pl_off[p->B];
     p->max_split = st_off[p->B];

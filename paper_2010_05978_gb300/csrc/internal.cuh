@@ -346,6 +346,14 @@ template <typename T>
 void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st);
 template <typename T>
 void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st);
+// Type-1 column pass (kFftPlain layout with the output epilogue) as a direct
+// DFT over the live rows only, for grids whose live band is a few tile rows:
+// out[k][c] = sum_{r live} w_n^{k r} in[r][c] over the kept outputs k, with
+// w_n^j from the n-point twiddle table.  Live rows beyond kDftMaxRows set
+// kStatusOverflow.
+constexpr int kDftMaxRows = 128;
+template <typename T>
+void launch_col_dft(const ColPassArgs& a, int n, unsigned* status, cudaStream_t st);
 bool fft_supported(int n, int is_double, int* max_cols);
 // Split of a length beyond one pass into fa * fb (both single-pass), or false.
 bool fft_split(int n, int is_double, int* fa, int* fb);

@@ -192,3 +192,20 @@ def test_random_star_batch32_full_size_sampled():
         ref = oracle.field(q["families"], q["lam"], q["z"], x, y)
         assert rel_l2(got, ref) <= 1e-6
     p.check()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_direct_column_dft_matches_fft_path(prec):
+    """One wavelength of the sweep: its grid has one live tile row, so the
+    column pass is the direct DFT over the live rows; the same plan forced
+    onto the four-step FFT (no row pruning, FFT column pass) gives the same
+    grid."""
+    from paper_2010_05978_gb300 import Plan
+    cfg = W.starshade_sweep(n_lambda=3)
+    q, g = cfg["problems"][1], cfg["grid"]
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    u = Plan(q["families"], q["lam"], q["z"], tol, precision=prec, grid=g,
+             output="occulter").eval().cpu().numpy()
+    v = Plan(q["families"], q["lam"], q["z"], tol, precision=prec, grid=g, output="occulter",
+             fft_split_above=256).eval().cpu().numpy()
+    assert rel_l2(1.0 - u, 1.0 - v) <= (1e-12 if prec == "fp64" else 2e-6)
