@@ -540,8 +540,9 @@ template void launch_fft_cols<double>(const FftPlan&, const ColPassArgs&, cudaSt
 // kept outputs is a small dense product: for problem b, kept output slot kp
 // (natural index k) and column c,
 //   out[kp][c] = sum_{r live} w_n^{k r} in[r][c],
-// i.e. (n_out x R) x (R x ncols) with R live rows.  A block takes a 64 x 64
-// tile of (outputs, columns), stages 32 (FP64: 16) live rows at a time of the input
+// i.e. (n_out x R) x (R x ncols) with R live rows.  A block takes 64
+// columns and up to four 64-output tiles; it stages 32 (FP64: 16) live rows
+// at a time of the input (once for all its tiles when they fit one chunk)
 // and of the twiddle matrix (from the exact n-point table, index k r mod n)
 // in shared memory, and each thread accumulates a 4 x 4 tile (outputs
 // ty + 16 i, columns tx + 16 j: conflict-free shared reads, coalesced stores)
@@ -559,86 +560,97 @@ k_col_dft(ColPassArgs a, int n, unsigned* __restrict__ status) {
     __shared__ C sX[kDftChunk][kDftTile];
     __shared__ C sW[kDftChunk][kDftTile];
     __shared__ int s_rows[kDftMaxRows];
-    __shared__ int s_nr;
+    __shared__ int s_nt;
     const int b = blockIdx.z;
-    const int k0 = blockIdx.y * kDftTile, c0 = blockIdx.x * kDftTile;
+    const int c0 = blockIdx.x * kDftTile;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    if (tid == 0) {   // the problem's live rows (tile rows of kTile), in order
-        int nr = 0;
-        for (int t = 0; t < a.nty; ++t) {
-            if (!a.live[(long long)b * a.nty + t]) continue;
-            for (int i = 0; i < kTile; ++i) {
-                if (nr < kDftMaxRows) s_rows[nr] = t * kTile + i;
-                ++nr;
-            }
-        }
-        if (nr > kDftMaxRows) {
-            atomicOr(status, kStatusOverflow);
-            nr = kDftMaxRows;
-        }
-        s_nr = nr;
-    }
+    // the problem's live tile rows, found in parallel (their order does not
+    // matter: input and twiddles use the same list)
+    if (tid == 0) s_nt = 0;
     __syncthreads();
-    const int R = s_nr;
+    for (int t = tid; t < a.nty; t += blockDim.x)
+        if (a.live[(long long)b * a.nty + t]) {
+            const int q = atomicAdd(&s_nt, 1);
+            if (q < kDftMaxRows / kTile)
+                for (int i = 0; i < kTile; ++i) s_rows[q * kTile + i] = t * kTile + i;
+        }
+    __syncthreads();
+    int R = s_nt * kTile;
+    if (R > kDftMaxRows) {
+        if (tid == 0) atomicOr(status, kStatusOverflow);
+        R = kDftMaxRows;
+    }
     const int len = a.out_len;
     const C* in = (const C*)a.in + (long long)b * a.in_bstride;
     const C* tw = (const C*)a.twiddle;
-    C acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = O::mk(0, 0);
-    for (int r0 = 0; r0 < R; r0 += kDftChunk) {
-        const int rc = min(kDftChunk, R - r0);
-        __syncthreads();   // the previous chunk is consumed
+    C* out = (C*)a.out + (long long)b * a.out_bstride;
+    const C* ax = a.ax ? (const C*)a.ax + (long long)b * a.ncols : nullptr;
+    const C* ay = a.ax ? (const C*)a.ay + (long long)b * len : nullptr;
+    // live rows fitting one chunk are staged once for all the block's output tiles
+    const bool one = R <= kDftChunk;
+    auto stage_x = [&](int r0, int rc) {
         for (int e = tid; e < kDftChunk * kDftTile; e += blockDim.x) {
             const int r = e / kDftTile, c = e % kDftTile, col = c0 + c;
             C x = O::mk(0, 0);
             if (r < rc && col < a.ncols) x = in[(long long)s_rows[r0 + r] * a.ncols + col];
             sX[r][c] = x;
-            // twiddle row r, output kk = c (same index ranges)
-            const int kp = k0 + c;
-            C w = O::mk(0, 0);
-            if (r < rc && kp < len) {
-                const int k = kp >= len / 2 ? kp - len / 2 : kp - len / 2 + n;
-                w = __ldg(&tw[(int)(((long long)k * s_rows[r0 + r]) % n)]);
-            }
-            sW[r][c] = w;
         }
-        __syncthreads();
-        for (int r = 0; r < rc; ++r) {
-            C w[4], x[4];
+    };
+    if (one) stage_x(0, R);
+    const int nkt = (len + kDftTile - 1) / kDftTile;
+    for (int kt = blockIdx.y; kt < nkt; kt += gridDim.y) {
+        const int k0 = kt * kDftTile;
+        C acc[4][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) w[i] = sW[r][ty + 16 * i];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = sX[r][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    acc[i][j].x = fma(w[i].x, x[j].x, fma(-w[i].y, x[j].y, acc[i][j].x));
-                    acc[i][j].y = fma(w[i].x, x[j].y, fma(w[i].y, x[j].x, acc[i][j].y));
+            for (int j = 0; j < 4; ++j) acc[i][j] = O::mk(0, 0);
+        for (int r0 = 0; r0 < R; r0 += kDftChunk) {
+            const int rc = min(kDftChunk, R - r0);
+            __syncthreads();   // the previous tile's or chunk's values are consumed
+            if (!one) stage_x(r0, rc);
+            for (int e = tid; e < kDftChunk * kDftTile; e += blockDim.x) {
+                // twiddle row r, output kk = c
+                const int r = e / kDftTile, c = e % kDftTile, kp = k0 + c;
+                C w = O::mk(0, 0);
+                if (r < rc && kp < len) {
+                    const unsigned k = kp >= len / 2 ? kp - len / 2 : kp - len / 2 + n;
+                    w = __ldg(&tw[(k * (unsigned)s_rows[r0 + r]) % (unsigned)n]);   // < 2^26
                 }
-        }
-    }
-    C* out = (C*)a.out + (long long)b * a.out_bstride;
-    const C* ax = a.ax ? (const C*)a.ax + (long long)b * a.ncols : nullptr;
-    const C* ay = a.ax ? (const C*)a.ay + (long long)b * len : nullptr;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int kp = k0 + ty + 16 * i;
-        if (kp >= len) continue;
-        const C yv = ay ? __ldg(&ay[kp]) : O::mk(1, 0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = c0 + tx + 16 * j;
-            if (col >= a.ncols) continue;
-            C v = acc[i][j];
-            if (ax) {
-                v = O::mul(O::mul(v, __ldg(&ax[col])), yv);
-                if (a.occulter) v = O::mk((T)1 - v.x, -v.y);
+                sW[r][c] = w;
             }
-            out[(long long)kp * a.ncols + col] = v;
+            __syncthreads();
+            for (int r = 0; r < rc; ++r) {
+                C w[4], x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[i] = sW[r][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[j] = sX[r][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        acc[i][j].x = fma(w[i].x, x[j].x, fma(-w[i].y, x[j].y, acc[i][j].x));
+                        acc[i][j].y = fma(w[i].x, x[j].y, fma(w[i].y, x[j].x, acc[i][j].y));
+                    }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kp = k0 + ty + 16 * i;
+            if (kp >= len) continue;
+            const C yv = ay ? __ldg(&ay[kp]) : O::mk(1, 0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int col = c0 + tx + 16 * j;
+                if (col >= a.ncols) continue;
+                C v = acc[i][j];
+                if (ax) {
+                    v = O::mul(O::mul(v, __ldg(&ax[col])), yv);
+                    if (a.occulter) v = O::mk((T)1 - v.x, -v.y);
+                }
+                out[(long long)kp * a.ncols + col] = v;
+            }
         }
     }
 }
@@ -647,8 +659,9 @@ k_col_dft(ColPassArgs a, int n, unsigned* __restrict__ status) {
 
 template <typename T>
 void launch_col_dft(const ColPassArgs& a, int n, unsigned* status, cudaStream_t st) {
-    const dim3 grid((a.ncols + kDftTile - 1) / kDftTile, (a.out_len + kDftTile - 1) / kDftTile,
-                    a.batch > 1 ? a.batch : 1);
+    // each block takes up to four 64-output tiles of its 64 columns
+    const int nkt = (a.out_len + kDftTile - 1) / kDftTile;
+    const dim3 grid((a.ncols + kDftTile - 1) / kDftTile, (nkt + 3) / 4, a.batch > 1 ? a.batch : 1);
     k_col_dft<T><<<grid, 256, 0, st>>>(a, n, status);
 }
 template void launch_col_dft<float>(const ColPassArgs&, int, unsigned*, cudaStream_t);
