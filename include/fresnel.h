@@ -119,6 +119,16 @@ typedef struct {
     const double* params;   /* host */
     long long n_params;
     double cx, cy;
+    /* PETALS only, or NULL: rigid motion of each petal (Sec. 5's perturbed
+     * starshades, second construction), 3 * n_panels values (phi_k, tx_k, ty_k):
+     * petal k's nodes move to c + R(phi_k) (x - c) + (tx_k, ty_k), weights
+     * unchanged, and a signed patch joins its root arc on the disc circle
+     * r = a (angles 2 pi k/n_panels +- pi/n_panels) to the moved base arc:
+     * P(s, t) = (1 - t) root(s) + t M_k(root(s)), weight dP/dt x dP/ds, on a
+     * max(2 p, 16) x 8 Gauss-Legendre rule in (s, t), appended after the
+     * family's nodes (gaps add, overlaps subtract).  HOST array, read during
+     * fresnel_plan.  Not with profile gradients. */
+    const double* motion;
 } fresnel_family;
 
 /* ---------------------------------------------------------------- options */

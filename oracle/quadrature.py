@@ -156,12 +156,52 @@ def starshade_rule(fam):
     r, wr = gauss_legendre(m, a, R)
     t, wt = gauss_legendre(n_p, -np.pi / Np, np.pi / Np)
     A = petal_profile(fam["profile"], a, R, r)
+    motion = fam.get("motion")
+    motion = None if motion is None else np.asarray(motion, float).reshape(Np, 3)
     for k in range(Np):
         theta = A[None, :] * t[:, None] + 2.0 * np.pi * k / Np     # [i, l]
-        xs.append((r[None, :] * np.cos(theta)).ravel())
-        ys.append((r[None, :] * np.sin(theta)).ravel())
+        px = (r[None, :] * np.cos(theta)).ravel()
+        py = (r[None, :] * np.sin(theta)).ravel()
+        if motion is not None:   # rigid motion about the centre, weights unchanged
+            phi, tx, ty = motion[k]
+            px, py = (np.cos(phi) * px - np.sin(phi) * py + tx,
+                      np.sin(phi) * px + np.cos(phi) * py + ty)
+        xs.append(px)
+        ys.append(py)
         ws.append((wt[:, None] * (r * wr * A)[None, :]).ravel())
+    if motion is not None:
+        for k in range(Np):
+            x, y, w = root_arc_patch(a, Np, k, motion[k], max(2 * n_p, 16), 8)
+            xs.append(x)
+            ys.append(y)
+            ws.append(w)
     return cx + np.concatenate(xs), cy + np.concatenate(ys), np.concatenate(ws)
+
+
+def root_arc_patch(a, Np, k, motion, qs, qt):
+    """Sec. 5 (perturbed starshades, second construction): the signed region
+    joining petal k's root arc on the disc circle r = a (angles 2 pi k/Np -
+    pi/Np .. + pi/Np) to its rigidly moved image, as the ruled surface
+    P(s, t) = (1 - t) g(s) + t M(g(s)), g the arc on s in (0, 1), M(x) =
+    R(phi) x + (tx, ty), integrated on a qs x qt Gauss-Legendre product rule
+    with the Jacobian dP/dt x dP/ds (positive where the petal has moved
+    outward, leaving a gap; negative over an overlap).  About the origin;
+    ordered s-major, t fastest."""
+    phi, tx, ty = motion
+    s, ws = gauss_legendre(qs, 0.0, 1.0)
+    t, wt = gauss_legendre(qt, 0.0, 1.0)
+    th = 2.0 * np.pi * (k - 0.5 + s) / Np
+    g = np.stack([a * np.cos(th), a * np.sin(th)], 1)
+    dg = (2.0 * np.pi / Np) * np.stack([-a * np.sin(th), a * np.cos(th)], 1)
+    Rm = np.array([[np.cos(phi), -np.sin(phi)], [np.sin(phi), np.cos(phi)]])
+    Mg = g @ Rm.T + np.array([tx, ty])
+    dMg = dg @ Rm.T
+    P = (1.0 - t)[None, :, None] * g[:, None, :] + t[None, :, None] * Mg[:, None, :]
+    Pt = (Mg - g)[:, None, :]
+    Ps = (1.0 - t)[None, :, None] * dg[:, None, :] + t[None, :, None] * dMg[:, None, :]
+    J = Pt[..., 0] * Ps[..., 1] - Pt[..., 1] * Ps[..., 0]
+    w = ws[:, None] * wt[None, :] * J
+    return P[..., 0].ravel(), P[..., 1].ravel(), w.ravel()
 
 
 def family_line_rule(fam):

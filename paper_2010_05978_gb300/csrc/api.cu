@@ -319,6 +319,15 @@ fresnel_status validate_family(const fresnel_family& f, long long* n_bdry, long 
             return fres_fail(FRESNEL_ERR_ARG, "family params contain a non-finite value");
     if (!std::isfinite(f.cx) || !std::isfinite(f.cy))
         return fres_fail(FRESNEL_ERR_ARG, "family centre not finite");
+    if (f.motion) {
+        if (f.kind != FRESNEL_FAMILY_PETALS)
+            return fres_fail(FRESNEL_ERR_ARG, "a motion is for PETALS families only");
+        if (f.n_panels < 1 || f.n_panels > 65536)
+            return fres_fail(FRESNEL_ERR_ARG, "PETALS family needs 1<=n_panels<=65536");
+        for (long long i = 0; i < 3LL * f.n_panels; ++i)
+            if (!std::isfinite(f.motion[i]))
+                return fres_fail(FRESNEL_ERR_ARG, "petal motion contains a non-finite value");
+    }
     switch (f.kind) {
         case FRESNEL_FAMILY_FOURIER:
             if (f.n_panels < 1 || f.p < 1 || f.m < 1 || f.p > 4096 || f.m > 65536)
@@ -770,12 +779,79 @@ fresnel_status setup_petal_family(Plan* p, FamilyDev& f, const fresnel_family& h
                             cudaMemcpyDeviceToHost, p->st));
     FRES_CK(cudaStreamSynchronize(p->st));
     FRES_CK(cudaGetLastError());
+    std::vector<double> sh(2 * f.n_panels, 0.0);
+    if (hf.motion) {   // rigid motions: rotation folded into rot, translation kept apart
+        for (int k = 0; k < f.n_panels; ++k) {
+            const double phi = hf.motion[3 * k], c = rot[2 * k], s = rot[2 * k + 1];
+            const double cp = std::cos(phi), sp = std::sin(phi);
+            rot[2 * k] = c * cp - s * sp;
+            rot[2 * k + 1] = s * cp + c * sp;
+            sh[2 * k] = hf.motion[3 * k + 1];
+            sh[2 * k + 1] = hf.motion[3 * k + 2];
+        }
+        FRES_TRY(dalloc(p, (void**)&f.shift, sizeof(double) * 2 * f.n_panels));
+        FRES_CK(cudaMemcpyAsync(f.rot, rot.data(), sizeof(double) * 2 * f.n_panels,
+                                cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaMemcpyAsync(f.shift, sh.data(), sizeof(double) * 2 * f.n_panels,
+                                cudaMemcpyHostToDevice, p->st));
+        FRES_CK(cudaStreamSynchronize(p->st));
+    }
     for (long long q = 0; q < nb; ++q) {
         if (!std::isfinite(u[q]) || !std::isfinite(v[q]))
             return fres_fail(FRESNEL_ERR_ARG, "petal profile gives a non-finite node");
         for (int k = 0; k < f.n_panels; ++k) {
             const double c = rot[2 * k], s = rot[2 * k + 1];
-            bb.add(f.cx + u[q] * c - v[q] * s, f.cy + u[q] * s + v[q] * c);
+            bb.add(f.cx + sh[2 * k] + u[q] * c - v[q] * s, f.cy + sh[2 * k + 1] + u[q] * s + v[q] * c);
+        }
+    }
+    return FRESNEL_OK;
+}
+
+// Root-arc patches of a starshade with moved petals (Sec. 5, second
+// construction): for petal k the signed region between its root arc on the
+// disc circle, root(s) = c + a (cos, sin)(2 pi k/N - pi/N + 2 pi s/N), and the
+// moved base arc M_k(root(s)) = c + R(phi_k)(root(s) - c) + t_k, as
+// P(s, t) = (1 - t) root(s) + t M_k(root(s)) with weight dP/dt x dP/ds on a
+// qs x qt Gauss-Legendre product rule in (s, t).  Returns x..., y..., w...
+// (FP64, host) for an explicit-node family.
+fresnel_status petal_patches(Plan* p, const fresnel_family& hf, std::vector<double>* out) {
+    const int N = hf.n_panels, qs = std::max(2 * hf.p, 16), qt = 8;
+    const double a = hf.params[0];
+    double* d = nullptr;
+    FRES_TRY(dalloc(p, (void**)&d, sizeof(double) * 2 * (qs + qt)));
+    launch_gauss_legendre(qs, d, d + qs, p->st);
+    launch_gauss_legendre(qt, d + 2 * qs, d + 2 * qs + qt, p->st);
+    std::vector<double> g(2 * (qs + qt));
+    FRES_CK(cudaMemcpyAsync(g.data(), d, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, p->st));
+    FRES_CK(cudaStreamSynchronize(p->st));
+    const double* ss = g.data();
+    const double* ws = g.data() + qs;
+    const double* tt = g.data() + 2 * qs;
+    const double* wt = g.data() + 2 * qs + qt;
+    const long long np = (long long)N * qs * qt;
+    out->assign(3 * np, 0.0);
+    double* X = out->data();
+    double* Y = X + np;
+    double* Wt = Y + np;
+    long long j = 0;
+    for (int k = 0; k < N; ++k) {
+        const double phi = hf.motion[3 * k], tx = hf.motion[3 * k + 1], ty = hf.motion[3 * k + 2];
+        const double cp = std::cos(phi), sp = std::sin(phi);
+        for (int i = 0; i < qs; ++i) {
+            const double th = kTwoPi * (k - 0.5 + ss[i]) / N;
+            const double rx = a * std::cos(th), ry = a * std::sin(th);          // root - c
+            const double dx = -a * std::sin(th) * kTwoPi / N, dy = a * std::cos(th) * kTwoPi / N;
+            const double mx = rx * cp - ry * sp + tx, my = rx * sp + ry * cp + ty;   // M - c
+            const double mdx = dx * cp - dy * sp, mdy = dx * sp + dy * cp;
+            const double ptx = mx - rx, pty = my - ry;                             // dP/dt
+            for (int l = 0; l < qt; ++l) {
+                const double t = tt[l];
+                const double psx = (1.0 - t) * dx + t * mdx, psy = (1.0 - t) * dy + t * mdy;
+                X[j] = hf.cx + (1.0 - t) * rx + t * mx;
+                Y[j] = hf.cy + (1.0 - t) * ry + t * my;
+                Wt[j] = ws[i] * wt[l] * (ptx * psy - pty * psx);
+                ++j;
+            }
         }
     }
     return FRESNEL_OK;
@@ -835,6 +911,20 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
             f.offset = off;
             off += nn;
             FRES_TRY(setup_petal_family(p, f, hf, bb));
+            if (hf.motion) {   // root-arc patches, after the petals
+                std::vector<double> pp;
+                FRES_TRY(petal_patches(p, hf, &pp));
+                FamilyDev pf{};
+                pf.prob = pb;
+                pf.kind = FRESNEL_FAMILY_NODES;
+                pf.n_nodes = (long long)pp.size() / 3;
+                p->fams.push_back(f);
+                pf.offset = off;
+                off += pf.n_nodes;
+                FRES_TRY(setup_nodes_family<T>(p, pf, pp.data(), (long long)pp.size(), bb));
+                p->fams.push_back(pf);
+                continue;
+            }
         } else {
             f.offset = off;
             off += nn;
@@ -1024,35 +1114,6 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
                 FRES_CK(cudaStreamSynchronize(p->st));
                 continue;
             }
-            if (f.kind == FRESNEL_FAMILY_PETALS) {
-                FRES_TRY(dalloc(p, (void**)&f.ptab, sizeof(float) * 8 * f.n_bdry));
-                FRES_TRY(dalloc(p, (void**)&f.pk, sizeof(float) * 12 * f.n_panels));
-                // per-petal slopes: phase E.d with E = 2 kq c - a, grid U d
-                std::vector<double> rot(2 * f.n_panels);
-                FRES_CK(cudaMemcpyAsync(rot.data(), f.rot, sizeof(double) * 2 * f.n_panels,
-                                        cudaMemcpyDeviceToHost, p->st));
-                FRES_CK(cudaStreamSynchronize(p->st));
-                const double E1 = 2.0 * cp.kq * f.cx - cp.a1, E2 = 2.0 * cp.kq * f.cy - cp.a2;
-                const double U1 = cp.type3 ? cp.inv_h1 : (double)cp.nf1 * cp.u1;
-                const double U2 = cp.type3 ? cp.inv_h2 : (double)cp.nf2 * cp.u2;
-                std::vector<float> pk(12 * f.n_panels);
-                for (int k = 0; k < f.n_panels; ++k) {
-                    const double c = rot[2 * k], sn = rot[2 * k + 1];
-                    const double vals[6] = {c * E1 + sn * E2, c * E2 - sn * E1, c * U1,
-                                            -sn * U1, sn * U2, c * U2};
-                    for (int v = 0; v < 6; ++v) {
-                        const dflt d = df_host(vals[v]);
-                        pk[12 * k + 2 * v] = d.hi;
-                        pk[12 * k + 2 * v + 1] = d.lo;
-                    }
-                }
-                FRES_CK(cudaMemcpyAsync(f.pk, pk.data(), sizeof(float) * 12 * f.n_panels,
-                                        cudaMemcpyHostToDevice, p->st));
-                FRES_CK(cudaStreamSynchronize(p->st));
-            } else {
-                FRES_TRY(dalloc(p, (void**)&f.spoke, sizeof(float) * 8 * f.n_bdry));
-                FRES_TRY(dalloc(p, (void**)&f.bcf, sizeof(float) * f.n_bdry));
-            }
             const double A0 = cp.kq * (f.cx * f.cx + f.cy * f.cy) - cp.a1 * f.cx - cp.a2 * f.cy + cp.a0;
             double G0x, G0y;
             if (!cp.type3) {
@@ -1061,6 +1122,44 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
             } else {
                 G0x = (f.cx - cp.C1) * cp.inv_h1 + 0.5 * cp.nf1 - 0.5 * w;
                 G0y = (f.cy - cp.C2) * cp.inv_h2 + 0.5 * cp.nf2 - 0.5 * w;
+            }
+            if (f.kind == FRESNEL_FAMILY_PETALS) {
+                FRES_TRY(dalloc(p, (void**)&f.ptab, sizeof(float) * 8 * f.n_bdry));
+                FRES_TRY(dalloc(p, (void**)&f.pk, sizeof(float) * kPetalK * f.n_panels));
+                // per petal: phase slopes E.d with E = 2 kq c_k - a, grid slopes
+                // U d, and the constants at the petal's own centre c_k = c + t_k
+                std::vector<double> rot(2 * f.n_panels), sh(2 * f.n_panels, 0.0);
+                FRES_CK(cudaMemcpyAsync(rot.data(), f.rot, sizeof(double) * 2 * f.n_panels,
+                                        cudaMemcpyDeviceToHost, p->st));
+                if (f.shift)
+                    FRES_CK(cudaMemcpyAsync(sh.data(), f.shift, sizeof(double) * 2 * f.n_panels,
+                                            cudaMemcpyDeviceToHost, p->st));
+                FRES_CK(cudaStreamSynchronize(p->st));
+                const double U1 = cp.type3 ? cp.inv_h1 : (double)cp.nf1 * cp.u1;
+                const double U2 = cp.type3 ? cp.inv_h2 : (double)cp.nf2 * cp.u2;
+                std::vector<float> pk(kPetalK * f.n_panels);
+                for (int k = 0; k < f.n_panels; ++k) {
+                    const double c = rot[2 * k], sn = rot[2 * k + 1];
+                    const double tx = sh[2 * k], ty = sh[2 * k + 1];
+                    const double ckx = f.cx + tx, cky = f.cy + ty;
+                    const double E1 = 2.0 * cp.kq * ckx - cp.a1, E2 = 2.0 * cp.kq * cky - cp.a2;
+                    const double vals[9] = {c * E1 + sn * E2, c * E2 - sn * E1, c * U1, -sn * U1,
+                                            sn * U2, c * U2,
+                                            cp.kq * (ckx * ckx + cky * cky) - cp.a1 * ckx -
+                                                cp.a2 * cky + cp.a0,
+                                            G0x + U1 * tx, G0y + U2 * ty};
+                    for (int v = 0; v < 9; ++v) {
+                        const dflt d = df_host(vals[v]);
+                        pk[kPetalK * k + 2 * v] = d.hi;
+                        pk[kPetalK * k + 2 * v + 1] = d.lo;
+                    }
+                }
+                FRES_CK(cudaMemcpyAsync(f.pk, pk.data(), sizeof(float) * kPetalK * f.n_panels,
+                                        cudaMemcpyHostToDevice, p->st));
+                FRES_CK(cudaStreamSynchronize(p->st));
+            } else {
+                FRES_TRY(dalloc(p, (void**)&f.spoke, sizeof(float) * 8 * f.n_bdry));
+                FRES_TRY(dalloc(p, (void**)&f.bcf, sizeof(float) * f.n_bdry));
             }
             const dflt a0 = df_host(A0), gx = df_host(G0x), gy = df_host(G0y);
             f.A0[0] = a0.hi;
@@ -1601,6 +1700,9 @@ fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, do
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients need a GRID plan");
     bool any = false;
     for (const FamilyDev& f : p->fams) any = any || f.kind == FRESNEL_FAMILY_PETALS;
+    for (const FamilyDev& f : p->fams)
+        if (f.shift)
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients do not take moved petals");
     if (!any) return fres_fail(FRESNEL_ERR_ARG, "the plan has no PETALS family");
     if (p->d1.big || p->d2.big)
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients need single-pass FFT lengths");

@@ -101,11 +101,13 @@ struct FamilyDev {
     float* awf;            // alpha_l wtilde_l as FP32
     // FP32 fast mode, PETALS: per table entry (i, l) 8 floats: u, v, the
     // phase kq r_l^2 mod 2 pi (each hi, lo), the weight, a pad; per petal k
-    // 12 floats: phase slopes P, Q and grid-coordinate slopes G1u, G1v, G2u,
-    // G2v (each hi, lo), so that phase = A0 + R + u P + v Q and grid
-    // coordinate (minus w/2) = G0 + u Gu + v Gv.
+    // 18 floats: phase slopes P, Q and grid-coordinate slopes G1u, G1v, G2u,
+    // G2v, then the petal's A0, G0x, G0y (each hi, lo), so that phase =
+    // A0_k + R + u P + v Q and grid coordinate (minus w/2) = G0_k + u Gu + v Gv
+    // (the constants differ between petals only when the petals are moved).
     float* ptab;
-    float* pk;
+    float* pk;             // kPetalK floats per petal: the 12 slopes, then its A0, G0x, G0y
+    double* shift;         // PETALS with a motion: per petal translation (tx, ty), else NULL
     float A0[2], G0x[2], G0y[2];
     // FP32 fast mode, TRIANGLES: per triangle 16 floats: v0 + c, v1 - v0 and
     // v2 - v1 (x, y of each as hi, lo) and (v1 - v0) x (v2 - v1) in FP32; per
@@ -116,6 +118,8 @@ struct FamilyDev {
     float* wpf;            // the plain Gauss-Legendre weights what_i as FP32
     float tk[10];
 };
+
+constexpr int kPetalK = 18;   // floats per petal in FamilyDev::pk
 
 // Everything a node kernel needs to turn (x, y, w) into a record.
 struct ChirpParams {

@@ -329,21 +329,25 @@ __device__ __forceinline__ void node_petal_df(const FamilyDev& f, const ChirpPar
     const float4 t0 = reinterpret_cast<const float4*>(f.ptab)[2 * q];
     const float4 t1 = reinterpret_cast<const float4*>(f.ptab)[2 * q + 1];
     const dflt u = {t0.x, t0.y}, v = {t0.z, t0.w};
-    const float* K = f.pk + 12 * k;
+    const float* K = f.pk + kPetalK * k;   // slopes, then the petal's own A0, G0x, G0y
     dflt ph = df_add(df_mul(u, dflt{K[0], K[1]}), df_mul(v, dflt{K[2], K[3]}));
-    ph = df_add(ph, df_add(dflt{t1.x, t1.y}, dflt{f.A0[0], f.A0[1]}));
+    ph = df_add(ph, df_add(dflt{t1.x, t1.y}, dflt{K[12], K[13]}));
     const float phr = df_reduce_2pi(ph);
     float sn, cs;
     sincosf(phr, &sn, &cs);
     dflt v1 = df_add(df_add(df_mul(u, dflt{K[4], K[5]}), df_mul(v, dflt{K[6], K[7]})),
-                     dflt{f.G0x[0], f.G0x[1]});
+                     dflt{K[14], K[15]});
     dflt v2 = df_add(df_add(df_mul(u, dflt{K[8], K[9]}), df_mul(v, dflt{K[10], K[11]})),
-                     dflt{f.G0y[0], f.G0y[1]});
+                     dflt{K[16], K[17]});
     float cre = t1.z * cs, cim = t1.z * sn;
-    if (scr.n1) {   // the node itself: petal 0's (u, v) rotated to petal k, in FP32
+    if (scr.n1) {   // the node itself: petal 0's (u, v) moved to petal k, in FP32
         const float c = (float)f.rot[2 * k], sr = (float)f.rot[2 * k + 1];
-        const float x = (float)f.cx + (u.hi * c - v.hi * sr);
-        const float y = (float)f.cy + (u.hi * sr + v.hi * c);
+        float x = (float)f.cx + (u.hi * c - v.hi * sr);
+        float y = (float)f.cy + (u.hi * sr + v.hi * c);
+        if (f.shift) {
+            x += (float)f.shift[2 * k];
+            y += (float)f.shift[2 * k + 1];
+        }
         apply_screen<float>(scr, cp.screen_k, x, y, cre, cim);
     }
     finish_df(v1, v2, cre, cim, cp, rec + f.offset + j, status, key);
@@ -447,6 +451,10 @@ __device__ __forceinline__ void node_generic(const FamilyDev& f, const ChirpPara
         const double c = f.rot[2 * k], s = f.rot[2 * k + 1];
         x = f.cx + (u * c - v * s);
         y = f.cy + (u * s + v * c);
+        if (f.shift) {   // a rigidly moved petal (rotation folded into rot)
+            x += f.shift[2 * k];
+            y += f.shift[2 * k + 1];
+        }
         w = f.bc[q];
     } else {
         const unsigned i = (unsigned)j / (unsigned)f.m;   // j < 2^30

@@ -36,7 +36,8 @@ class FresnelError(RuntimeError):
 class Family(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n_panels", ctypes.c_int), ("p", ctypes.c_int),
                 ("m", ctypes.c_int), ("params", ctypes.POINTER(ctypes.c_double)),
-                ("n_params", ctypes.c_longlong), ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+                ("n_params", ctypes.c_longlong), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("motion", ctypes.POINTER(ctypes.c_double))]
 
 
 class Problem(ctypes.Structure):
@@ -178,9 +179,14 @@ def _family_array(families):
     for i, f in enumerate(families):
         kind, npan, p, m, params, cx, cy = family_params(f)
         keep.append(params)
+        motion = None
+        if f.get("motion") is not None:   # petals: (n_petals, 3) rows phi, tx, ty
+            mo = np.ascontiguousarray(np.asarray(f["motion"], np.float64).ravel())
+            keep.append(mo)
+            motion = mo.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         fams[i] = Family(kind, int(npan), int(p), int(m),
                          params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         len(params), float(cx), float(cy))
+                         len(params), float(cx), float(cy), motion)
     return fams, keep
 
 

@@ -111,3 +111,51 @@ def test_starshade_bspline_profile_off_centre_t1(prec):
     tol, bar = BARS[prec]
     u = plan(fam, lz, 1.0, tol, precision=prec, grid=g).eval().cpu().numpy()
     assert rel_l2(u, ref) <= bar
+
+
+def _moved_starshade():
+    """A 6-petal starshade with seeded small rigid motions of every petal
+    (Sec. 5: perturbed starshades, moved petals plus root-arc patches)."""
+    fam = W.petal_family(6, 0.4, 1.0, {"kind": "hg", "b": 0.5, "q": 2.5}, 40, 20, 64, 24,
+                         cx=0.03, cy=-0.02)
+    g = W.rng(61, 0)
+    motion = np.column_stack([g.normal(0, 0.01, 6), g.normal(0, 0.006, 6), g.normal(0, 0.006, 6)])
+    return dict(fam, motion=motion)
+
+
+def test_moved_petal_nodes_match_oracle():
+    fam = _moved_starshade()
+    p = plan([fam], 0.05, 1.0, 1e-12, precision="fp64", grid=W.grid_spec(64, 64, 0.04))
+    x, y, w = (t.cpu().numpy() for t in p.nodes())
+    ox, oy, ow = Q.family_nodes(fam)
+    assert len(x) == len(ox)
+    assert np.max(np.abs(x - ox)) < 5e-15 and np.max(np.abs(y - oy)) < 5e-15
+    assert np.max(np.abs(w - ow)) < 1e-15
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_moved_petals_field(prec):
+    fam = [_moved_starshade()]
+    tol, bar = BARS[prec]
+    g = W.grid_spec(96, 96, 0.025)
+    xi, eta = oracle.grid_targets(96, 96, 0.025)
+    ref = oracle.field(fam, 0.05, 1.0, xi, eta, output="occulter").reshape(96, 96)
+    u = plan(fam, 0.05, 1.0, tol, precision=prec, grid=g, output="occulter").eval()
+    assert rel_l2(u.cpu().numpy(), ref) <= bar
+    xs, es = W.disc_targets(2000, 1.2, 62)
+    ref3 = oracle.field(fam, 0.05, 1.0, xs, es)
+    p3 = plan(fam, 0.05, 1.0, tol, precision=prec, box=(-1.2, 1.2, -1.2, 1.2))
+    u3 = p3.eval(torch.tensor(np.stack([xs, es], 1), device="cuda")).cpu().numpy()
+    assert rel_l2(u3, ref3) <= bar
+
+
+def test_moved_petals_rejected_by_profile_gradients():
+    from paper_2010_05978_gb300 import FresnelError
+    fam = W.petal_family(6, 0.4, 1.0, {"kind": "bspline", "coefs": np.full(8, 0.6)}, 12, 8)
+    fam = dict(fam, motion=np.zeros((6, 3)))
+    p = plan([fam], 0.05, 1.0, 1e-12, precision="fp64", grid=W.grid_spec(32, 32, 0.05))
+    with pytest.raises(FresnelError):
+        p.grad_profile(torch.ones((32, 32), dtype=torch.complex128, device="cuda"))
+    with pytest.raises(FresnelError):   # a motion on a non-petal family
+        plan([dict(W.fourier_family([1.0], 16, 8, 8), motion=np.zeros((16, 3)))], 0.05, 1.0,
+             1e-6, grid=W.grid_spec(32, 32, 0.05))

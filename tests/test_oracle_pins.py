@@ -643,3 +643,48 @@ def test_triangle_rule_matches_polygon_line_rule():
     u1 = oracle.field([{"kind": "triangles", "tri": tri, "p": 60}], 0.25, 1.0, xi, eta)
     u2 = oracle.field([line], 0.25, 1.0, xi, eta)
     assert np.max(np.abs(u1 - u2)) < 1e-11
+
+
+# ------------------------------------------------------------------ perturbed starshades (Sec. 5)
+def _resolved_starshade(**kw):
+    return W.petal_family(6, 0.4, 1.0, {"kind": "hg", "b": 0.5, "q": 2.5}, 48, 24, 96, 32, **kw)
+
+
+def test_moved_petals_zero_motion_is_the_ideal_rule():
+    fam = _resolved_starshade()
+    x0, y0, w0 = Q.family_nodes(fam)
+    x, y, w = Q.family_nodes(dict(fam, motion=np.zeros((6, 3))))
+    n = len(x0)
+    assert np.array_equal(x[:n], x0) and np.array_equal(y[:n], y0) and np.array_equal(w[:n], w0)
+    assert len(x) == n + 6 * 48 * 8 and np.all(w[n:] == 0.0)
+
+
+def test_moved_petals_common_translation_is_the_translated_starshade():
+    """Every petal translated by the same T: the root-arc patches sweep the
+    disc circle into its translate (adjacent patch sides cancel), so the
+    construction equals the ideal starshade centred at T."""
+    T = (0.013, -0.021)
+    fam = _resolved_starshade()
+    moved = dict(fam, motion=np.tile([0.0, T[0], T[1]], (6, 1)))
+    xi, eta = W.disc_targets(30, 1.0, 60)
+    u1 = oracle.field([moved], 0.1, 1.0, xi, eta)
+    u2 = oracle.field([dict(fam, cx=T[0], cy=T[1])], 0.1, 1.0, xi, eta)
+    assert np.max(np.abs(u1 - u2)) < 1e-11
+
+
+def test_root_arc_patch_areas():
+    """Pure translation T: the patch is the arc swept by T, signed area
+    T x (g(1) - g(0)) (its chord); pure rotation about the centre: the two
+    end segments cancel, area 0 (so rotations keep the starshade's area)."""
+    a, Np = 0.4, 6
+    for k in range(Np):
+        th0, th1 = 2 * np.pi * (k - 0.5) / Np, 2 * np.pi * (k + 0.5) / Np
+        ch = a * np.array([np.cos(th1) - np.cos(th0), np.sin(th1) - np.sin(th0)])
+        T = np.array([0.02 * np.cos(k), -0.015 + 0.003 * k])
+        w = Q.root_arc_patch(a, Np, k, (0.0, T[0], T[1]), 24, 8)[2]
+        assert abs(w.sum() - (T[0] * ch[1] - T[1] * ch[0])) < 1e-15
+        w = Q.root_arc_patch(a, Np, k, (0.01 * (k - 2), 0.0, 0.0), 24, 8)[2]
+        assert abs(w.sum()) < 1e-15
+    fam = _resolved_starshade()
+    rot = np.column_stack([0.01 * np.arange(6) - 0.02, np.zeros(6), np.zeros(6)])
+    assert abs(Q.family_nodes(dict(fam, motion=rot))[2].sum() - Q.family_nodes(fam)[2].sum()) < 1e-13
