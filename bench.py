@@ -89,48 +89,87 @@ def config_dict(cfg, n_gpus):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi sampling (every 100 ms) of SM clocks and throttle reasons
-    while the timed region runs."""
+    """nvidia-smi sampling (every 20 ms) of SM clocks and throttle reasons
+    while the timed region runs.
+
+    A reader thread timestamps each line as it arrives.  `start` returns once
+    the first sample is in (so sampling is live when the timed region opens)
+    and marks the region's start; `stop` marks its end, waits for one more
+    sample and keeps the samples taken inside the region, plus the one just
+    before it (a timed region shorter than the sampling period would
+    otherwise hold none)."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
-    def __init__(self, index):
+    def __init__(self, index, argv=None):
         self.index = index
+        self.argv = argv or ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.QUERY,
+                             "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)]
         self.samples = []
+        self._lines = []               # (monotonic time, fields)
         self._p = None
+        self._t = None
+        self._t0 = self._t1 = None
+
+    def _read(self):
+        for line in self._p.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 7:
+                self._lines.append((time.monotonic(), f))
+
+    def _wait_for(self, n, timeout):
+        t_end = time.monotonic() + timeout
+        while len(self._lines) < n and time.monotonic() < t_end and self._t.is_alive():
+            time.sleep(0.002)
 
     def start(self):
+        import threading
         try:
-            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
-                                        "--query-gpu=" + self.QUERY,
-                                        "--format=csv,noheader,nounits", "-lms", "100"],
-                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._p = subprocess.Popen(self.argv, stdout=subprocess.PIPE,
+                                       stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self._p = None
+        if self._p is not None:
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            self._wait_for(1, 5.0)
+        self._t0 = time.monotonic()
 
     def stop(self):
+        self._t1 = time.monotonic()
         if self._p is not None:
+            n_in = sum(1 for t, _ in self._lines if t <= self._t1)
+            self._wait_for(n_in + 1, 1.0)
             self._p.terminate()
             try:
-                out, _ = self._p.communicate(timeout=10)
+                self._p.wait(timeout=10)
             except Exception:
                 self._p.kill()
-                out, _ = self._p.communicate()
-            for line in out.splitlines():
-                f = [s.strip() for s in line.split(",")]
-                if len(f) >= 7:
-                    self.samples.append(f)
+                self._p.wait()
+            self._t.join(timeout=5)
+            before = [f for t, f in self._lines if t < self._t0][-1:]
+            inside = [f for t, f in self._lines if self._t0 <= t <= self._t1]
+            after = [f for t, f in self._lines if t > self._t1][:1]
+            # the samples bracketing the region when none fell inside it
+            self.samples = before + inside if inside else before + after
+        return self.summary(self._t1 - self._t0)
+
+    def summary(self, region_s=None):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
         mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None,
+               "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+               "samples": len(self.samples), "period_ms": self.PERIOD_MS}
+        if region_s is not None:
+            out["timed_region_s"] = round(region_s, 4)
+        return out
 
 
 # ------------------------------------------------------------------ CPU oracle timing

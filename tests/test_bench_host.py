@@ -1,0 +1,57 @@
+"""CPU tests of bench.py's host-side helpers: the clock sampler's bookkeeping
+(driven by a stand-in for nvidia-smi that prints CSV rows every 20 ms)."""
+import sys
+import time
+
+import pytest
+
+pytest.importorskip("torch")
+import bench  # noqa: E402
+
+FAKE = ("import sys, time\n"
+        "i = 0\n"
+        "while True:\n"
+        "    r = 'Active' if i == {throttle} else 'Not Active'\n"
+        "    print('0, %d, 2070, Not Active, %s, Not Active, Not Active' % (1900 + i, r), flush=True)\n"
+        "    i += 1\n"
+        "    time.sleep(0.02)\n")
+
+
+def _sampler(throttle=-1):
+    return bench.ClockSampler(0, argv=[sys.executable, "-c", FAKE.format(throttle=throttle)])
+
+
+def test_clock_sampler_keeps_samples_of_the_timed_region():
+    c = _sampler()
+    c.start()
+    assert c._lines, "start returns only once sampling is live"
+    time.sleep(0.2)
+    out = c.stop()
+    # ~10 samples inside a 200 ms region, plus the one before it
+    assert 6 <= out["samples"] <= 14
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == []
+    assert out["timed_region_s"] == pytest.approx(0.2, abs=0.05)
+    assert 1900 <= out["sm_mhz"] <= 1900 + 30
+
+
+def test_clock_sampler_short_region_brackets_it():
+    c = _sampler()
+    c.start()
+    out = c.stop()                   # a region far shorter than the period
+    assert 1 <= out["samples"] <= 2
+    assert out["sm_mhz"] is not None
+
+
+def test_clock_sampler_reports_throttle_reasons():
+    c = _sampler(throttle=0)         # the first sample shows hw_thermal_slowdown
+    c.start()
+    time.sleep(0.1)
+    out = c.stop()
+    assert out["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_clock_sampler_without_nvidia_smi():
+    c = bench.ClockSampler(0, argv=["/nonexistent/nvidia-smi"])
+    c.start()
+    assert c.stop()["reasons"] == ["unsampled"]
