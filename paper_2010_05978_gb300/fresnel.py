@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libfresnel.so")
 FRESNEL_OK = 0
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_TIMEOUT",
                 -5: "ERR_UNSUPPORTED", -6: "ERR_DEVICE"}
-FAMILY_KINDS = {"fourier": 0, "line_rule": 1, "nodes": 2, "petals": 3}
+FAMILY_KINDS = {"fourier": 0, "line_rule": 1, "nodes": 2, "petals": 3, "triangles": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 OUTPUTS = {"aperture": 0, "occulter": 1}
 GRID, SCATTERED = 0, 1
