@@ -125,17 +125,26 @@ class ClockSampler:
         while len(self._lines) < n and time.monotonic() < t_end and self._t.is_alive():
             time.sleep(0.002)
 
-    def start(self):
+    def _launch(self, argv):
         import threading
         try:
-            self._p = subprocess.Popen(self.argv, stdout=subprocess.PIPE,
+            self._p = subprocess.Popen(argv, stdout=subprocess.PIPE,
                                        stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self._p = None
-        if self._p is not None:
-            self._t = threading.Thread(target=self._read, daemon=True)
-            self._t.start()
-            self._wait_for(1, 5.0)
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        self._wait_for(1, 5.0)
+
+    def start(self):
+        self._launch(self.argv)
+        if self._p is not None and not self._lines and self._p.poll() is not None:
+            # a sampler that rejected the short period: the common 100 ms one
+            argv = [a if a != str(self.PERIOD_MS) else "100" for a in self.argv]
+            if argv != self.argv:
+                self.PERIOD_MS = 100
+                self._launch(argv)
         self._t0 = time.monotonic()
 
     def stop(self):

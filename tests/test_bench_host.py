@@ -55,3 +55,14 @@ def test_clock_sampler_without_nvidia_smi():
     c = bench.ClockSampler(0, argv=["/nonexistent/nvidia-smi"])
     c.start()
     assert c.stop()["reasons"] == ["unsampled"]
+
+
+def test_clock_sampler_falls_back_to_a_longer_period():
+    # a stand-in that exits at once when asked for a 20 ms period
+    prog = ("import sys, time\n"
+            "if sys.argv[1] == '20': sys.exit(2)\n" + FAKE.format(throttle=-1).split("\n", 1)[1])
+    c = bench.ClockSampler(0, argv=[sys.executable, "-c", prog, "20"])
+    c.start()
+    time.sleep(0.25)
+    out = c.stop()
+    assert out["period_ms"] == 100 and out["samples"] >= 1
