@@ -543,8 +543,8 @@ template void launch_fft_cols<double>(const FftPlan&, const ColPassArgs&, cudaSt
 // i.e. (n_out x R) x (R x ncols) with R live rows.  A block takes 64
 // columns and up to four 64-output tiles; it stages 32 (FP64: 16) live rows
 // at a time of the input (once for all its tiles when they fit one chunk)
-// and of the twiddle matrix (from the exact n-point table, index k r mod n)
-// in shared memory, and each thread accumulates a 4 x 4 tile (outputs
+// and of the twiddle matrix (from the exact n-point table, index k r mod n:
+// a mask for power-of-two n) in shared memory, and each thread accumulates a 4 x 4 tile (outputs
 // ty + 16 i, columns tx + 16 j: conflict-free shared reads, coalesced stores)
 // before the output epilogue of the FFT path.
 namespace {
@@ -553,7 +553,7 @@ constexpr int kDftTile = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_col_dft(ColPassArgs a, int n, unsigned* __restrict__ status) {
+k_col_dft(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status) {
     using C = cx_t<T>;
     using O = Ops<T>;
     constexpr int kDftChunk = sizeof(T) == 4 ? 32 : 16;   // live rows staged at a time
@@ -615,7 +615,8 @@ k_col_dft(ColPassArgs a, int n, unsigned* __restrict__ status) {
                 C w = O::mk(0, 0);
                 if (r < rc && kp < len) {
                     const unsigned k = kp >= len / 2 ? kp - len / 2 : kp - len / 2 + n;
-                    w = __ldg(&tw[(k * (unsigned)s_rows[r0 + r]) % (unsigned)n]);   // < 2^26
+                    const unsigned kr = k * (unsigned)s_rows[r0 + r];   // < 2^26
+                    w = __ldg(&tw[nmask ? (kr & nmask) : kr % (unsigned)n]);
                 }
                 sW[r][c] = w;
             }
@@ -662,7 +663,9 @@ void launch_col_dft(const ColPassArgs& a, int n, unsigned* status, cudaStream_t 
     // each block takes up to four 64-output tiles of its 64 columns
     const int nkt = (a.out_len + kDftTile - 1) / kDftTile;
     const dim3 grid((a.ncols + kDftTile - 1) / kDftTile, (nkt + 3) / 4, a.batch > 1 ? a.batch : 1);
-    k_col_dft<T><<<grid, 256, 0, st>>>(a, n, status);
+    // power-of-two n: the index reduction is a mask instead of a division
+    const unsigned nmask = (n & (n - 1)) == 0 ? (unsigned)(n - 1) : 0u;
+    k_col_dft<T><<<grid, 256, 0, st>>>(a, n, nmask, status);
 }
 template void launch_col_dft<float>(const ColPassArgs&, int, unsigned*, cudaStream_t);
 template void launch_col_dft<double>(const ColPassArgs&, int, unsigned*, cudaStream_t);
