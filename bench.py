@@ -75,12 +75,14 @@ def sweep_config(cfg, in_pupil, n_gpus):
             "parallelism": "replicas x%d (independent instances, no collective)" % n_gpus}
 
 
-def config_dict(cfg, n_gpus):
+def config_dict(cfg, n_gpus, precision="fp32"):
     g = cfg["grid"]
     return {"workload": "star5_F100: r=1+0.3cos5t, F=100 (lz=0.0169), 524288 nodes (128x16x256), "
                         "t1 1000x1000 grid h=0.003 + t3 1e6 targets in disc r<=1.5",
             "nodes": 524288, "t1_targets": g["n1"] * g["n2"], "t3_targets": M3,
-            "tol": TOL, "precision": "fp32 spread/fft/interp, fp64 phases",
+            "tol": TOL,
+            "precision": "fp32 spread/fft/interp, fp64 phases" if precision == "fp32" else
+                         "fp64 throughout (the plain FP64 path at the same tolerance)",
             "nodes_recomputed_each_step": True,
             "streams": "t1 and t3 plans on two streams, forked and joined every step",
             "l2": "flushed between timed steps (512 MiB write)",
@@ -227,7 +229,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 2e6 / v * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(cfg, args.gpus),
+            "config": config_dict(cfg, args.gpus, args.precision),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -262,10 +264,12 @@ STAR_DRAM_TRAFFIC = {
 }
 
 
-def algorithmic_bytes(info1, info3, n_nodes):
-    """Minimum bytes each stage must move (FP32 fast mode), per launch."""
-    rec = 24                       # node record: 2 x int32 cell, 2 x f32 fraction, c64 strength
-    c64 = 8
+def algorithmic_bytes(info1, info3, n_nodes, precision="fp32"):
+    """Minimum bytes each stage must move, per launch.  FP32 fast mode: a
+    24 B node record (2 x int32 cell, 2 x f32 fraction, c64 strength) and c64
+    grids; FP64 mode: a 40 B record (f64 fractions, c128 strength) and c128."""
+    rec = 24 if precision == "fp32" else 40
+    c64 = 8 if precision == "fp32" else 16
     nf1, nf2 = info1["nf1"], info1["nf2"]
     g3 = info3["nf1"] * info3["nf2"]
     F3 = info3["nfft1"] * info3["nfft2"]
@@ -280,6 +284,10 @@ def algorithmic_bytes(info1, info3, n_nodes):
         "t3.fft_cols": info3["nf2"] * info3["nfft1"] * c64 + F3 * c64,
         "t3.interp_epilogue": M3 * (16 + c64),
     }
+
+
+def star_cdtype(torch, precision):
+    return torch.complex64 if precision == "fp32" else torch.complex128
 
 
 def run_ours(args, rank, world, local_rank):
@@ -299,16 +307,18 @@ def run_ours(args, rank, world, local_rank):
     # the type-1 and type-3 evaluations are independent: each plan has its
     # own stream and a step forks the second off the first and joins it back
     stream3 = torch.cuda.Stream()
-    p1 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision="fp32", grid=g, recompute_nodes=True,
+    prec = args.precision
+    cdt = star_cdtype(torch, prec)
+    p1 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision=prec, grid=g, recompute_nodes=True,
               sync_status=False)
-    p3 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision="fp32", box=(-1.5, 1.5, -1.5, 1.5),
+    p3 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision=prec, box=(-1.5, 1.5, -1.5, 1.5),
               recompute_nodes=True, sync_status=False, stream=stream3)
     p1.set_timing(True)
     p3.set_timing(True)
     info1, info3 = p1.info(), p3.info()
     targets = torch.tensor(targets_np, dtype=torch.float64, device=dev)
-    out1 = torch.empty((g["n2"], g["n1"]), dtype=torch.complex64, device=dev)
-    out3 = torch.empty((M3,), dtype=torch.complex64, device=dev)
+    out1 = torch.empty((g["n2"], g["n1"]), dtype=cdt, device=dev)
+    out3 = torch.empty((M3,), dtype=cdt, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -356,8 +366,8 @@ def run_ours(args, rank, world, local_rank):
     # h_out3 hold the results.  The two plans' streams (and each plan's own
     # copy stream for the targets) overlap transfers with compute.
     h_t3 = torch.from_numpy(targets_np).pin_memory().numpy()
-    h_out1 = torch.empty((g["n2"], g["n1"]), dtype=torch.complex64, pin_memory=True).numpy()
-    h_out3 = torch.empty((M3,), dtype=torch.complex64, pin_memory=True).numpy()
+    h_out1 = torch.empty((g["n2"], g["n1"]), dtype=cdt, pin_memory=True).numpy()
+    h_out3 = torch.empty((M3,), dtype=cdt, pin_memory=True).numpy()
     for _ in range(2):
         p1.eval_host(None, h_out1)
         p3.eval_host(h_t3, h_out3)
@@ -379,7 +389,7 @@ def run_ours(args, rank, world, local_rank):
         return
     # ---------------- roofline of the dominant kernel
     per_launch = {k: v / args.steps for k, v in stage_sum.items()}
-    ab = algorithmic_bytes(info1, info3, info1["n_nodes"])
+    ab = algorithmic_bytes(info1, info3, info1["n_nodes"], prec)
     dominant = max((k for k in per_launch if k in ab), key=lambda k: per_launch[k])
     peaks = {}
     try:
@@ -388,14 +398,14 @@ def run_ours(args, rank, world, local_rank):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = ab[dominant] / (per_launch[dominant] * 1e-3) / 1e9
-    traffic = STAR_DRAM_TRAFFIC.get(dominant)
+    traffic = STAR_DRAM_TRAFFIC.get(dominant) if prec == "fp32" else None
     cpu = oracle_rate(cfg, targets_np, 10.0)
     launches = (info1["launches_per_eval"] + info3["launches_per_eval"]) * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(cfg, world),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+        "data": "synthetic", "config": config_dict(cfg, world, prec),
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
@@ -921,10 +931,15 @@ def main():
     ap.add_argument("--workload", default="star5_F100",
                     choices=["star5_F100", "starshade_sweep", "randstar_F1000", "randstar_batch32",
                              "koch_L13"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="star5_F100 only: fp64 times the plain FP64 path at the same "
+                         "tolerance (1e-6), for comparison with the FP32 fast mode")
     ap.add_argument("--lambdas", type=int, default=64,
                     help="starshade_sweep only: wavelengths per sweep (64 is the benchmark; "
                          "fewer for small profiling captures)")
     args = ap.parse_args()
+    if args.precision != "fp32" and args.workload != "star5_F100":
+        ap.error("--precision fp64 is offered for the star5_F100 workload only")
     sweep = args.workload == "starshade_sweep"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -66,3 +66,22 @@ def test_clock_sampler_falls_back_to_a_longer_period():
     time.sleep(0.25)
     out = c.stop()
     assert out["period_ms"] == 100 and out["samples"] >= 1
+
+
+def test_algorithmic_bytes_per_precision():
+    info1 = {"nf1": 2000, "nf2": 2000}
+    info3 = {"nf1": 1500, "nf2": 1400, "nfft1": 3000, "nfft2": 2800}
+    a32 = bench.algorithmic_bytes(info1, info3, 524288)
+    a64 = bench.algorithmic_bytes(info1, info3, 524288, "fp64")
+    assert a32["t3.spread"] == 524288 * 24 + 1500 * 1400 * 8
+    assert a64["t3.spread"] == 524288 * 40 + 1500 * 1400 * 16
+    assert a32["t3.interp_epilogue"] == bench.M3 * 24
+    assert a64["t3.interp_epilogue"] == bench.M3 * 32
+    assert set(a32) == set(a64)
+
+
+def test_precision_option_is_star_only():
+    import subprocess
+    r = subprocess.run([sys.executable, bench.__file__, "--workload", "starshade_sweep",
+                        "--precision", "fp64"], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2 and "star5_F100" in r.stderr
