@@ -112,7 +112,10 @@ def _disc_family():
 @pytest.mark.parametrize("case", ["no_families", "bad_lambda", "bad_z", "tol_low", "tol_high",
                                   "fp32_tol", "bad_grid", "bad_box", "bad_kind", "even_params",
                                   "nan_param", "bad_sigma", "bad_width", "petal_radii",
-                                  "petal_profile", "petal_table", "petal_disc"])
+                                  "petal_profile", "petal_table", "petal_disc", "nsli_far",
+                                  "screen_small", "screen_no_arrays", "screen_box", "binning",
+                                  "fft_split", "tri_params", "tri_order", "motion_fourier",
+                                  "motion_nan"])
 def test_plan_argument_errors(lib, case):
     fams, keep = _disc_family()
     kw = {}
@@ -151,6 +154,41 @@ def test_plan_argument_errors(lib, case):
         fams[0].kind = 3
         fams[0].params = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         fams[0].n_params = len(keep)
+    elif case == "nsli_far":
+        kw["opts"] = {"nsli_far": -0.5}
+    elif case.startswith("screen"):
+        amp = np.ones((8, 8))
+        keep = (keep, amp)
+        box = (ctypes.c_double * 4)(-1.0, 1.0, -1.0, 1.0)
+        o = {"screen_n1": 8, "screen_n2": 8, "screen_amp": amp.ctypes.data, "screen_box": box}
+        if case == "screen_small":
+            o["screen_n1"] = 3
+        elif case == "screen_no_arrays":
+            o["screen_amp"] = None
+        else:
+            o["screen_box"] = (ctypes.c_double * 4)(-1.0, 1.0, 1.0, -1.0)
+        kw["opts"] = o
+    elif case == "binning":
+        kw["opts"] = {"t3_binning": 2}
+    elif case == "fft_split":
+        kw["opts"] = {"fft_split_above": -1}
+    elif case.startswith("tri"):
+        keep = np.array([0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 2.0])   # one triangle + a stray value
+        fams[0].kind = 4
+        fams[0].params = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        fams[0].n_params = 7 if case == "tri_params" else 6
+        fams[0].n_panels = 1
+        fams[0].p = 3 if case == "tri_params" else 0
+    elif case.startswith("motion"):
+        mo = np.array([0.0, np.nan if case == "motion_nan" else 0.01, 0.0] * 8)
+        keep = (keep, mo)
+        if case == "motion_nan":
+            head = np.array([1.0, 2.0, 8, 4, 0, 0.5, 4], dtype=np.float64)
+            keep = (head, mo)
+            fams[0].kind = 3
+            fams[0].params = head.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            fams[0].n_params = len(head)
+        fams[0].motion = mo.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     elif case == "bad_sigma":
         kw["opts"] = {"sigma": 1.0}
     elif case == "bad_width":
@@ -159,7 +197,8 @@ def test_plan_argument_errors(lib, case):
     # on a machine without a GPU the family checks may surface as a CUDA
     # error instead (they run after the device query); both leave no plan
     expect = {-5} if case == "fp32_tol" else {-1}
-    if case in ("bad_kind", "even_params", "nan_param") or case.startswith("petal"):
+    if case in ("bad_kind", "even_params", "nan_param") or case.startswith(("petal", "tri",
+                                                                            "motion")):
         expect = expect | {-2}
     assert s in expect, (s, msg)
     assert h is None and msg
