@@ -231,3 +231,19 @@ def test_binding_family_marshalling():
     _, _, _, _, params, _, _ = fresnel.family_params(
         W.petal_family(8, 1.0, 2.0, {"kind": "bspline", "coefs": [1, 2, 3, 4, 5]}, 6, 5))
     assert list(params) == [1.0, 2.0, 0, 0, 1, 1, 2, 3, 4, 5]
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without libfresnel.so the binding raises, and so does
+    making a plan."""
+    from paper_2010_05978_gb300 import fresnel
+    import workloads as W
+    missing = str(tmp_path / "libfresnel.so")
+    monkeypatch.setattr(fresnel, "_lib", None)
+    with pytest.raises(fresnel.FresnelError, match="not found"):
+        fresnel.load_library(missing)
+    orig = fresnel.load_library
+    monkeypatch.setattr(fresnel, "load_library", lambda path=None: orig(missing))
+    with pytest.raises(fresnel.FresnelError, match="not found"):
+        fresnel.Plan([W.fourier_family([1.0], 8, 4, 4)], 0.1, 1.0, 1e-6,
+                     grid=W.grid_spec(8, 8, 0.1))
