@@ -360,6 +360,24 @@ class Plan(_PlanHandle):
     precision "fp32" (fast mode) or "fp64"; output "aperture" or "occulter";
     grid=dict(n1, n2, h, x0, y0) for type-1 targets, or box=(xmin, xmax,
     ymin, ymax) for scattered (type-3) targets.
+
+    Family dicts: {"kind": "fourier", "params", "n_panels", "p", "m"},
+    {"kind": "line_rule", "X", "Y", "W", "V", "m"}, {"kind": "nodes", "x",
+    "y", "w"}, {"kind": "triangles", "tri" (T x 6 vertex coordinates), "p"},
+    {"kind": "petals", "n_petals", "a", "R", "profile", "m", "n_p", "n_d",
+    "m_d"}; all but nodes take a centre "cx", "cy", and petals an optional
+    "motion" (n_petals x 3 rows phi, tx, ty: each petal rotated by phi about
+    the centre and translated, with root-arc patches added, Sec. 5.1).
+
+    Options: recompute_nodes regenerates nodes, chirps and bins at every
+    evaluation; sync_status=False makes evaluations asynchronous (read the
+    device status with check()); sigma, kernel_w override the NUFFT's
+    upsampling and kernel width; t3_binning (-1 off, 0 auto, 1 on) buckets
+    scattered targets; autotune measures candidate settings at plan time;
+    nsli_far is the distance beyond which nsli() uses the shadow fix (eq. li
+    with the rounded winding number); screen=dict(amp=, opd=, box=(x0, x1,
+    y0, y1)) multiplies each node's weight by A e^{2 pi i OPD / lam} from
+    sampled amplitude and optical path difference (n2 rows of n1 samples).
     """
 
     def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
