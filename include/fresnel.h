@@ -38,7 +38,7 @@ typedef enum {
     FRESNEL_ERR_ARG = -1,         /* invalid argument; nothing was launched */
     FRESNEL_ERR_CUDA = -2,        /* a CUDA runtime call failed */
     FRESNEL_ERR_OOM = -3,         /* device allocation failed or exceeded the cap */
-    FRESNEL_ERR_TIMEOUT = -4,     /* a bounded device wait gave up */
+    FRESNEL_ERR_TIMEOUT = -4,     /* reserved: no kernel of this library waits on another */
     FRESNEL_ERR_UNSUPPORTED = -5, /* valid request beyond this build's limits */
     FRESNEL_ERR_DEVICE = -6       /* a device-side check failed (e.g. target outside the plan's box) */
 } fresnel_status;
@@ -331,7 +331,9 @@ fresnel_status fresnel_nsli(fresnel_plan_t plan, const double* d_targets, long l
                             void* d_out);
 
 /* Synchronises the plan's stream and returns (then clears) the device status/* Synchronises the plan's stream and returns (then clears) the device status
- * word: FRESNEL_OK, FRESNEL_ERR_DEVICE or FRESNEL_ERR_TIMEOUT. */
+ * word: FRESNEL_OK or FRESNEL_ERR_DEVICE (the message names each check that
+ * failed: a target outside the box, a node support outside the type-3 grid, a
+ * non-finite coordinate, a sort region overflow). */
 fresnel_status fresnel_check(fresnel_plan_t plan);
 
 /* Releases everything the plan owns.  NULL-safe; synchronises the stream. */
