@@ -688,3 +688,61 @@ def test_root_arc_patch_areas():
     fam = _resolved_starshade()
     rot = np.column_stack([0.01 * np.arange(6) - 0.02, np.zeros(6), np.zeros(6)])
     assert abs(Q.family_nodes(dict(fam, motion=rot))[2].sum() - Q.family_nodes(fam)[2].sum()) < 1e-13
+
+
+# ------------------------------------------------------------------ Fraunhofer limit
+def _fraunhofer_disc_error(lz, R=1.0):
+    """max |u - u_F| / max |u_F| for the disc, u_F = (1/(i lz)) e^{i pi rho^2/lz}
+    pi R^2 2 J1(v)/v, v = 2 pi R rho / lz (the Airy pattern)."""
+    from scipy import special
+    fam = [W.fourier_family([R], 16, 16, 16)]
+    rho = np.linspace(0.0, 3.0 * lz, 25)
+    u = oracle.field(fam, lz, 1.0, rho * np.cos(0.3), rho * np.sin(0.3))
+    v = 2 * np.pi * R * rho / lz
+    airy = np.where(v > 0, 2 * special.j1(v) / np.where(v > 0, v, 1.0), 1.0)
+    ref = np.exp(1j * np.pi * rho ** 2 / lz) / (1j * lz) * np.pi * R * R * airy
+    return np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+
+
+def test_fraunhofer_limit_disc_airy():
+    """For F = R^2/lz -> 0 the source chirp e^{i pi |x|^2/lz}, the last factor
+    of eq. split, tends to 1 over the aperture, and u tends to the target
+    chirp times the aperture's Fourier transform at xi/lz (the Fraunhofer
+    limit, Sec. 4.1's remark on small Fresnel numbers).  The leading
+    correction is pi R^2/(2 lz), so the error falls tenfold for a tenfold
+    lz."""
+    e3, e4 = _fraunhofer_disc_error(1e3), _fraunhofer_disc_error(1e4)
+    assert e4 <= 0.6 * np.pi / 1e4
+    assert 8.0 < e3 / e4 < 12.0
+
+
+def _rect_fraunhofer_error(lz=1e3):
+    """Off-centre rectangle [x0 -+ a] x [y0 -+ b] (two triangles): its Fourier
+    transform is e^{-2 pi i q.c} sin(2 pi a qx)/(pi qx) sin(2 pi b qy)/(pi qy),
+    whose shift phase fixes the sign of the xi.x term."""
+    x0, y0, a, b = 0.3, -0.2, 0.5, 0.25
+    P = [(x0 - a, y0 - b), (x0 + a, y0 - b), (x0 + a, y0 + b), (x0 - a, y0 + b)]
+    tri = np.array([[*P[0], *P[1], *P[2]], [*P[0], *P[2], *P[3]]])
+    fam = [{"kind": "triangles", "tri": tri, "p": 12}]
+    g = W.rng(9, 0)
+    xi, eta = g.uniform(-2, 2, 40) * lz, g.uniform(-2, 2, 40) * lz
+    u = oracle.field(fam, lz, 1.0, xi, eta)
+    qx, qy = xi / lz, eta / lz
+    sx = np.sin(2 * np.pi * a * qx) / (np.pi * qx)
+    sy = np.sin(2 * np.pi * b * qy) / (np.pi * qy)
+    ref = (np.exp(1j * np.pi * (xi ** 2 + eta ** 2) / lz) / (1j * lz)
+           * np.exp(-2j * np.pi * (qx * x0 + qy * y0)) * sx * sy)
+    rmax2 = max(px * px + py * py for px, py in P)
+    return np.max(np.abs(u - ref)) / (4 * a * b / lz), np.pi * rmax2 / lz
+
+
+def test_fraunhofer_limit_offset_rectangle():
+    err, bound = _rect_fraunhofer_error()
+    assert err <= bound
+
+
+def test_planted_mirrored_nodes_fail_the_rectangle_limit(monkeypatch):
+    orig = D.direct_sum
+    monkeypatch.setattr(D, "direct_sum", lambda x, y, w, xi, eta, lz: orig(-x, -y, w, xi, eta, lz))
+    err, bound = _rect_fraunhofer_error()
+    assert err > 100 * bound
