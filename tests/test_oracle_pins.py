@@ -746,3 +746,32 @@ def test_planted_mirrored_nodes_fail_the_rectangle_limit(monkeypatch):
     monkeypatch.setattr(D, "direct_sum", lambda x, y, w, xi, eta, lz: orig(-x, -y, w, xi, eta, lz))
     err, bound = _rect_fraunhofer_error()
     assert err > 100 * bound
+
+
+def test_oracle_sums_do_not_depend_on_the_thread_count(tmp_path):
+    """The C sums parallelise over targets only, each target's sum in a fixed
+    order, so one and four OpenMP threads give bit-identical results."""
+    import subprocess
+    import sys
+    prog = (
+        "import sys, numpy as np\n"
+        "sys.path.insert(0, %r)\n"
+        "import workloads as W\n"
+        "from oracle import direct as D, quadrature as Q\n"
+        "fam = W.fourier_family(W.STAR_PARAMS, 16, 16, 24)\n"
+        "x, y, w = Q.family_nodes(fam)\n"
+        "X, Y, Wt, V, _, _ = Q.family_line_rule(fam)\n"
+        "g = W.rng(95, 0)\n"
+        "xi, eta = g.uniform(-1.5, 1.5, 64), g.uniform(-1.5, 1.5, 64)\n"
+        "c = w * np.exp(1j * np.pi * (x * x + y * y) / 0.05)\n"
+        "np.save(sys.argv[1], np.stack([D.direct_sum(x, y, w, xi, eta, 0.05),\n"
+        "                               D.sum3(x, y, c, xi, eta, 0.05),\n"
+        "                               D.nsli(X, Y, Wt, V, xi, eta, 0.05)]))\n"
+    ) % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for n in (1, 4):
+        f = str(tmp_path / ("t%d.npy" % n))
+        env = dict(os.environ, OMP_NUM_THREADS=str(n))
+        subprocess.run([sys.executable, "-c", prog, f], check=True, env=env, timeout=300)
+        out[n] = np.load(f)
+    assert np.array_equal(out[1], out[4])
