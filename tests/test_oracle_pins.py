@@ -775,3 +775,24 @@ def test_oracle_sums_do_not_depend_on_the_thread_count(tmp_path):
         subprocess.run([sys.executable, "-c", prog, f], check=True, env=env, timeout=300)
         out[n] = np.load(f)
     assert np.array_equal(out[1], out[4])
+
+
+def test_triangle_rule_vertex_choice_and_orientation():
+    """Sec. 4.3's triangle rule dilates about one vertex; the field it gives
+    must not depend on which vertex (cyclic relabelling), and the reversed
+    orientation negates every weight, hence the field."""
+    v = [(0.05, -0.1), (0.9, 0.2), (0.3, 0.85)]
+    xi, eta = np.array([0.0, 0.5, -0.7]), np.array([0.1, 0.4, 0.9])
+    lz = 0.1
+
+    def u(order):
+        tri = np.array([[*v[order[0]], *v[order[1]], *v[order[2]]]])
+        return oracle.field([{"kind": "triangles", "tri": tri, "p": 40}], lz, 1.0, xi, eta)
+
+    ref = u((0, 1, 2))
+    assert np.max(np.abs(u((1, 2, 0)) - ref)) < 1e-12
+    assert np.max(np.abs(u((2, 0, 1)) - ref)) < 1e-12
+    assert np.max(np.abs(u((0, 2, 1)) + ref)) < 1e-12
+    x, y, w = Q.triangle_rule(np.array([[*v[0], *v[2], *v[1]]]), 5)
+    area = 0.5 * ((v[1][0] - v[0][0]) * (v[2][1] - v[0][1]) - (v[1][1] - v[0][1]) * (v[2][0] - v[0][0]))
+    assert abs(w.sum() + area) < 1e-15
