@@ -155,7 +155,7 @@ typedef struct {
      * (FRESNEL_ERR_DEVICE). */
     double box[4];
     double sigma;        /* upsampling factor; 0 = automatic */
-    int kernel_w;        /* spreading kernel width in grid points; 0 = automatic */
+    int kernel_w;        /* spreading kernel width in grid points, 2..16; 0 = automatic */
     int recompute_nodes; /* 1: node generation, chirp and binning run inside every
                             fresnel_eval (nothing node-sized is cached); 0: done once */
     int sync_status;     /* 1: fresnel_eval synchronises the stream and returns the

@@ -1564,7 +1564,7 @@ fresnel_status fresnel_plan_many(const fresnel_problem* problems, int n_problems
     }
     if (opts->sigma != 0 && !(opts->sigma >= 1.2 && opts->sigma <= 4.0))
         return fres_fail(FRESNEL_ERR_ARG, "sigma must be 0 (auto) or in [1.2, 4]");
-    if (opts->kernel_w < 0 || opts->kernel_w > kMaxW)
+    if (opts->kernel_w < 0 || opts->kernel_w == 1 || opts->kernel_w > kMaxW)
         return fres_fail(FRESNEL_ERR_ARG, "kernel_w must be 0 (auto) or in [2, 16]");
     if (opts->t3_binning < -1 || opts->t3_binning > 1)
         return fres_fail(FRESNEL_ERR_ARG, "t3_binning must be -1, 0 or 1");

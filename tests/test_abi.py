@@ -114,7 +114,8 @@ def _disc_family():
                                   "nan_param", "bad_sigma", "bad_width", "petal_radii",
                                   "petal_profile", "petal_table", "petal_disc", "nsli_far",
                                   "screen_small", "screen_no_arrays", "screen_box", "binning",
-                                  "fft_split", "tri_params", "tri_order", "motion_fourier",
+                                  "fft_split", "width_one", "tri_params", "tri_order",
+                                  "motion_fourier",
                                   "motion_nan"])
 def test_plan_argument_errors(lib, case):
     fams, keep = _disc_family()
@@ -172,6 +173,8 @@ def test_plan_argument_errors(lib, case):
         kw["opts"] = {"t3_binning": 2}
     elif case == "fft_split":
         kw["opts"] = {"fft_split_above": -1}
+    elif case == "width_one":
+        kw["opts"] = {"kernel_w": 1}
     elif case.startswith("tri"):
         keep = np.array([0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 2.0])   # one triangle + a stray value
         fams[0].kind = 4
