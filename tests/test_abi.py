@@ -86,6 +86,11 @@ def test_default_opts(lib):
     lib.fresnel_default_opts(ctypes.byref(o))
     assert o.precision == 1 and o.target_kind == 0 and o.sync_status == 1
     assert o.grid_n1 == 100 and abs(o.grid_h - 0.03) < 1e-15
+    # every option added later defaults to off
+    assert (o.sigma, o.kernel_w, o.recompute_nodes, o.max_device_bytes, o.t3_binning,
+            o.fft_split_above, o.autotune, o.nsli_far) == (0.0, 0, 0, 0, 0, 0, 0, 0.0)
+    assert o.screen_amp is None and o.screen_opd is None and o.screen_n1 == o.screen_n2 == 0
+    assert list(o.box) == [-1.0, 1.0, -1.0, 1.0]
 
 
 def _plan_status(lib, fams, n, lam=0.1, z=1.0, tol=1e-6, opts=None):
