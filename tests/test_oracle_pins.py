@@ -749,8 +749,9 @@ def test_planted_mirrored_nodes_fail_the_rectangle_limit(monkeypatch):
 
 
 def test_oracle_sums_do_not_depend_on_the_thread_count(tmp_path):
-    """The C sums parallelise over targets only, each target's sum in a fixed
-    order, so one and four OpenMP threads give bit-identical results."""
+    """The C sums (direct, type 3, NSLI, the far-target line integral and the
+    adjoint sums) parallelise over their outputs only, each output's sum in a
+    fixed order, so one and four OpenMP threads give bit-identical results."""
     import subprocess
     import sys
     prog = (
@@ -764,9 +765,12 @@ def test_oracle_sums_do_not_depend_on_the_thread_count(tmp_path):
         "g = W.rng(95, 0)\n"
         "xi, eta = g.uniform(-1.5, 1.5, 64), g.uniform(-1.5, 1.5, 64)\n"
         "c = w * np.exp(1j * np.pi * (x * x + y * y) / 0.05)\n"
+        "far = D.line_integral_far(X, Y, Wt, V, xi, eta, 0.05, 0.2)\n"
+        "adj = D.adjoint_sums(x[:64], y[:64], xi, eta, 0.05, c[:64])\n"
         "np.save(sys.argv[1], np.stack([D.direct_sum(x, y, w, xi, eta, 0.05),\n"
         "                               D.sum3(x, y, c, xi, eta, 0.05),\n"
-        "                               D.nsli(X, Y, Wt, V, xi, eta, 0.05)]))\n"
+        "                               D.nsli(X, Y, Wt, V, xi, eta, 0.05),\n"
+        "                               far[0], far[1], adj[0]]))\n"
     ) % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = {}
     for n in (1, 4):
