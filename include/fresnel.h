@@ -330,7 +330,7 @@ fresnel_status fresnel_eval_host(fresnel_plan_t plan, const double* h_targets, l
 fresnel_status fresnel_nsli(fresnel_plan_t plan, const double* d_targets, long long M,
                             void* d_out);
 
-/* Synchronises the plan's stream and returns (then clears) the device status/* Synchronises the plan's stream and returns (then clears) the device status
+/* Synchronises the plan's stream and returns (then clears) the device status
  * word: FRESNEL_OK or FRESNEL_ERR_DEVICE (the message names each check that
  * failed: a target outside the box, a node support outside the type-3 grid, a
  * non-finite coordinate, a sort region overflow). */

@@ -255,3 +255,19 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     with pytest.raises(fresnel.FresnelError, match="not found"):
         fresnel.Plan([W.fourier_family([1.0], 8, 4, 4)], 0.1, 1.0, 1e-6,
                      grid=W.grid_spec(8, 8, 0.1))
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    """The boundary is a C ABI: the header compiles as C99 without warnings."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use.c"
+    src.write_text('#include "fresnel.h"\n'
+                   "int main(void) { fresnel_opts o; fresnel_default_opts(&o); return 0; }\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", inc, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
