@@ -388,8 +388,9 @@ fresnel_status fresnel_spread(const double* d_g1, const double* d_g2, const void
 /*
  * fresnel_spread for callers that cannot allocate device memory: code that
  * may not call cudaMalloc (or any allocating routine) because another
- * framework owns the device memory pool or is capturing a CUDA graph, and
- * embedded or real-time callers that forbid allocation after start-up.  The
+ * framework owns the device memory pool and forbids allocations it does not
+ * make, and embedded or real-time callers that forbid allocation after
+ * start-up.  The
  * paper has no counterpart: this is a property of the library, not of the
  * method.  Same arguments, result and errors as fresnel_spread, with limits:
  * N <= FRESNEL_SPREAD_NOALLOC_MAX_POINTS and nf1 * nf2 <=
@@ -397,10 +398,13 @@ fresnel_status fresnel_spread(const double* d_g1, const double* d_g2, const void
  * launched).  The scratch is a static device array of
  * FRESNEL_SPREAD_NOALLOC_SCRATCH_BYTES that every device which loads the
  * library holds until the process exits; the call allocates nothing.  The
- * first call on a device looks the array's address up (cudaGetSymbolAddress)
- * and should come before any stream capture.  All calls on a device share
- * the array, so calls that overlap on the GPU (other streams, other host
- * threads) race: serialise them.  Synchronises cuda_stream.
+ * first call on a device looks the array's address up (cudaGetSymbolAddress,
+ * with that device current) and should come before any stream capture; the
+ * address is kept until the process exits, so after a cudaDeviceReset the
+ * call must not be used again.  All calls on a device share the array, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  Every call reads a 4-byte status word back to the host
+ * and synchronises cuda_stream before it returns.
  */
 #define FRESNEL_SPREAD_NOALLOC_MAX_POINTS 65536
 #define FRESNEL_SPREAD_NOALLOC_MAX_GRID (2048 * 2048)

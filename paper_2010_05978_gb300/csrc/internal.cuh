@@ -17,6 +17,17 @@ constexpr int kMaxRadixStages = 32;
 constexpr int kMaxCheb = 64;       // Chebyshev terms kept for psihat (type 3)
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kPi = 3.141592653589793238462643383280;
+constexpr double kTwoPiHi = 6.28318530717958623199592693709;    // fl(2 pi)
+constexpr double kTwoPiLo = 2.44929359829470635445e-16;        // 2 pi - fl(2 pi)
+constexpr double kInvTwoPi = 0.159154943091895335768883763373;
+
+// Reduce an FP64 phase into [-pi, pi]: phi - 2 pi rint(phi / 2 pi), with 2 pi
+// split into two doubles so the product n * 2 pi is carried to ~2^-106.
+__device__ __forceinline__ double reduce_phase(double ph) {
+    double n = rint(ph * kInvTwoPi);
+    ph = fma(-n, kTwoPiHi, ph);
+    return fma(-n, kTwoPiLo, ph);
+}
 
 // Device status word bits (read back by fresnel_check).
 enum : unsigned {

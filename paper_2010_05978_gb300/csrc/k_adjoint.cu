@@ -27,16 +27,6 @@ namespace fres {
 
 namespace {
 
-constexpr double kTwoPiHi = 6.28318530717958623199592693709;
-constexpr double kTwoPiLo = 2.44929359829470635445e-16;
-constexpr double kInvTwoPi = 0.159154943091895335768883763373;
-
-__device__ __forceinline__ double reduce_phase(double ph) {
-    double n = rint(ph * kInvTwoPi);
-    ph = fma(-n, kTwoPiHi, ph);
-    return fma(-n, kTwoPiLo, ph);
-}
-
 // btilde input: sgn conj(gamma) ax ay (sgn = -1 for occulter output, whose
 // derivative is minus that of the aperture field).
 template <typename T>

@@ -22,16 +22,7 @@ namespace fres {
 
 namespace {
 
-constexpr double kTwoPiHi = 6.28318530717958623199592693709;
-constexpr double kTwoPiLo = 2.44929359829470635445e-16;
-constexpr double kInvTwoPi = 0.159154943091895335768883763373;
 constexpr int kBin = 16;            // target bins: 16 x 16 cells of F
-
-__device__ __forceinline__ double reduce_phase(double ph) {
-    double n = rint(ph * kInvTwoPi);
-    ph = fma(-n, kTwoPiHi, ph);
-    return fma(-n, kTwoPiLo, ph);
-}
 
 // psihat(t) for |t| <= t_max from its even Chebyshev series
 // sum_k a_k T_{2k}(t / t_max) = sum_k a_k T_k(2 (t/t_max)^2 - 1), by Clenshaw.

@@ -21,15 +21,6 @@ namespace fres {
 namespace {
 
 constexpr int kNsliThreads = 256;
-constexpr double kTwoPiHi = 6.28318530717958623199592693709;
-constexpr double kTwoPiLo = 2.44929359829470635445e-16;
-constexpr double kInvTwoPi = 0.159154943091895335768883763373;
-
-__device__ __forceinline__ double reduce_phase(double ph) {
-    double n = rint(ph * kInvTwoPi);
-    ph = fma(-n, kTwoPiHi, ph);
-    return fma(-n, kTwoPiLo, ph);
-}
 
 // One thread per target; the boundary nodes stream through shared memory in
 // tiles of one node per thread.  bnd = (X, Y, W, V) absolute coordinates.

@@ -144,9 +144,15 @@ extern "C" fresnel_status fresnel_spread(const double* d_g1, const double* d_g2,
         cudaGetLastError();
         return fres_fail(FRESNEL_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     }
-    cudaMemsetAsync(scratch + counts_off, 0, sizeof(int) * ntiles, st);
-    cudaMemsetAsync(scratch + work_off, 0, 2 * sizeof(int), st);
-    cudaMemsetAsync(scratch + status_off, 0, sizeof(unsigned), st);
+    e = cudaMemsetAsync(scratch + counts_off, 0, sizeof(int) * ntiles, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + work_off, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + status_off, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(scratch, st);
+        cudaStreamSynchronize(st);
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("fresnel_spread: clearing the scratch: ") +
+                                               cudaGetErrorString(e));
+    }
     s = fres_spread_run(d_g1, d_g2, d_c, N, nf1, nf2, w, beta, d_grid, scratch, st);
     unsigned h = 0;
     cudaMemcpyAsync(&h, scratch + status_off, sizeof(unsigned), cudaMemcpyDeviceToHost, st);

@@ -1,8 +1,7 @@
 // fresnel_spread_noalloc: fresnel_spread for callers that cannot allocate
-// device memory -- code that must not call cudaMalloc while another
-// framework owns the device's memory pool or is capturing work into a CUDA
-// graph, or embedded callers (plugins, real-time loops) that forbid
-// allocation after start-up.  The scratch the spreading kernels need (node
+// device memory -- code running inside another framework that owns the
+// device's memory pool and forbids allocations behind its back, or embedded
+// callers (plugins, real-time loops) that may not allocate after start-up.  The scratch the spreading kernels need (node
 // records, tile counts and cursors, work-item lists, counters) lives in one
 // file-scope static device array of fixed size; the caller still passes the
 // points, strengths and output grid.
@@ -15,7 +14,10 @@
 static __device__ __align__(256) unsigned char g_spread_scratch[FRESNEL_SPREAD_NOALLOC_SCRATCH_BYTES];
 
 // Host code must not use g_spread_scratch as a device address: its name on
-// the host is a stand-in.  The device address is looked up once per device.
+// the host is a stand-in.  The device address is looked up once per device
+// (with that device current) and kept for the life of the process; after a
+// cudaDeviceReset the module may load at another address, so the cached
+// address is then stale and the call must not be used again.
 static std::mutex g_scratch_mutex;
 static unsigned char* g_scratch_ptr[64] = {};
 
@@ -70,13 +72,16 @@ extern "C" fresnel_status fresnel_spread_noalloc(const double* d_g1, const doubl
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // The array keeps the previous call's contents: clear what must start at zero.
     const int ntiles = (nf1 / 32) * (nf2 / 32);
-    cudaMemsetAsync(scratch + counts_off, 0, sizeof(int) * ntiles, st);
-    cudaMemsetAsync(scratch + work_off, 0, 2 * sizeof(int), st);
-    cudaMemsetAsync(scratch + status_off, 0, sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(scratch + counts_off, 0, sizeof(int) * ntiles, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + work_off, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + status_off, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess)
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("fresnel_spread_noalloc: clearing the "
+                                                       "scratch: ") + cudaGetErrorString(e));
     s = fres_spread_run(d_g1, d_g2, d_c, N, nf1, nf2, w, beta, d_grid, scratch, st);
     if (s != FRESNEL_OK) return s;
     unsigned h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, scratch + status_off, sizeof(unsigned),
+    e = cudaMemcpyAsync(&h, scratch + status_off, sizeof(unsigned),
                                     cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)

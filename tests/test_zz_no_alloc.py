@@ -1,6 +1,7 @@
 """GPU test of fresnel_spread_noalloc, the spreading entry point for callers
-that cannot allocate device memory (a framework owns the memory pool or is
-capturing a CUDA graph; an embedded caller forbids allocation).  It must give
+that cannot allocate device memory (a framework that owns the memory pool
+forbids allocations it does not make; an embedded caller forbids allocation
+after start-up).  It must give
 the same grid as fresnel_spread, which allocates its scratch, on two calls in
 a row (the second call must not see the first call's leftover scratch).
 
