@@ -103,3 +103,82 @@ def loss_and_grad(theta, problems, grid, keep):
             dLdA += np.sum(gw * dw_dA + gx * dx_dA + gy * dy_dA, axis=0)
         grad += bspline_basis(a, R, len(theta), r).T @ dLdA
     return L / K, grad
+
+
+# ---------------------------------------------------------------- shape gradient (Fourier boundary)
+def fourier_mode(kk, t):
+    """dr/dp and dr'/dp at t for the coefficient p = params[kk] of
+    r(t) = r0 + sum_k (a_k cos kt + b_k sin kt), params = [r0, a1, b1, ...]."""
+    if kk == 0:
+        return np.ones_like(t), np.zeros_like(t)
+    k = (kk + 1) // 2
+    if kk % 2 == 1:
+        return np.cos(k * t), -k * np.sin(k * t)
+    return np.sin(k * t), k * np.cos(k * t)
+
+
+def shape_loss(params, fam, lam, z, xi, eta, output="aperture"):
+    """L(params) = mean over targets of |u|^2 for a Fourier-boundary family
+    whose radius r(t) = r0 + sum_k (a_k cos kt + b_k sin kt) has coefficients
+    params = [r0, a1, b1, ...] (the dilation rule of eqs. aqnod/aqwei on the
+    Gauss-Legendre panel line rule); u = u^ap, or u^oc = 1 - u^ap (eq. bab)."""
+    f = dict(fam, params=np.asarray(params, dtype=np.float64))
+    x, y, w = Q.family_nodes(f)
+    u = direct.direct_sum(x, y, w, xi, eta, lam * z)
+    if output == "occulter":
+        u = 1.0 - u
+    return float(np.mean(np.abs(u) ** 2))
+
+
+def shape_loss_and_grad(params, fam, lam, z, xi, eta, output="aperture"):
+    """(L, dL/dparams) for shape_loss by the adjoint of the direct sum.
+
+    The node and weight derivatives dL/dx_j, dL/dy_j, dL/dw_j are those of the
+    module docstring (adjoint sums of eq. faq with c_k = 2 s conj(u_k) / M,
+    s = -1 for the occulter field).  They are chained through the dilation
+    rule written out for boundary node i and radius l,
+        x = c + alpha_l (X_i - c),  w = alpha_l wtilde_l ((X_i - cx) V_i - (Y_i - cy) W_i),
+    and through the line rule X_i - cx = r(t_i) cos t_i, Y_i - cy = r(t_i) sin t_i,
+    W_i = what_i (r' cos t_i - r sin t_i), V_i = what_i (r' sin t_i + r cos t_i),
+    by the product rule with dr/dp and dr'/dp of each Fourier coefficient p."""
+    params = np.asarray(params, dtype=np.float64)
+    cx, cy = fam.get("cx", 0.0), fam.get("cy", 0.0)
+    n_panels, p, m = fam["n_panels"], fam["p"], fam["m"]
+    lz = lam * z
+    f = dict(fam, params=params)
+    x, y, w = Q.family_nodes(f)
+    u = direct.direct_sum(x, y, w, xi, eta, lz)
+    sgn = 1.0
+    if output == "occulter":
+        u = 1.0 - u
+        sgn = -1.0
+    M = len(xi)
+    L = float(np.mean(np.abs(u) ** 2))
+    c = sgn * 2.0 * np.conj(u) / M
+    P, Qx, Qy = direct.adjoint_sums(x, y, xi, eta, lz, c)
+    S, Tx, Ty = P / (1j * lz), Qx / (1j * lz), Qy / (1j * lz)
+    gw = S.real.reshape(-1, m)
+    gx = (1j * (2.0 * np.pi / lz) * w * Tx).real.reshape(-1, m)
+    gy = (1j * (2.0 * np.pi / lz) * w * Ty).real.reshape(-1, m)
+    # boundary rule and its pieces (same construction as quadrature.fourier_line_rule)
+    tq, wq = Q.gauss_legendre(p, 0.0, 2.0 * np.pi / n_panels)
+    t = (np.arange(n_panels)[:, None] * (2.0 * np.pi / n_panels) + tq[None, :]).ravel()
+    what = np.tile(wq, n_panels)
+    r, dr = Q.fourier_radius(params, t)
+    ct, st = np.cos(t), np.sin(t)
+    DX, DY = r * ct, r * st                                   # X - cx, Y - cy
+    Wb, Vb = what * (dr * ct - r * st), what * (dr * st + r * ct)
+    alpha, wt = Q.gauss_legendre(m, 0.0, 1.0)
+    # per boundary node: sums over radii of the derivatives wrt X - cx, Y - cy and the cross
+    gX = gx @ alpha                                           # dL/d(X - cx)
+    gY = gy @ alpha
+    gC = gw @ (alpha * wt)                                    # dL/d((X-cx) V - (Y-cy) W)
+    grad = np.zeros_like(params)
+    for kk in range(len(params)):
+        phi, dphi = fourier_mode(kk, t)
+        dDX, dDY = phi * ct, phi * st
+        dW = what * (dphi * ct - phi * st)
+        dV = what * (dphi * st + phi * ct)
+        dC = dDX * Vb + DX * dV - dDY * Wb - DY * dW
+        grad[kk] = np.sum(gX * dDX + gY * dDY + gC * dC)
+    return L, grad

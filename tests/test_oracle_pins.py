@@ -395,6 +395,51 @@ def test_planted_gradient_without_node_motion(monkeypatch):
     assert abs(g[10] - fd) > 1e-3 * abs(fd)
 
 
+def _shape_case():
+    fam = W.fourier_family(W.STAR_PARAMS, 16, 8, 12, cx=0.05, cy=-0.03)
+    params = np.array(fam["params"])
+    params[3], params[4] = 0.02, -0.015
+    xi, eta = W.disc_targets(60, 1.2, 31)
+    return params, fam, xi, eta
+
+
+def _shape_fd(G, params, fam, xi, eta, out, k, h=1e-6):
+    e = np.zeros_like(params)
+    e[k] = h
+    return (G.shape_loss(params + e, fam, 0.05, 1.0, xi, eta, out) -
+            G.shape_loss(params - e, fam, 0.05, 1.0, xi, eta, out)) / (2 * h)
+
+
+@pytest.mark.parametrize("out", ["aperture", "occulter"])
+def test_shape_gradient_matches_central_differences(out):
+    """Adjoint gradient of the mean |u|^2 w.r.t. every Fourier coefficient of an
+    off-centre star boundary against central differences (h = 1e-6) of the
+    loss itself."""
+    from oracle import gradient as G
+    params, fam, xi, eta = _shape_case()
+    L, g = G.shape_loss_and_grad(params, fam, 0.05, 1.0, xi, eta, out)
+    assert abs(L - G.shape_loss(params, fam, 0.05, 1.0, xi, eta, out)) < 1e-13
+    for k in range(len(params)):
+        fd = _shape_fd(G, params, fam, xi, eta, out, k)
+        assert abs(g[k] - fd) <= 1e-7 * np.max(np.abs(g)), (k, g[k], fd)
+
+
+def test_planted_shape_gradient_with_swapped_modes(monkeypatch):
+    """Taking the cosine mode's derivative for the sine coefficient (and back)
+    fails the central-difference pin."""
+    from oracle import gradient as G
+    params, fam, xi, eta = _shape_case()
+    orig = G.fourier_mode
+
+    def bad(kk, t):
+        return orig(kk + 1 if kk % 2 == 1 else (kk - 1 if kk > 0 else 0), t)
+    with monkeypatch.context() as mp:
+        mp.setattr(G, "fourier_mode", bad)
+        _, g = G.shape_loss_and_grad(params, fam, 0.05, 1.0, xi, eta, "aperture")
+    fd = np.array([_shape_fd(G, params, fam, xi, eta, "aperture", k) for k in range(len(params))])
+    assert np.max(np.abs(g - fd)) > 1e-3 * np.max(np.abs(fd))
+
+
 # ------------------------------------------------------------------ planted mistakes
 def _pins_fail(monkeypatch, patch):
     """Apply a plausible oracle bug and report whether the closed-form pins notice it."""
