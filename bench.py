@@ -8,17 +8,23 @@ r = 1 + 0.3 cos 5 theta at Fresnel number 100 (lambda z = 0.0169, R = 1.3),
 both in FP32 fast mode at tol 1e-6 (phases in FP64).  Metric value = 2e6
 targets / step time.  Synthetic, seeded inputs (workloads.py).
 
-Second workload (``--workload starshade_sweep``): the 24-petal offset
-hyper-Gaussian starshade (Sec. 4.2) at 64 wavelengths evenly spaced in
-[400, 1000] nm, z = 3.7e7 m, each wavelength with its own quadrature
-(14,040 .. 24,960 nodes), evaluated as the occulter field u^oc on the
-512 x 512 grid over the 2.4 m pupil in FP32 fast mode at tol 1e-6; one step =
-one batched evaluation of all 64 wavelengths (nodes regenerated).  Metric:
-wavelength sweeps per second.
+The default one-GPU line also carries, each with its own step time, plan
+time, roofline, error against the oracle and CPU baseline:
+  fp64_path       the same star workload on the plain FP64 path (tol 1e-6);
+  sweep           the 24-petal offset hyper-Gaussian starshade (Sec. 4.2) at
+                  64 wavelengths in [400, 1000] nm, z = 3.7e7 m, u^oc on the
+                  512 x 512 pupil grid, one batched evaluation per step
+                  (wavelength sweeps per second);
+  randstar_F1000  the random 20-mode aperture at Fresnel number 1000
+                  (10.5M nodes) to 1e8 scattered targets in [-1.2, 1.2]^2.
+Every result states its error against the oracle's direct FP64 sum on a
+seeded sample of its targets, from the outputs of the last timed step; the
+run exits 3 if any exceeds the tolerance.  Per-stage times come from a
+separate pass with the plans' stage events on (the timed steps carry none).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload star5_F100|starshade_sweep|randstar_F1000|
-                                   randstar_batch32|koch_L13]
+                                   randstar_batch32|koch_L13] [--no-extras]
 Under torchrun each rank runs an independent copy (weak scaling, no data
 collective); rank 0 prints one JSON line.
 """
@@ -183,9 +189,151 @@ class ClockSampler:
         return out
 
 
-# ------------------------------------------------------------------ CPU oracle timing
-def oracle_rate(cfg, targets, budget_s):
-    """Oracle (as it stands) on a bounded sample: quadrature + direct sum, targets/s."""
+# ------------------------------------------------------------------ shared helpers
+def _peaks():
+    """(HBM GB/s, source) from the measured peaks, else the stated fallback."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except Exception:
+        return 6800.0, "fallback 6800 GB/s"
+
+
+def rel_error(u, ref, tol, occulter=False):
+    """Relative L2 error of the aperture field u^ap against the oracle's on the
+    same targets (the tolerance's meaning: an occulter output u^oc is compared
+    as u^ap = 1 - u^oc, eq. bab), and the largest absolute difference (the
+    paper's metric on u^oc; Babinet only flips its sign)."""
+    u = np.asarray(u, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    if occulter:
+        u, ref = 1.0 - u, 1.0 - ref
+    d = u - ref
+    rel = float(np.linalg.norm(d) / max(np.linalg.norm(ref), 1e-300))
+    return {"rel_l2": rel, "field": "u^ap = 1 - u^oc" if occulter else "u^ap",
+            "max_abs": float(np.abs(d).max()) if d.size else 0.0,
+            "oracle_targets": int(ref.size), "tol": tol, "within_tol": bool(rel <= tol)}
+
+
+# Source files each measured kernel is built from (the DRAM traffic of an
+# ncu capture holds only while these are unchanged).
+KERNEL_SOURCES = {
+    "spread": ["spread.cuh", "k_spread_f32.cu", "internal.cuh"],
+    "interp": ["k_interp.cu", "spread.cuh", "dfloat.cuh", "internal.cuh"],
+    "fft": ["k_fft.cu", "internal.cuh"],
+    "nodes": ["k_nodes.cu", "dfloat.cuh", "internal.cuh"],
+}
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from one
+# ncu capture of the named workload) with the sha256 prefix of the kernel's
+# sources at the time of the capture.  A kernel whose sources changed since
+# reports traffic null.
+DRAM_TRAFFIC = {}
+
+
+def sources_sha(kind):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2010_05978_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stage_kind(stage):
+    s = stage.split(".")[-1]
+    if s.startswith("spread"):
+        return "spread"
+    if s.startswith("interp"):
+        return "interp"
+    if s.startswith("fft"):
+        return "fft"
+    if s.startswith("nodes") or s in ("scan", "scatter"):
+        return "nodes"
+    return None
+
+
+def measured_traffic(workload_name, stage):
+    """(bytes, note) of the ncu capture of this kernel on this workload, or
+    (None, why) when there is none or the kernel changed since."""
+    e = DRAM_TRAFFIC.get((workload_name, stage))
+    if e is None:
+        return None, "no ncu capture of this kernel on this workload"
+    kind = stage_kind(stage)
+    if kind is None or sources_sha(kind) != e["sources_sha"]:
+        return None, "kernel sources changed since the ncu capture"
+    return e["bytes"], e["note"]
+
+
+def roofline(workload_name, ab, per_launch, note):
+    """Roofline object of the stage with the largest time among those with
+    algorithmic bytes: achieved = algorithmic bytes / CUDA-event time."""
+    peak, src = _peaks()
+    dom = max((k for k in per_launch if k in ab), key=lambda k: per_launch[k])
+    achieved = ab[dom] / (per_launch[dom] * 1e-3) / 1e9
+    traffic, tnote = measured_traffic(workload_name, dom)
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "traffic_note": tnote,
+            "peak_source": src, "algorithmic_bytes": ab[dom], "ms_per_launch": per_launch[dom],
+            "timing": note}
+
+
+def time_steps(step, stream, steps, flush=None):
+    """Device time of each of `steps` calls of step(), CUDA events on the
+    launching stream; an L2 flush (not timed) before each."""
+    import torch
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step()
+        e.record(stream)
+        e.synchronize()
+        ms.append(s.elapsed_time(e))
+    return ms
+
+
+def stage_pass(plans, step, stream, steps, flush=None):
+    """Per-stage device times (ms per step) from a separate pass with the
+    plans' per-stage CUDA events on; `plans` is [(prefix, plan)].  Returns
+    (stage ms per step, ms per step of this pass)."""
+    for _, p in plans:
+        p.set_timing(True)
+    sums = {}
+
+    def one():
+        step()
+
+    ms = []
+    for _ in range(steps):
+        ms += time_steps(one, stream, 1, flush)
+        for pre, p in plans:
+            for k, v in p.stage_times().items():
+                key = pre + k
+                sums[key] = sums.get(key, 0.0) + v
+    for _, p in plans:
+        p.set_timing(False)
+    return {k: v / steps for k, v in sums.items()}, statistics.mean(ms)
+
+
+def timed_plan(make):
+    """A plan built by make() and its wall time with the device synchronised
+    on both sides (quadrature tables, sizes, allocations, autotuning)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p = make()
+    torch.cuda.synchronize()
+    return p, (time.perf_counter() - t0) * 1e3
+
+
+# ------------------------------------------------------------------ star workload (C2)
+def oracle_sample(cfg, targets, budget_s):
+    """The oracle (as it stands: quadrature rebuilt + direct FP64 sum) on a
+    bounded, seeded sample of the workload's targets, half on the grid and
+    half scattered.  Returns its rate and its values on the sample."""
     import oracle
     from oracle import direct
     fam = cfg["families"]
@@ -198,70 +346,129 @@ def oracle_rate(cfg, targets, budget_s):
     per_target = max((time.perf_counter() - t0) / 64, 1e-7)
     m = int(max(16, min(200000, budget_s / per_target)))
     m -= m % 2
-    ig = rng.choice(len(gx), m // 2, replace=False)
-    it = rng.choice(len(targets), m // 2, replace=False)
+    ig = np.sort(rng.choice(len(gx), m // 2, replace=False))
+    it = np.sort(rng.choice(len(targets), m // 2, replace=False))
     xi = np.concatenate([gx[ig], targets[it, 0]])
     eta = np.concatenate([gy[ig], targets[it, 1]])
     t0 = time.perf_counter()
-    oracle.field(fam, cfg["lam"], cfg["z"], xi, eta)
+    u = oracle.field(fam, cfg["lam"], cfg["z"], xi, eta)
     dt = time.perf_counter() - t0
-    return {"value": m / dt, "unit": UNIT, "cores": direct.max_threads(), "kind": "oracle",
+    rate = {"value": m / dt, "unit": UNIT, "cores": direct.max_threads(), "kind": "oracle",
             "sample": "%d targets (%d grid + %d scattered) of the same workload, quadrature "
                       "rebuilt + direct O(NM) FP64 sum (eq. faq), %.1f s" % (m, m // 2, m // 2, dt)}
+    return {"rate": rate, "ig": ig, "it": it, "ref1": u[: m // 2], "ref3": u[m // 2:]}
 
 
-def run_reference(args, rank, world):
-    cfg, targets = workload()
-    from oracle import build as obuild
-    obuild.build()
-    if rank != 0:
-        return
-    budget = 6.0
-    for _ in range(args.warmup):
-        oracle_rate(cfg, targets, 0.5)
-    vals, times = [], []
-    for _ in range(args.steps):
-        r = oracle_rate(cfg, targets, budget)
-        vals.append(r["value"])
-        times.append(budget)
-    v = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 2e6 / v * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(cfg, args.gpus, args.precision),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def star_error(out1, out3, sample, tol):
+    import torch
+    u1 = out1.reshape(-1)[torch.as_tensor(sample["ig"], device=out1.device)]
+    u3 = out3[torch.as_tensor(sample["it"], device=out3.device)]
+    u1, u3 = u1.cpu().numpy(), u3.cpu().numpy()
+    e1 = rel_error(u1, sample["ref1"], tol)
+    e3 = rel_error(u3, sample["ref3"], tol)
+    return {"t1_rel_l2": e1["rel_l2"], "t3_rel_l2": e3["rel_l2"],
+            "max_abs_uoc": max(e1["max_abs"], e3["max_abs"]),
+            "oracle_targets": e1["oracle_targets"] + e3["oracle_targets"], "tol": tol,
+            "within_tol": e1["within_tol"] and e3["within_tol"],
+            "against": "the oracle's direct FP64 sum (eq. faq) on its own quadrature, on the "
+                       "cpu_baseline sample's targets; outputs of the last timed step"}
 
 
-# ------------------------------------------------------------------ GPU arm
-def aggregate_ranks(total_ms, steps, units_per_step, world, device="cpu"):
-    """Weak scaling over independent replicas: every rank processed
-    units_per_step per step; the job's time is the slowest rank's (max over
-    ranks, the only collective).  Returns (ms per step, job units per second)."""
+def star_arm(args, dev, local_rank, world, precision, steps, warmup, sample=None, e2e=True):
+    """Times the star workload (type 1 on the 1000^2 grid + type 3 on 1e6
+    scattered targets, nodes regenerated every step) in one precision."""
+    import torch
+    from paper_2010_05978_gb300 import Plan
+    cfg, targets_np = workload()
+    fam, g = cfg["families"], cfg["grid"]
+    stream = torch.cuda.current_stream()
+    # the type-1 and type-3 evaluations are independent: each plan has its
+    # own stream and a step forks the second off the first and joins it back
+    stream3 = torch.cuda.Stream()
+    cdt = star_cdtype(torch, precision)
+    targets = torch.tensor(targets_np, dtype=torch.float64, device=dev)
+    p1, ms1 = timed_plan(lambda: Plan(fam, cfg["lam"], cfg["z"], TOL, precision=precision, grid=g,
+                                      recompute_nodes=True, sync_status=False))
+    p3, ms3 = timed_plan(lambda: Plan(fam, cfg["lam"], cfg["z"], TOL, precision=precision,
+                                      box=(-1.5, 1.5, -1.5, 1.5), recompute_nodes=True,
+                                      sync_status=False, stream=stream3))
+    info1, info3 = p1.info(), p3.info()
+    out1 = torch.empty((g["n2"], g["n1"]), dtype=cdt, device=dev)
+    out3 = torch.empty((M3,), dtype=cdt, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        stream3.wait_stream(stream)
+        p1.eval(None, out1)
+        p3.eval(targets, out3)
+        stream.wait_stream(stream3)
+
+    def step_serial():
+        p1.eval(None, out1)
+        stream3.wait_stream(stream)
+        p3.eval(targets, out3)
+        stream.wait_stream(stream3)
+
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    p1.check()
+    p3.check()
+    clocks = ClockSampler(local_rank) if local_rank == 0 else None
     if world > 1:
-        import torch
         import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    ms_per_step = total_ms / steps
-    return ms_per_step, units_per_step * world / (ms_per_step * 1e-3)
-
-
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
-# ncu capture of this workload) of the kernels that lead the star step, as
-# summarised in profiles/k_spread_star5_F100_fp32.md and
-# profiles/k_interp_coop_star5_F100_fp32.md.  A kernel changed since its
-# capture is left out (traffic null).
-STAR_DRAM_TRAFFIC = {
-    "t3.spread": 22_555_904,
-    "t1.spread": 21_811_712,
-    "t3.interp_epilogue": 21_467_904 + 2_304_000,
-}
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    step_ms = time_steps(step, stream, steps, flush)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    p1.check()
+    p3.check()
+    ms_per_step, value = aggregate_ranks(sum(step_ms), steps, 2e6, world, dev)
+    err = star_error(out1, out3, sample, TOL) if sample is not None else None
+    stages, stage_step_ms = stage_pass([("t1.", p1), ("t3.", p3)], step_serial, stream,
+                                       max(3, min(steps, 10)), flush)
+    res = {"ms_per_step": ms_per_step, "value": value, "plan_ms": ms1 + ms3,
+           "plan_plus_eval_ms": ms1 + ms3 + ms_per_step, "error": err,
+           "stages_ms_per_step": {k: round(v, 5) for k, v in sorted(stages.items())},
+           "stage_pass_ms_per_step": stage_step_ms,
+           "launches_per_step": info1["launches_per_eval"] + info3["launches_per_eval"],
+           "clocks": clk, "info": (info1, info3)}
+    ab = algorithmic_bytes(info1, info3, info1["n_nodes"], precision)
+    res["roofline"] = roofline("star5_F100" if precision == "fp32" else "star5_F100_fp64", ab,
+                               stages, "stage pass: per-stage CUDA events on each plan's stream, "
+                               "type 1 then type 3 serialised (no overlap), %d steps; the headline "
+                               "step is timed without stage events" % max(3, min(steps, 10)))
+    if e2e:
+        # end to end through the C ABI with host buffers: pinned host arrays
+        # in and out, host<->device copies inside the timed region; each step
+        # ends with one device synchronisation.
+        h_t3 = torch.from_numpy(targets_np).pin_memory().numpy()
+        h_out1 = torch.empty((g["n2"], g["n1"]), dtype=cdt, pin_memory=True).numpy()
+        h_out3 = torch.empty((M3,), dtype=cdt, pin_memory=True).numpy()
+        for _ in range(2):
+            p1.eval_host(None, h_out1)
+            p3.eval_host(h_t3, h_out3)
+            torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(max(3, min(steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p1.eval_host(None, h_out1)
+            p3.eval_host(h_t3, h_out3)
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        p1.check()
+        p3.check()
+        res["e2e"] = {"value": 2e6 * world / (statistics.median(e2e_ms) * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(h_t3.nbytes),
+                      "d2h_bytes_per_step": int(h_out1.nbytes + h_out3.nbytes)}
+    p1.close()
+    p3.close()
+    return res
 
 
 def algorithmic_bytes(info1, info3, n_nodes, precision="fp32"):
@@ -290,9 +497,50 @@ def star_cdtype(torch, precision):
     return torch.complex64 if precision == "fp32" else torch.complex128
 
 
-def run_ours(args, rank, world, local_rank):
+def run_reference(args, rank, world):
+    cfg, targets = workload()
+    from oracle import build as obuild
+    obuild.build()
+    if rank != 0:
+        return
+    budget = 6.0
+    for _ in range(args.warmup):
+        oracle_sample(cfg, targets, 0.5)
+    vals = []
+    for _ in range(args.steps):
+        r = oracle_sample(cfg, targets, budget)["rate"]
+        vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 2e6 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(cfg, args.gpus, args.precision),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def aggregate_ranks(total_ms, steps, units_per_step, world, device="cpu"):
+    """Weak scaling over independent replicas: every rank processed
+    units_per_step per step; the job's time is the slowest rank's (max over
+    ranks, the only collective).  Returns (ms per step, job units per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / steps
+    return ms_per_step, units_per_step * world / (ms_per_step * 1e-3)
+
+
+def _setup(rank, world, local_rank):
     import torch
-    from paper_2010_05978_gb300 import Plan, build
+    from paper_2010_05978_gb300 import build
     if rank == 0 or world == 1:
         build.build()
     if world > 1:
@@ -300,155 +548,196 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         build.build()
     torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    cfg, targets_np = workload()
-    fam, g = cfg["families"], cfg["grid"]
-    stream = torch.cuda.current_stream()
-    # the type-1 and type-3 evaluations are independent: each plan has its
-    # own stream and a step forks the second off the first and joins it back
-    stream3 = torch.cuda.Stream()
+    return torch.device("cuda", local_rank)
+
+
+def _compact(res, keys=("ms_per_step", "value", "plan_ms", "plan_plus_eval_ms", "error",
+                        "roofline", "stages_ms_per_step", "clocks")):
+    return {k: res[k] for k in keys if k in res}
+
+
+def run_ours(args, rank, world, local_rank):
+    """The headline line: the star workload in FP32 fast mode.  At one GPU the
+    same line also carries the plain FP64 path on the same workload and
+    tolerance, the 64-wavelength starshade sweep and the F = 1000 random
+    aperture with 1e8 targets, each with its own timing, roofline, error
+    against the oracle and CPU baseline."""
+    dev = _setup(rank, world, local_rank)
     prec = args.precision
-    cdt = star_cdtype(torch, prec)
-    p1 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision=prec, grid=g, recompute_nodes=True,
-              sync_status=False)
-    p3 = Plan(fam, cfg["lam"], cfg["z"], TOL, precision=prec, box=(-1.5, 1.5, -1.5, 1.5),
-              recompute_nodes=True, sync_status=False, stream=stream3)
-    p1.set_timing(True)
-    p3.set_timing(True)
-    info1, info3 = p1.info(), p3.info()
-    targets = torch.tensor(targets_np, dtype=torch.float64, device=dev)
-    out1 = torch.empty((g["n2"], g["n1"]), dtype=cdt, device=dev)
-    out3 = torch.empty((M3,), dtype=cdt, device=dev)
+    cfg, targets_np = workload()
+    sample = None
+    if rank == 0:
+        from oracle import build as obuild
+        obuild.build()
+        # the oracle on a bounded sample: the CPU baseline, and the reference
+        # values the GPU outputs of the timed steps are checked against
+        sample = oracle_sample(cfg, targets_np, 8.0)
+    main = star_arm(args, dev, local_rank, world, prec, args.steps, args.warmup, sample)
+    extras = {}
+    if world == 1 and args.extras and prec == "fp32":
+        f64 = star_arm(args, dev, local_rank, world, "fp64", min(args.steps, 20), 3, sample,
+                       e2e=False)
+        extras["fp64_path"] = dict(_compact(f64), precision="fp64 throughout, tol 1e-6",
+                                   fp32_speedup=main["value"] / f64["value"])
+        extras["sweep"] = sweep_arm(args, dev, local_rank, 1, 64, args.steps, args.warmup,
+                                    budget_s=5.0)
+        extras["randstar_F1000"] = randstar_arm(args, dev, local_rank, 1, False,
+                                                min(args.steps, 10), 3, budget_s=5.0)
+    if rank != 0:
+        return
+    info1, info3 = main["info"]
+    line = {
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": main["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": config_dict(cfg, world, prec),
+        "roofline": main["roofline"],
+        "error": main["error"],
+        "plan_ms": main["plan_ms"], "plan_plus_eval_ms": main["plan_plus_eval_ms"],
+        "stages_ms_per_step": main["stages_ms_per_step"],
+        "stage_pass_ms_per_step": main["stage_pass_ms_per_step"],
+        "cpu_baseline": sample["rate"],
+        "e2e": main["e2e"],
+        "gpu_launches": main["launches_per_step"] * args.steps,
+        "clocks": main["clocks"],
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    bad = [k for k, v in [("star", line["error"])] + [(k, e.get("error")) for k, e in extras.items()]
+           if v is not None and not v["within_tol"]]
+    if bad:
+        sys.stderr.write("error above tolerance in: %s\n" % ", ".join(bad))
+        sys.exit(3)
+
+
+# ------------------------------------------------------------------ starshade sweep (C3)
+def sweep_oracle_sample(cfg, budget_s):
+    """Oracle sweeps/s: direct sums of three wavelengths on sampled grid
+    targets, scaled to the full sweep (64 wavelengths x 512^2 targets); its
+    values on the sample are returned for the error of the GPU sweep."""
+    import oracle
+    from oracle import direct
+    g = cfg["grid"]
+    gx, gy = oracle.grid_targets(g["n1"], g["n2"], g["h"])
+    nb = len(cfg["problems"])
+    which = (0, nb // 2, nb - 1)
+    rng = W.rng(3, 21)
+    q = cfg["problems"][0]
+    t0 = time.perf_counter()
+    oracle.field(q["families"], q["lam"], q["z"], gx[:32], gy[:32])
+    per = max((time.perf_counter() - t0) / 32, 1e-7)
+    m = int(max(16, min(100000, budget_s / per / len(which))))
+    t_total, n_total, refs = 0.0, 0, []
+    for b in which:
+        q = cfg["problems"][b]
+        idx = np.sort(rng.choice(len(gx), m, replace=False))
+        t0 = time.perf_counter()
+        u = oracle.field(q["families"], q["lam"], q["z"], gx[idx], gy[idx], output="occulter")
+        t_total += time.perf_counter() - t0
+        n_total += m
+        refs.append((b, idx, u))
+    per_target = t_total / n_total
+    sweep_s = per_target * len(gx) * nb   # the whole sweep
+    rate = {"value": 1.0 / sweep_s, "unit": SWEEP_UNIT, "cores": direct.max_threads(),
+            "kind": "oracle",
+            "sample": "%d grid targets at each of 3 wavelengths (400, ~700, 1000 nm), quadrature "
+                      "rebuilt + direct O(NM) FP64 sum (eq. faq), %.1f s; scaled to %d x 512^2"
+                      % (m, t_total, nb)}
+    return rate, refs
+
+
+def sweep_arm(args, dev, local_rank, world, n_lambda, steps, warmup, budget_s=10.0):
+    import torch
+    from paper_2010_05978_gb300 import BatchPlan
+    cfg, in_pupil = sweep_workload(n_lambda)
+    g = cfg["grid"]
+    B = len(cfg["problems"])
+    stream = torch.cuda.current_stream()
+    p, plan_ms = timed_plan(lambda: BatchPlan(cfg["problems"], TOL, precision="fp32", grid=g,
+                                              output="occulter", recompute_nodes=True,
+                                              sync_status=False))
+    info = p.info()
+    out = torch.empty((B, g["n2"], g["n1"]), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def step():
-        stream3.wait_stream(stream)
-        p1.eval(None, out1)
-        p3.eval(targets, out3)
-        stream.wait_stream(stream3)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
+    for _ in range(max(warmup, 3)):
+        p.eval(out=out)
     torch.cuda.synchronize()
-    p1.check()
-    p3.check()
-
-    stage_sum = {}
-    step_ms = []
-    clocks = ClockSampler(local_rank) if rank == 0 else None
+    p.check()
+    clocks = ClockSampler(local_rank) if local_rank == 0 else None
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
-    for _ in range(args.steps):
-        flush.zero_()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        step()
-        e.record(stream)
-        e.synchronize()
-        step_ms.append(s.elapsed_time(e))
-        for k, v in p1.stage_times().items():
-            stage_sum["t1." + k] = stage_sum.get("t1." + k, 0.0) + v
-        for k, v in p3.stage_times().items():
-            stage_sum["t3." + k] = stage_sum.get("t3." + k, 0.0) + v
+    step_ms = time_steps(lambda: p.eval(out=out), stream, steps, flush)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    p1.check()
-    p3.check()
-    ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, 2e6, world, dev)
+    p.check()
+    ms_per_step, value = aggregate_ranks(sum(step_ms), steps, 1.0, world, dev)
+    cpu, refs, err = None, None, None
+    if local_rank == 0:
+        cpu, refs = sweep_oracle_sample(cfg, budget_s)
+        us = np.concatenate([out[b].reshape(-1)[torch.as_tensor(idx, device=dev)].cpu().numpy()
+                             for b, idx, _ in refs])
+        ref = np.concatenate([u for _, _, u in refs])
+        e = rel_error(us, ref, TOL, occulter=True)
+        err = dict(e, against="the oracle's direct FP64 sum (eq. faq) on its own quadrature, "
+                              "u^oc at sampled grid targets of 3 wavelengths (400, ~700, 1000 nm); "
+                              "outputs of the last timed step")
+    stages, stage_ms = stage_pass([("", p)], lambda: p.eval(out=out), stream,
+                                  max(3, min(steps, 10)), flush)
 
-    # ---------------- end-to-end through the C ABI with host buffers
-    # pinned host buffers (numpy views); the plans do not synchronise, so each
-    # step ends with one device synchronisation, after which h_out1 and
-    # h_out3 hold the results.  The two plans' streams (and each plan's own
-    # copy stream for the targets) overlap transfers with compute.
-    h_t3 = torch.from_numpy(targets_np).pin_memory().numpy()
-    h_out1 = torch.empty((g["n2"], g["n1"]), dtype=cdt, pin_memory=True).numpy()
-    h_out3 = torch.empty((M3,), dtype=cdt, pin_memory=True).numpy()
-    for _ in range(2):
-        p1.eval_host(None, h_out1)
-        p3.eval_host(h_t3, h_out3)
-        torch.cuda.synchronize()
+    # end to end: the same call plus the read-back of every field to pinned host memory
+    h_out = torch.empty((B, g["n2"], g["n1"]), dtype=torch.complex64, pin_memory=True)
     e2e_ms = []
-    for _ in range(max(3, min(args.steps, 10))):
+    for i in range(max(3, min(steps, 10)) + 1):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        p1.eval_host(None, h_out1)
-        p3.eval_host(h_t3, h_out3)
+        p.eval(out=out)
+        h_out.copy_(out, non_blocking=True)
         torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = 2e6 * world / (statistics.median(e2e_ms) * 1e-3)
-    p1.check()
-    p3.check()
+        if i:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    c64, rec = 8, 24
+    nf1, nf2, n1, n2 = info["nf1"], info["nf2"], g["n1"], g["n2"]
+    ab = {"spread": info["n_nodes"] * rec + B * nf1 * nf2 * c64,
+          "fft_rows": B * (nf1 * nf2 + n1 * nf2) * c64,
+          "fft_cols_epilogue": B * (n1 * nf2 + n1 * n2) * c64}
+    res = {"metric": SWEEP_METRIC_N % B, "unit": SWEEP_UNIT, "ms_per_step": ms_per_step,
+           "value": value, "plan_ms": plan_ms, "plan_plus_eval_ms": plan_ms + ms_per_step,
+           "targets_per_s": value * B * in_pupil, "error": err,
+           "config": sweep_config(cfg, in_pupil, world),
+           "roofline": roofline("hg24_sweep%d" % B, ab, stages,
+                                "stage pass: per-stage CUDA events, %d steps; the sweep step is "
+                                "timed without stage events" % max(3, min(steps, 10))),
+           "stages_ms_per_step": {k: round(v, 5) for k, v in sorted(stages.items())},
+           "stage_pass_ms_per_step": stage_ms,
+           "cpu_baseline": cpu,
+           "e2e": {"value": world / (statistics.median(e2e_ms) * 1e-3), "unit": SWEEP_UNIT,
+                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(h_out.numel() * 8)},
+           "gpu_launches": info["launches_per_eval"] * steps, "clocks": clk,
+           "steps": steps}
+    p.close()
+    return res
 
+
+def run_sweep(args, rank, world, local_rank):
+    dev = _setup(rank, world, local_rank)
+    if rank == 0:
+        from oracle import build as obuild
+        obuild.build()
+    r = sweep_arm(args, dev, local_rank, world, args.lambdas, args.steps, args.warmup)
     if rank != 0:
         return
-    # ---------------- roofline of the dominant kernel
-    per_launch = {k: v / args.steps for k, v in stage_sum.items()}
-    ab = algorithmic_bytes(info1, info3, info1["n_nodes"], prec)
-    dominant = max((k for k in per_launch if k in ab), key=lambda k: per_launch[k])
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = ab[dominant] / (per_launch[dominant] * 1e-3) / 1e9
-    traffic = STAR_DRAM_TRAFFIC.get(dominant) if prec == "fp32" else None
-    cpu = oracle_rate(cfg, targets_np, 10.0)
-    launches = (info1["launches_per_eval"] + info3["launches_per_eval"]) * args.steps
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
-        "data": "synthetic", "config": config_dict(cfg, world, prec),
-        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
-                                    "fallback 6800 GB/s",
-                     "algorithmic_bytes": ab[dominant], "ms_per_launch": per_launch[dominant]},
-        "stages_ms_per_step": {k: round(v, 5) for k, v in sorted(per_launch.items())},
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_t3.nbytes),
-                "d2h_bytes_per_step": int(h_out1.nbytes + h_out3.nbytes)},
-        "gpu_launches": launches,
-        "clocks": clk,
-    }
+    line = {"metric": r["metric"], "value": r["value"], "unit": SWEEP_UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": r["config"]}
+    line.update({k: v for k, v in r.items() if k not in line and k not in ("metric", "steps")})
     print(json.dumps(line), flush=True)
-
-
-def sweep_oracle_rate(cfg, budget_s):
-    """Oracle sweeps/s: direct sums of a few wavelengths on sampled grid
-    targets, scaled to the full sweep (64 wavelengths x 512^2 targets)."""
-    import oracle
-    from oracle import direct
-    g = cfg["grid"]
-    gx, gy = oracle.grid_targets(g["n1"], g["n2"], g["h"])
-    probs = [cfg["problems"][i] for i in (0, len(cfg["problems"]) // 2, len(cfg["problems"]) - 1)]
-    rng = W.rng(3, 21)
-    q = probs[0]
-    t0 = time.perf_counter()
-    oracle.field(q["families"], q["lam"], q["z"], gx[:32], gy[:32])
-    per = max((time.perf_counter() - t0) / 32, 1e-7)
-    m = int(max(16, min(100000, budget_s / per / len(probs))))
-    t_total, n_total = 0.0, 0
-    for q in probs:
-        idx = rng.choice(len(gx), m, replace=False)
-        t0 = time.perf_counter()
-        oracle.field(q["families"], q["lam"], q["z"], gx[idx], gy[idx], output="occulter")
-        t_total += time.perf_counter() - t0
-        n_total += m
-    per_target = t_total / n_total
-    sweep_s = per_target * len(gx) * len(cfg["problems"])   # the whole sweep
-    return {"value": 1.0 / sweep_s, "unit": SWEEP_UNIT, "cores": direct.max_threads(),
-            "kind": "oracle",
-            "sample": "%d grid targets at each of 3 wavelengths (400, ~700, 1000 nm), quadrature "
-                      "rebuilt + direct O(NM) FP64 sum (eq. faq), %.1f s; scaled to %d x 512^2"
-                      % (m, t_total, len(cfg["problems"]))}
 
 
 def run_sweep_reference(args, rank, world):
@@ -458,9 +747,9 @@ def run_sweep_reference(args, rank, world):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        sweep_oracle_rate(cfg, 0.3)
-    vals = [sweep_oracle_rate(cfg, 6.0)["value"] for _ in range(args.steps)]
-    r = sweep_oracle_rate(cfg, 1.0)
+        sweep_oracle_sample(cfg, 0.3)
+    vals = [sweep_oracle_sample(cfg, 6.0)[0]["value"] for _ in range(args.steps)]
+    r = sweep_oracle_sample(cfg, 1.0)[0]
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": SWEEP_METRIC_N % args.lambdas, "value": v,
             "unit": SWEEP_UNIT,
@@ -475,106 +764,7 @@ def run_sweep_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_sweep(args, rank, world, local_rank):
-    import torch
-    from paper_2010_05978_gb300 import BatchPlan, build
-    if rank == 0 or world == 1:
-        build.build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        build.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    cfg, in_pupil = sweep_workload(args.lambdas)
-    g = cfg["grid"]
-    B = len(cfg["problems"])
-    stream = torch.cuda.current_stream()
-    p = BatchPlan(cfg["problems"], TOL, precision="fp32", grid=g, output="occulter",
-                  recompute_nodes=True, sync_status=False)
-    p.set_timing(True)
-    info = p.info()
-    out = torch.empty((B, g["n2"], g["n1"]), dtype=torch.complex64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    for _ in range(max(args.warmup, 3)):
-        p.eval(out)
-    torch.cuda.synchronize()
-    p.check()
-    stage_sum, step_ms = {}, []
-    clocks = ClockSampler(local_rank) if rank == 0 else None
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-    for _ in range(args.steps):
-        flush.zero_()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        p.eval(out)
-        e.record(stream)
-        e.synchronize()
-        step_ms.append(s.elapsed_time(e))
-        for k, v in p.stage_times().items():
-            stage_sum[k] = stage_sum.get(k, 0.0) + v
-    torch.cuda.synchronize()
-    clk = clocks.stop() if clocks else None
-    p.check()
-    ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, 1.0, world, dev)
-
-    # end to end: the same call plus the read-back of every field to pinned host memory
-    h_out = torch.empty((B, g["n2"], g["n1"]), dtype=torch.complex64, pin_memory=True)
-    e2e_ms = []
-    for i in range(max(3, min(args.steps, 10)) + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        p.eval(out)
-        h_out.copy_(out, non_blocking=True)
-        torch.cuda.synchronize()
-        if i:
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = world / (statistics.median(e2e_ms) * 1e-3)
-    if rank != 0:
-        return
-    per_launch = {k: v / args.steps for k, v in stage_sum.items()}
-    c64, rec = 8, 24
-    nf1, nf2, n1, n2 = info["nf1"], info["nf2"], g["n1"], g["n2"]
-    ab = {"spread": info["n_nodes"] * rec + B * nf1 * nf2 * c64,
-          "fft_rows": B * (nf1 * nf2 + n1 * nf2) * c64,
-          "fft_cols_epilogue": B * (n1 * nf2 + n1 * n2) * c64}
-    dominant = max((k for k in per_launch if k in ab), key=lambda k: per_launch[k])
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = ab[dominant] / (per_launch[dominant] * 1e-3) / 1e9
-    cpu = sweep_oracle_rate(cfg, 10.0)
-    line = {
-        "metric": SWEEP_METRIC_N % B, "value": value, "unit": SWEEP_UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": sweep_config(cfg, in_pupil, world),
-        "targets_per_s": value * B * in_pupil,
-        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
-                                    "fallback 6800 GB/s",
-                     "algorithmic_bytes": ab[dominant], "ms_per_launch": per_launch[dominant]},
-        "stages_ms_per_step": {k: round(v, 5) for k, v in sorted(per_launch.items())},
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": SWEEP_UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": int(h_out.numel() * 8)},
-        "gpu_launches": info["launches_per_eval"] * args.steps,
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
-
-
-# ------------------------------------------------------------------ F = 1000 random aperture
+# ------------------------------------------------------------------ F = 1000 random aperture (C5)
 R1000_METRIC = "Fresnel target pts/sec at 1e-6 rel L2 err (F=1000, 1e7 nodes, 1e8 scattered targets)"
 BATCH_METRIC = "Fresnel target pts/sec at 1e-6 rel L2 err (32-instance batch, 1e5-2e6 nodes, 5.5e7 targets)"
 
@@ -590,37 +780,31 @@ def _host_targets(counts, config_id, streams):
 
 def _oracle_rate_t3(problems, targets_per, budget_s):
     """Oracle targets/s on a bounded sample: a few targets of each problem,
-    quadrature rebuilt + direct FP64 sum, scaled by each problem's share."""
+    quadrature rebuilt + direct FP64 sum; returns the values too (None for
+    problems the budget left out)."""
     import oracle
     from oracle import direct
-    t_total, n_total = 0.0, 0
+    t_total, n_total, refs = 0.0, 0, []
     for q, (x, y) in zip(problems, targets_per):
+        if t_total > budget_s:
+            refs.append(None)
+            continue
         t0 = time.perf_counter()
-        oracle.field(q["families"], q["lam"], q["z"], x, y)
+        refs.append(oracle.field(q["families"], q["lam"], q["z"], x, y))
         t_total += time.perf_counter() - t0
         n_total += len(x)
-        if t_total > budget_s:
-            break
-    return n_total / t_total, direct.max_threads(), n_total, t_total
+    return n_total / t_total, direct.max_threads(), n_total, t_total, refs
 
 
-def run_randstar(args, rank, world, local_rank, batch):
+def randstar_arm(args, dev, local_rank, world, batch, steps, warmup, budget_s=10.0):
     import torch
-    from paper_2010_05978_gb300 import BatchPlan, Plan, build
-    if rank == 0 or world == 1:
-        build.build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        build.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
+    from paper_2010_05978_gb300 import BatchPlan, Plan
     box = (-1.2, 1.2, -1.2, 1.2)
     if batch:
         problems, counts = W.random_star_batch()
         h_t = _host_targets(counts, 5, [100 + i for i in range(len(counts))])
-        p = BatchPlan(problems, TOL, precision="fp32", box=box, recompute_nodes=True,
-                      sync_status=False)
+        p, plan_ms = timed_plan(lambda: BatchPlan(problems, TOL, precision="fp32", box=box,
+                                                  recompute_nodes=True, sync_status=False))
         step = lambda t, o: p.eval(t, counts, o)
         metric, name = BATCH_METRIC, "randstar_batch32"
     else:
@@ -628,9 +812,9 @@ def run_randstar(args, rank, world, local_rank, batch):
         problems = [{"families": cfg["families"], "lam": cfg["lam"], "z": cfg["z"]}]
         counts = [100_000_000]
         h_t = _host_targets(counts, 5, [1])
-        p = Plan(cfg["families"], cfg["lam"], cfg["z"], TOL, precision="fp32", box=box,
-                 recompute_nodes=True, sync_status=False)
-        p.set_timing(True)
+        p, plan_ms = timed_plan(lambda: Plan(cfg["families"], cfg["lam"], cfg["z"], TOL,
+                                             precision="fp32", box=box, recompute_nodes=True,
+                                             sync_status=False))
         step = lambda t, o: p.eval(t, o)
         metric, name = R1000_METRIC, "randstar20_F1000"
     total = sum(counts)
@@ -638,32 +822,47 @@ def run_randstar(args, rank, world, local_rank, batch):
     t = torch.from_numpy(h_t).to(dev)
     out = torch.empty(total, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream()
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         step(t, out)
     torch.cuda.synchronize()
     p.check()
-    clocks = ClockSampler(local_rank) if rank == 0 else None
+    clocks = ClockSampler(local_rank) if local_rank == 0 else None
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
-    step_ms, stage_sum = [], {}
-    for _ in range(args.steps):       # inputs (1.6 GB / 0.9 GB) are larger than L2
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        step(t, out)
-        e.record(stream)
-        e.synchronize()
-        step_ms.append(s.elapsed_time(e))
-        if not batch:
-            for k, v in p.stage_times().items():
-                stage_sum[k] = stage_sum.get(k, 0.0) + v
+    # inputs (1.6 GB / 0.9 GB of targets) are larger than L2: no flush
+    step_ms = time_steps(lambda: step(t, out), stream, steps)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
     p.check()
-    ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, float(total), world, dev)
+    ms_per_step, value = aggregate_ranks(sum(step_ms), steps, float(total), world, dev)
+    # the oracle on a bounded sample of the same targets: CPU baseline and error
+    cpu, err = None, None
+    if local_rank == 0:
+        sample, offs = [], []
+        off = 0
+        for i, m in enumerate(counts):
+            idx = np.sort(W.rng(5, 900 + i).choice(m, 8 if batch else 200, replace=False))
+            sample.append((h_t[off + idx, 0], h_t[off + idx, 1]))
+            offs.append(off + idx)
+            off += m
+        rate, cores, n_s, t_s, refs = _oracle_rate_t3(problems, sample, budget_s)
+        keep = [i for i, r in enumerate(refs) if r is not None]
+        gidx = np.concatenate([offs[i] for i in keep])
+        ref = np.concatenate([refs[i] for i in keep])
+        u = out[torch.as_tensor(gidx, device=dev)].cpu().numpy()
+        err = dict(rel_error(u, ref, TOL),
+                   against="the oracle's direct FP64 sum (eq. faq) on its own quadrature at "
+                           "sampled targets; outputs of the last timed step")
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d targets of the same instances, quadrature rebuilt + direct O(NM) "
+                         "FP64 sum (eq. faq), %.1f s" % (n_s, t_s)}
+    stages, stage_ms = {}, None
+    if not batch:   # stage times are not kept inside the batch's captured graph
+        stages, stage_ms = stage_pass([("", p)], lambda: step(t, out), stream, 3)
     # end to end: host targets in, host fields out, inside the timed region
     h_out = torch.empty(total, dtype=torch.complex64, pin_memory=True)
     h_in = torch.from_numpy(h_t).pin_memory()
@@ -678,61 +877,59 @@ def run_randstar(args, rank, world, local_rank, batch):
         if i:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = total * world / (statistics.median(e2e_ms) * 1e-3)
-    if rank != 0:
-        return
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
+    peak, src = _peaks()
     c64 = 8
-    if batch:   # stage times are not kept inside the captured graph: whole step
+    if batch:
         ab = total * (16 + c64) + info["n_nodes"] * 24
         roof = {"bound": "hbm", "kernel": "whole batch step (one graph)", "achieved":
                 ab / (ms_per_step * 1e-3) / 1e9, "algorithmic_bytes": ab,
-                "ms_per_launch": ms_per_step}
+                "ms_per_launch": ms_per_step, "peak": peak, "unit": "GB/s",
+                "frac": ab / (ms_per_step * 1e-3) / 1e9 / peak, "traffic": None,
+                "traffic_note": "whole step, not one kernel", "peak_source": src,
+                "timing": "the timed steps"}
     else:
-        per = {k: v / args.steps for k, v in stage_sum.items()}
         g = info["nf1"] * info["nf2"]
         F = info["nfft1"] * info["nfft2"]
         ab = {"spread": info["n_nodes"] * 24 + g * c64,
               "fft_rows": (g + info["nf2"] * info["nfft1"]) * c64,
               "fft_cols": (info["nf2"] * info["nfft1"] + F) * c64,
               "interp_epilogue": total * (16 + c64)}
-        dom = max((k for k in per if k in ab), key=lambda k: per[k])
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ab[dom] / (per[dom] * 1e-3) / 1e9,
-                "algorithmic_bytes": ab[dom], "ms_per_launch": per[dom]}
-    roof.update({"peak": peak, "unit": "GB/s", "frac": roof["achieved"] / peak, "traffic": None,
-                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
-                                "fallback 6800 GB/s"})
-    sample = []
-    off = 0
-    for i, m in enumerate(counts):
-        idx = W.rng(5, 900 + i).choice(m, 8 if batch else 200, replace=False)
-        sample.append((h_t[off + idx, 0], h_t[off + idx, 1]))
-        off += m
-    rate, cores, n_s, t_s = _oracle_rate_t3(problems, sample, 10.0)
-    line = {
-        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": name, "targets": total, "nodes": info["n_nodes"],
-                   "instances": len(problems), "tol": TOL,
-                   "precision": "fp32 spread/fft/interp, double-float phases",
-                   "nodes_recomputed_each_step": True,
-                   "l2": "inputs larger than L2 (targets %.1f GB)" % (16 * total / 1e9),
-                   "parallelism": "replicas x%d (independent instances, no collective)" % world},
-        "roofline": roof,
-        "stages_ms_per_step": {k: round(v / args.steps, 4) for k, v in sorted(stage_sum.items())},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d targets of the same instances, quadrature rebuilt + "
-                                   "direct O(NM) FP64 sum (eq. faq), %.1f s" % (n_s, t_s)},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(16 * total),
-                "d2h_bytes_per_step": int(8 * total)},
-        "gpu_launches": p.info()["launches_per_eval"] * args.steps,
-        "clocks": clk,
-    }
+        roof = roofline(name, ab, stages, "stage pass: per-stage CUDA events, 3 steps; the "
+                        "headline step is timed without stage events")
+    res = {"metric": metric, "unit": UNIT, "ms_per_step": ms_per_step, "value": value,
+           "plan_ms": plan_ms, "plan_plus_eval_ms": plan_ms + ms_per_step, "error": err,
+           "config": {"workload": name, "targets": total, "nodes": info["n_nodes"],
+                      "instances": len(problems), "tol": TOL,
+                      "precision": "fp32 spread/fft/interp, double-float phases",
+                      "nodes_recomputed_each_step": True,
+                      "l2": "inputs larger than L2 (targets %.1f GB)" % (16 * total / 1e9),
+                      "parallelism": "replicas x%d (independent instances, no collective)" % world},
+           "roofline": roof,
+           "stages_ms_per_step": {k: round(v, 4) for k, v in sorted(stages.items())},
+           "stage_pass_ms_per_step": stage_ms,
+           "cpu_baseline": cpu,
+           "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(16 * total),
+                   "d2h_bytes_per_step": int(8 * total)},
+           "gpu_launches": info["launches_per_eval"] * steps, "clocks": clk, "steps": steps}
+    p.close()
+    del t, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_randstar(args, rank, world, local_rank, batch):
+    dev = _setup(rank, world, local_rank)
+    if rank == 0:
+        from oracle import build as obuild
+        obuild.build()
+    r = randstar_arm(args, dev, local_rank, world, batch, args.steps, args.warmup)
+    if rank != 0:
+        return
+    line = {"metric": r["metric"], "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": r["config"]}
+    line.update({k: v for k, v in r.items() if k not in line and k not in ("metric", "steps")})
     print(json.dumps(line), flush=True)
 
 
@@ -754,7 +951,7 @@ def run_randstar_reference(args, rank, world, batch):
         sample.append((x[: 4 if batch else 100], y[: 4 if batch else 100]))
     vals = []
     for _ in range(max(1, args.steps)):
-        rate, cores, n_s, t_s = _oracle_rate_t3(problems, sample, 8.0)
+        rate, cores, n_s, t_s, _ = _oracle_rate_t3(problems, sample, 8.0)
         vals.append(rate)
     v = statistics.median(vals)
     total = sum(counts)
@@ -769,13 +966,14 @@ def run_randstar_reference(args, rank, world, batch):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ Koch snowflake (Sec. 4.3)
 KOCH_METRIC = "Fresnel target pts/sec at 1e-6 rel L2 err (Koch snowflake L=13, 1000^2 grid)"
 KOCH_LEVEL, KOCH_LZ = 13, 0.01
 
 
 def _koch_oracle_rate(fams, budget_s):
     """The oracle as it stands (snowflake rule rebuilt + direct FP64 sum) on a
-    bounded sample of the 1000^2 grid's targets; targets/s."""
+    bounded sample of the 1000^2 grid's targets; targets/s, and its values."""
     import oracle
     from oracle import direct
     xi, eta = oracle.grid_targets(1000, 1000, 0.003)
@@ -784,11 +982,11 @@ def _koch_oracle_rate(fams, budget_s):
     oracle.field(fams, KOCH_LZ, 1.0, xi[:16], eta[:16], output="occulter")   # calibration
     per = max((time.perf_counter() - t0) / 16, 1e-6)
     m = int(max(16, min(4096, budget_s / per)))
-    idx = rng.choice(len(xi), m, replace=False)
+    idx = np.sort(rng.choice(len(xi), m, replace=False))
     t0 = time.perf_counter()
-    oracle.field(fams, KOCH_LZ, 1.0, xi[idx], eta[idx], output="occulter")
+    u = oracle.field(fams, KOCH_LZ, 1.0, xi[idx], eta[idx], output="occulter")
     dt = time.perf_counter() - t0
-    return m / dt, direct.max_threads(), m, dt
+    return m / dt, direct.max_threads(), m, dt, idx, u
 
 
 def run_koch(args, rank, world, local_rank):
@@ -796,21 +994,14 @@ def run_koch(args, rank, world, local_rank):
     by level: 67.2M nodes regenerated every step), type 1 to the 1000^2 grid
     over [-1.5, 1.5)^2 at lz = 0.01, occulter field, FP32 fast mode."""
     import torch
-    from paper_2010_05978_gb300 import Plan, build
-    if rank == 0 or world == 1:
-        build.build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        build.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
+    from paper_2010_05978_gb300 import Plan
+    dev = _setup(rank, world, local_rank)
     fams = W.koch_families(KOCH_LEVEL, KOCH_LZ)
     n_tri = sum(len(f["tri"]) for f in fams)
     g = W.grid_spec(1000, 1000, 0.003)
-    p = Plan(fams, KOCH_LZ, 1.0, TOL, precision="fp32", grid=g, output="occulter",
-             recompute_nodes=True, sync_status=False)
-    p.set_timing(True)
+    p, plan_ms = timed_plan(lambda: Plan(fams, KOCH_LZ, 1.0, TOL, precision="fp32", grid=g,
+                                         output="occulter", recompute_nodes=True,
+                                         sync_status=False))
     info = p.info()
     out = torch.empty((1000, 1000), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream()
@@ -825,20 +1016,14 @@ def run_koch(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
-    step_ms, stage_sum = [], {}
-    for _ in range(args.steps):       # the triangle list (3.2 GB) is larger than L2
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        p.eval(None, out)
-        e.record(stream)
-        e.synchronize()
-        step_ms.append(s.elapsed_time(e))
-        for k, v in p.stage_times().items():
-            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    # the triangle list (3.2 GB) is larger than L2: no flush
+    step_ms = time_steps(lambda: p.eval(None, out), stream, args.steps)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
     p.check()
     ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, 1e6, world, dev)
+    u_dev = out.reshape(-1).clone()
+    stages, stage_ms = stage_pass([("", p)], lambda: p.eval(None, out), stream, 3)
     h_out = torch.empty((1000, 1000), dtype=torch.complex64, pin_memory=True).numpy()
     e2e_ms = []
     for i in range(4):
@@ -852,27 +1037,20 @@ def run_koch(args, rank, world, local_rank):
     e2e = 1e6 * world / (statistics.median(e2e_ms) * 1e-3)
     if rank != 0:
         return
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    per = {k: v / args.steps for k, v in stage_sum.items()}
+    from oracle import build as obuild
+    obuild.build()
     N, c64 = info["n_nodes"], 8
     nf = info["nf1"] * info["nf2"]
     ab = {"nodes_chirp_count": 48 * n_tri + 24 * N,   # triangle vertices in, records out
           "spread": 24 * N + nf * c64,
           "fft_rows": (nf + 1000 * info["nf2"]) * c64,
           "fft_cols_epilogue": (1000 * info["nf2"] + 1000 * 1000) * c64}
-    dom = max((k for k in per if k in ab), key=lambda k: per[k])
-    roof = {"bound": "hbm", "kernel": dom, "achieved": ab[dom] / (per[dom] * 1e-3) / 1e9,
-            "algorithmic_bytes": ab[dom], "ms_per_launch": per[dom], "peak": peak,
-            "unit": "GB/s", "traffic": None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else
-                           "fallback 6800 GB/s"}
-    roof["frac"] = roof["achieved"] / peak
-    rate, cores, n_s, t_s = _koch_oracle_rate(fams, 10.0)
+    roof = roofline("koch_L13", ab, stages, "stage pass: per-stage CUDA events, 3 steps; the "
+                    "headline step is timed without stage events")
+    rate, cores, n_s, t_s, idx, ref = _koch_oracle_rate(fams, 10.0)
+    u = u_dev[torch.as_tensor(idx, device=dev)].cpu().numpy()
+    err = dict(rel_error(u, ref, TOL, occulter=True), against="the oracle's direct FP64 sum "
+               "(eq. faq) on its own snowflake rule, u^oc at sampled grid targets; outputs of the last timed step")
     line = {
         "metric": KOCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -885,8 +1063,10 @@ def run_koch(args, rank, world, local_rank):
                    "nodes_recomputed_each_step": True,
                    "l2": "inputs larger than L2 (triangle list %.1f GB)" % (48 * n_tri / 1e9),
                    "parallelism": "replicas x%d (independent instances, no collective)" % world},
-        "roofline": roof,
-        "stages_ms_per_step": {k: round(v, 4) for k, v in sorted(per.items())},
+        "roofline": roof, "error": err, "plan_ms": plan_ms,
+        "plan_plus_eval_ms": plan_ms + ms_per_step,
+        "stages_ms_per_step": {k: round(v, 4) for k, v in sorted(stages.items())},
+        "stage_pass_ms_per_step": stage_ms,
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d grid targets, snowflake rule rebuilt + direct O(NM) "
                                    "FP64 sum (eq. faq), %.1f s" % (n_s, t_s)},
@@ -934,6 +1114,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="star5_F100 only: fp64 times the plain FP64 path at the same "
                          "tolerance (1e-6), for comparison with the FP32 fast mode")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="star5_F100 only: time the headline workload alone (no FP64 path, "
+                         "sweep or F=1000 objects in the line)")
     ap.add_argument("--lambdas", type=int, default=64,
                     help="starshade_sweep only: wavelengths per sweep (64 is the benchmark; "
                          "fewer for small profiling captures)")

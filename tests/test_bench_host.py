@@ -85,3 +85,40 @@ def test_precision_option_is_star_only():
     r = subprocess.run([sys.executable, bench.__file__, "--workload", "starshade_sweep",
                         "--precision", "fp64"], capture_output=True, text=True, timeout=120)
     assert r.returncode == 2 and "star5_F100" in r.stderr
+
+
+def test_rel_error_reports_l2_max_and_tolerance():
+    import numpy as np
+    ref = np.array([1.0 + 1.0j, -2.0, 0.5j, 3.0])
+    u = ref + np.array([1e-7, 0.0, -2e-7j, 0.0])
+    e = bench.rel_error(u, ref, 1e-6)
+    assert e["rel_l2"] == pytest.approx(np.sqrt(5e-14) / np.linalg.norm(ref))
+    assert e["max_abs"] == pytest.approx(2e-7)
+    assert e["oracle_targets"] == 4 and e["within_tol"]
+    assert not bench.rel_error(ref * (1 + 1e-5), ref, 1e-6)["within_tol"]
+    # an occulter field is graded on u^ap = 1 - u^oc: a small u^oc keeps its
+    # absolute error but not its relative one
+    oc = np.array([1e-3, -2e-3j, 1.5e-3])
+    e = bench.rel_error(oc + 1e-7, oc, 1e-6, occulter=True)
+    assert e["within_tol"] and e["field"].startswith("u^ap")
+    assert not bench.rel_error(oc + 1e-7, oc, 1e-6)["within_tol"]
+
+
+def test_traffic_is_dropped_when_the_kernel_sources_change(monkeypatch):
+    sha = bench.sources_sha("spread")
+    monkeypatch.setitem(bench.DRAM_TRAFFIC, ("w", "t3.spread"),
+                        {"bytes": 123, "sources_sha": sha, "note": "capture"})
+    assert bench.measured_traffic("w", "t3.spread") == (123, "capture")
+    monkeypatch.setitem(bench.DRAM_TRAFFIC, ("w", "t3.spread"),
+                        {"bytes": 123, "sources_sha": "0" * 16, "note": "capture"})
+    b, why = bench.measured_traffic("w", "t3.spread")
+    assert b is None and "changed" in why
+    assert bench.measured_traffic("w", "t1.fft_rows")[0] is None
+
+
+def test_roofline_picks_the_slowest_stage_with_bytes():
+    r = bench.roofline("w", {"a.spread": 4e9, "a.fft_rows": 1e9},
+                       {"a.spread": 2.0, "a.fft_rows": 1.0, "a.scan": 5.0}, "note")
+    assert r["kernel"] == "a.spread"
+    assert r["achieved"] == pytest.approx(4e9 / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])

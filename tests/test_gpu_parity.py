@@ -250,17 +250,22 @@ def test_star_F100_t1_full_size_sampled(prec):
     assert rel_l2(u[idx], ref) <= bar
 
 
-def test_star_F100_t3_full_size_sampled():
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_star_F100_t3_full_size_sampled(prec):
+    """Star at F = 100, 524,288 nodes, type 3 to 1e6 targets in the disc of
+    radius 1.5 (the benchmark's launch configuration), in both precisions:
+    fast mode at tol 1e-6 and FP64 at tol 1e-12 (bar 1e-10)."""
     cfg = W.star()
     fam = cfg["families"]
+    tol, bar = BARS[prec]
     xi, eta = W.disc_targets(1000000, 1.5, 2)
-    p = plan(fam, cfg["lam"], 1.0, 1e-6, precision="fp32", box=(-1.5, 1.5, -1.5, 1.5),
+    p = plan(fam, cfg["lam"], 1.0, tol, precision=prec, box=(-1.5, 1.5, -1.5, 1.5),
              recompute_nodes=True)
     t = torch.tensor(np.stack([xi, eta], 1), dtype=torch.float64, device="cuda")
     u = p.eval(t).cpu().numpy()
     idx = W.rng(2, 8).choice(len(xi), 400, replace=False)
     ref = oracle.field(fam, cfg["lam"], 1.0, xi[idx], eta[idx])
-    assert rel_l2(u[idx], ref) <= 1e-6
+    assert rel_l2(u[idx], ref) <= bar
 
 
 # ------------------------------------------------------------------ autotuned plans
