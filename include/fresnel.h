@@ -291,6 +291,29 @@ fresnel_status fresnel_eval_many(fresnel_plan_t plan, void* d_out);
 fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, double* d_grad);
 
 /*
+ * Gradient of a real loss of a GRID plan's output with respect to the
+ * boundary coefficients of its FRESNEL_FAMILY_FOURIER families, for
+ * optimising aperture shapes: the boundary r(t) = r0 + sum_k (a_k cos kt +
+ * b_k sin kt) about (cx, cy) enters through its Gauss-Legendre panel line
+ * rule (eq. vliq1) and the dilation rule (Sec. 3.1, eqs. aqnod, aqwei):
+ * x = c + alpha_l r(t_i) (cos t_i, sin t_i), w = alpha_l wtilde_l what_i r(t_i)^2.
+ * d_gamma as for fresnel_grad_profile (dL = Re sum_k conj(gamma_k) du_k).
+ * d_grad (DEVICE, FP64) receives, for every FOURIER family in plan order
+ * (problem-major, then family order), dL/dparams in the layout of its params
+ * [r0, a_1, b_1, ..., a_K, b_K] (1 + 2K values).  A starshade's disc is not a
+ * FOURIER family for this purpose.  It is the exact derivative of the
+ * computed (discretised) field: the same type-2 adjoint transform as
+ * fresnel_grad_profile, interpolated at every node with the kernel and its
+ * derivative, chained to dL/dr(t_i) per boundary node and summed against
+ * cos kt_i, sin kt_i in a fixed order.  Reuses the plan's spreading grid
+ * (evaluate again afterwards).  Errors: FRESNEL_ERR_ARG for a NULL pointer or
+ * a plan without FOURIER families; FRESNEL_ERR_UNSUPPORTED for scattered
+ * targets, a source screen or an FFT length beyond one pass.  Asynchronous
+ * unless opts.sync_status = 1.
+ */
+fresnel_status fresnel_grad_shape(fresnel_plan_t plan, const void* d_gamma, double* d_grad);
+
+/*
  * Evaluates u at the plan's targets (plans with one problem).
  * GRID plans: d_targets is ignored (may be NULL) and M must equal n1 * n2.
  * SCATTERED plans: d_targets is a DEVICE array of M (xi, eta) FP64 pairs

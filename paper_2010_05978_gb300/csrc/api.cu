@@ -155,6 +155,14 @@ struct Plan {
     long long* gofs = nullptr;    // their offsets in the gradient output
     int npf = 0;
     long long n_grad = 0;
+    // shape-gradient lists (Fourier boundary families), allocated on first use
+    bool shape_ready = false;
+    int* sf = nullptr;            // Fourier families (indices into fams)
+    long long* sbofs = nullptr;   // their first boundary node in rbuf
+    long long* sgofs = nullptr;   // their first coefficient in the gradient output
+    double* rbuf = nullptr;       // dL/dr_i per boundary node
+    int nsf = 0, max_params = 0;
+    long long n_sgrad = 0, n_sbdry = 0;
 
     size_t csize() const { return prec == FRESNEL_FP64 ? 16 : 8; }
     size_t rsize() const { return prec == FRESNEL_FP64 ? sizeof(NodeRec<double>) : sizeof(NodeRec<float>); }
@@ -1433,35 +1441,16 @@ Plan* as_plan(fresnel_plan_t h) {
 struct fresnel_plan_s {};   // opaque handle type; the handle points at a Plan
 
 namespace {
+// The adjoint transform shared by the profile and shape gradients:
+// btilde = FFT(sgn conj(gamma) ax ay) on the plan's spreading grid.
 template <typename T>
-fresnel_status grad_profile_impl(Plan* p, const void* d_gamma, double* d_grad) {
-    const bool dbl = sizeof(T) == 8;
+fresnel_status adjoint_grid(Plan* p, const void* d_gamma) {
     const size_t cs = p->csize();
     if (!p->adj_in) {
-        std::vector<int> pf;
-        std::vector<long long> gofs;
-        long long off = 0;
-        for (int i = 0; i < (int)p->fams.size(); ++i)
-            if (p->fams[i].kind == FRESNEL_FAMILY_PETALS) {
-                pf.push_back(i);
-                gofs.push_back(off);
-                off += p->fams[i].n_prof;
-            }
         FRES_TRY(dalloc(p, &p->adj_in, cs * (size_t)p->n1 * p->n2 * p->B));
         FRES_TRY(dalloc(p, &p->adj_rows, cs * (size_t)p->n2 * p->nf1 * p->B));
         FRES_TRY(dalloc(p, (void**)&p->contrib, sizeof(double) * p->N));
-        FRES_TRY(dalloc(p, (void**)&p->pf, sizeof(int) * std::max<size_t>(1, pf.size())));
-        FRES_TRY(dalloc(p, (void**)&p->gofs, sizeof(long long) * std::max<size_t>(1, gofs.size())));
-        if (!pf.empty()) {
-            FRES_CK(cudaMemcpyAsync(p->pf, pf.data(), sizeof(int) * pf.size(), cudaMemcpyHostToDevice, p->st));
-            FRES_CK(cudaMemcpyAsync(p->gofs, gofs.data(), sizeof(long long) * gofs.size(),
-                                    cudaMemcpyHostToDevice, p->st));
-        }
-        FRES_CK(cudaStreamSynchronize(p->st));
-        p->npf = (int)pf.size();
-        p->n_grad = off;
     }
-    if (p->n_grad > 0) FRES_CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * p->n_grad, p->st));
     launch_adj_prologue<T>(d_gamma, p->ax, p->ay, p->adj_in, p->n1, p->n2, p->B,
                            p->output == FRESNEL_OCCULTER, p->st);
     RowPassArgs ra{};
@@ -1488,9 +1477,82 @@ fresnel_status grad_profile_impl(Plan* p, const void* d_gamma, double* d_grad) {
     ca.in_bstride = (long long)p->n2 * p->nf1;
     ca.out_bstride = (long long)p->nf2 * p->nf1;
     launch_fft_cols<T>(p->fp2, ca, p->st);
-    launch_adj_nodes<T>(p->ft, p->node_blocks, p->grid, p->nf1, p->nf2, p->ks, p->contrib, p->st);
+    return FRESNEL_OK;
+}
+
+template <typename T>
+fresnel_status grad_shape_impl(Plan* p, const void* d_gamma, double* d_grad) {
+    if (!p->shape_ready) {
+        std::vector<int> sf;
+        std::vector<long long> bofs, gofs;
+        long long boff = 0, goff = 0;
+        int maxp = 0;
+        for (int i = 0; i < (int)p->fams.size(); ++i) {
+            const FamilyDev& f = p->fams[i];
+            if (f.kind != FRESNEL_FAMILY_FOURIER || f.ptr) continue;
+            sf.push_back(i);
+            bofs.push_back(boff);
+            gofs.push_back(goff);
+            boff += f.n_bdry;
+            goff += 1 + 2 * f.K;
+            maxp = std::max(maxp, 1 + 2 * f.K);
+        }
+        const size_t nf = std::max<size_t>(1, sf.size());
+        FRES_TRY(dalloc(p, (void**)&p->sf, sizeof(int) * nf));
+        FRES_TRY(dalloc(p, (void**)&p->sbofs, sizeof(long long) * nf));
+        FRES_TRY(dalloc(p, (void**)&p->sgofs, sizeof(long long) * nf));
+        FRES_TRY(dalloc(p, (void**)&p->rbuf, sizeof(double) * std::max<long long>(1, boff)));
+        if (!sf.empty()) {
+            FRES_CK(cudaMemcpyAsync(p->sf, sf.data(), sizeof(int) * sf.size(), cudaMemcpyHostToDevice, p->st));
+            FRES_CK(cudaMemcpyAsync(p->sbofs, bofs.data(), sizeof(long long) * sf.size(),
+                                    cudaMemcpyHostToDevice, p->st));
+            FRES_CK(cudaMemcpyAsync(p->sgofs, gofs.data(), sizeof(long long) * sf.size(),
+                                    cudaMemcpyHostToDevice, p->st));
+        }
+        FRES_CK(cudaStreamSynchronize(p->st));
+        p->nsf = (int)sf.size();
+        p->n_sgrad = goff;
+        p->n_sbdry = boff;
+        p->max_params = maxp;
+        p->shape_ready = true;
+    }
+    FRES_TRY(adjoint_grid<T>(p, d_gamma));
+    launch_adj_nodes<T>(p->ft, p->node_blocks, p->grid, p->nf1, p->nf2, p->ks, p->contrib, 1, p->st);
+    launch_adj_shape_reduce(p->ft.fams, p->sf, p->nsf, p->max_params, p->n_sbdry, p->sbofs,
+                            p->sgofs, p->contrib, p->rbuf, d_grad, p->st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fres_fail(FRESNEL_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return FRESNEL_OK;
+}
+
+template <typename T>
+fresnel_status grad_profile_impl(Plan* p, const void* d_gamma, double* d_grad) {
+    if (!p->pf) {
+        std::vector<int> pf;
+        std::vector<long long> gofs;
+        long long off = 0;
+        for (int i = 0; i < (int)p->fams.size(); ++i)
+            if (p->fams[i].kind == FRESNEL_FAMILY_PETALS) {
+                pf.push_back(i);
+                gofs.push_back(off);
+                off += p->fams[i].n_prof;
+            }
+        FRES_TRY(dalloc(p, (void**)&p->pf, sizeof(int) * std::max<size_t>(1, pf.size())));
+        FRES_TRY(dalloc(p, (void**)&p->gofs, sizeof(long long) * std::max<size_t>(1, gofs.size())));
+        if (!pf.empty()) {
+            FRES_CK(cudaMemcpyAsync(p->pf, pf.data(), sizeof(int) * pf.size(), cudaMemcpyHostToDevice, p->st));
+            FRES_CK(cudaMemcpyAsync(p->gofs, gofs.data(), sizeof(long long) * gofs.size(),
+                                    cudaMemcpyHostToDevice, p->st));
+        }
+        FRES_CK(cudaStreamSynchronize(p->st));
+        p->npf = (int)pf.size();
+        p->n_grad = off;
+    }
+    if (p->n_grad > 0) FRES_CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * p->n_grad, p->st));
+    FRES_TRY(adjoint_grid<T>(p, d_gamma));
+    launch_adj_nodes<T>(p->ft, p->node_blocks, p->grid, p->nf1, p->nf2, p->ks, p->contrib, 0, p->st);
     launch_adj_reduce(p->ft.fams, p->pf, p->gofs, p->npf, p->contrib, d_grad, p->st);
-    (void)dbl;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fres_fail(FRESNEL_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -1711,6 +1773,26 @@ fresnel_status fresnel_grad_profile(fresnel_plan_t plan, const void* d_gamma, do
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "profile gradients do not take a source screen");
     fresnel_status s = p->prec == FRESNEL_FP64 ? grad_profile_impl<double>(p, d_gamma, d_grad)
                                                : grad_profile_impl<float>(p, d_gamma, d_grad);
+    if (s != FRESNEL_OK) return s;
+    if (p->opts.sync_status) return read_status(p);
+    return FRESNEL_OK;
+}
+
+fresnel_status fresnel_grad_shape(fresnel_plan_t plan, const void* d_gamma, double* d_grad) {
+    Plan* p = as_plan(plan);
+    if (!p) return fres_fail(FRESNEL_ERR_ARG, "invalid plan handle");
+    if (p->tkind != FRESNEL_GRID)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "shape gradients need a GRID plan");
+    bool any = false;
+    for (const FamilyDev& f : p->fams) any = any || (f.kind == FRESNEL_FAMILY_FOURIER && !f.ptr);
+    if (!any) return fres_fail(FRESNEL_ERR_ARG, "the plan has no FOURIER family");
+    if (p->d1.big || p->d2.big)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "shape gradients need single-pass FFT lengths");
+    if (!d_gamma || !d_grad) return fres_fail(FRESNEL_ERR_ARG, "d_gamma or d_grad is NULL");
+    if (p->ft.scr.n1 > 0)
+        return fres_fail(FRESNEL_ERR_UNSUPPORTED, "shape gradients do not take a source screen");
+    fresnel_status s = p->prec == FRESNEL_FP64 ? grad_shape_impl<double>(p, d_gamma, d_grad)
+                                               : grad_shape_impl<float>(p, d_gamma, d_grad);
     if (s != FRESNEL_OK) return s;
     if (p->opts.sync_status) return read_status(p);
     return FRESNEL_OK;

@@ -297,11 +297,18 @@ void launch_nsli(const FamilyDev* fams_host, int nfam, double lz, const double* 
 template <typename T>
 void launch_adj_prologue(const void* gamma, const void* ax, const void* ay, void* out, int n1,
                          int n2, int B, int occulter, cudaStream_t st);
+// mode 0: PETALS profiles (per-node dL/dA_l contributions); mode 1: Fourier
+// boundary families (per-node dL/dr_i contributions)
 template <typename T>
 void launch_adj_nodes(const FamTable& ft, int nblocks, const void* bt, int nf1, int nf2,
-                      const KernelShape& ks, double* contrib, cudaStream_t st);
+                      const KernelShape& ks, double* contrib, int mode, cudaStream_t st);
 void launch_adj_reduce(const FamilyDev* fams, const int* pf, const long long* gofs, int npf,
                        const double* contrib, double* grad, cudaStream_t st);
+// Fourier families sf[0..nsf): dL/dr_i into rbuf (at bofs[f]), then dL/dp of
+// each family's 1 + 2K coefficients into grad (at gofs[f])
+void launch_adj_shape_reduce(const FamilyDev* fams, const int* sf, int nsf, int max_params,
+                             long long n_bdry_total, const long long* bofs, const long long* gofs,
+                             const double* contrib, double* rbuf, double* grad, cudaStream_t st);
 
 // k_fft.cu
 struct RowPassArgs {

@@ -15,8 +15,16 @@
 // A petal node (k, i, l) at radius r_l and angle theta = A_l t_i + 2 pi k / Np
 // has w = r_l what_l A_l omegahat_i, so dw/dA_l = r_l what_l omegahat_i and
 // d(x, y)/dA_l = r_l t_i (-sin theta, cos theta); dL/dA_l sums its nodes, and
-// the profile parameters follow from dA_l/dparam (petal.cuh).  This is the
-// exact derivative of the discrete map the plan computes.
+// the profile parameters follow from dA_l/dparam (petal.cuh).
+// A node (i, l) of a Fourier boundary family (boundary rule on Gauss-Legendre
+// panels, dilation rule of eqs. aqnod/aqwei about c) sits at
+// x = c + alpha_l r_i (cos t_i, sin t_i) with weight
+// w = alpha_l wtilde_l ((X_i - cx) V_i - (Y_i - cy) W_i) = alpha_l wtilde_l what_i r_i^2
+// (the tangent terms r'(t_i) cancel in the cross product), so
+// dL/dr_i = sum_l alpha_l (cos t_i dL/dx + sin t_i dL/dy) + 2 alpha_l wtilde_l what_i r_i dL/dw,
+// and dL/dp = sum_i dL/dr_i dr_i/dp for the coefficients p = (r0, a_k, b_k) of
+// r(t) = r0 + sum_k (a_k cos kt + b_k sin kt).  Both are the exact derivative
+// of the discrete map the plan computes.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -48,36 +56,14 @@ __global__ void k_adj_prologue(const cx_t<T>* __restrict__ gamma, const cx_t<T>*
     }
 }
 
-// One thread per node of the PETALS families (other families' blocks exit):
-// F, dF/dg by kernel and kernel-derivative interpolation of btilde (stored
-// fftshifted: natural cell l at (l + nf/2) mod nf), then dL/dA_l
-// contributions (FP64 throughout).
+// dL/dw, dL/dx, dL/dy of a node with strength w e^{i phi}: F and dF/dg by
+// kernel and kernel-derivative interpolation of btilde (stored fftshifted:
+// natural cell l at (l + nf/2) mod nf), FP64 throughout.
 template <typename T, int W>
-__global__ void __launch_bounds__(kNodeThreads)
-k_adj_nodes(FamTable ft, const cx_t<T>* __restrict__ bt, int nf1, int nf2, double beta,
-            double* __restrict__ contrib) {
-    __shared__ int s_fi;
-    if (threadIdx.x == 0) {
-        int a = 0, b = ft.nfam - 1;
-        while (a < b) {
-            const int mid = (a + b + 1) >> 1;
-            if (ft.blk0[mid] <= (int)blockIdx.x) a = mid;
-            else b = mid - 1;
-        }
-        s_fi = a;
-    }
-    __syncthreads();
-    const FamilyDev& f = ft.fams[s_fi];
-    if (f.kind != FRESNEL_FAMILY_PETALS) return;
-    const ChirpParams& cp = ft.cps[f.prob];
-    const long long j = (long long)(blockIdx.x - ft.blk0[s_fi]) * blockDim.x + threadIdx.x;
-    if (j >= f.n_nodes) return;
-    const long long k = j / f.n_bdry, q = j - k * f.n_bdry;
-    const int i = (int)(q / f.m), l = (int)(q - (long long)i * f.m);
-    const double u = f.bx[q], v = f.by[q];
-    const double cr = f.rot[2 * k], sr = f.rot[2 * k + 1];
-    const double dx0 = u * cr - v * sr, dy0 = u * sr + v * cr;   // x - c
-    const double x = f.cx + dx0, y = f.cy + dy0, w = f.bc[q];
+__device__ __forceinline__ void node_derivs(const ChirpParams& cp, double x, double y, double w,
+                                            const cx_t<T>* __restrict__ G, int nf1, int nf2,
+                                            double beta, double* dLdw, double* dLdx,
+                                            double* dLdy) {
     // chirp phase and (shifted, folded) grid coordinates, as the forward pass
     double sp, cph;
     sincos(reduce_phase(cp.kq * (x * x + y * y) - cp.a1 * x - cp.a2 * y + cp.a0), &sp, &cph);
@@ -103,7 +89,6 @@ k_adj_nodes(FamTable ft, const cx_t<T>* __restrict__ bt, int nf1, int nf2, doubl
         d1[a] = r1 > 0.0 ? p1[a] * beta * z1 / sqrt(r1) * (2.0 / W) : 0.0;
         d2[a] = r2 > 0.0 ? p2[a] * beta * z2 / sqrt(r2) * (2.0 / W) : 0.0;
     }
-    const cx_t<T>* G = bt + (long long)f.prob * nf1 * nf2;
     double Fr = 0, Fi = 0, G1r = 0, G1i = 0, G2r = 0, G2i = 0;
     for (int b = 0; b < W; ++b) {
         int row = s2 + b + nf2 / 2;
@@ -132,16 +117,129 @@ k_adj_nodes(FamTable ft, const cx_t<T>* __restrict__ bt, int nf1, int nf2, doubl
     // e^{i phi} F and c dF/dg with c = w e^{i phi}
     const double eFr = cph * Fr - sp * Fi, eFi = cph * Fi + sp * Fr;
     const double U1 = cp.nf1 * cp.u1, U2 = cp.nf2 * cp.u2;
-    const double dLdw = eFr;
+    *dLdw = eFr;
     // Re(i w eF dphi/dx + w e^{i phi} dF/dg1 U1)
-    const double dLdx = -w * eFi * (2.0 * cp.kq * x - cp.a1) + w * U1 * (cph * G1r - sp * G1i);
-    const double dLdy = -w * eFi * (2.0 * cp.kq * y - cp.a2) + w * U2 * (cph * G2r - sp * G2i);
+    *dLdx = -w * eFi * (2.0 * cp.kq * x - cp.a1) + w * U1 * (cph * G1r - sp * G1i);
+    *dLdy = -w * eFi * (2.0 * cp.kq * y - cp.a2) + w * U2 * (cph * G2r - sp * G2i);
+}
+
+__device__ __forceinline__ int family_of_block(const FamTable& ft) {
+    int a = 0, b = ft.nfam - 1;
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (ft.blk0[mid] <= (int)blockIdx.x) a = mid;
+        else b = mid - 1;
+    }
+    return a;
+}
+
+// Boundary parameter t_i and weight what_i of boundary node i of a Fourier
+// family: Gauss-Legendre panels (the periodic trapezoid rule, eq. ptr, for a
+// starshade's disc).
+__device__ __forceinline__ void fourier_t(const FamilyDev& f, long long i, double* t,
+                                          double* what) {
+    const int q = (int)(i / f.p), s = (int)(i - (long long)q * f.p);
+    const double hP = kTwoPi / f.n_panels;
+    *t = f.ptr ? (q + 1) * hP : (q + f.gl_p_t[s]) * hP;
+    *what = f.ptr ? hP : f.gl_p_w[s] * hP;
+}
+
+// One thread per node of the families the gradient is taken for (other
+// families' blocks exit).  mode 0: PETALS families, contribution to dL/dA_l;
+// mode 1: Fourier boundary families (not a starshade's internal disc),
+// contribution to dL/dr_i.
+template <typename T, int W>
+__global__ void __launch_bounds__(kNodeThreads)
+k_adj_nodes(FamTable ft, const cx_t<T>* __restrict__ bt, int nf1, int nf2, double beta,
+            double* __restrict__ contrib, int mode) {
+    __shared__ int s_fi;
+    if (threadIdx.x == 0) s_fi = family_of_block(ft);
+    __syncthreads();
+    const FamilyDev& f = ft.fams[s_fi];
+    if (mode == 0 && f.kind != FRESNEL_FAMILY_PETALS) return;
+    if (mode == 1 && (f.kind != FRESNEL_FAMILY_FOURIER || f.ptr)) return;
+    const ChirpParams& cp = ft.cps[f.prob];
+    const long long j = (long long)(blockIdx.x - ft.blk0[s_fi]) * blockDim.x + threadIdx.x;
+    if (j >= f.n_nodes) return;
+    const cx_t<T>* G = bt + (long long)f.prob * nf1 * nf2;
+    double dLdw, dLdx, dLdy;
+    if (mode == 1) {
+        const long long i = j / f.m;
+        const int l = (int)(j - i * f.m);
+        const double a = f.gl_m_a[l], aw = f.gl_m_aw[l];
+        const double x = f.cx + a * f.bx[i], y = f.cy + a * f.by[i], w = aw * f.bc[i];
+        node_derivs<T, W>(cp, x, y, w, G, nf1, nf2, beta, &dLdw, &dLdx, &dLdy);
+        double t, what, st, ct;
+        fourier_t(f, i, &t, &what);
+        sincos(t, &st, &ct);
+        const double r = f.bx[i] * ct + f.by[i] * st;
+        contrib[f.offset + j] = a * (ct * dLdx + st * dLdy) + 2.0 * aw * what * r * dLdw;
+        return;
+    }
+    const long long k = j / f.n_bdry, q = j - k * f.n_bdry;
+    const int i = (int)(q / f.m), l = (int)(q - (long long)i * f.m);
+    const double u = f.bx[q], v = f.by[q];
+    const double cr = f.rot[2 * k], sr = f.rot[2 * k + 1];
+    const double dx0 = u * cr - v * sr, dy0 = u * sr + v * cr;   // x - c
+    const double x = f.cx + dx0, y = f.cy + dy0, w = f.bc[q];
+    node_derivs<T, W>(cp, x, y, w, G, nf1, nf2, beta, &dLdw, &dLdx, &dLdy);
     // chain to A_l: dw/dA = r what omegahat, d(x,y)/dA = r t (-sin, cos) = t (-(y-cy), x-cx)
     const double span = f.pR - f.pa, wedge = kTwoPi / f.n_panels;
     const double r = f.pa + span * f.gl_m_a[l];
     const double dwdA = r * (span * f.gl_m_aw[l]) * (wedge * f.gl_p_w[i]);
     const double t = -0.5 * wedge + wedge * f.gl_p_t[i];
     contrib[f.offset + j] = dLdw * dwdA + t * (-dy0 * dLdx + dx0 * dLdy);
+}
+
+// Fourier families (list sf): dL/dr_i = sum over radii of the node
+// contributions, one warp per boundary node, into rbuf[bofs[f] + i].
+__global__ void k_adj_rsum(const FamilyDev* __restrict__ fams, const int* __restrict__ sf, int nsf,
+                           const long long* __restrict__ bofs, const double* __restrict__ contrib,
+                           double* __restrict__ rbuf) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    long long base = 0;
+    for (int fi = 0; fi < nsf; ++fi) {
+        const FamilyDev& f = fams[sf[fi]];
+        if (wid < base + f.n_bdry) {
+            const long long i = wid - base;
+            double s = 0.0;
+            for (int l = lane; l < f.m; l += 32) s += contrib[f.offset + i * f.m + l];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) rbuf[bofs[fi] + i] = s;
+            return;
+        }
+        base += f.n_bdry;
+    }
+}
+
+// One block per (Fourier family, coefficient): dL/dp = sum_i dL/dr_i dr_i/dp
+// with dr/dr0 = 1, dr/da_k = cos k t, dr/db_k = sin k t (fixed-order block sum).
+__global__ void k_adj_modes(const FamilyDev* __restrict__ fams, const int* __restrict__ sf,
+                            const long long* __restrict__ bofs, const long long* __restrict__ gofs,
+                            const double* __restrict__ rbuf, double* __restrict__ grad) {
+    __shared__ double s_part[32];
+    const int fi = blockIdx.y, kk = blockIdx.x;
+    const FamilyDev& f = fams[sf[fi]];
+    if (kk > 2 * f.K) return;
+    const int k = (kk + 1) / 2;
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < f.n_bdry; i += blockDim.x) {
+        double t, what;
+        fourier_t(f, i, &t, &what);
+        const double phi = kk == 0 ? 1.0 : (kk % 2 == 1 ? cos(k * t) : sin(k * t));
+        s += rbuf[bofs[fi] + i] * phi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_part[w];
+        grad[gofs[fi] + kk] = tot;
+    }
 }
 
 // One block per PETALS family (list pf): dL/dA_l = sum over petals and angles
@@ -187,11 +285,11 @@ template void launch_adj_prologue<double>(const void*, const void*, const void*,
 
 template <typename T>
 void launch_adj_nodes(const FamTable& ft, int nblocks, const void* bt, int nf1, int nf2,
-                      const KernelShape& ks, double* contrib, cudaStream_t st) {
+                      const KernelShape& ks, double* contrib, int mode, cudaStream_t st) {
 #define FRES_ADJ_CASE(WW)                                                                     \
     case WW:                                                                                  \
         k_adj_nodes<T, WW><<<nblocks, kNodeThreads, 0, st>>>(ft, (const cx_t<T>*)bt, nf1, nf2, \
-                                                            ks.beta, contrib);                \
+                                                            ks.beta, contrib, mode);          \
         break;
     switch (ks.w) {
         FRES_ADJ_CASE(2) FRES_ADJ_CASE(3) FRES_ADJ_CASE(4) FRES_ADJ_CASE(5) FRES_ADJ_CASE(6)
@@ -202,13 +300,22 @@ void launch_adj_nodes(const FamTable& ft, int nblocks, const void* bt, int nf1, 
 #undef FRES_ADJ_CASE
 }
 template void launch_adj_nodes<float>(const FamTable&, int, const void*, int, int,
-                                      const KernelShape&, double*, cudaStream_t);
+                                      const KernelShape&, double*, int, cudaStream_t);
 template void launch_adj_nodes<double>(const FamTable&, int, const void*, int, int,
-                                       const KernelShape&, double*, cudaStream_t);
+                                       const KernelShape&, double*, int, cudaStream_t);
 
 void launch_adj_reduce(const FamilyDev* fams, const int* pf, const long long* gofs, int npf,
                        const double* contrib, double* grad, cudaStream_t st) {
     if (npf > 0) k_adj_reduce<<<npf, 256, 0, st>>>(fams, pf, gofs, contrib, grad);
+}
+
+void launch_adj_shape_reduce(const FamilyDev* fams, const int* sf, int nsf, int max_params,
+                             long long n_bdry_total, const long long* bofs, const long long* gofs,
+                             const double* contrib, double* rbuf, double* grad, cudaStream_t st) {
+    if (nsf <= 0) return;
+    const long long threads = 32 * n_bdry_total;
+    k_adj_rsum<<<(int)((threads + 255) / 256), 256, 0, st>>>(fams, sf, nsf, bofs, contrib, rbuf);
+    k_adj_modes<<<dim3(max_params, nsf), 256, 0, st>>>(fams, sf, bofs, gofs, rbuf, grad);
 }
 
 }  // namespace fres

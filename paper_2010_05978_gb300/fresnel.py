@@ -70,7 +70,7 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_plan_many", "fresnel_eval",
            "fresnel_eval_many", "fresnel_eval_many_scattered", "fresnel_eval_host",
-           "fresnel_grad_profile", "fresnel_nsli",
+           "fresnel_grad_profile", "fresnel_grad_shape", "fresnel_nsli",
            "fresnel_check", "fresnel_destroy", "fresnel_last_error", "fresnel_get_info",
            "fresnel_get_nodes", "fresnel_set_timing", "fresnel_stage_times", "fresnel_spread",
            "fresnel_spread_noalloc"]
@@ -104,6 +104,8 @@ def load_library(path=LIB_PATH):
     lib.fresnel_eval_many_scattered.restype = ctypes.c_int
     lib.fresnel_grad_profile.argtypes = [vp, vp, vp]
     lib.fresnel_grad_profile.restype = ctypes.c_int
+    lib.fresnel_grad_shape.argtypes = [vp, vp, vp]
+    lib.fresnel_grad_shape.restype = ctypes.c_int
     lib.fresnel_nsli.argtypes = [vp, vp, ll, vp]
     lib.fresnel_nsli.restype = ctypes.c_int
     lib.fresnel_eval_host.argtypes = [vp, vp, ll, vp]
@@ -239,6 +241,11 @@ def _profile_sizes(families):
     return [len(family_params(f)[4]) - 5 for f in families if f["kind"] == "petals"]
 
 
+def _shape_sizes(families):
+    """Coefficient count of each FOURIER family (the shape-gradient layout)."""
+    return [len(family_params(f)[4]) for f in families if f["kind"] == "fourier"]
+
+
 class _PlanHandle:
     """Methods shared by single and batched plans."""
 
@@ -251,6 +258,16 @@ class _PlanHandle:
         out = torch.empty(max(1, sum(self.profile_sizes)), dtype=torch.float64, device="cuda")
         _check(load_library().fresnel_grad_profile(self.handle, gamma.data_ptr(), out.data_ptr()))
         return out[:sum(self.profile_sizes)]
+
+    def grad_shape(self, gamma):
+        """dL/d(boundary coefficients) of every FOURIER family (FP64 CUDA tensor,
+        each family's [r0, a1, b1, ...] concatenated in plan order) for
+        dL = Re sum conj(gamma) du, gamma shaped like the output."""
+        torch = self._torch
+        gamma = gamma.to(self.cdtype).contiguous()
+        out = torch.empty(max(1, sum(self.shape_sizes)), dtype=torch.float64, device="cuda")
+        _check(load_library().fresnel_grad_shape(self.handle, gamma.data_ptr(), out.data_ptr()))
+        return out[:sum(self.shape_sizes)]
 
     def check(self):
         _check(load_library().fresnel_check(self.handle))
@@ -309,6 +326,7 @@ class BatchPlan(_PlanHandle):
         self._torch = torch
         probs = (Problem * len(problems))()
         self.profile_sizes = [n for q in problems for n in _profile_sizes(q["families"])]
+        self.shape_sizes = [n for q in problems for n in _shape_sizes(q["families"])]
         self._keep = []
         for b, q in enumerate(problems):
             fams, keep = _family_array(q["families"])
@@ -389,6 +407,7 @@ class Plan(_PlanHandle):
         self._torch = torch
         fams, keep = _family_array(families)
         self.profile_sizes = _profile_sizes(families)
+        self.shape_sizes = _shape_sizes(families)
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
                        nsli_far, screen)
@@ -488,6 +507,36 @@ def profile_field(theta, make_plan):
             return gt.to(theta.device, theta.dtype).view_as(theta)
 
     return _ProfileField.apply(theta)
+
+
+def shape_field(theta, make_plan):
+    """The field of an aperture as a differentiable function of its Fourier
+    boundary coefficients theta = [r0, a1, b1, ...] (a float64 torch tensor).
+
+    make_plan(theta_numpy) returns a Plan or BatchPlan (grid targets) whose
+    FOURIER families all take their params from theta.  Returns the output
+    tensor; backward gives dL/dtheta through fresnel_grad_shape (summed over
+    the families sharing theta)."""
+    import torch
+
+    class _ShapeField(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            plan = make_plan(th.detach().cpu().numpy().astype(np.float64))
+            u = plan.eval()
+            ctx.plan = plan
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            plan = ctx.plan
+            g = plan.grad_shape(grad_u)
+            n = theta.numel()
+            assert all(k == n for k in plan.shape_sizes)
+            gt = g.view(len(plan.shape_sizes), n).sum(0)
+            return gt.to(theta.device, theta.dtype).view_as(theta)
+
+    return _ShapeField.apply(theta)
 
 
 # C-ABI names, for callers that want the flat interface.
