@@ -810,7 +810,7 @@ def randstar_arm(args, dev, local_rank, world, batch, steps, warmup, budget_s=10
     else:
         cfg = W.random_star()
         problems = [{"families": cfg["families"], "lam": cfg["lam"], "z": cfg["z"]}]
-        counts = [100_000_000]
+        counts = [int(getattr(args, "targets", 0) or 100_000_000)]
         h_t = _host_targets(counts, 5, [1])
         p, plan_ms = timed_plan(lambda: Plan(cfg["families"], cfg["lam"], cfg["z"], TOL,
                                              precision="fp32", box=box, recompute_nodes=True,
@@ -1117,6 +1117,9 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="star5_F100 only: time the headline workload alone (no FP64 path, "
                          "sweep or F=1000 objects in the line)")
+    ap.add_argument("--targets", type=int, default=0,
+                    help="randstar_F1000 only: scattered targets (default 1e8; fewer for small "
+                         "profiling captures)")
     ap.add_argument("--lambdas", type=int, default=64,
                     help="starshade_sweep only: wavelengths per sweep (64 is the benchmark; "
                          "fewer for small profiling captures)")

@@ -38,7 +38,7 @@ typedef enum {
     FRESNEL_ERR_ARG = -1,         /* invalid argument; nothing was launched */
     FRESNEL_ERR_CUDA = -2,        /* a CUDA runtime call failed */
     FRESNEL_ERR_OOM = -3,         /* device allocation failed or exceeded the cap */
-    FRESNEL_ERR_TIMEOUT = -4,     /* reserved: no kernel of this library waits on another */
+    FRESNEL_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up (fresnel_opts.max_spin) */
     FRESNEL_ERR_UNSUPPORTED = -5, /* valid request beyond this build's limits */
     FRESNEL_ERR_DEVICE = -6       /* a device-side check failed (e.g. target outside the plan's box) */
 } fresnel_status;
@@ -205,6 +205,15 @@ typedef struct {
     const double* screen_opd;
     int screen_n1, screen_n2;
     double screen_box[4];
+    /* Bound on the one device-side wait of the spreading stage: the chunks
+     * of a tile that holds more records than one work item takes wait, before
+     * adding into the tile, for the flag with which the tile's first chunk
+     * reports having cleared it.  Polls per wait (~256 ns apart) before the
+     * wait gives up, skips its addition and flags FRESNEL_ERR_TIMEOUT (read by
+     * fresnel_check or a synchronous evaluation): 0 = the built-in 2^22
+     * (about a second), > 0 = that many, < 0 = none at all (every such wait
+     * gives up at once; for tests of the timeout path). */
+    long long max_spin;
 } fresnel_opts;
 
 /* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,

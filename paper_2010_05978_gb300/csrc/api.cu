@@ -81,6 +81,7 @@ struct Plan {
     int n1 = 0, n2 = 0;
     int ntx = 0, nty = 0, ntiles = 0;
     int chunk_cap = 0, max_chunks = 0, max_split = 0;
+    int* ready = nullptr;         // split tiles' ready flags (zero between evaluations)
     bool col_dft = false;         // type-1 column pass as a direct DFT over the live rows
     long long n_records = 0;
     int spread_blocks = 0;
@@ -262,11 +263,12 @@ void choose_kernel(Plan* p) {
     if (p->prec == FRESNEL_FP32_FAST) fit_horner(w, beta, &p->ks.horner);
 }
 
-// Fit, for each of the w unit pieces of the kernel, a polynomial in
-// t = 2 f - 1 (f the node's fractional offset): Chebyshev interpolation at
-// deg + 1 points, converted to monomials in long double.  The degree grows
-// until the maximum error (on a fine grid) stops improving or drops below
-// 1e-9; the kernel's square-root end points set a floor near e^-beta.
+// Fit, for each of the unit pieces a < ceil(w/2) of the kernel (the others
+// are their mirror images), a polynomial in t = 2 f - 1 (f the node's
+// fractional offset): Chebyshev interpolation at deg + 1 points, converted to
+// monomials in long double and split into even and odd parts.  The degree
+// grows until the maximum error (on a fine grid) stops improving or drops
+// below 1e-9; the kernel's square-root end points set a floor near e^-beta.
 void fit_horner(int w, double beta, HornerTab* h) {
     auto psi = [&](long double z) -> long double {
         long double a = 1.0L - z * z;
@@ -280,7 +282,7 @@ void fit_horner(int w, double beta, HornerTab* h) {
         HornerTab t{};
         t.deg = d;
         double err = 0.0;
-        for (int a = 0; a < w; ++a) {
+        for (int a = 0; a < (w + 1) / 2; ++a) {
             auto g = [&](long double tt) {
                 long double f = 0.5L * (tt + 1.0L);
                 return psi(((long double)a + 1.0L - 0.5L * w - f) * 2.0L / w);
@@ -305,7 +307,10 @@ void fit_horner(int w, double beta, HornerTab* h) {
                     T1 = T2;
                 }
             }
-            for (int j = 0; j < n; ++j) t.c[a][j] = (float)mono[j];
+            for (int j = 0; j < n; ++j) {
+                if (j % 2 == 0) t.e[a][j / 2] = (float)mono[j];
+                else t.o[a][j / 2] = (float)mono[j];
+            }
             for (int i = 0; i <= 400; ++i) {
                 long double tt = -1.0L + i / 200.0L, acc = 0.0L;
                 for (int j = n - 1; j >= 0; --j) acc = acc * tt + mono[j];
@@ -536,10 +541,12 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ev_record(p, "scatter");
         p->nodes_ready = true;
     }
+    const long long spin = p->opts.max_spin == 0 ? kDefaultMaxSpin
+                                                 : std::max(0LL, p->opts.max_spin);
     launch_spread<T>((const NodeRec<T>*)p->sorted, p->chunks, p->n_meta, p->max_chunks,
-                     p->split_tiles, p->max_split, (cx_t<T>*)p->grid, p->work, p->nf1, p->nf2,
-                     p->ntx, p->ntiles, p->ks, p->spread_blocks, p->st);
-    p->launches += p->max_split > 0 ? 2 : 1;
+                     p->ready, p->max_split, spin, (cx_t<T>*)p->grid, p->work, p->status, p->nf1,
+                     p->nf2, p->ntx, p->ntiles, p->ks, p->spread_blocks, p->st);
+    p->launches += 1;
     ev_record(p, "spread");
     if (p->tkind == FRESNEL_GRID) {
         RowPassArgs ra{};
@@ -652,6 +659,11 @@ fresnel_status read_status(Plan* p) {
         if (h & kStatusNodeOutside) msg += " node support outside the type-3 grid;";
         if (h & kStatusNonFinite) msg += " non-finite coordinate;";
         if (h & kStatusOverflow) msg += " sort region overflow;";
+        if (h & kStatusTimeout) {
+            msg += " a split tile's chunk gave up waiting for the tile to be cleared"
+                   " (fresnel_opts.max_spin);";
+            return fres_fail(FRESNEL_ERR_TIMEOUT, msg);
+        }
         return fres_fail(FRESNEL_ERR_DEVICE, msg);
     }
     return FRESNEL_OK;
@@ -1309,6 +1321,8 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     FRES_TRY(dalloc(p, (void**)&p->chunks, sizeof(Chunk) * p->max_chunks));
     FRES_TRY(dalloc(p, (void**)&p->n_meta, 2 * sizeof(int)));
     FRES_TRY(dalloc(p, (void**)&p->split_tiles, sizeof(int) * std::max(1, p->max_split)));
+    FRES_TRY(dalloc(p, (void**)&p->ready, sizeof(int) * std::max(1, p->max_split)));
+    FRES_CK(cudaMemsetAsync(p->ready, 0, sizeof(int) * std::max(1, p->max_split), p->st));
     {
         int* d_sc = nullptr;
         int* d_pl = nullptr;
@@ -1867,7 +1881,6 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
     info->device_bytes = p->bytes;
     int nl = 4;   // spread, two FFT passes, (type 3) interpolation
     if (p->tkind == FRESNEL_GRID) nl = 3;
-    if (p->max_split > 0) nl += 1;   // clearing of split tiles before the spread
     if (p->opts.recompute_nodes) nl += 3;   // nodes, scan, scatter
     info->launches_per_eval = p->last_launches > 0 ? p->last_launches : nl;
     return FRESNEL_OK;

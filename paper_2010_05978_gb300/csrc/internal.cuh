@@ -35,7 +35,11 @@ enum : unsigned {
     kStatusNodeOutside = 2u,       // a node's support left the type-3 spreading grid
     kStatusNonFinite = 4u,         // a non-finite coordinate was met
     kStatusOverflow = 8u,          // a sort region was smaller than its records (batched plans)
+    kStatusTimeout = 16u,          // a bounded device-side wait gave up (its work was skipped)
 };
+
+// Polls of a device-side wait before it gives up when fresnel_opts.max_spin = 0.
+constexpr long long kDefaultMaxSpin = 1LL << 22;
 
 template <typename T> struct Cx;
 template <> struct Cx<float> { using type = float2; };
@@ -54,15 +58,22 @@ struct __align__(2 * sizeof(T) > 8 ? 16 : 8) NodeRec {
 
 // A spreading work item: nodes [begin, end) of the sorted record list that
 // touch tile `tile`.  Tiles with more than the chunk cap of records are split
-// into several chunks; their grid tile is cleared first and every chunk adds
-// its nonzero cells with global atomic adds.  Unsplit tiles (including empty
-// ones) are written with plain stores.  Chunks of split tiles come first in
-// the list so the heaviest work starts first.
+// into several consecutive chunks: the first clears the grid tile and raises
+// the tile's ready flag, and every chunk adds its nonzero cells with global
+// atomic adds (the others after waiting for the flag).  Unsplit tiles
+// (including empty ones) are written with plain stores.  Chunks of split
+// tiles come first in the list so the heaviest work starts first.
+// split: 0 plain chunk; 1 padding (no records, does nothing); >= 2 a chunk
+// of split tile number (split >> 1) - 1 (its ready flag), the tile's first
+// chunk when split is odd.
 struct Chunk {
     int tile;
     int begin, end;
-    int split;       // 1: tile shared by several chunks
+    int split;
 };
+__host__ __device__ __forceinline__ int split_code(int split_index, bool first) {
+    return ((split_index + 1) << 1) | (first ? 1 : 0);
+}
 
 // Radix plan of one FFT length.
 struct FftPlan {
@@ -153,16 +164,23 @@ struct ChirpParams {
 };
 
 // Piecewise-polynomial form of the spreading kernel for FP32: the value at
-// cell a of a node with fractional offset f is c[a][0] + c[a][1] t + ... with
+// cell a of a node with fractional offset f is a polynomial p_a(t) in
 // t = 2 f - 1 (fitted once per plan on the Chebyshev points of each unit
-// piece).  Every piece is evaluated to the fixed degree kHornerDeg (the fit's
-// own degree, at most kHornerDeg, zero-padded), so the fully unrolled Horner
-// chain takes its coefficients as constant operands.  deg < 0 means
-// "evaluate exp/sqrt directly".  Passed by value, so it lives in the
-// kernel-parameter constant bank (uniform access).
+// piece).  The kernel is even, so piece w - 1 - a is piece a mirrored:
+// p_{w-1-a}(t) = p_a(-t).  Only the pieces a < ceil(w/2) are stored, split
+// into even and odd parts in u = t^2: p_a(t) = E_a(u) + t O_a(u), giving the
+// pair p_a, p_{w-1-a} = E_a -/+ ... from one evaluation of E_a and O_a.  Every
+// piece is evaluated to the fixed degree kHornerDeg (the fit's own degree, at
+// most kHornerDeg, zero-padded), so the fully unrolled Horner chains take
+// their coefficients as constant operands.  deg < 0 means "evaluate exp/sqrt
+// directly".  Passed by value, so it lives in the kernel-parameter constant
+// bank (uniform access).
 constexpr int kHornerDeg = 10;
+constexpr int kHornerEven = kHornerDeg / 2 + 1;        // t^0, t^2, ..., t^10
+constexpr int kHornerOdd = (kHornerDeg + 1) / 2;       // t^1, t^3, ..., t^9
 struct HornerTab {
-    float c[kMaxW][kHornerDeg + 1];
+    float e[(kMaxW + 1) / 2][kHornerEven];
+    float o[(kMaxW + 1) / 2][kHornerOdd];
     int deg;
 };
 
@@ -175,13 +193,17 @@ struct KernelShape {
 
 template <int W>
 __device__ __forceinline__ void horner_eval(const HornerTab& h, float f, float* out) {
-    const float t = 2.0f * f - 1.0f;
+    const float t = 2.0f * f - 1.0f, u = t * t;
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-        float acc = h.c[a][kHornerDeg];
+    for (int a = 0; a < (W + 1) / 2; ++a) {
+        float E = h.e[a][kHornerEven - 1];
 #pragma unroll
-        for (int k = kHornerDeg - 1; k >= 0; --k) acc = fmaf(acc, t, h.c[a][k]);
-        out[a] = acc;
+        for (int k = kHornerEven - 2; k >= 0; --k) E = fmaf(E, u, h.e[a][k]);
+        float O = h.o[a][kHornerOdd - 1];
+#pragma unroll
+        for (int k = kHornerOdd - 2; k >= 0; --k) O = fmaf(O, u, h.o[a][k]);
+        out[a] = fmaf(t, O, E);
+        if (W - 1 - a != a) out[W - 1 - a] = fmaf(-t, O, E);
     }
 }
 
@@ -278,15 +300,16 @@ void launch_t3_deconv(int ng, int nfft, int w, double beta, void* table, int is_
                       const double* gq_t, const double* gq_w, int q, cudaStream_t st);
 
 // k_spread.cu
-// work[0]: next chunk, work[1]: finished blocks (both return to 0 at exit)
-// Chunk tiles are global tile ids: problem = tile / ntiles (its grid is
-// nf1 * nf2 cells after the previous problem's); split_tiles entries < 0 are
-// padding.
+// work[0]: next chunk, work[1]: finished blocks (both return to 0 at exit);
+// ready[0 .. max_split): the split tiles' ready flags (zero on entry, left
+// zero); max_spin: polls of the ready wait (< 0: none).  Chunk tiles are
+// global tile ids: problem = tile / ntiles (its grid is nf1 * nf2 cells
+// after the previous problem's).
 template <typename T>
 void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
-                   int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
-                   int* work, int nf1, int nf2, int ntx, int ntiles, const KernelShape& ks,
-                   int nblocks, cudaStream_t st);
+                   int max_chunks, int* ready, int max_split, long long max_spin,
+                   cx_t<T>* grid, int* work, unsigned* status, int nf1, int nf2, int ntx,
+                   int ntiles, const KernelShape& ks, int nblocks, cudaStream_t st);
 
 // k_nsli.cu: non-singular line integral (Appendix, eq. nsli) over the
 // boundary rules of the given families, FP64, one thread per target

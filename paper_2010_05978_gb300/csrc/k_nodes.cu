@@ -742,7 +742,7 @@ __global__ void k_scan_chunks(int ntiles, int* __restrict__ counts, int* __restr
                         ch.tile = i;
                         ch.begin = (int)(roff + (long long)k * chunk_cap);
                         ch.end = (int)min(roff + (long long)(k + 1) * chunk_cap, roff + c);
-                        ch.split = 1;
+                        ch.split = stoff < max_split ? split_code((int)stoff, k == 0) : 1;
                         chunks[ci] = ch;
                     }
                 }
@@ -783,7 +783,7 @@ __global__ void k_scan_chunks(int ntiles, int* __restrict__ counts, int* __restr
             ch.tile = split_tiles[a];
             ch.begin = (int)(r0 + (long long)k * chunk_cap);
             ch.end = (int)min(r0 + (long long)(k + 1) * chunk_cap, r0 + c);
-            ch.split = 1;
+            ch.split = a < max_split ? split_code(a, k == 0) : 1;
             chunks[ci] = ch;
         }
     }
@@ -898,7 +898,7 @@ k_scan_problems(int ntiles, int* __restrict__ counts, int* __restrict__ cursor,
                         ch.tile = base + i;
                         ch.begin = (int)(r0 + roff + (long long)k * chunk_cap);
                         ch.end = (int)(r0 + min(roff + (long long)(k + 1) * chunk_cap, roff + c));
-                        ch.split = 1;
+                        ch.split = st0 + stoff < st1 ? split_code((int)(st0 + stoff), k == 0) : 1;
                         chunks[ci] = ch;
                     }
                 }
@@ -939,7 +939,7 @@ k_scan_problems(int ntiles, int* __restrict__ counts, int* __restrict__ cursor,
             ch.tile = split_tiles[st0 + a];
             ch.begin = (int)(r0 + ro + (long long)k * chunk_cap);
             ch.end = (int)(r0 + min(ro + (long long)(k + 1) * chunk_cap, ro + c));
-            ch.split = 1;
+            ch.split = split_code(st0 + a, k == 0);
             chunks[sc0 + ci] = ch;
         }
     }

@@ -12,7 +12,12 @@
 // dilation rule's spokes all meet at the centre, so a few tiles can hold
 // tens of thousands) are split into chunks that run in parallel; such a tile
 // is cleared first and its chunks add their nonzero cells with global atomic
-// adds.  Work items are handed out dynamically, split chunks first.
+// adds.  Work items are handed out dynamically, split chunks first.  A split
+// tile's first chunk clears the tile and then raises its ready flag; the
+// tile's other chunks build their private sums first and wait for the flag
+// (a bounded wait: on giving up they skip their addition and flag
+// kStatusTimeout) only before adding.  The first chunk is claimed before the
+// others, so its block is running and the wait ends.
 //
 // Inside a chunk there are no atomics either: each warp owns a private copy
 // of the tile in shared memory.  A warp stages 32 records at a time (one per
@@ -80,9 +85,9 @@ struct SpreadSmem {
     T kx[kSpreadWarps][32][W + 1];
     int dxy[kSpreadWarps][32][2];
     int s_ci;
+    int s_ok;
 };
 
-// Clears the grid tiles that several chunks will add into.
 // Tile ids are global over the problems of a batched plan: problem
 // tile / ntiles, whose grid starts nf1 * nf2 cells after the previous one's.
 template <typename T>
@@ -93,22 +98,19 @@ __device__ __forceinline__ cx_t<T>* tile_origin(cx_t<T>* grid, int tile, int nf1
            (lt % ntx) * kTile;
 }
 
-template <typename T>
-__global__ void k_zero_split_tiles(const int* __restrict__ split_tiles,
-                                   const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid,
-                                   int nf1, int nf2, int ntx, int ntiles) {
-    const int ns = n_meta[1];
-    for (int i = blockIdx.x; i < ns; i += gridDim.x) {
-        const int tile = split_tiles[i];
-        if (tile < 0) continue;
-        cx_t<T>* dst = tile_origin<T>(grid, tile, nf1, nf2, ntx, ntiles);
-        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-            cx_t<T> z;
-            z.x = (T)0;
-            z.y = (T)0;
-            dst[(long long)(e / kTile) * nf1 + e % kTile] = z;
-        }
+// Thread 0 waits for a split tile's ready flag: at most max_spin polls
+// (< 0: none), 256 ns apart.  Returns true once the flag is up; on giving up
+// flags kStatusTimeout and returns false.
+__device__ __forceinline__ bool wait_ready(const int* ready, long long max_spin,
+                                           unsigned* status) {
+    for (long long it = 0; it < max_spin; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ready) : "memory");
+        if (v) return true;
+        __nanosleep(256);
     }
+    if (status) atomicOr(status, kStatusTimeout);
+    return false;
 }
 
 // A lane's NPASS staged values (adjacent slots): 16-byte loads where the
@@ -134,6 +136,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks,
          const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid, int* __restrict__ work,
+         int* __restrict__ ready, int max_split, long long max_spin, unsigned* __restrict__ status,
          int nf1, int nf2, int ntx, int ntiles, T beta, const HornerTab hz) {
     constexpr int TT = kTile * kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -148,6 +151,23 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
         const int ci = sm.s_ci;
         if (ci >= n_chunks) break;
         const Chunk ch = chunks[ci];
+        // padding chunks (split 1) hold no records and add nothing
+        const int sidx = ch.split >= 2 ? (ch.split >> 1) - 1 : -1;
+        cx_t<T>* dst = tile_origin<T>(grid, ch.tile, nf1, nf2, ntx, ntiles);
+        if (sidx >= 0 && (ch.split & 1)) {   // a split tile's first chunk: clear it, raise the flag
+            for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+                cx_t<T> z;
+                z.x = (T)0;
+                z.y = (T)0;
+                dst[(long long)(e / kTile) * nf1 + e % kTile] = z;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && sidx < max_split) {
+                __threadfence();
+                asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(ready + sidx), "r"(1)
+                             : "memory");
+            }
+        }
         const int lt = ch.tile % ntiles;
         const int tx0 = (lt % ntx) * kTile;
         const int ty0 = (lt / ntx) * kTile;
@@ -209,9 +229,16 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
                 __syncwarp();
             }
         }
+        // a split tile's later chunks add only once its first chunk cleared it
+        if (threadIdx.x == 0) {
+            sm.s_ok = 1;
+            if (sidx >= 0 && !(ch.split & 1))
+                sm.s_ok = sidx < max_split ? (wait_ready(ready + sidx, max_spin, status) ? 1 : 0)
+                                           : 0;
+        }
         __syncthreads();
+        if (!sm.s_ok) continue;   // gave up (flagged): the tile misses this chunk
         // sum the warps' tiles (fixed order); store, or add into a shared tile
-        cx_t<T>* dst = tile_origin<T>(grid, ch.tile, nf1, nf2, ntx, ntiles);
         for (int e = threadIdx.x; e < TT; e += blockDim.x) {
             const int rr = e / kTile, cc = e % kTile;
             cx_t<T> s = sm.tile[0][rr * kTileStride + cc];
@@ -231,9 +258,15 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
         }
         __syncthreads();
     }
+    // the last block to finish puts the counters and the ready flags back to zero
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&work[1], 1) == (int)gridDim.x - 1) {
+        sm.s_ok = atomicAdd(&work[1], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (sm.s_ok) {
+        for (int i = threadIdx.x; i < max_split; i += blockDim.x) ready[i] = 0;
+        if (threadIdx.x == 0) {
             work[0] = 0;
             work[1] = 0;
         }
@@ -242,12 +275,9 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
 
 template <typename T, int W>
 void launch_spread_w(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
-                     int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
-                     int* work, int nf1, int nf2, int ntx, int ntiles, T beta,
-                     const HornerTab& hz, int nblocks, cudaStream_t st) {
-    if (max_split > 0)
-        k_zero_split_tiles<T><<<max_split, 256, 0, st>>>(split_tiles, n_meta, grid, nf1, nf2,
-                                                         ntx, ntiles);
+                     int max_chunks, int* ready, int max_split, long long max_spin,
+                     cx_t<T>* grid, int* work, unsigned* status, int nf1, int nf2, int ntx,
+                     int ntiles, T beta, const HornerTab& hz, int nblocks, cudaStream_t st) {
     const size_t smem = sizeof(SpreadSmem<T, W>);
     cudaFuncSetAttribute(k_spread<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -257,21 +287,22 @@ void launch_spread_w(const NodeRec<T>* sorted, const Chunk* chunks, const int* n
     if (nblocks > 0 && nblocks < g) g = nblocks;
     if (g > max_chunks) g = max_chunks;
     if (g < 1) g = 1;
-    k_spread<T, W><<<g, kSpreadWarps * 32, smem, st>>>(sorted, chunks, n_meta, grid, work, nf1,
+    k_spread<T, W><<<g, kSpreadWarps * 32, smem, st>>>(sorted, chunks, n_meta, grid, work,
+                                                       ready, max_split, max_spin, status, nf1,
                                                        nf2, ntx, ntiles, beta, hz);
 }
 
 template <typename T>
 void launch_spread_impl(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
-                        int max_chunks, const int* split_tiles, int max_split, cx_t<T>* grid,
-                        int* work, int nf1, int nf2, int ntx, int ntiles, const KernelShape& ks,
-                        int nblocks, cudaStream_t st) {
+                        int max_chunks, int* ready, int max_split, long long max_spin,
+                        cx_t<T>* grid, int* work, unsigned* status, int nf1, int nf2, int ntx,
+                        int ntiles, const KernelShape& ks, int nblocks, cudaStream_t st) {
     T beta = (T)ks.beta;
 #define FRES_SPREAD_CASE(WW)                                                                  \
     case WW:                                                                                  \
-        launch_spread_w<T, WW>(sorted, chunks, n_meta, max_chunks, split_tiles, max_split,   \
-                               grid, work, nf1, nf2, ntx, ntiles, beta, ks.horner, nblocks,  \
-                               st);                                                          \
+        launch_spread_w<T, WW>(sorted, chunks, n_meta, max_chunks, ready, max_split,         \
+                               max_spin, grid, work, status, nf1, nf2, ntx, ntiles, beta,    \
+                               ks.horner, nblocks, st);                                      \
         break;
     switch (ks.w) {
         FRES_SPREAD_CASE(2) FRES_SPREAD_CASE(3) FRES_SPREAD_CASE(4) FRES_SPREAD_CASE(5)

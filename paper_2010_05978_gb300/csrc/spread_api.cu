@@ -23,6 +23,7 @@ struct SpreadScratch {
     int* n_meta;
     int* work;
     unsigned* status;
+    int* ready;
 };
 
 // Upper bounds that hold for any input: every point touches at most four
@@ -37,7 +38,7 @@ long long max_chunks(long long n, int ntiles) {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Byte offsets of the scratch pieces inside one block of memory.
-size_t scratch_layout(long long n, int ntiles, size_t off[9]) {
+size_t scratch_layout(long long n, int ntiles, size_t off[10]) {
     size_t o = 0;
     off[0] = o; o = align256(o + sizeof(NodeRec<float>) * (size_t)std::max(1LL, n));
     off[1] = o; o = align256(o + sizeof(NodeRec<float>) * (size_t)std::max(1LL, max_records(n)));
@@ -48,10 +49,11 @@ size_t scratch_layout(long long n, int ntiles, size_t off[9]) {
     off[6] = o; o = align256(o + 2 * sizeof(int));
     off[7] = o; o = align256(o + 2 * sizeof(int));
     off[8] = o; o = align256(o + sizeof(unsigned));
+    off[9] = o; o = align256(o + sizeof(int) * (size_t)ntiles);
     return o;
 }
 
-SpreadScratch carve(unsigned char* base, const size_t off[9]) {
+SpreadScratch carve(unsigned char* base, const size_t off[10]) {
     SpreadScratch s;
     s.rec = (NodeRec<float>*)(base + off[0]);
     s.sorted = (NodeRec<float>*)(base + off[1]);
@@ -62,6 +64,7 @@ SpreadScratch carve(unsigned char* base, const size_t off[9]) {
     s.n_meta = (int*)(base + off[6]);
     s.work = (int*)(base + off[7]);
     s.status = (unsigned*)(base + off[8]);
+    s.ready = (int*)(base + off[9]);
     return s;
 }
 
@@ -81,13 +84,13 @@ fresnel_status fres_spread_check(const double* g1, const double* g2, const void*
     return FRESNEL_OK;
 }
 
-// Runs the spreading pipeline with scratch already in place.  counts and
-// work must be zero on entry (both are left zero).
+// Runs the spreading pipeline with scratch already in place.  counts, work
+// and the split tiles' ready flags must be zero on entry (all are left zero).
 fresnel_status fres_spread_run(const double* g1, const double* g2, const void* c, long long n,
                                int nf1, int nf2, int w, double beta, void* grid,
                                unsigned char* scratch, cudaStream_t st) {
     const int ntx = nf1 / kTile, nty = nf2 / kTile, ntiles = ntx * nty;
-    size_t off[9];
+    size_t off[10];
     scratch_layout(n, ntiles, off);
     SpreadScratch s = carve(scratch, off);
     ChirpParams cp{};
@@ -106,8 +109,8 @@ fresnel_status fres_spread_run(const double* g1, const double* g2, const void* c
     launch_scan_chunks(ntiles, s.counts, s.cursor, s.chunks, s.n_meta, s.split_tiles,
                        kStandaloneChunkCap, mch, ntiles, st);
     launch_scatter<float>(n, cp, s.rec, s.cursor, s.sorted, max_records(n), s.status, st);
-    launch_spread<float>(s.sorted, s.chunks, s.n_meta, mch, s.split_tiles, ntiles, (float2*)grid,
-                         s.work, nf1, nf2, ntx, ntiles, ks, 0, st);
+    launch_spread<float>(s.sorted, s.chunks, s.n_meta, mch, s.ready, ntiles, kDefaultMaxSpin,
+                         (float2*)grid, s.work, s.status, nf1, nf2, ntx, ntiles, ks, 0, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fres_fail(FRESNEL_ERR_CUDA, std::string("spread launch: ") + cudaGetErrorString(e));
@@ -115,17 +118,18 @@ fresnel_status fres_spread_run(const double* g1, const double* g2, const void* c
 }
 
 size_t fres_spread_scratch_bytes(long long n, int nf1, int nf2) {
-    size_t off[9];
+    size_t off[10];
     return scratch_layout(n, (nf1 / kTile) * (nf2 / kTile), off);
 }
 
 size_t fres_spread_zero_offsets(long long n, int nf1, int nf2, size_t* counts_off,
-                                size_t* work_off, size_t* status_off) {
-    size_t off[9];
+                                size_t* work_off, size_t* status_off, size_t* ready_off) {
+    size_t off[10];
     size_t total = scratch_layout(n, (nf1 / kTile) * (nf2 / kTile), off);
     *counts_off = off[2];
     *work_off = off[7];
     *status_off = off[8];
+    *ready_off = off[9];
     return total;
 }
 
@@ -135,8 +139,9 @@ extern "C" fresnel_status fresnel_spread(const double* d_g1, const double* d_g2,
     fresnel_status s = fres_spread_check(d_g1, d_g2, d_c, N, nf1, nf2, w, beta, d_grid);
     if (s != FRESNEL_OK) return s;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    size_t counts_off, work_off, status_off;
-    const size_t bytes = fres_spread_zero_offsets(N, nf1, nf2, &counts_off, &work_off, &status_off);
+    size_t counts_off, work_off, status_off, ready_off;
+    const size_t bytes = fres_spread_zero_offsets(N, nf1, nf2, &counts_off, &work_off, &status_off,
+                                                  &ready_off);
     const int ntiles = (nf1 / kTile) * (nf2 / kTile);
     unsigned char* scratch = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&scratch, bytes, st);
@@ -147,6 +152,7 @@ extern "C" fresnel_status fresnel_spread(const double* d_g1, const double* d_g2,
     e = cudaMemsetAsync(scratch + counts_off, 0, sizeof(int) * ntiles, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + work_off, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + status_off, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + ready_off, 0, sizeof(int) * ntiles, st);
     if (e != cudaSuccess) {
         cudaFreeAsync(scratch, st);
         cudaStreamSynchronize(st);
@@ -161,6 +167,8 @@ extern "C" fresnel_status fresnel_spread(const double* d_g1, const double* d_g2,
     if (s != FRESNEL_OK) return s;
     if (e != cudaSuccess)
         return fres_fail(FRESNEL_ERR_CUDA, std::string("fresnel_spread: ") + cudaGetErrorString(e));
+    if (h & kStatusTimeout)
+        return fres_fail(FRESNEL_ERR_TIMEOUT, "fresnel_spread: a split tile's chunk gave up waiting");
     if (h) return fres_fail(FRESNEL_ERR_DEVICE, "fresnel_spread: non-finite coordinate");
     return FRESNEL_OK;
 }

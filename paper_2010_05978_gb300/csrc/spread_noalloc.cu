@@ -27,7 +27,7 @@ fresnel_status fres_spread_run(const double* g1, const double* g2, const void* c
                                int nf1, int nf2, int w, double beta, void* grid,
                                unsigned char* scratch, cudaStream_t st);
 size_t fres_spread_zero_offsets(long long n, int nf1, int nf2, size_t* counts_off,
-                                size_t* work_off, size_t* status_off);
+                                size_t* work_off, size_t* status_off, size_t* ready_off);
 
 static fresnel_status scratch_address(unsigned char** out) {
     int dev = 0;
@@ -62,8 +62,9 @@ extern "C" fresnel_status fresnel_spread_noalloc(const double* d_g1, const doubl
         return fres_fail(FRESNEL_ERR_UNSUPPORTED,
                          "fresnel_spread_noalloc: nf1 * nf2 exceeds FRESNEL_SPREAD_NOALLOC_MAX_GRID (" +
                              std::to_string(FRESNEL_SPREAD_NOALLOC_MAX_GRID) + ")");
-    size_t counts_off, work_off, status_off;
-    const size_t bytes = fres_spread_zero_offsets(N, nf1, nf2, &counts_off, &work_off, &status_off);
+    size_t counts_off, work_off, status_off, ready_off;
+    const size_t bytes = fres_spread_zero_offsets(N, nf1, nf2, &counts_off, &work_off, &status_off,
+                                                  &ready_off);
     if (bytes > (size_t)FRESNEL_SPREAD_NOALLOC_SCRATCH_BYTES)
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "fresnel_spread_noalloc: scratch too small");
     unsigned char* scratch = nullptr;
@@ -75,6 +76,7 @@ extern "C" fresnel_status fresnel_spread_noalloc(const double* d_g1, const doubl
     cudaError_t e = cudaMemsetAsync(scratch + counts_off, 0, sizeof(int) * ntiles, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + work_off, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + status_off, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + ready_off, 0, sizeof(int) * ntiles, st);
     if (e != cudaSuccess)
         return fres_fail(FRESNEL_ERR_CUDA, std::string("fresnel_spread_noalloc: clearing the "
                                                        "scratch: ") + cudaGetErrorString(e));
@@ -87,6 +89,8 @@ extern "C" fresnel_status fresnel_spread_noalloc(const double* d_g1, const doubl
     if (e != cudaSuccess)
         return fres_fail(FRESNEL_ERR_CUDA, std::string("fresnel_spread_noalloc: ") +
                                                cudaGetErrorString(e));
+    if (h & fres::kStatusTimeout)
+        return fres_fail(FRESNEL_ERR_TIMEOUT, "fresnel_spread_noalloc: a split tile's chunk gave up waiting");
     if (h) return fres_fail(FRESNEL_ERR_DEVICE, "fresnel_spread_noalloc: non-finite coordinate");
     return FRESNEL_OK;
 }

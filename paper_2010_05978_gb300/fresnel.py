@@ -57,7 +57,7 @@ class Opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("nsli_far", ctypes.c_double),
                 ("screen_amp", ctypes.c_void_p), ("screen_opd", ctypes.c_void_p),
                 ("screen_n1", ctypes.c_int), ("screen_n2", ctypes.c_int),
-                ("screen_box", ctypes.c_double * 4)]
+                ("screen_box", ctypes.c_double * 4), ("max_spin", ctypes.c_longlong)]
 
 
 class Info(ctypes.Structure):
@@ -194,7 +194,7 @@ def _family_array(families):
 
 def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes, sync_status,
                max_device_bytes, t3_binning, fft_split_above=0, autotune=False, nsli_far=0.0,
-               screen=None):
+               screen=None, max_spin=0):
     o = Opts()
     lib.fresnel_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -217,6 +217,7 @@ def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nod
     o.fft_split_above = int(fft_split_above)
     o.autotune = int(bool(autotune))
     o.nsli_far = float(nsli_far)
+    o.max_spin = int(max_spin)
     o._keep = []
     if screen is not None:
         # dict(amp=, opd=, box=(x0, x1, y0, y1)): 2D arrays (n2 rows of n1)
@@ -320,7 +321,7 @@ class BatchPlan(_PlanHandle):
     def __init__(self, problems, tol, precision="fp32", output="aperture", grid=None, box=None,
                  sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None, nsli_far=0.0, screen=None):
+                 stream=None, nsli_far=0.0, screen=None, max_spin=0):
         import torch
         lib = load_library()
         self._torch = torch
@@ -334,7 +335,7 @@ class BatchPlan(_PlanHandle):
             probs[b] = Problem(fams, len(q["families"]), float(q["lam"]), float(q["z"]))
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
-                       nsli_far, screen)
+                       nsli_far, screen, max_spin)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -395,13 +396,15 @@ class Plan(_PlanHandle):
     nsli_far is the distance beyond which nsli() uses the shadow fix (eq. li
     with the rounded winding number); screen=dict(amp=, opd=, box=(x0, x1,
     y0, y1)) multiplies each node's weight by A e^{2 pi i OPD / lam} from
-    sampled amplitude and optical path difference (n2 rows of n1 samples).
+    sampled amplitude and optical path difference (n2 rows of n1 samples);
+    max_spin bounds the spreading stage's one device-side wait (polls before
+    FRESNEL_ERR_TIMEOUT; 0 the built-in ~1 s, < 0 none: tests of that path).
     """
 
     def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
                  box=None, sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None, nsli_far=0.0, screen=None):
+                 stream=None, nsli_far=0.0, screen=None, max_spin=0):
         import torch
         lib = load_library()
         self._torch = torch
@@ -410,7 +413,7 @@ class Plan(_PlanHandle):
         self.shape_sizes = _shape_sizes(families)
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
-                       nsli_far, screen)
+                       nsli_far, screen, max_spin)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
