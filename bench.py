@@ -320,8 +320,11 @@ def stage_pass(plans, step, stream, steps, flush=None):
 
 def timed_plan(make):
     """A plan built by make() and its wall time with the device synchronised
-    on both sides (quadrature tables, sizes, allocations, autotuning)."""
+    on both sides (quadrature tables, sizes, allocations, autotuning).  The
+    plan is built twice and the second build timed: the first in a process
+    also pays the one-time loading of the library's kernels."""
     import torch
+    make().close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p = make()

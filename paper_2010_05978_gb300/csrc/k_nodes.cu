@@ -96,37 +96,60 @@ __device__ __forceinline__ void node_tiles(int s1, int s2, const ChirpParams& cp
 }
 
 // ------------------------------------------------------------------ Gauss-Legendre
-// Roots of P_n by Newton's method on the three-term recurrence; the weights
-// 2 / ((1 - x^2) P_n'(x)^2); both mapped from (-1, 1) to (0, 1), ascending.
+// Roots of P_n by Newton's method on the three-term recurrence
+// (j + 1) P_{j+1} = (2j + 1) x P_j - j P_{j-1}, from Tricomi's asymptotic
+// estimate of each root; the weights 2 / ((1 - x^2) P_n'(x)^2); both mapped
+// from (-1, 1) to (0, 1), ascending.  The roots are symmetric (x_{n-1-i} =
+// -x_i): thread i < ceil(n/2) finds root i and writes both.  The recurrence
+// divides by j + 1 through a per-block table of reciprocals (FP64 division is
+// many times the cost of a multiply).
+template <bool kTable>
+__device__ __forceinline__ void legendre_pn(int n, double x, const double* inv, double* pn,
+                                            double* pn1) {
+    double p0 = 1.0, p1 = x;
+    for (int j = 1; j < n; ++j) {
+        const double q = (2.0 * j + 1.0) * x * p1 - j * p0;
+        const double p2 = kTable ? q * inv[j + 1] : q / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    *pn = p1;
+    *pn1 = p0;
+}
+
+// kTable: the reciprocals 1/j (j <= n) in dynamic shared memory (n small
+// enough); otherwise the recurrence divides.
+template <bool kTable>
 __global__ void k_gauss_legendre(int n, double* t01, double* w01) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x = cos(kPi * (i + 0.75) / (n + 0.5));
-    double dp = 1.0;
+    extern __shared__ double s_inv[];   // s_inv[j] = 1 / j, j = 1 .. n
+    if (kTable) {
+        for (int j = threadIdx.x; j <= n; j += blockDim.x) s_inv[j] = j > 0 ? 1.0 / j : 0.0;
+        __syncthreads();
+    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int half = (n + 1) / 2;
+    if (i >= half) return;
+    const double nn = (double)n;
+    double x = (1.0 - (nn - 1.0) / (8.0 * nn * nn * nn)) * cos(kPi * (i + 0.75) / (nn + 0.5));
+    if (2 * i + 1 == n) x = 0.0;   // odd n: the middle root
+    double pn, pn1;
     int converged = 0;
     for (int it = 0; it < 100 && converged < 2; ++it) {
-        double p0 = 1.0, p1 = x;
-        for (int j = 1; j < n; ++j) {
-            double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = n * (x * p1 - p0) / (x * x - 1.0);
-        double dx = p1 / dp;
+        legendre_pn<kTable>(n, x, s_inv, &pn, &pn1);
+        const double dp = nn * (x * pn - pn1) / (x * x - 1.0);
+        const double dx = pn / dp;
         x -= dx;
         if (fabs(dx) < 1e-15) ++converged;
     }
-    {
-        double p0 = 1.0, p1 = x;
-        for (int j = 1; j < n; ++j) {
-            double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = n * (x * p1 - p0) / (x * x - 1.0);
-    }
+    legendre_pn<kTable>(n, x, s_inv, &pn, &pn1);
+    const double dp = nn * (x * pn - pn1) / (x * x - 1.0);
+    const double w = 1.0 / ((1.0 - x * x) * dp * dp);
     t01[i] = 0.5 * (1.0 - x);
-    w01[i] = 1.0 / ((1.0 - x * x) * dp * dp);
+    w01[i] = w;
+    if (n - 1 - i != i) {
+        t01[n - 1 - i] = 0.5 * (1.0 + x);
+        w01[n - 1 - i] = w;
+    }
 }
 
 // ------------------------------------------------------------------ boundary line rules
@@ -1007,7 +1030,13 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
 void launch_gauss_legendre(int n, double* t01, double* w01, cudaStream_t st) {
-    k_gauss_legendre<<<nblk(n, 128), 128, 0, st>>>(n, t01, w01);
+    const size_t dyn = sizeof(double) * ((size_t)n + 1);
+    const int blocks = nblk((n + 1) / 2, 64);
+    if (dyn <= 48 * 1024) {
+        k_gauss_legendre<true><<<blocks, 64, dyn, st>>>(n, t01, w01);
+    } else {
+        k_gauss_legendre<false><<<blocks, 64, 0, st>>>(n, t01, w01);
+    }
 }
 
 void launch_boundary(const FamilyDev& f, const ChirpParams& cp, cudaStream_t st) {
