@@ -224,11 +224,43 @@ KERNEL_SOURCES = {
     "nodes": ["k_nodes.cu", "dfloat.cuh", "internal.cuh"],
 }
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from one
-# ncu capture of the named workload) with the sha256 prefix of the kernel's
-# sources at the time of the capture.  A kernel whose sources changed since
-# reports traffic null.
-DRAM_TRAFFIC = {}
+# Per launch, from one ncu capture of the named workload (sections
+# SpeedOfLight, MemoryWorkloadAnalysis, ComputeWorkloadAnalysis, Occupancy,
+# LaunchStats, SchedulerStats, WarpStateStats, InstructionStats): DRAM bytes
+# read + written (dram__bytes.sum.per_second x gpu__time_duration.sum), and the
+# SM-side utilisations (issue slots busy, LSU pipe, L1/TEX throughput, each a
+# fraction of its own peak), with the sha256 prefix of the kernel's sources
+# at the time of the capture.  A kernel whose sources changed since reports
+# traffic null.
+_CAP_STAR = "ncu capture of this workload (second warm-up step, every kernel)"
+_CAP_SWEEP = "ncu capture of this workload (second warm-up step)"
+_CAP_R1000 = "ncu capture of this workload at 3e7 targets (the spread does not depend on them)"
+_SHA_SPREAD, _SHA_FFT, _SHA_INTERP = "a65c6f64dd874152", "78a9e035d10ff9c2", "67ccf77c976268a1"
+
+
+def _cap(nbytes, issue, lsu, l1, sha, note):
+    return {"bytes": nbytes, "sm_side": {"issue_slots_busy": issue, "lsu_pipe": lsu,
+                                         "l1tex_throughput": l1},
+            "sources_sha": sha, "note": note}
+
+
+DRAM_TRAFFIC = {
+    ("star5_F100", "t1.spread"): _cap(18210560, 0.487, 0.410, 0.708, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t3.spread"): _cap(19069696, 0.483, 0.414, 0.700, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t1.fft_rows"): _cap(15310848, 0.279, 0.090, 0.447, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t1.fft_cols_epilogue"): _cap(7558400, 0.236, 0.067, 0.283, _SHA_FFT,
+                                                 _CAP_STAR),
+    ("star5_F100", "t3.fft_rows"): _cap(6742272, 0.373, 0.132, 0.317, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.fft_cols"): _cap(15194624, 0.370, 0.106, 0.468, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.interp_epilogue"): _cap(21465600, 0.608, 0.351, 0.903, _SHA_INTERP,
+                                               _CAP_STAR),
+    ("hg24_sweep64", "spread"): _cap(23635725, 0.511, 0.433, 0.768, _SHA_SPREAD, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_rows"): _cap(16903692, 0.267, 0.066, 0.224, _SHA_FFT, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_cols_epilogue"): _cap(82326301, 0.741, 0.269, 0.461, _SHA_FFT,
+                                                _CAP_SWEEP),
+    ("randstar20_F1000", "spread"): _cap(826517793, 0.514, 0.434, 0.733, _SHA_SPREAD,
+                                         _CAP_R1000),
+}
 
 
 def sources_sha(kind):
@@ -254,15 +286,16 @@ def stage_kind(stage):
 
 
 def measured_traffic(workload_name, stage):
-    """(bytes, note) of the ncu capture of this kernel on this workload, or
-    (None, why) when there is none or the kernel changed since."""
+    """(bytes, note, SM-side utilisations) of the ncu capture of this kernel
+    on this workload, or (None, why, None) when there is none or the kernel
+    changed since."""
     e = DRAM_TRAFFIC.get((workload_name, stage))
     if e is None:
-        return None, "no ncu capture of this kernel on this workload"
+        return None, "no ncu capture of this kernel on this workload", None
     kind = stage_kind(stage)
     if kind is None or sources_sha(kind) != e["sources_sha"]:
-        return None, "kernel sources changed since the ncu capture"
-    return e["bytes"], e["note"]
+        return None, "kernel sources changed since the ncu capture", None
+    return e["bytes"], e["note"], e.get("sm_side")
 
 
 def roofline(workload_name, ab, per_launch, note):
@@ -271,11 +304,15 @@ def roofline(workload_name, ab, per_launch, note):
     peak, src = _peaks()
     dom = max((k for k in per_launch if k in ab), key=lambda k: per_launch[k])
     achieved = ab[dom] / (per_launch[dom] * 1e-3) / 1e9
-    traffic, tnote = measured_traffic(workload_name, dom)
-    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "traffic_note": tnote,
-            "peak_source": src, "algorithmic_bytes": ab[dom], "ms_per_launch": per_launch[dom],
-            "timing": note}
+    traffic, tnote, sm_side = measured_traffic(workload_name, dom)
+    out = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": traffic, "traffic_note": tnote,
+           "peak_source": src, "algorithmic_bytes": ab[dom], "ms_per_launch": per_launch[dom],
+           "timing": note}
+    if sm_side:
+        # the ceiling on the SM side: each utilisation is a fraction of its own peak (1.0)
+        out["sm_side"] = dict(sm_side, ceiling=1.0, source=tnote)
+    return out
 
 
 def time_steps(step, stream, steps, flush=None):

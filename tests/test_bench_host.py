@@ -107,12 +107,13 @@ def test_rel_error_reports_l2_max_and_tolerance():
 def test_traffic_is_dropped_when_the_kernel_sources_change(monkeypatch):
     sha = bench.sources_sha("spread")
     monkeypatch.setitem(bench.DRAM_TRAFFIC, ("w", "t3.spread"),
-                        {"bytes": 123, "sources_sha": sha, "note": "capture"})
-    assert bench.measured_traffic("w", "t3.spread") == (123, "capture")
+                        bench._cap(123, 0.5, 0.4, 0.7, sha, "capture"))
+    b, why, sm = bench.measured_traffic("w", "t3.spread")
+    assert (b, why) == (123, "capture") and sm["issue_slots_busy"] == 0.5
     monkeypatch.setitem(bench.DRAM_TRAFFIC, ("w", "t3.spread"),
-                        {"bytes": 123, "sources_sha": "0" * 16, "note": "capture"})
-    b, why = bench.measured_traffic("w", "t3.spread")
-    assert b is None and "changed" in why
+                        bench._cap(123, 0.5, 0.4, 0.7, "0" * 16, "capture"))
+    b, why, sm = bench.measured_traffic("w", "t3.spread")
+    assert b is None and sm is None and "changed" in why
     assert bench.measured_traffic("w", "t1.fft_rows")[0] is None
 
 
@@ -122,3 +123,13 @@ def test_roofline_picks_the_slowest_stage_with_bytes():
     assert r["kernel"] == "a.spread"
     assert r["achieved"] == pytest.approx(4e9 / 2e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_capture_table_entries_are_well_formed():
+    """Every traffic entry carries its bytes, SM-side utilisations (fractions
+    of their own peaks), a source hash and a note; entries whose kernel
+    sources changed report null (measured_traffic)."""
+    for (wl, stage), e in bench.DRAM_TRAFFIC.items():
+        assert bench.stage_kind(stage) in bench.KERNEL_SOURCES
+        assert e["bytes"] > 0 and e["note"] and len(e["sources_sha"]) == 16
+        assert all(0 < v <= 1 for v in e["sm_side"].values())
