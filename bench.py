@@ -903,6 +903,27 @@ def randstar_arm(args, dev, local_rank, world, batch, steps, warmup, budget_s=10
     stages, stage_ms = {}, None
     if not batch:   # stage times are not kept inside the batch's captured graph
         stages, stage_ms = stage_pass([("", p)], lambda: step(t, out), stream, 3)
+    unbatched = None
+    if batch:
+        # the same instances as separate plans evaluated one after another on
+        # one stream: what the batch (one captured graph over four streams)
+        # replaces
+        singles = [Plan(q["families"], q["lam"], q["z"], TOL, precision="fp32", box=box,
+                        recompute_nodes=True, sync_status=False) for q in problems]
+        offs = np.concatenate([[0], np.cumsum(counts)])
+
+        def seq():
+            for i, q in enumerate(singles):
+                singles[i].eval(t[offs[i]:offs[i + 1]], out[offs[i]:offs[i + 1]])
+        for _ in range(2):
+            seq()
+        torch.cuda.synchronize()
+        seq_ms = statistics.median(time_steps(seq, stream, max(3, min(steps, 5))))
+        for q in singles:
+            q.close()
+        unbatched = {"ms_per_step": seq_ms, "value": total / (seq_ms * 1e-3),
+                     "how": "the same %d instances as separate plans, evaluated one after "
+                            "another on one stream" % len(problems)}
     # end to end: host targets in, host fields out, inside the timed region
     h_out = torch.empty(total, dtype=torch.complex64, pin_memory=True)
     h_in = torch.from_numpy(h_t).pin_memory()
@@ -950,7 +971,10 @@ def randstar_arm(args, dev, local_rank, world, batch, steps, warmup, budget_s=10
            "cpu_baseline": cpu,
            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(16 * total),
                    "d2h_bytes_per_step": int(8 * total)},
-           "gpu_launches": info["launches_per_eval"] * steps, "clocks": clk, "steps": steps}
+           "gpu_launches": p.info()["launches_per_eval"] * steps, "clocks": clk, "steps": steps}
+    if unbatched:
+        res["unbatched"] = unbatched
+        res["batching_speedup"] = unbatched["ms_per_step"] / ms_per_step
     p.close()
     del t, out
     torch.cuda.empty_cache()

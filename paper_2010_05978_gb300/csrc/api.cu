@@ -1861,8 +1861,10 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
         long long bytes = 0;
         int launches = 0;
         for (Plan* q : p->subs) {
+            fresnel_info qi{};
+            FRES_TRY(fresnel_get_info(reinterpret_cast<fresnel_plan_t>(q), &qi));
             bytes += q->bytes;
-            launches += q->last_launches;
+            launches += qi.launches_per_eval;
         }
         info->device_bytes = bytes;
         info->launches_per_eval = launches;
