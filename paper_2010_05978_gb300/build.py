@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]
 SOURCES = ["api.cu", "k_nodes.cu", "k_spread_f32.cu", "k_spread_f64.cu", "k_fft.cu", "k_interp.cu",
-           "k_adjoint.cu", "k_nsli.cu", "spread_api.cu", "spread_noalloc.cu"]
+           "k_adjoint.cu", "k_nsli.cu", "spread_api.cu", "spread_noalloc.cu", "k_col_dft_tc.cu"]
 
 
 def _nvcc():

@@ -83,6 +83,7 @@ struct Plan {
     int chunk_cap = 0, max_chunks = 0, max_split = 0;
     int* ready = nullptr;         // split tiles' ready flags (zero between evaluations)
     bool col_dft = false;         // type-1 column pass as a direct DFT over the live rows
+    int max_live_rows = 0;        // live tile rows of the fullest problem
     long long n_records = 0;
     int spread_blocks = 0;
     ChirpParams cp{};
@@ -582,7 +583,12 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ca.nty = p->nty;
         if (p->col_dft) {
             ca.twiddle = p->d2.tw;
-            launch_col_dft<T>(ca, p->nf2, p->status, p->st);
+            // FP32: the product on the tensor cores (split-TF32 operands);
+            // FP64 (no FP64 tensor path worth taking here): FMA loop
+            if (sizeof(T) == 4 && col_dft_tc_supported(ca, kTile * p->max_live_rows))
+                launch_col_dft_tc(ca, p->nf2, p->status, p->st);
+            else
+                launch_col_dft<T>(ca, p->nf2, p->status, p->st);
             p->launches++;
         } else {
             run_cols<T>(p, ca);
@@ -1311,6 +1317,7 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     // point of the nf2-point transform (measured over three radix stages):
     // direct when R n2 <= 24 nf2 (e.g. one live tile row, 512 of 1024 modes)
     {
+        p->max_live_rows = max_live_rows;
         const long long R = (long long)kTile * max_live_rows;
         p->col_dft = prune && R > 0 && R <= kDftMaxRows && R * p->n2 <= 24LL * p->nf2;
     }

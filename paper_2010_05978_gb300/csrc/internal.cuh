@@ -399,6 +399,11 @@ void launch_fft_cols(const FftPlan& fp, const ColPassArgs& a, cudaStream_t st);
 constexpr int kDftMaxRows = 128;
 template <typename T>
 void launch_col_dft(const ColPassArgs& a, int n, unsigned* status, cudaStream_t st);
+// k_col_dft_tc.cu: the same product (FP32 in and out) on the tensor cores,
+// tcgen05 MMAs of kind::tf32 on split high / low TF32 operands, for plans whose
+// problems have one live tile row (live_rows = 32)
+bool col_dft_tc_supported(const ColPassArgs& a, int live_rows);
+void launch_col_dft_tc(const ColPassArgs& a, int n, unsigned* status, cudaStream_t st);
 bool fft_supported(int n, int is_double, int* max_cols);
 // Split of a length beyond one pass into fa * fb (both single-pass), or false.
 bool fft_split(int n, int is_double, int* fa, int* fb);
