@@ -220,7 +220,7 @@ def rel_error(u, ref, tol, occulter=False):
 KERNEL_SOURCES = {
     "spread": ["spread.cuh", "k_spread_f32.cu", "internal.cuh"],
     "interp": ["k_interp.cu", "spread.cuh", "dfloat.cuh", "internal.cuh"],
-    "fft": ["k_fft.cu", "internal.cuh"],
+    "fft": ["k_fft.cu", "k_col_dft_tc.cu", "internal.cuh"],
     "nodes": ["k_nodes.cu", "dfloat.cuh", "internal.cuh"],
 }
 
@@ -276,7 +276,7 @@ def stage_kind(stage):
     s = stage.split(".")[-1]
     if s.startswith("spread"):
         return "spread"
-    if s.startswith("interp"):
+    if s.startswith("interp") or s == "target_sort":
         return "interp"
     if s.startswith("fft"):
         return "fft"
@@ -955,6 +955,8 @@ def randstar_arm(args, dev, local_rank, world, batch, steps, warmup, budget_s=10
               "fft_rows": (g + info["nf2"] * info["nfft1"]) * c64,
               "fft_cols": (info["nf2"] * info["nfft1"] + F) * c64,
               "interp_epilogue": total * (16 + c64)}
+        if "target_sort" in stages:   # binned interpolation: targets read, permutation written
+            ab["target_sort"] = total * (16 + 4)
         roof = roofline(name, ab, stages, "stage pass: per-stage CUDA events, 3 steps; the "
                         "headline step is timed without stage events")
     res = {"metric": metric, "unit": UNIT, "ms_per_step": ms_per_step, "value": value,

@@ -41,7 +41,7 @@ namespace {
 
 constexpr uint64_t kMagic = 0x46524553'4e454c31ull;   // "FRESNEL1"
 constexpr int kMaxEvents = 16;
-// FP32 type-3 target binning (16 x 16 blocks of the FFT grid, interpolation
+// FP32 type-3 target binning (kTargetBin x kTargetBin blocks of the FFT grid, interpolation
 // from shared-memory patches) is chosen automatically only when the FFT grid
 // would not stay in L2 and the target set is large.  Measured on the
 // F = 100 star workload (29 MB grid, 1e6 targets): binned 0.18 ms against
@@ -638,7 +638,9 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
                 }
                 sort = T3Sort{p->tcounts, p->tstart, p->tcursor, p->perm, p->twork, p->tpartial};
                 sp = &sort;
+                launch_target_sort(d_targets, M, p->ip, p->ks.w, sp, p->st);
                 p->launches += p->ip.nbin1 * p->ip.nbin2 <= kBinScanStaged ? 3 : 5;
+                ev_record(p, "target_sort");
             }
             launch_interp_w<T>(d_targets, M, (const cx_t<T>*)p->F, p->ip, p->ks, p->cheb,
                                p->ncheb, d_out, p->status, sp, p->st);
@@ -1022,8 +1024,8 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         for (int i = 0; i < 4; ++i) ip.box[i] = b[i];
         ip.nfft1 = p->nfft1;
         ip.nfft2 = p->nfft2;
-        ip.nbin1 = (p->nfft1 + 15) / 16;
-        ip.nbin2 = (p->nfft2 + 15) / 16;
+        ip.nbin1 = (p->nfft1 + kTargetBin - 1) / kTargetBin;
+        ip.nbin2 = (p->nfft2 + kTargetBin - 1) / kTargetBin;
         auto put = [](float* d, double v) {
             dflt s = df_host(v);
             d[0] = s.hi;

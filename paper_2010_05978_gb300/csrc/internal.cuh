@@ -423,7 +423,7 @@ struct InterpParams {
     float dK1[2], dK2[2], dG1[2], dG2[2], dkq[2], dp1[2], dp2[2];
     float boxf[4];
     float shK1, shK2;        // (g + w/2) * shK = argument of psihat
-    int nbin1, nbin2;        // 16 x 16 target bins per dimension of the FFT grid
+    int nbin1, nbin2;        // kTargetBin x kTargetBin target bins per dimension of the FFT grid
     double box[4];
     int nfft1, nfft2;
     int occulter;
@@ -439,11 +439,17 @@ struct T3Sort {
     int* work;
     int* partial;   // per 4096-bin chunk sums (bin counts too many to scan in one block)
 };
+constexpr int kTargetBin = 16;          // edge of a target bin (cells of the FFT grid)
 constexpr int kBinScanStaged = 40000;   // bins scanned by one block in shared memory
 constexpr int kBinChunk = 4096;         // bins per block of the multi-block scan
+// FP32 binned path, step 1: bucket the targets by bin (count, scan, scatter
+// into sort->perm; three or five launches).  w must satisfy
+// interp_binned_width.
+void launch_target_sort(const double* targets, long long M, const InterpParams& ip, int w,
+                        const T3Sort* sort, cudaStream_t st);
 // sort == NULL (or FP64, or a width without a binned kernel): one thread per
-// target straight from global memory.  Otherwise four launches: bin count,
-// scan, scatter, binned interpolation.
+// target straight from global memory.  Otherwise the binned interpolation
+// from sort->perm, which launch_target_sort has filled on the same stream.
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
                      const KernelShape& ks, const double* cheb, int ncheb,

@@ -22,7 +22,7 @@ namespace fres {
 
 namespace {
 
-constexpr int kBin = 16;            // target bins: 16 x 16 cells of F
+constexpr int kBin = kTargetBin;    // target bins: kBin x kBin cells of F
 
 // psihat(t) for |t| <= t_max from its even Chebyshev series
 // sum_k a_k T_{2k}(t / t_max) = sum_k a_k T_k(2 (t/t_max)^2 - 1), by Clenshaw.
@@ -438,16 +438,27 @@ __global__ void k_bin_chunk_write(int nbins, int* __restrict__ counts, const int
 template <int W>
 __global__ void k_target_scatter(const double* __restrict__ targets, long long M, InterpParams ip,
                                  int* __restrict__ cursor, int* __restrict__ perm) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M;
-         k += (long long)gridDim.x * blockDim.x) {
-        const double2 t = reinterpret_cast<const double2*>(targets)[k];
-        const int pos = atomicAdd(&cursor[target_bin<W>(t, ip)], 1);
-        if (pos >= 0 && pos < M) perm[pos] = (int)k;
+    // four targets per thread and pass: four atomics in flight at once
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < M; k += 4 * stride) {
+        int pos[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long ku = k + u * stride;
+            pos[u] = -1;
+            if (ku < M) {
+                const double2 t = reinterpret_cast<const double2*>(targets)[ku];
+                pos[u] = atomicAdd(&cursor[target_bin<W>(t, ip)], 1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (pos[u] >= 0 && pos[u] < M) perm[pos[u]] = (int)(k + u * stride);
     }
 }
 
 // Binned interpolation: a block takes bins dynamically (work[0]); it copies
-// the bin's (16 + w) x (16 + w) patch of F to shared memory and interpolates
+// the bin's (kBin + w) x (kBin + w) patch of F to shared memory and interpolates
 // the bin's targets from it, writing each result to the target's own index.
 template <int W>
 __global__ void __launch_bounds__(128)
@@ -483,6 +494,15 @@ k_interp_binned(const double* __restrict__ targets, long long M, const float2* _
         const int beg = s_start[b - b0];
         const int end = s_start[b - b0 + 1];
         if (beg >= end) continue;
+        // the first two targets of this thread: perm entries two steps
+        // ahead, target coordinates one step ahead, so a target's loads are
+        // in flight while the previous one (or the patch copy) is worked on
+        const int bs = blockDim.x;
+        int i = beg + threadIdx.x;
+        int k0 = i < end ? __ldg(&perm[i]) : -1;
+        int k1 = i + bs < end ? __ldg(&perm[i + bs]) : -1;
+        double2 t0 = k0 >= 0 ? __ldg(&reinterpret_cast<const double2*>(targets)[k0])
+                             : make_double2(0.0, 0.0);
         __syncthreads();   // the previous bin's targets are done with the patch
         const int ox = (b % ip.nbin1) * kBin, oy = (b / ip.nbin1) * kBin;
         for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
@@ -493,9 +513,12 @@ k_interp_binned(const double* __restrict__ targets, long long M, const float2* _
             patch[r * PS + c] = v;
         }
         __syncthreads();
-        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-            const int k = perm[i];
-            const double2 t = reinterpret_cast<const double2*>(targets)[k];
+        for (; i < end; i += bs) {
+            const int k = k0;
+            const double2 t = t0;
+            k0 = k1;
+            if (k1 >= 0) t0 = __ldg(&reinterpret_cast<const double2*>(targets)[k1]);
+            k1 = i + 2 * bs < end ? __ldg(&perm[i + 2 * bs]) : -1;
             dflt xi, eta;
             int s1, s2;
             float f1, f2, targ1, targ2;
@@ -560,6 +583,41 @@ void launch_cheb_samples(int n, double tmax, int w, double beta, const double* g
     k_cheb_samples<<<(n + 63) / 64, 64, 0, st>>>(n, tmax, w, beta, gq_t, gq_w, q, out);
 }
 
+void launch_target_sort(const double* targets, long long M, const InterpParams& ip, int w,
+                        const T3Sort* sort, cudaStream_t st) {
+    if (M <= 0) return;
+    const int nbins = ip.nbin1 * ip.nbin2;
+    const int gb = nblk(M, 256, 152 * 16);
+    if (nbins <= kBinScanStaged) {
+        const size_t dyn = sizeof(int) * (size_t)nbins;
+        cudaFuncSetAttribute(k_target_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    }
+    auto scan = [&]() {
+        if (nbins <= kBinScanStaged) {
+            k_target_scan<<<1, 1024, sizeof(int) * (size_t)nbins, st>>>(nbins, sort->counts,
+                                                                        sort->start, sort->cursor);
+        } else {
+            const int nchunks = (nbins + kBinChunk - 1) / kBinChunk;
+            k_bin_chunk_sums<<<nchunks, 256, 0, st>>>(nbins, sort->counts, sort->partial);
+            k_bin_chunk_scan<<<1, 32, 0, st>>>(nchunks, sort->partial);
+            k_bin_chunk_write<<<nchunks, 256, 0, st>>>(nbins, sort->counts, sort->partial,
+                                                       sort->start, sort->cursor);
+        }
+    };
+#define FRES_SORT_CASE(WW)                                                                     \
+    case WW:                                                                                   \
+        k_target_count<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->counts);                  \
+        scan();                                                                                \
+        k_target_scatter<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->cursor, sort->perm);    \
+        return;
+    switch (w) {
+        FRES_SORT_CASE(4) FRES_SORT_CASE(5) FRES_SORT_CASE(6) FRES_SORT_CASE(7)
+        FRES_SORT_CASE(8) FRES_SORT_CASE(9) FRES_SORT_CASE(10)
+        default: break;
+    }
+#undef FRES_SORT_CASE
+}
+
 template <typename T>
 void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const InterpParams& ip,
                      const KernelShape& ks, const double* cheb, int ncheb, void* out,
@@ -567,31 +625,10 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
     if (M <= 0) return;
     T beta = (T)ks.beta;
     if constexpr (std::is_same<T, float>::value) {
-        if (sort) {   // binned path: count, scan, scatter, interpolate from patches
+        if (sort) {   // binned path: interpolate each bin's targets from its patch
             const int nbins = ip.nbin1 * ip.nbin2;
-            const int gb = nblk(M, 256, 152 * 16);
-            const bool staged = nbins <= kBinScanStaged;
-            const size_t dyn = sizeof(int) * (size_t)nbins;
-            const int nchunks = (nbins + kBinChunk - 1) / kBinChunk;
-            if (staged)
-                cudaFuncSetAttribute(k_target_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)dyn);
-            auto scan = [&]() {
-                if (staged) {
-                    k_target_scan<<<1, 1024, dyn, st>>>(nbins, sort->counts, sort->start,
-                                                        sort->cursor);
-                } else {
-                    k_bin_chunk_sums<<<nchunks, 256, 0, st>>>(nbins, sort->counts, sort->partial);
-                    k_bin_chunk_scan<<<1, 32, 0, st>>>(nchunks, sort->partial);
-                    k_bin_chunk_write<<<nchunks, 256, 0, st>>>(nbins, sort->counts, sort->partial,
-                                                               sort->start, sort->cursor);
-                }
-            };
 #define FRES_BINNED_CASE(WW)                                                                   \
     case WW:                                                                                   \
-        k_target_count<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->counts);                  \
-        scan();                                                                                \
-        k_target_scatter<WW><<<gb, 256, 0, st>>>(targets, M, ip, sort->cursor, sort->perm);    \
         k_interp_binned<WW><<<152 * 8, 128, 0, st>>>(targets, M, F, ip, cheb, ncheb,           \
                                                       (float2*)out, status, ks.horner,         \
                                                       sort->perm, sort->start, nbins,          \
