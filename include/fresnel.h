@@ -214,6 +214,19 @@ typedef struct {
      * (about a second), > 0 = that many, < 0 = none at all (every such wait
      * gives up at once; for tests of the timeout path). */
     long long max_spin;
+    /* 1: results repeat bit for bit from evaluation to evaluation and plan
+     * to plan (same device, library and options).  The spreading stage then
+     * sums in exact fixed point (each contribution scaled by a power of two
+     * fixed per evaluation from the largest strength and the fullest tile,
+     * then rounded once to an integer), so neither the order of the records
+     * within a tile nor the order of a split tile's chunks can change a bit;
+     * every other stage already sums in a fixed order.  Costs two launches
+     * more per evaluation and a slower spread (shared-memory 64-bit atomic
+     * adds); plans whose fullest tile holds 2^23 or more records are
+     * refused (FRESNEL_ERR_UNSUPPORTED).  The accuracy meets tol as in the
+     * default mode.  0 (default): the spread sums in floating point in the
+     * order the records arrive, which varies by a few ulp between runs. */
+    int deterministic;
 } fresnel_opts;
 
 /* Fills *opts with defaults: FP32_FAST, aperture, grid 100 x 100 with h = 0.03,
@@ -385,6 +398,8 @@ typedef struct {
     int tile_x, tile_y;     /* spreading tile */
     long long device_bytes; /* device memory the plan holds */
     int launches_per_eval;  /* kernels launched by one fresnel_eval */
+    int split_tiles;        /* spreading tiles whose records are split over several work items */
+    int max_tile_records;   /* node records of the fullest spreading tile */
 } fresnel_info;
 
 fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info);

@@ -82,6 +82,9 @@ struct Plan {
     int ntx = 0, nty = 0, ntiles = 0;
     int chunk_cap = 0, max_chunks = 0, max_split = 0;
     int* ready = nullptr;         // split tiles' ready flags (zero between evaluations)
+    unsigned long long* det_acc = nullptr;   // deterministic mode: split tiles' fixed-point sums
+    double* det_part = nullptr;   // deterministic mode: the strengths' partial maxima
+    int det_tmax = 0;             // records of the fullest tile
     bool col_dft = false;         // type-1 column pass as a direct DFT over the live rows
     int max_live_rows = 0;        // live tile rows of the fullest problem
     long long n_records = 0;
@@ -542,12 +545,20 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ev_record(p, "scatter");
         p->nodes_ready = true;
     }
-    const long long spin = p->opts.max_spin == 0 ? kDefaultMaxSpin
-                                                 : std::max(0LL, p->opts.max_spin);
-    launch_spread<T>((const NodeRec<T>*)p->sorted, p->chunks, p->n_meta, p->max_chunks,
-                     p->ready, p->max_split, spin, (cx_t<T>*)p->grid, p->work, p->status, p->nf1,
-                     p->nf2, p->ntx, p->ntiles, p->ks, p->spread_blocks, p->st);
-    p->launches += 1;
+    if (p->opts.deterministic) {
+        launch_spread_det<T>((const NodeRec<T>*)p->sorted, p->n_records, p->chunks, p->n_meta,
+                             p->max_chunks, p->split_tiles, p->max_split, p->det_acc,
+                             p->det_part, p->det_tmax, (cx_t<T>*)p->grid, p->work, p->status,
+                             p->nf1, p->nf2, p->ntx, p->ntiles, p->ks, p->st);
+        p->launches += p->max_split > 0 ? 3 : 2;
+    } else {
+        const long long spin = p->opts.max_spin == 0 ? kDefaultMaxSpin
+                                                     : std::max(0LL, p->opts.max_spin);
+        launch_spread<T>((const NodeRec<T>*)p->sorted, p->chunks, p->n_meta, p->max_chunks,
+                         p->ready, p->max_split, spin, (cx_t<T>*)p->grid, p->work, p->status,
+                         p->nf1, p->nf2, p->ntx, p->ntiles, p->ks, p->spread_blocks, p->st);
+        p->launches += 1;
+    }
     ev_record(p, "spread");
     if (p->tkind == FRESNEL_GRID) {
         RowPassArgs ra{};
@@ -1274,7 +1285,13 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     // atomic tile additions.  Small plans keep the base cap.
     {
         long long total = 0;
-        for (int c : hc) total += c;
+        for (int c : hc) {
+            total += c;
+            p->det_tmax = std::max(p->det_tmax, c);
+        }
+        if (p->opts.deterministic && p->det_tmax >= kDetMaxTileRecords)
+            return fres_fail(FRESNEL_ERR_UNSUPPORTED,
+                             "deterministic mode: a spreading tile holds 2^23 or more records");
         const long long slots = 152LL * 4 * 8;
         const long long base = p->chunk_cap;
         p->chunk_cap = (int)std::max(base, std::min(total / slots, 1LL << 20));
@@ -1332,6 +1349,12 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     FRES_TRY(dalloc(p, (void**)&p->split_tiles, sizeof(int) * std::max(1, p->max_split)));
     FRES_TRY(dalloc(p, (void**)&p->ready, sizeof(int) * std::max(1, p->max_split)));
     FRES_CK(cudaMemsetAsync(p->ready, 0, sizeof(int) * std::max(1, p->max_split), p->st));
+    if (p->opts.deterministic) {
+        const size_t acc = sizeof(unsigned long long) * 4 * kTile * kTile * std::max(1, p->max_split);
+        FRES_TRY(dalloc(p, (void**)&p->det_acc, acc));
+        FRES_CK(cudaMemsetAsync(p->det_acc, 0, acc, p->st));
+        FRES_TRY(dalloc(p, (void**)&p->det_part, sizeof(double) * kDetPartials));
+    }
     {
         int* d_sc = nullptr;
         int* d_pl = nullptr;
@@ -1877,6 +1900,10 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
         }
         info->device_bytes = bytes;
         info->launches_per_eval = launches;
+        for (size_t i = 1; i < p->subs.size(); ++i) {
+            info->split_tiles += p->subs[i]->max_split;
+            info->max_tile_records = std::max(info->max_tile_records, p->subs[i]->det_tmax);
+        }
         return FRESNEL_OK;
     }
     info->n_nodes = p->N;
@@ -1893,7 +1920,10 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
     int nl = 4;   // spread, two FFT passes, (type 3) interpolation
     if (p->tkind == FRESNEL_GRID) nl = 3;
     if (p->opts.recompute_nodes) nl += 3;   // nodes, scan, scatter
+    if (p->opts.deterministic) nl += 2;      // strengths' maxima, split tiles' conversion
     info->launches_per_eval = p->last_launches > 0 ? p->last_launches : nl;
+    info->split_tiles = p->max_split;
+    info->max_tile_records = p->det_tmax;
     return FRESNEL_OK;
 }
 

@@ -310,6 +310,20 @@ void launch_spread(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_m
                    int max_chunks, int* ready, int max_split, long long max_spin,
                    cx_t<T>* grid, int* work, unsigned* status, int nf1, int nf2, int ntx,
                    int ntiles, const KernelShape& ks, int nblocks, cudaStream_t st);
+// Deterministic mode (fresnel_opts.deterministic): the same grid from exact
+// fixed-point sums, bit for bit whatever the records' order within a tile
+// and the split tiles' chunk order.  Three launches: the strengths' partial
+// maxima into det_part[kDetPartials], the spreading pass, and the split
+// tiles' conversion.  split_acc: max_split x 32 KB, zero on entry (left
+// zero); tmax: records of the fullest tile (< kDetMaxTileRecords).
+template <typename T>
+void launch_spread_det(const NodeRec<T>* sorted, long long n_records, const Chunk* chunks,
+                       const int* n_meta, int max_chunks, const int* split_tiles, int max_split,
+                       unsigned long long* split_acc, double* det_part, int tmax, cx_t<T>* grid,
+                       int* work, unsigned* status, int nf1, int nf2, int ntx, int ntiles,
+                       const KernelShape& ks, cudaStream_t st);
+constexpr int kDetPartials = 152 * 4;          // det_part entries
+constexpr int kDetMaxTileRecords = 1 << 23;
 
 // k_nsli.cu: non-singular line integral (Appendix, eq. nsli) over the
 // boundary rules of the given families, FP64, one thread per target

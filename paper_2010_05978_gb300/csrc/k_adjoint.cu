@@ -243,25 +243,37 @@ __global__ void k_adj_modes(const FamilyDev* __restrict__ fams, const int* __res
 }
 
 // One block per PETALS family (list pf): dL/dA_l = sum over petals and angles
-// of the node contributions (one warp per l), then the profile parameters.
+// of the node contributions (one warp per l), then the profile parameters,
+// added by one thread in increasing l (a fixed order: the gradient repeats
+// bit for bit), kL radii at a time.
 __global__ void k_adj_reduce(const FamilyDev* __restrict__ fams, const int* __restrict__ pf,
                              const long long* __restrict__ gofs,
                              const double* __restrict__ contrib, double* __restrict__ grad) {
+    constexpr int kL = 1024;
+    __shared__ double s_l[kL];
     const FamilyDev& f = fams[pf[blockIdx.x]];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long nki = (long long)f.n_panels * f.p;      // nodes per radius
-    for (int l = warp; l < f.m; l += nw) {
-        double s = 0.0;
-        for (long long e = lane; e < nki; e += 32) s += contrib[f.offset + e * f.m + l];
+    for (int l0 = 0; l0 < f.m; l0 += kL) {
+        const int l1 = min(l0 + kL, f.m);
+        for (int l = l0 + warp; l < l1; l += nw) {
+            double s = 0.0;
+            for (long long e = lane; e < nki; e += 32) s += contrib[f.offset + e * f.m + l];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            const double r = f.pa + (f.pR - f.pa) * f.gl_m_a[l];
-            int idx[4];
-            double val[4];
-            const int cnt = petal_profile_grad(f, l, r, idx, val);
-            for (int q = 0; q < cnt; ++q) atomicAdd(&grad[gofs[blockIdx.x] + idx[q]], s * val[q]);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) s_l[l - l0] = s;
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int l = l0; l < l1; ++l) {
+                const double r = f.pa + (f.pR - f.pa) * f.gl_m_a[l];
+                int idx[4];
+                double val[4];
+                const int cnt = petal_profile_grad(f, l, r, idx, val);
+                for (int q = 0; q < cnt; ++q) grad[gofs[blockIdx.x] + idx[q]] += s_l[l - l0] * val[q];
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -564,16 +564,21 @@ k_col_dft(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status) {
     const int b = blockIdx.z;
     const int c0 = blockIdx.x * kDftTile;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    // the problem's live tile rows, found in parallel (their order does not
-    // matter: input and twiddles use the same list)
-    if (tid == 0) s_nt = 0;
-    __syncthreads();
-    for (int t = tid; t < a.nty; t += blockDim.x)
-        if (a.live[(long long)b * a.nty + t]) {
-            const int q = atomicAdd(&s_nt, 1);
-            if (q < kDftMaxRows / kTile)
+    // the problem's live tile rows in increasing order (one warp, ballots):
+    // a fixed summation order, so the outputs repeat bit for bit
+    if (tid < 32) {
+        int cnt = 0;
+        for (int t0 = 0; t0 < a.nty; t0 += 32) {
+            const int t = t0 + tid;
+            const bool on = t < a.nty && a.live[(long long)b * a.nty + t] != 0;
+            const unsigned m = __ballot_sync(0xffffffffu, on);
+            const int q = cnt + __popc(m & ((1u << tid) - 1u));
+            if (on && q < kDftMaxRows / kTile)
                 for (int i = 0; i < kTile; ++i) s_rows[q * kTile + i] = t * kTile + i;
+            cnt += __popc(m);
         }
+        if (tid == 0) s_nt = cnt;
+    }
     __syncthreads();
     int R = s_nt * kTile;
     if (R > kDftMaxRows) {

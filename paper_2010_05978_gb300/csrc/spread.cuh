@@ -273,6 +273,310 @@ k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks
     }
 }
 
+// ------------------------------------------------------------------ deterministic mode
+// Exact fixed-point accumulation.  Every contribution v (one component of
+// c_j psi psi, rounded once in T) is scaled by 2^S and held as H 2^40 + L with
+// integers H = rint(2^(S-40) v) and L = rint(2^S v - H 2^40): the difference
+// is exact in T, so L only rounds 2^S v to an integer.  Sums of integers do
+// not depend on the order of the additions (two's-complement adds wrap
+// associatively), so neither the order of the records within a tile (it
+// follows the scatter's atomic reservations) nor the order in which a split
+// tile's chunks finish changes a bit of the grid.  S is fixed per evaluation
+// from B = 2 T_max c_max (T_max: records of the fullest tile; c_max: the
+// largest strength component, a maximum, which no order changes):
+// 2^S B <= 2^100, so |sum H| < 2^61 and, with T_max < 2^23, |sum L| < 2^62.
+// The resolution 2^-S <= B 2^-99 lies far below either precision's rounding.
+
+template <typename T>
+struct DetScale {
+    T a, b;       // 2^S = a b (each factor inside T's range)
+    double inv;   // 2^-S
+};
+
+// c_max from the partial maxima (+inf marks a non-finite strength) and the
+// scale; flags kStatusNonFinite (scale 1) or kStatusOverflow (B > 2^350).
+template <typename T>
+__device__ __forceinline__ DetScale<T> det_scale(double cmax, int tmax, unsigned* status,
+                                                 bool report) {
+    int S = 0;
+    if (!(cmax < INFINITY)) {
+        if (report && status) atomicOr(status, kStatusNonFinite);
+    } else if (cmax > 0.0) {
+        int e;
+        frexp(2.0 * (double)max(tmax, 1) * cmax, &e);   // B < 2^e
+        S = 100 - e;
+        if (S < -250) {
+            if (report && status) atomicOr(status, kStatusOverflow);
+            S = -250;
+        }
+        S = min(S, 250);
+    }
+    DetScale<T> d;
+    d.a = (T)ldexp(1.0, S / 2);
+    d.b = (T)ldexp(1.0, S - S / 2);
+    d.inv = ldexp(1.0, -S);
+    return d;
+}
+
+__device__ __forceinline__ long long det_to_ll(float v) { return __float2ll_rn(v); }
+__device__ __forceinline__ long long det_to_ll(double v) { return __double2ll_rn(v); }
+
+// (H, L) of one contribution
+template <typename T>
+__device__ __forceinline__ void det_split(T v, const DetScale<T>& sc, long long& h, long long& l) {
+    const T x = (v * sc.a) * sc.b;
+    const T hh = rint(x * (T)9.094947017729282379150390625e-13);   // 2^-40
+    h = det_to_ll(hh);
+    l = det_to_ll(x - hh * (T)1099511627776.0);                    // 2^40
+}
+
+template <typename T>
+__device__ __forceinline__ T det_value(long long h, long long l, double inv) {
+    return (T)(((double)h * 1099511627776.0 + (double)l) * inv);
+}
+
+// Block maximum of |cre|, |cim| over the records into part[blockIdx.x]
+// (+inf where a strength is not finite).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_det_cmax(const NodeRec<T>* __restrict__ rec, long long n, double* __restrict__ part) {
+    __shared__ double s[8];
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double a = fabs((double)rec[i].cre), b = fabs((double)rec[i].cim);
+        m = (a < INFINITY && b < INFINITY) ? fmax(m, fmax(a, b)) : INFINITY;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s[w]);
+        part[blockIdx.x] = m;
+    }
+}
+
+// max over the kDetPartials partial maxima, by one block (every block
+// computes the same value)
+__device__ __forceinline__ double det_block_cmax(const double* __restrict__ part, double* s_red) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < kDetPartials; i += blockDim.x) m = fmax(m, part[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = s_red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
+    __syncthreads();
+    return m;
+}
+
+template <typename T, int W>
+struct DetSmem {
+    unsigned long long acc[kTile * kTile * 4];   // per cell: re H, re L, im H, im L
+    cx_t<T> cky[kSpreadWarps][32][LaneMap<T, W>::CS];
+    T kx[kSpreadWarps][32][W + 1];
+    int dxy[kSpreadWarps][32][2];
+    double red[kSpreadWarps];
+    int s_ci;
+    int s_last;
+};
+
+// The deterministic spreading pass: one fixed-point tile per block (shared
+// 64-bit atomic adds: warps may meet on a cell), chunks claimed dynamically
+// as in k_spread.  A plain tile is converted and stored; a split tile's
+// chunks add their nonzero cells into its fixed-point accumulator in global
+// memory (64-bit atomic adds), which k_spread_det_finish converts.  No chunk
+// waits on another.
+template <typename T, int W>
+__global__ void __launch_bounds__(kSpreadWarps * 32)
+k_spread_det(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks,
+             const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid, int* __restrict__ work,
+             unsigned long long* __restrict__ split_acc, int max_split,
+             const double* __restrict__ det_part, int tmax, unsigned* __restrict__ status,
+             int nf1, int nf2, int ntx, int ntiles, T beta, const HornerTab hz) {
+    constexpr int TT = kTile * kTile;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DetSmem<T, W>& sm = *reinterpret_cast<DetSmem<T, W>*>(smem_raw);
+    constexpr int RPW = LaneMap<T, W>::RPW, NPASS = LaneMap<T, W>::NPASS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const DetScale<T> sc =
+        det_scale<T>(det_block_cmax(det_part, sm.red), tmax, status, blockIdx.x == 0 && threadIdx.x == 0);
+    const int n_chunks = n_meta[0];
+    for (;;) {
+        if (threadIdx.x == 0) sm.s_ci = atomicAdd(&work[0], 1);
+        __syncthreads();
+        const int ci = sm.s_ci;
+        if (ci >= n_chunks) break;
+        const Chunk ch = chunks[ci];
+        if (ch.split == 1) {   // padding: no records
+            __syncthreads();
+            continue;
+        }
+        const int sidx = ch.split >= 2 ? (ch.split >> 1) - 1 : -1;
+        const int lt = ch.tile % ntiles;
+        const int tx0 = (lt % ntx) * kTile;
+        const int ty0 = (lt / ntx) * kTile;
+        for (int e = threadIdx.x; e < TT * 4; e += blockDim.x) sm.acc[e] = 0ull;
+        __syncthreads();
+        for (int base = ch.begin + warp * 32; base < ch.end; base += kSpreadWarps * 32) {
+            const int k = base + lane;
+            const int cnt = min(32, ch.end - base);
+            if (lane < cnt) {
+                const NodeRec<T> r = sorted[k];
+                int dx = r.s1 - tx0;
+                if (dx >= kTile) dx -= nf1;
+                int dy = r.s2 - ty0;
+                if (dy >= kTile) dy -= nf2;
+                sm.dxy[warp][lane][0] = dx;
+                sm.dxy[warp][lane][1] = dy;
+                T kxv[W], kyv[W];
+                kernel_values<T, W>(r.f1, beta, hz, kxv);
+                kernel_values<T, W>(r.f2, beta, hz, kyv);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    sm.kx[warp][lane][a] = kxv[a];
+                    cx_t<T> v;
+                    v.x = r.cre * kyv[a];
+                    v.y = r.cim * kyv[a];
+                    sm.cky[warp][lane][(a % RPW) * NPASS + a / RPW] = v;
+                }
+                sm.kx[warp][lane][W] = (T)0;
+            }
+            __syncwarp();
+            const int a = lane % W, b0 = lane / W;
+            const bool lane_on = lane < RPW * W;
+            for (int j = 0; j < cnt; ++j) {
+                const int dx = sm.dxy[warp][j][0], dy = sm.dxy[warp][j][1];
+                const int x = dx + a;
+                if (lane_on && (unsigned)x < (unsigned)kTile) {
+                    const T kxv = sm.kx[warp][j][a];
+#pragma unroll
+                    for (int q = 0; q < NPASS; ++q) {
+                        const int b = b0 + q * RPW;
+                        const int y = dy + b;
+                        if (b < W && (unsigned)y < (unsigned)kTile) {
+                            const cx_t<T> c = sm.cky[warp][j][b0 * NPASS + q];
+                            long long h, l;
+                            unsigned long long* cell = sm.acc + (y * kTile + x) * 4;
+                            det_split<T>(c.x * kxv, sc, h, l);
+                            atomicAdd(cell, (unsigned long long)h);
+                            atomicAdd(cell + 1, (unsigned long long)l);
+                            det_split<T>(c.y * kxv, sc, h, l);
+                            atomicAdd(cell + 2, (unsigned long long)h);
+                            atomicAdd(cell + 3, (unsigned long long)l);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (sidx < 0) {
+            cx_t<T>* dst = tile_origin<T>(grid, ch.tile, nf1, nf2, ntx, ntiles);
+            for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+                const unsigned long long* c = sm.acc + e * 4;
+                cx_t<T> v;
+                v.x = det_value<T>((long long)c[0], (long long)c[1], sc.inv);
+                v.y = det_value<T>((long long)c[2], (long long)c[3], sc.inv);
+                dst[(long long)(e / kTile) * nf1 + e % kTile] = v;
+            }
+        } else if (sidx < max_split) {
+            unsigned long long* g = split_acc + (size_t)sidx * TT * 4;
+            for (int e = threadIdx.x; e < TT * 4; e += blockDim.x)
+                if (sm.acc[e]) atomicAdd(g + e, sm.acc[e]);
+        } else if (threadIdx.x == 0 && status) {
+            atomicOr(status, kStatusOverflow);   // no accumulator for this split tile
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        sm.s_last = atomicAdd(&work[1], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (sm.s_last && threadIdx.x == 0) {
+        work[0] = 0;
+        work[1] = 0;
+    }
+}
+
+// Split tiles: fixed-point accumulator -> grid tile, then the accumulator
+// back to zero for the next evaluation.  Block s takes split tiles s,
+// s + gridDim.x, ... (split_tiles[s] < 0: unused slot).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_spread_det_finish(const int* __restrict__ split_tiles, int max_split,
+                    unsigned long long* __restrict__ split_acc, const double* __restrict__ det_part,
+                    int tmax, cx_t<T>* __restrict__ grid, int nf1, int nf2, int ntx, int ntiles) {
+    constexpr int TT = kTile * kTile;
+    __shared__ double red[8];
+    const DetScale<T> sc = det_scale<T>(det_block_cmax(det_part, red), tmax, nullptr, false);
+    for (int s = blockIdx.x; s < max_split; s += gridDim.x) {
+        const int tile = split_tiles[s];
+        if (tile < 0) continue;
+        cx_t<T>* dst = tile_origin<T>(grid, tile, nf1, nf2, ntx, ntiles);
+        unsigned long long* g = split_acc + (size_t)s * TT * 4;
+        for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+            const unsigned long long* c = g + e * 4;
+            cx_t<T> v;
+            v.x = det_value<T>((long long)c[0], (long long)c[1], sc.inv);
+            v.y = det_value<T>((long long)c[2], (long long)c[3], sc.inv);
+            dst[(long long)(e / kTile) * nf1 + e % kTile] = v;
+            g[e * 4] = g[e * 4 + 1] = g[e * 4 + 2] = g[e * 4 + 3] = 0ull;
+        }
+    }
+}
+
+template <typename T, int W>
+void launch_spread_det_w(const NodeRec<T>* sorted, long long n_records, const Chunk* chunks,
+                         const int* n_meta, int max_chunks, const int* split_tiles, int max_split,
+                         unsigned long long* split_acc, double* det_part, int tmax,
+                         cx_t<T>* grid, int* work, unsigned* status, int nf1, int nf2, int ntx,
+                         int ntiles, T beta, const HornerTab& hz, cudaStream_t st) {
+    k_det_cmax<T><<<kDetPartials, 256, 0, st>>>(sorted, n_records, det_part);
+    const size_t smem = sizeof(DetSmem<T, W>);
+    cudaFuncSetAttribute(k_spread_det<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_det<T, W>, kSpreadWarps * 32,
+                                                  smem);
+    int g = 152 * (per_sm < 1 ? 1 : per_sm);
+    if (g > max_chunks) g = max_chunks;
+    if (g < 1) g = 1;
+    k_spread_det<T, W><<<g, kSpreadWarps * 32, smem, st>>>(sorted, chunks, n_meta, grid, work,
+                                                           split_acc, max_split, det_part, tmax,
+                                                           status, nf1, nf2, ntx, ntiles, beta,
+                                                           hz);
+    if (max_split > 0)
+        k_spread_det_finish<T><<<max_split < 152 * 4 ? max_split : 152 * 4, 256, 0, st>>>(
+            split_tiles, max_split, split_acc, det_part, tmax, grid, nf1, nf2, ntx, ntiles);
+}
+
+template <typename T>
+void launch_spread_det_impl(const NodeRec<T>* sorted, long long n_records, const Chunk* chunks,
+                            const int* n_meta, int max_chunks, const int* split_tiles,
+                            int max_split, unsigned long long* split_acc, double* det_part,
+                            int tmax, cx_t<T>* grid, int* work, unsigned* status, int nf1,
+                            int nf2, int ntx, int ntiles, const KernelShape& ks, cudaStream_t st) {
+    T beta = (T)ks.beta;
+#define FRES_DET_CASE(WW)                                                                     \
+    case WW:                                                                                  \
+        launch_spread_det_w<T, WW>(sorted, n_records, chunks, n_meta, max_chunks, split_tiles, \
+                                   max_split, split_acc, det_part, tmax, grid, work, status,  \
+                                   nf1, nf2, ntx, ntiles, beta, ks.horner, st);               \
+        break;
+    switch (ks.w) {
+        FRES_DET_CASE(2) FRES_DET_CASE(3) FRES_DET_CASE(4) FRES_DET_CASE(5)
+        FRES_DET_CASE(6) FRES_DET_CASE(7) FRES_DET_CASE(8) FRES_DET_CASE(9)
+        FRES_DET_CASE(10) FRES_DET_CASE(11) FRES_DET_CASE(12) FRES_DET_CASE(13)
+        FRES_DET_CASE(14) FRES_DET_CASE(15) FRES_DET_CASE(16)
+        default: break;
+    }
+#undef FRES_DET_CASE
+}
+
 template <typename T, int W>
 void launch_spread_w(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
                      int max_chunks, int* ready, int max_split, long long max_spin,

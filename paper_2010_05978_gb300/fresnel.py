@@ -57,7 +57,8 @@ class Opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("nsli_far", ctypes.c_double),
                 ("screen_amp", ctypes.c_void_p), ("screen_opd", ctypes.c_void_p),
                 ("screen_n1", ctypes.c_int), ("screen_n2", ctypes.c_int),
-                ("screen_box", ctypes.c_double * 4), ("max_spin", ctypes.c_longlong)]
+                ("screen_box", ctypes.c_double * 4), ("max_spin", ctypes.c_longlong),
+                ("deterministic", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -65,7 +66,8 @@ class Info(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("nf1", ctypes.c_int), ("nf2", ctypes.c_int),
                 ("nfft1", ctypes.c_int), ("nfft2", ctypes.c_int), ("tile_x", ctypes.c_int),
                 ("tile_y", ctypes.c_int), ("device_bytes", ctypes.c_longlong),
-                ("launches_per_eval", ctypes.c_int)]
+                ("launches_per_eval", ctypes.c_int), ("split_tiles", ctypes.c_int),
+                ("max_tile_records", ctypes.c_int)]
 
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_plan_many", "fresnel_eval",
@@ -194,7 +196,7 @@ def _family_array(families):
 
 def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes, sync_status,
                max_device_bytes, t3_binning, fft_split_above=0, autotune=False, nsli_far=0.0,
-               screen=None, max_spin=0):
+               screen=None, max_spin=0, deterministic=False):
     o = Opts()
     lib.fresnel_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -218,6 +220,7 @@ def _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nod
     o.autotune = int(bool(autotune))
     o.nsli_far = float(nsli_far)
     o.max_spin = int(max_spin)
+    o.deterministic = int(bool(deterministic))
     o._keep = []
     if screen is not None:
         # dict(amp=, opd=, box=(x0, x1, y0, y1)): 2D arrays (n2 rows of n1)
@@ -321,7 +324,8 @@ class BatchPlan(_PlanHandle):
     def __init__(self, problems, tol, precision="fp32", output="aperture", grid=None, box=None,
                  sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None, nsli_far=0.0, screen=None, max_spin=0):
+                 stream=None, nsli_far=0.0, screen=None, max_spin=0,
+                 deterministic=False):
         import torch
         lib = load_library()
         self._torch = torch
@@ -335,7 +339,7 @@ class BatchPlan(_PlanHandle):
             probs[b] = Problem(fams, len(q["families"]), float(q["lam"]), float(q["z"]))
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
-                       nsli_far, screen, max_spin)
+                       nsli_far, screen, max_spin, deterministic)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -398,13 +402,16 @@ class Plan(_PlanHandle):
     y0, y1)) multiplies each node's weight by A e^{2 pi i OPD / lam} from
     sampled amplitude and optical path difference (n2 rows of n1 samples);
     max_spin bounds the spreading stage's one device-side wait (polls before
-    FRESNEL_ERR_TIMEOUT; 0 the built-in ~1 s, < 0 none: tests of that path).
+    FRESNEL_ERR_TIMEOUT; 0 the built-in ~1 s, < 0 none: tests of that path);
+    deterministic=True makes the outputs repeat bit for bit (exact
+    fixed-point sums in the spreading stage).
     """
 
     def __init__(self, families, lam, z, tol, precision="fp32", output="aperture", grid=None,
                  box=None, sigma=0.0, kernel_w=0, recompute_nodes=False, sync_status=True,
                  max_device_bytes=0, t3_binning=0, fft_split_above=0, autotune=False,
-                 stream=None, nsli_far=0.0, screen=None, max_spin=0):
+                 stream=None, nsli_far=0.0, screen=None, max_spin=0,
+                 deterministic=False):
         import torch
         lib = load_library()
         self._torch = torch
@@ -413,7 +420,7 @@ class Plan(_PlanHandle):
         self.shape_sizes = _shape_sizes(families)
         o = _make_opts(lib, precision, output, grid, box, sigma, kernel_w, recompute_nodes,
                        sync_status, max_device_bytes, t3_binning, fft_split_above, autotune,
-                       nsli_far, screen, max_spin)
+                       nsli_far, screen, max_spin, deterministic)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

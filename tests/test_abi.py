@@ -88,8 +88,8 @@ def test_default_opts(lib):
     assert o.grid_n1 == 100 and abs(o.grid_h - 0.03) < 1e-15
     # every option added later defaults to off
     assert (o.sigma, o.kernel_w, o.recompute_nodes, o.max_device_bytes, o.t3_binning,
-            o.fft_split_above, o.autotune, o.nsli_far, o.max_spin) == (0.0, 0, 0, 0, 0, 0, 0,
-                                                                      0.0, 0)
+            o.fft_split_above, o.autotune, o.nsli_far, o.max_spin,
+            o.deterministic) == (0.0, 0, 0, 0, 0, 0, 0, 0.0, 0, 0)
     assert o.screen_amp is None and o.screen_opd is None and o.screen_n1 == o.screen_n2 == 0
     assert list(o.box) == [-1.0, 1.0, -1.0, 1.0]
 
