@@ -427,11 +427,13 @@ def star_arm(args, dev, local_rank, world, precision, steps, warmup, sample=None
     stream3 = torch.cuda.Stream()
     cdt = star_cdtype(torch, precision)
     targets = torch.tensor(targets_np, dtype=torch.float64, device=dev)
+    det = bool(getattr(args, "deterministic", False))
     p1, ms1 = timed_plan(lambda: Plan(fam, cfg["lam"], cfg["z"], TOL, precision=precision, grid=g,
-                                      recompute_nodes=True, sync_status=False))
+                                      recompute_nodes=True, sync_status=False,
+                                      deterministic=det))
     p3, ms3 = timed_plan(lambda: Plan(fam, cfg["lam"], cfg["z"], TOL, precision=precision,
                                       box=(-1.5, 1.5, -1.5, 1.5), recompute_nodes=True,
-                                      sync_status=False, stream=stream3))
+                                      sync_status=False, stream=stream3, deterministic=det))
     info1, info3 = p1.info(), p3.info()
     out1 = torch.empty((g["n2"], g["n1"]), dtype=cdt, device=dev)
     out3 = torch.empty((M3,), dtype=cdt, device=dev)
@@ -614,7 +616,7 @@ def run_ours(args, rank, world, local_rank):
         sample = oracle_sample(cfg, targets_np, 8.0)
     main = star_arm(args, dev, local_rank, world, prec, args.steps, args.warmup, sample)
     extras = {}
-    if world == 1 and args.extras and prec == "fp32":
+    if world == 1 and args.extras and prec == "fp32" and not args.deterministic:
         f64 = star_arm(args, dev, local_rank, world, "fp64", min(args.steps, 20), 3, sample,
                        e2e=False)
         extras["fp64_path"] = dict(_compact(f64), precision="fp64 throughout, tol 1e-6",
@@ -631,7 +633,9 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": main["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": config_dict(cfg, world, prec),
+        "config": dict(config_dict(cfg, world, prec),
+                       **({"deterministic": "exact fixed-point spreading (bitwise-repeatable)"}
+                          if args.deterministic else {})),
         "roofline": main["roofline"],
         "error": main["error"],
         "plan_ms": main["plan_ms"], "plan_plus_eval_ms": main["plan_plus_eval_ms"],
@@ -1183,6 +1187,9 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="star5_F100 only: time the headline workload alone (no FP64 path, "
                          "sweep or F=1000 objects in the line)")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="star5_F100 only: plans in deterministic mode (exact fixed-point "
+                         "spreading, bitwise-repeatable outputs); the line carries the star alone")
     ap.add_argument("--targets", type=int, default=0,
                     help="randstar_F1000 only: scattered targets (default 1e8; fewer for small "
                          "profiling captures)")
@@ -1192,6 +1199,8 @@ def main():
     args = ap.parse_args()
     if args.precision != "fp32" and args.workload != "star5_F100":
         ap.error("--precision fp64 is offered for the star5_F100 workload only")
+    if args.deterministic and args.workload != "star5_F100":
+        ap.error("--deterministic is offered for the star5_F100 workload only")
     sweep = args.workload == "starshade_sweep"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -137,6 +137,12 @@ struct Plan {
     cudaStream_t cst = nullptr;
     cudaEvent_t ev_h2d = nullptr, ev_free = nullptr;
     cudaEvent_t wait_tgt = nullptr;
+    // FP32 binned type 3: the target sort runs on sort_st, forked from st at
+    // the start of an evaluation (ev_sort_fork: the previous evaluation's
+    // interpolation is done with the sort buffers) and joined before the
+    // interpolation (ev_sorted), so it overlaps the spreading and the FFT
+    cudaStream_t sort_st = nullptr;
+    cudaEvent_t ev_sort_fork = nullptr, ev_sorted = nullptr;
     int timing = 0;
     cudaEvent_t ev[kMaxEvents] = {};
     const char* ev_name[kMaxEvents] = {};
@@ -209,6 +215,12 @@ void free_plan(Plan* p) {
         cudaStreamSynchronize(p->cst);
         cudaStreamDestroy(p->cst);
     }
+    if (p->sort_st) {
+        cudaStreamSynchronize(p->sort_st);
+        cudaStreamDestroy(p->sort_st);
+    }
+    for (cudaEvent_t e : {p->ev_sort_fork, p->ev_sorted})
+        if (e) cudaEventDestroy(e);
     for (void* a : p->allocs) cudaFree(a);
     if (p->perm) cudaFree(p->perm);
     for (int i = 0; i < kMaxEvents; ++i)
@@ -538,6 +550,38 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
     p->launches = 0;
     p->nev = 0;
     ev_record(p, "start");
+    // FP32 type 3 with binned interpolation: the target sort depends on the
+    // targets and the plan's geometry only, so it runs on its own stream
+    // beside the node, spreading and FFT stages (serially on st when stage
+    // times are recorded, so that each stage is timed on its own)
+    bool binned = false;
+    if (p->tkind == FRESNEL_SCATTERED && M > 0 && sizeof(T) == 4) {
+        const long long fbytes = (long long)p->nfft1 * p->nfft2 * (long long)sizeof(cx_t<T>);
+        const bool want = p->opts.t3_binning > 0 ||
+                          (p->opts.t3_binning == 0 && M >= kSortTargetsFrom &&
+                           fbytes > kBinFromGridBytes);
+        binned = want && M < (1LL << 31) && interp_binned_width(p->ks.w);
+    }
+    T3Sort sort{};
+    const bool overlap = binned && !p->timing && p->sort_st;
+    if (binned) {
+        if (M > p->perm_cap) {   // grown once; later evaluations reuse it
+            if (p->perm) cudaFree(p->perm);
+            p->perm = nullptr;
+            p->perm_cap = 0;
+            FRES_CK(cudaMalloc((void**)&p->perm, sizeof(int) * (size_t)M));
+            p->perm_cap = M;
+        }
+        sort = T3Sort{p->tcounts, p->tstart, p->tcursor, p->perm, p->twork, p->tpartial};
+        p->launches += p->ip.nbin1 * p->ip.nbin2 <= kBinScanStaged ? 3 : 5;
+    }
+    if (overlap) {
+        FRES_CK(cudaEventRecord(p->ev_sort_fork, p->st));
+        FRES_CK(cudaStreamWaitEvent(p->sort_st, p->ev_sort_fork, 0));
+        if (p->wait_tgt) FRES_CK(cudaStreamWaitEvent(p->sort_st, p->wait_tgt, 0));
+        launch_target_sort(d_targets, M, p->ip, p->ks.w, &sort, p->sort_st);
+        FRES_CK(cudaEventRecord(p->ev_sorted, p->sort_st));
+    }
     if (p->opts.recompute_nodes || !p->nodes_ready) {
         FRES_TRY(run_nodes<T>(p, nullptr, nullptr, nullptr));
         ev_record(p, "nodes_chirp_count");
@@ -633,24 +677,11 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
                 FRES_CK(cudaStreamWaitEvent(p->st, p->wait_tgt, 0));
                 p->wait_tgt = nullptr;
             }
-            T3Sort sort{};
-            const T3Sort* sp = nullptr;
-            const long long fbytes = (long long)p->nfft1 * p->nfft2 * (long long)sizeof(cx_t<T>);
-            const bool want = p->opts.t3_binning > 0 ||
-                              (p->opts.t3_binning == 0 && M >= kSortTargetsFrom &&
-                               fbytes > kBinFromGridBytes);
-            if (sizeof(T) == 4 && want && M < (1LL << 31) && interp_binned_width(p->ks.w)) {
-                if (M > p->perm_cap) {   // grown once; later evaluations reuse it
-                    if (p->perm) cudaFree(p->perm);
-                    p->perm = nullptr;
-                    p->perm_cap = 0;
-                    FRES_CK(cudaMalloc((void**)&p->perm, sizeof(int) * (size_t)M));
-                    p->perm_cap = M;
-                }
-                sort = T3Sort{p->tcounts, p->tstart, p->tcursor, p->perm, p->twork, p->tpartial};
-                sp = &sort;
+            const T3Sort* sp = binned ? &sort : nullptr;
+            if (overlap) {
+                FRES_CK(cudaStreamWaitEvent(p->st, p->ev_sorted, 0));
+            } else if (binned) {
                 launch_target_sort(d_targets, M, p->ip, p->ks.w, sp, p->st);
-                p->launches += p->ip.nbin1 * p->ip.nbin2 <= kBinScanStaged ? 3 : 5;
                 ev_record(p, "target_sort");
             }
             launch_interp_w<T>(d_targets, M, (const cx_t<T>*)p->F, p->ip, p->ks, p->cheb,
@@ -1467,6 +1498,11 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         FRES_TRY(dalloc(p, (void**)&p->tstart, sizeof(int) * nbins));
         FRES_TRY(dalloc(p, (void**)&p->tcursor, sizeof(int) * nbins));
         FRES_TRY(dalloc(p, (void**)&p->twork, 2 * sizeof(int)));
+        if (!dbl) {
+            FRES_CK(cudaStreamCreateWithFlags(&p->sort_st, cudaStreamNonBlocking));
+            FRES_CK(cudaEventCreateWithFlags(&p->ev_sort_fork, cudaEventDisableTiming));
+            FRES_CK(cudaEventCreateWithFlags(&p->ev_sorted, cudaEventDisableTiming));
+        }
         FRES_CK(cudaMemsetAsync(p->tcounts, 0, sizeof(int) * nbins, p->st));
         FRES_CK(cudaMemsetAsync(p->twork, 0, 2 * sizeof(int), p->st));
         p->ip.inv_tmax = 1.0 / tmax;
