@@ -235,7 +235,7 @@ KERNEL_SOURCES = {
 _CAP_STAR = "ncu capture of this workload (second warm-up step, every kernel)"
 _CAP_SWEEP = "ncu capture of this workload (second warm-up step)"
 _CAP_R1000 = "ncu capture of this workload at 3e7 targets (the spread does not depend on them)"
-_SHA_SPREAD, _SHA_FFT, _SHA_INTERP = "a65c6f64dd874152", "78a9e035d10ff9c2", "67ccf77c976268a1"
+_SHA_SPREAD, _SHA_FFT, _SHA_INTERP = "c22f9976781bc31e", "680f92d43c4759da", "56f3d463e8f40aaa"
 
 
 def _cap(nbytes, issue, lsu, l1, sha, note):
@@ -245,20 +245,20 @@ def _cap(nbytes, issue, lsu, l1, sha, note):
 
 
 DRAM_TRAFFIC = {
-    ("star5_F100", "t1.spread"): _cap(18210560, 0.487, 0.410, 0.708, _SHA_SPREAD, _CAP_STAR),
-    ("star5_F100", "t3.spread"): _cap(19069696, 0.483, 0.414, 0.700, _SHA_SPREAD, _CAP_STAR),
-    ("star5_F100", "t1.fft_rows"): _cap(15310848, 0.279, 0.090, 0.447, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t1.fft_cols_epilogue"): _cap(7558400, 0.236, 0.067, 0.283, _SHA_FFT,
+    ("star5_F100", "t1.spread"): _cap(18210816, 0.483, 0.405, 0.699, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t3.spread"): _cap(19069952, 0.483, 0.414, 0.698, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t1.fft_rows"): _cap(15310848, 0.270, 0.088, 0.441, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t1.fft_cols_epilogue"): _cap(7558400, 0.233, 0.067, 0.282, _SHA_FFT,
                                                  _CAP_STAR),
-    ("star5_F100", "t3.fft_rows"): _cap(6742272, 0.373, 0.132, 0.317, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t3.fft_cols"): _cap(15194624, 0.370, 0.106, 0.468, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t3.interp_epilogue"): _cap(21465600, 0.608, 0.351, 0.903, _SHA_INTERP,
+    ("star5_F100", "t3.fft_rows"): _cap(6742272, 0.356, 0.129, 0.307, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.fft_cols"): _cap(15440896, 0.363, 0.105, 0.461, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.interp_epilogue"): _cap(21466368, 0.607, 0.351, 0.903, _SHA_INTERP,
                                                _CAP_STAR),
-    ("hg24_sweep64", "spread"): _cap(23635725, 0.511, 0.433, 0.768, _SHA_SPREAD, _CAP_SWEEP),
-    ("hg24_sweep64", "fft_rows"): _cap(16903692, 0.267, 0.066, 0.224, _SHA_FFT, _CAP_SWEEP),
-    ("hg24_sweep64", "fft_cols_epilogue"): _cap(82326301, 0.741, 0.269, 0.461, _SHA_FFT,
+    ("hg24_sweep64", "spread"): _cap(23632921, 0.506, 0.431, 0.764, _SHA_SPREAD, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_rows"): _cap(16906489, 0.265, 0.065, 0.222, _SHA_FFT, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_cols_epilogue"): _cap(82485511, 0.434, 0.101, 0.460, _SHA_FFT,
                                                 _CAP_SWEEP),
-    ("randstar20_F1000", "spread"): _cap(826517793, 0.514, 0.434, 0.733, _SHA_SPREAD,
+    ("randstar20_F1000", "spread"): _cap(826018395, 0.512, 0.432, 0.729, _SHA_SPREAD,
                                          _CAP_R1000),
 }
 

@@ -400,6 +400,9 @@ typedef struct {
     int launches_per_eval;  /* kernels launched by one fresnel_eval */
     int split_tiles;        /* spreading tiles whose records are split over several work items */
     int max_tile_records;   /* node records of the fullest spreading tile */
+    int t3_binning;         /* FP32 SCATTERED plans: 1 binned interpolation, -1 direct
+                               gathers, 0 chosen per evaluation (fresnel_opts.t3_binning,
+                               after the autotuner's choice when it ran) */
 } fresnel_info;
 
 fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info);

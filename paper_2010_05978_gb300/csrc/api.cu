@@ -1960,6 +1960,7 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
     info->launches_per_eval = p->last_launches > 0 ? p->last_launches : nl;
     info->split_tiles = p->max_split;
     info->max_tile_records = p->det_tmax;
+    info->t3_binning = p->opts.t3_binning;
     return FRESNEL_OK;
 }
 

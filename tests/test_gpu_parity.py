@@ -286,6 +286,8 @@ def test_autotuned_plans_match_oracle(prec):
     x3, y3 = W.disc_targets(40000, 1.5, 12)
     t = torch.tensor(np.stack([x3, y3], 1), dtype=torch.float64, device="cuda")
     p3 = plan(fam3, 0.03, 1.0, tol, precision=prec, box=(-1.5, 1.5, -1.5, 1.5), autotune=True)
+    # FP32: the autotuner fixed the interpolation mode, which info() reports
+    assert p3.info()["t3_binning"] in ((1, -1) if prec == "fp32" else (0,))
     u3 = p3.eval(t).cpu().numpy()
     idx = np.arange(0, 40000, 97)
     assert rel_l2(u3[idx], oracle.field(fam3, 0.03, 1.0, x3[idx], y3[idx])) <= bar
