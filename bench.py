@@ -513,20 +513,30 @@ def star_arm(args, dev, local_rank, world, precision, steps, warmup, sample=None
     return res
 
 
+def live_rows(info, full):
+    """Grid rows a type-1 plan spreads and transforms: its live tile rows
+    (those holding nodes) times the tile height, else every row."""
+    lr = info.get("live_tile_rows", 0)
+    return min(full, lr * info.get("tile_y", 32)) if lr > 0 else full
+
+
 def algorithmic_bytes(info1, info3, n_nodes, precision="fp32"):
     """Minimum bytes each stage must move, per launch.  FP32 fast mode: a
     24 B node record (2 x int32 cell, 2 x f32 fraction, c64 strength) and c64
-    grids; FP64 mode: a 40 B record (f64 fractions, c128 strength) and c128."""
+    grids; FP64 mode: a 40 B record (f64 fractions, c128 strength) and c128.
+    Type 1 counts only the live rows of its spreading grid (the passes skip
+    rows that hold no nodes)."""
     rec = 24 if precision == "fp32" else 40
     c64 = 8 if precision == "fp32" else 16
     nf1, nf2 = info1["nf1"], info1["nf2"]
+    r1 = live_rows(info1, nf2)
     g3 = info3["nf1"] * info3["nf2"]
     F3 = info3["nfft1"] * info3["nfft2"]
     return {
         # t1
-        "t1.spread": n_nodes * rec + nf1 * nf2 * c64,
-        "t1.fft_rows": nf1 * nf2 * c64 + 1000 * nf2 * c64,
-        "t1.fft_cols_epilogue": 1000 * nf2 * c64 + 1000 * 1000 * c64,
+        "t1.spread": n_nodes * rec + nf1 * r1 * c64,
+        "t1.fft_rows": nf1 * r1 * c64 + 1000 * r1 * c64,
+        "t1.fft_cols_epilogue": 1000 * r1 * c64 + 1000 * 1000 * c64,
         # t3
         "t3.spread": n_nodes * rec + g3 * c64,
         "t3.fft_rows": g3 * c64 + info3["nf2"] * info3["nfft1"] * c64,
@@ -747,9 +757,10 @@ def sweep_arm(args, dev, local_rank, world, n_lambda, steps, warmup, budget_s=10
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     c64, rec = 8, 24
     nf1, nf2, n1, n2 = info["nf1"], info["nf2"], g["n1"], g["n2"]
-    ab = {"spread": info["n_nodes"] * rec + B * nf1 * nf2 * c64,
-          "fft_rows": B * (nf1 * nf2 + n1 * nf2) * c64,
-          "fft_cols_epilogue": B * (n1 * nf2 + n1 * n2) * c64}
+    rows = live_rows(info, B * nf2)   # grid rows the pruned passes spread and transform
+    ab = {"spread": info["n_nodes"] * rec + rows * nf1 * c64,
+          "fft_rows": rows * (nf1 + n1) * c64,
+          "fft_cols_epilogue": (rows * n1 + B * n1 * n2) * c64}
     res = {"metric": SWEEP_METRIC_N % B, "unit": SWEEP_UNIT, "ms_per_step": ms_per_step,
            "value": value, "plan_ms": plan_ms, "plan_plus_eval_ms": plan_ms + ms_per_step,
            "targets_per_s": value * B * in_pupil, "error": err,

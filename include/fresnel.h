@@ -403,6 +403,8 @@ typedef struct {
     int t3_binning;         /* FP32 SCATTERED plans: 1 binned interpolation, -1 direct
                                gathers, 0 chosen per evaluation (fresnel_opts.t3_binning,
                                after the autotuner's choice when it ran) */
+    int live_tile_rows;     /* spreading-tile rows holding nodes, summed over the problems
+                               (GRID plans spread and transform only these rows) */
 } fresnel_info;
 
 fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info);

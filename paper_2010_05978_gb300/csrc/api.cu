@@ -10,6 +10,7 @@
 //   spread -> FFT rows -> FFT columns (+ fused type-1 epilogue)
 //   [type 3: -> interpolation + deconvolution + post-phase/chirp]
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -87,6 +88,7 @@ struct Plan {
     int det_tmax = 0;             // records of the fullest tile
     bool col_dft = false;         // type-1 column pass as a direct DFT over the live rows
     int max_live_rows = 0;        // live tile rows of the fullest problem
+    long long live_rows_total = 0;   // live tile rows summed over the problems
     long long n_records = 0;
     int spread_blocks = 0;
     ChirpParams cp{};
@@ -1336,6 +1338,7 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
     if (prune && p->nty > kMaxTileRows)
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "spreading grid too tall");
     int max_live_rows = 0;   // live tile rows of the fullest problem
+    p->live_rows_total = 0;
     for (int b = 0; b < p->B; ++b) {
         long long nrec = 0, nsc = 0, nsplit = 0, nlive = 0;
         std::vector<char> live(p->nty, prune ? 0 : 1);
@@ -1345,6 +1348,7 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         int lr = 0;
         for (int r = 0; r < p->nty; ++r) lr += live[r] ? 1 : 0;
         max_live_rows = std::max(max_live_rows, lr);
+        p->live_rows_total += lr;
         for (int i = 0; i < p->ntiles; ++i) {
             const int c = hc[(size_t)b * p->ntiles + i];
             nrec += c;
@@ -1939,6 +1943,7 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
         for (size_t i = 1; i < p->subs.size(); ++i) {
             info->split_tiles += p->subs[i]->max_split;
             info->max_tile_records = std::max(info->max_tile_records, p->subs[i]->det_tmax);
+            info->live_tile_rows += (int)std::min<long long>(p->subs[i]->live_rows_total, INT_MAX);
         }
         return FRESNEL_OK;
     }
@@ -1961,6 +1966,7 @@ fresnel_status fresnel_get_info(fresnel_plan_t plan, fresnel_info* info) {
     info->split_tiles = p->max_split;
     info->max_tile_records = p->det_tmax;
     info->t3_binning = p->opts.t3_binning;
+    info->live_tile_rows = (int)std::min<long long>(p->live_rows_total, INT_MAX);
     return FRESNEL_OK;
 }
 

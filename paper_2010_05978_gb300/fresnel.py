@@ -67,7 +67,8 @@ class Info(ctypes.Structure):
                 ("nfft1", ctypes.c_int), ("nfft2", ctypes.c_int), ("tile_x", ctypes.c_int),
                 ("tile_y", ctypes.c_int), ("device_bytes", ctypes.c_longlong),
                 ("launches_per_eval", ctypes.c_int), ("split_tiles", ctypes.c_int),
-                ("max_tile_records", ctypes.c_int), ("t3_binning", ctypes.c_int)]
+                ("max_tile_records", ctypes.c_int), ("t3_binning", ctypes.c_int),
+                ("live_tile_rows", ctypes.c_int)]
 
 
 EXPORTS = ["fresnel_default_opts", "fresnel_plan", "fresnel_plan_many", "fresnel_eval",

@@ -78,6 +78,11 @@ def test_algorithmic_bytes_per_precision():
     assert a32["t3.interp_epilogue"] == bench.M3 * 24
     assert a64["t3.interp_epilogue"] == bench.M3 * 32
     assert set(a32) == set(a64)
+    # a pruned type-1 plan moves only its live rows (here 40 tile rows of 32)
+    a = bench.algorithmic_bytes(dict(info1, live_tile_rows=40, tile_y=32), info3, 524288)
+    assert a["t1.spread"] == 524288 * 24 + 2000 * 1280 * 8
+    assert a["t1.fft_cols_epilogue"] == (1000 * 1280 + 1000 * 1000) * 8
+    assert bench.live_rows({"live_tile_rows": 0}, 777) == 777
 
 
 def test_precision_option_is_star_only():
