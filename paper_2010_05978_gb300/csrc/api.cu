@@ -252,6 +252,7 @@ int nice_size(double target, int mult) {
 // the band edge) and designs the kernel for tol/10, leaving room for FP32
 // rounding under the requested tolerance.
 void fit_horner(int w, double beta, HornerTab* h);
+double fit_horner_d(int w, double beta, HornerTabD* h);
 
 void choose_kernel(Plan* p) {
     double tk = p->tol;
@@ -278,7 +279,12 @@ void choose_kernel(Plan* p) {
     p->ks.beta = beta;
     p->ks.betaf = (float)beta;
     p->ks.horner.deg = -1;
-    if (p->prec == FRESNEL_FP32_FAST) fit_horner(w, beta, &p->ks.horner);
+    p->ks.hornerd.deg = -1;
+    if (p->prec == FRESNEL_FP32_FAST) {
+        fit_horner(w, beta, &p->ks.horner);
+    } else if (fit_horner_d(w, beta, &p->ks.hornerd) > 0.2 * p->tol) {
+        p->ks.hornerd.deg = -1;   // the fit's floor is above this tolerance: exp/sqrt
+    }
 }
 
 // Fit, for each of the unit pieces a < ceil(w/2) of the kernel (the others
@@ -286,18 +292,20 @@ void choose_kernel(Plan* p) {
 // fractional offset): Chebyshev interpolation at deg + 1 points, converted to
 // monomials in long double and split into even and odd parts.  The degree
 // grows until the maximum error (on a fine grid) stops improving or drops
-// below 1e-9; the kernel's square-root end points set a floor near e^-beta.
-void fit_horner(int w, double beta, HornerTab* h) {
+// below `stop`; the kernel's square-root end points set a floor near
+// beta e^-beta / deg.  Returns the kept table's maximum error.
+template <typename Tab, typename R, int kMaxDeg>
+double fit_pieces(int w, double beta, int deg0, double stop, Tab* h) {
     auto psi = [&](long double z) -> long double {
         long double a = 1.0L - z * z;
         return a > 0 ? std::exp((long double)beta * (std::sqrt(a) - 1.0L)) : 0.0L;
     };
-    double prev_err = 1e300;
-    HornerTab best{};
+    double prev_err = 1e300, best_err = 1e300;
+    Tab best{};
     best.deg = -1;
-    for (int d = 4; d <= kHornerDeg; ++d) {
+    for (int d = deg0; d <= kMaxDeg; ++d) {
         const int n = d + 1;
-        HornerTab t{};
+        Tab t{};
         t.deg = d;
         double err = 0.0;
         for (int a = 0; a < (w + 1) / 2; ++a) {
@@ -326,8 +334,8 @@ void fit_horner(int w, double beta, HornerTab* h) {
                 }
             }
             for (int j = 0; j < n; ++j) {
-                if (j % 2 == 0) t.e[a][j / 2] = (float)mono[j];
-                else t.o[a][j / 2] = (float)mono[j];
+                if (j % 2 == 0) t.e[a][j / 2] = (R)mono[j];
+                else t.o[a][j / 2] = (R)mono[j];
             }
             for (int i = 0; i <= 400; ++i) {
                 long double tt = -1.0L + i / 200.0L, acc = 0.0L;
@@ -335,11 +343,23 @@ void fit_horner(int w, double beta, HornerTab* h) {
                 err = std::max(err, (double)std::fabs(acc - g(tt)));
             }
         }
-        if (err < prev_err) best = t;
-        if (err < 1e-9 || err > 0.9 * prev_err) break;
+        if (err < best_err) {
+            best = t;
+            best_err = err;
+        }
+        if (err < stop || err > 0.9 * prev_err) break;
         prev_err = err;
     }
     *h = best;
+    return best_err;
+}
+
+void fit_horner(int w, double beta, HornerTab* h) {
+    fit_pieces<HornerTab, float, kHornerDeg>(w, beta, 4, 1e-9, h);
+}
+
+double fit_horner_d(int w, double beta, HornerTabD* h) {
+    return fit_pieces<HornerTabD, double, kHornerDegD>(w, beta, 6, 1e-16, h);
 }
 
 fresnel_status validate_family(const fresnel_family& f, long long* n_bdry, long long* n_nodes,

@@ -163,7 +163,7 @@ struct ChirpParams {
     double screen_k;       // 2 pi / lambda of the problem (source screens)
 };
 
-// Piecewise-polynomial form of the spreading kernel for FP32: the value at
+// Piecewise-polynomial form of the spreading kernel: the value at
 // cell a of a node with fractional offset f is a polynomial p_a(t) in
 // t = 2 f - 1 (fitted once per plan on the Chebyshev points of each unit
 // piece).  The kernel is even, so piece w - 1 - a is piece a mirrored:
@@ -174,22 +174,41 @@ struct ChirpParams {
 // most kHornerDeg, zero-padded), so the fully unrolled Horner chains take
 // their coefficients as constant operands.  deg < 0 means "evaluate exp/sqrt
 // directly".  Passed by value, so it lives in the kernel-parameter constant
-// bank (uniform access).
+// bank (uniform access).  FP32 tables (HornerTab) go to degree 10, FP64
+// tables (HornerTabD, the FP64 mode at any tolerance) to degree 14 (the
+// fits level off at degree 9-14 for w <= 16: the end points' square roots).
 constexpr int kHornerDeg = 10;
 constexpr int kHornerEven = kHornerDeg / 2 + 1;        // t^0, t^2, ..., t^10
 constexpr int kHornerOdd = (kHornerDeg + 1) / 2;       // t^1, t^3, ..., t^9
 struct HornerTab {
     float e[(kMaxW + 1) / 2][kHornerEven];
     float o[(kMaxW + 1) / 2][kHornerOdd];
-    int deg;
+    int deg = -1;
 };
+constexpr int kHornerDegD = 14;
+constexpr int kHornerEvenD = kHornerDegD / 2 + 1;      // t^0, t^2, ..., t^14
+constexpr int kHornerOddD = (kHornerDegD + 1) / 2;     // t^1, t^3, ..., t^13
+struct HornerTabD {
+    double e[(kMaxW + 1) / 2][kHornerEvenD];
+    double o[(kMaxW + 1) / 2][kHornerOddD];
+    int deg = -1;
+};
+template <typename T> struct HornerFor { using type = HornerTab; };
+template <> struct HornerFor<double> { using type = HornerTabD; };
+template <typename T> using horner_t = typename HornerFor<T>::type;
 
 struct KernelShape {
     int w;
     double beta;
     float betaf;
     HornerTab horner;
+    HornerTabD hornerd;
 };
+template <typename T>
+inline const horner_t<T>& horner_of(const KernelShape& ks) {
+    if constexpr (sizeof(T) == 8) return ks.hornerd;
+    else return ks.horner;
+}
 
 template <int W>
 __device__ __forceinline__ void horner_eval(const HornerTab& h, float f, float* out) {
@@ -204,6 +223,21 @@ __device__ __forceinline__ void horner_eval(const HornerTab& h, float f, float* 
         for (int k = kHornerOdd - 2; k >= 0; --k) O = fmaf(O, u, h.o[a][k]);
         out[a] = fmaf(t, O, E);
         if (W - 1 - a != a) out[W - 1 - a] = fmaf(-t, O, E);
+    }
+}
+template <int W>
+__device__ __forceinline__ void horner_eval(const HornerTabD& h, double f, double* out) {
+    const double t = 2.0 * f - 1.0, u = t * t;
+#pragma unroll
+    for (int a = 0; a < (W + 1) / 2; ++a) {
+        double E = h.e[a][kHornerEvenD - 1];
+#pragma unroll
+        for (int k = kHornerEvenD - 2; k >= 0; --k) E = fma(E, u, h.e[a][k]);
+        double O = h.o[a][kHornerOddD - 1];
+#pragma unroll
+        for (int k = kHornerOddD - 2; k >= 0; --k) O = fma(O, u, h.o[a][k]);
+        out[a] = fma(t, O, E);
+        if (W - 1 - a != a) out[W - 1 - a] = fma(-t, O, E);
     }
 }
 

@@ -105,7 +105,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(256)
 k_interp(const double* __restrict__ targets, long long M, const cx_t<T>* __restrict__ F,
          InterpParams ip, T beta, const double* __restrict__ cheb, int ncheb,
-         cx_t<T>* __restrict__ out, unsigned* __restrict__ status, const HornerTab hz) {
+         cx_t<T>* __restrict__ out, unsigned* __restrict__ status, const horner_t<T> hz) {
     __shared__ T s_a[kMaxCheb];
     for (int i = threadIdx.x; i < ncheb; i += blockDim.x) s_a[i] = (T)cheb[i];
     __syncthreads();
@@ -663,7 +663,7 @@ void launch_interp_w(const double* targets, long long M, const cx_t<T>* F, const
 #define FRES_INTERP_CASE(WW)                                                                   \
     case WW:                                                                                   \
         k_interp<T, WW><<<blocks, 256, 0, st>>>(targets, M, F, ip, beta, cheb, ncheb,         \
-                                                (cx_t<T>*)out, status, ks.horner);             \
+                                                (cx_t<T>*)out, status, horner_of<T>(ks));      \
         break;
     switch (ks.w) {
         FRES_INTERP_CASE(2) FRES_INTERP_CASE(3) FRES_INTERP_CASE(4) FRES_INTERP_CASE(5)

@@ -45,15 +45,13 @@ template <> __device__ __forceinline__ double es_kernel<double>(double z, double
 }
 
 // The w kernel values of a node with fractional offset f: cell s + a sits at
-// offset (a + 1 - w/2 - f) from the node.  FP32 uses the plan's Horner
-// polynomials when present; FP64 evaluates exp/sqrt.
+// offset (a + 1 - w/2 - f) from the node.  The plan's piecewise polynomials
+// when present (FP32 and FP64 tables), else exp/sqrt.
 template <typename T, int W>
-__device__ __forceinline__ void kernel_values(T f, T beta, const HornerTab& hz, T* out) {
-    if constexpr (std::is_same<T, float>::value) {
-        if (hz.deg >= 0) {
-            horner_eval<W>(hz, f, out);
-            return;
-        }
+__device__ __forceinline__ void kernel_values(T f, T beta, const horner_t<T>& hz, T* out) {
+    if (hz.deg >= 0) {
+        horner_eval<W>(hz, f, out);
+        return;
     }
     const T half_w = (T)(0.5 * W), two_over_w = (T)(2.0 / W);
 #pragma unroll
@@ -137,7 +135,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ chunks,
          const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid, int* __restrict__ work,
          int* __restrict__ ready, int max_split, long long max_spin, unsigned* __restrict__ status,
-         int nf1, int nf2, int ntx, int ntiles, T beta, const HornerTab hz) {
+         int nf1, int nf2, int ntx, int ntiles, T beta, const horner_t<T> hz) {
     constexpr int TT = kTile * kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpreadSmem<T, W>& sm = *reinterpret_cast<SpreadSmem<T, W>*>(smem_raw);
@@ -395,7 +393,7 @@ k_spread_det(const NodeRec<T>* __restrict__ sorted, const Chunk* __restrict__ ch
              const int* __restrict__ n_meta, cx_t<T>* __restrict__ grid, int* __restrict__ work,
              unsigned long long* __restrict__ split_acc, int max_split,
              const double* __restrict__ det_part, int tmax, unsigned* __restrict__ status,
-             int nf1, int nf2, int ntx, int ntiles, T beta, const HornerTab hz) {
+             int nf1, int nf2, int ntx, int ntiles, T beta, const horner_t<T> hz) {
     constexpr int TT = kTile * kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DetSmem<T, W>& sm = *reinterpret_cast<DetSmem<T, W>*>(smem_raw);
@@ -534,7 +532,7 @@ void launch_spread_det_w(const NodeRec<T>* sorted, long long n_records, const Ch
                          const int* n_meta, int max_chunks, const int* split_tiles, int max_split,
                          unsigned long long* split_acc, double* det_part, int tmax,
                          cx_t<T>* grid, int* work, unsigned* status, int nf1, int nf2, int ntx,
-                         int ntiles, T beta, const HornerTab& hz, cudaStream_t st) {
+                         int ntiles, T beta, const horner_t<T>& hz, cudaStream_t st) {
     k_det_cmax<T><<<kDetPartials, 256, 0, st>>>(sorted, n_records, det_part);
     const size_t smem = sizeof(DetSmem<T, W>);
     cudaFuncSetAttribute(k_spread_det<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -565,7 +563,7 @@ void launch_spread_det_impl(const NodeRec<T>* sorted, long long n_records, const
     case WW:                                                                                  \
         launch_spread_det_w<T, WW>(sorted, n_records, chunks, n_meta, max_chunks, split_tiles, \
                                    max_split, split_acc, det_part, tmax, grid, work, status,  \
-                                   nf1, nf2, ntx, ntiles, beta, ks.horner, st);               \
+                                   nf1, nf2, ntx, ntiles, beta, horner_of<T>(ks), st);        \
         break;
     switch (ks.w) {
         FRES_DET_CASE(2) FRES_DET_CASE(3) FRES_DET_CASE(4) FRES_DET_CASE(5)
@@ -581,7 +579,7 @@ template <typename T, int W>
 void launch_spread_w(const NodeRec<T>* sorted, const Chunk* chunks, const int* n_meta,
                      int max_chunks, int* ready, int max_split, long long max_spin,
                      cx_t<T>* grid, int* work, unsigned* status, int nf1, int nf2, int ntx,
-                     int ntiles, T beta, const HornerTab& hz, int nblocks, cudaStream_t st) {
+                     int ntiles, T beta, const horner_t<T>& hz, int nblocks, cudaStream_t st) {
     const size_t smem = sizeof(SpreadSmem<T, W>);
     cudaFuncSetAttribute(k_spread<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -606,7 +604,7 @@ void launch_spread_impl(const NodeRec<T>* sorted, const Chunk* chunks, const int
     case WW:                                                                                  \
         launch_spread_w<T, WW>(sorted, chunks, n_meta, max_chunks, ready, max_split,         \
                                max_spin, grid, work, status, nf1, nf2, ntx, ntiles, beta,    \
-                               ks.horner, nblocks, st);                                      \
+                               horner_of<T>(ks), nblocks, st);                               \
         break;
     switch (ks.w) {
         FRES_SPREAD_CASE(2) FRES_SPREAD_CASE(3) FRES_SPREAD_CASE(4) FRES_SPREAD_CASE(5)
