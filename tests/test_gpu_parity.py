@@ -367,14 +367,18 @@ def test_t3_fp32_kernel_widths(tol, w):
     assert rel_l2(u, ref) <= max(tol, 1e-6)
 
 
-def test_eval_host_async_pinned_back_to_back():
+@pytest.mark.parametrize("binning", [0, 1])
+def test_eval_host_async_pinned_back_to_back(binning):
     """Host-buffer evaluations with sync_status off return once queued: two
     calls with different pinned target sets, then one check (stream
     synchronisation).  The second call's target copy must not overwrite the
-    staged targets while the first evaluation still reads them."""
+    staged targets while the first evaluation still reads them.  With the
+    binned interpolation (binning 1) the target sort runs on its own stream:
+    it must wait for its evaluation's target copy, and the second sort must
+    not overwrite the permutation the first interpolation still reads."""
     fam = [W.fourier_family(W.STAR_PARAMS, 32, 16, 48)]
     p = plan(fam, 0.05, 1.0, 1e-6, precision="fp32", box=(-1.5, 1.5, -1.5, 1.5),
-             sync_status=False)
+             sync_status=False, t3_binning=binning)
     xa, ya = W.disc_targets(60000, 1.5, 21)
     xb, yb = W.disc_targets(60000, 1.5, 22)
     ha = torch.tensor(np.stack([xa, ya], 1), dtype=torch.float64).pin_memory()
