@@ -300,6 +300,15 @@ double fit_pieces(int w, double beta, int deg0, double stop, Tab* h) {
         long double a = 1.0L - z * z;
         return a > 0 ? std::exp((long double)beta * (std::sqrt(a) - 1.0L)) : 0.0L;
     };
+    // the kernel on each piece's error grid, once for every degree tried
+    // (long double is software quad precision on some hosts)
+    constexpr int kGrid = 400;
+    std::vector<long double> gv((size_t)((w + 1) / 2) * (kGrid + 1));
+    for (int a = 0; a < (w + 1) / 2; ++a)
+        for (int i = 0; i <= kGrid; ++i) {
+            const long double f = 0.5L * (-1.0L + i / (0.5L * kGrid) + 1.0L);
+            gv[(size_t)a * (kGrid + 1) + i] = psi(((long double)a + 1.0L - 0.5L * w - f) * 2.0L / w);
+        }
     double prev_err = 1e300, best_err = 1e300;
     Tab best{};
     best.deg = -1;
@@ -337,10 +346,10 @@ double fit_pieces(int w, double beta, int deg0, double stop, Tab* h) {
                 if (j % 2 == 0) t.e[a][j / 2] = (R)mono[j];
                 else t.o[a][j / 2] = (R)mono[j];
             }
-            for (int i = 0; i <= 400; ++i) {
-                long double tt = -1.0L + i / 200.0L, acc = 0.0L;
+            for (int i = 0; i <= kGrid; ++i) {
+                long double tt = -1.0L + i / (0.5L * kGrid), acc = 0.0L;
                 for (int j = n - 1; j >= 0; --j) acc = acc * tt + mono[j];
-                err = std::max(err, (double)std::fabs(acc - g(tt)));
+                err = std::max(err, (double)std::fabs(acc - gv[(size_t)a * (kGrid + 1) + i]));
             }
         }
         if (err < best_err) {
