@@ -19,7 +19,7 @@
 // term is ~2^-22 of the product); the Xi Wi product uses the instruction's
 // negate-A flag.
 //
-// One CTA (8 warps, two per SM) per (problem, 128 columns, 128 outputs).
+// One CTA (8 warps, two per SM) per (problem, 128 columns, 16 chunks of outputs).
 // The input block is staged once in shared memory (no-swizzle K-major layout
 // of the MMA descriptors: 8-row x 16-byte core matrices); the twiddle blocks
 // of successive 32-output chunks and their accumulators are double-buffered,
@@ -40,7 +40,7 @@ constexpr int kTcK = 2 * kTcR;       // real K: [Xr | Xi] against [Wr | Wi]
 constexpr int kTcThreads = 288;     // 8 staging / epilogue warps and an MMA-issuing warp
 constexpr int kTcWork = 256;        // threads of the staging / epilogue warps
 constexpr int kTcCols = 4 * kTcN;    // TMEM: 2 buffers x (Re, Im) x kTcN columns
-constexpr int kTcChunksPerCta = 4;   // output chunks of one CTA
+constexpr int kTcChunksPerCta = 16;  // output chunks of one CTA (512 outputs: the whole column)
 constexpr long long kTcMaxPolls = 1LL << 24;   // ~1 s of 64 ns back-offs
 
 struct TcSmem {
