@@ -4,7 +4,10 @@
 // the column transform of the NUFFT of Sec. 3.3 reduces to a dense complex
 // product over those R = 32 live rows (see k_col_dft in k_fft.cu):
 //   out[kp][c] = sum_{r live} w_n^{k r} in[r][c],   k the natural index of slot kp,
-// then the output epilogue (deconvolution, target chirp, Babinet).
+// then the output epilogue out[kp][c] ax[c] ay[kp] (deconvolution, target
+// chirp) and Babinet.  The product is linear, so the column factor ax[c]
+// scales the staged input block and the output factor ay[kp] the staged
+// twiddles: the epilogue is left with Babinet and the store.
 //
 // It runs transposed, out^T = in^T W^T, so that a tensor-memory lane is a
 // column c and an accumulator column an output kp: in the epilogue the 32
@@ -134,15 +137,17 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
 }
 
 // Twiddle chunk starting at output slot kp0 into buffer q: W(m, j) = Wr,
-// W(m, kTcR + j) = Wi for output kp0 + m and live row row0 + j (zero past the
-// kept outputs).  Thread t: output m = t % 32, rows 4 (t / 32) .. + 3.
+// W(m, kTcR + j) = Wi for output kp0 + m and live row row0 + j, each times
+// the output's epilogue factor ay[kp0 + m] (zero past the kept outputs).  Thread t: output m = t % 32, rows 4 (t / 32) .. + 3.
 __device__ __forceinline__ void stage_twiddles(TcSmem& sm, int q, int kp0, int len, int n,
                                                unsigned nmask, int row0,
-                                               const float2* __restrict__ tw) {
+                                               const float2* __restrict__ tw,
+                                               const float2* __restrict__ ay) {
     const int m = threadIdx.x & (kTcN - 1), j0 = (threadIdx.x / kTcN) * 4;
     const int kp = kp0 + m;
     unsigned kn = 0;
     if (kp < len) kn = kp >= len / 2 ? kp - len / 2 : kp - len / 2 + n;
+    const float2 yv = (ay && kp < len) ? __ldg(&ay[kp]) : make_float2(1.0f, 0.0f);
     {
         const int j = j0;
         float wr[4], wi[4];
@@ -153,8 +158,8 @@ __device__ __forceinline__ void stage_twiddles(TcSmem& sm, int q, int kp0, int l
                 const unsigned kr = kn * (unsigned)(row0 + j + u);   // < 2^26
                 w = __ldg(&tw[nmask ? (kr & nmask) : kr % (unsigned)n]);
             }
-            wr[u] = w.x;
-            wi[u] = w.y;
+            wr[u] = w.x * yv.x - w.y * yv.y;
+            wi[u] = w.x * yv.y + w.y * yv.x;
         }
         float4 h, l;
         split4(wr, h, l);
@@ -252,7 +257,6 @@ k_col_dft_tc(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status
     // and outputs 16 (w / 4) .. + 15 of each chunk
     const int col = c0 + 32 * (warp & 3) + lane;
     const int mh = 16 * (warp >> 2);
-    const float2 xv = (ax && col < a.ncols) ? __ldg(&ax[col]) : make_float2(1.0f, 0.0f);
     const unsigned tlane = (unsigned)(32 * (warp & 3)) << 16;
     if (nt == 0 && tid < kTcWork) {   // no nodes in this problem: u^ap = 0 (u^oc = 1)
         if (col < a.ncols)
@@ -268,14 +272,17 @@ k_col_dft_tc(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status
         if (tid < kTcWork) {
             const float2* in = (const float2*)a.in + (long long)b * a.in_bstride;
             const int c = tid & (kTcM - 1), j0 = (tid >> 7) * (kTcR / 2);
+            // the column factor ax[c] of the epilogue, folded into the input
+            const float2 xs = (ax && c0 + c < a.ncols) ? __ldg(&ax[c0 + c])
+                                                       : make_float2(1.0f, 0.0f);
             for (int j = j0; j < j0 + kTcR / 2; j += 4) {
                 float xr[4], xi[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float2 x = make_float2(0.0f, 0.0f);
                     if (c0 + c < a.ncols) x = in[(long long)(row0 + j + u) * a.ncols + c0 + c];
-                    xr[u] = x.x;
-                    xi[u] = x.y;
+                    xr[u] = x.x * xs.x - x.y * xs.y;
+                    xi[u] = x.x * xs.y + x.y * xs.x;
                 }
                 float4 h, l;
                 split4(xr, h, l);
@@ -288,7 +295,8 @@ k_col_dft_tc(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status
         }
         for (int ch = ch0; ch <= ch1; ++ch) {
             const int q = (ch - ch0) & 1;
-            if (ch < ch1 && tid < kTcWork) stage_twiddles(sm, q, ch * kTcN, len, n, nmask, row0, tw);
+            if (ch < ch1 && tid < kTcWork)
+                stage_twiddles(sm, q, ch * kTcN, len, n, nmask, row0, tw, ay);
             // staged operands visible to the tensor cores; the accumulator reads of
             // the previous epilogue done; every thread's wait succeeded so far
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -315,23 +323,15 @@ k_col_dft_tc(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status
                 tmem_ld16(tb + kTcN, im);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (col < a.ncols) {
+                    // the epilogue's factors are in the operands: only Babinet remains
+                    const bool bab = ay && a.occulter;
+                    float2* o = out + (long long)kp0 * a.ncols + col;
+                    const int jn = min(16, len - kp0);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int kp = kp0 + j;
-                        if (kp >= len) continue;
-                        float vr = re[j], vi = im[j];
-                        if (ay) {
-                            const float2 yv = __ldg(&ay[kp]);
-                            const float tr = vr * xv.x - vi * xv.y;
-                            const float ti = vr * xv.y + vi * xv.x;
-                            vr = tr * yv.x - ti * yv.y;
-                            vi = tr * yv.y + ti * yv.x;
-                            if (a.occulter) {
-                                vr = 1.0f - vr;
-                                vi = -vi;
-                            }
-                        }
-                        out[(long long)kp * a.ncols + col] = make_float2(vr, vi);
+                        if (j < jn)
+                            o[(long long)j * a.ncols] =
+                                bab ? make_float2(1.0f - re[j], -im[j]) : make_float2(re[j], im[j]);
                     }
                 }
             }
