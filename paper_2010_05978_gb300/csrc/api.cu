@@ -89,6 +89,8 @@ struct Plan {
     bool col_dft = false;         // type-1 column pass as a direct DFT over the live rows
     int max_live_rows = 0;        // live tile rows of the fullest problem
     long long live_rows_total = 0;   // live tile rows summed over the problems
+    int* row_list = nullptr;      // type 1, pruned: the spreading-grid rows of live tile rows
+    int n_row_list = 0;
     long long n_records = 0;
     int spread_blocks = 0;
     ChirpParams cp{};
@@ -648,6 +650,8 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ra.live = p->layout.live;
         ra.batch_rows = p->nf2;
         ra.nty = p->nty;
+        ra.row_list = p->row_list;
+        ra.nlist = p->n_row_list;
         run_rows<T>(p, ra);
         ev_record(p, "fft_rows");
         ColPassArgs ca{};
@@ -1368,6 +1372,7 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         return fres_fail(FRESNEL_ERR_UNSUPPORTED, "spreading grid too tall");
     int max_live_rows = 0;   // live tile rows of the fullest problem
     p->live_rows_total = 0;
+    std::vector<int> rows;   // the row pass's work list (pruned plans)
     for (int b = 0; b < p->B; ++b) {
         long long nrec = 0, nsc = 0, nsplit = 0, nlive = 0;
         std::vector<char> live(p->nty, prune ? 0 : 1);
@@ -1378,6 +1383,10 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         for (int r = 0; r < p->nty; ++r) lr += live[r] ? 1 : 0;
         max_live_rows = std::max(max_live_rows, lr);
         p->live_rows_total += lr;
+        if (prune)
+            for (int r = 0; r < p->nty; ++r)
+                if (live[r])
+                    for (int i = 0; i < kTile; ++i) rows.push_back(b * p->nf2 + r * kTile + i);
         for (int i = 0; i < p->ntiles; ++i) {
             const int c = hc[(size_t)b * p->ntiles + i];
             nrec += c;
@@ -1403,6 +1412,12 @@ fresnel_status build_plan(Plan* p, const fresnel_problem* problems) {
         p->max_live_rows = max_live_rows;
         const long long R = (long long)kTile * max_live_rows;
         p->col_dft = prune && R > 0 && R <= kDftMaxRows && R * p->n2 <= 24LL * p->nf2;
+    }
+    if (prune && !rows.empty() && (long long)p->nf2 * p->B < (1LL << 31)) {
+        FRES_TRY(dalloc(p, (void**)&p->row_list, sizeof(int) * rows.size()));
+        FRES_CK(cudaMemcpyAsync(p->row_list, rows.data(), sizeof(int) * rows.size(),
+                                cudaMemcpyHostToDevice, p->st));
+        p->n_row_list = (int)rows.size();
     }
     p->n_records = rec_off[p->B];
     p->max_chunks = pl_off[p->B];

@@ -396,6 +396,10 @@ struct RowPassArgs {
     // are skipped: neither read nor written.  NULL: every row is live.
     const int* live;
     int batch_rows, nty;
+    // when not NULL: the nlist rows to transform (ascending), instead of
+    // walking every row and skipping dead ones by their live flag
+    const int* row_list;
+    int nlist;
 };
 struct ColPassArgs {
     const void* in; void* out;

@@ -270,14 +270,16 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
     const int n = fp.n;
     const C* tw = (const C*)a.twiddle;
     const T* dcol = (const T*)a.deconv_col;
-    // rows of dead tile rows are zero in and out of the transform: skipped
+    // rows of dead tile rows are zero in and out of the transform: skipped,
+    // through the plan's list of live rows when it has one, else by the rows'
+    // live flags
     auto next_live = [&](int r) {
         if (a.live)
             while (r < a.nrows && !a.live[(r / a.batch_rows) * a.nty + (r % a.batch_rows) / kTile])
                 r += gridDim.x;
         return r;
     };
-    for (int row = next_live(blockIdx.x); row < a.nrows; row = next_live(row + gridDim.x)) {
+    auto transform = [&](int row) {
         const C* in = (const C*)a.in + (long long)row * a.in_stride;
         C* out = (C*)a.out + (long long)row * a.out_stride;
         const T rowf = a.deconv_row ? ((const T*)a.deconv_row)[row] : (T)1;
@@ -293,6 +295,12 @@ k_fft_rows(FftPlan fp, RowPassArgs a) {
             if (kp >= 0) out[kp] = v;
         };
         fft_fused<T, 1>(S, S2, fp, tw, load, store);
+    };
+    if (a.row_list) {
+        for (int i = blockIdx.x; i < a.nlist; i += gridDim.x) transform(a.row_list[i]);
+    } else {
+        for (int row = next_live(blockIdx.x); row < a.nrows; row = next_live(row + gridDim.x))
+            transform(row);
     }
 }
 
@@ -471,7 +479,8 @@ void launch_fft_rows(const FftPlan& fp, const RowPassArgs& a, cudaStream_t st) {
     // plan gets n/16 threads, all busy in its radix-16 stages, and more rows
     // resident per SM
     const int threads = threads_for(fp.n, fp.radix[0] > emax<T>() ? fp.radix[0] : emax<T>());
-    int blocks = a.nrows < 152 * 16 ? a.nrows : 152 * 16;
+    const int nwork = a.row_list ? a.nlist : a.nrows;
+    int blocks = nwork < 152 * 16 ? nwork : 152 * 16;
     if (blocks < 1) blocks = 1;
     cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fft_rows<T><<<blocks, threads, smem, st>>>(fp, a);
