@@ -235,7 +235,7 @@ KERNEL_SOURCES = {
 _CAP_STAR = "ncu capture of this workload (second warm-up step, every kernel)"
 _CAP_SWEEP = "ncu capture of this workload (second warm-up step)"
 _CAP_R1000 = "ncu capture of this workload at 3e7 targets (the spread does not depend on them)"
-_SHA_SPREAD, _SHA_FFT, _SHA_INTERP = "232d6f932ebd0466", "514621cb20fefd3b", "af1594ab9835d0bd"
+_SHA_SPREAD, _SHA_FFT, _SHA_INTERP = "a7ee95f12a0a079e", "95d243dbbdbe23a6", "8f3e78fb7ced9a1b"
 
 
 def _cap(nbytes, issue, lsu, l1, sha, note):
@@ -245,20 +245,20 @@ def _cap(nbytes, issue, lsu, l1, sha, note):
 
 
 DRAM_TRAFFIC = {
-    ("star5_F100", "t1.spread"): _cap(18209792, 0.486, 0.406, 0.701, _SHA_SPREAD, _CAP_STAR),
-    ("star5_F100", "t3.spread"): _cap(19070208, 0.485, 0.415, 0.700, _SHA_SPREAD, _CAP_STAR),
-    ("star5_F100", "t1.fft_rows"): _cap(15310592, 0.280, 0.089, 0.444, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t1.fft_cols_epilogue"): _cap(7558144, 0.240, 0.069, 0.291, _SHA_FFT,
+    ("star5_F100", "t1.spread"): _cap(18210048, 0.488, 0.409, 0.706, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t3.spread"): _cap(19070208, 0.484, 0.413, 0.698, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t1.fft_rows"): _cap(15312896, 0.293, 0.097, 0.484, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t1.fft_cols_epilogue"): _cap(7558656, 0.240, 0.066, 0.277, _SHA_FFT,
                                                  _CAP_STAR),
-    ("star5_F100", "t3.fft_rows"): _cap(6742016, 0.364, 0.133, 0.319, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t3.fft_cols"): _cap(15359232, 0.360, 0.106, 0.469, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t3.interp_epilogue"): _cap(21465088, 0.608, 0.351, 0.904, _SHA_INTERP,
+    ("star5_F100", "t3.fft_rows"): _cap(6747904, 0.353, 0.130, 0.315, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.fft_cols"): _cap(15227392, 0.363, 0.105, 0.460, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.interp_epilogue"): _cap(21466880, 0.605, 0.351, 0.905, _SHA_INTERP,
                                                _CAP_STAR),
-    ("hg24_sweep64", "spread"): _cap(23636985, 0.509, 0.431, 0.763, _SHA_SPREAD, _CAP_SWEEP),
-    ("hg24_sweep64", "fft_rows"): _cap(16911347, 0.261, 0.066, 0.224, _SHA_FFT, _CAP_SWEEP),
-    ("hg24_sweep64", "fft_cols_epilogue"): _cap(82067965, 0.434, 0.102, 0.466, _SHA_FFT,
+    ("hg24_sweep64", "spread"): _cap(23629574, 0.509, 0.429, 0.760, _SHA_SPREAD, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_rows"): _cap(16897017, 0.296, 0.109, 0.441, _SHA_FFT, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_cols_epilogue"): _cap(81520135, 0.396, 0.079, 0.632, _SHA_FFT,
                                                 _CAP_SWEEP),
-    ("randstar20_F1000", "spread"): _cap(826224277, 0.514, 0.434, 0.733, _SHA_SPREAD,
+    ("randstar20_F1000", "spread"): _cap(826163568, 0.514, 0.434, 0.733, _SHA_SPREAD,
                                          _CAP_R1000),
 }
 
