@@ -673,10 +673,12 @@ fresnel_status eval_impl(Plan* p, const double* d_targets, long long M, void* d_
         ca.nty = p->nty;
         if (p->col_dft) {
             ca.twiddle = p->d2.tw;
-            // FP32: the product on the tensor cores (split-TF32 operands);
-            // FP64 (no FP64 tensor path worth taking here): FMA loop
+            // one live tile row: FP32 on the tensor cores (split-TF32
+            // operands), FP64 as a pruned FFT; several: the direct FMA sum
             if (sizeof(T) == 4 && col_dft_tc_supported(ca, kTile * p->max_live_rows))
                 launch_col_dft_tc(ca, p->nf2, p->status, p->st);
+            else if (sizeof(T) == 8 && col_pfft_supported(p->nf2, kTile * p->max_live_rows))
+                launch_col_pfft_d(ca, p->nf2, p->status, p->st);
             else
                 launch_col_dft<T>(ca, p->nf2, p->status, p->st);
             p->launches++;

@@ -456,6 +456,11 @@ void launch_col_dft(const ColPassArgs& a, int n, unsigned* status, cudaStream_t 
 // problems have one live tile row (live_rows = 32)
 bool col_dft_tc_supported(const ColPassArgs& a, int live_rows);
 void launch_col_dft_tc(const ColPassArgs& a, int n, unsigned* status, cudaStream_t st);
+// The same column pass for one live tile row (live_rows = 32) in FP64 as a
+// pruned FFT: per output residue b modulo n / 32, a 32-point DFT of the live
+// rows twiddled by w_n^{b j} (n a multiple of 32, at most 32768)
+bool col_pfft_supported(int n, int live_rows);
+void launch_col_pfft_d(const ColPassArgs& a, int n, unsigned* status, cudaStream_t st);
 bool fft_supported(int n, int is_double, int* max_cols);
 // Split of a length beyond one pass into fa * fb (both single-pass), or false.
 bool fft_split(int n, int is_double, int* fa, int* fb);

@@ -670,6 +670,133 @@ k_col_dft(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status) {
     }
 }
 
+// In-register 32-point DFT, y_t = sum_q u_q e^{-2 pi i q t / 32}, in place:
+// q = 4 m + q2, t = t1 + 8 t2 (Cooley-Tukey): 8-point DFTs over m, twiddles
+// w_32^{q2 t1}, then 4-point DFTs over q2.
+template <typename T>
+__device__ __forceinline__ void dft32(cx_t<T>* y) {
+    using C = cx_t<T>;
+    using O = Ops<T>;
+    // cos (2 pi j / 32), j = 0..8; sin (2 pi j / 32) = cos (2 pi (8 - j) / 32)
+    const T c[9] = {(T)1, (T)0.98078528040323044912618223613424,
+                    (T)0.92387953251128675612818318939679,
+                    (T)0.83146961230254523707878837761791,
+                    (T)0.70710678118654752440084436210485,
+                    (T)0.55557023301960222474283081394853,
+                    (T)0.38268343236508977172845998403040,
+                    (T)0.19509032201612826784828486847702, (T)0};
+    C A[4][8];
+#pragma unroll
+    for (int q2 = 0; q2 < 4; ++q2) {
+        C v[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = y[4 * m + q2];
+        Dft<T, 8>::run(v, A[q2]);
+#pragma unroll
+        for (int t1 = 1; t1 < 8; ++t1) {
+            const int j = q2 * t1;   // < 32: w_32^j = (cos, -sin) of 2 pi j / 32
+            if (j == 0) continue;
+            const int jq = j & 7, quad = j >> 3;   // j = 8 quad + jq
+            // (cos, sin) of 2 pi j / 32 from the first quadrant
+            T cs = c[jq], sn = c[8 - jq];
+            if (quad == 1) { const T t = cs; cs = -sn; sn = t; }
+            else if (quad == 2) { cs = -cs; sn = -sn; }
+            else if (quad == 3) { const T t = cs; cs = sn; sn = -t; }
+            A[q2][t1] = O::mul(A[q2][t1], O::mk(cs, -sn));
+        }
+    }
+#pragma unroll
+    for (int t1 = 0; t1 < 8; ++t1) {
+        C v[4] = {A[0][t1], A[1][t1], A[2][t1], A[3][t1]}, d[4];
+        Dft<T, 4>::run(v, d);
+#pragma unroll
+        for (int t2 = 0; t2 < 4; ++t2) y[t1 + 8 * t2] = d[t2];
+    }
+}
+
+// Type-1 column pass over one live tile row by a pruned FFT.  A problem
+// whose nodes occupy the 32 grid rows row0 .. row0 + 31 has, for the
+// natural output index k = P a + b (P = n / 32, a < 32, b < P),
+//   sum_j w_n^{k (row0 + j)} x_j = w_n^{k row0} sum_j w_32^{a j} (w_n^{b j} x_j):
+// a 32-point DFT per b of the inputs twiddled by w_n^{b j}, about 30
+// operations per output instead of the direct sum's 32 multiply-adds, then
+// the epilogue (ax[c] folded into the staged inputs, ay[k] and Babinet).
+// A warp takes 32 adjacent columns and one b; the block's 8 warps (8 b)
+// share the staged 32 x 32 input block.  Stores: each output row segment of
+// a warp is 32 adjacent columns.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_col_pfft(ColPassArgs a, int n, unsigned nmask, unsigned* __restrict__ status) {
+    using C = cx_t<T>;
+    using O = Ops<T>;
+    __shared__ C xs[kTile][kTile + 1];
+    __shared__ int s_nt, s_row0;
+    const int pb = blockIdx.z, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = blockIdx.x * kTile, col = c0 + lane;
+    const int P = n / kTile;
+    const int bb = blockIdx.y * 8 + warp;   // this warp's b
+    const int len = a.out_len;
+    if (tid == 0) {
+        s_nt = 0;
+        s_row0 = 0;
+    }
+    __syncthreads();
+    for (int t = tid; t < a.nty; t += blockDim.x)
+        if (a.live[(long long)pb * a.nty + t]) {
+            atomicAdd(&s_nt, 1);
+            s_row0 = t * kTile;
+        }
+    __syncthreads();
+    const int nt = s_nt, row0 = s_row0;
+    const C* in = (const C*)a.in + (long long)pb * a.in_bstride;
+    C* out = (C*)a.out + (long long)pb * a.out_bstride;
+    const C* tw = (const C*)a.twiddle;
+    const C* ax = a.ax ? (const C*)a.ax + (long long)pb * a.ncols : nullptr;
+    const C* ay = a.ax ? (const C*)a.ay + (long long)pb * len : nullptr;
+    const bool bab = ay && a.occulter;
+    if (nt != 1) {   // no nodes: u^ap = 0 (u^oc = 1); several live tile rows: flagged
+        if (nt > 1 && tid == 0) atomicOr(status, kStatusOverflow);
+        if (nt == 0 && bb < P && col < a.ncols)
+            for (int aa = 0; aa < kTile; ++aa) {
+                const int kp = out_slot(P * aa + bb, len, n);
+                if (kp >= 0) out[(long long)kp * a.ncols + col] = O::mk(bab ? (T)1 : (T)0, 0);
+            }
+        return;
+    }
+    for (int e = tid; e < kTile * kTile; e += blockDim.x) {
+        const int r = e / kTile, cc = e % kTile, cg = c0 + cc;
+        C x = O::mk(0, 0);
+        if (cg < a.ncols) {
+            x = in[(long long)(row0 + r) * a.ncols + cg];
+            if (ax) x = O::mul(x, ax[cg]);
+        }
+        xs[r][cc] = x;
+    }
+    __syncthreads();
+    if (bb >= P || col >= a.ncols) return;
+    C y[kTile];
+#pragma unroll
+    for (int j = 0; j < kTile; ++j) {
+        const C x = xs[j][lane];
+        y[j] = j == 0 ? x : O::mul(x, __ldg(&tw[bb * j]));   // bb j < n
+    }
+    dft32<T>(y);
+#pragma unroll
+    for (int aa = 0; aa < kTile; ++aa) {
+        const int k = P * aa + bb;
+        const int kp = out_slot(k, len, n);
+        if (kp >= 0) {
+            const unsigned kr = (unsigned)k * (unsigned)row0;   // < n^2 <= 2^30
+            C v = O::mul(y[aa], __ldg(&tw[nmask ? (kr & nmask) : kr % (unsigned)n]));
+            if (ay) {
+                v = O::mul(v, __ldg(&ay[kp]));
+                if (a.occulter) v = O::mk((T)1 - v.x, -v.y);
+            }
+            out[(long long)kp * a.ncols + col] = v;
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -683,5 +810,16 @@ void launch_col_dft(const ColPassArgs& a, int n, unsigned* status, cudaStream_t 
 }
 template void launch_col_dft<float>(const ColPassArgs&, int, unsigned*, cudaStream_t);
 template void launch_col_dft<double>(const ColPassArgs&, int, unsigned*, cudaStream_t);
+
+bool col_pfft_supported(int n, int live_rows) {
+    return live_rows == kTile && n % kTile == 0 && n <= 32768;
+}
+
+void launch_col_pfft_d(const ColPassArgs& a, int n, unsigned* status, cudaStream_t st) {
+    const int P = n / kTile;
+    const dim3 grid((a.ncols + kTile - 1) / kTile, (P + 7) / 8, a.batch > 1 ? a.batch : 1);
+    const unsigned nmask = (n & (n - 1)) == 0 ? (unsigned)(n - 1) : 0u;
+    k_col_pfft<double><<<grid, 256, 0, st>>>(a, n, nmask, status);
+}
 
 }  // namespace fres
