@@ -235,7 +235,7 @@ KERNEL_SOURCES = {
 _CAP_STAR = "ncu capture of this workload (second warm-up step, every kernel)"
 _CAP_SWEEP = "ncu capture of this workload (second warm-up step)"
 _CAP_R1000 = "ncu capture of this workload at 3e7 targets (the spread does not depend on them)"
-_SHA_SPREAD, _SHA_FFT, _SHA_INTERP = "a7ee95f12a0a079e", "95d243dbbdbe23a6", "8f3e78fb7ced9a1b"
+_SHA_SPREAD, _SHA_FFT, _SHA_INTERP = "96e6910da872462a", "6c767b5c00f7c5ff", "6d7b1b741a45e8d0"
 
 
 def _cap(nbytes, issue, lsu, l1, sha, note):
@@ -245,20 +245,20 @@ def _cap(nbytes, issue, lsu, l1, sha, note):
 
 
 DRAM_TRAFFIC = {
-    ("star5_F100", "t1.spread"): _cap(18210048, 0.488, 0.409, 0.706, _SHA_SPREAD, _CAP_STAR),
-    ("star5_F100", "t3.spread"): _cap(19070208, 0.484, 0.413, 0.698, _SHA_SPREAD, _CAP_STAR),
-    ("star5_F100", "t1.fft_rows"): _cap(15312896, 0.293, 0.097, 0.484, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t1.fft_cols_epilogue"): _cap(7558656, 0.240, 0.066, 0.277, _SHA_FFT,
+    ("star5_F100", "t1.spread"): _cap(18212608, 0.487, 0.408, 0.704, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t3.spread"): _cap(19070208, 0.483, 0.413, 0.698, _SHA_SPREAD, _CAP_STAR),
+    ("star5_F100", "t1.fft_rows"): _cap(15313152, 0.273, 0.099, 0.495, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t1.fft_cols_epilogue"): _cap(7558144, 0.230, 0.063, 0.266, _SHA_FFT,
                                                  _CAP_STAR),
-    ("star5_F100", "t3.fft_rows"): _cap(6747904, 0.353, 0.130, 0.315, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t3.fft_cols"): _cap(15227392, 0.363, 0.105, 0.460, _SHA_FFT, _CAP_STAR),
-    ("star5_F100", "t3.interp_epilogue"): _cap(21466880, 0.605, 0.351, 0.905, _SHA_INTERP,
+    ("star5_F100", "t3.fft_rows"): _cap(6747392, 0.350, 0.126, 0.304, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.fft_cols"): _cap(15152384, 0.361, 0.103, 0.455, _SHA_FFT, _CAP_STAR),
+    ("star5_F100", "t3.interp_epilogue"): _cap(21465344, 0.608, 0.350, 0.902, _SHA_INTERP,
                                                _CAP_STAR),
-    ("hg24_sweep64", "spread"): _cap(23629574, 0.509, 0.429, 0.760, _SHA_SPREAD, _CAP_SWEEP),
-    ("hg24_sweep64", "fft_rows"): _cap(16897017, 0.296, 0.109, 0.441, _SHA_FFT, _CAP_SWEEP),
-    ("hg24_sweep64", "fft_cols_epilogue"): _cap(81520135, 0.396, 0.079, 0.632, _SHA_FFT,
+    ("hg24_sweep64", "spread"): _cap(23639579, 0.508, 0.430, 0.761, _SHA_SPREAD, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_rows"): _cap(16898826, 0.308, 0.104, 0.420, _SHA_FFT, _CAP_SWEEP),
+    ("hg24_sweep64", "fft_cols_epilogue"): _cap(81341417, 0.393, 0.078, 0.627, _SHA_FFT,
                                                 _CAP_SWEEP),
-    ("randstar20_F1000", "spread"): _cap(826163568, 0.514, 0.434, 0.733, _SHA_SPREAD,
+    ("randstar20_F1000", "spread"): _cap(826690109, 0.511, 0.431, 0.728, _SHA_SPREAD,
                                          _CAP_R1000),
 }
 
