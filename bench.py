@@ -805,6 +805,27 @@ def sweep_arm(args, dev, local_rank, world, n_lambda, steps, warmup, budget_s=10
     res["nodes_cached"] = {"ms_per_step": c_per, "value": c_value, "unit": SWEEP_UNIT,
                            "launches_per_step": q.info()["launches_per_eval"]}
     q.close()
+    # the same sweep at the paper's precision: FP64 throughout at tol 1e-12
+    # (bar 1e-10), nodes rebuilt every step
+    d = BatchPlan(cfg["problems"], 1e-12, precision="fp64", grid=g, output="occulter",
+                  recompute_nodes=True, sync_status=False)
+    out64 = torch.empty((B, g["n2"], g["n1"]), dtype=torch.complex128, device=dev)
+    for _ in range(3):
+        d.eval(out=out64)
+    torch.cuda.synchronize()
+    d_ms = time_steps(lambda: d.eval(out=out64), stream, max(3, min(steps, 10)), flush)
+    d.check()
+    d_per, d_value = aggregate_ranks(sum(d_ms), len(d_ms), 1.0, world, dev)
+    e64 = None
+    if refs is not None:
+        us64 = np.concatenate([out64[b].reshape(-1)[torch.as_tensor(idx, device=dev)].cpu().numpy()
+                               for b, idx, _ in refs])
+        e64 = rel_error(us64, ref, 1e-10, occulter=True)
+    res["fp64_tol_1e-12"] = {"ms_per_step": d_per, "value": d_value, "unit": SWEEP_UNIT,
+                             "error": e64, "kernel": {"w": d.info()["w"],
+                                                      "sigma": d.info()["sigma"]}}
+    d.close()
+    del out64
     return res
 
 
