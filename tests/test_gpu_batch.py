@@ -209,3 +209,26 @@ def test_direct_column_dft_matches_fft_path(prec):
     v = Plan(q["families"], q["lam"], q["z"], tol, precision=prec, grid=g, output="occulter",
              fft_split_above=256).eval().cpu().numpy()
     assert rel_l2(1.0 - u, 1.0 - v) <= (1e-12 if prec == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("n", [512, 480])
+def test_one_live_row_fp64_pruned_fft(n):
+    """FP64 plan whose nodes occupy one tile row: the column pass is the
+    pruned FFT (32-point DFTs of the twiddled live rows), for a power-of-two
+    column length (n = 512: 1024) and one that is not (n = 480: 960); it
+    equals the unpruned four-step FFT path and the oracle's direct sum."""
+    from paper_2010_05978_gb300 import Plan
+    cfg = W.starshade_sweep(n_lambda=3, n=n)
+    q, g = cfg["problems"][1], cfg["grid"]
+    p = Plan(q["families"], q["lam"], q["z"], 1e-12, precision="fp64", grid=g,
+             output="occulter")
+    assert p.info()["live_tile_rows"] == 1
+    u = p.eval().cpu().numpy()
+    v = Plan(q["families"], q["lam"], q["z"], 1e-12, precision="fp64", grid=g, output="occulter",
+             fft_split_above=256).eval().cpu().numpy()
+    assert rel_l2(1.0 - u, 1.0 - v) <= 1e-12
+    xi, eta = oracle.grid_targets(g["n1"], g["n2"], g["h"])
+    idx = W.rng(6, n).choice(len(xi), 300, replace=False)
+    ref = oracle.field(q["families"], q["lam"], q["z"], xi[idx], eta[idx])
+    assert rel_l2(1.0 - u.ravel()[idx], ref) <= 1e-10
+
