@@ -989,6 +989,26 @@ def randstar_arm(args, dev, local_rank, world, batch, steps, warmup, budget_s=10
         unbatched = {"ms_per_step": seq_ms, "value": total / (seq_ms * 1e-3),
                      "how": "the same %d instances as separate plans, evaluated one after "
                             "another on one stream" % len(problems)}
+        # the same batch with the upsampling factor 1.5 instead of 2 (the
+        # option fresnel_opts.sigma): 0.56 x the FFT cells for a wider
+        # kernel, and a larger FP32 error (the deconvolution amplifies the
+        # rounding more), so not the default
+        q15 = BatchPlan(problems, TOL, precision="fp32", box=box, recompute_nodes=True,
+                        sync_status=False, sigma=1.5)
+        out15 = torch.empty_like(out)
+        for _ in range(2):
+            q15.eval(t, counts, out15)
+        torch.cuda.synchronize()
+        s15 = statistics.median(time_steps(lambda: q15.eval(t, counts, out15), stream,
+                                           max(3, min(steps, 5))))
+        q15.check()
+        e15 = None
+        if local_rank == 0:
+            e15 = rel_error(out15[torch.as_tensor(gidx, device=dev)].cpu().numpy(), ref, TOL)
+        sigma15 = {"ms_per_step": s15, "value": total / (s15 * 1e-3), "error": e15,
+                   "kernel": {"w": q15.info()["w"], "sigma": q15.info()["sigma"]}}
+        q15.close()
+        del out15
     # end to end: host targets in, host fields out, inside the timed region
     h_out = torch.empty(total, dtype=torch.complex64, pin_memory=True)
     h_in = torch.from_numpy(h_t).pin_memory()
@@ -1041,6 +1061,7 @@ def randstar_arm(args, dev, local_rank, world, batch, steps, warmup, budget_s=10
            "gpu_launches": p.info()["launches_per_eval"] * steps, "clocks": clk, "steps": steps}
     if unbatched:
         res["unbatched"] = unbatched
+        res["sigma_1.5"] = sigma15
         res["batching_speedup"] = unbatched["ms_per_step"] / ms_per_step
     p.close()
     del t, out
